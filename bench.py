@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Throughput of the VMC hot path: walker-evaluations per second.
+
+A step is one measured sweep over all walkers of the workload: every electron of every
+walker attempts one Metropolis move (Sherman-Morrison update on acceptance), the inverses
+are rebuilt in FP64, and E_L, d ln Psi/dR, dE_L/dR and O are evaluated and accumulated into
+the walker sums behind E, the forces and dE/dC. value = walkers x steps / device time.
+
+Default workload: C2OH6 (26 electrons, 72 AOs, 9 nuclei), 16384 walkers per GPU, Gaussian
+step 0.3 bohr, re-inversion every 26 moves, mixed precision; the FP64 GPU path is timed on
+the same workload for comparison. Inputs are synthetic (seeded generator). L2 is flushed
+between timed steps (the walker state, 32 MB, would otherwise stay in the 129 MB L2).
+
+--impl reference times the CPU oracle (the plain FP64 C++ reference implementation) on
+the host cores, on a bounded sample of the same workload.
+Multi-GPU: launched by torch.distributed.run, one process per GPU; each rank owns its own
+walkers (weak scaling, no data-path collective); the timed region is bracketed by barriers
+and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+WORKLOADS = {
+    "c2oh6": dict(cfg=1, walkers=16384, name="C2OH6 all-electron, 26 e-, 72 AOs, 9 nuclei"),
+    "water": dict(cfg=0, walkers=1024, name="H2O all-electron, 10 e-, 24 AOs, 3 nuclei"),
+    "c9o4h8": dict(cfg=4, walkers=65536, name="C9O4H8 all-electron, 94 e-, 222 AOs, 21 nuclei"),
+}
+METRIC = "walker-evals/s (E_L+forces+dE/dC) at 26 e⁻, mixed vs FP64 GPU; % of roofline"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), ws, int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines: list[str] = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_steps(sysx, walkers: int, budget_s: float, max_s: float, key=(5222, 1)):
+    """Time the FP64 CPU oracle on `walkers` walkers of the workload: equilibrate briefly,
+    then measured sweeps (sweep + re-inversion + evaluation + walker sums) until budget_s."""
+    import oracle
+    from oracle import estimators
+    from paper_2511_05222_gb300 import systems as S
+    o = oracle.Oracle(sysx)
+    st = o.new_state(S.initial_walkers(sysx, walkers, seed=99), key=key)
+    o.sample(st, 2)
+    nb = 8
+    sums = estimators.new_sums(nb, sysx.K, o.nO)
+    blk = np.arange(walkers) * nb // walkers
+    t0 = time.perf_counter()
+    steps, per = 0, []
+    while True:
+        t1 = time.perf_counter()
+        o.sample(st, 1)
+        o.force_refresh(st)
+        out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+        estimators.accumulate(sums, blk, out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], -150.0)
+        per.append(time.perf_counter() - t1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or el + per[-1] > max_s:
+            break
+    return walkers * steps / sum(per), steps, sum(per)
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args, wl):
+    rank, ws, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2511_05222_gb300 import systems as S
+    sysx = S.make_system(wl["cfg"])
+    sample_w = 128 if wl["cfg"] != 4 else 8
+    vals = []
+    for _ in range(args.warmup):
+        oracle_steps(sysx, sample_w, 0.0, 1e9)
+    tot_w, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        v, n, t = oracle_steps(sysx, sample_w, 0.0, 1e9)
+        vals.append(v)
+        tot_w += sample_w * n
+        tot_t += t
+    value = tot_w / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "walker-evals/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "walkers_per_step": sample_w, "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "walker-evals/s", "cores": cores(), "kind": "oracle",
+                             "sample": f"{sample_w} walkers x 1 measured sweep per step"},
+            "e2e": {"value": value, "unit": "walker-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="vmcf", choices=["vmcf", "reference"])
+    ap.add_argument("--workload", default="c2oh6", choices=sorted(WORKLOADS))
+    ap.add_argument("--walkers", type=int, default=0, help="walkers per GPU (default: the workload's)")
+    ap.add_argument("--equil", type=int, default=10, help="unmeasured sweeps before the warm-up steps")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    from paper_2511_05222_gb300 import systems as S
+    from paper_2511_05222_gb300 import vmcf, workmodel
+
+    rank, ws, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    W = args.walkers or wl["walkers"]
+    sysx = S.make_system(wl["cfg"])
+    pos0 = S.initial_walkers(sysx, W, seed=rank)
+    nb = 64
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def timed_steps(wk, K, profile=False):
+        if profile:
+            wk.profile(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier()
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            wk.sample(1, 0.3, 26, measure=True, stream=stream)
+            b.record(stream)
+        barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        kt = wk.kernel_times(reset=True) if profile else None
+        if profile:
+            wk.profile(False)
+        return ms, kt
+
+    def prepare(precision):
+        g = vmcf.System(sysx, precision)
+        wk = vmcf.Walkers(g, pos0, key=(5222, 1), wid0=rank * W, nblocks=nb, stream=stream)
+        wk.sample(args.equil, 0.3, 26, measure=False, stream=stream)
+        p = torch.empty((W, sysx.Ne, 3), dtype=torch.float64, device=dev)
+        wk.positions_into(p, stream=stream)
+        el = vmcf.vmcf_evaluate(g, p, want=("EL",), stream=stream)["EL"]
+        wk.reset_accumulators(float(el.mean().item()), stream=stream)
+        return g, wk
+
+    peaks = vmcf.vmcf_probe_pipes(stream=stream)
+
+    # ---- mixed precision (headline)
+    g, wk = prepare(vmcf.MIXED)
+    for _ in range(args.warmup):
+        wk.sample(1, 0.3, 26, measure=True, stream=stream)
+    with ClockSampler(local) as clk:
+        ms, kt = timed_steps(wk, args.steps, profile=True)
+    ms = max_over_ranks(ms)
+    value = ws * W * args.steps / (ms * 1e-3)
+    cnt = wk.counters(stream=stream)
+    acc = cnt["accepted"] / max(1, cnt["moves"])
+    est = wk.reduce_estimators(stream=stream)
+
+    work = workmodel.per_walker_eval(sysx.K, g.M, sysx.n_up, sysx.n_dn, int(sysx.shell_nprim.sum()), acc)
+    dom = max(("move", "measure"), key=lambda k: kt[k]["ms"])
+    t_launch = kt[dom]["ms"] / max(1, kt[dom]["launches"]) * 1e-3
+    bound, t_roof_w = workmodel.roofline_time(work[dom], peaks)
+    pipe_flops = {"fp32": work[dom]["fp32"], "fp64": work[dom]["fp64"], "sfu": work[dom]["exp"]}[bound]
+    peak = {"fp32": peaks["fp32_tflops"], "fp64": peaks["fp64_tflops"], "sfu": peaks["exp_gops"] / 1e3}[bound]
+    achieved = pipe_flops * W / t_launch / 1e12
+    roofline = {"bound": "alu", "pipe": bound, "kernel": f"{dom}_kernel<float>", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s" if bound != "sfu" else "Texp/s", "frac": achieved / peak,
+                "peak_source": "measured in this run by vmcf_probe_pipes (register-only FMA/exp kernels)",
+                "traffic": None, "launch_ms": t_launch * 1e3,
+                "kernel_share": {k: kt[k]["ms"] / max(1e-9, sum(v["ms"] for v in kt.values())) for k in kt},
+                "whole_step_frac": workmodel.roofline_time(work["total"], peaks)[1] * W / (ms * 1e-3 / args.steps)}
+
+    line = {"metric": METRIC, "value": value, "unit": "walker-evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "walkers_per_gpu": W, "electrons": sysx.Ne, "aos": g.M,
+                       "step_sigma": 0.3, "refresh_every": 26, "precision": "mixed (FP32 + FP64 inverse/ratio/sums)",
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "roofline": roofline, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
+            "acceptance": acc, "estimates": {"E": est["E"], "E_err": est["E_err"]}}
+
+    # ---- FP64 GPU path on the same workload
+    if not args.no_fp64:
+        del wk, g
+        g64, wk64 = prepare(vmcf.FP64)
+        wk64.sample(1, 0.3, 26, measure=True, stream=stream)
+        k64 = max(2, args.steps // 4)
+        ms64, _ = timed_steps(wk64, k64)
+        ms64 = max_over_ranks(ms64)
+        v64 = ws * W * k64 / (ms64 * 1e-3)
+        line["fp64_gpu"] = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64}
+        line["mixed_over_fp64"] = value / v64
+        del wk64, g64
+
+    # ---- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        g, wk = prepare(vmcf.MIXED)
+        host = torch.empty((W, sysx.Ne, 3), dtype=torch.float64, pin_memory=True).numpy()
+        host[:] = wk.positions(stream=stream)
+        ke = max(2, args.steps // 2)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            wk.set_positions(host, stream=stream)          # H2D, inverses rebuilt
+            wk.sample(1, 0.3, 26, measure=True, stream=stream)
+            _ = wk.reduce_estimators(stream=stream)         # D2H block sums + host finish
+            host[:] = wk.positions(stream=stream)           # D2H positions for the next step
+        barrier()
+        te = max_over_ranks(time.perf_counter() - t0)
+        h2d = W * sysx.Ne * 3 * 8
+        d2h = W * sysx.Ne * 3 * 8 + nb * g.accL * 8
+        line["e2e"] = {"value": ws * W * ke / te, "unit": "walker-evals/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "steps": ke}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    if not args.no_cpu and ws == 1:
+        v, n, t = oracle_steps(sysx, 256 if wl["cfg"] != 4 else 16, 10.0, 30.0)
+        line["cpu_baseline"] = {"value": v, "unit": "walker-evals/s", "cores": cores(), "kind": "oracle",
+                                "sample": f"{256 if wl['cfg'] != 4 else 16} walkers x {n} measured sweeps "
+                                          f"({t:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

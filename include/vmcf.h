@@ -1,0 +1,183 @@
+/*
+ * vmcf — GB300-native VMC evaluation of a Jastrow x spin-block Slater wavefunction with
+ * frozen orbitals: local energy, Hellmann-Feynman + Pulay atomic forces and the
+ * orbital-coefficient gradient dE/dC, over many independent walkers.
+ *
+ * Method: arXiv:2511.05222, "Fast Evaluation of Unbiased Atomic Forces in ab initio
+ * Variational Monte Carlo via the Lagrangian Technique".
+ *   - wavefunction: App. A ("Wavefunction Ansatz"): Psi = exp(J) det A_up det A_dn, the
+ *     Jastrow-Slater determinant that the JAGP becomes when the geminal is expanded over
+ *     the occupied orbitals; MOs phi_i = sum_mu C_{mu i} psi_mu (Eq. restricted-C);
+ *     Pade two-body Jastrow (Eq. twobody_v) made spin dependent, plus the one-body
+ *     e-n cusp term chi_I(r) = -Z_I r / (1 + b r);
+ *   - local energy E_L = H Psi / Psi and the MCMC averages (App. A, Eq. eval-observable);
+ *   - forces F = -<dE_L/dR> - 2 <(E_L - E) d ln Psi / dR> (Eqs. hf, pulay); the
+ *     non-variational term (Eq. add) needs the CPKS response and is not computed here;
+ *   - dE/dC = 2 (<E_L O> - E <O>), O = d ln Psi / dC (App. A, Eq. fc-vmc-eval, whose
+ *     printed sign is the generalised-force convention -dE/dC);
+ *   - optional right-hand side -B Q of the Z-vector equations (Eqs. Q_projector,
+ *     AZ_eq_B_elements) when the AO overlap S is supplied;
+ *   - jackknife error bars over walker blocks (Sec. II, last paragraph).
+ *
+ * Conventions shared by every entry point:
+ *   - atomic units (bohr, hartree); row-major arrays; double precision at the boundary;
+ *   - every call returns a vmcf_status code; no exception crosses the boundary; the text
+ *     of the last error of the calling thread is returned by vmcf_last_error();
+ *   - "device" pointers are CUDA device (or managed) memory owned by the caller;
+ *     "host" pointers are host memory owned by the caller; the library copies what it
+ *     keeps and never frees a caller's pointer;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream);
+ *     calls are asynchronous on that stream unless stated otherwise;
+ *   - electrons are ordered spin up first: 0..n_up-1 up, n_up..n_up+n_dn-1 down.
+ *     Positions are [W][Ne][3]; O and dE/dC are [2 spin blocks] = [M][n_up] followed by
+ *     [M][n_dn] (compound index (mu i sigma) of the paper's App. B);
+ *   - AOs: real solid harmonics r^l Y_lm (unit-sphere normalised), p = (x, y, z),
+ *     d = (xy, yz, 3z^2 - r^2, xz, x^2 - y^2); each primitive normalised, then the
+ *     contraction renormalised; AOs are numbered shell by shell in input order.
+ */
+#ifndef VMCF_H
+#define VMCF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VMCF_OK = 0,
+  VMCF_EINVAL = -1,     /* bad argument (sizes, pointers, basis, NaN input) */
+  VMCF_ENOMEM = -2,     /* device or host allocation failed */
+  VMCF_ECUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+  VMCF_ESINGULAR = -4,  /* a Slater matrix had a zero pivot (walker on a node) */
+  VMCF_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+  VMCF_ENOTSUP = -6     /* configuration not supported by this build */
+} vmcf_status;
+
+typedef enum {
+  VMCF_FP64 = 0,  /* every step in double precision */
+  VMCF_MIXED = 1  /* FP32 AOs, MOs, Jastrow, adjoint and O; FP64 LU/inverse, ratio,
+                     refresh and walker sums */
+} vmcf_precision;
+
+typedef struct vmcf_system_s* vmcf_system_t;   /* opaque, library-owned */
+typedef struct vmcf_walkers_s* vmcf_walkers_t; /* opaque, library-owned device state */
+
+typedef struct {
+  int K;            /* number of nuclei, >= 1 */
+  const int* Z;     /* host [K], nuclear charges >= 1 */
+  const double* R;  /* host [K][3], positions */
+} vmcf_nuclei;
+
+typedef struct {
+  int nshell;           /* >= 1 */
+  int maxprim;          /* row stride of exps/coefs, 1..8 */
+  const int* center;    /* host [nshell], 0..K-1 */
+  const int* l;         /* host [nshell], 0..2 */
+  const int* nprim;     /* host [nshell], 1..maxprim */
+  const double* exps;   /* host [nshell][maxprim], > 0 */
+  const double* coefs;  /* host [nshell][maxprim], coefficients of normalised primitives */
+} vmcf_basis;
+
+typedef struct {
+  double F_anti, F_par; /* Pade denominators F (Eq. twobody_v); default 0.8, 0.8 */
+  double a_anti, a_par; /* Pade numerators; Kato cusps: 0.5 antiparallel, 0.25 parallel */
+  double b_en;          /* one-body chi_I(r) = -Z_I r / (1 + b_en r); default 1.5 */
+  int enable_J1;        /* one-body term on/off */
+  int enable_J2;        /* two-body term on/off */
+} vmcf_jastrow;
+
+typedef struct {
+  uint64_t moves;            /* attempted single-electron moves since creation */
+  uint64_t accepted;         /* accepted moves */
+  uint64_t rejected_nonfinite; /* moves rejected because the ratio was 0 or not finite */
+  uint64_t singular;         /* Slater inversions that met a zero pivot */
+  uint64_t refreshes;        /* full re-inversions performed (per walker, summed) */
+  uint64_t sweeps;           /* sweeps performed */
+  uint64_t measured_sweeps;  /* sweeps accumulated into the estimators */
+} vmcf_counters;
+
+/* Build a system: validates the input, normalises the basis, uploads tables and C.
+ * C_up [M][n_up], C_dn [M][n_dn]: host, double, row-major [mu][i] (M = number of AOs).
+ * S: host [M][M] AO overlap, or NULL (then rhs_BQ is unavailable).
+ * n_up >= n_dn >= 0, n_up >= 1, n_up <= 64, M <= 1024.
+ * The call synchronises the current device. */
+int vmcf_init_system(const vmcf_nuclei* nuclei, const vmcf_basis* basis, const double* C_up,
+                     const double* C_dn, int n_up, int n_dn, const vmcf_jastrow* jastrow,
+                     const double* S, int precision, vmcf_system_t* out);
+int vmcf_system_destroy(vmcf_system_t sys);
+/* Sizes of a system: number of nuclei, AOs, up and down electrons (any pointer may be NULL). */
+int vmcf_system_info(vmcf_system_t sys, int* K, int* M, int* n_up, int* n_dn);
+
+/* Walker state for sampling: positions, Slater inverses, counters, accumulators.
+ * pos: [W][Ne][3] double, device (is_host = 0) or host (is_host = 1) memory.
+ * key0, key1: Philox4x64-10 key; wid0: global id of walker 0 (Philox counter word 0), so
+ * that shards of one walker set on several GPUs draw the same streams as one GPU would.
+ * nblocks: jackknife blocks (contiguous walker groups), 2 <= nblocks <= W.
+ * The initial inverses are built (a full FP64 inversion) before the call returns. */
+int vmcf_walkers_create(vmcf_system_t sys, int W, const double* pos, int is_host, uint64_t key0,
+                        uint64_t key1, uint64_t wid0, int nblocks, void* stream, vmcf_walkers_t* out);
+int vmcf_walkers_destroy(vmcf_walkers_t wk);
+/* Replace the positions (device or host memory) and rebuild the inverses. */
+int vmcf_walkers_set_positions(vmcf_system_t sys, vmcf_walkers_t wk, const double* pos, int is_host,
+                               void* stream);
+/* Copy the current positions out ([W][Ne][3], device or host memory). */
+int vmcf_walkers_get_positions(vmcf_walkers_t wk, double* pos, int is_host, void* stream);
+/* Zero the estimator accumulators and set the reference energy subtracted from E_L
+ * before it multiplies d ln Psi / dR or O (cancellation control; results do not depend
+ * on it except by rounding). */
+int vmcf_reset_accumulators(vmcf_walkers_t wk, double e_ref, void* stream);
+
+/* Metropolis sweeps (App. A, MCMC). Each sweep moves every electron once, in order, with
+ * a Gaussian proposal of width step_sigma; the Philox counter is (walker id, sweep index,
+ * electron, 0) for the three normals (Box-Muller) and (..., 1) for the acceptance draw.
+ * Accepted moves update the inverse by Sherman-Morrison; every refresh_k attempted moves
+ * the inverses are rebuilt from scratch in FP64. measure != 0: after each sweep the
+ * inverse is rebuilt (if not fresh) and E_L, d ln Psi/dR, dE_L/dR and O are accumulated
+ * into the estimator sums. */
+int vmcf_sample(vmcf_system_t sys, vmcf_walkers_t wk, int n_sweeps, double step_sigma, int refresh_k,
+                int measure, void* stream);
+
+/* Fixed-walker evaluation (no sampling). pos: device [W][Ne][3]. Outputs are device
+ * buffers owned by the caller; any may be NULL:
+ *   EL [W], logpsi [W] (ln|Psi|), dlnpsi_dR [W][K][3], dEL_dR [W][K][3],
+ *   O [W][M*(n_up+n_dn)], dEL_dC [W][M*(n_up+n_dn)] (the explicit dE_L/dC, for tests). */
+int vmcf_evaluate(vmcf_system_t sys, const double* pos, int W, double* EL, double* logpsi,
+                  double* dlnpsi_dR, double* dEL_dR, double* O, double* dEL_dC, void* stream);
+
+/* Finish the estimators from the accumulated sums (synchronises the stream). Host outputs
+ * (any may be NULL): E, E_err (scalars), F, F_err [K][3], dEdC, dEdC_err [M*(n_up+n_dn)],
+ * rhs_BQ [M*(n_up+n_dn)] = -sum_mu B_{mu i} Q_{mu nu} (needs S at init, else VMCF_EINVAL).
+ * Error bars: delete-one-block jackknife over the walker blocks. */
+int vmcf_reduce_estimators(vmcf_system_t sys, vmcf_walkers_t wk, double* E, double* E_err, double* F,
+                           double* F_err, double* dEdC, double* dEdC_err, double* rhs_BQ, void* stream);
+/* Raw block sums (synchronises): host [nblocks][vmcf_accumulator_length()] doubles, layout
+ * n, sum E_L, sum E_L^2, sum dE_L/dR [3K], sum dlnPsi/dR [3K], sum (E_L-E_ref) dlnPsi/dR [3K],
+ * sum O [nO], sum (E_L-E_ref) O [nO], with nO = M (n_up + n_dn). */
+int vmcf_block_sums(vmcf_system_t sys, vmcf_walkers_t wk, double* out, void* stream);
+int vmcf_accumulator_length(vmcf_system_t sys);
+
+/* Counters (synchronises the stream). */
+int vmcf_status_counters(vmcf_walkers_t wk, vmcf_counters* out, void* stream);
+
+/* Diagnostics (not part of the paper's method).
+ * vmcf_profile: record a CUDA event pair around every kernel this walker set launches from
+ * now on (enable != 0) or stop recording (0).
+ * vmcf_kernel_times: synchronise on the recorded events and return the summed device time
+ * in ms and the launch count per kernel kind: [0] Metropolis sweep kernel, [1] measurement
+ * kernel, [2] refresh kernel (host arrays of 3; either may be NULL); reset != 0 zeroes the
+ * totals afterwards.
+ * vmcf_probe_pipes: measure this GPU's FP64 FMA and FP32 FMA throughput (TFLOP/s) and FP32
+ * expf throughput (G/s) with short register-only kernels on `stream` (synchronises; about
+ * 30 ms). Used as the measured ALU peaks of the roofline. */
+int vmcf_profile(vmcf_walkers_t wk, int enable);
+int vmcf_kernel_times(vmcf_walkers_t wk, double* ms, long long* count, int reset);
+int vmcf_probe_pipes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, void* stream);
+
+const char* vmcf_strerror(int status);
+const char* vmcf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VMCF_H */

@@ -1,0 +1,73 @@
+"""Build libvmcf.so (the C-ABI library) in-tree with nvcc for sm_103a.
+
+Translation units are compiled in parallel and linked into
+paper_2511_05222_gb300/_build/libvmcf.so. A rebuild happens only when a source is newer
+than the library.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+from pathlib import Path
+
+PKG = Path(__file__).resolve().parent
+SRC = PKG / "csrc"
+INC = PKG.parent / "include"
+OUT_DIR = PKG / "_build"
+LIB = OUT_DIR / "libvmcf.so"
+UNITS = ["vmcf_api.cu", "k_fp64.cu", "k_fp32.cu", "k_reduce.cu", "k_probe.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and Path(cand).exists():
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libvmcf")
+
+
+def _sources():
+    return [SRC / u for u in UNITS] + sorted(SRC.glob("*.cuh")) + sorted(SRC.glob("*.h")) + sorted(INC.glob("*.h"))
+
+
+def up_to_date() -> bool:
+    if not LIB.exists():
+        return False
+    t = LIB.stat().st_mtime
+    return all(p.stat().st_mtime <= t for p in _sources())
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> Path:
+    if not force and up_to_date():
+        return LIB
+    OUT_DIR.mkdir(exist_ok=True)
+    cc = nvcc()
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(INC)] + (extra_flags or [])
+    tag = f"{os.getpid()}"
+
+    def compile_unit(u: str) -> Path:
+        obj = OUT_DIR / (Path(u).stem + f".{tag}.o")
+        cmd = [cc, *flags, "-c", str(SRC / u), "-o", str(obj)]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {u}:\n{r.stderr}")
+        if verbose and r.stderr:
+            print(r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+        objs = list(ex.map(compile_unit, UNITS))
+    tmp = OUT_DIR / f"libvmcf.{tag}.so"
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs)], capture_output=True, text=True)
+    for o in objs:
+        o.unlink(missing_ok=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose=True))

@@ -1,0 +1,585 @@
+// Kernels of the VMC hot path (arXiv:2511.05222, App. A), templated on the arithmetic type
+// T (double: FP64 mode; float: mixed mode) and the walker-group size GS.
+//
+//  refresh_kernel  fresh FP64 Slater inverses from positions
+//  move_kernel     Metropolis sweeps with Sherman-Morrison updates and periodic refresh
+//  measure_kernel  fresh inverse, E_L, adjoint nuclear derivatives, O = dlnPsi/dC, and
+//                  either per-walker outputs or the walker sums behind E, F and dE/dC
+#pragma once
+#include "vmcf_device.cuh"
+#include "vmcf_internal.h"
+
+namespace vmcf {
+
+template <typename T>
+__device__ __forceinline__ T* sm_ptr(unsigned char* base, int off) {
+  return reinterpret_cast<T*>(base + off);
+}
+
+// Positions to shared memory: double, plus the float-float split used by mixed mode.
+template <int GS>
+__device__ __forceinline__ void load_positions(const double* src, int n3, double* pos, float* ph, float* pl) {
+  const int t = threadIdx.x % GS;
+  for (int i = t; i < n3; i += GS) {
+    const double v = src[i];
+    pos[i] = v;
+    const float h = (float)v;
+    ph[i] = h;
+    pl[i] = (float)(v - (double)h);
+  }
+}
+
+// Rebuild the inverses of both spin blocks of one walker into B (T) from positions.
+template <typename T, int GS>
+__device__ void refresh_walker(const DevSys& S, const double* pos, T* B, double* A, T* ao, int* piv, double* f,
+                               int* flag) {
+  const int t = threadIdx.x % GS;
+  for (int sg = 0; sg < 2; ++sg) {
+    const int n = sg == 0 ? S.nup : S.ndn;
+    if (n == 0) continue;
+    build_slater<T, GS>(S, pos, sg, A, ao);
+    double la = 0.0, sgn = 1.0;
+    gj_inverse<GS>(A, n, piv, f, flag, &la, &sgn, false);
+    T* Bs = B + (sg == 0 ? 0 : S.nup * S.nup);
+    for (int idx = t; idx < n * n; idx += GS) Bs[idx] = (T)A[idx];
+    gsync<GS>();
+  }
+}
+
+// ---------------------------------------------------------------- refresh
+template <typename T, int GS>
+__global__ void __launch_bounds__(128) refresh_kernel(DevSys S, GroupLayout L, const double* __restrict__ pos_g,
+                                                      T* __restrict__ B_g, int W, unsigned long long* counters) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int gpb = blockDim.x / GS, gid = threadIdx.x / GS, t = threadIdx.x % GS;
+  unsigned char* base = smem + gid * L.bytes;
+  double* pos = sm_ptr<double>(base, L.pos);
+  double* A = sm_ptr<double>(base, L.Bd);
+  T* ao = sm_ptr<T>(base, L.ao);
+  T* B = sm_ptr<T>(base, L.Bt);
+  int* piv = sm_ptr<int>(base, L.piv);
+  double* f = sm_ptr<double>(base, L.f);
+  int* flag = sm_ptr<int>(base, L.scal);
+  const int w = blockIdx.x * gpb + gid;
+  if (w >= W) return;  // the whole group leaves together; only group barriers are used
+  const int Ne = S.Ne;
+  for (int i = t; i < 3 * Ne; i += GS) pos[i] = pos_g[(size_t)w * 3 * Ne + i];
+  if (t == 0) *flag = 0;
+  gsync<GS>();
+  refresh_walker<T, GS>(S, pos, B, A, ao, piv, f, flag);
+  for (int i = t; i < S.nB; i += GS) B_g[(size_t)w * S.nB + i] = B[i];
+  if (t == 0) {
+    if (*flag) atomicAdd(&counters[0], 1ull);
+    atomicAdd(&counters[1], 1ull);
+  }
+}
+
+// ---------------------------------------------------------------- Metropolis sweeps
+template <typename T, int GS>
+__global__ void __launch_bounds__(128) move_kernel(DevSys S, GroupLayout L, MoveParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int gpb = blockDim.x / GS, gid = threadIdx.x / GS, t = threadIdx.x % GS;
+  unsigned char* base = smem + gid * L.bytes;
+  double* pos = sm_ptr<double>(base, L.pos);
+  float* ph = sm_ptr<float>(base, L.ph);
+  float* pl = sm_ptr<float>(base, L.pl);
+  double* A = sm_ptr<double>(base, L.Bd);
+  T* B = sm_ptr<T>(base, L.Bt);
+  T* ao = sm_ptr<T>(base, L.ao);
+  T* row = sm_ptr<T>(base, L.row);
+  T* wv = sm_ptr<T>(base, L.wv);
+  T* col = sm_ptr<T>(base, L.col);
+  int* piv = sm_ptr<int>(base, L.piv);
+  double* f = sm_ptr<double>(base, L.f);
+  double* red = sm_ptr<double>(base, L.red);
+  int* flag = sm_ptr<int>(base, L.scal);
+  const int w = blockIdx.x * gpb + gid;
+  if (w >= P.W) return;
+  const int Ne = S.Ne, nup = S.nup, K = S.K;
+  double* posg = P.pos + (size_t)w * 3 * Ne;
+  T* Bg = reinterpret_cast<T*>(P.B) + (size_t)w * S.nB;
+  load_positions<GS>(posg, 3 * Ne, pos, ph, pl);
+  for (int i = t; i < S.nB; i += GS) B[i] = Bg[i];
+  if (t == 0) *flag = 0;
+  gsync<GS>();
+  const uint64_t wid = P.wid0 + (uint64_t)w;
+  int c = P.c0;
+  uint32_t nacc = 0, nrej = 0, nref = 0;
+  for (int sw = 0; sw < P.nsweeps; ++sw) {
+    const uint64_t sweep = P.sweep0 + (uint64_t)sw;
+    for (int e = 0; e < Ne; ++e) {
+      const int sg = e < nup ? 0 : 1;
+      const int n = sg == 0 ? nup : S.ndn, el = e - (sg == 0 ? 0 : nup);
+      T* Bs = B + (sg == 0 ? 0 : nup * nup);
+      const T* C = coefC<T>(S, sg);
+      uint64_t r[4] = {wid, sweep, (uint64_t)e, 0};
+      philox4x64_10(r, P.k0, P.k1);
+      double xi[3];
+      normals3(r, xi, T(0));
+      const double rn[3] = {pos[3 * e] + P.sigma * xi[0], pos[3 * e + 1] + P.sigma * xi[1],
+                            pos[3 * e + 2] + P.sigma * xi[2]};
+      const EPos pn = make_epos(rn);
+      const EPos po = make_epos(pos + 3 * e);
+      ao_point<T, GS, 0, false>(S, pn, ao, 0);
+      gsync<GS>();
+      double part[2] = {0.0, 0.0};
+      for (int i = t; i < n; i += GS) {
+        T v = 0;
+        for (int mu = 0; mu < S.M; ++mu) v += ao[mu] * __ldg(C + mu * n + i);
+        row[i] = v;
+        part[0] += (double)v * (double)Bs[i * n + el];
+      }
+      // Jastrow ratio: pairs with every other electron, and the e-n terms
+      for (int q = t; q < Ne + K; q += GS) {
+        if (q < Ne) {
+          if (q == e || !S.J2) continue;
+          const bool par = (q < nup) == (e < nup);
+          const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+          T d1[3], d0[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            if constexpr (sizeof(T) == 8) {
+              d1[k] = rn[k] - pos[3 * q + k];
+              d0[k] = pos[3 * e + k] - pos[3 * q + k];
+            } else {
+              d1[k] = (pn.h[k] - ph[3 * q + k]) + (pn.l[k] - pl[3 * q + k]);
+              d0[k] = (po.h[k] - ph[3 * q + k]) + (po.l[k] - pl[3 * q + k]);
+            }
+          }
+          part[1] += (double)(pade_value<T>(a, F, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
+                              pade_value<T>(a, F, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2])));
+        } else {
+          if (!S.J1) continue;
+          const int I = q - Ne;
+          const T mz = (T)(-__ldg(S.Z + I)), b = (T)S.ben;
+          T d1[3], d0[3];
+          disp_nuc<T>(S, pn, I, d1);
+          disp_nuc<T>(S, po, I, d0);
+          part[1] += (double)(pade_value<T>(mz, b, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
+                              pade_value<T>(mz, b, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2])));
+        }
+      }
+      gsync<GS>();
+      group_sum<GS, 2>(part, red);
+      const double R = part[0];
+      uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
+      philox4x64_10(r2, P.k0, P.k1);
+      const double u = u01(r2[0]);
+      const double pr = R * R * (double)dexp<T>((T)(2.0 * part[1]));
+      const bool ok = isfinite(pr) && R != 0.0;
+      if (!ok) ++nrej;
+      if (ok && u < pr) {
+        // Sherman-Morrison: row el of A becomes `row`; with w_j = sum_i row_i B_ij - delta_j,el,
+        // B_kj <- B_kj - B_k,el w_j / R.
+        for (int j = t; j < n; j += GS) {
+          T v = 0;
+          for (int i = 0; i < n; ++i) v += row[i] * Bs[i * n + j];
+          wv[j] = v - (j == el ? T(1) : T(0));
+          col[j] = Bs[j * n + el];
+        }
+        gsync<GS>();
+        const T rinv = (T)(1.0 / R);
+        for (int idx = t; idx < n * n; idx += GS) {
+          const int k = idx / n, j = idx - k * n;
+          Bs[idx] -= col[k] * wv[j] * rinv;
+        }
+        if (t < 3) {
+          pos[3 * e + t] = rn[t];
+          ph[3 * e + t] = pn.h[t];
+          pl[3 * e + t] = pn.l[t];
+        }
+        ++nacc;
+        gsync<GS>();
+      }
+      if (++c == P.kref) {
+        const bool last = (sw == P.nsweeps - 1) && (e == Ne - 1);
+        if (!(last && P.skip_final_refresh)) {
+          refresh_walker<T, GS>(S, pos, B, A, ao, piv, f, flag);
+          ++nref;
+        }
+        c = 0;
+      }
+    }
+  }
+  gsync<GS>();
+  for (int i = t; i < 3 * Ne; i += GS) posg[i] = pos[i];
+  for (int i = t; i < S.nB; i += GS) Bg[i] = B[i];
+  if (t == 0) {
+    P.nacc[w] += nacc;
+    P.nrej[w] += nrej;
+    if (*flag) atomicAdd(&P.counters[0], 1ull);
+    if (nref) atomicAdd(&P.counters[1], (unsigned long long)nref);
+  }
+}
+
+// ---------------------------------------------------------------- measurement
+template <typename T, int GS>
+__device__ void measure_walker(const DevSys& S, const GroupLayout& L, const MeasParams& P, unsigned char* base,
+                               T* acc_s, double* acc_g, int w) {
+  const int t = threadIdx.x % GS;
+  const int Ne = S.Ne, nup = S.nup, K = S.K, M = S.M, nmax = S.nmax;
+  double* pos = sm_ptr<double>(base, L.pos);
+  float* ph = sm_ptr<float>(base, L.ph);
+  float* pl = sm_ptr<float>(base, L.pl);
+  double* Bd = sm_ptr<double>(base, L.Bd);
+  T* Bt = sm_ptr<T>(base, L.Bt);
+  T* Pm = sm_ptr<T>(base, L.P);
+  T* Q = sm_ptr<T>(base, L.Q);
+  T* Jg = sm_ptr<T>(base, L.Jg);
+  T* Jl = sm_ptr<T>(base, L.Jl);
+  T* gd = sm_ptr<T>(base, L.gd);
+  T* ao = sm_ptr<T>(base, L.ao);
+  T* mo = sm_ptr<T>(base, L.mo);
+  T* frc = sm_ptr<T>(base, L.frc);  // [0,3K) d ln Psi/dR, [3K,6K) dE_L/dR
+  T* Ow = sm_ptr<T>(base, L.Ow);
+  T* D = sm_ptr<T>(base, L.D);
+  int* piv = sm_ptr<int>(base, L.piv);
+  double* f = sm_ptr<double>(base, L.f);
+  double* red = sm_ptr<double>(base, L.red);
+  int* flag = sm_ptr<int>(base, L.scal);
+  double* la = sm_ptr<double>(base, L.scal + 8);
+  double* sgn = sm_ptr<double>(base, L.scal + 16);
+  const bool want_dC = P.dELdC != nullptr;
+
+  load_positions<GS>(P.pos + (size_t)w * 3 * Ne, 3 * Ne, pos, ph, pl);
+  for (int i = t; i < 6 * K; i += GS) frc[i] = T(0);
+  if (t == 0) {
+    *flag = 0;
+    *la = 0.0;
+    *sgn = 1.0;
+  }
+  gsync<GS>();
+
+  // Jastrow gradient/Laplacian per electron, Jastrow value and potentials.
+  double vs[3] = {0.0, 0.0, 0.0};  // V_ee, V_en, J
+  for (int e = t; e < Ne; e += GS) {
+    T jg0 = 0, jg1 = 0, jg2 = 0, jl = 0;
+    const bool up = e < nup;
+    for (int j = 0; j < Ne; ++j) {
+      if (j == e) continue;
+      const T dx = edisp<T>(pos, ph, pl, e, j, 0), dy = edisp<T>(pos, ph, pl, e, j, 1),
+              dz = edisp<T>(pos, ph, pl, e, j, 2);
+      const T r = dsqrt<T>(dx * dx + dy * dy + dz * dz), ri = T(1) / r;
+      if (j > e) vs[0] += (double)ri;
+      if (S.J2) {
+        const bool par = (j < nup) == up;
+        const Rad3<T> u = pade<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), r);
+        const T gr = u.h1 * ri;
+        jg0 += gr * dx;
+        jg1 += gr * dy;
+        jg2 += gr * dz;
+        jl += u.h2 + T(2) * u.h1 * ri;
+        if (j > e) vs[2] += (double)u.h;
+      }
+    }
+    const EPos pe = make_epos(pos + 3 * e);
+    for (int I = 0; I < K; ++I) {
+      T dd[3];
+      disp_nuc<T>(S, pe, I, dd);
+      const T dx = dd[0], dy = dd[1], dz = dd[2];
+      const T r = dsqrt<T>(dx * dx + dy * dy + dz * dz), ri = T(1) / r;
+      const T Z = (T)S.Z[I];
+      vs[1] -= (double)(Z * ri);
+      if (S.J1) {
+        const Rad3<T> c = pade<T>(-Z, (T)S.ben, r);
+        const T gr = c.h1 * ri;
+        jg0 += gr * dx;
+        jg1 += gr * dy;
+        jg2 += gr * dz;
+        jl += c.h2 + T(2) * c.h1 * ri;
+        vs[2] += (double)c.h;
+      }
+    }
+    Jg[3 * e] = jg0;
+    Jg[3 * e + 1] = jg1;
+    Jg[3 * e + 2] = jg2;
+    Jl[e] = jl;
+  }
+  gsync<GS>();
+  group_sum<GS, 3>(vs, red);
+
+  // Pass 1: Slater matrices (T) and their FP64 inverses.
+  for (int sg = 0; sg < 2; ++sg) {
+    const int n = sg == 0 ? nup : S.ndn;
+    if (n == 0) continue;
+    double* A = Bd + (sg == 0 ? 0 : nup * nup);
+    build_slater<T, GS>(S, pos, sg, A, ao);
+    gj_inverse<GS>(A, n, piv, f, flag, la, sgn, P.logpsi != nullptr);
+  }
+  if (static_cast<void*>(Bt) != static_cast<void*>(Bd)) {
+    for (int i = t; i < S.nB; i += GS) Bt[i] = (T)Bd[i];
+  }
+  gsync<GS>();
+
+  // Pass 2: gradient and Laplacian rows of the MOs per electron; determinant drift
+  // g_e = sum_i G_ei B_ie, l_e = sum_i L_ei B_ie; P_ei = L_ei + 2 gradJ_e . G_ei;
+  // kinetic term -1/2 (l_e + lap J_e + |grad J_e|^2 + 2 grad J_e . g_e).
+  double ekin = 0.0;
+  for (int e = 0; e < Ne; ++e) {
+    const int sg = e < nup ? 0 : 1;
+    const int n = sg == 0 ? nup : S.ndn, el = e - (sg == 0 ? 0 : nup), off = sg == 0 ? 0 : nup * nup;
+    const T* Bs = Bt + off;
+    const T* C = coefC<T>(S, sg);
+    ao_point<T, GS, 1, true>(S, make_epos(pos + 3 * e), ao, M);
+    gsync<GS>();
+    for (int q = t; q < 4 * n; q += GS) {
+      const int c = q / n, i = q - c * n;
+      const T* a = ao + c * M;
+      T v = 0;
+      for (int mu = 0; mu < M; ++mu) v += a[mu] * __ldg(C + mu * n + i);
+      mo[c * nmax + i] = v;
+    }
+    gsync<GS>();
+    double part[4] = {0.0, 0.0, 0.0, 0.0};
+    const T j0 = Jg[3 * e], j1 = Jg[3 * e + 1], j2 = Jg[3 * e + 2];
+    for (int i = t; i < n; i += GS) {
+      const T b = Bs[i * n + el];
+      const T g0 = mo[i], g1 = mo[nmax + i], g2 = mo[2 * nmax + i], lp = mo[3 * nmax + i];
+      part[0] += (double)(g0 * b);
+      part[1] += (double)(g1 * b);
+      part[2] += (double)(g2 * b);
+      part[3] += (double)(lp * b);
+      Pm[off + el * n + i] = lp + T(2) * (j0 * g0 + j1 * g1 + j2 * g2);
+    }
+    group_sum<GS, 4>(part, red);
+    if (t == 0) {
+      gd[3 * e] = (T)part[0];
+      gd[3 * e + 1] = (T)part[1];
+      gd[3 * e + 2] = (T)part[2];
+    }
+    const double jj = (double)j0 * j0 + (double)j1 * j1 + (double)j2 * j2;
+    const double jgd = (double)j0 * part[0] + (double)j1 * part[1] + (double)j2 * part[2];
+    ekin += -0.5 * (part[3] + (double)Jl[e] + jj + 2.0 * jgd);
+    gsync<GS>();
+  }
+  const double EL = ekin + vs[0] + vs[1] + S.Vnn;
+  const double cw = EL - P.e_ref;
+
+  // Pass 3, per spin: X = B P B (adjoint weight of A), Y = C X^T and C B back-projected
+  // per AO; nuclear derivatives from the recomputed AO gradient, Hessian and gradient of
+  // the Laplacian; O_{mu i} = sum_e psi_mu(r_e) B_ie.
+  const int nO = M * (nup + S.ndn);
+  for (int sg = 0; sg < 2; ++sg) {
+    const int n = sg == 0 ? nup : S.ndn;
+    if (n == 0) continue;
+    const int e0 = sg == 0 ? 0 : nup, off = sg == 0 ? 0 : nup * nup, ooff = sg == 0 ? 0 : M * nup;
+    const T* Bs = Bt + off;
+    T* Ps = Pm + off;
+    const T* C = coefC<T>(S, sg);
+    for (int idx = t; idx < n * n; idx += GS) {  // Q = B P
+      const int i = idx / n, j = idx - i * n;
+      T v = 0;
+      for (int e = 0; e < n; ++e) v += Bs[i * n + e] * Ps[e * n + j];
+      Q[idx] = v;
+    }
+    for (int idx = t; idx < M * n; idx += GS) {
+      Ow[idx] = T(0);
+      if (want_dC) D[idx] = T(0);
+    }
+    gsync<GS>();
+    for (int idx = t; idx < n * n; idx += GS) {  // X[e][i] = (B P B)_{i e}, over P
+      const int e = idx / n, i = idx - e * n;
+      T v = 0;
+      for (int j = 0; j < n; ++j) v += Q[i * n + j] * Bs[j * n + e];
+      Ps[idx] = v;
+    }
+    gsync<GS>();
+    for (int el = 0; el < n; ++el) {
+      const int e = e0 + el;
+      const EPos pe = make_epos(pos + 3 * e);
+      ao_point<T, GS, 2, true>(S, pe, ao, M);
+      gsync<GS>();
+      const T j0 = Jg[3 * e], j1 = Jg[3 * e + 1], j2 = Jg[3 * e + 2];
+      for (int mu = t; mu < M; mu += GS) {
+        T yA = 0, yL = 0;
+        const T* Cr = C + mu * n;
+        for (int i = 0; i < n; ++i) {
+          const T cmi = __ldg(Cr + i);
+          yA += cmi * Ps[el * n + i];
+          yL += cmi * Bs[i * n + el];
+        }
+        const T v = ao[mu], g0 = ao[M + mu], g1 = ao[2 * M + mu], g2 = ao[3 * M + mu], lp = ao[4 * M + mu];
+        const T hxx = ao[5 * M + mu], hyy = ao[6 * M + mu], hzz = ao[7 * M + mu];
+        const T hxy = ao[8 * M + mu], hxz = ao[9 * M + mu], hyz = ao[10 * M + mu];
+        const T l0 = ao[11 * M + mu], l1 = ao[12 * M + mu], l2 = ao[13 * M + mu];
+        const T hj0 = hxx * j0 + hxy * j1 + hxz * j2;
+        const T hj1 = hxy * j0 + hyy * j1 + hyz * j2;
+        const T hj2 = hxz * j0 + hyz * j1 + hzz * j2;
+        const int I = __ldg(S.ao_center + mu);
+        atomicAdd(&frc[3 * I + 0], -g0 * yL);
+        atomicAdd(&frc[3 * I + 1], -g1 * yL);
+        atomicAdd(&frc[3 * I + 2], -g2 * yL);
+        atomicAdd(&frc[3 * K + 3 * I + 0], T(-0.5) * (g0 * yA - yL * (l0 + T(2) * hj0)));
+        atomicAdd(&frc[3 * K + 3 * I + 1], T(-0.5) * (g1 * yA - yL * (l1 + T(2) * hj1)));
+        atomicAdd(&frc[3 * K + 3 * I + 2], T(-0.5) * (g2 * yA - yL * (l2 + T(2) * hj2)));
+        const T tdc = lp + T(2) * (j0 * g0 + j1 * g1 + j2 * g2);
+        for (int i = 0; i < n; ++i) {
+          const T b = Bs[i * n + el];
+          Ow[mu * n + i] += v * b;
+          if (want_dC) D[mu * n + i] += b * tdc;
+        }
+      }
+      gsync<GS>();
+      // e-n Jastrow and V_en terms, one nucleus per thread
+      for (int I = t; I < K; I += GS) {
+        T sd[3];
+        disp_nuc<T>(S, pe, I, sd);
+        const T sx = sd[0], sy = sd[1], sz = sd[2];
+        const T r = dsqrt<T>(sx * sx + sy * sy + sz * sz), ri = T(1) / r;
+        const T Z = (T)S.Z[I];
+        const T sv[3] = {sx, sy, sz};
+        const T nn[3] = {sx * ri, sy * ri, sz * ri};
+        const T ven = -Z * ri * ri * ri;
+        for (int d = 0; d < 3; ++d) frc[3 * K + 3 * I + d] += ven * sv[d];
+        if (S.J1) {
+          const Rad3<T> c = pade<T>(-Z, (T)S.ben, r);
+          const T gsum[3] = {gd[3 * e] + Jg[3 * e], gd[3 * e + 1] + Jg[3 * e + 1], gd[3 * e + 2] + Jg[3 * e + 2]};
+          const T dl = c.h3 + T(2) * c.h2 * ri - T(2) * c.h1 * ri * ri;
+          for (int d = 0; d < 3; ++d) {
+            T hs = 0;
+            for (int cc = 0; cc < 3; ++cc)
+              hs += (c.h2 * nn[d] * nn[cc] + c.h1 * ri * ((d == cc ? T(1) : T(0)) - nn[d] * nn[cc])) * gsum[cc];
+            frc[3 * I + d] += -c.h1 * nn[d];
+            frc[3 * K + 3 * I + d] += hs + T(0.5) * dl * nn[d];
+          }
+        }
+      }
+      gsync<GS>();
+    }
+    // this spin's O (and explicit dE_L/dC): outputs and walker sums
+    const int oo = 3 + 9 * K;
+    for (int idx = t; idx < M * n; idx += GS) {
+      const T o = Ow[idx];
+      if (P.O) P.O[(size_t)w * nO + ooff + idx] = (double)o;
+      if (want_dC) {
+        const int mu = idx / n, i = idx - mu * n;
+        T q = 0;
+        for (int j = 0; j < n; ++j) q += Ow[mu * n + j] * Q[i * n + j];
+        P.dELdC[(size_t)w * nO + ooff + idx] = -0.5 * ((double)D[idx] - (double)q);
+      }
+      if (acc_s) {
+        atomicAdd(&acc_s[oo + ooff + idx], o);
+        atomicAdd(&acc_s[oo + nO + ooff + idx], (T)cw * o);
+      } else if (acc_g) {
+        acc_g[oo + ooff + idx] += (double)o;
+        acc_g[oo + nO + ooff + idx] += cw * (double)o;
+      }
+    }
+    gsync<GS>();
+  }
+
+  // per-walker outputs and scalar / force sums
+  for (int i = t; i < 3 * K; i += GS) {
+    const double dl = (double)frc[i];
+    const double de = (double)frc[3 * K + i] + __ldg(S.dVnn + i);
+    if (P.dlnpsi) P.dlnpsi[(size_t)w * 3 * K + i] = dl;
+    if (P.dEL) P.dEL[(size_t)w * 3 * K + i] = de;
+    if (acc_s) {
+      atomicAdd(&acc_s[3 + i], (T)de);
+      atomicAdd(&acc_s[3 + 3 * K + i], (T)dl);
+      atomicAdd(&acc_s[3 + 6 * K + i], (T)(cw * dl));
+    } else if (acc_g) {
+      acc_g[3 + i] += de;
+      acc_g[3 + 3 * K + i] += dl;
+      acc_g[3 + 6 * K + i] += cw * dl;
+    }
+  }
+  if (t == 0) {
+    if (P.EL) P.EL[w] = EL;
+    if (P.logpsi) P.logpsi[w] = *la + vs[2];
+    if (acc_s) {
+      atomicAdd(&acc_s[0], T(1));
+      atomicAdd(&acc_s[1], (T)cw);
+      atomicAdd(&acc_s[2], (T)(cw * cw));
+    } else if (acc_g) {
+      acc_g[0] += 1.0;
+      acc_g[1] += EL;
+      acc_g[2] += EL * EL;
+    }
+    if (*flag) atomicAdd(&P.counters[0], 1ull);
+  }
+  if (P.Bout) {
+    T* Bg = reinterpret_cast<T*>(P.Bout) + (size_t)w * S.nB;
+    for (int i = t; i < S.nB; i += GS) Bg[i] = Bt[i];
+  }
+  gsync<GS>();
+}
+
+// CTA c handles walkers [W c / grid, W (c+1) / grid); its groups take them in turn. Walker
+// sums go to a CTA shared-memory accumulator (several groups per CTA) or straight to the
+// CTA's FP64 slot (one group per CTA), and the slot is only ever touched by its CTA.
+// In the shared accumulator, acc[1] and acc[2] hold sums of (E_L - E_ref) and its square;
+// they are turned into sums of E_L and E_L^2 when the CTA flushes.
+template <typename T, int GS>
+__global__ void __launch_bounds__(128) measure_kernel(DevSys S, GroupLayout L, MeasParams P, int acc_off) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int gpb = blockDim.x / GS, gid = threadIdx.x / GS;
+  unsigned char* base = smem + gid * L.bytes;
+  T* acc_s = (P.acc && P.acc_in_smem) ? sm_ptr<T>(smem, acc_off) : nullptr;
+  double* acc_g = (P.acc && !P.acc_in_smem) ? P.acc + (size_t)blockIdx.x * P.accL : nullptr;
+  if (acc_s) {
+    for (int i = threadIdx.x; i < P.accL; i += blockDim.x) acc_s[i] = T(0);
+    __syncthreads();
+  }
+  const long long w0 = (long long)P.W * blockIdx.x / gridDim.x;
+  const long long w1 = (long long)P.W * (blockIdx.x + 1) / gridDim.x;
+  for (long long w = w0 + gid; w < w1; w += gpb) measure_walker<T, GS>(S, L, P, base, acc_s, acc_g, (int)w);
+  if (acc_s) {
+    __syncthreads();
+    double* slot = P.acc + (size_t)blockIdx.x * P.accL;
+    const double cnt = (double)acc_s[0];
+    for (int i = threadIdx.x; i < P.accL; i += blockDim.x) {
+      double v = (double)acc_s[i];
+      if (i == 2) v = v + 2.0 * P.e_ref * (double)acc_s[1] + cnt * P.e_ref * P.e_ref;
+      if (i == 1) v = v + cnt * P.e_ref;
+      slot[i] += v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+cudaError_t set_smem_limits_impl() {
+  const int lim = 227 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(refresh_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(refresh_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(move_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(move_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_refresh_impl(const DevSys& S, const Launch& lc, const double* pos, void* B, int W,
+                                unsigned long long* counters, cudaStream_t st) {
+  const dim3 grid(lc.grid), block(lc.GS * lc.groups);
+  if (lc.GS == 32)
+    refresh_kernel<T, 32><<<grid, block, lc.smem, st>>>(S, lc.L, pos, reinterpret_cast<T*>(B), W, counters);
+  else
+    refresh_kernel<T, 128><<<grid, block, lc.smem, st>>>(S, lc.L, pos, reinterpret_cast<T*>(B), W, counters);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_move_impl(const DevSys& S, const Launch& lc, const MoveParams& P, cudaStream_t st) {
+  const dim3 grid(lc.grid), block(lc.GS * lc.groups);
+  if (lc.GS == 32)
+    move_kernel<T, 32><<<grid, block, lc.smem, st>>>(S, lc.L, P);
+  else
+    move_kernel<T, 128><<<grid, block, lc.smem, st>>>(S, lc.L, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_measure_impl(const DevSys& S, const Launch& lc, const MeasParams& P, cudaStream_t st) {
+  const dim3 grid(lc.grid), block(lc.GS * lc.groups);
+  if (lc.GS == 32)
+    measure_kernel<T, 32><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
+  else
+    measure_kernel<T, 128><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
+  return cudaGetLastError();
+}
+
+}  // namespace vmcf

@@ -1,0 +1,800 @@
+// Host side of the C ABI declared in include/vmcf.h: input validation, basis
+// normalisation, device tables, launch planning, the sampling loop and the estimator finish.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/vmcf.h"
+#include "vmcf_internal.h"
+
+using namespace vmcf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return VMCF_ECUDA;
+}
+
+#define VMCF_CUDA(call)                                  \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call);  \
+  } while (0)
+
+int align16(int x) { return (x + 15) & ~15; }
+
+constexpr int kSmemCap = 227 * 1024;
+constexpr double kSharpAlpha = 48.0;
+
+}  // namespace
+
+struct vmcf_system_s {
+  int precision = 0;
+  int K = 0, M = 0, nup = 0, ndn = 0, Ne = 0, nshell = 0, nB = 0, nmax = 0;
+  std::vector<double> R, Z, S, C[2];
+  std::vector<int> ao_center;
+  bool has_S = false;
+  DevSys dev{};
+  void* dmem = nullptr;
+  // launch planning
+  int GS = 32;
+  GroupLayout Lrm{}, Lmeas{}, LmeasD{};
+  int gpb_rm = 1, gpb_meas = 1, gpb_measD = 1;
+  int accL = 0;
+  bool acc_smem = false;
+  int acc_off = -1;
+  double* scratch_counters = nullptr;  // device [2] for evaluate
+};
+
+struct vmcf_walkers_s {
+  vmcf_system_s* sys = nullptr;
+  int W = 0, nblocks = 0, cpb = 1, grid_meas = 1;
+  uint64_t k0 = 0, k1 = 0, wid0 = 0;
+  double* pos = nullptr;
+  void* B = nullptr;
+  uint32_t* nacc = nullptr;
+  uint32_t* nrej = nullptr;
+  unsigned long long* counters = nullptr;  // [0] singular, [1] refreshes
+  double* acc = nullptr;                   // [grid_meas][accL]
+  double* blocks = nullptr;                // [nblocks][accL]
+  uint64_t sweep = 0, measured = 0;
+  int counter = 0;
+  double e_ref = 0.0;
+  // per-kernel timing (kind 0 move, 1 measure, 2 refresh): event pairs around launches
+  bool profiling = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
+  double kernel_ms[3] = {0, 0, 0};
+  long long kernel_n[3] = {0, 0, 0};
+};
+
+namespace {
+// Event pair around one launch when profiling is on.
+struct Timed {
+  vmcf_walkers_s* wk;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timed(vmcf_walkers_s* w, int k, cudaStream_t s) : wk(w), kind(k), st(s) {
+    if (wk->profiling) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~Timed() {
+    if (wk->profiling) {
+      cudaEventRecord(b, st);
+      wk->events.push_back({kind, {a, b}});
+    }
+  }
+};
+}  // namespace
+
+namespace {
+
+// ---------------------------------------------------------------- normalisation
+// Radial normalisation of r^l exp(-a r^2) times a unit-sphere harmonic:
+// N^2 = 2 (2a)^{l+3/2} / Gamma(l + 3/2).
+double radial_norm(double a, int l) { return std::sqrt(2.0 * std::pow(2.0 * a, l + 1.5) / std::tgamma(l + 1.5)); }
+// Overlap of two normalised primitives with the same centre, l and m:
+// N_a N_b Gamma(l + 3/2) / (2 (a + b)^{l+3/2}).
+double same_centre_overlap(double a, double b, int l) {
+  return radial_norm(a, l) * radial_norm(b, l) * std::tgamma(l + 1.5) / (2.0 * std::pow(a + b, l + 1.5));
+}
+
+template <typename T>
+size_t tsize() { return sizeof(T); }
+
+// Shared-memory plan of one walker group for the refresh and move kernels.
+GroupLayout layout_refresh_move(const vmcf_system_s& s, size_t tsz, int GS) {
+  GroupLayout L{};
+  int o = 0;
+  auto take = [&](int bytes) { int at = o; o = align16(o + bytes); return at; };
+  L.pos = take(8 * 3 * s.Ne);
+  L.ph = take(4 * 3 * s.Ne);
+  L.pl = take(4 * 3 * s.Ne);
+  L.Bd = take(8 * s.nmax * s.nmax);
+  L.Bt = take((int)tsz * s.nB);
+  L.ao = take((int)tsz * s.M);
+  L.row = take((int)tsz * s.nmax);
+  L.wv = take((int)tsz * s.nmax);
+  L.col = take((int)tsz * s.nmax);
+  L.piv = take(4 * s.nmax);
+  L.f = take(8 * s.nmax);
+  L.red = take(8 * 4 * std::max(1, GS / 32));
+  L.scal = take(32);
+  L.bytes = align16(o);
+  return L;
+}
+
+// Shared-memory plan of one walker group for the measure kernel.
+GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool withD) {
+  GroupLayout L{};
+  int o = 0;
+  auto take = [&](int bytes) { int at = o; o = align16(o + bytes); return at; };
+  L.pos = take(8 * 3 * s.Ne);
+  L.ph = take(4 * 3 * s.Ne);
+  L.pl = take(4 * 3 * s.Ne);
+  L.Bd = take(8 * s.nB);
+  L.Bt = (tsz == 8) ? L.Bd : take((int)tsz * s.nB);
+  L.P = take((int)tsz * s.nB);
+  L.Q = take((int)tsz * s.nmax * s.nmax);
+  L.Jg = take((int)tsz * 3 * s.Ne);
+  L.Jl = take((int)tsz * s.Ne);
+  L.gd = take((int)tsz * 3 * s.Ne);
+  L.ao = take((int)tsz * 14 * s.M);
+  L.mo = take((int)tsz * 4 * s.nmax);
+  L.frc = take((int)tsz * 6 * s.K);
+  L.Ow = take((int)tsz * s.M * s.nmax);
+  L.D = withD ? take((int)tsz * s.M * s.nmax) : L.Ow;
+  L.piv = take(4 * s.nmax);
+  L.f = take(8 * s.nmax);
+  L.red = take(8 * 4 * std::max(1, GS / 32));
+  L.scal = take(32);
+  L.bytes = align16(o);
+  return L;
+}
+
+int plan(vmcf_system_s& s) {
+  const size_t tsz = s.precision == VMCF_FP64 ? 8 : 4;
+  s.GS = (s.nmax <= 24) ? 32 : 128;
+  s.Lrm = layout_refresh_move(s, tsz, s.GS);
+  s.Lmeas = layout_measure(s, tsz, s.GS, false);
+  s.LmeasD = layout_measure(s, tsz, s.GS, true);
+  const int maxg = s.GS == 32 ? 4 : 1;
+  s.gpb_rm = std::max(1, std::min(maxg, kSmemCap / std::max(1, s.Lrm.bytes)));
+  if (s.Lrm.bytes > kSmemCap) return fail(VMCF_ENOTSUP, "system too large for the shared-memory plan (sampling)");
+  if (s.Lmeas.bytes > kSmemCap) return fail(VMCF_ENOTSUP, "system too large for the shared-memory plan (measure)");
+  s.gpb_measD = s.LmeasD.bytes > kSmemCap ? 0 : std::max(1, std::min(maxg, kSmemCap / s.LmeasD.bytes));
+  s.accL = 3 + 9 * s.K + 2 * s.M * (s.nup + s.ndn);
+  const int accBytes = align16((int)tsz * s.accL);
+  int g = maxg;
+  while (g > 1 && g * s.Lmeas.bytes + accBytes > kSmemCap) --g;
+  if (g * s.Lmeas.bytes + accBytes <= kSmemCap) {
+    s.acc_smem = true;
+    s.gpb_meas = g;
+    s.acc_off = g * s.Lmeas.bytes;
+  } else {
+    s.acc_smem = false;  // one group per CTA, sums go straight to the CTA's FP64 slot
+    s.gpb_meas = 1;
+    s.acc_off = -1;
+  }
+  return VMCF_OK;
+}
+
+Launch launch_rm(const vmcf_system_s& s, int W) {
+  Launch lc{};
+  lc.GS = s.GS;
+  lc.groups = s.gpb_rm;
+  lc.grid = (W + lc.groups - 1) / lc.groups;
+  lc.L = s.Lrm;
+  lc.smem = (size_t)lc.groups * s.Lrm.bytes;
+  lc.acc_off = -1;
+  return lc;
+}
+
+Launch launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD) {
+  Launch lc{};
+  lc.GS = s.GS;
+  if (withD) {
+    lc.groups = s.gpb_measD;
+    lc.L = s.LmeasD;
+    lc.smem = (size_t)lc.groups * s.LmeasD.bytes;
+    lc.acc_off = -1;
+  } else if (accum && s.acc_smem) {
+    lc.groups = s.gpb_meas;
+    lc.L = s.Lmeas;
+    lc.acc_off = s.acc_off;
+    const size_t tsz = s.precision == VMCF_FP64 ? 8 : 4;
+    lc.smem = (size_t)s.acc_off + align16((int)tsz * s.accL);
+  } else if (accum) {
+    lc.groups = 1;
+    lc.L = s.Lmeas;
+    lc.smem = s.Lmeas.bytes;
+    lc.acc_off = -1;
+  } else {
+    lc.groups = s.gpb_meas;
+    lc.L = s.Lmeas;
+    lc.smem = (size_t)lc.groups * s.Lmeas.bytes;
+    lc.acc_off = -1;
+  }
+  lc.grid = grid;
+  return lc;
+}
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+int do_refresh(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
+  const Launch lc = launch_rm(*s, wk->W);
+  Timed tm(wk, 2, st);
+  cudaError_t e = s->precision == VMCF_FP64
+                      ? launch_refresh<double>(s->dev, lc, wk->pos, wk->B, wk->W, wk->counters, st)
+                      : launch_refresh<float>(s->dev, lc, wk->pos, wk->B, wk->W, wk->counters, st);
+  if (e != cudaSuccess) return cuda_fail(e, "refresh kernel launch");
+  wk->counter = 0;
+  return VMCF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vmcf_strerror(int status) {
+  switch (status) {
+    case VMCF_OK: return "ok";
+    case VMCF_EINVAL: return "invalid argument";
+    case VMCF_ENOMEM: return "out of memory";
+    case VMCF_ECUDA: return "CUDA error";
+    case VMCF_ESINGULAR: return "singular Slater matrix";
+    case VMCF_ETIMEOUT: return "device wait timed out";
+    case VMCF_ENOTSUP: return "not supported";
+    default: return "unknown status";
+  }
+}
+
+const char* vmcf_last_error(void) { return g_last_error.c_str(); }
+
+int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double* C_up, const double* C_dn,
+                     int n_up, int n_dn, const vmcf_jastrow* jas, const double* S, int precision,
+                     vmcf_system_t* out) {
+  if (!out) return fail(VMCF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!nuc || !bas || !jas || !C_up) return fail(VMCF_EINVAL, "NULL input");
+  if (precision != VMCF_FP64 && precision != VMCF_MIXED) return fail(VMCF_EINVAL, "bad precision");
+  if (nuc->K < 1 || !nuc->Z || !nuc->R) return fail(VMCF_EINVAL, "need at least one nucleus");
+  if (!finite_all(nuc->R, 3 * (size_t)nuc->K)) return fail(VMCF_EINVAL, "nuclear positions not finite");
+  for (int I = 0; I < nuc->K; ++I)
+    if (nuc->Z[I] < 1) return fail(VMCF_EINVAL, "nuclear charge < 1");
+  if (bas->nshell < 1 || bas->maxprim < 1 || bas->maxprim > kMaxPrim || !bas->center || !bas->l || !bas->nprim ||
+      !bas->exps || !bas->coefs)
+    return fail(VMCF_EINVAL, "bad basis description");
+  if (n_up < 1 || n_dn < 0 || n_dn > n_up || n_up > 64) return fail(VMCF_EINVAL, "need 1 <= n_dn <= n_up <= 64");
+  if (n_dn > 0 && !C_dn) return fail(VMCF_EINVAL, "C_dn is NULL");
+
+  auto* s = new vmcf_system_s();
+  s->precision = precision;
+  s->K = nuc->K;
+  s->nshell = bas->nshell;
+  s->nup = n_up;
+  s->ndn = n_dn;
+  s->Ne = n_up + n_dn;
+  s->nB = n_up * n_up + n_dn * n_dn;
+  s->nmax = std::max(n_up, n_dn);
+  s->R.assign(nuc->R, nuc->R + 3 * s->K);
+  s->Z.resize(s->K);
+  for (int I = 0; I < s->K; ++I) s->Z[I] = nuc->Z[I];
+
+  std::vector<int4> shells(s->nshell);
+  std::vector<int> sharp(s->nshell, 0);
+  std::vector<double> alpha(s->nshell * kMaxPrim, 0.0), coef(s->nshell * kMaxPrim, 0.0);
+  int M = 0;
+  for (int sh = 0; sh < s->nshell; ++sh) {
+    const int c = bas->center[sh], l = bas->l[sh], np = bas->nprim[sh];
+    if (c < 0 || c >= s->K || l < 0 || l > 2 || np < 1 || np > bas->maxprim) {
+      delete s;
+      return fail(VMCF_EINVAL, "bad shell (centre, l in 0..2, nprim)");
+    }
+    double d[kMaxPrim], a[kMaxPrim];
+    for (int k = 0; k < np; ++k) {
+      a[k] = bas->exps[sh * bas->maxprim + k];
+      d[k] = bas->coefs[sh * bas->maxprim + k];
+      if (!(a[k] > 0.0) || !std::isfinite(a[k]) || !std::isfinite(d[k])) {
+        delete s;
+        return fail(VMCF_EINVAL, "exponents must be positive and finite");
+      }
+    }
+    double norm2 = 0.0;
+    for (int p = 0; p < np; ++p)
+      for (int q = 0; q < np; ++q) norm2 += d[p] * d[q] * same_centre_overlap(a[p], a[q], l);
+    if (!(norm2 > 0.0)) {
+      delete s;
+      return fail(VMCF_EINVAL, "contraction has zero norm");
+    }
+    for (int k = 0; k < np; ++k) {
+      // In mixed mode a primitive this sharp has a r^2 and its Laplacian factors formed in
+      // double: the float rounding of a r^2 times a would dominate the local energy error.
+      if (a[k] > kSharpAlpha) sharp[sh] |= 1 << k;
+      alpha[sh * kMaxPrim + k] = a[k];
+      coef[sh * kMaxPrim + k] = d[k] * radial_norm(a[k], l) / std::sqrt(norm2);
+    }
+    shells[sh] = make_int4(c, l, np, M);
+    for (int m = 0; m < 2 * l + 1; ++m) s->ao_center.push_back(c);
+    M += 2 * l + 1;
+  }
+  s->M = M;
+  if (M > 1024) {
+    delete s;
+    return fail(VMCF_ENOTSUP, "more than 1024 AOs");
+  }
+  s->C[0].assign(C_up, C_up + (size_t)M * n_up);
+  if (n_dn > 0) s->C[1].assign(C_dn, C_dn + (size_t)M * n_dn);
+  if (!finite_all(s->C[0].data(), s->C[0].size()) || !finite_all(s->C[1].data(), s->C[1].size())) {
+    delete s;
+    return fail(VMCF_EINVAL, "C not finite");
+  }
+  if (S) {
+    s->S.assign(S, S + (size_t)M * M);
+    s->has_S = true;
+  }
+  // nuclear repulsion and its derivative
+  double Vnn = 0.0;
+  std::vector<double> dVnn(3 * s->K, 0.0);
+  for (int I = 0; I < s->K; ++I)
+    for (int J = 0; J < s->K; ++J) {
+      if (I == J) continue;
+      double d[3], r2 = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        d[k] = s->R[3 * I + k] - s->R[3 * J + k];
+        r2 += d[k] * d[k];
+      }
+      const double r = std::sqrt(r2);
+      if (J > I) Vnn += s->Z[I] * s->Z[J] / r;
+      for (int k = 0; k < 3; ++k) dVnn[3 * I + k] -= s->Z[I] * s->Z[J] * d[k] / (r2 * r);
+    }
+
+  int rc = plan(*s);
+  if (rc != VMCF_OK) {
+    delete s;
+    return rc;
+  }
+
+  // one device allocation for all tables
+  std::vector<float> alpha_f(alpha.begin(), alpha.end()), coef_f(coef.begin(), coef.end());
+  std::vector<float> Rh(3 * s->K), Rl(3 * s->K);
+  for (int i = 0; i < 3 * s->K; ++i) {
+    Rh[i] = (float)s->R[i];
+    Rl[i] = (float)(s->R[i] - (double)Rh[i]);
+  }
+  std::vector<float> Cf0(s->C[0].begin(), s->C[0].end()), Cf1(s->C[1].begin(), s->C[1].end());
+  size_t off = 0;
+  auto slot = [&](size_t bytes) { size_t at = off; off = (off + bytes + 255) & ~size_t(255); return at; };
+  const size_t oR = slot(8 * s->R.size()), oZ = slot(8 * s->Z.size()), oSh = slot(sizeof(int4) * shells.size()),
+               oA = slot(8 * alpha.size()), oC = slot(8 * coef.size()), oAf = slot(4 * alpha.size()),
+               oCf = slot(4 * coef.size()), oAoc = slot(4 * (size_t)M), oC0 = slot(8 * s->C[0].size()),
+               oC1 = slot(8 * std::max<size_t>(1, s->C[1].size())), oCf0 = slot(4 * Cf0.size()),
+               oCf1 = slot(4 * std::max<size_t>(1, Cf1.size())), oDv = slot(8 * dVnn.size()), oCnt = slot(16),
+               oRh = slot(4 * Rh.size()), oRl = slot(4 * Rl.size()), oSharp = slot(4 * sharp.size());
+  cudaError_t e = cudaMalloc(&s->dmem, off);
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_fail(e, "cudaMalloc(system tables)");
+  }
+  char* b = static_cast<char*>(s->dmem);
+  auto up = [&](size_t at, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpy(b + at, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  cudaError_t ce = cudaSuccess;
+  ce = ce ? ce : up(oR, s->R.data(), 8 * s->R.size());
+  ce = ce ? ce : up(oZ, s->Z.data(), 8 * s->Z.size());
+  ce = ce ? ce : up(oSh, shells.data(), sizeof(int4) * shells.size());
+  ce = ce ? ce : up(oA, alpha.data(), 8 * alpha.size());
+  ce = ce ? ce : up(oC, coef.data(), 8 * coef.size());
+  ce = ce ? ce : up(oAf, alpha_f.data(), 4 * alpha_f.size());
+  ce = ce ? ce : up(oCf, coef_f.data(), 4 * coef_f.size());
+  ce = ce ? ce : up(oAoc, s->ao_center.data(), 4 * (size_t)M);
+  ce = ce ? ce : up(oC0, s->C[0].data(), 8 * s->C[0].size());
+  ce = ce ? ce : up(oC1, s->C[1].data(), 8 * s->C[1].size());
+  ce = ce ? ce : up(oCf0, Cf0.data(), 4 * Cf0.size());
+  ce = ce ? ce : up(oCf1, Cf1.data(), 4 * Cf1.size());
+  ce = ce ? ce : up(oDv, dVnn.data(), 8 * dVnn.size());
+  ce = ce ? ce : cudaMemset(b + oCnt, 0, 16);
+  ce = ce ? ce : up(oRh, Rh.data(), 4 * Rh.size());
+  ce = ce ? ce : up(oRl, Rl.data(), 4 * Rl.size());
+  ce = ce ? ce : up(oSharp, sharp.data(), 4 * sharp.size());
+  if (ce == cudaSuccess) ce = s->precision == VMCF_FP64 ? set_smem_limits<double>(s->GS) : set_smem_limits<float>(s->GS);
+  if (ce != cudaSuccess) {
+    cudaFree(s->dmem);
+    delete s;
+    return cuda_fail(ce, "uploading system tables");
+  }
+  DevSys& D = s->dev;
+  D.K = s->K; D.M = M; D.nup = n_up; D.ndn = n_dn; D.Ne = s->Ne; D.nshell = s->nshell; D.nB = s->nB; D.nmax = s->nmax;
+  D.R = reinterpret_cast<const double*>(b + oR);
+  D.Z = reinterpret_cast<const double*>(b + oZ);
+  D.shell = reinterpret_cast<const int4*>(b + oSh);
+  D.alpha = reinterpret_cast<const double*>(b + oA);
+  D.coef = reinterpret_cast<const double*>(b + oC);
+  D.alpha_f = reinterpret_cast<const float*>(b + oAf);
+  D.coef_f = reinterpret_cast<const float*>(b + oCf);
+  D.ao_center = reinterpret_cast<const int*>(b + oAoc);
+  D.Rh = reinterpret_cast<const float*>(b + oRh);
+  D.Rl = reinterpret_cast<const float*>(b + oRl);
+  D.sharp = reinterpret_cast<const int*>(b + oSharp);
+  D.C[0] = reinterpret_cast<const double*>(b + oC0);
+  D.C[1] = reinterpret_cast<const double*>(b + oC1);
+  D.Cf[0] = reinterpret_cast<const float*>(b + oCf0);
+  D.Cf[1] = reinterpret_cast<const float*>(b + oCf1);
+  D.Fa = jas->F_anti; D.Fp = jas->F_par; D.aa = jas->a_anti; D.ap = jas->a_par; D.ben = jas->b_en;
+  D.J1 = jas->enable_J1 ? 1 : 0;
+  D.J2 = jas->enable_J2 ? 1 : 0;
+  D.Vnn = Vnn;
+  D.dVnn = reinterpret_cast<const double*>(b + oDv);
+  s->scratch_counters = reinterpret_cast<double*>(b + oCnt);
+  *out = s;
+  return VMCF_OK;
+}
+
+int vmcf_system_destroy(vmcf_system_t s) {
+  if (!s) return VMCF_OK;
+  if (s->dmem) cudaFree(s->dmem);
+  delete s;
+  return VMCF_OK;
+}
+
+int vmcf_system_info(vmcf_system_t s, int* K, int* M, int* n_up, int* n_dn) {
+  if (!s) return fail(VMCF_EINVAL, "NULL system");
+  if (K) *K = s->K;
+  if (M) *M = s->M;
+  if (n_up) *n_up = s->nup;
+  if (n_dn) *n_dn = s->ndn;
+  return VMCF_OK;
+}
+
+int vmcf_accumulator_length(vmcf_system_t s) { return s ? s->accL : VMCF_EINVAL; }
+
+int vmcf_walkers_create(vmcf_system_t s, int W, const double* pos, int is_host, uint64_t key0, uint64_t key1,
+                        uint64_t wid0, int nblocks, void* stream, vmcf_walkers_t* out) {
+  if (!out) return fail(VMCF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!s || !pos) return fail(VMCF_EINVAL, "NULL system or positions");
+  if (W < 1 || nblocks < 2 || nblocks > W) return fail(VMCF_EINVAL, "need W >= 1 and 2 <= nblocks <= W");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto* wk = new vmcf_walkers_s();
+  wk->sys = s;
+  wk->W = W;
+  wk->nblocks = nblocks;
+  wk->k0 = key0;
+  wk->k1 = key1;
+  wk->wid0 = wid0;
+  const int per_cta = std::max(1, 4 * (s->acc_smem ? s->gpb_meas : 1));
+  wk->cpb = std::max(1, (int)std::lround((double)W / ((double)nblocks * per_cta)));
+  wk->grid_meas = nblocks * wk->cpb;
+  const size_t tsz = s->precision == VMCF_FP64 ? 8 : 4;
+  const size_t npos = (size_t)W * 3 * s->Ne;
+  cudaError_t e;
+  if ((e = cudaMalloc(&wk->pos, 8 * npos)) || (e = cudaMalloc(&wk->B, tsz * (size_t)W * s->nB)) ||
+      (e = cudaMalloc(&wk->nacc, 4 * (size_t)W)) || (e = cudaMalloc(&wk->nrej, 4 * (size_t)W)) ||
+      (e = cudaMalloc(&wk->counters, 16)) ||
+      (e = cudaMalloc(&wk->acc, 8 * (size_t)wk->grid_meas * s->accL)) ||
+      (e = cudaMalloc(&wk->blocks, 8 * (size_t)nblocks * s->accL))) {
+    vmcf_walkers_destroy(wk);
+    return fail(VMCF_ENOMEM, std::string("walker state allocation: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaMemcpyAsync(wk->pos, pos, 8 * npos, is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st)) ||
+      (e = cudaMemsetAsync(wk->nacc, 0, 4 * (size_t)W, st)) || (e = cudaMemsetAsync(wk->nrej, 0, 4 * (size_t)W, st)) ||
+      (e = cudaMemsetAsync(wk->counters, 0, 16, st)) ||
+      (e = cudaMemsetAsync(wk->acc, 0, 8 * (size_t)wk->grid_meas * s->accL, st))) {
+    vmcf_walkers_destroy(wk);
+    return cuda_fail(e, "walker state initialisation");
+  }
+  int rc = do_refresh(s, wk, st);
+  if (rc == VMCF_OK) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "initial refresh");
+  }
+  if (rc != VMCF_OK) {
+    vmcf_walkers_destroy(wk);
+    return rc;
+  }
+  *out = wk;
+  return VMCF_OK;
+}
+
+int vmcf_walkers_destroy(vmcf_walkers_t wk) {
+  if (!wk) return VMCF_OK;
+  for (auto& ev : wk->events) {
+    cudaEventDestroy(ev.second.first);
+    cudaEventDestroy(ev.second.second);
+  }
+  cudaFree(wk->pos);
+  cudaFree(wk->B);
+  cudaFree(wk->nacc);
+  cudaFree(wk->nrej);
+  cudaFree(wk->counters);
+  cudaFree(wk->acc);
+  cudaFree(wk->blocks);
+  delete wk;
+  return VMCF_OK;
+}
+
+int vmcf_walkers_set_positions(vmcf_system_t s, vmcf_walkers_t wk, const double* pos, int is_host, void* stream) {
+  if (!s || !wk || !pos || wk->sys != s) return fail(VMCF_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  VMCF_CUDA(cudaMemcpyAsync(wk->pos, pos, 8 * (size_t)wk->W * 3 * s->Ne,
+                            is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  return do_refresh(s, wk, st);
+}
+
+int vmcf_walkers_get_positions(vmcf_walkers_t wk, double* pos, int is_host, void* stream) {
+  if (!wk || !pos) return fail(VMCF_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  VMCF_CUDA(cudaMemcpyAsync(pos, wk->pos, 8 * (size_t)wk->W * 3 * wk->sys->Ne,
+                            is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  if (is_host) VMCF_CUDA(cudaStreamSynchronize(st));
+  return VMCF_OK;
+}
+
+int vmcf_reset_accumulators(vmcf_walkers_t wk, double e_ref, void* stream) {
+  if (!wk || !std::isfinite(e_ref)) return fail(VMCF_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  VMCF_CUDA(cudaMemsetAsync(wk->acc, 0, 8 * (size_t)wk->grid_meas * wk->sys->accL, st));
+  wk->e_ref = e_ref;
+  wk->measured = 0;
+  return VMCF_OK;
+}
+
+int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_sigma, int refresh_k, int measure,
+                void* stream) {
+  if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
+  if (n_sweeps < 0 || !(step_sigma > 0.0) || !std::isfinite(step_sigma) || refresh_k < 1)
+    return fail(VMCF_EINVAL, "need n_sweeps >= 0, step_sigma > 0, refresh_k >= 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MoveParams P{};
+  P.pos = wk->pos;
+  P.B = wk->B;
+  P.nacc = wk->nacc;
+  P.nrej = wk->nrej;
+  P.counters = wk->counters;
+  P.W = wk->W;
+  P.wid0 = wk->wid0;
+  P.k0 = wk->k0;
+  P.k1 = wk->k1;
+  P.kref = refresh_k;
+  P.sigma = step_sigma;
+  const Launch lm = launch_rm(*s, wk->W);
+  const bool fp64 = s->precision == VMCF_FP64;
+  auto move = [&](int nsw, int skip) -> int {
+    P.sweep0 = wk->sweep;
+    P.nsweeps = nsw;
+    P.c0 = wk->counter;
+    P.skip_final_refresh = skip;
+    Timed tm(wk, 0, st);
+    cudaError_t e = fp64 ? launch_move<double>(s->dev, lm, P, st) : launch_move<float>(s->dev, lm, P, st);
+    if (e != cudaSuccess) return cuda_fail(e, "move kernel launch");
+    wk->sweep += nsw;
+    wk->counter = (int)((wk->counter + (long long)nsw * s->Ne) % refresh_k);
+    return VMCF_OK;
+  };
+  if (!measure) {
+    if (n_sweeps > 0) return move(n_sweeps, 0);
+    return VMCF_OK;
+  }
+  MeasParams M{};
+  M.pos = wk->pos;
+  M.Bout = wk->B;
+  M.acc = wk->acc;
+  M.accL = s->accL;
+  M.acc_in_smem = s->acc_smem ? 1 : 0;
+  M.e_ref = wk->e_ref;
+  M.counters = wk->counters;
+  M.W = wk->W;
+  const Launch lme = launch_meas(*s, wk->grid_meas, true, false);
+  for (int k = 0; k < n_sweeps; ++k) {
+    int rc = move(1, 1);
+    if (rc != VMCF_OK) return rc;
+    Timed tm(wk, 1, st);
+    cudaError_t e = fp64 ? launch_measure<double>(s->dev, lme, M, st) : launch_measure<float>(s->dev, lme, M, st);
+    if (e != cudaSuccess) return cuda_fail(e, "measure kernel launch");
+    wk->counter = 0;  // the measurement rebuilt the inverses
+    wk->measured += 1;
+  }
+  return VMCF_OK;
+}
+
+int vmcf_evaluate(vmcf_system_t s, const double* pos, int W, double* EL, double* logpsi, double* dlnpsi_dR,
+                  double* dEL_dR, double* O, double* dEL_dC, void* stream) {
+  if (!s || !pos || W < 0) return fail(VMCF_EINVAL, "bad arguments");
+  if (W == 0) return VMCF_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool withD = dEL_dC != nullptr;
+  if (withD && s->gpb_measD == 0) return fail(VMCF_ENOTSUP, "dEL_dC output does not fit shared memory for this system");
+  MeasParams M{};
+  M.pos = pos;
+  M.EL = EL;
+  M.logpsi = logpsi;
+  M.dlnpsi = dlnpsi_dR;
+  M.dEL = dEL_dR;
+  M.O = O;
+  M.dELdC = dEL_dC;
+  M.counters = reinterpret_cast<unsigned long long*>(s->scratch_counters);
+  M.W = W;
+  const int groups = withD ? s->gpb_measD : s->gpb_meas;
+  const int grid = (W + 2 * groups - 1) / (2 * groups);
+  const Launch lc = launch_meas(*s, grid, false, withD);
+  cudaError_t e = s->precision == VMCF_FP64 ? launch_measure<double>(s->dev, lc, M, st)
+                                            : launch_measure<float>(s->dev, lc, M, st);
+  if (e != cudaSuccess) return cuda_fail(e, "measure kernel launch (evaluate)");
+  return VMCF_OK;
+}
+
+int vmcf_block_sums(vmcf_system_t s, vmcf_walkers_t wk, double* out, void* stream) {
+  if (!s || !wk || !out || wk->sys != s) return fail(VMCF_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_block_reduce(wk->acc, wk->grid_meas, wk->cpb, s->accL, wk->blocks, wk->nblocks, st);
+  if (e != cudaSuccess) return cuda_fail(e, "block reduce launch");
+  VMCF_CUDA(cudaMemcpyAsync(out, wk->blocks, 8 * (size_t)wk->nblocks * s->accL, cudaMemcpyDeviceToHost, st));
+  VMCF_CUDA(cudaStreamSynchronize(st));
+  return VMCF_OK;
+}
+
+int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double* E_err, double* F, double* F_err,
+                           double* dEdC, double* dEdC_err, double* rhs_BQ, void* stream) {
+  if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
+  if (rhs_BQ && !s->has_S) return fail(VMCF_EINVAL, "rhs_BQ needs the AO overlap S at init");
+  const int L = s->accL, nb = wk->nblocks, K3 = 3 * s->K, nO = s->M * (s->nup + s->ndn);
+  std::vector<double> blk((size_t)nb * L);
+  int rc = vmcf_block_sums(s, wk, blk.data(), stream);
+  if (rc != VMCF_OK) return rc;
+  std::vector<double> tot(L, 0.0);
+  for (int b = 0; b < nb; ++b)
+    for (int i = 0; i < L; ++i) tot[i] += blk[(size_t)b * L + i];
+  if (!(tot[0] > 0.0)) return fail(VMCF_EINVAL, "no measured samples");
+  const double er = wk->e_ref;
+  const int o_dEL = 3, o_d = 3 + K3, o_Ed = 3 + 2 * K3, o_O = 3 + 3 * K3, o_EO = 3 + 3 * K3 + nO;
+  // estimates from a sum vector v (all blocks, or all but one)
+  auto est = [&](const double* v, double* Eo, double* Fo, double* Bo) {
+    const double n = v[0], Em = v[1] / n;
+    *Eo = Em;
+    if (Fo)
+      for (int i = 0; i < K3; ++i) Fo[i] = -(v[o_dEL + i] / n + 2.0 * (v[o_Ed + i] / n - (Em - er) * v[o_d + i] / n));
+    if (Bo)
+      for (int i = 0; i < nO; ++i) Bo[i] = 2.0 * (v[o_EO + i] / n - (Em - er) * v[o_O + i] / n);
+  };
+  double Ev;
+  std::vector<double> Fv(K3), Bv(nO);
+  est(tot.data(), &Ev, Fv.data(), Bv.data());
+  // delete-one-block jackknife
+  std::vector<double> Ej(nb), Fj((size_t)nb * K3), Bj((size_t)nb * nO), loo(L);
+  for (int b = 0; b < nb; ++b) {
+    for (int i = 0; i < L; ++i) loo[i] = tot[i] - blk[(size_t)b * L + i];
+    est(loo.data(), &Ej[b], Fj.data() + (size_t)b * K3, Bj.data() + (size_t)b * nO);
+  }
+  auto jk = [&](const double* th, int stride, int idx) {
+    double m = 0.0;
+    for (int b = 0; b < nb; ++b) m += th[(size_t)b * stride + idx];
+    m /= nb;
+    double v = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      const double d = th[(size_t)b * stride + idx] - m;
+      v += d * d;
+    }
+    return std::sqrt((nb - 1.0) / nb * v);
+  };
+  if (E) *E = Ev;
+  if (E_err) *E_err = jk(Ej.data(), 1, 0);
+  for (int i = 0; i < K3; ++i) {
+    if (F) F[i] = Fv[i];
+    if (F_err) F_err[i] = jk(Fj.data(), K3, i);
+  }
+  for (int i = 0; i < nO; ++i) {
+    if (dEdC) dEdC[i] = Bv[i];
+    if (dEdC_err) dEdC_err[i] = jk(Bj.data(), nO, i);
+  }
+  if (rhs_BQ) {
+    // Q^s = 1 - C^s C^s^T S (Eq. Q_projector); rhs_{nu i} = -sum_mu B_{mu i} Q_{mu nu}
+    const int M = s->M;
+    int ooff = 0;
+    for (int sg = 0; sg < 2; ++sg) {
+      const int n = sg == 0 ? s->nup : s->ndn;
+      const std::vector<double>& C = s->C[sg];
+      std::vector<double> CtB((size_t)n * n, 0.0);  // (C^T B)_{k i}
+      for (int k = 0; k < n; ++k)
+        for (int i = 0; i < n; ++i) {
+          double v = 0.0;
+          for (int mu = 0; mu < M; ++mu) v += C[(size_t)mu * n + k] * Bv[ooff + (size_t)mu * n + i];
+          CtB[(size_t)k * n + i] = v;
+        }
+      // sum_mu B_{mu i} (delta_{mu nu} - sum_k C_{mu k} (S C)_{nu k})
+      std::vector<double> SC((size_t)M * n, 0.0);
+      for (int nu = 0; nu < M; ++nu)
+        for (int k = 0; k < n; ++k) {
+          double v = 0.0;
+          for (int la = 0; la < M; ++la) v += s->S[(size_t)nu * M + la] * C[(size_t)la * n + k];
+          SC[(size_t)nu * n + k] = v;
+        }
+      for (int nu = 0; nu < M; ++nu)
+        for (int i = 0; i < n; ++i) {
+          double v = Bv[ooff + (size_t)nu * n + i];
+          for (int k = 0; k < n; ++k) v -= SC[(size_t)nu * n + k] * CtB[(size_t)k * n + i];
+          rhs_BQ[ooff + (size_t)nu * n + i] = -v;
+        }
+      ooff += M * n;
+    }
+  }
+  return VMCF_OK;
+}
+
+int vmcf_profile(vmcf_walkers_t wk, int enable) {
+  if (!wk) return fail(VMCF_EINVAL, "NULL walkers");
+  wk->profiling = enable != 0;
+  return VMCF_OK;
+}
+
+int vmcf_kernel_times(vmcf_walkers_t wk, double* ms, long long* count, int reset) {
+  if (!wk) return fail(VMCF_EINVAL, "NULL walkers");
+  for (auto& ev : wk->events) {
+    VMCF_CUDA(cudaEventSynchronize(ev.second.second));
+    float t = 0.f;
+    VMCF_CUDA(cudaEventElapsedTime(&t, ev.second.first, ev.second.second));
+    wk->kernel_ms[ev.first] += t;
+    wk->kernel_n[ev.first] += 1;
+    cudaEventDestroy(ev.second.first);
+    cudaEventDestroy(ev.second.second);
+  }
+  wk->events.clear();
+  for (int k = 0; k < 3; ++k) {
+    if (ms) ms[k] = wk->kernel_ms[k];
+    if (count) count[k] = wk->kernel_n[k];
+    if (reset) {
+      wk->kernel_ms[k] = 0.0;
+      wk->kernel_n[k] = 0;
+    }
+  }
+  return VMCF_OK;
+}
+
+int vmcf_probe_pipes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, void* stream) {
+  cudaError_t e = run_probes(fp64_tflops, fp32_tflops, exp_gops, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "pipe probes");
+  return VMCF_OK;
+}
+
+int vmcf_status_counters(vmcf_walkers_t wk, vmcf_counters* out, void* stream) {
+  if (!wk || !out) return fail(VMCF_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<uint32_t> a(wk->W), r(wk->W);
+  unsigned long long c[2];
+  VMCF_CUDA(cudaMemcpyAsync(a.data(), wk->nacc, 4 * (size_t)wk->W, cudaMemcpyDeviceToHost, st));
+  VMCF_CUDA(cudaMemcpyAsync(r.data(), wk->nrej, 4 * (size_t)wk->W, cudaMemcpyDeviceToHost, st));
+  VMCF_CUDA(cudaMemcpyAsync(c, wk->counters, 16, cudaMemcpyDeviceToHost, st));
+  VMCF_CUDA(cudaStreamSynchronize(st));
+  std::memset(out, 0, sizeof(*out));
+  for (int w = 0; w < wk->W; ++w) {
+    out->accepted += a[w];
+    out->rejected_nonfinite += r[w];
+  }
+  out->sweeps = wk->sweep;
+  out->moves = wk->sweep * (uint64_t)wk->W * (uint64_t)wk->sys->Ne;
+  out->singular = c[0];
+  out->refreshes = c[1];
+  out->measured_sweeps = wk->measured;
+  return VMCF_OK;
+}
+
+}  // extern "C"

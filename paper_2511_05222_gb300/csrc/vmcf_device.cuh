@@ -1,0 +1,423 @@
+// Device building blocks of the VMC hot path (arXiv:2511.05222, App. A).
+//
+// Work is organised by walker groups: GS threads (one warp for small electron counts, a
+// whole CTA for large ones) cooperate on one walker, with all its per-walker matrices in
+// shared memory. T is the arithmetic type of AOs, MOs, Jastrow and adjoint work (double in
+// FP64 mode, float in mixed mode); the Slater inversion, the determinant ratio and the walker
+// sums are always double.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vmcf {
+
+constexpr int kMaxPrim = 8;
+
+struct DevSys {
+  int K, M, nup, ndn, Ne, nshell, nB, nmax;
+  const double* R;       // [K][3]
+  const double* Z;       // [K]
+  const int4* shell;     // (center, l, nprim, ao0)
+  const double* alpha;   // [nshell][kMaxPrim]
+  const double* coef;    // [nshell][kMaxPrim], normalised contraction coefficients
+  const float* alpha_f;
+  const float* coef_f;
+  const int* ao_center;  // [M]
+  const float* Rh;       // [K][3] nuclear positions as float-float pairs (mixed mode)
+  const float* Rl;
+  const int* sharp;      // [nshell] bit k set: primitive k is sharp (its a r^2 is formed in FP64)
+  const double* C[2];    // [M][n_s]
+  const float* Cf[2];
+  double Fa, Fp, aa, ap, ben;
+  int J1, J2;
+  double Vnn;
+  const double* dVnn;    // [K][3], derivative of V_nn
+};
+
+template <typename T> __device__ __forceinline__ const T* coefC(const DevSys& S, int s);
+template <> __device__ __forceinline__ const double* coefC<double>(const DevSys& S, int s) { return S.C[s]; }
+template <> __device__ __forceinline__ const float* coefC<float>(const DevSys& S, int s) { return S.Cf[s]; }
+
+template <typename T> __device__ __forceinline__ T dexp(T x);
+template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
+template <typename T> __device__ __forceinline__ T dsqrt(T x);
+template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+
+template <typename T> __device__ __forceinline__ T prim_alpha(const DevSys& S, int s, int k);
+template <> __device__ __forceinline__ double prim_alpha<double>(const DevSys& S, int s, int k) { return __ldg(S.alpha + s * kMaxPrim + k); }
+template <> __device__ __forceinline__ float prim_alpha<float>(const DevSys& S, int s, int k) { return __ldg(S.alpha_f + s * kMaxPrim + k); }
+template <typename T> __device__ __forceinline__ T prim_coef(const DevSys& S, int s, int k);
+template <> __device__ __forceinline__ double prim_coef<double>(const DevSys& S, int s, int k) { return __ldg(S.coef + s * kMaxPrim + k); }
+template <> __device__ __forceinline__ float prim_coef<float>(const DevSys& S, int s, int k) { return __ldg(S.coef_f + s * kMaxPrim + k); }
+
+// ---------------------------------------------------------------- group synchronisation
+template <int GS>
+__device__ __forceinline__ void gsync() {
+  if constexpr (GS == 32) {
+    __syncwarp();
+  } else {
+    // named barrier per group (id 1 + group index); GS threads take part
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / GS)), "r"(GS) : "memory");
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of NV values over the group; every thread receives identical results (the xor
+// butterfly adds the same operands in every lane). scratch: >= NV * GS/32 doubles.
+template <int GS, int NV>
+__device__ __forceinline__ void group_sum(double (&v)[NV], double* scratch) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if constexpr (GS > 32) {
+    constexpr int NW = GS / 32;
+    const int t = threadIdx.x % GS;
+    if ((t & 31) == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) scratch[k * NW + (t >> 5)] = v[k];
+    gsync<GS>();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < NW; ++w) s += scratch[k * NW + w];
+      v[k] = s;
+    }
+    gsync<GS>();
+  }
+}
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Salmon et al., "Parallel random numbers: as easy as 1, 2, 3" (SC'11), 10 rounds.
+__device__ __forceinline__ void philox4x64_10(uint64_t x[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint64_t hi0 = __umul64hi(M0, x[0]), lo0 = M0 * x[0];
+    const uint64_t hi1 = __umul64hi(M1, x[2]), lo1 = M1 * x[2];
+    const uint64_t y0 = hi1 ^ x[1] ^ k0, y2 = hi0 ^ x[3] ^ k1;
+    x[0] = y0;
+    x[1] = lo1;
+    x[2] = y2;
+    x[3] = lo0;
+  }
+}
+// 53 random bits -> [0, 1)
+__device__ __forceinline__ double u01(uint64_t x) { return (double)(x >> 11) * 0x1.0p-53; }
+
+// Three standard normals (Box-Muller on 4 uniforms) for one proposal.
+__device__ __forceinline__ void normals3(const uint64_t r[4], double xi[3], double) {
+  const double twopi = 6.283185307179586;
+  const double u1 = u01(r[0]), u2 = u01(r[1]), u3 = u01(r[2]), u4 = u01(r[3]);
+  const double a = sqrt(-2.0 * log(1.0 - u1));
+  const double b = sqrt(-2.0 * log(1.0 - u3));
+  xi[0] = a * cos(twopi * u2);
+  xi[1] = a * sin(twopi * u2);
+  xi[2] = b * cos(twopi * u4);
+}
+__device__ __forceinline__ void normals3(const uint64_t r[4], double xi[3], float) {
+  const float twopi = 6.2831853071795865f;
+  const float a = sqrtf(-2.0f * logf((float)(1.0 - u01(r[0]))));
+  const float b = sqrtf(-2.0f * logf((float)(1.0 - u01(r[2]))));
+  float s, c;
+  sincosf(twopi * (float)u01(r[1]), &s, &c);
+  xi[0] = (double)(a * c);
+  xi[1] = (double)(a * s);
+  xi[2] = (double)(b * cosf(twopi * (float)u01(r[3])));
+}
+
+// ---------------------------------------------------------------- AO shells
+// Angular factor P (a real solid harmonic r^l Y_lm with its unit-sphere normalisation),
+// its gradient g and its constant Hessian h (xx, yy, zz, xy, xz, yz).
+template <typename T>
+__device__ __forceinline__ void angular(int l, int m, T x, T y, T z, T& P, T g[3], T h[6]) {
+  const T ns = T(0.28209479177387814);   // sqrt(1/(4 pi))
+  const T np = T(0.48860251190291992);   // sqrt(3/(4 pi))
+  const T nd = T(1.0925484305920792);    // sqrt(15/(4 pi))
+  const T n0 = T(0.31539156525252005);   // sqrt(5/(16 pi))
+  const T n2 = T(0.54627421529603959);   // sqrt(15/(16 pi))
+#pragma unroll
+  for (int k = 0; k < 6; ++k) h[k] = T(0);
+  g[0] = g[1] = g[2] = T(0);
+  if (l == 0) {
+    P = ns;
+  } else if (l == 1) {
+    const T c[3] = {x, y, z};
+    P = np * c[m];
+    g[m] = np;
+  } else {
+    switch (m) {
+      case 0: P = nd * x * y; g[0] = nd * y; g[1] = nd * x; h[3] = nd; break;          // xy
+      case 1: P = nd * y * z; g[1] = nd * z; g[2] = nd * y; h[5] = nd; break;          // yz
+      case 2: P = n0 * (T(2) * z * z - x * x - y * y);                                 // 3z^2 - r^2
+        g[0] = T(-2) * n0 * x; g[1] = T(-2) * n0 * y; g[2] = T(4) * n0 * z;
+        h[0] = T(-2) * n0; h[1] = T(-2) * n0; h[2] = T(4) * n0; break;
+      case 3: P = nd * x * z; g[0] = nd * z; g[2] = nd * x; h[4] = nd; break;          // xz
+      default: P = n2 * (x * x - y * y); g[0] = T(2) * n2 * x; g[1] = T(-2) * n2 * y;  // x^2 - y^2
+        h[0] = T(2) * n2; h[1] = T(-2) * n2; break;
+    }
+  }
+}
+
+// Electron position in the two forms the AO and Jastrow code use: double, and a
+// float-float pair (h + l) whose float differences keep full float relative precision.
+struct EPos {
+  double d[3];
+  float h[3], l[3];
+};
+__device__ __forceinline__ EPos make_epos(const double* r) {
+  EPos p;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    p.d[c] = r[c];
+    p.h[c] = (float)r[c];
+    p.l[c] = (float)(r[c] - (double)p.h[c]);
+  }
+  return p;
+}
+
+// Shell s at displacement (x, y, z) = r - R_center. LEVEL 0: value. LEVEL 1: gradient (3)
+// and Laplacian. LEVEL 2: value, gradient (3), Laplacian, Hessian (xx yy zz xy xz yz),
+// gradient of the Laplacian (3). out[c * stride + ao] for component c.
+// With e_k = c_k exp(-a_k r^2), R0 = sum e_k, R1 = sum -2a_k e_k, R2 = sum 4a_k^2 e_k:
+//   d_i F = x_i R1, d_i d_j F = x_i x_j R2 + delta_ij R1; for a harmonic homogeneous P of
+//   degree l: lap(P F) = P sum_k -2a_k e_k ((2l+3) - 2 a_k r^2) and
+//   d_k lap(P F) = P_k lap F + P x_k sum_k 4a_k^2 e_k ((2l+5) - 2 a_k r^2).
+// Each primitive's factor (2l+3) - 2 a r^2 is where the Laplacian cancels; for primitives
+// marked sharp (mixed mode only) a r^2 and the factors are formed in double from r2d.
+template <typename T, int LEVEL>
+__device__ __forceinline__ void shell_eval(const DevSys& S, int s, T x, T y, T z, double r2d, T* out, int stride) {
+  const int4 sh = __ldg(S.shell + s);
+  const int l = sh.y, np = sh.z, ao0 = sh.w;
+  const T r2 = x * x + y * y + z * z;
+  const int smask = (r2d >= 0.0) ? __ldg(S.sharp + s) : 0;
+  T R0 = 0, R1 = 0, R2 = 0, LF = 0, T3 = 0;
+  for (int k = 0; k < np; ++k) {
+    const T a = prim_alpha<T>(S, s, k);
+    T e, f3, f5;
+    if ((smask >> k) & 1) {
+      const double xa = __ldg(S.alpha + s * kMaxPrim + k) * r2d;
+      e = prim_coef<T>(S, s, k) * dexp<T>((T)(-xa));
+      f3 = (T)((2 * l + 3) - 2.0 * xa);
+      f5 = (T)((2 * l + 5) - 2.0 * xa);
+    } else {
+      const T xa = a * r2;
+      e = prim_coef<T>(S, s, k) * dexp<T>(-xa);
+      f3 = T(2 * l + 3) - T(2) * xa;
+      f5 = T(2 * l + 5) - T(2) * xa;
+    }
+    R0 += e;
+    if (LEVEL >= 1) {
+      const T m2ae = T(-2) * a * e;
+      R1 += m2ae;
+      LF += m2ae * f3;
+      if (LEVEL >= 2) {
+        const T a4e = T(4) * a * a * e;
+        R2 += a4e;
+        T3 += a4e * f5;
+      }
+    }
+  }
+  const int nc = 2 * l + 1;
+  const T xs[3] = {x, y, z};
+  for (int m = 0; m < nc; ++m) {
+    T P, g[3], h[6];
+    angular<T>(l, m, x, y, z, P, g, h);
+    const int ao = ao0 + m;
+    if (LEVEL == 0) {
+      out[ao] = P * R0;
+    } else {
+      T grad[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) grad[i] = g[i] * R0 + P * xs[i] * R1;
+      if (LEVEL == 1) {
+        out[0 * stride + ao] = grad[0];
+        out[1 * stride + ao] = grad[1];
+        out[2 * stride + ao] = grad[2];
+        out[3 * stride + ao] = P * LF;
+      } else {
+        out[0 * stride + ao] = P * R0;
+        out[1 * stride + ao] = grad[0];
+        out[2 * stride + ao] = grad[1];
+        out[3 * stride + ao] = grad[2];
+        out[4 * stride + ao] = P * LF;
+        const int hi[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const int i = hi[k][0], j = hi[k][1];
+          out[(5 + k) * stride + ao] = h[k] * R0 + (g[i] * xs[j] + g[j] * xs[i]) * R1 +
+                                       P * (xs[i] * xs[j] * R2 + (i == j ? R1 : T(0)));
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[(11 + k) * stride + ao] = g[k] * LF + P * xs[k] * T3;
+      }
+    }
+  }
+}
+
+// Displacement of an electron from nucleus c: double in FP64 mode; in mixed mode the
+// float-float difference, accurate to a float ulp of the displacement itself.
+template <typename T>
+__device__ __forceinline__ void disp_nuc(const DevSys& S, const EPos& p, int c, T d[3]);
+template <>
+__device__ __forceinline__ void disp_nuc<double>(const DevSys& S, const EPos& p, int c, double d[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = p.d[k] - __ldg(S.R + 3 * c + k);
+}
+template <>
+__device__ __forceinline__ void disp_nuc<float>(const DevSys& S, const EPos& p, int c, float d[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) d[k] = (p.h[k] - __ldg(S.Rh + 3 * c + k)) + (p.l[k] - __ldg(S.Rl + 3 * c + k));
+}
+
+// AO components at one point for all shells, threads of the group over shells. SHARP64:
+// form a r^2 of sharp primitives in double (mixed mode).
+template <typename T, int GS, int LEVEL, bool SHARP64>
+__device__ __forceinline__ void ao_point(const DevSys& S, const EPos& p, T* out, int stride) {
+  const int t = threadIdx.x % GS;
+  for (int s = t; s < S.nshell; s += GS) {
+    const int c = __ldg(S.shell + s).x;
+    T d[3];
+    disp_nuc<T>(S, p, c, d);
+    double r2d = -1.0;
+    if (SHARP64 && sizeof(T) == 4 && __ldg(S.sharp + s)) {
+      const double dx = p.d[0] - __ldg(S.R + 3 * c), dy = p.d[1] - __ldg(S.R + 3 * c + 1),
+                   dz = p.d[2] - __ldg(S.R + 3 * c + 2);
+      r2d = dx * dx + dy * dy + dz * dz;
+    }
+    shell_eval<T, LEVEL>(S, s, d[0], d[1], d[2], r2d, out, stride);
+  }
+}
+
+// Electron-electron displacement from the shared-memory position arrays.
+template <typename T>
+__device__ __forceinline__ T edisp(const double* pos, const float* ph, const float* pl, int i, int j, int c);
+template <>
+__device__ __forceinline__ double edisp<double>(const double* pos, const float*, const float*, int i, int j, int c) {
+  return pos[3 * i + c] - pos[3 * j + c];
+}
+template <>
+__device__ __forceinline__ float edisp<float>(const double*, const float* ph, const float* pl, int i, int j, int c) {
+  return (ph[3 * i + c] - ph[3 * j + c]) + (pl[3 * i + c] - pl[3 * j + c]);
+}
+
+// ---------------------------------------------------------------- Jastrow radial functions
+// Pade a r / (1 + F r) and its first three derivatives.
+template <typename T>
+struct Rad3 { T h, h1, h2, h3; };
+template <typename T>
+__device__ __forceinline__ Rad3<T> pade(T a, T F, T r) {
+  const T q = T(1) / (T(1) + F * r);
+  const T q2 = q * q;
+  return {a * r * q, a * q2, T(-2) * a * F * q2 * q, T(6) * a * F * F * q2 * q2};
+}
+template <typename T>
+__device__ __forceinline__ T pade_value(T a, T F, T r) {
+  return a * r / (T(1) + F * r);
+}
+
+// ---------------------------------------------------------------- FP64 Gauss-Jordan inverse
+// In-place inversion of the n x n row-major matrix A (shared memory, double) with partial
+// row pivoting. piv: int[n], f: double[n] scratch, flag: int (set to 1 if a pivot is zero
+// or not finite). logabs/sign are accumulated when want_logdet. Every thread of the group
+// must call it.
+template <int GS>
+__device__ void gj_inverse(double* A, int n, int* piv, double* f, int* flag, double* logabs, double* sgn,
+                           bool want_logdet) {
+  const int t = threadIdx.x % GS;
+  for (int k = 0; k < n; ++k) {
+    // pivot search by the first warp of the group
+    if (t < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + t; i < n; i += 32) {
+        const double v = fabs(A[i * n + k]);
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (t == 0) {
+        piv[k] = bi;
+        const double p = A[bi * n + k];
+        if (!(p != 0.0) || !isfinite(p)) *flag = 1;
+        if (want_logdet) {
+          *logabs += log(fabs(p));
+          if (p < 0) *sgn = -*sgn;
+          if (bi != k) *sgn = -*sgn;
+        }
+      }
+    }
+    gsync<GS>();
+    const int p = piv[k];
+    if (p != k)
+      for (int j = t; j < n; j += GS) {
+        const double a = A[k * n + j];
+        A[k * n + j] = A[p * n + j];
+        A[p * n + j] = a;
+      }
+    gsync<GS>();
+    const double pinv = 1.0 / A[k * n + k];
+    for (int i = t; i < n; i += GS) f[i] = A[i * n + k];
+    gsync<GS>();
+    for (int j = t; j < n; j += GS) A[k * n + j] = (j == k ? 1.0 : A[k * n + j]) * pinv;
+    gsync<GS>();
+    for (int idx = t; idx < n * n; idx += GS) {
+      const int i = idx / n, j = idx - i * n;
+      if (i != k) A[idx] = (j == k ? 0.0 : A[idx]) - f[i] * A[k * n + j];
+    }
+    gsync<GS>();
+  }
+  // undo the row permutation as column swaps, last pivot first
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = t; i < n; i += GS) {
+        const double a = A[i * n + k];
+        A[i * n + k] = A[i * n + p];
+        A[i * n + p] = a;
+      }
+    gsync<GS>();
+  }
+}
+
+// ---------------------------------------------------------------- Slater matrix build
+// A^s_{el, i} = phi_i(r_e) = sum_mu psi_mu(r_e) C^s_{mu i} (Eq. restricted-C), computed
+// in T and stored in double for the inversion. aorow: T[M] scratch.
+template <typename T, int GS>
+__device__ void build_slater(const DevSys& S, const double* pos, int sg, double* A, T* aorow) {
+  const int t = threadIdx.x % GS;
+  const int n = sg == 0 ? S.nup : S.ndn, e0 = sg == 0 ? 0 : S.nup;
+  const T* C = coefC<T>(S, sg);
+  for (int el = 0; el < n; ++el) {
+    const EPos p = make_epos(pos + 3 * (e0 + el));
+    ao_point<T, GS, 0, true>(S, p, aorow, 0);
+    gsync<GS>();
+    for (int i = t; i < n; i += GS) {
+      T v = 0;
+      for (int mu = 0; mu < S.M; ++mu) v += aorow[mu] * __ldg(C + mu * n + i);
+      A[el * n + i] = (double)v;
+    }
+    gsync<GS>();
+  }
+}
+
+}  // namespace vmcf

@@ -1,0 +1,65 @@
+// Internal interfaces between the host API (vmcf_api.cu) and the kernel translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "vmcf_device.cuh"
+
+namespace vmcf {
+
+// Byte offsets of one walker group's shared-memory region; computed on the host.
+struct GroupLayout {
+  int pos, ph, pl, Bd, Bt, P, Q, Jg, Jl, gd, ao, mo, frc, Ow, D, piv, f, red, scal, row, wv, col;
+  int bytes;  // size of one group's region (16-byte multiple)
+};
+
+struct Launch {
+  int GS;          // threads per walker group: 32 or 128
+  int groups;      // groups per CTA
+  int grid;        // CTAs
+  size_t smem;     // dynamic shared memory per CTA
+  GroupLayout L;
+  int acc_off;     // CTA accumulator region offset (measure kernel), -1 if none
+};
+
+struct MoveParams {
+  double* pos;      // [W][Ne][3]
+  void* B;          // T [W][nB]
+  uint32_t* nacc;   // [W]
+  uint32_t* nrej;   // [W]
+  unsigned long long* counters;  // [0] singular inversions, [1] refreshes
+  int W;
+  uint64_t wid0, k0, k1, sweep0;
+  int nsweeps, kref, c0, skip_final_refresh;
+  double sigma;
+};
+
+struct MeasParams {
+  const double* pos;  // [W][Ne][3]
+  void* Bout;         // T [W][nB] or NULL
+  double *EL, *logpsi, *dlnpsi, *dEL, *O, *dELdC;  // outputs or NULL
+  double* acc;        // [grid][accL] FP64 slots, or NULL
+  int accL, acc_in_smem;
+  double e_ref;
+  unsigned long long* counters;
+  int W;
+};
+
+// Launchers (one instantiation per precision and group size, see k_fp64.cu / k_fp32.cu).
+template <typename T>
+cudaError_t launch_refresh(const DevSys& S, const Launch& lc, const double* pos, void* B, int W,
+                           unsigned long long* counters, cudaStream_t st);
+template <typename T>
+cudaError_t launch_move(const DevSys& S, const Launch& lc, const MoveParams& P, cudaStream_t st);
+template <typename T>
+cudaError_t launch_measure(const DevSys& S, const Launch& lc, const MeasParams& P, cudaStream_t st);
+template <typename T>
+cudaError_t set_smem_limits(int GS);
+
+cudaError_t run_probes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, cudaStream_t st);
+
+cudaError_t launch_block_reduce(const double* acc, int grid, int cpb, int accL, double* out, int nblocks,
+                                cudaStream_t st);
+
+}  // namespace vmcf

@@ -1,0 +1,277 @@
+"""Thin Python binding of the C ABI in include/vmcf.h (argument marshalling only).
+
+Every step of the VMC path runs in libvmcf's CUDA kernels; this module only converts
+arguments: device buffers are torch CUDA tensors (data_ptr), streams are torch streams.
+If the compiled library is missing, loading fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+from . import build as _build
+
+FP64, MIXED = 0, 1
+_STATUS = {0: "VMCF_OK", -1: "VMCF_EINVAL", -2: "VMCF_ENOMEM", -3: "VMCF_ECUDA", -4: "VMCF_ESINGULAR",
+           -5: "VMCF_ETIMEOUT", -6: "VMCF_ENOTSUP"}
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+
+
+class VmcfError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().vmcf_last_error().decode()
+        super().__init__(f"{where}: {_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Nuclei(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("Z", _ip), ("R", _dp)]
+
+
+class _Basis(ctypes.Structure):
+    _fields_ = [("nshell", ctypes.c_int), ("maxprim", ctypes.c_int), ("center", _ip), ("l", _ip), ("nprim", _ip),
+                ("exps", _dp), ("coefs", _dp)]
+
+
+class _Jastrow(ctypes.Structure):
+    _fields_ = [("F_anti", ctypes.c_double), ("F_par", ctypes.c_double), ("a_anti", ctypes.c_double),
+                ("a_par", ctypes.c_double), ("b_en", ctypes.c_double), ("enable_J1", ctypes.c_int),
+                ("enable_J2", ctypes.c_int)]
+
+
+class Counters(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in
+                ("moves", "accepted", "rejected_nonfinite", "singular", "refreshes", "sweeps", "measured_sweeps")]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+def library_path() -> Path:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libvmcf.so (building it with nvcc when missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing:
+            _build.build()
+        path = _build.LIB
+        if not path.exists():
+            raise RuntimeError(f"libvmcf.so not found at {path}; run paper_2511_05222_gb300.build.build()")
+        L = ctypes.CDLL(str(path))
+        L.vmcf_last_error.restype = ctypes.c_char_p
+        L.vmcf_strerror.restype = ctypes.c_char_p
+        L.vmcf_init_system.argtypes = [ctypes.POINTER(_Nuclei), ctypes.POINTER(_Basis), _dp, _dp, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(_Jastrow), _dp, ctypes.c_int, ctypes.POINTER(_vp)]
+        L.vmcf_system_destroy.argtypes = [_vp]
+        L.vmcf_system_info.argtypes = [_vp, _ip, _ip, _ip, _ip]
+        L.vmcf_accumulator_length.argtypes = [_vp]
+        L.vmcf_walkers_create.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                          ctypes.c_uint64, ctypes.c_int, _vp, ctypes.POINTER(_vp)]
+        L.vmcf_walkers_destroy.argtypes = [_vp]
+        L.vmcf_walkers_set_positions.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
+        L.vmcf_walkers_get_positions.argtypes = [_vp, _vp, ctypes.c_int, _vp]
+        L.vmcf_reset_accumulators.argtypes = [_vp, ctypes.c_double, _vp]
+        L.vmcf_sample.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp]
+        L.vmcf_evaluate.argtypes = [_vp, _vp, ctypes.c_int] + [_vp] * 6 + [_vp]
+        L.vmcf_reduce_estimators.argtypes = [_vp, _vp] + [_dp] * 7 + [_vp]
+        L.vmcf_block_sums.argtypes = [_vp, _vp, _dp, _vp]
+        L.vmcf_status_counters.argtypes = [_vp, ctypes.POINTER(Counters), _vp]
+        L.vmcf_profile.argtypes = [_vp, ctypes.c_int]
+        L.vmcf_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
+        L.vmcf_probe_pipes.argtypes = [_dp, _dp, _dp, _vp]
+        _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise VmcfError(code, where)
+
+
+def _ptr(t):
+    """Device pointer of a torch CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or t.dtype.itemsize != 8:
+        raise ValueError("device buffers must be contiguous float64 CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _np(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+class System:
+    """vmcf_init_system: a molecule, its basis, frozen orbitals and Jastrow, on the GPU."""
+
+    def __init__(self, sys, precision: int = FP64):
+        L = lib()
+        j = sys.jastrow
+        self._hold = dict(Z=_np(sys.Z, np.int32), R=_np(sys.R, np.float64), c=_np(sys.shell_center, np.int32),
+                          l=_np(sys.shell_l, np.int32), np=_np(sys.shell_nprim, np.int32),
+                          e=_np(sys.shell_exp, np.float64), co=_np(sys.shell_coef, np.float64),
+                          Cu=_np(sys.C_up, np.float64), Cd=_np(sys.C_dn, np.float64),
+                          S=None if sys.S is None else _np(sys.S, np.float64))
+        h = self._hold
+        dp = lambda a: None if a is None else a.ctypes.data_as(_dp)
+        ip = lambda a: a.ctypes.data_as(_ip)
+        nuc = _Nuclei(sys.K, ip(h["Z"]), dp(h["R"]))
+        bas = _Basis(sys.nshell, h["e"].shape[1], ip(h["c"]), ip(h["l"]), ip(h["np"]), dp(h["e"]), dp(h["co"]))
+        jas = _Jastrow(j.F_anti, j.F_par, j.a_anti, j.a_par, j.b_en, int(j.enable_J1), int(j.enable_J2))
+        out = _vp()
+        _check(L.vmcf_init_system(ctypes.byref(nuc), ctypes.byref(bas), dp(h["Cu"]), dp(h["Cd"]), sys.n_up, sys.n_dn,
+                                  ctypes.byref(jas), dp(h["S"]), precision, ctypes.byref(out)), "vmcf_init_system")
+        self.h = out
+        self.precision = precision
+        self.sys = sys
+        K, M, nu, nd = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(L.vmcf_system_info(self.h, ctypes.byref(K), ctypes.byref(M), ctypes.byref(nu), ctypes.byref(nd)),
+               "vmcf_system_info")
+        self.K, self.M, self.n_up, self.n_dn = K.value, M.value, nu.value, nd.value
+        self.Ne = self.n_up + self.n_dn
+        self.nO = self.M * self.Ne
+        self.accL = L.vmcf_accumulator_length(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vmcf_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vmcf_evaluate(system: System, pos, want=("EL",), stream=None):
+    """vmcf_evaluate on device positions pos (W, Ne, 3) float64. Returns a dict of torch
+    CUDA tensors for the requested outputs among EL, logpsi, dlnpsi_dR, dEL_dR, O, dEL_dC."""
+    import torch
+    W = pos.shape[0]
+    dev = pos.device
+    shapes = {"EL": (W,), "logpsi": (W,), "dlnpsi_dR": (W, system.K, 3), "dEL_dR": (W, system.K, 3),
+              "O": (W, system.nO), "dEL_dC": (W, system.nO)}
+    out = {k: torch.empty(shapes[k], dtype=torch.float64, device=dev) for k in want}
+    order = ["EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O", "dEL_dC"]
+    _check(lib().vmcf_evaluate(system.h, _ptr(pos.contiguous()), W, *[_ptr(out.get(k)) for k in order],
+                               _stream(stream)), "vmcf_evaluate")
+    return out
+
+
+class Walkers:
+    """vmcf_walkers_create: device walker state for sampling."""
+
+    def __init__(self, system: System, pos, key=(5222, 1), wid0: int = 0, nblocks: int = 64, stream=None):
+        L = lib()
+        self.system = system
+        out = _vp()
+        if isinstance(pos, np.ndarray):
+            self._host = _np(pos, np.float64)
+            W = self._host.shape[0]
+            p, is_host = ctypes.c_void_p(self._host.ctypes.data), 1
+        else:
+            W = pos.shape[0]
+            p, is_host = _ptr(pos.contiguous()), 0
+        _check(L.vmcf_walkers_create(system.h, W, p, is_host, int(key[0]), int(key[1]), int(wid0), nblocks,
+                                     _stream(stream), ctypes.byref(out)), "vmcf_walkers_create")
+        self.h = out
+        self.W = W
+        self.nblocks = nblocks
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vmcf_walkers_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_positions(self, pos, stream=None):
+        if isinstance(pos, np.ndarray):
+            a = _np(pos, np.float64)
+            _check(lib().vmcf_walkers_set_positions(self.system.h, self.h, ctypes.c_void_p(a.ctypes.data), 1,
+                                                    _stream(stream)), "vmcf_walkers_set_positions")
+        else:
+            _check(lib().vmcf_walkers_set_positions(self.system.h, self.h, _ptr(pos.contiguous()), 0,
+                                                    _stream(stream)), "vmcf_walkers_set_positions")
+
+    def positions(self, stream=None) -> np.ndarray:
+        out = np.empty((self.W, self.system.Ne, 3))
+        _check(lib().vmcf_walkers_get_positions(self.h, ctypes.c_void_p(out.ctypes.data), 1, _stream(stream)),
+               "vmcf_walkers_get_positions")
+        return out
+
+    def positions_into(self, dev_tensor, stream=None):
+        _check(lib().vmcf_walkers_get_positions(self.h, _ptr(dev_tensor), 0, _stream(stream)),
+               "vmcf_walkers_get_positions")
+
+    def reset_accumulators(self, e_ref: float, stream=None):
+        _check(lib().vmcf_reset_accumulators(self.h, float(e_ref), _stream(stream)), "vmcf_reset_accumulators")
+
+    def sample(self, n_sweeps: int, step_sigma: float = 0.3, refresh_k: int = 26, measure: bool = False,
+               stream=None):
+        _check(lib().vmcf_sample(self.system.h, self.h, int(n_sweeps), float(step_sigma), int(refresh_k),
+                                 int(bool(measure)), _stream(stream)), "vmcf_sample")
+
+    def reduce_estimators(self, with_rhs: bool = False, stream=None) -> dict:
+        s = self.system
+        E, Ee = np.zeros(1), np.zeros(1)
+        F, Fe = np.zeros(3 * s.K), np.zeros(3 * s.K)
+        B, Be = np.zeros(s.nO), np.zeros(s.nO)
+        rhs = np.zeros(s.nO) if with_rhs else None
+        dp = lambda a: None if a is None else a.ctypes.data_as(_dp)
+        _check(lib().vmcf_reduce_estimators(s.h, self.h, dp(E), dp(Ee), dp(F), dp(Fe), dp(B), dp(Be), dp(rhs),
+                                            _stream(stream)), "vmcf_reduce_estimators")
+        out = {"E": float(E[0]), "E_err": float(Ee[0]), "F": F.reshape(s.K, 3), "F_err": Fe.reshape(s.K, 3),
+               "dEdC": B, "dEdC_err": Be}
+        if with_rhs:
+            out["rhs_BQ"] = rhs
+        return out
+
+    def block_sums(self, stream=None) -> np.ndarray:
+        s = self.system
+        out = np.zeros((self.nblocks, s.accL))
+        _check(lib().vmcf_block_sums(s.h, self.h, out.ctypes.data_as(_dp), _stream(stream)), "vmcf_block_sums")
+        return out
+
+    def profile(self, enable: bool = True):
+        _check(lib().vmcf_profile(self.h, int(enable)), "vmcf_profile")
+
+    def kernel_times(self, reset: bool = True) -> dict:
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_longlong * 3)()
+        _check(lib().vmcf_kernel_times(self.h, ms, n, int(reset)), "vmcf_kernel_times")
+        names = ("move", "measure", "refresh")
+        return {names[k]: {"ms": float(ms[k]), "launches": int(n[k])} for k in range(3)}
+
+    def counters(self, stream=None) -> dict:
+        c = Counters()
+        _check(lib().vmcf_status_counters(self.h, ctypes.byref(c), _stream(stream)), "vmcf_status_counters")
+        return c.as_dict()
+
+
+def vmcf_probe_pipes(stream=None) -> dict:
+    """Measured FP64/FP32 FMA throughput (TFLOP/s) and FP32 expf throughput (G/s)."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().vmcf_probe_pipes(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _stream(stream)),
+           "vmcf_probe_pipes")
+    return {"fp64_tflops": a.value, "fp32_tflops": b.value, "exp_gops": c.value}

@@ -1,0 +1,49 @@
+"""Algorithmic work of one walker-evaluation, by pipe, for the roofline.
+
+One walker-eval = one measured sweep of one walker: Ne single-electron Metropolis moves
+(AO row, MO row, determinant and Jastrow ratios, Sherman-Morrison update on acceptance)
+followed by one evaluation of E_L, d ln Psi/dR, dE_L/dR and O with its walker sums.
+
+Only what the method has to compute is counted (one AO evaluation per electron with all
+derivatives, one MO contraction, one inversion per spin, one adjoint sweep); recomputation
+done by an implementation is not counted, so it lowers the achieved fraction. Counts are
+flops (an FMA is 2) split by the pipe that executes them in mixed mode: FP64 (inversion,
+ratio dot products) and FP32 (everything else), plus exponentials (one per primitive per
+electron per pass) counted separately for the SFU.
+"""
+from __future__ import annotations
+
+
+def per_walker_eval(K: int, M: int, n_up: int, n_dn: int, nprim: int, acc: float = 0.5) -> dict:
+    Ne = n_up + n_dn
+    ns = [n_up] * n_up + [n_dn] * n_dn  # orbital count seen by each electron
+    move = {
+        "exp": Ne * nprim,
+        "fp32": sum(3 * nprim + 3 * M + 2 * M * n + (Ne - 1 + K) * 16 + acc * 4 * n * n for n in ns),
+        "fp64": sum(2 * n for n in ns),
+    }
+    spins = [n for n in (n_up, n_dn) if n > 0]
+    measure = {
+        "exp": Ne * nprim,
+        "fp32": (Ne * (8 * nprim + 40 * M)                       # AO value, gradient, Laplacian, Hessian, grad-Laplacian
+                 + sum(10 * M * n for n in ns)                   # MO rows: value, gradient (3), Laplacian
+                 + 25 * (Ne * (Ne - 1) // 2) + 25 * Ne * K       # Jastrow and potentials
+                 + sum(8 * n for n in ns)                        # drift and Laplacian ratios
+                 + sum(4 * n ** 3 for n in spins)                # adjoint weights B P B
+                 + sum(4 * M * n for n in ns) + 30 * Ne * M      # back-projection and force contraction
+                 + 40 * Ne * K                                   # e-n Jastrow and V_en derivatives
+                 + sum(2 * M * n for n in ns)                    # O
+                 + sum(4 * M * n for n in spins) + 18 * K),      # walker sums
+        "fp64": sum(2 * n ** 3 for n in spins),                  # Gauss-Jordan inversion per spin
+    }
+    total = {k: move[k] + measure[k] for k in move}
+    return {"move": move, "measure": measure, "total": total}
+
+
+def roofline_time(work: dict, peaks: dict) -> tuple[str, float]:
+    """Binding pipe and the time (s) one unit of `work` needs at the measured peaks."""
+    t = {"fp32": work["fp32"] / (peaks["fp32_tflops"] * 1e12),
+         "fp64": work["fp64"] / (peaks["fp64_tflops"] * 1e12),
+         "sfu": work["exp"] / (peaks["exp_gops"] * 1e9)}
+    bound = max(t, key=t.get)
+    return bound, t[bound]

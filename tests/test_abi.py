@@ -1,0 +1,35 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every entry point
+that include/vmcf.h declares (no compute call is made here)."""
+import re
+from pathlib import Path
+
+from paper_2511_05222_gb300 import vmcf
+
+HEADER = Path(__file__).resolve().parents[1] / "include" / "vmcf.h"
+
+
+def test_library_exports_every_declared_symbol():
+    L = vmcf.lib()
+    declared = set(re.findall(r"\b(vmcf_[a-z_]+)\s*\(", HEADER.read_text()))
+    assert len(declared) >= 14
+    missing = [n for n in sorted(declared) if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_error_text():
+    L = vmcf.lib()
+    assert L.vmcf_strerror(0) == b"ok"
+    assert L.vmcf_strerror(-4) == b"singular Slater matrix"
+    assert L.vmcf_strerror(12345) == b"unknown status"
+
+
+def test_invalid_arguments_are_rejected_without_touching_the_gpu():
+    import ctypes
+    L = vmcf.lib()
+    out = ctypes.c_void_p()
+    # NULL inputs: rejected before any CUDA call
+    rc = L.vmcf_init_system(None, None, None, None, 1, 1, None, None, 0, ctypes.byref(out))
+    assert rc == -1 and out.value is None
+    assert b"NULL" in L.vmcf_last_error()
+    assert L.vmcf_sample(None, None, 1, 0.3, 26, 0, None) == -1
+    assert L.vmcf_evaluate(None, None, 1, None, None, None, None, None, None, None) == -1

@@ -1,0 +1,155 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on identical seeded inputs.
+
+FP64 mode: every output within 1e-10 relative, normwise per tensor (max|a-b| / max|b|).
+Mixed mode: per-walker E_L within 1e-5 relative; the other outputs are reported by the
+mixed-vs-FP64 statistical tests.
+Sampling: FP64 trajectories follow the oracle's Markov chain (same Philox streams);
+acceptance decisions are compared except where the oracle saw a near tie.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import estimators
+from paper_2511_05222_gb300 import systems as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2511_05222_gb300 import vmcf  # noqa: E402
+
+TOL64 = 1e-10
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def gpu_eval(system, pos, want):
+    out = vmcf.vmcf_evaluate(system, dev(pos), want=want)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+ALL = ("EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O", "dEL_dC")
+
+
+@pytest.mark.parametrize("W", [1, 37, 256])
+def test_evaluate_fp64_water(sys0, W):
+    pos = S.initial_walkers(sys0, W, seed=5)
+    ref = oracle.Oracle(sys0).eval(pos, want=ALL)
+    got = gpu_eval(vmcf.System(sys0, vmcf.FP64), pos, ALL)
+    for k in ALL:
+        assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
+
+
+def test_evaluate_fp64_c2oh6(sys1):
+    pos = S.initial_walkers(sys1, 96, seed=6)
+    ref = oracle.Oracle(sys1).eval(pos, want=ALL)
+    got = gpu_eval(vmcf.System(sys1, vmcf.FP64), pos, ALL)
+    for k in ALL:
+        assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
+
+
+def test_evaluate_fp64_c9o4h8_sample():
+    sys4 = S.make_system(4)
+    pos = S.initial_walkers(sys4, 6, seed=7)
+    want = ("EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O")
+    ref = oracle.Oracle(sys4).eval(pos, want=want)
+    got = gpu_eval(vmcf.System(sys4, vmcf.FP64), pos, want)
+    for k in want:
+        assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_evaluate_mixed_local_energy(cfg):
+    sysx = S.make_system(cfg)
+    pos = S.initial_walkers(sysx, 512, seed=8)
+    ref = oracle.Oracle(sysx).eval(pos, want=("EL",))["EL"]
+    got = gpu_eval(vmcf.System(sysx, vmcf.MIXED), pos, ("EL",))["EL"]
+    r = np.abs(got - ref) / np.abs(ref)
+    assert np.median(r) < 1e-6
+    assert np.quantile(r, 0.99) < 1e-5, np.sort(r)[-10:]
+
+
+def test_hydrogen_closed_form_on_gpu():
+    """One electron in exp(-a r^2) about a proton, no Jastrow: E_L = 3a - 2a^2 r^2 - 1/r."""
+    a = 0.7
+    sysx = S.custom_system("H", [1], [[0, 0, 0]], [(0, 0, [a], [1.0])], 1, 0, [[1.0]], None,
+                           S.Jastrow(enable_J1=False, enable_J2=False))
+    pos = np.random.default_rng(0).normal(size=(33, 1, 3))
+    r = np.linalg.norm(pos[:, 0], axis=1)
+    got = gpu_eval(vmcf.System(sysx, vmcf.FP64), pos, ("EL",))["EL"]
+    np.testing.assert_allclose(got, 3 * a - 2 * a * a * r * r - 1 / r, rtol=1e-12)
+
+
+def block_map(W, nb):
+    """The library's jackknife blocks: block b holds walkers [W b / nb, W (b + 1) / nb)."""
+    blk = np.zeros(W, int)
+    for b in range(nb):
+        blk[(W * b) // nb:(W * (b + 1)) // nb] = b
+    return blk
+
+
+@pytest.mark.parametrize("kref", [26, 7])
+def test_fp64_trajectories_follow_the_oracle(sys0, kref):
+    W, sweeps = 128, 4
+    pos = S.initial_walkers(sys0, W, seed=9)
+    o = oracle.Oracle(sys0)
+    st = o.new_state(pos, key=(5222, 0))
+    o.sample(st, sweeps, sigma=0.3, refresh_k=kref)
+    g = vmcf.System(sys0, vmcf.FP64)
+    wk = vmcf.Walkers(g, pos, key=(5222, 0), nblocks=8)
+    wk.sample(sweeps, 0.3, kref, measure=False)
+    gp = wk.positions()
+    ok = st["margin"] >= 1e-9  # walkers whose every decision was clear of a tie
+    assert ok.sum() >= W - 2
+    assert np.abs(gp[ok] - st["pos"][ok]).max() < 1e-9
+    if ok.all():
+        assert wk.counters()["accepted"] == int(st["nacc"].sum())
+
+
+def test_fp64_measured_estimators_match_the_oracle(sys0):
+    W, nb, warm, meas, e_ref = 256, 8, 3, 3, -76.0
+    pos = S.initial_walkers(sys0, W, seed=10)
+    o = oracle.Oracle(sys0)
+    st = o.new_state(pos, key=(5222, 0))
+    o.sample(st, warm)
+    g = vmcf.System(sys0, vmcf.FP64)
+    wk = vmcf.Walkers(g, pos, key=(5222, 0), nblocks=nb)
+    wk.sample(warm, measure=False)
+    wk.reset_accumulators(e_ref)
+    wk.sample(meas, measure=True)
+    sums = estimators.new_sums(nb, sys0.K, o.nO)
+    blk = block_map(W, nb)
+    for _ in range(meas):
+        o.sample(st, 1)
+        o.force_refresh(st)
+        out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+        estimators.accumulate(sums, blk, out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], e_ref)
+    assert st["margin"].min() >= 1e-9
+    assert np.abs(wk.positions() - st["pos"]).max() < 1e-9
+    np.testing.assert_array_equal(wk.block_sums()[:, 0], sums["n"])
+    ref = estimators.finish(sums, e_ref)
+    got = wk.reduce_estimators()
+    assert abs(got["E"] - ref["E"]) < 1e-10 * abs(ref["E"])
+    assert rel(got["F"].ravel(), ref["F"]) < 1e-9
+    assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
+    assert abs(got["E_err"] - ref["E_err"]) < 1e-8 * ref["E_err"]
+    assert rel(got["F_err"].ravel(), ref["F_err"]) < 1e-7
+    assert rel(got["dEdC_err"], ref["dEdC_err"]) < 1e-7
+
+
+def test_counters_and_singular_free_run(sys1):
+    g = vmcf.System(sys1, vmcf.MIXED)
+    wk = vmcf.Walkers(g, S.initial_walkers(sys1, 512, seed=11), key=(5222, 1), nblocks=16)
+    wk.sample(5, measure=False)
+    c = wk.counters()
+    assert c["moves"] == 5 * 512 * sys1.Ne
+    assert 0.2 < c["accepted"] / c["moves"] < 0.9
+    assert c["singular"] == 0
