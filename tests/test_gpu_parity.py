@@ -68,13 +68,18 @@ def test_evaluate_fp64_c9o4h8_sample():
 
 @pytest.mark.parametrize("cfg", [0, 1])
 def test_evaluate_mixed_local_energy(cfg):
+    """Mixed mode on walkers drawn from |Psi|^2 (40 oracle sweeps): per-walker E_L within
+    1e-5 of max(|E_L|, |mean E_L|) (normwise reading: E_L crosses zero on some walkers)."""
     sysx = S.make_system(cfg)
-    pos = S.initial_walkers(sysx, 512, seed=8)
-    ref = oracle.Oracle(sysx).eval(pos, want=("EL",))["EL"]
+    o = oracle.Oracle(sysx)
+    st = o.new_state(S.initial_walkers(sysx, 512, seed=8), key=(5222, 8))
+    o.sample(st, 40)
+    pos = st["pos"]
+    ref = o.eval(pos, want=("EL",))["EL"]
     got = gpu_eval(vmcf.System(sysx, vmcf.MIXED), pos, ("EL",))["EL"]
-    r = np.abs(got - ref) / np.abs(ref)
+    r = np.abs(got - ref) / np.maximum(np.abs(ref), abs(ref.mean()))
     assert np.median(r) < 1e-6
-    assert np.quantile(r, 0.99) < 1e-5, np.sort(r)[-10:]
+    assert r.max() < 1e-5, np.sort(r)[-10:]
 
 
 def test_hydrogen_closed_form_on_gpu():
