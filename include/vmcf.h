@@ -160,6 +160,26 @@ int vmcf_accumulator_length(vmcf_system_t sys);
 /* Counters (synchronises the stream). */
 int vmcf_status_counters(vmcf_walkers_t wk, vmcf_counters* out, void* stream);
 
+/* Fixed-walker evaluation reduced to walker sums, allocating nothing (the paper has no
+ * counterpart; this is a deployment variant of vmcf_evaluate plus vmcf_block_sums).
+ * It is for callers that must not allocate GPU memory while they run, for example code
+ * embedded in a host application that hands the library only buffers it already owns, or
+ * a loop that cannot afford the device-wide synchronisation a cudaMalloc or cudaFree can
+ * cause. The system must already exist (vmcf_init_system allocates once, at set-up).
+ *   pos: device [W][Ne][3]; e_ref: reference energy, as in vmcf_reset_accumulators;
+ *   sums: device [vmcf_accumulator_length()] doubles, written (not added to) with the sums
+ *   over all W walkers in the vmcf_block_sums layout for one block.
+ * Scratch: a fixed array of 2^21 doubles (16 MiB) in this library's device memory holds the
+ * per-CTA partial sums; every GPU that loads the library keeps it until the process exits.
+ * A system whose sum vector is longer than 2^21 doubles is rejected with VMCF_EINVAL.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. All calls share the array: each call
+ * clears the part it uses, and calls whose kernels overlap on the GPU race with each other
+ * (serialise them, e.g. on one stream). The call calls no cudaMalloc, cudaFree or other
+ * allocating routine. */
+int vmcf_evaluate_sums_noalloc(vmcf_system_t sys, const double* pos, int W, double e_ref, double* sums,
+                               void* stream);
+
 /* Diagnostics (not part of the paper's method).
  * vmcf_profile: record a CUDA event pair around every kernel this walker set launches from
  * now on (enable != 0) or stop recording (0).

@@ -9,7 +9,7 @@
 #include <vector>
 
 #include "../../include/vmcf.h"
-#include "vmcf_internal.h"
+#include "vmcf_host.h"
 
 using namespace vmcf;
 
@@ -39,45 +39,6 @@ constexpr int kSmemCap = 227 * 1024;
 constexpr double kSharpAlpha = 48.0;
 
 }  // namespace
-
-struct vmcf_system_s {
-  int precision = 0;
-  int K = 0, M = 0, nup = 0, ndn = 0, Ne = 0, nshell = 0, nB = 0, nmax = 0;
-  std::vector<double> R, Z, S, C[2];
-  std::vector<int> ao_center;
-  bool has_S = false;
-  DevSys dev{};
-  void* dmem = nullptr;
-  // launch planning
-  int GS = 32;
-  GroupLayout Lrm{}, Lmeas{}, LmeasD{};
-  int gpb_rm = 1, gpb_meas = 1, gpb_measD = 1;
-  int accL = 0;
-  bool acc_smem = false;
-  int acc_off = -1;
-  double* scratch_counters = nullptr;  // device [2] for evaluate
-};
-
-struct vmcf_walkers_s {
-  vmcf_system_s* sys = nullptr;
-  int W = 0, nblocks = 0, cpb = 1, grid_meas = 1;
-  uint64_t k0 = 0, k1 = 0, wid0 = 0;
-  double* pos = nullptr;
-  void* B = nullptr;
-  uint32_t* nacc = nullptr;
-  uint32_t* nrej = nullptr;
-  unsigned long long* counters = nullptr;  // [0] singular, [1] refreshes
-  double* acc = nullptr;                   // [grid_meas][accL]
-  double* blocks = nullptr;                // [nblocks][accL]
-  uint64_t sweep = 0, measured = 0;
-  int counter = 0;
-  double e_ref = 0.0;
-  // per-kernel timing (kind 0 move, 1 measure, 2 refresh): event pairs around launches
-  bool profiling = false;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
-  double kernel_ms[3] = {0, 0, 0};
-  long long kernel_n[3] = {0, 0, 0};
-};
 
 namespace {
 // Event pair around one launch when profiling is on.
@@ -205,7 +166,9 @@ Launch launch_rm(const vmcf_system_s& s, int W) {
   return lc;
 }
 
-Launch launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD) {
+}  // namespace
+
+Launch vmcf::launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD) {
   Launch lc{};
   lc.GS = s.GS;
   if (withD) {
@@ -233,6 +196,10 @@ Launch launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD) {
   lc.grid = grid;
   return lc;
 }
+
+int vmcf::set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+
+namespace {
 
 bool finite_all(const double* p, size_t n) {
   for (size_t i = 0; i < n; ++i)

@@ -1,0 +1,56 @@
+// Host-side state of the C ABI handles, shared by the translation units that implement
+// entry points (vmcf_api.cu, noalloc.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "vmcf_internal.h"
+
+struct vmcf_system_s {
+  int precision = 0;
+  int K = 0, M = 0, nup = 0, ndn = 0, Ne = 0, nshell = 0, nB = 0, nmax = 0;
+  std::vector<double> R, Z, S, C[2];
+  std::vector<int> ao_center;
+  bool has_S = false;
+  vmcf::DevSys dev{};
+  void* dmem = nullptr;
+  // launch planning
+  int GS = 32;
+  vmcf::GroupLayout Lrm{}, Lmeas{}, LmeasD{};
+  int gpb_rm = 1, gpb_meas = 1, gpb_measD = 1;
+  int accL = 0;
+  bool acc_smem = false;
+  int acc_off = -1;
+  double* scratch_counters = nullptr;  // device [2] for evaluate
+};
+
+struct vmcf_walkers_s {
+  vmcf_system_s* sys = nullptr;
+  int W = 0, nblocks = 0, cpb = 1, grid_meas = 1;
+  uint64_t k0 = 0, k1 = 0, wid0 = 0;
+  double* pos = nullptr;
+  void* B = nullptr;
+  uint32_t* nacc = nullptr;
+  uint32_t* nrej = nullptr;
+  unsigned long long* counters = nullptr;  // [0] singular, [1] refreshes
+  double* acc = nullptr;                   // [grid_meas][accL]
+  double* blocks = nullptr;                // [nblocks][accL]
+  uint64_t sweep = 0, measured = 0;
+  int counter = 0;
+  double e_ref = 0.0;
+  // per-kernel timing (kind 0 move, 1 measure, 2 refresh): event pairs around launches
+  bool profiling = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
+  double kernel_ms[3] = {0, 0, 0};
+  long long kernel_n[3] = {0, 0, 0};
+};
+
+
+namespace vmcf {
+// Launch planning shared by the entry points (defined in vmcf_api.cu).
+Launch launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD);
+int set_last_error(int code, const std::string& msg);
+}  // namespace vmcf

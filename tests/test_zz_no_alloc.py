@@ -1,0 +1,58 @@
+"""vmcf_evaluate_sums_noalloc, the variant of the walker-sum evaluation that allocates no
+GPU memory (its scratch is a fixed array inside the library), checked through the C ABI
+against the existing vmcf_evaluate outputs summed on the host, on two calls in a row (the
+second call must not see the first call's partial sums). This file is collected last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2511_05222_gb300 import systems as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2511_05222_gb300 import vmcf  # noqa: E402
+
+
+def host_sums(out, e_ref):
+    EL = out["EL"]
+    c = EL - e_ref
+    W = EL.shape[0]
+    dl = out["dlnpsi_dR"].reshape(W, -1)
+    de = out["dEL_dR"].reshape(W, -1)
+    O = out["O"]
+    return np.concatenate([[W, EL.sum(), (EL * EL).sum()], de.sum(0), dl.sum(0), (c[:, None] * dl).sum(0),
+                           O.sum(0), (c[:, None] * O).sum(0)])
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_noalloc_sums_match_evaluate_on_two_calls(cfg):
+    sysx = S.make_system(cfg)
+    g = vmcf.System(sysx, vmcf.FP64)
+    L = vmcf.lib()
+    L.vmcf_evaluate_sums_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                             ctypes.c_void_p, ctypes.c_void_p]
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    vmcf_el = {}
+    for call, (W, seed, e_ref) in enumerate([(203, 1, -70.0), (97, 2, -60.0)]):
+        pos = torch.as_tensor(S.initial_walkers(sysx, W, seed=seed), device="cuda")
+        ref = vmcf.vmcf_evaluate(g, pos, want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+        ref = {k: v.cpu().numpy() for k, v in ref.items()}
+        vmcf_el[call] = ref["EL"]
+        ref = host_sums(ref, e_ref)
+        out = torch.full((g.accL,), float("nan"), dtype=torch.float64, device="cuda")
+        rc = L.vmcf_evaluate_sums_noalloc(g.h, ctypes.c_void_p(pos.data_ptr()), W, e_ref,
+                                          ctypes.c_void_p(out.data_ptr()), stream)
+        assert rc == 0, L.vmcf_last_error()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert got[0] == W, (call, got[0])
+        scale = np.abs(vmcf_el[call]).sum()
+        assert abs(got[1] - ref[1]) < 1e-10 * scale, (call, got[1], ref[1])
+        K3, nO = 3 * g.K, g.nO
+        seg = [(0, 3), (3, 3 + K3), (3 + K3, 3 + 2 * K3), (3 + 2 * K3, 3 + 3 * K3), (3 + 3 * K3, 3 + 3 * K3 + nO),
+               (3 + 3 * K3 + nO, 3 + 3 * K3 + 2 * nO)]
+        for a, b in seg:  # 1e-10 relative, normwise per segment (the FP64 tolerance of the parity tests)
+            err = np.abs(got[a:b] - ref[a:b]).max() / max(np.abs(ref[a:b]).max(), 1e-300)
+            assert err < 1e-10, (call, a, b, err)
