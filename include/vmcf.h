@@ -60,6 +60,12 @@ typedef enum {
                      refresh and walker sums */
 } vmcf_precision;
 
+/* OR-ed into `precision` at vmcf_init_system: run a system that fits the small-system
+ * kernels (at most 32 electrons and 16 orbitals per spin) on the general walker-group kernels
+ * instead. Both give the same results within rounding; this exists to test one against the
+ * other. */
+#define VMCF_FORCE_GROUP_PATH 0x100
+
 typedef struct vmcf_system_s* vmcf_system_t;   /* opaque, library-owned */
 typedef struct vmcf_walkers_s* vmcf_walkers_t; /* opaque, library-owned device state */
 

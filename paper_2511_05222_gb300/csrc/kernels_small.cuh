@@ -1,0 +1,799 @@
+// Small-system kernels (at most 32 electrons, 16 orbitals per spin): the VMC hot path of
+// arXiv:2511.05222, App. A, laid out so that every lane does independent work.
+//
+//  move_small     one lane per walker: a run of single-electron Metropolis moves with the
+//                 MO row in registers and the walker's inverse in walker-interleaved global
+//                 memory (coalesced across the warp)
+//  measure_small  one warp per walker, one lane per electron: AOs evaluated shell by shell
+//                 and contracted straight into register MO rows (C rows broadcast from shared
+//                 memory); FP64 Gauss-Jordan inversion and B P B cooperatively in the warp;
+//                 E_L, adjoint nuclear derivatives, O and the walker sums
+//
+// Walker state on this path: positions [3 Ne][W] (double, plus a float-float copy in mixed
+// mode) and inverses [n_up^2 + n_dn^2][W], walker index fastest.
+#pragma once
+#include "vmcf_device.cuh"
+#include "vmcf_internal.h"
+
+namespace vmcf {
+
+// Radial sums of a shell at displacement (x, y, z): R0 = sum e_k, R1 = sum -2a_k e_k,
+// R2 = sum 4a_k^2 e_k, LF = sum -2a_k e_k ((2l+3) - 2a_k r^2), T3 = sum 4a_k^2 e_k ((2l+5) - 2a_k r^2).
+template <typename T>
+struct Radial {
+  T R0, R1, R2, LF, T3;
+};
+
+template <typename T, int LEVEL>
+__device__ __forceinline__ Radial<T> radial_sums(const DevSys& S, int s, int l, int np, T r2, int smask, R2FF r2ff) {
+  Radial<T> o{T(0), T(0), T(0), T(0), T(0)};
+  for (int k = 0; k < np; ++k) {
+    const T a = prim_alpha<T>(S, s, k);
+    T e, f3, f5;
+    if (sizeof(T) == 4 && ((smask >> k) & 1)) {
+      // a r^2 in float-float: (ah + al)(r2h + r2l)
+      const float ah = __ldg(S.alpha_f + s * kMaxPrim + k), al = __ldg(S.alpha_lo + s * kMaxPrim + k);
+      const float xh = ah * r2ff.h;
+      const float xl = fmaf(ah, r2ff.h, -xh) + (ah * r2ff.l + al * r2ff.h);
+      e = (T)(prim_coef<float>(S, s, k) * expf(-xh) * (1.0f - xl));
+      f3 = (T)((float(2 * l + 3) - 2.0f * xh) - 2.0f * xl);
+      f5 = (T)((float(2 * l + 5) - 2.0f * xh) - 2.0f * xl);
+    } else {
+      const T xa = a * r2;
+      e = prim_coef<T>(S, s, k) * dexp<T>(-xa);
+      f3 = T(2 * l + 3) - T(2) * xa;
+      f5 = T(2 * l + 5) - T(2) * xa;
+    }
+    o.R0 += e;
+    if (LEVEL >= 1) {
+      const T m2ae = T(-2) * a * e;
+      o.R1 += m2ae;
+      o.LF += m2ae * f3;
+      if (LEVEL >= 2) {
+        const T a4e = T(4) * a * a * e;
+        o.R2 += a4e;
+        o.T3 += a4e * f5;
+      }
+    }
+  }
+  return o;
+}
+
+// Displacement of the electron from nucleus c (double in FP64 mode; float from the
+// float-float positions in mixed mode), and for shells with sharp primitives (mixed mode)
+// the squared distance as a float-float pair; returns the shell's sharp mask (0 if none).
+template <typename T>
+__device__ __forceinline__ int shell_disp(const DevSys& S, int s, int c, const double p[3], const float ph[3],
+                                          const float pl[3], T d[3], R2FF& r2ff) {
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = p[k] - __ldg(S.R + 3 * c + k);
+    return 0;
+  } else {
+    const int smask = __ldg(S.sharp + s);
+    if (!smask) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) d[k] = (ph[k] - __ldg(S.Rh + 3 * c + k)) + (pl[k] - __ldg(S.Rl + 3 * c + k));
+      return 0;
+    }
+    float hsum = 0.f, lsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float dh, dl, sdiff, eh;
+      two_sum(ph[k], -__ldg(S.Rh + 3 * c + k), sdiff, eh);
+      fast_two_sum(sdiff, (pl[k] - __ldg(S.Rl + 3 * c + k)) + eh, dh, dl);
+      d[k] = dh;
+      const float pp = dh * dh, pe = fmaf(dh, dh, -pp);
+      float t;
+      two_sum(hsum, pp, hsum, t);
+      lsum += t + pe + 2.0f * dh * dl;
+    }
+    fast_two_sum(hsum, lsum, r2ff.h, r2ff.l);
+    return smask;
+  }
+}
+
+__device__ __forceinline__ void split_ff(double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (double)h);
+}
+
+// a r / (1 + F r) at r = |d| for the Metropolis ratio: in mixed mode with the approximate
+// reciprocal square root and division (a few ulp; the ratio feeds an acceptance test only).
+template <typename T>
+__device__ __forceinline__ T pade_at(T a, T F, const T d[3]) {
+  const T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  if constexpr (sizeof(T) == 4) {
+    const float r = r2 * rsqrtf(fmaxf(r2, 1e-30f));
+    return __fdividef(a * r, 1.0f + F * r);
+  } else {
+    const double r = sqrt(r2);
+    return a * r / (1.0 + F * r);
+  }
+}
+
+template <typename T, int NM>
+__device__ __forceinline__ void axpy_row(T (&acc)[NM], T a, const T* __restrict__ crow) {
+#pragma unroll
+  for (int i = 0; i < NM; ++i) acc[i] += a * crow[i];
+}
+
+template <typename T, int NM>
+__device__ __forceinline__ T dot_row(const T (&x)[NM], const T* __restrict__ crow) {
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < NM; ++i) s += x[i] * crow[i];
+  return s;
+}
+
+// Stage C^up and C^dn into shared memory as [2][M][NM], zero-padded beyond n_s.
+template <typename T, int NM>
+__device__ __forceinline__ void stage_C(const DevSys& S, T* Cs) {
+  for (int idx = threadIdx.x; idx < 2 * S.M * NM; idx += blockDim.x) {
+    const int sg = idx / (S.M * NM), r = idx - sg * S.M * NM, mu = r / NM, i = r - mu * NM;
+    const int n = sg == 0 ? S.nup : S.ndn;
+    Cs[idx] = (i < n) ? __ldg(coefC<T>(S, sg) + mu * n + i) : T(0);
+  }
+}
+
+
+// ---------------------------------------------------------------- moves, one lane per walker
+template <typename T, int NM>
+__global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* Cs = reinterpret_cast<T*>(smem);
+  stage_C<T, NM>(S, Cs);
+  __syncthreads();
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= P.W) return;
+  const int W = P.W, Ne = S.Ne, nup = S.nup, K = S.K;
+  T* B = reinterpret_cast<T*>(P.B);
+  const uint64_t wid = P.wid0 + (uint64_t)w;
+  uint32_t nacc = 0, nrej = 0;
+  for (int mv = 0; mv < P.nmoves; ++mv) {
+    const uint64_t gm = P.move0 + (uint64_t)mv;
+    const int e = (int)(gm % (uint64_t)Ne);
+    const uint64_t sweep = gm / (uint64_t)Ne;
+    const int sg = e < nup ? 0 : 1;
+    const int n = sg == 0 ? nup : S.ndn, el = e - (sg == 0 ? 0 : nup);
+    const int off = sg == 0 ? 0 : nup * nup;
+    const T* Csg = Cs + sg * S.M * NM;
+    uint64_t r[4] = {wid, sweep, (uint64_t)e, 0};
+    philox4x64_10(r, P.k0, P.k1);
+    double xi[3];
+    normals3(r, xi, T(0));
+    double po[3], rn[3];
+    float nh[3], nl[3], oh[3], ol[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      po[k] = P.pos[(size_t)(3 * e + k) * W + w];
+      rn[k] = po[k] + P.sigma * xi[k];
+      split_ff(rn[k], nh[k], nl[k]);
+      if constexpr (sizeof(T) == 4) {
+        const float2 f = P.posf[(size_t)(3 * e + k) * W + w];
+        oh[k] = f.x;
+        ol[k] = f.y;
+      }
+    }
+    // new orbital row
+    T row[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) row[i] = T(0);
+    for (int s = 0; s < S.nshell; ++s) {
+      const int4 sh = __ldg(S.shell + s);
+      T d[3];
+      if constexpr (sizeof(T) == 8) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = rn[k] - __ldg(S.R + 3 * sh.x + k);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = (nh[k] - __ldg(S.Rh + 3 * sh.x + k)) + (nl[k] - __ldg(S.Rl + 3 * sh.x + k));
+      }
+      const T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      const Radial<T> rs = radial_sums<T, 0>(S, s, sh.y, sh.z, r2, 0, R2FF{0.f, 0.f});
+      for (int m = 0; m < 2 * sh.y + 1; ++m) {
+        T Pa, g[3], h[6];
+        angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
+        axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * NM);
+      }
+    }
+    double R = 0.0;
+#pragma unroll
+    for (int i = 0; i < NM; ++i)
+      if (i < n) R += (double)row[i] * (double)B[(size_t)(off + i * n + el) * W + w];
+    // Jastrow ratio
+    double dJ = 0.0;
+    if (S.J2) {
+      T acc = 0;
+      for (int q = 0; q < Ne; ++q) {
+        if (q == e) continue;
+        const bool par = (q < nup) == (e < nup);
+        const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+        T d1[3], d0[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if constexpr (sizeof(T) == 8) {
+            const double pq = P.pos[(size_t)(3 * q + k) * W + w];
+            d1[k] = rn[k] - pq;
+            d0[k] = po[k] - pq;
+          } else {
+            const float2 f = P.posf[(size_t)(3 * q + k) * W + w];
+            d1[k] = (nh[k] - f.x) + (nl[k] - f.y);
+            d0[k] = (oh[k] - f.x) + (ol[k] - f.y);
+          }
+        }
+        acc += pade_at<T>(a, F, d1) - pade_at<T>(a, F, d0);
+      }
+      dJ += (double)acc;
+    }
+    if (S.J1) {
+      T acc = 0;
+      for (int I = 0; I < K; ++I) {
+        const T mz = (T)(-__ldg(S.Z + I)), b = (T)S.ben;
+        T d1[3], d0[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if constexpr (sizeof(T) == 8) {
+            d1[k] = rn[k] - __ldg(S.R + 3 * I + k);
+            d0[k] = po[k] - __ldg(S.R + 3 * I + k);
+          } else {
+            d1[k] = (nh[k] - __ldg(S.Rh + 3 * I + k)) + (nl[k] - __ldg(S.Rl + 3 * I + k));
+            d0[k] = (oh[k] - __ldg(S.Rh + 3 * I + k)) + (ol[k] - __ldg(S.Rl + 3 * I + k));
+          }
+        }
+        acc += pade_at<T>(mz, b, d1) - pade_at<T>(mz, b, d0);
+      }
+      dJ += (double)acc;
+    }
+    uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
+    philox4x64_10(r2, P.k0, P.k1);
+    const double u = u01(r2[0]);
+    const double pr = R * R * (double)dexp<T>((T)(2.0 * dJ));
+    const bool ok = isfinite(pr) && R != 0.0;
+    if (!ok) ++nrej;
+    if (ok && u < pr) {
+      // Sherman-Morrison: w_j = sum_i row_i B_ij - delta_j,el; B_kj <- B_kj - B_k,el w_j / R
+      T wv[NM], col[NM];
+#pragma unroll
+      for (int j = 0; j < NM; ++j) {
+        wv[j] = T(0);
+        col[j] = T(0);
+      }
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        if (i >= n) continue;
+        const T ri = row[i];
+#pragma unroll
+        for (int j = 0; j < NM; ++j)
+          if (j < n) wv[j] += ri * B[(size_t)(off + i * n + j) * W + w];
+      }
+#pragma unroll
+      for (int j = 0; j < NM; ++j) {
+        if (j < n) {
+          if (j == el) wv[j] -= T(1);
+          col[j] = B[(size_t)(off + j * n + el) * W + w];
+        }
+      }
+      const T rinv = (T)(1.0 / R);
+#pragma unroll
+      for (int k = 0; k < NM; ++k) {
+        if (k >= n) continue;
+        const T ck = col[k] * rinv;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) {
+          if (j >= n) continue;
+          T& b = B[(size_t)(off + k * n + j) * W + w];
+          b -= ck * wv[j];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        P.pos[(size_t)(3 * e + k) * W + w] = rn[k];
+        if constexpr (sizeof(T) == 4) P.posf[(size_t)(3 * e + k) * W + w] = make_float2(nh[k], nl[k]);
+      }
+      ++nacc;
+    }
+  }
+  P.nacc[w] += nacc;
+  P.nrej[w] += nrej;
+}
+
+// ---------------------------------------------------------------- measurement, one warp per walker
+
+
+template <int NV>
+__device__ __forceinline__ void warp_sum_f(float (&v)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+template <int NV>
+__device__ __forceinline__ void warp_sum_f(double (&v)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+}
+
+template <typename T, int NM>
+__global__ void __launch_bounds__(256) measure_small(DevSys S, SmallLayout L, SmallMeasParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  T* Cs = reinterpret_cast<T*>(smem + L.cta_C);
+  T* acc_s = reinterpret_cast<T*>(smem + L.cta_acc);
+  unsigned char* base = smem + L.cta_bytes + warp * L.bytes;
+  double* pd = reinterpret_cast<double*>(base + L.pd);
+  float* ph = reinterpret_cast<float*>(base + L.ph);
+  float* pl = reinterpret_cast<float*>(base + L.pl);
+  double* Ad = reinterpret_cast<double*>(base + L.Ad);
+  T* Bf = reinterpret_cast<T*>(base + L.Bf);
+  T* Pm = reinterpret_cast<T*>(base + L.Pm);
+  T* Q = reinterpret_cast<T*>(base + L.Q);
+  int* piv = reinterpret_cast<int*>(base + L.piv);
+  double* f = reinterpret_cast<double*>(base + L.f);
+  T* frc = reinterpret_cast<T*>(base + L.frc);
+  T* phi = reinterpret_cast<T*>(base + L.phi);
+  int* flag = reinterpret_cast<int*>(base + L.scal);
+  double* la = reinterpret_cast<double*>(base + L.scal + 8);
+  double* sgn = reinterpret_cast<double*>(base + L.scal + 16);
+
+  const int Ne = S.Ne, nup = S.nup, ndn = S.ndn, K = S.K, M = S.M, W = P.W;
+  const int nO = M * Ne;
+  const bool accum = P.mode == 2;
+  stage_C<T, NM>(S, Cs);
+  if (accum)
+    for (int i = threadIdx.x; i < P.accL; i += blockDim.x) acc_s[i] = T(0);
+  __syncthreads();
+
+  const long long w0 = (long long)W * blockIdx.x / gridDim.x, w1 = (long long)W * (blockIdx.x + 1) / gridDim.x;
+  const int e = lane;
+  const bool has_e = e < Ne;
+  const int sg = e < nup ? 0 : 1;
+  const int n = sg == 0 ? nup : ndn, el = e - (sg == 0 ? 0 : nup), off = sg == 0 ? 0 : nup * nup;
+  for (long long wl = w0 + warp; wl < w1; wl += nwarps) {
+    const int w = (int)wl;
+    // ---- positions
+    double p[3] = {0.0, 0.0, 0.0};
+    float hh[3] = {0.f, 0.f, 0.f}, ll[3] = {0.f, 0.f, 0.f};
+    if (has_e) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        p[k] = P.pos[(long long)(3 * e + k) * P.pos_sk + (long long)w * P.pos_sw];
+        split_ff(p[k], hh[k], ll[k]);
+        pd[3 * e + k] = p[k];
+        ph[3 * e + k] = hh[k];
+        pl[3 * e + k] = ll[k];
+        if (P.posf_out) P.posf_out[(size_t)(3 * e + k) * W + w] = make_float2(hh[k], ll[k]);
+      }
+    }
+    if (lane == 0) {
+      *flag = 0;
+      *la = 0.0;
+      *sgn = 1.0;
+    }
+    // ---- pass 1: Slater rows (one per lane) -> FP64 -> Gauss-Jordan per spin
+    if (has_e) {
+      T row[NM];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) row[i] = T(0);
+      const T* Csg = Cs + sg * M * NM;
+      for (int s = 0; s < S.nshell; ++s) {
+        const int4 sh = __ldg(S.shell + s);
+        T d[3];
+        R2FF r2ff{0.f, 0.f};
+        const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
+        const Radial<T> rs = radial_sums<T, 0>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
+        for (int m = 0; m < 2 * sh.y + 1; ++m) {
+          T Pa, g[3], h[6];
+          angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
+          axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * NM);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+        if (i < n) Ad[off + el * n + i] = (double)row[i];
+    }
+    __syncwarp();
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int ns = s2 == 0 ? nup : ndn;
+      if (ns > 0) gj_inverse<32>(Ad + (s2 == 0 ? 0 : nup * nup), ns, piv, f, flag, la, sgn, P.logpsi != nullptr);
+    }
+    if (static_cast<void*>(Bf) != static_cast<void*>(Ad))
+      for (int i = lane; i < S.nB; i += 32) Bf[i] = (T)Ad[i];
+    __syncwarp();
+    if (P.Bout && P.mode != 1) {
+      T* Bg = reinterpret_cast<T*>(P.Bout);
+      for (int i = lane; i < S.nB; i += 32) Bg[(size_t)i * W + w] = Bf[i];
+    }
+    if (lane == 0 && *flag) atomicAdd(&P.counters[0], 1ull);
+    if (P.mode == 0) {
+      __syncwarp();
+      continue;
+    }
+
+    // ---- Jastrow and potentials (lane = electron)
+    T jg[3] = {T(0), T(0), T(0)}, jl = T(0);
+    double vpart[4] = {0.0, 0.0, 0.0, 0.0};  // kinetic, V_ee, V_en, J
+    if (has_e) {
+      T vee = 0, ven = 0, jv = 0;
+      for (int j = 0; j < Ne; ++j) {
+        if (j == e) continue;
+        T d[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if constexpr (sizeof(T) == 8) d[k] = p[k] - pd[3 * j + k];
+          else d[k] = (hh[k] - ph[3 * j + k]) + (ll[k] - pl[3 * j + k]);
+        }
+        const T r = dsqrt<T>(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), ri = T(1) / r;
+        if (j > e) vee += ri;
+        if (S.J2) {
+          const bool par = (j < nup) == (e < nup);
+          const Rad3<T> u = pade<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), r);
+          const T gr = u.h1 * ri;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) jg[k] += gr * d[k];
+          jl += u.h2 + T(2) * gr;
+          if (j > e) jv += u.h;
+        }
+      }
+      for (int I = 0; I < K; ++I) {
+        T d[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if constexpr (sizeof(T) == 8) d[k] = p[k] - __ldg(S.R + 3 * I + k);
+          else d[k] = (hh[k] - __ldg(S.Rh + 3 * I + k)) + (ll[k] - __ldg(S.Rl + 3 * I + k));
+        }
+        const T r = dsqrt<T>(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), ri = T(1) / r;
+        const T Z = (T)__ldg(S.Z + I);
+        ven -= Z * ri;
+        if (S.J1) {
+          const Rad3<T> c = pade<T>(-Z, (T)S.ben, r);
+          const T gr = c.h1 * ri;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) jg[k] += gr * d[k];
+          jl += c.h2 + T(2) * gr;
+          jv += c.h;
+        }
+      }
+      vpart[1] = (double)vee;
+      vpart[2] = (double)ven;
+      vpart[3] = (double)jv;
+    }
+
+    // ---- pass 2: gradient and Laplacian rows; drift g_e, l_e; P row; kinetic term
+    T bc[NM];  // column el of B^s: B_{i, el}
+#pragma unroll
+    for (int i = 0; i < NM; ++i) bc[i] = (has_e && i < n) ? Bf[off + i * n + el] : T(0);
+    T gd[3] = {T(0), T(0), T(0)};
+    if (has_e) {
+      T G0[NM], G1[NM], G2[NM], Lr[NM];
+#pragma unroll
+      for (int i = 0; i < NM; ++i) G0[i] = G1[i] = G2[i] = Lr[i] = T(0);
+      const T* Csg = Cs + sg * M * NM;
+      for (int s = 0; s < S.nshell; ++s) {
+        const int4 sh = __ldg(S.shell + s);
+        T d[3];
+        R2FF r2ff{0.f, 0.f};
+        const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
+        const Radial<T> rs = radial_sums<T, 1>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
+        for (int m = 0; m < 2 * sh.y + 1; ++m) {
+          T Pa, g[3], h[6];
+          angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
+          const T* cr = Csg + (sh.w + m) * NM;
+          axpy_row<T, NM>(G0, g[0] * rs.R0 + Pa * d[0] * rs.R1, cr);
+          axpy_row<T, NM>(G1, g[1] * rs.R0 + Pa * d[1] * rs.R1, cr);
+          axpy_row<T, NM>(G2, g[2] * rs.R0 + Pa * d[2] * rs.R1, cr);
+          axpy_row<T, NM>(Lr, Pa * rs.LF, cr);
+        }
+      }
+      T lsum = 0;
+#pragma unroll
+      for (int i = 0; i < NM; ++i) {
+        gd[0] += G0[i] * bc[i];
+        gd[1] += G1[i] * bc[i];
+        gd[2] += G2[i] * bc[i];
+        lsum += Lr[i] * bc[i];
+      }
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+        if (i < n) Pm[off + el * n + i] = Lr[i] + T(2) * (jg[0] * G0[i] + jg[1] * G1[i] + jg[2] * G2[i]);
+      const T te = lsum + jl + (jg[0] * jg[0] + jg[1] * jg[1] + jg[2] * jg[2]) +
+                   T(2) * (jg[0] * gd[0] + jg[1] * gd[1] + jg[2] * gd[2]);
+      vpart[0] = -0.5 * (double)te;
+    }
+    warp_sum_f<4>(vpart);
+    const double EL = vpart[0] + vpart[1] + vpart[2] + S.Vnn;
+    const double cw = EL - P.e_ref;
+    __syncwarp();
+
+    // ---- adjoint weights per spin: Q = B P, X = Q B (X[e][i] = (B P B)_{i e}, over P)
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const int ns = s2 == 0 ? nup : ndn, o2 = s2 == 0 ? 0 : nup * nup;
+      if (ns == 0) continue;
+      const T* Bs = Bf + o2;
+      T* Ps = Pm + o2;
+      for (int idx = lane; idx < ns * ns; idx += 32) {
+        const int i = idx / ns, j = idx - i * ns;
+        T v = 0;
+        for (int k = 0; k < ns; ++k) v += Bs[i * ns + k] * Ps[k * ns + j];
+        Q[idx] = v;
+      }
+      __syncwarp();
+      for (int idx = lane; idx < ns * ns; idx += 32) {
+        const int ee = idx / ns, i = idx - ee * ns;
+        T v = 0;
+        for (int j = 0; j < ns; ++j) v += Q[i * ns + j] * Bs[j * ns + ee];
+        Ps[idx] = v;
+      }
+      __syncwarp();
+    }
+    for (int i = lane; i < 6 * K; i += 32) frc[i] = T(0);
+    __syncwarp();
+
+    // ---- pass 3: nuclear derivatives (lane = electron) and O in AO chunks
+    T xr[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) xr[i] = (has_e && i < n) ? Pm[off + el * n + i] : T(0);
+    T fl[3] = {T(0), T(0), T(0)}, fe[3] = {T(0), T(0), T(0)};
+    int cur = -1;
+    int chunk0 = 0, chunk_n = 0;  // AOs [chunk0, chunk0 + chunk_n) pending in phi
+    const T* Csg = Cs + sg * M * NM;
+    auto flush_centre = [&](int I) {
+      float v6f[6];
+      double v6d[6];
+      if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          v6f[k] = fl[k];
+          v6f[3 + k] = fe[k];
+        }
+        warp_sum_f<6>(v6f);
+        if (lane == 0)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            frc[3 * I + k] += v6f[k];
+            frc[3 * K + 3 * I + k] += v6f[3 + k];
+          }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          v6d[k] = fl[k];
+          v6d[3 + k] = fe[k];
+        }
+        warp_sum_f<6>(v6d);
+        if (lane == 0)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            frc[3 * I + k] += v6d[k];
+            frc[3 * K + 3 * I + k] += v6d[3 + k];
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fl[k] = fe[k] = T(0);
+    };
+    // O^s[mu][i] = sum over electrons e of spin s of psi_mu(r_e) B_{i, el(e)}; lanes 0..15 take
+    // spin up, 16..31 spin down, one orbital i each.
+    auto flush_chunk = [&]() {
+      __syncwarp();
+      const int g = lane >> 4, i = lane & 15;
+      const int ng = g == 0 ? nup : ndn, og = g == 0 ? 0 : nup * nup, e0 = g == 0 ? 0 : nup;
+      const int ooff = g == 0 ? 0 : M * nup;
+      if (i < ng) {
+        T brow[NM];
+#pragma unroll
+        for (int k = 0; k < NM; ++k) brow[k] = (k < ng) ? Bf[og + i * ng + k] : T(0);
+        for (int c = 0; c < chunk_n; ++c) {
+          T s = 0;
+#pragma unroll
+          for (int k = 0; k < NM; ++k)
+            if (k < ng) s += phi[(e0 + k) * L.chunk + c] * brow[k];
+          const int mu = chunk0 + c;
+          if (P.O) P.O[(size_t)w * nO + ooff + mu * ng + i] = (double)s;
+          if (accum) {
+            atomicAdd(&acc_s[3 + 9 * K + ooff + mu * ng + i], s);
+            atomicAdd(&acc_s[3 + 9 * K + nO + ooff + mu * ng + i], (T)cw * s);
+          }
+        }
+      }
+      __syncwarp();
+      chunk0 += chunk_n;
+      chunk_n = 0;
+    };
+    for (int s = 0; s < S.nshell; ++s) {
+      const int4 sh = __ldg(S.shell + s);
+      const int ncomp = 2 * sh.y + 1;
+      if (chunk_n + ncomp > L.chunk) flush_chunk();
+      if (sh.x != cur) {
+        if (cur >= 0) flush_centre(cur);
+        cur = sh.x;
+      }
+      if (has_e) {
+        T d[3];
+        R2FF r2ff{0.f, 0.f};
+        const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
+        const Radial<T> rs = radial_sums<T, 2>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
+        for (int m = 0; m < ncomp; ++m) {
+          T Pa, g[3], h[6];
+          angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
+          const T* cr = Csg + (sh.w + m) * NM;
+          const T yA = dot_row<T, NM>(xr, cr), yL = dot_row<T, NM>(bc, cr);
+          T gv[3], gl[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            gv[k] = g[k] * rs.R0 + Pa * d[k] * rs.R1;
+            gl[k] = g[k] * rs.LF + Pa * d[k] * rs.T3;
+          }
+          // Hessian (xx, yy, zz, xy, xz, yz) contracted with grad J
+          T H[3][3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+              const int hk = (a == b) ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5));
+              H[a][b] = h[hk] * rs.R0 + (g[a] * d[b] + g[b] * d[a]) * rs.R1 +
+                        Pa * (d[a] * d[b] * rs.R2 + (a == b ? rs.R1 : T(0)));
+            }
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const T hj = H[k][0] * jg[0] + H[k][1] * jg[1] + H[k][2] * jg[2];
+            fl[k] -= gv[k] * yL;
+            fe[k] += T(-0.5) * (gv[k] * yA - yL * (gl[k] + T(2) * hj));
+          }
+          phi[e * L.chunk + chunk_n + m] = Pa * rs.R0;
+        }
+      }
+      chunk_n += ncomp;
+    }
+    if (cur >= 0) flush_centre(cur);
+    flush_chunk();
+    // e-n Jastrow and V_en derivatives, one nucleus at a time
+    for (int I = 0; I < K; ++I) {
+      T c6[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+      if (has_e) {
+        T sd[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if constexpr (sizeof(T) == 8) sd[k] = p[k] - __ldg(S.R + 3 * I + k);
+          else sd[k] = (hh[k] - __ldg(S.Rh + 3 * I + k)) + (ll[k] - __ldg(S.Rl + 3 * I + k));
+        }
+        const T r = dsqrt<T>(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]), ri = T(1) / r;
+        const T Z = (T)__ldg(S.Z + I);
+        const T nn[3] = {sd[0] * ri, sd[1] * ri, sd[2] * ri};
+        const T ven = -Z * ri * ri * ri;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c6[3 + k] = ven * sd[k];
+        if (S.J1) {
+          const Rad3<T> c = pade<T>(-Z, (T)S.ben, r);
+          const T gs[3] = {gd[0] + jg[0], gd[1] + jg[1], gd[2] + jg[2]};
+          const T dl = c.h3 + T(2) * c.h2 * ri - T(2) * c.h1 * ri * ri;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            T hs = 0;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc)
+              hs += (c.h2 * nn[k] * nn[cc] + c.h1 * ri * ((k == cc ? T(1) : T(0)) - nn[k] * nn[cc])) * gs[cc];
+            c6[k] = -c.h1 * nn[k];
+            c6[3 + k] += hs + T(0.5) * dl * nn[k];
+          }
+        }
+      }
+      if constexpr (sizeof(T) == 4) {
+        float v6[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v6[k] = c6[k];
+        warp_sum_f<6>(v6);
+        if (lane == 0)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            frc[3 * I + k] += v6[k];
+            frc[3 * K + 3 * I + k] += v6[3 + k];
+          }
+      } else {
+        double v6[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v6[k] = c6[k];
+        warp_sum_f<6>(v6);
+        if (lane == 0)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            frc[3 * I + k] += v6[k];
+            frc[3 * K + 3 * I + k] += v6[3 + k];
+          }
+      }
+    }
+    __syncwarp();
+    // ---- outputs and walker sums
+    for (int i = lane; i < 3 * K; i += 32) {
+      const double dl = (double)frc[i];
+      const double de = (double)frc[3 * K + i] + __ldg(S.dVnn + i);
+      if (P.dlnpsi) P.dlnpsi[(size_t)w * 3 * K + i] = dl;
+      if (P.dEL) P.dEL[(size_t)w * 3 * K + i] = de;
+      if (accum) {
+        atomicAdd(&acc_s[3 + i], (T)de);
+        atomicAdd(&acc_s[3 + 3 * K + i], (T)dl);
+        atomicAdd(&acc_s[3 + 6 * K + i], (T)(cw * dl));
+      }
+    }
+    if (lane == 0) {
+      if (P.EL) P.EL[w] = EL;
+      if (P.logpsi) P.logpsi[w] = *la + vpart[3];
+      if (accum) {
+        atomicAdd(&acc_s[0], T(1));
+        atomicAdd(&acc_s[1], (T)cw);
+        atomicAdd(&acc_s[2], (T)(cw * cw));
+      }
+    }
+    __syncwarp();
+  }
+  if (accum) {
+    __syncthreads();
+    double* slot = P.acc + (size_t)blockIdx.x * P.accL;
+    const double cnt = (double)acc_s[0];
+    for (int i = threadIdx.x; i < P.accL; i += blockDim.x) {
+      double v = (double)acc_s[i];
+      if (i == 2) v = v + 2.0 * P.e_ref * (double)acc_s[1] + cnt * P.e_ref * P.e_ref;
+      if (i == 1) v = v + cnt * P.e_ref;
+      slot[i] += v;
+    }
+  }
+}
+
+// Layout conversion between the ABI's [W][Ne][3] and the walker-interleaved [3 Ne][W].
+static __global__ void to_interleaved(const double* __restrict__ src, double* __restrict__ dst, float2* __restrict__ dstf,
+                               int W, int n3) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)W * n3;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(idx / W), w = (int)(idx - (long long)k * W);
+    const double v = src[(size_t)w * n3 + k];
+    dst[idx] = v;
+    if (dstf) {
+      float h, l;
+      split_ff(v, h, l);
+      dstf[idx] = make_float2(h, l);
+    }
+  }
+}
+static __global__ void from_interleaved(const double* __restrict__ src, double* __restrict__ dst, int W, int n3) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)W * n3;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(idx / n3), k = (int)(idx - (long long)w * n3);
+    dst[idx] = src[(size_t)k * W + w];
+  }
+}
+
+template <typename T>
+cudaError_t launch_move_small_impl(const DevSys& S, int nm, int W, size_t smem, const SmallMoveParams& P,
+                                   cudaStream_t st) {
+  const int threads = 32;
+  const dim3 grid((W + threads - 1) / threads);
+  if (nm <= 8)
+    move_small<T, 8><<<grid, threads, smem, st>>>(S, P);
+  else
+    move_small<T, 16><<<grid, threads, smem, st>>>(S, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_measure_small_impl(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
+                                      const SmallMeasParams& P, cudaStream_t st) {
+  const size_t smem = (size_t)L.cta_bytes + (size_t)warps * L.bytes;
+  if (nm <= 8)
+    measure_small<T, 8><<<grid, 32 * warps, smem, st>>>(S, L, P);
+  else
+    measure_small<T, 16><<<grid, 32 * warps, smem, st>>>(S, L, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t set_smem_limits_small_impl() {
+  const int lim = 227 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(move_small<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(move_small<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_small<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_small<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  return cudaSuccess;
+}
+
+}  // namespace vmcf

@@ -93,7 +93,7 @@ GroupLayout layout_refresh_move(const vmcf_system_s& s, size_t tsz, int GS) {
   L.wv = take((int)tsz * s.nmax);
   L.col = take((int)tsz * s.nmax);
   L.piv = take(4 * s.nmax);
-  L.f = take(8 * s.nmax);
+  L.f = take(8 * (s.nmax + 1));
   L.red = take(8 * 4 * std::max(1, GS / 32));
   L.scal = take(32);
   L.bytes = align16(o);
@@ -121,7 +121,7 @@ GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool with
   L.Ow = take((int)tsz * s.M * s.nmax);
   L.D = withD ? take((int)tsz * s.M * s.nmax) : L.Ow;
   L.piv = take(4 * s.nmax);
-  L.f = take(8 * s.nmax);
+  L.f = take(8 * (s.nmax + 1));
   L.red = take(8 * 4 * std::max(1, GS / 32));
   L.scal = take(32);
   L.bytes = align16(o);
@@ -153,6 +153,45 @@ int plan(vmcf_system_s& s) {
     s.acc_off = -1;
   }
   return VMCF_OK;
+}
+
+// Small-system path: one lane per electron in the measurement, one lane per walker in the
+// moves. Eligible when the electrons fit one warp, the orbitals per spin fit a 16-wide
+// register row, and the shared-memory plan fits.
+void plan_small(vmcf_system_s& s) {
+  s.small = false;
+  if (s.Ne > 32 || s.nmax > 16) return;
+  const int tsz = s.precision == VMCF_FP64 ? 8 : 4;
+  s.small_nm = s.nmax <= 8 ? 8 : 16;
+  SmallLayout L{};
+  L.chunk = 20;
+  int o = 0;
+  auto take = [&](int bytes) { int at = o; o = align16(o + bytes); return at; };
+  L.pd = take(8 * 3 * s.Ne);
+  L.ph = take(4 * 3 * s.Ne);
+  L.pl = take(4 * 3 * s.Ne);
+  L.Ad = take(8 * s.nB);
+  L.Bf = (tsz == 8) ? L.Ad : take(tsz * s.nB);
+  L.Pm = take(tsz * s.nB);
+  L.Q = take(tsz * s.nmax * s.nmax);
+  L.piv = take(4 * s.nmax);
+  L.f = take(8 * (s.nmax + 1));
+  L.frc = take(tsz * 6 * s.K);
+  L.phi = take(tsz * s.Ne * L.chunk);
+  L.red = take(16);
+  L.scal = take(32);
+  L.bytes = align16(o);
+  L.cta_C = 0;
+  L.cta_acc = align16(tsz * 2 * s.M * s.small_nm);
+  L.cta_bytes = L.cta_acc + align16(tsz * s.accL);
+  int warps = 8;
+  while (warps > 2 && L.cta_bytes + warps * L.bytes > kSmemCap) warps /= 2;
+  if (L.cta_bytes + warps * L.bytes > kSmemCap) return;
+  s.SL = L;
+  s.small_warps = warps;
+  s.small_move_smem = (size_t)tsz * 2 * s.M * s.small_nm;
+  if (s.small_move_smem > (size_t)kSmemCap) return;
+  s.small = true;
 }
 
 Launch launch_rm(const vmcf_system_s& s, int W) {
@@ -207,7 +246,40 @@ bool finite_all(const double* p, size_t n) {
   return true;
 }
 
+// Small path: measurement kernel settings for `W` walkers (grid for evaluate/refresh).
+SmallMeasParams small_params(const vmcf_system_s& s, int W) {
+  SmallMeasParams P{};
+  P.W = W;
+  P.accL = s.accL;
+  return P;
+}
+
+int launch_small_measure(vmcf_system_s* s, int grid, const SmallMeasParams& P, cudaStream_t st) {
+  cudaError_t e = s->precision == VMCF_FP64
+                      ? launch_measure_small<double>(s->dev, s->small_nm, s->SL, grid, s->small_warps, P, st)
+                      : launch_measure_small<float>(s->dev, s->small_nm, s->SL, grid, s->small_warps, P, st);
+  if (e != cudaSuccess) return cuda_fail(e, "small measurement kernel launch");
+  return VMCF_OK;
+}
+
+int eval_grid(const vmcf_system_s& s, int W) { return std::max(1, (W + 2 * s.small_warps - 1) / (2 * s.small_warps)); }
+
+// Fresh inverses from the current positions.
 int do_refresh(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
+  if (s->small) {
+    Timed tm(wk, 2, st);
+    SmallMeasParams P = small_params(*s, wk->W);
+    P.pos = wk->pos;
+    P.pos_sk = wk->W;
+    P.pos_sw = 1;
+    P.mode = 0;
+    P.Bout = wk->B;
+    P.counters = wk->counters;
+    int rc = launch_small_measure(s, eval_grid(*s, wk->W), P, st);
+    if (rc != VMCF_OK) return rc;
+    wk->counter = 0;
+    return VMCF_OK;
+  }
   const Launch lc = launch_rm(*s, wk->W);
   Timed tm(wk, 2, st);
   cudaError_t e = s->precision == VMCF_FP64
@@ -215,6 +287,19 @@ int do_refresh(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
                       : launch_refresh<float>(s->dev, lc, wk->pos, wk->B, wk->W, wk->counters, st);
   if (e != cudaSuccess) return cuda_fail(e, "refresh kernel launch");
   wk->counter = 0;
+  return VMCF_OK;
+}
+
+// Bring positions in the ABI layout [W][Ne][3] (device or host) into the walker state.
+int load_positions_state(vmcf_system_s* s, vmcf_walkers_s* wk, const double* pos, int is_host, cudaStream_t st) {
+  const size_t bytes = 8 * (size_t)wk->W * 3 * s->Ne;
+  const cudaMemcpyKind kind = is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (!s->small) {
+    VMCF_CUDA(cudaMemcpyAsync(wk->pos, pos, bytes, kind, st));
+    return VMCF_OK;
+  }
+  VMCF_CUDA(cudaMemcpyAsync(wk->stage, pos, bytes, kind, st));
+  VMCF_CUDA(launch_to_interleaved(wk->stage, wk->pos, wk->posf, wk->W, 3 * s->Ne, st));
   return VMCF_OK;
 }
 
@@ -243,6 +328,8 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   if (!out) return fail(VMCF_EINVAL, "out is NULL");
   *out = nullptr;
   if (!nuc || !bas || !jas || !C_up) return fail(VMCF_EINVAL, "NULL input");
+  const bool force_group = (precision & VMCF_FORCE_GROUP_PATH) != 0;
+  precision &= ~VMCF_FORCE_GROUP_PATH;
   if (precision != VMCF_FP64 && precision != VMCF_MIXED) return fail(VMCF_EINVAL, "bad precision");
   if (nuc->K < 1 || !nuc->Z || !nuc->R) return fail(VMCF_EINVAL, "need at least one nucleus");
   if (!finite_all(nuc->R, 3 * (size_t)nuc->K)) return fail(VMCF_EINVAL, "nuclear positions not finite");
@@ -340,9 +427,12 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
     delete s;
     return rc;
   }
+  if (!force_group) plan_small(*s);
 
   // one device allocation for all tables
   std::vector<float> alpha_f(alpha.begin(), alpha.end()), coef_f(coef.begin(), coef.end());
+  std::vector<float> alpha_lo(alpha.size());
+  for (size_t i = 0; i < alpha.size(); ++i) alpha_lo[i] = (float)(alpha[i] - (double)alpha_f[i]);
   std::vector<float> Rh(3 * s->K), Rl(3 * s->K);
   for (int i = 0; i < 3 * s->K; ++i) {
     Rh[i] = (float)s->R[i];
@@ -356,7 +446,8 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
                oCf = slot(4 * coef.size()), oAoc = slot(4 * (size_t)M), oC0 = slot(8 * s->C[0].size()),
                oC1 = slot(8 * std::max<size_t>(1, s->C[1].size())), oCf0 = slot(4 * Cf0.size()),
                oCf1 = slot(4 * std::max<size_t>(1, Cf1.size())), oDv = slot(8 * dVnn.size()), oCnt = slot(16),
-               oRh = slot(4 * Rh.size()), oRl = slot(4 * Rl.size()), oSharp = slot(4 * sharp.size());
+               oRh = slot(4 * Rh.size()), oRl = slot(4 * Rl.size()), oSharp = slot(4 * sharp.size()),
+               oAlo = slot(4 * alpha_lo.size());
   cudaError_t e = cudaMalloc(&s->dmem, off);
   if (e != cudaSuccess) {
     delete s;
@@ -384,7 +475,19 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   ce = ce ? ce : up(oRh, Rh.data(), 4 * Rh.size());
   ce = ce ? ce : up(oRl, Rl.data(), 4 * Rl.size());
   ce = ce ? ce : up(oSharp, sharp.data(), 4 * sharp.size());
+  ce = ce ? ce : up(oAlo, alpha_lo.data(), 4 * alpha_lo.size());
   if (ce == cudaSuccess) ce = s->precision == VMCF_FP64 ? set_smem_limits<double>(s->GS) : set_smem_limits<float>(s->GS);
+  if (ce == cudaSuccess && s->small)
+    ce = s->precision == VMCF_FP64 ? set_smem_limits_small<double>() : set_smem_limits_small<float>();
+  if (ce == cudaSuccess && s->small) {
+    int dev = 0, sms = 0;
+    ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t cta = (size_t)s->SL.cta_bytes + (size_t)s->small_warps * s->SL.bytes;
+    const int by_smem = (int)((228 * 1024) / (cta + 1024));
+    const int by_regs = 65536 / (32 * s->small_warps * 128);
+    s->small_res = std::max(1, sms * std::max(1, std::min(by_smem, by_regs)));
+  }
   if (ce != cudaSuccess) {
     cudaFree(s->dmem);
     delete s;
@@ -403,6 +506,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   D.Rh = reinterpret_cast<const float*>(b + oRh);
   D.Rl = reinterpret_cast<const float*>(b + oRl);
   D.sharp = reinterpret_cast<const int*>(b + oSharp);
+  D.alpha_lo = reinterpret_cast<const float*>(b + oAlo);
   D.C[0] = reinterpret_cast<const double*>(b + oC0);
   D.C[1] = reinterpret_cast<const double*>(b + oC1);
   D.Cf[0] = reinterpret_cast<const float*>(b + oCf0);
@@ -454,23 +558,41 @@ int vmcf_walkers_create(vmcf_system_t s, int W, const double* pos, int is_host, 
   wk->grid_meas = nblocks * wk->cpb;
   const size_t tsz = s->precision == VMCF_FP64 ? 8 : 4;
   const size_t npos = (size_t)W * 3 * s->Ne;
+  if (s->small) {
+    // G = nblocks x cpb CTAs; pick cpb for the fewest walkers per warp times waves
+    double best = 1e300;
+    for (int cpb = 1; cpb <= 1024; ++cpb) {
+      const long long G = (long long)nblocks * cpb;
+      if (G > W) break;
+      const long long per_cta = (W + G - 1) / G, per_warp = (per_cta + s->small_warps - 1) / s->small_warps;
+      const long long waves = (G + s->small_res - 1) / s->small_res;
+      const double est = (double)waves * per_warp + 1e-3 * cpb;
+      if (est < best) {
+        best = est;
+        wk->cpb = cpb;
+      }
+    }
+    wk->grid_meas = nblocks * wk->cpb;
+  }
   cudaError_t e;
   if ((e = cudaMalloc(&wk->pos, 8 * npos)) || (e = cudaMalloc(&wk->B, tsz * (size_t)W * s->nB)) ||
       (e = cudaMalloc(&wk->nacc, 4 * (size_t)W)) || (e = cudaMalloc(&wk->nrej, 4 * (size_t)W)) ||
       (e = cudaMalloc(&wk->counters, 16)) ||
       (e = cudaMalloc(&wk->acc, 8 * (size_t)wk->grid_meas * s->accL)) ||
-      (e = cudaMalloc(&wk->blocks, 8 * (size_t)nblocks * s->accL))) {
+      (e = cudaMalloc(&wk->blocks, 8 * (size_t)nblocks * s->accL)) ||
+      (s->small && (e = cudaMalloc(&wk->stage, 8 * npos))) ||
+      (s->small && s->precision == VMCF_MIXED && (e = cudaMalloc(&wk->posf, sizeof(float2) * npos)))) {
     vmcf_walkers_destroy(wk);
     return fail(VMCF_ENOMEM, std::string("walker state allocation: ") + cudaGetErrorString(e));
   }
-  if ((e = cudaMemcpyAsync(wk->pos, pos, 8 * npos, is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st)) ||
-      (e = cudaMemsetAsync(wk->nacc, 0, 4 * (size_t)W, st)) || (e = cudaMemsetAsync(wk->nrej, 0, 4 * (size_t)W, st)) ||
+  if ((e = cudaMemsetAsync(wk->nacc, 0, 4 * (size_t)W, st)) || (e = cudaMemsetAsync(wk->nrej, 0, 4 * (size_t)W, st)) ||
       (e = cudaMemsetAsync(wk->counters, 0, 16, st)) ||
       (e = cudaMemsetAsync(wk->acc, 0, 8 * (size_t)wk->grid_meas * s->accL, st))) {
     vmcf_walkers_destroy(wk);
     return cuda_fail(e, "walker state initialisation");
   }
-  int rc = do_refresh(s, wk, st);
+  int rc = load_positions_state(s, wk, pos, is_host, st);
+  if (rc == VMCF_OK) rc = do_refresh(s, wk, st);
   if (rc == VMCF_OK) {
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "initial refresh");
@@ -496,6 +618,8 @@ int vmcf_walkers_destroy(vmcf_walkers_t wk) {
   cudaFree(wk->counters);
   cudaFree(wk->acc);
   cudaFree(wk->blocks);
+  cudaFree(wk->stage);
+  cudaFree(wk->posf);
   delete wk;
   return VMCF_OK;
 }
@@ -503,16 +627,22 @@ int vmcf_walkers_destroy(vmcf_walkers_t wk) {
 int vmcf_walkers_set_positions(vmcf_system_t s, vmcf_walkers_t wk, const double* pos, int is_host, void* stream) {
   if (!s || !wk || !pos || wk->sys != s) return fail(VMCF_EINVAL, "bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  VMCF_CUDA(cudaMemcpyAsync(wk->pos, pos, 8 * (size_t)wk->W * 3 * s->Ne,
-                            is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+  int rc = load_positions_state(s, wk, pos, is_host, st);
+  if (rc != VMCF_OK) return rc;
   return do_refresh(s, wk, st);
 }
 
 int vmcf_walkers_get_positions(vmcf_walkers_t wk, double* pos, int is_host, void* stream) {
   if (!wk || !pos) return fail(VMCF_EINVAL, "bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  VMCF_CUDA(cudaMemcpyAsync(pos, wk->pos, 8 * (size_t)wk->W * 3 * wk->sys->Ne,
-                            is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+  const vmcf_system_s* s = wk->sys;
+  const size_t bytes = 8 * (size_t)wk->W * 3 * s->Ne;
+  const double* src = wk->pos;
+  if (s->small) {
+    VMCF_CUDA(launch_from_interleaved(wk->pos, wk->stage, wk->W, 3 * s->Ne, st));
+    src = wk->stage;
+  }
+  VMCF_CUDA(cudaMemcpyAsync(pos, src, bytes, is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
   if (is_host) VMCF_CUDA(cudaStreamSynchronize(st));
   return VMCF_OK;
 }
@@ -532,6 +662,62 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
   if (n_sweeps < 0 || !(step_sigma > 0.0) || !std::isfinite(step_sigma) || refresh_k < 1)
     return fail(VMCF_EINVAL, "need n_sweeps >= 0, step_sigma > 0, refresh_k >= 1");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (s->small) {
+    const bool fp64 = s->precision == VMCF_FP64;
+    SmallMoveParams P{};
+    P.pos = wk->pos;
+    P.posf = wk->posf;
+    P.B = wk->B;
+    P.nacc = wk->nacc;
+    P.nrej = wk->nrej;
+    P.W = wk->W;
+    P.wid0 = wk->wid0;
+    P.k0 = wk->k0;
+    P.k1 = wk->k1;
+    P.sigma = step_sigma;
+    SmallMeasParams M = small_params(*s, wk->W);
+    M.pos = wk->pos;
+    M.pos_sk = wk->W;
+    M.pos_sw = 1;
+    M.mode = 2;
+    M.Bout = wk->B;
+    M.acc = wk->acc;
+    M.e_ref = wk->e_ref;
+    M.counters = wk->counters;
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+      int done = 0;
+      while (done < s->Ne) {
+        const int chunk = std::min(s->Ne - done, refresh_k - wk->counter);
+        P.move0 = wk->sweep * (uint64_t)s->Ne + (uint64_t)done;
+        P.nmoves = chunk;
+        {
+          Timed tm(wk, 0, st);
+          cudaError_t e = fp64 ? launch_move_small<double>(s->dev, s->small_nm, wk->W, s->small_move_smem, P, st)
+                               : launch_move_small<float>(s->dev, s->small_nm, wk->W, s->small_move_smem, P, st);
+          if (e != cudaSuccess) return cuda_fail(e, "small move kernel launch");
+        }
+        done += chunk;
+        wk->counter += chunk;
+        if (wk->counter == refresh_k) {
+          const bool end_of_sweep = done == s->Ne;
+          if (!(measure && end_of_sweep)) {
+            int rc = do_refresh(s, wk, st);
+            if (rc != VMCF_OK) return rc;
+          }
+          wk->counter = 0;
+        }
+      }
+      wk->sweep += 1;
+      if (measure) {
+        Timed tm(wk, 1, st);
+        int rc = launch_small_measure(s, wk->grid_meas, M, st);
+        if (rc != VMCF_OK) return rc;
+        wk->counter = 0;
+        wk->measured += 1;
+      }
+    }
+    return VMCF_OK;
+  }
   MoveParams P{};
   P.pos = wk->pos;
   P.B = wk->B;
@@ -590,6 +776,20 @@ int vmcf_evaluate(vmcf_system_t s, const double* pos, int W, double* EL, double*
   if (W == 0) return VMCF_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool withD = dEL_dC != nullptr;
+  if (s->small && !withD) {
+    SmallMeasParams P = small_params(*s, W);
+    P.pos = pos;
+    P.pos_sk = 1;
+    P.pos_sw = 3 * s->Ne;
+    P.mode = 1;
+    P.EL = EL;
+    P.logpsi = logpsi;
+    P.dlnpsi = dlnpsi_dR;
+    P.dEL = dEL_dR;
+    P.O = O;
+    P.counters = reinterpret_cast<unsigned long long*>(s->scratch_counters);
+    return launch_small_measure(s, eval_grid(*s, W), P, st);
+  }
   if (withD && s->gpb_measD == 0) return fail(VMCF_ENOTSUP, "dEL_dC output does not fit shared memory for this system");
   MeasParams M{};
   M.pos = pos;

@@ -25,7 +25,8 @@ struct DevSys {
   const int* ao_center;  // [M]
   const float* Rh;       // [K][3] nuclear positions as float-float pairs (mixed mode)
   const float* Rl;
-  const int* sharp;      // [nshell] bit k set: primitive k is sharp (its a r^2 is formed in FP64)
+  const int* sharp;      // [nshell] bit k set: primitive k is sharp (its a r^2 keeps extra precision)
+  const float* alpha_lo; // [nshell][kMaxPrim] alpha - (float)alpha, for float-float a r^2
   const double* C[2];    // [M][n_s]
   const float* Cf[2];
   double Fa, Fp, aa, ap, ben;
@@ -141,6 +142,23 @@ __device__ __forceinline__ void normals3(const uint64_t r[4], double xi[3], floa
   xi[2] = (double)(b * cosf(twopi * (float)u01(r[3])));
 }
 
+// Error-free float transformations (Knuth two-sum; Dekker fast two-sum, |a| >= |b|).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  e = b - (s - a);
+}
+
+// Squared distance of a shell's centre as a float-float pair (r2h + r2l), formed from the
+// float-float positions; used for primitives whose a r^2 must keep more than float precision.
+struct R2FF {
+  float h, l;
+};
+
 // ---------------------------------------------------------------- AO shells
 // Angular factor P (a real solid harmonic r^l Y_lm with its unit-sphere normalisation),
 // its gradient g and its constant Hessian h (xx, yy, zz, xy, xz, yz).
@@ -201,20 +219,22 @@ __device__ __forceinline__ EPos make_epos(const double* r) {
 // Each primitive's factor (2l+3) - 2 a r^2 is where the Laplacian cancels; for primitives
 // marked sharp (mixed mode only) a r^2 and the factors are formed in double from r2d.
 template <typename T, int LEVEL>
-__device__ __forceinline__ void shell_eval(const DevSys& S, int s, T x, T y, T z, double r2d, T* out, int stride) {
+__device__ __forceinline__ void shell_eval(const DevSys& S, int s, T x, T y, T z, int smask, R2FF r2ff, T* out,
+                                           int stride) {
   const int4 sh = __ldg(S.shell + s);
   const int l = sh.y, np = sh.z, ao0 = sh.w;
   const T r2 = x * x + y * y + z * z;
-  const int smask = (r2d >= 0.0) ? __ldg(S.sharp + s) : 0;
   T R0 = 0, R1 = 0, R2 = 0, LF = 0, T3 = 0;
   for (int k = 0; k < np; ++k) {
     const T a = prim_alpha<T>(S, s, k);
     T e, f3, f5;
-    if ((smask >> k) & 1) {
-      const double xa = __ldg(S.alpha + s * kMaxPrim + k) * r2d;
-      e = prim_coef<T>(S, s, k) * dexp<T>((T)(-xa));
-      f3 = (T)((2 * l + 3) - 2.0 * xa);
-      f5 = (T)((2 * l + 5) - 2.0 * xa);
+    if (sizeof(T) == 4 && ((smask >> k) & 1)) {
+      const float ah = __ldg(S.alpha_f + s * kMaxPrim + k), al = __ldg(S.alpha_lo + s * kMaxPrim + k);
+      const float xh = ah * r2ff.h;
+      const float xl = fmaf(ah, r2ff.h, -xh) + (ah * r2ff.l + al * r2ff.h);
+      e = (T)(prim_coef<float>(S, s, k) * expf(-xh) * (1.0f - xl));
+      f3 = (T)((float(2 * l + 3) - 2.0f * xh) - 2.0f * xl);
+      f5 = (T)((float(2 * l + 5) - 2.0f * xh) - 2.0f * xl);
     } else {
       const T xa = a * r2;
       e = prim_coef<T>(S, s, k) * dexp<T>(-xa);
@@ -285,22 +305,34 @@ __device__ __forceinline__ void disp_nuc<float>(const DevSys& S, const EPos& p, 
   for (int k = 0; k < 3; ++k) d[k] = (p.h[k] - __ldg(S.Rh + 3 * c + k)) + (p.l[k] - __ldg(S.Rl + 3 * c + k));
 }
 
-// AO components at one point for all shells, threads of the group over shells. SHARP64:
-// form a r^2 of sharp primitives in double (mixed mode).
-template <typename T, int GS, int LEVEL, bool SHARP64>
+// AO components at one point for all shells, threads of the group over shells. SHARP:
+// in mixed mode, form a r^2 of sharp primitives in float-float arithmetic.
+template <typename T, int GS, int LEVEL, bool SHARP>
 __device__ __forceinline__ void ao_point(const DevSys& S, const EPos& p, T* out, int stride) {
   const int t = threadIdx.x % GS;
   for (int s = t; s < S.nshell; s += GS) {
     const int c = __ldg(S.shell + s).x;
     T d[3];
-    disp_nuc<T>(S, p, c, d);
-    double r2d = -1.0;
-    if (SHARP64 && sizeof(T) == 4 && __ldg(S.sharp + s)) {
-      const double dx = p.d[0] - __ldg(S.R + 3 * c), dy = p.d[1] - __ldg(S.R + 3 * c + 1),
-                   dz = p.d[2] - __ldg(S.R + 3 * c + 2);
-      r2d = dx * dx + dy * dy + dz * dz;
+    R2FF r2ff{0.f, 0.f};
+    int smask = 0;
+    if (SHARP && sizeof(T) == 4 && (smask = __ldg(S.sharp + s))) {
+      float hsum = 0.f, lsum = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        float dh, dl, sdiff, eh;
+        two_sum(p.h[k], -__ldg(S.Rh + 3 * c + k), sdiff, eh);
+        fast_two_sum(sdiff, (p.l[k] - __ldg(S.Rl + 3 * c + k)) + eh, dh, dl);
+        d[k] = (T)dh;
+        const float pp = dh * dh, pe = fmaf(dh, dh, -pp);
+        float tt;
+        two_sum(hsum, pp, hsum, tt);
+        lsum += tt + pe + 2.0f * dh * dl;
+      }
+      fast_two_sum(hsum, lsum, r2ff.h, r2ff.l);
+    } else {
+      disp_nuc<T>(S, p, c, d);
     }
-    shell_eval<T, LEVEL>(S, s, d[0], d[1], d[2], r2d, out, stride);
+    shell_eval<T, LEVEL>(S, s, d[0], d[1], d[2], smask, r2ff, out, stride);
   }
 }
 
@@ -333,7 +365,7 @@ __device__ __forceinline__ T pade_value(T a, T F, T r) {
 
 // ---------------------------------------------------------------- FP64 Gauss-Jordan inverse
 // In-place inversion of the n x n row-major matrix A (shared memory, double) with partial
-// row pivoting. piv: int[n], f: double[n] scratch, flag: int (set to 1 if a pivot is zero
+// row pivoting. piv: int[n], f: double[n + 1] scratch, flag: int (set to 1 if a pivot is zero
 // or not finite). logabs/sign are accumulated when want_logdet. Every thread of the group
 // must call it.
 template <int GS>
@@ -341,17 +373,18 @@ __device__ void gj_inverse(double* A, int n, int* piv, double* f, int* flag, dou
                            bool want_logdet) {
   const int t = threadIdx.x % GS;
   for (int k = 0; k < n; ++k) {
-    // pivot search by the first warp of the group
+    // pivot search by the first warp of the group; |x| of doubles compared through their bit
+    // patterns (monotone for non-negative values), so the search needs no FP64 instruction
     if (t < 32) {
-      double best = -1.0;
+      long long best = -1;
       int bi = k;
       for (int i = k + t; i < n; i += 32) {
-        const double v = fabs(A[i * n + k]);
+        const long long v = __double_as_longlong(A[i * n + k]) & 0x7fffffffffffffffLL;
         if (v > best) { best = v; bi = i; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
@@ -359,6 +392,7 @@ __device__ void gj_inverse(double* A, int n, int* piv, double* f, int* flag, dou
         piv[k] = bi;
         const double p = A[bi * n + k];
         if (!(p != 0.0) || !isfinite(p)) *flag = 1;
+        f[n] = 1.0 / p;  // the pivot's reciprocal, computed once
         if (want_logdet) {
           *logabs += log(fabs(p));
           if (p < 0) *sgn = -*sgn;
@@ -375,7 +409,7 @@ __device__ void gj_inverse(double* A, int n, int* piv, double* f, int* flag, dou
         A[p * n + j] = a;
       }
     gsync<GS>();
-    const double pinv = 1.0 / A[k * n + k];
+    const double pinv = f[n];
     for (int i = t; i < n; i += GS) f[i] = A[i * n + k];
     gsync<GS>();
     for (int j = t; j < n; j += GS) A[k * n + j] = (j == k ? 1.0 : A[k * n + j]) * pinv;

@@ -25,6 +25,13 @@ struct vmcf_system_s {
   bool acc_smem = false;
   int acc_off = -1;
   double* scratch_counters = nullptr;  // device [2] for evaluate
+  // small-system path (at most 32 electrons and 16 orbitals per spin)
+  bool small = false;
+  int small_nm = 16;          // register row width: 8 or 16
+  int small_warps = 8;        // warps per CTA of the measurement kernel
+  int small_res = 1;          // resident measurement CTAs on the device
+  vmcf::SmallLayout SL{};
+  size_t small_move_smem = 0;  // C staging of the move kernel
 };
 
 struct vmcf_walkers_s {
@@ -41,6 +48,9 @@ struct vmcf_walkers_s {
   uint64_t sweep = 0, measured = 0;
   int counter = 0;
   double e_ref = 0.0;
+  // small-system path state: positions and inverses walker-interleaved
+  float2* posf = nullptr;   // float-float positions (mixed mode)
+  double* stage = nullptr;  // [W][Ne][3] staging for layout conversion
   // per-kernel timing (kind 0 move, 1 measure, 2 refresh): event pairs around launches
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;

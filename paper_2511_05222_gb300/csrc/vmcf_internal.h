@@ -57,6 +57,51 @@ cudaError_t launch_measure(const DevSys& S, const Launch& lc, const MeasParams& 
 template <typename T>
 cudaError_t set_smem_limits(int GS);
 
+// ---- small-system path (kernels_small.cuh)
+struct SmallMoveParams {
+  double* pos;   // [3 Ne][W]
+  float2* posf;  // [3 Ne][W] float-float (mixed mode) or NULL
+  void* B;       // T [nB][W]
+  uint32_t* nacc;
+  uint32_t* nrej;
+  int W;
+  uint64_t wid0, k0, k1;
+  uint64_t move0;  // global index of the first move: sweep = move0 / Ne, electron = move0 % Ne
+  int nmoves;
+  double sigma;
+};
+
+struct SmallLayout {
+  int pd, ph, pl, Ad, Bf, Pm, Q, piv, f, frc, phi, red, scal;
+  int bytes;  // per warp
+  int cta_C, cta_acc, cta_bytes;
+  int chunk;  // AOs per O chunk (Phi buffer width)
+};
+
+struct SmallMeasParams {
+  const double* pos;  // positions, element (w, k) at pos[k * pos_sk + w * pos_sw], k = 3 e + xyz
+  long long pos_sk, pos_sw;
+  int mode;             // 0 refresh only, 1 evaluate, 2 accumulate
+  void* Bout;           // T [nB][W] (refresh and accumulate modes) or NULL
+  float2* posf_out;     // float-float positions [3 Ne][W] to refresh (mixed, refresh mode) or NULL
+  double *EL, *logpsi, *dlnpsi, *dEL, *O;  // evaluate-mode outputs (any may be NULL)
+  double* acc;          // [grid][accL] FP64 slots (accumulate mode)
+  int accL;
+  double e_ref;
+  unsigned long long* counters;
+  int W;
+};
+
+template <typename T>
+cudaError_t launch_move_small(const DevSys& S, int nm, int W, size_t smem, const SmallMoveParams& P, cudaStream_t st);
+template <typename T>
+cudaError_t launch_measure_small(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
+                                 const SmallMeasParams& P, cudaStream_t st);
+template <typename T>
+cudaError_t set_smem_limits_small();
+cudaError_t launch_to_interleaved(const double* src, double* dst, float2* dstf, int W, int n3, cudaStream_t st);
+cudaError_t launch_from_interleaved(const double* src, double* dst, int W, int n3, cudaStream_t st);
+
 cudaError_t run_probes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, cudaStream_t st);
 
 cudaError_t launch_block_reduce(const double* acc, int grid, int cpb, int accL, double* out, int nblocks,

@@ -14,6 +14,7 @@ import numpy as np
 from . import build as _build
 
 FP64, MIXED = 0, 1
+FORCE_GROUP_PATH = 0x100
 _STATUS = {0: "VMCF_OK", -1: "VMCF_EINVAL", -2: "VMCF_ENOMEM", -3: "VMCF_ECUDA", -4: "VMCF_ESINGULAR",
            -5: "VMCF_ETIMEOUT", -6: "VMCF_ENOTSUP"}
 
@@ -119,7 +120,7 @@ def _np(a, dt):
 class System:
     """vmcf_init_system: a molecule, its basis, frozen orbitals and Jastrow, on the GPU."""
 
-    def __init__(self, sys, precision: int = FP64):
+    def __init__(self, sys, precision: int = FP64, force_group: bool = False):
         L = lib()
         j = sys.jastrow
         self._hold = dict(Z=_np(sys.Z, np.int32), R=_np(sys.R, np.float64), c=_np(sys.shell_center, np.int32),
@@ -135,7 +136,8 @@ class System:
         jas = _Jastrow(j.F_anti, j.F_par, j.a_anti, j.a_par, j.b_en, int(j.enable_J1), int(j.enable_J2))
         out = _vp()
         _check(L.vmcf_init_system(ctypes.byref(nuc), ctypes.byref(bas), dp(h["Cu"]), dp(h["Cd"]), sys.n_up, sys.n_dn,
-                                  ctypes.byref(jas), dp(h["S"]), precision, ctypes.byref(out)), "vmcf_init_system")
+                                  ctypes.byref(jas), dp(h["S"]), precision | (FORCE_GROUP_PATH if force_group else 0),
+                                  ctypes.byref(out)), "vmcf_init_system")
         self.h = out
         self.precision = precision
         self.sys = sys
