@@ -186,6 +186,14 @@ int vmcf_status_counters(vmcf_walkers_t wk, vmcf_counters* out, void* stream);
 int vmcf_evaluate_sums_noalloc(vmcf_system_t sys, const double* pos, int W, double e_ref, double* sums,
                                void* stream);
 
+/* Launch-shape knobs of a system (not part of the paper's method; results are unchanged):
+ *   "move_lanes_per_walker": 1, 2, 4 or 8 lanes share one walker in the Metropolis kernel of
+ *                            the small-system path (default 1);
+ *   "measure_warps":         2, 4 or 8 walkers (one warp each) per CTA of the small-system
+ *                            measurement kernel (default: the most that fit shared memory, up to 8).
+ * Takes effect for walker sets created afterwards (measure_warps) or at the next call. */
+int vmcf_set_tuning(vmcf_system_t sys, const char* key, int value);
+
 /* Diagnostics (not part of the paper's method).
  * vmcf_profile: record a CUDA event pair around every kernel this walker set launches from
  * now on (enable != 0) or stop recording (0).

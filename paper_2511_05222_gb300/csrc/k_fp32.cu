@@ -21,9 +21,9 @@ cudaError_t set_smem_limits<float>(int) {
   return set_smem_limits_impl<float>();
 }
 template <>
-cudaError_t launch_move_small<float>(const DevSys& S, int nm, int W, size_t smem, const SmallMoveParams& P,
-                                   cudaStream_t st) {
-  return launch_move_small_impl<float>(S, nm, W, smem, P, st);
+cudaError_t launch_move_small<float>(const DevSys& S, int nm, int lpw, int W, size_t smem,
+                                   const SmallMoveParams& P, cudaStream_t st) {
+  return launch_move_small_impl<float>(S, nm, lpw, W, smem, P, st);
 }
 template <>
 cudaError_t launch_measure_small<float>(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,

@@ -23,9 +23,9 @@ cudaError_t set_smem_limits<double>(int) {
   return set_smem_limits_impl<double>();
 }
 template <>
-cudaError_t launch_move_small<double>(const DevSys& S, int nm, int W, size_t smem, const SmallMoveParams& P,
-                                   cudaStream_t st) {
-  return launch_move_small_impl<double>(S, nm, W, smem, P, st);
+cudaError_t launch_move_small<double>(const DevSys& S, int nm, int lpw, int W, size_t smem,
+                                   const SmallMoveParams& P, cudaStream_t st) {
+  return launch_move_small_impl<double>(S, nm, lpw, W, smem, P, st);
 }
 template <>
 cudaError_t launch_measure_small<double>(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,

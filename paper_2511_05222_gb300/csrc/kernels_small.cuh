@@ -120,10 +120,13 @@ __device__ __forceinline__ void axpy_row(T (&acc)[NM], T a, const T* __restrict_
 
 template <typename T, int NM>
 __device__ __forceinline__ T dot_row(const T (&x)[NM], const T* __restrict__ crow) {
-  T s = 0;
+  T s0 = 0, s1 = 0;  // two chains for instruction-level parallelism
 #pragma unroll
-  for (int i = 0; i < NM; ++i) s += x[i] * crow[i];
-  return s;
+  for (int i = 0; i < NM; i += 2) {
+    s0 += x[i] * crow[i];
+    if (i + 1 < NM) s1 += x[i + 1] * crow[i + 1];
+  }
+  return s0 + s1;
 }
 
 // Stage C^up and C^dn into shared memory as [2][M][NM], zero-padded beyond n_s.
@@ -137,15 +140,31 @@ __device__ __forceinline__ void stage_C(const DevSys& S, T* Cs) {
 }
 
 
-// ---------------------------------------------------------------- moves, one lane per walker
-template <typename T, int NM>
+// ---------------------------------------------------------------- moves, LPW lanes per walker
+// Sum over the LPW lanes of a walker (xor butterfly: every lane receives the same bits).
+template <int LPW, typename V>
+__device__ __forceinline__ V lane_group_sum(V v, unsigned mask) {
+#pragma unroll
+  for (int o = 1; o < LPW; o <<= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+// A run of single-electron Metropolis moves. LPW lanes cooperate on one walker: shells, ratio
+// terms, Jastrow pairs and Sherman-Morrison columns are split across them and combined with
+// butterfly sums, so the accept decision is identical in all of a walker's lanes.
+template <typename T, int NM, int LPW>
 __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* Cs = reinterpret_cast<T*>(smem);
   stage_C<T, NM>(S, Cs);
   __syncthreads();
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = gtid / LPW, q = gtid % LPW;
+  // whole lane groups leave together (LPW divides 32)
   if (w >= P.W) return;
+  // lanes of this walker only: barriers inside the accept branch must not wait for other
+  // walkers' lanes, which take their own branch
+  const unsigned mask = (LPW == 32) ? 0xffffffffu : (((1u << LPW) - 1u) << ((threadIdx.x & 31) & ~(LPW - 1)));
   const int W = P.W, Ne = S.Ne, nup = S.nup, K = S.K;
   T* B = reinterpret_cast<T*>(P.B);
   const uint64_t wid = P.wid0 + (uint64_t)w;
@@ -175,11 +194,11 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
         ol[k] = f.y;
       }
     }
-    // new orbital row
+    // new orbital row: this lane's shells, then the group sum
     T row[NM];
 #pragma unroll
     for (int i = 0; i < NM; ++i) row[i] = T(0);
-    for (int s = 0; s < S.nshell; ++s) {
+    for (int s = q; s < S.nshell; s += LPW) {
       const int4 sh = __ldg(S.shell + s);
       T d[3];
       if constexpr (sizeof(T) == 8) {
@@ -197,38 +216,39 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
         axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * NM);
       }
     }
+#pragma unroll
+    for (int i = 0; i < NM; ++i) row[i] = lane_group_sum<LPW>(row[i], mask);
+    // determinant ratio (FP64): this lane's orbitals i = q, q + LPW, ...
     double R = 0.0;
 #pragma unroll
     for (int i = 0; i < NM; ++i)
-      if (i < n) R += (double)row[i] * (double)B[(size_t)(off + i * n + el) * W + w];
-    // Jastrow ratio
-    double dJ = 0.0;
+      if (i % LPW == q && i < n) R += (double)row[i] * (double)B[(size_t)(off + i * n + el) * W + w];
+    R = lane_group_sum<LPW>(R, mask);
+    // Jastrow ratio: this lane's partners j = q, q + LPW, ... and nuclei I = q, q + LPW, ...
+    T jacc = 0;
     if (S.J2) {
-      T acc = 0;
-      for (int q = 0; q < Ne; ++q) {
-        if (q == e) continue;
-        const bool par = (q < nup) == (e < nup);
+      for (int j = q; j < Ne; j += LPW) {
+        if (j == e) continue;
+        const bool par = (j < nup) == (e < nup);
         const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
         T d1[3], d0[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           if constexpr (sizeof(T) == 8) {
-            const double pq = P.pos[(size_t)(3 * q + k) * W + w];
-            d1[k] = rn[k] - pq;
-            d0[k] = po[k] - pq;
+            const double pj = P.pos[(size_t)(3 * j + k) * W + w];
+            d1[k] = rn[k] - pj;
+            d0[k] = po[k] - pj;
           } else {
-            const float2 f = P.posf[(size_t)(3 * q + k) * W + w];
+            const float2 f = P.posf[(size_t)(3 * j + k) * W + w];
             d1[k] = (nh[k] - f.x) + (nl[k] - f.y);
             d0[k] = (oh[k] - f.x) + (ol[k] - f.y);
           }
         }
-        acc += pade_at<T>(a, F, d1) - pade_at<T>(a, F, d0);
+        jacc += pade_at<T>(a, F, d1) - pade_at<T>(a, F, d0);
       }
-      dJ += (double)acc;
     }
     if (S.J1) {
-      T acc = 0;
-      for (int I = 0; I < K; ++I) {
+      for (int I = q; I < K; I += LPW) {
         const T mz = (T)(-__ldg(S.Z + I)), b = (T)S.ben;
         T d1[3], d0[3];
 #pragma unroll
@@ -241,10 +261,10 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
             d0[k] = (oh[k] - __ldg(S.Rh + 3 * I + k)) + (ol[k] - __ldg(S.Rl + 3 * I + k));
           }
         }
-        acc += pade_at<T>(mz, b, d1) - pade_at<T>(mz, b, d0);
+        jacc += pade_at<T>(mz, b, d1) - pade_at<T>(mz, b, d0);
       }
-      dJ += (double)acc;
     }
+    const double dJ = (double)lane_group_sum<LPW>(jacc, mask);
     uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
     philox4x64_10(r2, P.k0, P.k1);
     const double u = u01(r2[0]);
@@ -252,12 +272,13 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
     const bool ok = isfinite(pr) && R != 0.0;
     if (!ok) ++nrej;
     if (ok && u < pr) {
-      // Sherman-Morrison: w_j = sum_i row_i B_ij - delta_j,el; B_kj <- B_kj - B_k,el w_j / R
+      // Sherman-Morrison: w_j = sum_i row_i B_ij - delta_j,el; B_kj <- B_kj - B_k,el w_j / R.
+      // This lane owns columns j = q, q + LPW, ...; every lane reads the whole column el first.
       T wv[NM], col[NM];
 #pragma unroll
       for (int j = 0; j < NM; ++j) {
         wv[j] = T(0);
-        col[j] = T(0);
+        col[j] = (j < n) ? B[(size_t)(off + j * n + el) * W + w] : T(0);
       }
 #pragma unroll
       for (int i = 0; i < NM; ++i) {
@@ -265,37 +286,36 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
         const T ri = row[i];
 #pragma unroll
         for (int j = 0; j < NM; ++j)
-          if (j < n) wv[j] += ri * B[(size_t)(off + i * n + j) * W + w];
+          if (j % LPW == q && j < n) wv[j] += ri * B[(size_t)(off + i * n + j) * W + w];
       }
-#pragma unroll
-      for (int j = 0; j < NM; ++j) {
-        if (j < n) {
-          if (j == el) wv[j] -= T(1);
-          col[j] = B[(size_t)(off + j * n + el) * W + w];
-        }
-      }
+      if (LPW > 1) __syncwarp(mask);  // column el is read by all lanes before its owner rewrites it
       const T rinv = (T)(1.0 / R);
 #pragma unroll
-      for (int k = 0; k < NM; ++k) {
-        if (k >= n) continue;
-        const T ck = col[k] * rinv;
+      for (int j = 0; j < NM; ++j) {
+        if (j % LPW != q || j >= n) continue;
+        const T wj = (j == el) ? wv[j] - T(1) : wv[j];
 #pragma unroll
-        for (int j = 0; j < NM; ++j) {
-          if (j >= n) continue;
-          T& b = B[(size_t)(off + k * n + j) * W + w];
-          b -= ck * wv[j];
+        for (int k = 0; k < NM; ++k) {
+          if (k >= n) continue;
+          T& bkj = B[(size_t)(off + k * n + j) * W + w];
+          bkj -= col[k] * rinv * wj;
         }
       }
+      if (q == 0) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        P.pos[(size_t)(3 * e + k) * W + w] = rn[k];
-        if constexpr (sizeof(T) == 4) P.posf[(size_t)(3 * e + k) * W + w] = make_float2(nh[k], nl[k]);
+        for (int k = 0; k < 3; ++k) {
+          P.pos[(size_t)(3 * e + k) * W + w] = rn[k];
+          if constexpr (sizeof(T) == 4) P.posf[(size_t)(3 * e + k) * W + w] = make_float2(nh[k], nl[k]);
+        }
       }
       ++nacc;
     }
+    if (LPW > 1) __syncwarp(mask);  // the new position is visible to the group's next move
   }
-  P.nacc[w] += nacc;
-  P.nrej[w] += nrej;
+  if (q == 0) {
+    P.nacc[w] += nacc;
+    P.nrej[w] += nrej;
+  }
 }
 
 // ---------------------------------------------------------------- measurement, one warp per walker
@@ -317,7 +337,7 @@ __device__ __forceinline__ void warp_sum_f(double (&v)[NV]) {
 }
 
 template <typename T, int NM>
-__global__ void __launch_bounds__(256) measure_small(DevSys S, SmallLayout L, SmallMeasParams P) {
+__global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L, SmallMeasParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   T* Cs = reinterpret_cast<T*>(smem + L.cta_C);
@@ -613,32 +633,27 @@ __global__ void __launch_bounds__(256) measure_small(DevSys S, SmallLayout L, Sm
         R2FF r2ff{0.f, 0.f};
         const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
         const Radial<T> rs = radial_sums<T, 2>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
+        const T xj = d[0] * jg[0] + d[1] * jg[1] + d[2] * jg[2];
         for (int m = 0; m < ncomp; ++m) {
           T Pa, g[3], h[6];
           angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
           const T* cr = Csg + (sh.w + m) * NM;
           const T yA = dot_row<T, NM>(xr, cr), yL = dot_row<T, NM>(bc, cr);
-          T gv[3], gl[3];
+          // Hessian of the AO contracted with grad J without forming it:
+          // (H j)_a = (h j)_a R0 + g_a (x.j) R1 + (g.j) x_a R1 + P x_a (x.j) R2 + P j_a R1
+          const T hj0 = h[0] * jg[0] + h[3] * jg[1] + h[4] * jg[2];
+          const T hj1 = h[3] * jg[0] + h[1] * jg[1] + h[5] * jg[2];
+          const T hj2 = h[4] * jg[0] + h[5] * jg[1] + h[2] * jg[2];
+          const T hjv[3] = {hj0, hj1, hj2};
+          const T gj = g[0] * jg[0] + g[1] * jg[1] + g[2] * jg[2];
+          const T PxjR2 = Pa * xj * rs.R2, gjR1 = gj * rs.R1, PR1 = Pa * rs.R1, xjR1 = xj * rs.R1;
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            gv[k] = g[k] * rs.R0 + Pa * d[k] * rs.R1;
-            gl[k] = g[k] * rs.LF + Pa * d[k] * rs.T3;
-          }
-          // Hessian (xx, yy, zz, xy, xz, yz) contracted with grad J
-          T H[3][3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-              const int hk = (a == b) ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5));
-              H[a][b] = h[hk] * rs.R0 + (g[a] * d[b] + g[b] * d[a]) * rs.R1 +
-                        Pa * (d[a] * d[b] * rs.R2 + (a == b ? rs.R1 : T(0)));
-            }
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const T hj = H[k][0] * jg[0] + H[k][1] * jg[1] + H[k][2] * jg[2];
-            fl[k] -= gv[k] * yL;
-            fe[k] += T(-0.5) * (gv[k] * yA - yL * (gl[k] + T(2) * hj));
+            const T gv = g[k] * rs.R0 + Pa * d[k] * rs.R1;
+            const T gl = g[k] * rs.LF + Pa * d[k] * rs.T3;
+            const T hj = hjv[k] * rs.R0 + g[k] * xjR1 + d[k] * (gjR1 + PxjR2) + jg[k] * PR1;
+            fl[k] -= gv * yL;
+            fe[k] += T(-0.5) * (gv * yA - yL * (gl + T(2) * hj));
           }
           phi[e * L.chunk + chunk_n + m] = Pa * rs.R0;
         }
@@ -762,16 +777,26 @@ static __global__ void from_interleaved(const double* __restrict__ src, double* 
   }
 }
 
-template <typename T>
-cudaError_t launch_move_small_impl(const DevSys& S, int nm, int W, size_t smem, const SmallMoveParams& P,
-                                   cudaStream_t st) {
-  const int threads = 32;
-  const dim3 grid((W + threads - 1) / threads);
-  if (nm <= 8)
-    move_small<T, 8><<<grid, threads, smem, st>>>(S, P);
-  else
-    move_small<T, 16><<<grid, threads, smem, st>>>(S, P);
+template <typename T, int NM>
+cudaError_t launch_move_small_lpw(int lpw, const DevSys& S, int W, size_t smem, const SmallMoveParams& P,
+                                  cudaStream_t st) {
+  const int threads = 64;
+  const long long lanes = (long long)W * lpw;
+  const dim3 grid((unsigned)((lanes + threads - 1) / threads));
+  switch (lpw) {
+    case 1: move_small<T, NM, 1><<<grid, threads, smem, st>>>(S, P); break;
+    case 2: move_small<T, NM, 2><<<grid, threads, smem, st>>>(S, P); break;
+    case 4: move_small<T, NM, 4><<<grid, threads, smem, st>>>(S, P); break;
+    default: move_small<T, NM, 8><<<grid, threads, smem, st>>>(S, P); break;
+  }
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_move_small_impl(const DevSys& S, int nm, int lpw, int W, size_t smem, const SmallMoveParams& P,
+                                   cudaStream_t st) {
+  if (nm <= 8) return launch_move_small_lpw<T, 8>(lpw, S, W, smem, P, st);
+  return launch_move_small_lpw<T, 16>(lpw, S, W, smem, P, st);
 }
 
 template <typename T>
@@ -789,8 +814,11 @@ template <typename T>
 cudaError_t set_smem_limits_small_impl() {
   const int lim = 227 * 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(move_small<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(move_small<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+#define VMCF_MOVE_ATTR(NM, L)                                                                                   \
+  if ((e = cudaFuncSetAttribute(move_small<T, NM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  VMCF_MOVE_ATTR(8, 1) VMCF_MOVE_ATTR(8, 2) VMCF_MOVE_ATTR(8, 4) VMCF_MOVE_ATTR(8, 8)
+  VMCF_MOVE_ATTR(16, 1) VMCF_MOVE_ATTR(16, 2) VMCF_MOVE_ATTR(16, 4) VMCF_MOVE_ATTR(16, 8)
+#undef VMCF_MOVE_ATTR
   if ((e = cudaFuncSetAttribute(measure_small<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(measure_small<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   return cudaSuccess;

@@ -164,7 +164,7 @@ void plan_small(vmcf_system_s& s) {
   const int tsz = s.precision == VMCF_FP64 ? 8 : 4;
   s.small_nm = s.nmax <= 8 ? 8 : 16;
   SmallLayout L{};
-  L.chunk = 20;
+  L.chunk = 21;  // odd row stride: lanes writing phi[e][c] fall in distinct banks
   int o = 0;
   auto take = [&](int bytes) { int at = o; o = align16(o + bytes); return at; };
   L.pd = take(8 * 3 * s.Ne);
@@ -692,8 +692,9 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
         P.nmoves = chunk;
         {
           Timed tm(wk, 0, st);
-          cudaError_t e = fp64 ? launch_move_small<double>(s->dev, s->small_nm, wk->W, s->small_move_smem, P, st)
-                               : launch_move_small<float>(s->dev, s->small_nm, wk->W, s->small_move_smem, P, st);
+          cudaError_t e =
+              fp64 ? launch_move_small<double>(s->dev, s->small_nm, s->move_lpw, wk->W, s->small_move_smem, P, st)
+                   : launch_move_small<float>(s->dev, s->small_nm, s->move_lpw, wk->W, s->small_move_smem, P, st);
           if (e != cudaSuccess) return cuda_fail(e, "small move kernel launch");
         }
         done += chunk;
@@ -905,6 +906,23 @@ int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double
     }
   }
   return VMCF_OK;
+}
+
+int vmcf_set_tuning(vmcf_system_t s, const char* key, int value) {
+  if (!s || !key) return fail(VMCF_EINVAL, "bad arguments");
+  const std::string k(key);
+  if (k == "move_lanes_per_walker") {
+    if (value != 1 && value != 2 && value != 4 && value != 8) return fail(VMCF_EINVAL, "lanes per walker: 1, 2, 4 or 8");
+    s->move_lpw = value;
+    return VMCF_OK;
+  }
+  if (k == "measure_warps") {
+    if (!s->small || (value != 2 && value != 4 && value != 8)) return fail(VMCF_EINVAL, "measure warps: 2, 4 or 8");
+    if (s->SL.cta_bytes + value * s->SL.bytes > kSmemCap) return fail(VMCF_EINVAL, "does not fit shared memory");
+    s->small_warps = value;
+    return VMCF_OK;
+  }
+  return fail(VMCF_EINVAL, "unknown tuning key");
 }
 
 int vmcf_profile(vmcf_walkers_t wk, int enable) {

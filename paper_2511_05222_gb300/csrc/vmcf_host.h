@@ -32,6 +32,7 @@ struct vmcf_system_s {
   int small_res = 1;          // resident measurement CTAs on the device
   vmcf::SmallLayout SL{};
   size_t small_move_smem = 0;  // C staging of the move kernel
+  int move_lpw = 1;            // lanes per walker in the move kernel (1, 2, 4 or 8)
 };
 
 struct vmcf_walkers_s {

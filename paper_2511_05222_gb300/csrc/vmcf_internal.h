@@ -93,7 +93,8 @@ struct SmallMeasParams {
 };
 
 template <typename T>
-cudaError_t launch_move_small(const DevSys& S, int nm, int W, size_t smem, const SmallMoveParams& P, cudaStream_t st);
+cudaError_t launch_move_small(const DevSys& S, int nm, int lpw, int W, size_t smem, const SmallMoveParams& P,
+                              cudaStream_t st);
 template <typename T>
 cudaError_t launch_measure_small(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
                                  const SmallMeasParams& P, cudaStream_t st);

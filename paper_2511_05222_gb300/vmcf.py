@@ -87,6 +87,7 @@ def lib(build_if_missing: bool = True):
         L.vmcf_block_sums.argtypes = [_vp, _vp, _dp, _vp]
         L.vmcf_status_counters.argtypes = [_vp, ctypes.POINTER(Counters), _vp]
         L.vmcf_profile.argtypes = [_vp, ctypes.c_int]
+        L.vmcf_set_tuning.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int]
         L.vmcf_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
         L.vmcf_probe_pipes.argtypes = [_dp, _dp, _dp, _vp]
         _lib = L
@@ -148,6 +149,9 @@ class System:
         self.Ne = self.n_up + self.n_dn
         self.nO = self.M * self.Ne
         self.accL = L.vmcf_accumulator_length(self.h)
+
+    def set_tuning(self, key: str, value: int):
+        _check(lib().vmcf_set_tuning(self.h, key.encode(), int(value)), "vmcf_set_tuning")
 
     def close(self):
         if getattr(self, "h", None):
