@@ -144,6 +144,11 @@ int vmcf_reset_accumulators(vmcf_walkers_t wk, double e_ref, void* stream);
 int vmcf_sample(vmcf_system_t sys, vmcf_walkers_t wk, int n_sweeps, double step_sigma, int refresh_k,
                 int measure, void* stream);
 
+/* One measurement of the walkers' current positions, without moving them: the inverses
+ * are rebuilt in FP64 and E_L, d ln Psi/dR, dE_L/dR and O are added to the walker sums (as
+ * one measured sweep of vmcf_sample does). Used for estimators on fixed configurations. */
+int vmcf_measure(vmcf_system_t sys, vmcf_walkers_t wk, void* stream);
+
 /* Fixed-walker evaluation (no sampling). pos: device [W][Ne][3]. Outputs are device
  * buffers owned by the caller; any may be NULL:
  *   EL [W], logpsi [W] (ln|Psi|), dlnpsi_dR [W][K][3], dEL_dR [W][K][3],
@@ -162,6 +167,14 @@ int vmcf_reduce_estimators(vmcf_system_t sys, vmcf_walkers_t wk, double* E, doub
  * sum O [nO], sum (E_L-E_ref) O [nO], with nO = M (n_up + n_dn). */
 int vmcf_block_sums(vmcf_system_t sys, vmcf_walkers_t wk, double* out, void* stream);
 int vmcf_accumulator_length(vmcf_system_t sys);
+
+/* Host-only estimator finish (no GPU needed): Eqs. hf/pulay and fc-vmc-eval from block sums
+ * `blocks` [nblocks][3 + 9K + 2 M (n_up + n_dn)] in the vmcf_block_sums layout, with e_ref the
+ * reference energy the sums were taken with. This is what several ranks call after gathering
+ * their block sums (the blocks of all ranks side by side); vmcf_reduce_estimators calls it too.
+ * Host outputs as in vmcf_reduce_estimators (any may be NULL). */
+int vmcf_finish_estimators(const double* blocks, int nblocks, int K, int M, int n_up, int n_dn, double e_ref,
+                           double* E, double* E_err, double* F, double* F_err, double* dEdC, double* dEdC_err);
 
 /* Counters (synchronises the stream). */
 int vmcf_status_counters(vmcf_walkers_t wk, vmcf_counters* out, void* stream);

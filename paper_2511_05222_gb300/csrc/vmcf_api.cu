@@ -771,6 +771,43 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
   return VMCF_OK;
 }
 
+int vmcf_measure(vmcf_system_t s, vmcf_walkers_t wk, void* stream) {
+  if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (s->small) {
+    SmallMeasParams M = small_params(*s, wk->W);
+    M.pos = wk->pos;
+    M.pos_sk = wk->W;
+    M.pos_sw = 1;
+    M.mode = 2;
+    M.Bout = wk->B;
+    M.acc = wk->acc;
+    M.e_ref = wk->e_ref;
+    M.counters = wk->counters;
+    Timed tm(wk, 1, st);
+    int rc = launch_small_measure(s, wk->grid_meas, M, st);
+    if (rc != VMCF_OK) return rc;
+  } else {
+    MeasParams M{};
+    M.pos = wk->pos;
+    M.Bout = wk->B;
+    M.acc = wk->acc;
+    M.accL = s->accL;
+    M.acc_in_smem = s->acc_smem ? 1 : 0;
+    M.e_ref = wk->e_ref;
+    M.counters = wk->counters;
+    M.W = wk->W;
+    const Launch lme = launch_meas(*s, wk->grid_meas, true, false);
+    Timed tm(wk, 1, st);
+    cudaError_t e = s->precision == VMCF_FP64 ? launch_measure<double>(s->dev, lme, M, st)
+                                              : launch_measure<float>(s->dev, lme, M, st);
+    if (e != cudaSuccess) return cuda_fail(e, "measure kernel launch");
+  }
+  wk->counter = 0;
+  wk->measured += 1;
+  return VMCF_OK;
+}
+
 int vmcf_evaluate(vmcf_system_t s, const double* pos, int W, double* EL, double* logpsi, double* dlnpsi_dR,
                   double* dEL_dR, double* O, double* dEL_dC, void* stream) {
   if (!s || !pos || W < 0) return fail(VMCF_EINVAL, "bad arguments");
@@ -821,28 +858,23 @@ int vmcf_block_sums(vmcf_system_t s, vmcf_walkers_t wk, double* out, void* strea
   return VMCF_OK;
 }
 
-int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double* E_err, double* F, double* F_err,
-                           double* dEdC, double* dEdC_err, double* rhs_BQ, void* stream) {
-  if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
-  if (rhs_BQ && !s->has_S) return fail(VMCF_EINVAL, "rhs_BQ needs the AO overlap S at init");
-  const int L = s->accL, nb = wk->nblocks, K3 = 3 * s->K, nO = s->M * (s->nup + s->ndn);
-  std::vector<double> blk((size_t)nb * L);
-  int rc = vmcf_block_sums(s, wk, blk.data(), stream);
-  if (rc != VMCF_OK) return rc;
+int vmcf_finish_estimators(const double* blk, int nb, int K, int M, int n_up, int n_dn, double er, double* E,
+                           double* E_err, double* F, double* F_err, double* dEdC, double* dEdC_err) {
+  if (!blk || nb < 2 || K < 1 || M < 1 || n_up < 0 || n_dn < 0) return fail(VMCF_EINVAL, "bad arguments");
+  const int K3 = 3 * K, nO = M * (n_up + n_dn), L = 3 + 9 * K + 2 * nO;
   std::vector<double> tot(L, 0.0);
   for (int b = 0; b < nb; ++b)
     for (int i = 0; i < L; ++i) tot[i] += blk[(size_t)b * L + i];
   if (!(tot[0] > 0.0)) return fail(VMCF_EINVAL, "no measured samples");
-  const double er = wk->e_ref;
+  for (int b = 0; b < nb; ++b)
+    if (!(tot[0] - blk[(size_t)b * L] > 0.0)) return fail(VMCF_EINVAL, "a jackknife block holds every sample");
   const int o_dEL = 3, o_d = 3 + K3, o_Ed = 3 + 2 * K3, o_O = 3 + 3 * K3, o_EO = 3 + 3 * K3 + nO;
-  // estimates from a sum vector v (all blocks, or all but one)
+  // estimates from a sum vector v (all blocks, or all but one); E_ref cancels algebraically
   auto est = [&](const double* v, double* Eo, double* Fo, double* Bo) {
     const double n = v[0], Em = v[1] / n;
     *Eo = Em;
-    if (Fo)
-      for (int i = 0; i < K3; ++i) Fo[i] = -(v[o_dEL + i] / n + 2.0 * (v[o_Ed + i] / n - (Em - er) * v[o_d + i] / n));
-    if (Bo)
-      for (int i = 0; i < nO; ++i) Bo[i] = 2.0 * (v[o_EO + i] / n - (Em - er) * v[o_O + i] / n);
+    for (int i = 0; i < K3; ++i) Fo[i] = -(v[o_dEL + i] / n + 2.0 * (v[o_Ed + i] / n - (Em - er) * v[o_d + i] / n));
+    for (int i = 0; i < nO; ++i) Bo[i] = 2.0 * (v[o_EO + i] / n - (Em - er) * v[o_O + i] / n);
   };
   double Ev;
   std::vector<double> Fv(K3), Bv(nO);
@@ -874,6 +906,22 @@ int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double
     if (dEdC) dEdC[i] = Bv[i];
     if (dEdC_err) dEdC_err[i] = jk(Bj.data(), nO, i);
   }
+  return VMCF_OK;
+}
+
+int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double* E_err, double* F, double* F_err,
+                           double* dEdC, double* dEdC_err, double* rhs_BQ, void* stream) {
+  if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
+  if (rhs_BQ && !s->has_S) return fail(VMCF_EINVAL, "rhs_BQ needs the AO overlap S at init");
+  const int L = s->accL, nb = wk->nblocks, nO = s->M * (s->nup + s->ndn);
+  std::vector<double> blk((size_t)nb * L);
+  int rc = vmcf_block_sums(s, wk, blk.data(), stream);
+  if (rc != VMCF_OK) return rc;
+  std::vector<double> Bv(nO);
+  rc = vmcf_finish_estimators(blk.data(), nb, s->K, s->M, s->nup, s->ndn, wk->e_ref, E, E_err, F, F_err,
+                              Bv.data(), dEdC_err);
+  if (rc != VMCF_OK) return rc;
+  if (dEdC) std::copy(Bv.begin(), Bv.end(), dEdC);
   if (rhs_BQ) {
     // Q^s = 1 - C^s C^s^T S (Eq. Q_projector); rhs_{nu i} = -sum_mu B_{mu i} Q_{mu nu}
     const int M = s->M;
@@ -888,8 +936,7 @@ int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double
           for (int mu = 0; mu < M; ++mu) v += C[(size_t)mu * n + k] * Bv[ooff + (size_t)mu * n + i];
           CtB[(size_t)k * n + i] = v;
         }
-      // sum_mu B_{mu i} (delta_{mu nu} - sum_k C_{mu k} (S C)_{nu k})
-      std::vector<double> SC((size_t)M * n, 0.0);
+      std::vector<double> SC((size_t)M * n, 0.0);  // (S C)_{nu k}
       for (int nu = 0; nu < M; ++nu)
         for (int k = 0; k < n; ++k) {
           double v = 0.0;

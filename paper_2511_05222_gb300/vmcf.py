@@ -82,6 +82,7 @@ def lib(build_if_missing: bool = True):
         L.vmcf_walkers_get_positions.argtypes = [_vp, _vp, ctypes.c_int, _vp]
         L.vmcf_reset_accumulators.argtypes = [_vp, ctypes.c_double, _vp]
         L.vmcf_sample.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp]
+        L.vmcf_measure.argtypes = [_vp, _vp, _vp]
         L.vmcf_evaluate.argtypes = [_vp, _vp, ctypes.c_int] + [_vp] * 6 + [_vp]
         L.vmcf_reduce_estimators.argtypes = [_vp, _vp] + [_dp] * 7 + [_vp]
         L.vmcf_block_sums.argtypes = [_vp, _vp, _dp, _vp]
@@ -199,6 +200,7 @@ class Walkers:
         self.h = out
         self.W = W
         self.nblocks = nblocks
+        self.e_ref = 0.0
 
     def close(self):
         if getattr(self, "h", None):
@@ -232,11 +234,16 @@ class Walkers:
 
     def reset_accumulators(self, e_ref: float, stream=None):
         _check(lib().vmcf_reset_accumulators(self.h, float(e_ref), _stream(stream)), "vmcf_reset_accumulators")
+        self.e_ref = float(e_ref)
 
     def sample(self, n_sweeps: int, step_sigma: float = 0.3, refresh_k: int = 26, measure: bool = False,
                stream=None):
         _check(lib().vmcf_sample(self.system.h, self.h, int(n_sweeps), float(step_sigma), int(refresh_k),
                                  int(bool(measure)), _stream(stream)), "vmcf_sample")
+
+    def measure(self, stream=None):
+        """vmcf_measure: accumulate one measurement of the current positions (no moves)."""
+        _check(lib().vmcf_measure(self.system.h, self.h, _stream(stream)), "vmcf_measure")
 
     def reduce_estimators(self, with_rhs: bool = False, stream=None) -> dict:
         s = self.system

@@ -185,3 +185,32 @@ def test_counters_and_singular_free_run(sys1):
     assert c["moves"] == 5 * 512 * sys1.Ne
     assert 0.2 < c["accepted"] / c["moves"] < 0.9
     assert c["singular"] == 0
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_mixed_estimators_within_a_tenth_of_their_error_bars(cfg):
+    """Mixed-precision sampling; the FP64 path measures the same configurations after every
+    sweep (paired). Every walker-averaged estimator (E, each force component, each dE/dC
+    element) of the mixed path lies within 0.1 x its own jackknife error bar of the FP64 one."""
+    sysx = S.make_system(cfg)
+    W = 4096
+    pos = S.initial_walkers(sysx, W, seed=12)
+    gm = vmcf.System(sysx, vmcf.MIXED)
+    g64 = vmcf.System(sysx, vmcf.FP64)
+    wm = vmcf.Walkers(gm, pos, key=(5222, cfg), nblocks=32)
+    wm.sample(20, measure=False)
+    w64 = vmcf.Walkers(g64, wm.positions(), key=(5222, cfg), nblocks=32)
+    e_ref = -76.0 if cfg == 0 else -150.0
+    wm.reset_accumulators(e_ref)
+    w64.reset_accumulators(e_ref)
+    for _ in range(6):
+        wm.sample(1, measure=True)
+        w64.set_positions(wm.positions())
+        w64.measure()
+    em, e64 = wm.reduce_estimators(), w64.reduce_estimators()
+    assert abs(em["E"] - e64["E"]) <= 0.1 * e64["E_err"], (em["E"], e64["E"], e64["E_err"])
+    dF = np.abs(em["F"] - e64["F"]) / e64["F_err"]
+    assert dF.max() <= 0.1, dF.max()
+    ok = e64["dEdC_err"] > 0
+    dB = np.abs(em["dEdC"] - e64["dEdC"])[ok] / e64["dEdC_err"][ok]
+    assert dB.max() <= 0.1, dB.max()
