@@ -203,7 +203,11 @@ int vmcf_evaluate_sums_noalloc(vmcf_system_t sys, const double* pos, int W, doub
  *   "move_lanes_per_walker": 1, 2, 4 or 8 lanes share one walker in the Metropolis kernel of
  *                            the small-system path (default 1);
  *   "measure_warps":         2, 4 or 8 walkers (one warp each) per CTA of the small-system
- *                            measurement kernel (default: the most that fit shared memory, up to 8).
+ *                            measurement kernel (default: the most that fit shared memory, up to 8);
+ *   "tensor_core_sums":      1: in mixed precision, the walker sums of O and (E_L - E_ref) O are
+ *                            one bf16 GEMM on the tensor cores (tcgen05, FP32 accumulation in
+ *                            tensor memory, FP64 across CTAs); 0: FP32 SIMT sums (default 1 where
+ *                            the AOs fit 128 rows and 2 n_up fits 32 columns).
  * Takes effect for walker sets created afterwards (measure_warps) or at the next call. */
 int vmcf_set_tuning(vmcf_system_t sys, const char* key, int value);
 
@@ -212,8 +216,8 @@ int vmcf_set_tuning(vmcf_system_t sys, const char* key, int value);
  * now on (enable != 0) or stop recording (0).
  * vmcf_kernel_times: synchronise on the recorded events and return the summed device time
  * in ms and the launch count per kernel kind: [0] Metropolis sweep kernel, [1] measurement
- * kernel, [2] refresh kernel (host arrays of 3; either may be NULL); reset != 0 zeroes the
- * totals afterwards.
+ * kernel, [2] refresh kernel, [3] tensor-core walker-sum kernel (host arrays of 4; either may
+ * be NULL); reset != 0 zeroes the totals afterwards.
  * vmcf_probe_pipes: measure this GPU's FP64 FMA and FP32 FMA throughput (TFLOP/s) and FP32
  * expf throughput (G/s) with short register-only kernels on `stream` (synchronises; about
  * 30 ms). Used as the measured ALU peaks of the roofline. */

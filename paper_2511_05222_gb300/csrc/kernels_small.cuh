@@ -12,6 +12,8 @@
 // Walker state on this path: positions [3 Ne][W] (double, plus a float-float copy in mixed
 // mode) and inverses [n_up^2 + n_dn^2][W], walker index fastest.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "vmcf_device.cuh"
 #include "vmcf_internal.h"
 
@@ -361,6 +363,8 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
   const int Ne = S.Ne, nup = S.nup, ndn = S.ndn, K = S.K, M = S.M, W = P.W;
   const int nO = M * Ne;
   const bool accum = P.mode == 2;
+  // mixed-mode walker sums of O through the tensor-core kernel: emit PhiT and YT tiles
+  const bool tc = accum && sizeof(T) == 4 && P.phiT[0] != nullptr;
   stage_C<T, NM>(S, Cs);
   if (accum)
     for (int i = threadIdx.x; i < P.accL; i += blockDim.x) acc_s[i] = T(0);
@@ -595,6 +599,11 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
     // O^s[mu][i] = sum over electrons e of spin s of psi_mu(r_e) B_{i, el(e)}; lanes 0..15 take
     // spin up, 16..31 spin down, one orbital i each.
     auto flush_chunk = [&]() {
+      if (tc) {
+        chunk0 += chunk_n;
+        chunk_n = 0;
+        return;
+      }
       __syncwarp();
       const int g = lane >> 4, i = lane & 15;
       const int ng = g == 0 ? nup : ndn, og = g == 0 ? 0 : nup * nup, e0 = g == 0 ? 0 : nup;
@@ -655,13 +664,26 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
             fl[k] -= gv * yL;
             fe[k] += T(-0.5) * (gv * yA - yL * (gl + T(2) * hj));
           }
-          phi[e * L.chunk + chunk_n + m] = Pa * rs.R0;
+          if (tc)
+            reinterpret_cast<__nv_bfloat16*>(P.phiT[sg])[((size_t)w * P.Mp + sh.w + m) * 16 + el] =
+                __float2bfloat16_rn((float)(Pa * rs.R0));
+          else
+            phi[e * L.chunk + chunk_n + m] = Pa * rs.R0;
         }
       }
       chunk_n += ncomp;
     }
     if (cur >= 0) flush_centre(cur);
     flush_chunk();
+    if (tc && has_e) {  // Y rows: B_{i, el} and (E_L - E_ref) B_{i, el}
+      __nv_bfloat16* y = reinterpret_cast<__nv_bfloat16*>(P.yT[sg]) + (size_t)w * P.Np * 16;
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+        if (i < n) {
+          y[i * 16 + el] = __float2bfloat16_rn((float)bc[i]);
+          y[(n + i) * 16 + el] = __float2bfloat16_rn((float)((T)cw * bc[i]));
+        }
+    }
     // e-n Jastrow and V_en derivatives, one nucleus at a time
     for (int I = 0; I < K; ++I) {
       T c6[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};

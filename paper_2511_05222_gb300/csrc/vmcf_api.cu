@@ -192,6 +192,9 @@ void plan_small(vmcf_system_s& s) {
   s.small_move_smem = (size_t)tsz * 2 * s.M * s.small_nm;
   if (s.small_move_smem > (size_t)kSmemCap) return;
   s.small = true;
+  s.tc_Mp = (s.M + 7) / 8 * 8;
+  s.tc_Np = (2 * s.nmax + 15) / 16 * 16;
+  s.tc_sums = s.precision == VMCF_MIXED && s.tc_Mp <= 128 && s.tc_Np <= 32;
 }
 
 Launch launch_rm(const vmcf_system_s& s, int W) {
@@ -300,6 +303,62 @@ int load_positions_state(vmcf_system_s* s, vmcf_walkers_s* wk, const double* pos
   }
   VMCF_CUDA(cudaMemcpyAsync(wk->stage, pos, bytes, kind, st));
   VMCF_CUDA(launch_to_interleaved(wk->stage, wk->pos, wk->posf, wk->W, 3 * s->Ne, st));
+  return VMCF_OK;
+}
+
+// Tensor-core walker sums: bf16 tiles (zero-filled: electron slots beyond n and Y columns
+// beyond 2n are never written and must stay zero), FP64 slots and an error flag.
+cudaError_t alloc_tc(vmcf_system_s* s, vmcf_walkers_s* wk) {
+  const size_t W = wk->W;
+  wk->tc_cpb = std::max(1, (int)(W / ((size_t)wk->nblocks * 64)));
+  const size_t nslot = 2 * (size_t)wk->nblocks * wk->tc_cpb * s->tc_Mp * s->tc_Np;
+  cudaError_t e;
+  for (int k = 0; k < 2; ++k) {
+    if ((e = cudaMalloc(&wk->phiT[k], 2 * W * s->tc_Mp * 16))) return e;
+    if ((e = cudaMalloc(&wk->yT[k], 2 * W * s->tc_Np * 16))) return e;
+    if ((e = cudaMemset(wk->phiT[k], 0, 2 * W * s->tc_Mp * 16))) return e;
+    if ((e = cudaMemset(wk->yT[k], 0, 2 * W * s->tc_Np * 16))) return e;
+  }
+  if ((e = cudaMalloc(&wk->tc_slots, 8 * nslot))) return e;
+  if ((e = cudaMemset(wk->tc_slots, 0, 8 * nslot))) return e;
+  if ((e = cudaMalloc(&wk->tc_flag, sizeof(int)))) return e;
+  if ((e = cudaMemset(wk->tc_flag, 0, sizeof(int)))) return e;
+  wk->tc = true;
+  return cudaSuccess;
+}
+
+// One measurement of the walker state: the small-path kernel, and in tensor-core mode the
+// walker-sum GEMM over the tiles it wrote.
+int measure_state_small(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
+  SmallMeasParams M = small_params(*s, wk->W);
+  M.pos = wk->pos;
+  M.pos_sk = wk->W;
+  M.pos_sw = 1;
+  M.mode = 2;
+  M.Bout = wk->B;
+  M.acc = wk->acc;
+  M.e_ref = wk->e_ref;
+  M.counters = wk->counters;
+  const bool tc = wk->tc && s->tc_sums;
+  if (tc) {
+    for (int k = 0; k < 2; ++k) {
+      M.phiT[k] = wk->phiT[k];
+      M.yT[k] = wk->yT[k];
+    }
+    M.Mp = s->tc_Mp;
+    M.Np = s->tc_Np;
+  }
+  {
+    Timed tm(wk, 1, st);
+    int rc = launch_small_measure(s, wk->grid_meas, M, st);
+    if (rc != VMCF_OK) return rc;
+  }
+  if (tc) {
+    Timed tm(wk, 3, st);
+    cudaError_t e = launch_tc_sumprod(wk->phiT[0], wk->phiT[1], wk->yT[0], wk->yT[1], wk->W, s->tc_Mp, s->tc_Np, s->nup,
+                                      s->ndn, wk->nblocks * wk->tc_cpb, wk->tc_slots, wk->tc_flag, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core walker-sum kernel launch");
+  }
   return VMCF_OK;
 }
 
@@ -581,7 +640,8 @@ int vmcf_walkers_create(vmcf_system_t s, int W, const double* pos, int is_host, 
       (e = cudaMalloc(&wk->acc, 8 * (size_t)wk->grid_meas * s->accL)) ||
       (e = cudaMalloc(&wk->blocks, 8 * (size_t)nblocks * s->accL)) ||
       (s->small && (e = cudaMalloc(&wk->stage, 8 * npos))) ||
-      (s->small && s->precision == VMCF_MIXED && (e = cudaMalloc(&wk->posf, sizeof(float2) * npos)))) {
+      (s->small && s->precision == VMCF_MIXED && (e = cudaMalloc(&wk->posf, sizeof(float2) * npos))) ||
+      (s->small && s->tc_sums && (e = alloc_tc(s, wk)))) {
     vmcf_walkers_destroy(wk);
     return fail(VMCF_ENOMEM, std::string("walker state allocation: ") + cudaGetErrorString(e));
   }
@@ -620,6 +680,12 @@ int vmcf_walkers_destroy(vmcf_walkers_t wk) {
   cudaFree(wk->blocks);
   cudaFree(wk->stage);
   cudaFree(wk->posf);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(wk->phiT[k]);
+    cudaFree(wk->yT[k]);
+  }
+  cudaFree(wk->tc_slots);
+  cudaFree(wk->tc_flag);
   delete wk;
   return VMCF_OK;
 }
@@ -651,6 +717,9 @@ int vmcf_reset_accumulators(vmcf_walkers_t wk, double e_ref, void* stream) {
   if (!wk || !std::isfinite(e_ref)) return fail(VMCF_EINVAL, "bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   VMCF_CUDA(cudaMemsetAsync(wk->acc, 0, 8 * (size_t)wk->grid_meas * wk->sys->accL, st));
+  if (wk->tc)
+    VMCF_CUDA(cudaMemsetAsync(wk->tc_slots, 0,
+                              8 * 2 * (size_t)wk->nblocks * wk->tc_cpb * wk->sys->tc_Mp * wk->sys->tc_Np, st));
   wk->e_ref = e_ref;
   wk->measured = 0;
   return VMCF_OK;
@@ -710,8 +779,7 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
       }
       wk->sweep += 1;
       if (measure) {
-        Timed tm(wk, 1, st);
-        int rc = launch_small_measure(s, wk->grid_meas, M, st);
+        int rc = measure_state_small(s, wk, st);
         if (rc != VMCF_OK) return rc;
         wk->counter = 0;
         wk->measured += 1;
@@ -775,17 +843,7 @@ int vmcf_measure(vmcf_system_t s, vmcf_walkers_t wk, void* stream) {
   if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (s->small) {
-    SmallMeasParams M = small_params(*s, wk->W);
-    M.pos = wk->pos;
-    M.pos_sk = wk->W;
-    M.pos_sw = 1;
-    M.mode = 2;
-    M.Bout = wk->B;
-    M.acc = wk->acc;
-    M.e_ref = wk->e_ref;
-    M.counters = wk->counters;
-    Timed tm(wk, 1, st);
-    int rc = launch_small_measure(s, wk->grid_meas, M, st);
+    int rc = measure_state_small(s, wk, st);
     if (rc != VMCF_OK) return rc;
   } else {
     MeasParams M{};
@@ -853,6 +911,16 @@ int vmcf_block_sums(vmcf_system_t s, vmcf_walkers_t wk, double* out, void* strea
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = launch_block_reduce(wk->acc, wk->grid_meas, wk->cpb, s->accL, wk->blocks, wk->nblocks, st);
   if (e != cudaSuccess) return cuda_fail(e, "block reduce launch");
+  if (wk->tc) {
+    const int nO = s->M * (s->nup + s->ndn);
+    e = launch_tc_fold(wk->tc_slots, wk->nblocks, wk->tc_cpb, s->tc_Mp, s->tc_Np, s->M, s->nup, s->ndn, 3 + 9 * s->K, nO,
+                       s->accL, wk->blocks, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core fold launch");
+    int flag = 0;
+    VMCF_CUDA(cudaMemcpyAsync(&flag, wk->tc_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VMCF_CUDA(cudaStreamSynchronize(st));
+    if (flag) return fail(VMCF_ETIMEOUT, "tensor-core walker-sum kernel: a bounded wait timed out");
+  }
   VMCF_CUDA(cudaMemcpyAsync(out, wk->blocks, 8 * (size_t)wk->nblocks * s->accL, cudaMemcpyDeviceToHost, st));
   VMCF_CUDA(cudaStreamSynchronize(st));
   return VMCF_OK;
@@ -963,6 +1031,13 @@ int vmcf_set_tuning(vmcf_system_t s, const char* key, int value) {
     s->move_lpw = value;
     return VMCF_OK;
   }
+  if (k == "tensor_core_sums") {
+    const bool want = value != 0;
+    if (want && !(s->small && s->precision == VMCF_MIXED && s->tc_Mp <= 128 && s->tc_Np <= 32))
+      return fail(VMCF_EINVAL, "tensor-core walker sums need the mixed small-system path, M <= 128, 2n <= 32");
+    s->tc_sums = want;
+    return VMCF_OK;
+  }
   if (k == "measure_warps") {
     if (!s->small || (value != 2 && value != 4 && value != 8)) return fail(VMCF_EINVAL, "measure warps: 2, 4 or 8");
     if (s->SL.cta_bytes + value * s->SL.bytes > kSmemCap) return fail(VMCF_EINVAL, "does not fit shared memory");
@@ -990,7 +1065,7 @@ int vmcf_kernel_times(vmcf_walkers_t wk, double* ms, long long* count, int reset
     cudaEventDestroy(ev.second.second);
   }
   wk->events.clear();
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     if (ms) ms[k] = wk->kernel_ms[k];
     if (count) count[k] = wk->kernel_n[k];
     if (reset) {

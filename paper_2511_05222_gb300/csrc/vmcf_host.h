@@ -33,6 +33,8 @@ struct vmcf_system_s {
   vmcf::SmallLayout SL{};
   size_t small_move_smem = 0;  // C staging of the move kernel
   int move_lpw = 1;            // lanes per walker in the move kernel (1, 2, 4 or 8)
+  bool tc_sums = false;        // mixed small path: walker sums of O on the tensor cores
+  int tc_Mp = 0, tc_Np = 0;    // padded AO rows and Y columns of those tiles
 };
 
 struct vmcf_walkers_s {
@@ -51,12 +53,18 @@ struct vmcf_walkers_s {
   double e_ref = 0.0;
   // small-system path state: positions and inverses walker-interleaved
   float2* posf = nullptr;   // float-float positions (mixed mode)
+  void* phiT[2] = {nullptr, nullptr};  // tensor-core walker sums: [W][Mp][16] bf16 per spin
+  void* yT[2] = {nullptr, nullptr};    // [W][Np][16] bf16 per spin
+  double* tc_slots = nullptr;          // [2][nblocks * tc_cpb][Mp][Np]
+  int* tc_flag = nullptr;
+  int tc_cpb = 1;
+  bool tc = false;
   double* stage = nullptr;  // [W][Ne][3] staging for layout conversion
   // per-kernel timing (kind 0 move, 1 measure, 2 refresh): event pairs around launches
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
-  double kernel_ms[3] = {0, 0, 0};
-  long long kernel_n[3] = {0, 0, 0};
+  double kernel_ms[4] = {0, 0, 0, 0};  // move, measure, refresh, tensor-core walker sums
+  long long kernel_n[4] = {0, 0, 0, 0};
 };
 
 

@@ -86,6 +86,9 @@ struct SmallMeasParams {
   float2* posf_out;     // float-float positions [3 Ne][W] to refresh (mixed, refresh mode) or NULL
   double *EL, *logpsi, *dlnpsi, *dEL, *O;  // evaluate-mode outputs (any may be NULL)
   double* acc;          // [grid][accL] FP64 slots (accumulate mode)
+  void* phiT[2];        // tensor-core walker sums (mixed accumulate mode): [W][Mp][16] bf16 per spin, or NULL
+  void* yT[2];          // [W][Np][16] bf16 per spin
+  int Mp, Np;
   int accL;
   double e_ref;
   unsigned long long* counters;
@@ -102,6 +105,12 @@ template <typename T>
 cudaError_t set_smem_limits_small();
 cudaError_t launch_to_interleaved(const double* src, double* dst, float2* dstf, int W, int n3, cudaStream_t st);
 cudaError_t launch_from_interleaved(const double* src, double* dst, int W, int n3, cudaStream_t st);
+
+cudaError_t launch_tc_sumprod(const void* phiT_up, const void* phiT_dn, const void* yT_up, const void* yT_dn, int W,
+                              int Mp, int Np, int n_up, int n_dn, int grid_x, double* slots, int* flag,
+                              cudaStream_t st);
+cudaError_t launch_tc_fold(const double* slots, int nblocks, int cpb, int Mp, int Np, int M, int n_up, int n_dn,
+                           int oo, int nO, int accL, double* blocks, cudaStream_t st);
 
 cudaError_t run_probes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, cudaStream_t st);
 

@@ -270,11 +270,11 @@ class Walkers:
         _check(lib().vmcf_profile(self.h, int(enable)), "vmcf_profile")
 
     def kernel_times(self, reset: bool = True) -> dict:
-        ms = (ctypes.c_double * 3)()
-        n = (ctypes.c_longlong * 3)()
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_longlong * 4)()
         _check(lib().vmcf_kernel_times(self.h, ms, n, int(reset)), "vmcf_kernel_times")
-        names = ("move", "measure", "refresh")
-        return {names[k]: {"ms": float(ms[k]), "launches": int(n[k])} for k in range(3)}
+        names = ("move", "measure", "refresh", "tc_sums")
+        return {names[k]: {"ms": float(ms[k]), "launches": int(n[k])} for k in range(4)}
 
     def counters(self, stream=None) -> dict:
         c = Counters()

@@ -214,3 +214,31 @@ def test_mixed_estimators_within_a_tenth_of_their_error_bars(cfg):
     ok = e64["dEdC_err"] > 0
     dB = np.abs(em["dEdC"] - e64["dEdC"])[ok] / e64["dEdC_err"][ok]
     assert dB.max() <= 0.1, dB.max()
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_tensor_core_walker_sums_match_simt(cfg):
+    """The tcgen05 GEMM that forms sum_w O_w and sum_w (E_L - E_ref) O_w (bf16 operands, FP32
+    accumulation) against the FP32 SIMT sums of the same kernel, on the same configurations."""
+    sysx = S.make_system(cfg)
+    W = 2048
+    o = oracle.Oracle(sysx)
+    st = o.new_state(S.initial_walkers(sysx, W, seed=21), key=(5222, 3))
+    o.sample(st, 10)
+    out = {}
+    for tc in (1, 0):
+        g = vmcf.System(sysx, vmcf.MIXED)
+        g.set_tuning("tensor_core_sums", tc)
+        wk = vmcf.Walkers(g, st["pos"], nblocks=16)
+        wk.reset_accumulators(-70.0 if cfg == 0 else -150.0)
+        wk.measure()
+        out[tc] = wk.block_sums()
+    K3, nO = 3 * sysx.K, sysx.M * sysx.Ne
+    oo = 3 + 3 * K3
+    a, b = out[1], out[0]
+    np.testing.assert_array_equal(a[:, 0], b[:, 0])
+    assert rel(a[:, :oo], b[:, :oo]) < 1e-6
+    for sec in (slice(oo, oo + nO), slice(oo + nO, oo + 2 * nO)):
+        assert rel(a[:, sec], b[:, sec]) < 1e-2, rel(a[:, sec], b[:, sec])
+        # per-element agreement well beyond chance: correlation of the two sum vectors
+        assert np.corrcoef(a[:, sec].ravel(), b[:, sec].ravel())[0, 1] > 0.9999
