@@ -251,7 +251,7 @@ def main():
     est = wk.reduce_estimators(stream=stream)
 
     work = workmodel.per_walker_eval(sysx.K, g.M, sysx.n_up, sysx.n_dn, int(sysx.shell_nprim.sum()), acc)
-    dom = max(("move", "measure"), key=lambda k: kt[k]["ms"])
+    dom = max(("move", "measure"), key=lambda k: kt[k]["ms"])  # the tensor-core sums take ~2%
     t_launch = kt[dom]["ms"] / max(1, kt[dom]["launches"]) * 1e-3
     bound, t_roof_w = workmodel.roofline_time(work[dom], peaks)
     pipe_flops = {"fp32": work[dom]["fp32"], "fp64": work[dom]["fp64"], "sfu": work[dom]["exp"]}[bound]
@@ -270,7 +270,7 @@ def main():
             "config": {"workload": wl["name"], "walkers_per_gpu": W, "electrons": sysx.Ne, "aos": g.M,
                        "step_sigma": 0.3, "refresh_every": 26, "precision": "mixed (FP32 + FP64 inverse/ratio/sums)",
                        "l2": "flushed (256 MB write) between timed steps"},
-            "roofline": roofline, "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
+            "roofline": roofline, "gpu_launches": sum(v["launches"] for v in kt.values()), "clocks": clk.summary(),
             "acceptance": acc, "estimates": {"E": est["E"], "E_err": est["E_err"]}}
 
     # ---- FP64 GPU path on the same workload

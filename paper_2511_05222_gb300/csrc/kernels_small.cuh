@@ -157,18 +157,27 @@ __device__ __forceinline__ V lane_group_sum(V v, unsigned mask) {
 template <typename T, int NM, int LPW>
 __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
+  // shared memory: C^up, C^dn [2][M][NM], then the CTA's inverses walker-interleaved [nB][WPC]
   T* Cs = reinterpret_cast<T*>(smem);
+  const int WPC = blockDim.x / LPW;
+  T* Bs = Cs + 2 * S.M * NM;
   stage_C<T, NM>(S, Cs);
+  const int W = P.W, Ne = S.Ne, nup = S.nup, K = S.K, nB = S.nB;
+  const int wbase = blockIdx.x * WPC;
+  T* Bg = reinterpret_cast<T*>(P.B);
+  for (int idx = threadIdx.x; idx < nB * WPC; idx += blockDim.x) {
+    const int k = idx / WPC, ws = idx - k * WPC;
+    if (wbase + ws < W) Bs[idx] = Bg[(size_t)k * W + wbase + ws];
+  }
   __syncthreads();
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int w = gtid / LPW, q = gtid % LPW;
+  const int w = gtid / LPW, q = gtid % LPW, ws = w - wbase;
   // whole lane groups leave together (LPW divides 32)
   if (w >= P.W) return;
   // lanes of this walker only: barriers inside the accept branch must not wait for other
   // walkers' lanes, which take their own branch
   const unsigned mask = (LPW == 32) ? 0xffffffffu : (((1u << LPW) - 1u) << ((threadIdx.x & 31) & ~(LPW - 1)));
-  const int W = P.W, Ne = S.Ne, nup = S.nup, K = S.K;
-  T* B = reinterpret_cast<T*>(P.B);
+  T* B = Bs + ws;  // element k of this walker's inverses at B[k * WPC]
   const uint64_t wid = P.wid0 + (uint64_t)w;
   uint32_t nacc = 0, nrej = 0;
   for (int mv = 0; mv < P.nmoves; ++mv) {
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
     double R = 0.0;
 #pragma unroll
     for (int i = 0; i < NM; ++i)
-      if (i % LPW == q && i < n) R += (double)row[i] * (double)B[(size_t)(off + i * n + el) * W + w];
+      if (i % LPW == q && i < n) R += (double)row[i] * (double)B[(off + i * n + el) * WPC];
     R = lane_group_sum<LPW>(R, mask);
     // Jastrow ratio: this lane's partners j = q, q + LPW, ... and nuclei I = q, q + LPW, ...
     T jacc = 0;
@@ -280,7 +289,7 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
 #pragma unroll
       for (int j = 0; j < NM; ++j) {
         wv[j] = T(0);
-        col[j] = (j < n) ? B[(size_t)(off + j * n + el) * W + w] : T(0);
+        col[j] = (j < n) ? B[(off + j * n + el) * WPC] : T(0);
       }
 #pragma unroll
       for (int i = 0; i < NM; ++i) {
@@ -288,7 +297,7 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
         const T ri = row[i];
 #pragma unroll
         for (int j = 0; j < NM; ++j)
-          if (j % LPW == q && j < n) wv[j] += ri * B[(size_t)(off + i * n + j) * W + w];
+          if (j % LPW == q && j < n) wv[j] += ri * B[(off + i * n + j) * WPC];
       }
       if (LPW > 1) __syncwarp(mask);  // column el is read by all lanes before its owner rewrites it
       const T rinv = (T)(1.0 / R);
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
           if (k >= n) continue;
-          T& bkj = B[(size_t)(off + k * n + j) * W + w];
+          T& bkj = B[(off + k * n + j) * WPC];
           bkj -= col[k] * rinv * wj;
         }
       }
@@ -318,6 +327,9 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
     P.nacc[w] += nacc;
     P.nrej[w] += nrej;
   }
+  // this walker's inverses back to global memory (its lanes share the copy)
+  if (LPW > 1) __syncwarp(mask);
+  for (int k = q; k < nB; k += LPW) Bg[(size_t)k * W + w] = B[k * WPC];
 }
 
 // ---------------------------------------------------------------- measurement, one warp per walker
@@ -802,7 +814,8 @@ static __global__ void from_interleaved(const double* __restrict__ src, double* 
 template <typename T, int NM>
 cudaError_t launch_move_small_lpw(int lpw, const DevSys& S, int W, size_t smem, const SmallMoveParams& P,
                                   cudaStream_t st) {
-  const int threads = 64;
+  const int threads = 32 * lpw;  // 32 walkers per CTA
+  smem += sizeof(T) * (size_t)S.nB * 32;
   const long long lanes = (long long)W * lpw;
   const dim3 grid((unsigned)((lanes + threads - 1) / threads));
   switch (lpw) {
