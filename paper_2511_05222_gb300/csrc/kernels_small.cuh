@@ -14,6 +14,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "vmcf_device.cuh"
 #include "vmcf_internal.h"
 
@@ -157,10 +159,13 @@ __device__ __forceinline__ V lane_group_sum(V v, unsigned mask) {
 template <typename T, int NM, int LPW>
 __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // shared memory: C^up, C^dn [2][M][NM], then the CTA's inverses walker-interleaved [nB][WPC]
+  // shared memory: C^up, C^dn [2][M][NM]; the CTA's inverses walker-interleaved [nB][WPC]; its
+  // positions [3 Ne][WPC] (float-float pairs in mixed mode, double in FP64 mode)
   T* Cs = reinterpret_cast<T*>(smem);
-  const int WPC = blockDim.x / LPW;
+  const int WPC = P.wpc;
   T* Bs = Cs + 2 * S.M * NM;
+  using PosT = typename std::conditional<sizeof(T) == 4, float2, double>::type;
+  PosT* Ps = reinterpret_cast<PosT*>(Bs + (size_t)S.nB * WPC);
   stage_C<T, NM>(S, Cs);
   const int W = P.W, Ne = S.Ne, nup = S.nup, K = S.K, nB = S.nB;
   const int wbase = blockIdx.x * WPC;
@@ -169,15 +174,28 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
     const int k = idx / WPC, ws = idx - k * WPC;
     if (wbase + ws < W) Bs[idx] = Bg[(size_t)k * W + wbase + ws];
   }
+  for (int idx = threadIdx.x; idx < 3 * Ne * WPC; idx += blockDim.x) {
+    const int k = idx / WPC, ws = idx - k * WPC;
+    if (wbase + ws < W) {
+      const double v = P.pos[(size_t)k * W + wbase + ws];
+      if constexpr (sizeof(T) == 4) {
+        float h, l;
+        split_ff(v, h, l);
+        Ps[idx] = make_float2(h, l);
+      } else {
+        Ps[idx] = v;
+      }
+    }
+  }
   __syncthreads();
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int w = gtid / LPW, q = gtid % LPW, ws = w - wbase;
+  const int ws = threadIdx.x / LPW, q = threadIdx.x % LPW, w = wbase + ws;
   // whole lane groups leave together (LPW divides 32)
-  if (w >= P.W) return;
+  if (ws >= WPC || w >= P.W) return;
   // lanes of this walker only: barriers inside the accept branch must not wait for other
   // walkers' lanes, which take their own branch
   const unsigned mask = (LPW == 32) ? 0xffffffffu : (((1u << LPW) - 1u) << ((threadIdx.x & 31) & ~(LPW - 1)));
-  T* B = Bs + ws;  // element k of this walker's inverses at B[k * WPC]
+  T* B = Bs + ws;     // element k of this walker's inverses at B[k * WPC]
+  PosT* pp = Ps + ws;  // coordinate k of this walker's electrons at pp[k * WPC]
   const uint64_t wid = P.wid0 + (uint64_t)w;
   uint32_t nacc = 0, nrej = 0;
   for (int mv = 0; mv < P.nmoves; ++mv) {
@@ -200,7 +218,7 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
       rn[k] = po[k] + P.sigma * xi[k];
       split_ff(rn[k], nh[k], nl[k]);
       if constexpr (sizeof(T) == 4) {
-        const float2 f = P.posf[(size_t)(3 * e + k) * W + w];
+        const float2 f = pp[(3 * e + k) * WPC];
         oh[k] = f.x;
         ol[k] = f.y;
       }
@@ -246,11 +264,11 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           if constexpr (sizeof(T) == 8) {
-            const double pj = P.pos[(size_t)(3 * j + k) * W + w];
+            const double pj = pp[(3 * j + k) * WPC];
             d1[k] = rn[k] - pj;
             d0[k] = po[k] - pj;
           } else {
-            const float2 f = P.posf[(size_t)(3 * j + k) * W + w];
+            const float2 f = pp[(3 * j + k) * WPC];
             d1[k] = (nh[k] - f.x) + (nl[k] - f.y);
             d0[k] = (oh[k] - f.x) + (ol[k] - f.y);
           }
@@ -316,7 +334,8 @@ __global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           P.pos[(size_t)(3 * e + k) * W + w] = rn[k];
-          if constexpr (sizeof(T) == 4) P.posf[(size_t)(3 * e + k) * W + w] = make_float2(nh[k], nl[k]);
+          if constexpr (sizeof(T) == 4) pp[(3 * e + k) * WPC] = make_float2(nh[k], nl[k]);
+          else pp[(3 * e + k) * WPC] = rn[k];
         }
       }
       ++nacc;
@@ -814,10 +833,9 @@ static __global__ void from_interleaved(const double* __restrict__ src, double* 
 template <typename T, int NM>
 cudaError_t launch_move_small_lpw(int lpw, const DevSys& S, int W, size_t smem, const SmallMoveParams& P,
                                   cudaStream_t st) {
-  const int threads = 32 * lpw;  // 32 walkers per CTA
-  smem += sizeof(T) * (size_t)S.nB * 32;
-  const long long lanes = (long long)W * lpw;
-  const dim3 grid((unsigned)((lanes + threads - 1) / threads));
+  const int threads = (P.wpc * lpw + 31) / 32 * 32;
+  smem += (sizeof(T) * (size_t)S.nB + (sizeof(T) == 4 ? 8 : 8) * (size_t)(3 * S.Ne)) * P.wpc;
+  const dim3 grid((unsigned)((W + P.wpc - 1) / P.wpc));
   switch (lpw) {
     case 1: move_small<T, NM, 1><<<grid, threads, smem, st>>>(S, P); break;
     case 2: move_small<T, NM, 2><<<grid, threads, smem, st>>>(S, P); break;

@@ -265,6 +265,17 @@ int launch_small_measure(vmcf_system_s* s, int grid, const SmallMeasParams& P, c
   return VMCF_OK;
 }
 
+// Walkers per CTA of the move kernel: one CTA per SM when the walkers, their inverses and
+// positions fit shared memory, else as many as fit.
+int move_walkers_per_cta(const vmcf_system_s& s, int W) {
+  const size_t tsz = s.precision == VMCF_FP64 ? 8 : 4;
+  const size_t per = tsz * s.nB + 8 * 3 * (size_t)s.Ne;
+  const size_t room = (size_t)kSmemCap - s.small_move_smem;
+  int cap = (int)std::min<size_t>(room / per, (size_t)(1024 / s.move_lpw));
+  int want = (W + s.small_sms - 1) / s.small_sms;
+  return std::max(1, std::min(cap, want));
+}
+
 int eval_grid(const vmcf_system_s& s, int W) { return std::max(1, (W + 2 * s.small_warps - 1) / (2 * s.small_warps)); }
 
 // Fresh inverses from the current positions.
@@ -546,6 +557,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
     const int by_smem = (int)((228 * 1024) / (cta + 1024));
     const int by_regs = 65536 / (32 * s->small_warps * 128);
     s->small_res = std::max(1, sms * std::max(1, std::min(by_smem, by_regs)));
+    s->small_sms = std::max(1, sms);
   }
   if (ce != cudaSuccess) {
     cudaFree(s->dmem);
@@ -744,6 +756,7 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
     P.k0 = wk->k0;
     P.k1 = wk->k1;
     P.sigma = step_sigma;
+    P.wpc = move_walkers_per_cta(*s, wk->W);
     SmallMeasParams M = small_params(*s, wk->W);
     M.pos = wk->pos;
     M.pos_sk = wk->W;

@@ -30,6 +30,7 @@ struct vmcf_system_s {
   int small_nm = 16;          // register row width: 8 or 16
   int small_warps = 8;        // warps per CTA of the measurement kernel
   int small_res = 1;          // resident measurement CTAs on the device
+  int small_sms = 1;          // SMs on the device
   vmcf::SmallLayout SL{};
   size_t small_move_smem = 0;  // C staging of the move kernel
   int move_lpw = 1;            // lanes per walker in the move kernel (1, 2, 4 or 8)

@@ -68,6 +68,7 @@ struct SmallMoveParams {
   uint64_t wid0, k0, k1;
   uint64_t move0;  // global index of the first move: sweep = move0 / Ne, electron = move0 % Ne
   int nmoves;
+  int wpc;         // walkers per CTA
   double sigma;
 };
 
