@@ -201,7 +201,7 @@ int vmcf_evaluate_sums_noalloc(vmcf_system_t sys, const double* pos, int W, doub
 
 /* Launch-shape knobs of a system (not part of the paper's method; results are unchanged):
  *   "move_lanes_per_walker": 1, 2, 4 or 8 lanes share one walker in the Metropolis kernel of
- *                            the small-system path (default 1);
+ *                            the small-system path (default 2);
  *   "measure_warps":         2, 4 or 8 walkers (one warp each) per CTA of the small-system
  *                            measurement kernel (default: the most that fit shared memory, up to 8);
  *   "tensor_core_sums":      1: in mixed precision, the walker sums of O and (E_L - E_ref) O are

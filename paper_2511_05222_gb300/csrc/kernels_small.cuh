@@ -157,7 +157,7 @@ __device__ __forceinline__ V lane_group_sum(V v, unsigned mask) {
 // terms, Jastrow pairs and Sherman-Morrison columns are split across them and combined with
 // butterfly sums, so the accept decision is identical in all of a walker's lanes.
 template <typename T, int NM, int LPW>
-__global__ void __launch_bounds__(128) move_small(DevSys S, SmallMoveParams P) {
+__global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   // shared memory: C^up, C^dn [2][M][NM]; the CTA's inverses walker-interleaved [nB][WPC]; its
   // positions [3 Ne][WPC] (float-float pairs in mixed mode, double in FP64 mode)

@@ -271,7 +271,7 @@ int move_walkers_per_cta(const vmcf_system_s& s, int W) {
   const size_t tsz = s.precision == VMCF_FP64 ? 8 : 4;
   const size_t per = tsz * s.nB + 8 * 3 * (size_t)s.Ne;
   const size_t room = (size_t)kSmemCap - s.small_move_smem;
-  int cap = (int)std::min<size_t>(room / per, (size_t)(1024 / s.move_lpw));
+  int cap = (int)std::min<size_t>(room / per, (size_t)(256 / s.move_lpw));  // 256 threads per CTA at most
   int want = (W + s.small_sms - 1) / s.small_sms;
   return std::max(1, std::min(cap, want));
 }
