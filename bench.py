@@ -125,6 +125,35 @@ def oracle_steps(sysx, walkers: int, budget_s: float, max_s: float, key=(5222, 1
     return walkers * steps / sum(per), steps, sum(per)
 
 
+ROOT = os.path.dirname(os.path.abspath(__file__))
+
+
+def measure_source_sha1() -> str:
+    """Hash of the measurement kernel's source (its function text and the shared device header)."""
+    import hashlib
+    ks = open(os.path.join(ROOT, "paper_2511_05222_gb300/csrc/kernels_small.cuh")).read()
+    a = ks.index("__global__ void __launch_bounds__(256, 2) measure_small(")
+    b = ks.index("// Layout conversion between the ABI")
+    dev = open(os.path.join(ROOT, "paper_2511_05222_gb300/csrc/vmcf_device.cuh")).read()
+    return hashlib.sha1((ks[a:b] + dev).encode()).hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the measurement kernel from the committed ncu summary, or None
+    when the kernel source changed since it was captured."""
+    try:
+        txt = open(os.path.join(ROOT, "profiles/measure_small_c2oh6.md")).read()
+    except OSError:
+        return None
+    import re
+    m = re.search(r"source-sha1: ([0-9a-f]+)", txt)
+    r = re.search(r"\| DRAM read \| ([0-9.]+) Mbyte", txt)
+    w = re.search(r"\| DRAM write \| ([0-9.]+) (K|M)byte", txt)
+    if not (m and r and w) or m.group(1) != measure_source_sha1():
+        return None
+    return float(r.group(1)) * 1e6 + float(w.group(1)) * (1e3 if w.group(2) == "K" else 1e6)
+
+
 def cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -230,10 +259,9 @@ def main():
         g = vmcf.System(sysx, precision)
         wk = vmcf.Walkers(g, pos0, key=(5222, 1), wid0=rank * W, nblocks=nb, stream=stream)
         wk.sample(args.equil, 0.3, 26, measure=False, stream=stream)
-        p = torch.empty((W, sysx.Ne, 3), dtype=torch.float64, device=dev)
-        wk.positions_into(p, stream=stream)
-        el = vmcf.vmcf_evaluate(g, p, want=("EL",), stream=stream)["EL"]
-        wk.reset_accumulators(float(el.mean().item()), stream=stream)
+        wk.reset_accumulators(0.0, stream=stream)
+        wk.measure(stream=stream)  # E_ref: the mean local energy after equilibration
+        wk.reset_accumulators(wk.reduce_estimators(stream=stream)["E"], stream=stream)
         return g, wk
 
     peaks = vmcf.vmcf_probe_pipes(stream=stream)
@@ -260,7 +288,7 @@ def main():
     roofline = {"bound": "alu", "pipe": bound, "kernel": f"{dom}_kernel<float>", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s" if bound != "sfu" else "Texp/s", "frac": achieved / peak,
                 "peak_source": "measured in this run by vmcf_probe_pipes (register-only FMA/exp kernels)",
-                "traffic": None, "launch_ms": t_launch * 1e3,
+                "traffic": profiled_traffic() if dom == "measure" else None, "launch_ms": t_launch * 1e3,
                 "kernel_share": {k: kt[k]["ms"] / max(1e-9, sum(v["ms"] for v in kt.values())) for k in kt},
                 "whole_step_frac": workmodel.roofline_time(work["total"], peaks)[1] * W / (ms * 1e-3 / args.steps)}
 
