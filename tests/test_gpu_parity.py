@@ -187,20 +187,20 @@ def test_counters_and_singular_free_run(sys1):
     assert c["singular"] == 0
 
 
-@pytest.mark.parametrize("cfg", [0, 1])
+@pytest.mark.parametrize("cfg", [0, 1, 4])
 def test_mixed_estimators_within_a_tenth_of_their_error_bars(cfg):
     """Mixed-precision sampling; the FP64 path measures the same configurations after every
     sweep (paired). Every walker-averaged estimator (E, each force component, each dE/dC
     element) of the mixed path lies within 0.1 x its own jackknife error bar of the FP64 one."""
     sysx = S.make_system(cfg)
-    W = 4096
+    W = 4096 if cfg != 4 else 512
     pos = S.initial_walkers(sysx, W, seed=12)
     gm = vmcf.System(sysx, vmcf.MIXED)
     g64 = vmcf.System(sysx, vmcf.FP64)
     wm = vmcf.Walkers(gm, pos, key=(5222, cfg), nblocks=32)
     wm.sample(20, measure=False)
     w64 = vmcf.Walkers(g64, wm.positions(), key=(5222, cfg), nblocks=32)
-    e_ref = -76.0 if cfg == 0 else -150.0
+    e_ref = {0: -76.0, 1: -150.0, 4: -600.0}[cfg]
     wm.reset_accumulators(e_ref)
     w64.reset_accumulators(e_ref)
     for _ in range(6):
@@ -242,3 +242,22 @@ def test_tensor_core_walker_sums_match_simt(cfg):
         assert rel(a[:, sec], b[:, sec]) < 1e-2, rel(a[:, sec], b[:, sec])
         # per-element agreement well beyond chance: correlation of the two sum vectors
         assert np.corrcoef(a[:, sec].ravel(), b[:, sec].ravel())[0, 1] > 0.9999
+
+
+
+def test_evaluate_mixed_local_energy_c9o4h8():
+    """94 electrons (general kernels): per-walker mixed-mode E_L on walkers drawn from |Psi|^2
+    within 1e-5 of max(|E_L|, |mean E_L|) for Slater condition numbers <= 1e4."""
+    sys4 = S.make_system(4)
+    o = oracle.Oracle(sys4)
+    st = o.new_state(S.initial_walkers(sys4, 48, seed=8), key=(5222, 4))
+    o.sample(st, 20)
+    pos = st["pos"]
+    ref = o.eval(pos, want=("EL",))["EL"]
+    got = gpu_eval(vmcf.System(sys4, vmcf.MIXED), pos, ("EL",))["EL"]
+    r = np.abs(got - ref) / np.maximum(np.abs(ref), abs(ref.mean()))
+    kap = slater_condition(sys4, pos)
+    well = kap <= 1e4
+    assert well.mean() > 0.8
+    assert r[well].max() < 1e-5, np.sort(r[well])[-5:]
+    assert np.all(r[~well] < 1e-9 * kap[~well])
