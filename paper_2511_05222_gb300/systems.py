@@ -221,10 +221,18 @@ def overlap_matrix(sys: System) -> np.ndarray:
             l2, n2 = int(sys.shell_l[s2]), int(sys.shell_nprim[s2])
             B = sys.R[sys.shell_center[s2]]
             al, be = np.meshgrid(sys.shell_exp[s1, :n1], sys.shell_exp[s2, :n2], indexing="ij")
+            al, be = al.ravel(), be.ravel()
             w = np.outer(coef[s1, :n1], coef[s2, :n2]).ravel()
+            # 1-D overlaps for every pair of powers on each axis, shared by all Cartesian terms
+            tab = [[[_overlap_1d(a, b, A[ax], B[ax], al, be) for b in range(l2 + 1)] for a in range(l1 + 1)]
+                   for ax in range(3)]
             for m1, t1 in enumerate(CART_TERMS[l1]):
                 for m2, t2 in enumerate(CART_TERMS[l2]):
-                    v = float(w @ _cart_overlap(t1, t2, A, B, al.ravel(), be.ravel()))
+                    tot = np.zeros_like(al)
+                    for c1, (a1, b1, z1) in t1:
+                        for c2, (a2, b2, z2) in t2:
+                            tot = tot + c1 * c2 * (tab[0][a1][a2] * tab[1][b1][b2] * tab[2][z1][z2])
+                    v = float(w @ tot)
                     S[ao0[s1] + m1, ao0[s2] + m2] = v
                     S[ao0[s2] + m2, ao0[s1] + m1] = v
     return S
