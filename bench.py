@@ -34,6 +34,8 @@ WORKLOADS = {
     "c2oh6": dict(cfg=1, walkers=16384, name="C2OH6 all-electron, 26 e-, 72 AOs, 9 nuclei"),
     "water": dict(cfg=0, walkers=1024, name="H2O all-electron, 10 e-, 24 AOs, 3 nuclei"),
     "c9o4h8": dict(cfg=4, walkers=65536, name="C9O4H8 all-electron, 94 e-, 222 AOs, 21 nuclei"),
+    "ragged64": dict(cfg=3, walkers=0, name="ragged batch: 64 covalent-walk H/C/O molecules, 3-21 nuclei, "
+                                           "10-94 e-, 24-212 AOs, 512-4096 walkers each"),
 }
 METRIC = "walker-evals/s (E_L+forces+dE/dC) at 26 e⁻, mixed vs FP64 GPU; % of roofline"
 
@@ -189,6 +191,102 @@ def run_reference(args, wl):
     return 0
 
 
+def shard_geometries(plan, ws):
+    """Geometries per rank: longest-processing-time-first by N_e^3 x W."""
+    load = [0.0] * ws
+    own = [[] for _ in range(ws)]
+    for g in sorted(range(len(plan)), key=lambda g: -(sum(plan[g][0]) ** 3) * plan[g][1]):
+        r = min(range(ws), key=lambda r: load[r])
+        own[r].append(g)
+        load[r] += sum(plan[g][0]) ** 3 * plan[g][1]
+    return [sorted(o) for o in own]
+
+
+def run_ragged(args, wl):
+    """One step = one measured sweep of every geometry of the ragged batch, as one replay of
+    the batch's captured graph (persistent kernels, autotuned launch shapes)."""
+    import torch
+    from paper_2511_05222_gb300 import systems as S
+    from paper_2511_05222_gb300 import vmcf, workmodel
+
+    rank, ws, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    plan = S.ragged_batch_plan(64)
+    mine = shard_geometries(plan, ws)[rank]
+    geos = S.make_ragged_batch(64, only=set(mine))
+    systems = [vmcf.System(sx, vmcf.MIXED, force_group=True) for sx, _ in geos]
+    walkers = [vmcf.Walkers(systems[i], S.initial_walkers(sx, W, seed=g), key=(5222, 3000 + g), nblocks=64,
+                            stream=stream) for i, ((sx, W), g) in enumerate(zip(geos, mine))]
+    batch = vmcf.Batch(systems, walkers, stream=stream)
+    batch.sample(max(1, args.equil // 2), 0.3, 26, measure=False, stream=stream)
+    batch.autotune(0.3, 26, stream=stream)
+    for w in walkers:  # E_ref: each geometry's mean local energy after equilibration
+        w.reset_accumulators(0.0, stream=stream)
+        w.measure(stream=stream)
+        w.reset_accumulators(w.reduce_estimators(stream=stream)["E"], stream=stream)
+    for _ in range(args.warmup):
+        batch.sample(1, 0.3, 26, measure=True, stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        for a, b in ev:
+            flush.fill_(1.0)
+            a.record(stream)
+            batch.sample(1, 0.3, 26, measure=True, stream=stream)
+            b.record(stream)
+        barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    total_w = sum(W for _, W in plan)
+    value = total_w * args.steps / (ms * 1e-3)
+    peaks = vmcf.vmcf_probe_pipes(stream=stream)
+    t_roof, acc_n, acc_d = 0.0, 0, 0
+    for (sx, W), w, sy in zip(geos, walkers, systems):
+        c = w.counters(stream=stream)
+        acc_n += c["accepted"]
+        acc_d += c["moves"]
+        wk = workmodel.per_walker_eval(sx.K, sy.M, sx.n_up, sx.n_dn, int(sx.shell_nprim.sum()),
+                                       c["accepted"] / max(1, c["moves"]))
+        t_roof += W * workmodel.roofline_time(wk["total"], peaks)[1]
+    info = batch.info()
+    shapes = sorted({(gi["GS"], gi["groups"]) for gi in info["geometries"]})
+    line = {"metric": METRIC, "value": value, "unit": "walker-evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "geometries": len(plan), "walkers_total": total_w,
+                       "geometries_per_rank": len(mine), "step_sigma": 0.3, "refresh_every": 26,
+                       "precision": "mixed (FP32 + FP64 inverse/ratio/sums)",
+                       "l2": "flushed (256 MB write) between timed steps",
+                       "buckets": info["buckets"], "persistent_kernels_per_sweep": info["launches"],
+                       "launch_shapes": [f"{a}x{b}" for a, b in shapes]},
+            "roofline": {"bound": "alu", "pipe": "whole step, per geometry", "frac": t_roof * ws / (ms * 1e-3 / args.steps)
+                         if ws == 1 else None, "peak_source": "measured in this run by vmcf_probe_pipes"},
+            "gpu_launches": args.steps * (info["launches"] + 1), "clocks": clk.summary(),
+            "acceptance": acc_n / max(1, acc_d)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -205,6 +303,8 @@ def main():
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.workload == "ragged64":
+        return run_ragged(args, wl)
 
     import torch
     from paper_2511_05222_gb300 import systems as S

@@ -225,6 +225,54 @@ int vmcf_profile(vmcf_walkers_t wk, int enable);
 int vmcf_kernel_times(vmcf_walkers_t wk, double* ms, long long* count, int reset);
 int vmcf_probe_pipes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, void* stream);
 
+/* ---- Ragged batches of geometries.
+ * Many independent geometries (different nuclei, electron and AO counts, walker counts) are
+ * sampled together: each VMC sweep of the whole batch is one replay of a captured CUDA
+ * graph that holds one persistent kernel per launch shape, plus a one-thread-block clock
+ * kernel. Walker groups in the persistent kernels pull work items (one geometry, one range of
+ * its walkers) from a device queue, longest first, so that small and large geometries share
+ * the SMs; per walker a group runs the Metropolis sweep and, when measuring, the full
+ * evaluation (E_L, forces, O) right after it. The method per walker is exactly that of
+ * vmcf_sample (App. A, the MCMC sampling and the estimators of Eqs. hf, pulay and
+ * fc-vmc-eval); batching changes neither a walker's chain nor its contributions, only where
+ * and when they are computed. The paper batches nothing across geometries: this is the
+ * deployment form for many molecules (or many displaced geometries) at once.
+ *
+ * vmcf_batch_create: systems[g], walkers[g] for g < G: each walker set belongs to its system;
+ *   every system has the same precision and runs on the walker-group kernels (systems that
+ *   qualify for the small-system kernels must be created with VMCF_FORCE_GROUP_PATH), else
+ *   VMCF_ENOTSUP. The batch keeps the handles (the caller keeps ownership and must keep them
+ *   alive until vmcf_batch_destroy) and allocates its own device tables. Geometries are put in
+ *   buckets by (ceil(Ne / 16), ceil(M / 64)); every bucket starts with the default launch
+ *   shape (32 threads per walker while n_up, n_dn <= 24, else 128; as many walker groups per
+ *   CTA, up to 4, as fit shared memory). Synchronises `stream`.
+ * vmcf_batch_autotune: for every bucket, time one sweep-plus-evaluation of the bucket's walkers
+ *   with each feasible launch shape (threads per walker 32 or 128, walker groups per CTA 1, 2
+ *   or 4) and keep the fastest; also records each geometry's measured cost for the
+ *   longest-first order. Every timed sweep is a real sweep of the bucket's chains followed by
+ *   a fresh inversion, exactly as vmcf_sample(..., measure = 0) plus an evaluation whose sums
+ *   are discarded: call it during equilibration. Synchronises `stream`.
+ * vmcf_batch_set_shape: force the launch shape of the bucket that holds geometry g
+ *   (GS = 32 or 128 threads per walker, groups = walker groups per CTA); VMCF_EINVAL if it
+ *   does not fit shared memory.
+ * vmcf_batch_sample: n_sweeps sweeps of every geometry, as vmcf_sample on each walker set
+ *   (same arguments and meaning; measure != 0 adds each sweep's evaluation to each walker
+ *   set's sums, read with vmcf_reduce_estimators / vmcf_block_sums on that walker set).
+ *   The first call with a given (measure, refresh_k, step_sigma) captures the graph; later
+ *   calls replay it. Asynchronous on `stream`.
+ * vmcf_batch_info: number of buckets and of persistent kernels per sweep, and for geometry g
+ *   (if 0 <= g < G) its bucket and launch shape; any output may be NULL. */
+typedef struct vmcf_batch_s* vmcf_batch_t; /* opaque, library-owned */
+int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walkers, int G, void* stream,
+                      vmcf_batch_t* out);
+int vmcf_batch_destroy(vmcf_batch_t batch);
+int vmcf_batch_autotune(vmcf_batch_t batch, double step_sigma, int refresh_k, void* stream);
+int vmcf_batch_set_shape(vmcf_batch_t batch, int g, int GS, int groups);
+int vmcf_batch_sample(vmcf_batch_t batch, int n_sweeps, double step_sigma, int refresh_k, int measure,
+                      void* stream);
+int vmcf_batch_info(vmcf_batch_t batch, int* n_buckets, int* n_launches, int g, int* bucket, int* GS,
+                    int* groups);
+
 const char* vmcf_strerror(int status);
 const char* vmcf_last_error(void);
 

@@ -1,0 +1,487 @@
+// Host side of the ragged-batch entry points (vmcf_batch_*): buckets, launch shapes, the
+// autotuner, the longest-first work order and the captured sweep graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/vmcf.h"
+#include "vmcf_host.h"
+
+using namespace vmcf;
+
+namespace {
+
+int fail(int code, const std::string& msg) { return vmcf::set_last_error(code, msg); }
+
+int cuda_fail(cudaError_t e, const std::string& where) {
+  return vmcf::set_last_error(VMCF_ECUDA, where + ": " + cudaGetErrorString(e));
+}
+
+#define BATCH_CUDA(call)                                 \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call);  \
+  } while (0)
+
+int align16(int x) { return (x + 15) & ~15; }
+
+// Header of a walker group's shared-memory region: the geometry copy and two ints.
+constexpr int kHdr = (int)((sizeof(BatchGeom) + 16 + 15) / 16 * 16);
+
+struct Shape {
+  int GS = 32, groups = 1;
+  bool operator<(const Shape& o) const { return std::tie(GS, groups) < std::tie(o.GS, o.groups); }
+  bool operator==(const Shape& o) const { return GS == o.GS && groups == o.groups; }
+};
+
+struct LaunchPlan {
+  Shape shape;
+  int grid = 1;
+  size_t smem = 0;
+  int region = 0;
+  int item0 = 0, n_items = 0;
+};
+
+}  // namespace
+
+struct vmcf_batch_s {
+  int G = 0, precision = 0, sms = 1;
+  std::vector<vmcf_system_s*> sys;
+  std::vector<vmcf_walkers_s*> wk;
+  std::vector<int> bucket;           // per geometry
+  std::vector<Shape> bucket_shape;   // per bucket
+  std::vector<double> cost;          // per geometry: relative cost of one walker-sweep
+  std::vector<LaunchPlan> launches;
+  std::vector<BatchGeom> h_geo;
+  std::vector<BatchClock> h_clk;
+  BatchGeom* d_geo = nullptr;
+  BatchClock* d_clk = nullptr;
+  int2* d_items = nullptr;
+  size_t items_cap = 0;
+  int* d_queue = nullptr;  // one counter per launch
+  int queue_cap = 0;
+  // captured sweep graph and the (mode, kref, sigma) it was captured for
+  cudaGraphExec_t exec = nullptr;
+  int g_mode = -1, g_kref = -1;
+  double g_sigma = 0.0;
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> forks;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork_ev = nullptr;
+};
+
+namespace {
+
+int tsize(const vmcf_batch_s& b) { return b.precision == VMCF_FP64 ? 8 : 4; }
+
+// Bytes of one walker group's region for geometry g at group size GS.
+int region_bytes(const vmcf_batch_s& b, int g, int GS) {
+  const GroupLayout a = group_layout_rm(*b.sys[g], GS), m = group_layout_meas(*b.sys[g], GS);
+  return kHdr + align16(std::max(a.bytes, m.bytes));
+}
+
+int bucket_region(const vmcf_batch_s& b, int bk, int GS) {
+  int r = 0;
+  for (int g = 0; g < b.G; ++g)
+    if (b.bucket[g] == bk) r = std::max(r, region_bytes(b, g, GS));
+  return r;
+}
+
+int occupancy(const vmcf_batch_s& b, const Shape& sh, size_t smem, int* ctas) {
+  cudaError_t e = b.precision == VMCF_FP64 ? batch_occupancy<double>(sh.GS, sh.groups, smem, ctas)
+                                           : batch_occupancy<float>(sh.GS, sh.groups, smem, ctas);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the batch kernel");
+  return VMCF_OK;
+}
+
+bool shape_fits(const vmcf_batch_s& b, int bk, const Shape& sh) {
+  if (!((sh.GS == 32 && (sh.groups == 1 || sh.groups == 2 || sh.groups == 4)) || (sh.GS == 128 && sh.groups == 1)))
+    return false;
+  return (size_t)sh.groups * bucket_region(b, bk, sh.GS) <= (size_t)kSmemCapBytes;
+}
+
+Shape default_shape(const vmcf_batch_s& b, int bk) {
+  int nmax = 0;
+  for (int g = 0; g < b.G; ++g)
+    if (b.bucket[g] == bk) nmax = std::max(nmax, b.sys[g]->nmax);
+  Shape sh;
+  sh.GS = nmax <= 24 ? 32 : 128;
+  sh.groups = 1;
+  if (sh.GS == 32)
+    for (int gr : {4, 2}) {
+      Shape t{32, gr};
+      if (shape_fits(b, bk, t)) {
+        sh = t;
+        break;
+      }
+    }
+  if (!shape_fits(b, bk, sh)) sh = Shape{128, 1};
+  return sh;
+}
+
+// Relative cost of one walker-sweep with evaluation, from the operation counts of the
+// method: AO/MO rows per move and per evaluation, inversions, Jastrow pairs.
+double heuristic_cost(const vmcf_system_s& s) {
+  const double Ne = s.Ne, M = s.M, n = s.nmax, K = s.K;
+  return Ne * (3.0 * M * n + 30.0 * M) + 4.0 * n * n * n * (1.0 + Ne / 26.0) + 60.0 * Ne * (Ne + K);
+}
+
+void fill_geo(vmcf_batch_s& b, int g, int GS) {
+  const vmcf_system_s& s = *b.sys[g];
+  const vmcf_walkers_s& w = *b.wk[g];
+  BatchGeom G{};
+  G.S = s.dev;
+  G.Lrm = group_layout_rm(s, GS);
+  G.Lmeas = group_layout_meas(s, GS);
+  G.P.pos = w.pos;
+  G.P.B = w.B;
+  G.P.nacc = w.nacc;
+  G.P.nrej = w.nrej;
+  G.P.counters = w.counters;
+  G.P.W = w.W;
+  G.P.wid0 = w.wid0;
+  G.P.k0 = w.k0;
+  G.P.k1 = w.k1;
+  G.Mp.pos = w.pos;
+  G.Mp.Bout = w.B;
+  G.Mp.acc = w.acc;
+  G.Mp.accL = s.accL;
+  G.Mp.acc_in_smem = 0;
+  G.Mp.e_ref = w.e_ref;
+  G.Mp.counters = w.counters;
+  G.Mp.W = w.W;
+  G.grid_meas = w.grid_meas;
+  b.h_geo[g] = G;
+}
+
+void invalidate_graph(vmcf_batch_s& b) {
+  if (b.exec) cudaGraphExecDestroy(b.exec);
+  b.exec = nullptr;
+  b.g_mode = -1;
+}
+
+// Launch list and work order for the current bucket shapes, restricted to the geometries
+// with take[g] (all when take is empty). Items of one launch are ordered by the cost of the
+// walkers they hold, largest first.
+int build_plan(vmcf_batch_s& b, const std::vector<char>& take, cudaStream_t st) {
+  std::map<Shape, std::vector<int>> by_shape;
+  for (int g = 0; g < b.G; ++g)
+    if (take.empty() || take[g]) by_shape[b.bucket_shape[b.bucket[g]]].push_back(g);
+  std::vector<int2> items;
+  b.launches.clear();
+  for (auto& kv : by_shape) {
+    LaunchPlan lp;
+    lp.shape = kv.first;
+    int region = 0;
+    for (int g : kv.second) region = std::max(region, region_bytes(b, g, lp.shape.GS));
+    lp.region = region;
+    lp.smem = (size_t)lp.shape.groups * region;
+    if (lp.smem > (size_t)kSmemCapBytes) return fail(VMCF_ENOTSUP, "batch launch shape does not fit shared memory");
+    std::vector<std::pair<double, int2>> its;
+    for (int g : kv.second) {
+      fill_geo(b, g, lp.shape.GS);
+      const vmcf_walkers_s& w = *b.wk[g];
+      for (int c = 0; c < w.grid_meas; ++c) {
+        const long long n = (long long)w.W * (c + 1) / w.grid_meas - (long long)w.W * c / w.grid_meas;
+        its.push_back({b.cost[g] * (double)n, make_int2(g, c)});
+      }
+    }
+    std::stable_sort(its.begin(), its.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    lp.item0 = (int)items.size();
+    lp.n_items = (int)its.size();
+    for (auto& it : its) items.push_back(it.second);
+    int ctas = 0;
+    int rc = occupancy(b, lp.shape, lp.smem, &ctas);
+    if (rc != VMCF_OK) return rc;
+    if (ctas < 1) return fail(VMCF_ENOTSUP, "batch kernel cannot be resident with this launch shape");
+    const long long groups_needed = lp.n_items;
+    const long long grid_full = (long long)ctas * b.sms;
+    lp.grid = (int)std::max(1LL, std::min(grid_full, (groups_needed + lp.shape.groups - 1) / lp.shape.groups));
+    b.launches.push_back(lp);
+  }
+  if (items.size() > b.items_cap) {
+    cudaFree(b.d_items);
+    b.d_items = nullptr;
+    BATCH_CUDA(cudaMalloc(&b.d_items, sizeof(int2) * items.size()));
+    b.items_cap = items.size();
+  }
+  if ((int)b.launches.size() > b.queue_cap) {
+    cudaFree(b.d_queue);
+    b.d_queue = nullptr;
+    BATCH_CUDA(cudaMalloc(&b.d_queue, sizeof(int) * b.launches.size()));
+    b.queue_cap = (int)b.launches.size();
+  }
+  if (!items.empty())
+    BATCH_CUDA(cudaMemcpyAsync(b.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaStreamSynchronize(st));
+  while (b.forks.size() + 1 < b.launches.size()) {
+    cudaStream_t s2;
+    cudaEvent_t ev;
+    BATCH_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    BATCH_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    b.forks.push_back(s2);
+    b.joins.push_back(ev);
+  }
+  invalidate_graph(b);
+  return VMCF_OK;
+}
+
+// Geometry tables (with the current E_ref of each walker set), chain clocks and queues.
+int upload_state(vmcf_batch_s& b, cudaStream_t st) {
+  for (int g = 0; g < b.G; ++g) {
+    b.h_geo[g].Mp.e_ref = b.wk[g]->e_ref;
+    b.h_clk[g].sweep = b.wk[g]->sweep;
+    b.h_clk[g].c = b.wk[g]->counter;
+    b.h_clk[g].Ne = b.sys[g]->Ne;
+  }
+  BATCH_CUDA(cudaMemcpyAsync(b.d_geo, b.h_geo.data(), sizeof(BatchGeom) * b.G, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaMemcpyAsync(b.d_clk, b.h_clk.data(), sizeof(BatchClock) * b.G, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(int) * b.launches.size(), st));
+  return VMCF_OK;
+}
+
+BatchArgs args_for(const vmcf_batch_s& b, int k, int mode, int kref, double sigma) {
+  const LaunchPlan& lp = b.launches[k];
+  BatchArgs A{};
+  A.geo = b.d_geo;
+  A.clk = b.d_clk;
+  A.items = b.d_items + lp.item0;
+  A.n_items = lp.n_items;
+  A.queue = b.d_queue + k;
+  A.mode = mode;
+  A.kref = kref;
+  A.sigma = sigma;
+  A.region = lp.region;
+  A.hdr = kHdr;
+  return A;
+}
+
+cudaError_t launch_k(const vmcf_batch_s& b, int k, int mode, int kref, double sigma, cudaStream_t st) {
+  const LaunchPlan& lp = b.launches[k];
+  const BatchArgs A = args_for(b, k, mode, kref, sigma);
+  return b.precision == VMCF_FP64 ? launch_batch<double>(lp.shape.GS, lp.shape.groups, lp.grid, lp.smem, A, st)
+                                  : launch_batch<float>(lp.shape.GS, lp.shape.groups, lp.grid, lp.smem, A, st);
+}
+
+// One sweep of the batch as a graph: fork one branch per launch, join, advance the clocks.
+int capture(vmcf_batch_s& b, int mode, int kref, double sigma) {
+  invalidate_graph(b);
+  BATCH_CUDA(cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaEventRecord(b.fork_ev, b.cap);
+  for (size_t k = 0; e == cudaSuccess && k < b.launches.size(); ++k) {
+    cudaStream_t sk = k == 0 ? b.cap : b.forks[k - 1];
+    if (k > 0) e = cudaStreamWaitEvent(sk, b.fork_ev, 0);
+    if (e == cudaSuccess) e = launch_k(b, (int)k, mode, kref, sigma, sk);
+    if (e == cudaSuccess && k > 0) e = cudaEventRecord(b.joins[k - 1], sk);
+    if (e == cudaSuccess && k > 0) e = cudaStreamWaitEvent(b.cap, b.joins[k - 1], 0);
+  }
+  if (e == cudaSuccess) e = launch_batch_advance(b.d_clk, b.G, mode, kref, b.d_queue, (int)b.launches.size(), b.cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b.cap, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    b.exec = nullptr;
+    return cuda_fail(e, "capturing the batch sweep graph");
+  }
+  b.g_mode = mode;
+  b.g_kref = kref;
+  b.g_sigma = sigma;
+  return VMCF_OK;
+}
+
+void advance_host(vmcf_batch_s& b, const std::vector<char>& take, int n, int mode, int kref) {
+  for (int g = 0; g < b.G; ++g) {
+    if (!take.empty() && !take[g]) continue;
+    vmcf_walkers_s& w = *b.wk[g];
+    w.sweep += (uint64_t)n;
+    if (mode != 0) {
+      w.counter = 0;
+      if (mode == 1) w.measured += (uint64_t)n;
+    } else {
+      w.counter = (int)((w.counter + (long long)n * b.sys[g]->Ne) % kref);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int vmcf_batch_destroy(vmcf_batch_t b) {
+  if (!b) return VMCF_OK;
+  invalidate_graph(*b);
+  for (auto s : b->forks) cudaStreamDestroy(s);
+  for (auto e : b->joins) cudaEventDestroy(e);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaFree(b->d_geo);
+  cudaFree(b->d_clk);
+  cudaFree(b->d_items);
+  cudaFree(b->d_queue);
+  delete b;
+  return VMCF_OK;
+}
+
+int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walkers, int G, void* stream,
+                      vmcf_batch_t* out) {
+  if (!out) return fail(VMCF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!systems || !walkers || G < 1) return fail(VMCF_EINVAL, "need G >= 1 systems and walker sets");
+  for (int g = 0; g < G; ++g) {
+    if (!systems[g] || !walkers[g] || walkers[g]->sys != systems[g])
+      return fail(VMCF_EINVAL, "geometry " + std::to_string(g) + ": walker set does not belong to its system");
+    if (systems[g]->precision != systems[0]->precision)
+      return fail(VMCF_EINVAL, "all systems of a batch must have the same precision");
+    if (systems[g]->small)
+      return fail(VMCF_ENOTSUP, "geometry " + std::to_string(g) +
+                                    ": batches run on the walker-group kernels; create the system with "
+                                    "VMCF_FORCE_GROUP_PATH");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  auto* b = new vmcf_batch_s();
+  b->G = G;
+  b->precision = systems[0]->precision;
+  b->sys.assign(systems, systems + G);
+  b->wk.assign(walkers, walkers + G);
+  b->h_geo.resize(G);
+  b->h_clk.resize(G);
+  b->cost.resize(G);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_geo, sizeof(BatchGeom) * G);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_clk, sizeof(BatchClock) * G);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    vmcf_batch_destroy(b);
+    return cuda_fail(e, "batch set-up");
+  }
+  // buckets by (ceil(Ne / 16), ceil(M / 64))
+  std::map<std::pair<int, int>, int> keys;
+  b->bucket.resize(G);
+  for (int g = 0; g < G; ++g) {
+    const std::pair<int, int> k{(systems[g]->Ne + 15) / 16, (systems[g]->M + 63) / 64};
+    auto it = keys.find(k);
+    if (it == keys.end()) it = keys.emplace(k, (int)keys.size()).first;
+    b->bucket[g] = it->second;
+    b->cost[g] = heuristic_cost(*systems[g]);
+  }
+  b->bucket_shape.resize(keys.size());
+  for (int bk = 0; bk < (int)keys.size(); ++bk) b->bucket_shape[bk] = default_shape(*b, bk);
+  int rc = build_plan(*b, {}, st);
+  if (rc != VMCF_OK) {
+    vmcf_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return VMCF_OK;
+}
+
+int vmcf_batch_set_shape(vmcf_batch_t b, int g, int GS, int groups) {
+  if (!b || g < 0 || g >= b->G) return fail(VMCF_EINVAL, "bad batch or geometry index");
+  const int bk = b->bucket[g];
+  const Shape sh{GS, groups};
+  if (!shape_fits(*b, bk, sh)) return fail(VMCF_EINVAL, "launch shape not supported or does not fit shared memory");
+  b->bucket_shape[bk] = sh;
+  return build_plan(*b, {}, nullptr);
+}
+
+int vmcf_batch_info(vmcf_batch_t b, int* n_buckets, int* n_launches, int g, int* bucket, int* GS, int* groups) {
+  if (!b) return fail(VMCF_EINVAL, "NULL batch");
+  if (n_buckets) *n_buckets = (int)b->bucket_shape.size();
+  if (n_launches) *n_launches = (int)b->launches.size();
+  if (g >= 0 && g < b->G) {
+    const Shape& sh = b->bucket_shape[b->bucket[g]];
+    if (bucket) *bucket = b->bucket[g];
+    if (GS) *GS = sh.GS;
+    if (groups) *groups = sh.groups;
+  }
+  return VMCF_OK;
+}
+
+int vmcf_batch_sample(vmcf_batch_t b, int n_sweeps, double step_sigma, int refresh_k, int measure, void* stream) {
+  if (!b) return fail(VMCF_EINVAL, "NULL batch");
+  if (n_sweeps < 0 || !(step_sigma > 0.0) || !std::isfinite(step_sigma) || refresh_k < 1)
+    return fail(VMCF_EINVAL, "need n_sweeps >= 0, step_sigma > 0, refresh_k >= 1");
+  if (n_sweeps == 0) return VMCF_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int mode = measure ? 1 : 0;
+  if (!b->exec || b->g_mode != mode || b->g_kref != refresh_k || b->g_sigma != step_sigma) {
+    int rc = capture(*b, mode, refresh_k, step_sigma);
+    if (rc != VMCF_OK) return rc;
+  }
+  int rc = upload_state(*b, st);
+  if (rc != VMCF_OK) return rc;
+  for (int i = 0; i < n_sweeps; ++i) BATCH_CUDA(cudaGraphLaunch(b->exec, st));
+  advance_host(*b, {}, n_sweeps, mode, refresh_k);
+  return VMCF_OK;
+}
+
+int vmcf_batch_autotune(vmcf_batch_t b, double step_sigma, int refresh_k, void* stream) {
+  if (!b) return fail(VMCF_EINVAL, "NULL batch");
+  if (!(step_sigma > 0.0) || !std::isfinite(step_sigma) || refresh_k < 1)
+    return fail(VMCF_EINVAL, "need step_sigma > 0, refresh_k >= 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t t0, t1;
+  BATCH_CUDA(cudaEventCreate(&t0));
+  BATCH_CUDA(cudaEventCreate(&t1));
+  const int nb = (int)b->bucket_shape.size();
+  int rc = VMCF_OK;
+  for (int bk = 0; bk < nb && rc == VMCF_OK; ++bk) {
+    std::vector<char> take(b->G, 0);
+    long long walkers = 0;
+    for (int g = 0; g < b->G; ++g)
+      if (b->bucket[g] == bk) {
+        take[g] = 1;
+        walkers += b->wk[g]->W;
+      }
+    Shape best = b->bucket_shape[bk];
+    float best_ms = 1e30f;
+    for (const Shape cand : {Shape{32, 1}, Shape{32, 2}, Shape{32, 4}, Shape{128, 1}}) {
+      if (!shape_fits(*b, bk, cand)) continue;
+      b->bucket_shape[bk] = cand;
+      rc = build_plan(*b, take, st);
+      if (rc != VMCF_OK) break;
+      rc = upload_state(*b, st);
+      if (rc != VMCF_OK) break;
+      cudaError_t e = cudaEventRecord(t0, st);
+      if (e == cudaSuccess) e = launch_k(*b, 0, 2, refresh_k, step_sigma, st);
+      if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+      if (e != cudaSuccess) {
+        rc = cuda_fail(e, "autotuning launch");
+        break;
+      }
+      advance_host(*b, take, 1, 2, refresh_k);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cand;
+      }
+    }
+    b->bucket_shape[bk] = best;
+    // measured cost of one walker-sweep of this bucket, shared by its geometries in
+    // proportion to their operation counts
+    if (rc == VMCF_OK && best_ms < 1e29f && walkers > 0) {
+      double hsum = 0.0;
+      for (int g = 0; g < b->G; ++g)
+        if (take[g]) hsum += heuristic_cost(*b->sys[g]) * b->wk[g]->W;
+      for (int g = 0; g < b->G; ++g)
+        if (take[g]) b->cost[g] = (double)best_ms * heuristic_cost(*b->sys[g]) / hsum;
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (rc != VMCF_OK) return rc;
+  return build_plan(*b, {}, st);
+}
+
+}  // extern "C"

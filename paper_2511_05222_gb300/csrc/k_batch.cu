@@ -1,0 +1,100 @@
+// Ragged batch of geometries: one persistent kernel per launch shape (threads per walker GS,
+// walker groups per CTA) that sweeps and measures the walkers of every geometry assigned to
+// that shape. Each walker group pulls work items (geometry g, accumulator slot c) from a
+// device queue; item (g, c) covers the walkers of g whose walker sums go to slot c, so a slot
+// is only ever touched by the group that holds its item and is updated without atomics.
+// Per walker the group runs one Metropolis sweep (move_walker) and, when measuring, the
+// full evaluation (measure_walker) straight after, while the walker is hot in L1/L2.
+#include "kernels.cuh"
+
+namespace vmcf {
+
+template <typename T, int GS>
+__global__ void __launch_bounds__(128) batch_kernel(BatchArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int gid = threadIdx.x / GS, t = threadIdx.x % GS;
+  unsigned char* region = smem + (size_t)gid * A.region;
+  BatchGeom* G = reinterpret_cast<BatchGeom*>(region);
+  int* cur = reinterpret_cast<int*>(region + A.hdr - 16);  // [0] geometry held, [1] item taken
+  unsigned char* base = region + A.hdr;
+  if (t == 0) cur[0] = -1;
+  for (;;) {
+    if (t == 0) cur[1] = atomicAdd(A.queue, 1);
+    gsync<GS>();
+    const int it = cur[1];
+    if (it >= A.n_items) break;  // uniform over the group
+    const int2 item = A.items[it];
+    if (item.x != cur[0]) {
+      gsync<GS>();  // every thread has read cur[0]
+      const int* src = reinterpret_cast<const int*>(A.geo + item.x);
+      int* dst = reinterpret_cast<int*>(G);
+      for (int i = t; i < (int)(sizeof(BatchGeom) / 4); i += GS) dst[i] = src[i];
+      gsync<GS>();
+      if (t == 0) {
+        cur[0] = item.x;
+        const BatchClock ck = A.clk[item.x];
+        G->P.sweep0 = ck.sweep;
+        G->P.c0 = ck.c;
+        G->P.nsweeps = 1;
+        G->P.kref = A.kref;
+        G->P.sigma = A.sigma;
+        G->P.skip_final_refresh = A.mode != 0;
+        G->Mp.acc_in_smem = 0;
+      }
+      gsync<GS>();
+    }
+    const int W = G->P.W;
+    const long long w0 = (long long)W * item.y / G->grid_meas, w1 = (long long)W * (item.y + 1) / G->grid_meas;
+    double* slot = A.mode == 1 ? G->Mp.acc + (size_t)item.y * G->Mp.accL : nullptr;
+    for (long long w = w0; w < w1; ++w) {
+      move_walker<T, GS>(G->S, G->Lrm, G->P, base, (int)w, G->P.c0, G->P.sweep0);
+      if (A.mode != 0) measure_walker<T, GS>(G->S, G->Lmeas, G->Mp, base, nullptr, slot, (int)w);
+    }
+    gsync<GS>();  // cur[1] is read by every thread before it is overwritten
+  }
+}
+
+// After a sweep of the whole batch: advance every geometry's clock and rewind the queues.
+__global__ void batch_advance_kernel(BatchClock* clk, int G, int mode, int kref, int* queues, int nq) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    BatchClock c = clk[g];
+    c.sweep += 1;
+    c.c = mode != 0 ? 0 : (int)((c.c + c.Ne) % kref);  // a measurement rebuilds the inverses
+    clk[g] = c;
+  }
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) queues[q] = 0;
+}
+
+template <typename T>
+cudaError_t launch_batch(int GS, int groups, int grid, size_t smem, const BatchArgs& A, cudaStream_t st) {
+  const dim3 g(grid), b(GS * groups);
+  if (GS == 32)
+    batch_kernel<T, 32><<<g, b, smem, st>>>(A);
+  else if (GS == 128)
+    batch_kernel<T, 128><<<g, b, smem, st>>>(A);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t batch_occupancy(int GS, int groups, size_t smem, int* ctas_per_sm) {
+  const void* fn = GS == 32 ? reinterpret_cast<const void*>(batch_kernel<T, 32>)
+                            : reinterpret_cast<const void*>(batch_kernel<T, 128>);
+  if (GS != 32 && GS != 128) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, GS * groups, smem);
+}
+
+cudaError_t launch_batch_advance(BatchClock* clk, int G, int mode, int kref, int* queues, int nq, cudaStream_t st) {
+  batch_advance_kernel<<<1, 128, 0, st>>>(clk, G, mode, kref, queues, nq);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_batch<float>(int, int, int, size_t, const BatchArgs&, cudaStream_t);
+template cudaError_t launch_batch<double>(int, int, int, size_t, const BatchArgs&, cudaStream_t);
+template cudaError_t batch_occupancy<float>(int, int, size_t, int*);
+template cudaError_t batch_occupancy<double>(int, int, size_t, int*);
+
+}  // namespace vmcf

@@ -75,11 +75,12 @@ __global__ void __launch_bounds__(128) refresh_kernel(DevSys S, GroupLayout L, c
 }
 
 // ---------------------------------------------------------------- Metropolis sweeps
+// All sweeps of one walker (index w of P's arrays) by one group. c0: attempted moves since
+// the last refresh when the launch starts; sweep0: global sweep index of the first sweep.
 template <typename T, int GS>
-__global__ void __launch_bounds__(128) move_kernel(DevSys S, GroupLayout L, MoveParams P) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int gpb = blockDim.x / GS, gid = threadIdx.x / GS, t = threadIdx.x % GS;
-  unsigned char* base = smem + gid * L.bytes;
+__device__ void move_walker(const DevSys& S, const GroupLayout& L, const MoveParams& P, unsigned char* base, int w,
+                            int c0, uint64_t sweep0) {
+  const int t = threadIdx.x % GS;
   double* pos = sm_ptr<double>(base, L.pos);
   float* ph = sm_ptr<float>(base, L.ph);
   float* pl = sm_ptr<float>(base, L.pl);
@@ -93,8 +94,6 @@ __global__ void __launch_bounds__(128) move_kernel(DevSys S, GroupLayout L, Move
   double* f = sm_ptr<double>(base, L.f);
   double* red = sm_ptr<double>(base, L.red);
   int* flag = sm_ptr<int>(base, L.scal);
-  const int w = blockIdx.x * gpb + gid;
-  if (w >= P.W) return;
   const int Ne = S.Ne, nup = S.nup, K = S.K;
   double* posg = P.pos + (size_t)w * 3 * Ne;
   T* Bg = reinterpret_cast<T*>(P.B) + (size_t)w * S.nB;
@@ -103,10 +102,10 @@ __global__ void __launch_bounds__(128) move_kernel(DevSys S, GroupLayout L, Move
   if (t == 0) *flag = 0;
   gsync<GS>();
   const uint64_t wid = P.wid0 + (uint64_t)w;
-  int c = P.c0;
+  int c = c0;
   uint32_t nacc = 0, nrej = 0, nref = 0;
   for (int sw = 0; sw < P.nsweeps; ++sw) {
-    const uint64_t sweep = P.sweep0 + (uint64_t)sw;
+    const uint64_t sweep = sweep0 + (uint64_t)sw;
     for (int e = 0; e < Ne; ++e) {
       const int sg = e < nup ? 0 : 1;
       const int n = sg == 0 ? nup : S.ndn, el = e - (sg == 0 ? 0 : nup);
@@ -210,7 +209,18 @@ __global__ void __launch_bounds__(128) move_kernel(DevSys S, GroupLayout L, Move
     if (*flag) atomicAdd(&P.counters[0], 1ull);
     if (nref) atomicAdd(&P.counters[1], (unsigned long long)nref);
   }
+  gsync<GS>();
 }
+
+template <typename T, int GS>
+__global__ void __launch_bounds__(128) move_kernel(DevSys S, GroupLayout L, MoveParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int gpb = blockDim.x / GS, gid = threadIdx.x / GS;
+  const int w = blockIdx.x * gpb + gid;
+  if (w >= P.W) return;  // the whole group leaves together; only group barriers are used
+  move_walker<T, GS>(S, L, P, smem + gid * L.bytes, w, P.c0, P.sweep0);
+}
+
 
 // ---------------------------------------------------------------- measurement
 template <typename T, int GS>

@@ -210,6 +210,14 @@ Launch launch_rm(const vmcf_system_s& s, int W) {
 
 }  // namespace
 
+GroupLayout vmcf::group_layout_rm(const vmcf_system_s& s, int GS) {
+  return layout_refresh_move(s, s.precision == VMCF_FP64 ? 8 : 4, GS);
+}
+
+GroupLayout vmcf::group_layout_meas(const vmcf_system_s& s, int GS) {
+  return layout_measure(s, s.precision == VMCF_FP64 ? 8 : 4, GS, false);
+}
+
 Launch vmcf::launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD) {
   Launch lc{};
   lc.GS = s.GS;

@@ -72,5 +72,9 @@ struct vmcf_walkers_s {
 namespace vmcf {
 // Launch planning shared by the entry points (defined in vmcf_api.cu).
 Launch launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD);
+// Walker-group shared-memory plans of the sweep and measurement kernels for group size GS.
+GroupLayout group_layout_rm(const vmcf_system_s& s, int GS);
+GroupLayout group_layout_meas(const vmcf_system_s& s, int GS);
+constexpr int kSmemCapBytes = 227 * 1024;
 int set_last_error(int code, const std::string& msg);
 }  // namespace vmcf

@@ -113,6 +113,44 @@ cudaError_t launch_tc_sumprod(const void* phiT_up, const void* phiT_dn, const vo
 cudaError_t launch_tc_fold(const double* slots, int nblocks, int cpb, int Mp, int Np, int M, int n_up, int n_dn,
                            int oo, int nO, int accL, double* blocks, cudaStream_t st);
 
+// ---- ragged batch of geometries (k_batch.cu): one persistent kernel per launch shape
+// Everything a walker group needs to work on one geometry; copied into the group's shared
+// memory when it switches geometry.
+struct BatchGeom {
+  DevSys S;
+  GroupLayout Lrm, Lmeas;
+  MoveParams P;   // walker state; sweep0, c0, nsweeps, kref, skip_final_refresh and sigma set per launch
+  MeasParams Mp;  // accumulator slots [grid_meas][accL]; acc_in_smem = 0
+  int grid_meas;  // slot c holds walkers [W c / grid_meas, W (c + 1) / grid_meas)
+  int pad_;
+};
+
+// Per-geometry chain clock: global sweep index and moves since the last refresh.
+struct BatchClock {
+  unsigned long long sweep;
+  int c;
+  int Ne;
+};
+
+struct BatchArgs {
+  const BatchGeom* geo;
+  const BatchClock* clk;
+  const int2* items;  // (geometry, slot) in processing order
+  int n_items;
+  int* queue;         // next item index (reset to 0 after each sweep)
+  int mode;           // 0 moves only, 1 moves + measurement into the slots, 2 moves + measurement without sums
+  int kref;
+  double sigma;
+  int region;         // bytes of shared memory per walker group (header + working set)
+  int hdr;            // header bytes (geometry copy and the group's scalars) at the start of a region
+};
+
+template <typename T>
+cudaError_t launch_batch(int GS, int groups, int grid, size_t smem, const BatchArgs& A, cudaStream_t st);
+template <typename T>
+cudaError_t batch_occupancy(int GS, int groups, size_t smem, int* ctas_per_sm);
+cudaError_t launch_batch_advance(BatchClock* clk, int G, int mode, int kref, int* queues, int nq, cudaStream_t st);
+
 cudaError_t run_probes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, cudaStream_t st);
 
 cudaError_t launch_block_reduce(const double* acc, int grid, int cpb, int accL, double* out, int nblocks,

@@ -289,9 +289,10 @@ def make_system(cfg: int) -> System:
     return make_molecule(name, Z, R, _rng(base, 1), _rng(base, 2))
 
 
-def make_ragged_batch(n_geom: int = 64, seed: int = 3):
-    """Ragged batch: n_geom covalent-walk molecules of 3..21 H/C/O nuclei, an even electron
-    count in [10, 94], and 512..4096 walkers each (multiple of 128)."""
+def ragged_batch_plan(n_geom: int = 64, seed: int = 3) -> list[tuple[list[int], int]]:
+    """Compositions and walker counts of the ragged batch, without building the molecules:
+    n_geom lists of 3..21 H/C/O nuclear charges (a C or O first) with an even electron count
+    in [10, 94], and 512..4096 walkers each (multiple of 128)."""
     rng = np.random.default_rng([GEN_SEED_BASE + seed, 0])
     out = []
     while len(out) < n_geom:
@@ -300,12 +301,24 @@ def make_ragged_batch(n_geom: int = 64, seed: int = 3):
         ne = sum(Z)
         if ne % 2 or not (10 <= ne <= 94):
             continue
-        g = len(out)
+        W = int(rng.integers(512, 4097)) // 128 * 128
+        out.append((Z, max(W, 512)))
+    return out
+
+
+def make_ragged_batch(n_geom: int = 64, seed: int = 3, only=None):
+    """Ragged batch: n_geom covalent-walk molecules of 3..21 H/C/O nuclei, an even electron
+    count in [10, 94], and 512..4096 walkers each (multiple of 128). Returns (System, W) per
+    geometry; with `only` (indices), just those geometries, in index order."""
+    plan = ragged_batch_plan(n_geom, seed)
+    out = []
+    for g, (Z, W) in enumerate(plan):
+        if only is not None and g not in only:
+            continue
         R = covalent_walk(Z, np.random.default_rng([GEN_SEED_BASE + seed, 1, g]))
         sys = make_molecule(f"ragged{g}", Z, R, np.random.default_rng([GEN_SEED_BASE + seed, 2, g]),
                             np.random.default_rng([GEN_SEED_BASE + seed, 3, g]))
-        W = int(rng.integers(512, 4097)) // 128 * 128
-        out.append((sys, max(W, 512)))
+        out.append((sys, W))
     return out
 
 

@@ -91,6 +91,13 @@ def lib(build_if_missing: bool = True):
         L.vmcf_set_tuning.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int]
         L.vmcf_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
         L.vmcf_probe_pipes.argtypes = [_dp, _dp, _dp, _vp]
+        L.vmcf_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp,
+                                        ctypes.POINTER(_vp)]
+        L.vmcf_batch_destroy.argtypes = [_vp]
+        L.vmcf_batch_autotune.argtypes = [_vp, ctypes.c_double, ctypes.c_int, _vp]
+        L.vmcf_batch_set_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.vmcf_batch_sample.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp]
+        L.vmcf_batch_info.argtypes = [_vp, _ip, _ip, ctypes.c_int, _ip, _ip, _ip]
         _lib = L
     return _lib
 
@@ -288,3 +295,55 @@ def vmcf_probe_pipes(stream=None) -> dict:
     _check(lib().vmcf_probe_pipes(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _stream(stream)),
            "vmcf_probe_pipes")
     return {"fp64_tflops": a.value, "fp32_tflops": b.value, "exp_gops": c.value}
+
+
+class Batch:
+    """vmcf_batch_create: a ragged batch of geometries, each a (System, Walkers) pair whose
+    system was created with force_group=True; every sweep of the whole batch is one replay of
+    a captured CUDA graph of persistent kernels. Each Walkers object keeps its own sums."""
+
+    def __init__(self, systems, walkers, stream=None):
+        L = lib()
+        G = len(systems)
+        if G != len(walkers) or G == 0:
+            raise ValueError("need one walker set per system")
+        self.systems, self.walkers = list(systems), list(walkers)
+        hs = (_vp * G)(*[s.h for s in systems])
+        hw = (_vp * G)(*[w.h for w in walkers])
+        out = _vp()
+        _check(L.vmcf_batch_create(hs, hw, G, _stream(stream), ctypes.byref(out)), "vmcf_batch_create")
+        self.h = out
+        self.G = G
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vmcf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, step_sigma: float = 0.3, refresh_k: int = 26, stream=None):
+        _check(lib().vmcf_batch_autotune(self.h, float(step_sigma), int(refresh_k), _stream(stream)),
+               "vmcf_batch_autotune")
+
+    def set_shape(self, g: int, GS: int, groups: int):
+        _check(lib().vmcf_batch_set_shape(self.h, int(g), int(GS), int(groups)), "vmcf_batch_set_shape")
+
+    def sample(self, n_sweeps: int, step_sigma: float = 0.3, refresh_k: int = 26, measure: bool = False,
+               stream=None):
+        _check(lib().vmcf_batch_sample(self.h, int(n_sweeps), float(step_sigma), int(refresh_k),
+                                       int(bool(measure)), _stream(stream)), "vmcf_batch_sample")
+
+    def info(self) -> dict:
+        nb, nl = ctypes.c_int(), ctypes.c_int()
+        geo = []
+        for g in range(self.G):
+            b, gs, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+            _check(lib().vmcf_batch_info(self.h, ctypes.byref(nb), ctypes.byref(nl), g, ctypes.byref(b),
+                                         ctypes.byref(gs), ctypes.byref(gr)), "vmcf_batch_info")
+            geo.append({"bucket": b.value, "GS": gs.value, "groups": gr.value})
+        return {"buckets": nb.value, "launches": nl.value, "geometries": geo}

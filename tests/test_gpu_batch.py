@@ -1,0 +1,150 @@
+"""Ragged batches of geometries (vmcf_batch_*): every sweep of several molecules of different
+sizes is one replay of a captured graph of persistent kernels. Batching must not change any
+walker's chain or contribution: positions follow the single-geometry path and the oracle's
+Markov chain, and the per-geometry walker sums give the same estimators."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import estimators
+from paper_2511_05222_gb300 import systems as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2511_05222_gb300 import vmcf  # noqa: E402
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    """Water plus the first three covalent-walk molecules of the ragged-batch generator: 10,
+    38, 76 and 42 electrons, 24 to 174 AOs; the 76-electron one runs with 128 threads per
+    walker."""
+    rb = S.make_ragged_batch(3)
+    return [(S.make_system(0), 96)] + [(s, W) for s, W in rb]
+
+
+def _walkers(systems, specs, seed0, nb=4):
+    out = []
+    for g, (sx, W) in enumerate(specs):
+        pos = S.initial_walkers(sx, W, seed=seed0 + g)
+        out.append(vmcf.Walkers(systems[g], pos, key=(5222, 300 + g), nblocks=nb))
+    return out
+
+
+@pytest.mark.parametrize("precision", [vmcf.FP64, vmcf.MIXED])
+def test_batch_follows_the_single_geometry_path(ragged, precision):
+    """Same chains and sums as vmcf_sample on each walker set alone (positions bit for bit;
+    walker sums to rounding: FP64 1e-12, mixed 1e-5 since the single path sums in FP32 shared
+    memory before its FP64 slots)."""
+    specs = [(sx, W) for (sx, _), W in zip(ragged, (64, 40, 56, 24))]
+    systems = [vmcf.System(sx, precision, force_group=True) for sx, _ in specs]
+    wa = _walkers(systems, specs, 20)
+    wb = _walkers(systems, specs, 20)
+    batch = vmcf.Batch(systems, wa)
+    info = batch.info()
+    assert info["buckets"] == 3 and info["launches"] >= 2  # the 38- and 42-electron molecules share one
+    assert info["geometries"][2]["GS"] == 128
+    e_ref = [-76.0, -150.0, -160.0, -300.0]
+    batch.sample(3, measure=False)
+    for g, w in enumerate(wa):
+        w.reset_accumulators(e_ref[g])
+        wb[g].sample(3, measure=False)
+        wb[g].reset_accumulators(e_ref[g])
+    batch.sample(2, measure=True)
+    batch.sample(1, measure=True)  # a second call replays the same graph from the uploaded clocks
+    for w in wb:
+        w.sample(3, measure=True)
+    tol = 1e-12 if precision == vmcf.FP64 else 1e-5
+    for g in range(len(specs)):
+        np.testing.assert_array_equal(wa[g].positions(), wb[g].positions())
+        ca, cb = wa[g].counters(), wb[g].counters()
+        assert ca["accepted"] == cb["accepted"] and ca["moves"] == cb["moves"]
+        sa, sb = wa[g].block_sums(), wb[g].block_sums()
+        np.testing.assert_array_equal(sa[:, 0], sb[:, 0])
+        assert rel(sa, sb) < tol, (g, rel(sa, sb))
+        ea, eb = wa[g].reduce_estimators(), wb[g].reduce_estimators()
+        assert abs(ea["E"] - eb["E"]) <= tol * abs(eb["E"])
+        assert np.all(np.abs(ea["F"] - eb["F"]) <= 0.01 * eb["F_err"] + 1e-12)
+
+
+def test_batch_estimators_match_the_oracle(ragged):
+    """The water geometry inside a ragged FP64 batch: chain and estimators as the oracle's."""
+    specs = [(ragged[0][0], 128), (ragged[1][0], 32), (ragged[2][0], 16)]
+    sys0 = specs[0][0]
+    W, nb, warm, meas, e_ref = 128, 8, 3, 3, -76.0
+    systems = [vmcf.System(sx, vmcf.FP64, force_group=True) for sx, _ in specs]
+    pos = S.initial_walkers(sys0, W, seed=10)
+    wk = [vmcf.Walkers(systems[0], pos, key=(5222, 0), nblocks=nb)]
+    wk += [vmcf.Walkers(systems[g], S.initial_walkers(specs[g][0], specs[g][1], seed=g), key=(5222, 9 + g),
+                        nblocks=4) for g in (1, 2)]
+    batch = vmcf.Batch(systems, wk)
+    o = oracle.Oracle(sys0)
+    st = o.new_state(pos, key=(5222, 0))
+    o.sample(st, warm)
+    batch.sample(warm, measure=False)
+    for g, w in enumerate(wk):
+        w.reset_accumulators(e_ref if g == 0 else -100.0)
+    batch.sample(meas, measure=True)
+    sums = estimators.new_sums(nb, sys0.K, o.nO)
+    blk = np.zeros(W, dtype=np.int64)
+    for b in range(nb):
+        blk[(W * b) // nb:(W * (b + 1)) // nb] = b
+    for _ in range(meas):
+        o.sample(st, 1)
+        o.force_refresh(st)
+        out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+        estimators.accumulate(sums, blk, out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], e_ref)
+    assert st["margin"].min() >= 1e-9
+    assert np.abs(wk[0].positions() - st["pos"]).max() < 1e-9
+    ref = estimators.finish(sums, e_ref)
+    got = wk[0].reduce_estimators()
+    assert abs(got["E"] - ref["E"]) < 1e-10 * abs(ref["E"])
+    assert rel(got["F"].ravel(), ref["F"]) < 1e-9
+    assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
+    assert abs(got["E_err"] - ref["E_err"]) < 1e-8 * ref["E_err"]
+
+
+def test_launch_shape_and_autotuning_leave_the_chains_unchanged(ragged):
+    """Two batches over identical walker sets: one autotuned, one with every bucket forced to
+    one walker group of 128 threads per CTA. Autotuning runs the same number of sweeps
+    whatever it picks, and no shape changes a chain beyond FP64 rounding."""
+    specs = [(sx, W) for (sx, _), W in zip(ragged, (64, 40, 48, 24))]
+    systems = [vmcf.System(sx, vmcf.FP64, force_group=True) for sx, _ in specs]
+    wa = _walkers(systems, specs, 40)
+    wb = _walkers(systems, specs, 40)
+    ba = vmcf.Batch(systems, wa)
+    bb = vmcf.Batch(systems, wb)
+    ba.autotune()
+    bb.autotune()
+    for g in range(len(specs)):
+        bb.set_shape(g, 128, 1)
+    info = ba.info()
+    for geo in info["geometries"]:
+        assert geo["GS"] in (32, 128) and geo["groups"] in (1, 2, 4)
+    for w in wa + wb:
+        w.reset_accumulators(-100.0)
+    ba.sample(2, measure=True)
+    bb.sample(2, measure=True)
+    for g in range(len(specs)):
+        assert np.abs(wa[g].positions() - wb[g].positions()).max() < 1e-12
+        assert wa[g].counters()["accepted"] == wb[g].counters()["accepted"]
+        assert rel(wa[g].block_sums(), wb[g].block_sums()) < 1e-11
+
+
+def test_batch_rejects_small_path_systems_and_mixed_precisions(ragged):
+    s_small = vmcf.System(ragged[0][0], vmcf.FP64)  # qualifies for the small-system kernels
+    w_small = vmcf.Walkers(s_small, S.initial_walkers(ragged[0][0], 16, seed=1), nblocks=2)
+    with pytest.raises(vmcf.VmcfError):
+        vmcf.Batch([s_small], [w_small])
+    a = vmcf.System(ragged[0][0], vmcf.FP64, force_group=True)
+    b = vmcf.System(ragged[1][0], vmcf.MIXED, force_group=True)
+    wa = vmcf.Walkers(a, S.initial_walkers(ragged[0][0], 16, seed=1), nblocks=2)
+    wb = vmcf.Walkers(b, S.initial_walkers(ragged[1][0], 16, seed=1), nblocks=2)
+    with pytest.raises(vmcf.VmcfError):
+        vmcf.Batch([a, b], [wa, wb])
