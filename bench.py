@@ -266,7 +266,7 @@ def run_ragged(args, wl):
                                        c["accepted"] / max(1, c["moves"]))
         t_roof += W * workmodel.roofline_time(wk["total"], peaks)[1]
     info = batch.info()
-    shapes = sorted({(gi["GS"], gi["groups"]) for gi in info["geometries"]})
+    shapes = {ph: sorted({gi[ph] for gi in info["geometries"]}) for ph in ("sweep", "evaluation")}
     line = {"metric": METRIC, "value": value, "unit": "walker-evals/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -275,7 +275,7 @@ def run_ragged(args, wl):
                        "precision": "mixed (FP32 + FP64 inverse/ratio/sums)",
                        "l2": "flushed (256 MB write) between timed steps",
                        "buckets": info["buckets"], "persistent_kernels_per_sweep": info["launches"],
-                       "launch_shapes": [f"{a}x{b}" for a, b in shapes]},
+                       "launch_shapes": {ph: [f"{a}x{b}" for a, b in v] for ph, v in shapes.items()}},
             "roofline": {"bound": "alu", "pipe": "whole step, per geometry", "frac": t_roof * ws / (ms * 1e-3 / args.steps)
                          if ws == 1 else None, "peak_source": "measured in this run by vmcf_probe_pipes"},
             "gpu_launches": args.steps * (info["launches"] + 1), "clocks": clk.summary(),

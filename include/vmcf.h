@@ -176,6 +176,20 @@ int vmcf_accumulator_length(vmcf_system_t sys);
 int vmcf_finish_estimators(const double* blocks, int nblocks, int K, int M, int n_up, int n_dn, double e_ref,
                            double* E, double* E_err, double* F, double* F_err, double* dEdC, double* dEdC_err);
 
+/* Host-only covariance of the estimators, as the low-rank factor that the error propagation
+ * through the Z-vector equations needs (App. "Error propagation": Var(F^c) = R^T G Cov(B) G^T R,
+ * with Cov(B) = b b^T for a factor b with few columns). From block sums in the vmcf_block_sums
+ * layout, with theta_k the estimate that leaves block k out (k < nblocks) and theta-bar their
+ * mean, the delete-one-block jackknife covariance is
+ *   Cov = (nb - 1)/nb sum_k (theta_k - theta-bar)(theta_k - theta-bar)^T = b b^T,
+ *   b[i][k] = sqrt((nb - 1)/nb) (theta_k[i] - theta-bar[i]),
+ * so diag(b b^T) is the square of the error bars of vmcf_finish_estimators. Outputs (any may be
+ * NULL): F_factor host [3K][nblocks] for the forces, B_factor host [nO][nblocks] for dE/dC, with
+ * nO = M (n_up + n_dn) in the dEdC order. Blocks of several ranks placed side by side give the
+ * factor of the combined estimate. */
+int vmcf_finish_covariance(const double* blocks, int nblocks, int K, int M, int n_up, int n_dn, double e_ref,
+                           double* F_factor, double* B_factor);
+
 /* Counters (synchronises the stream). */
 int vmcf_status_counters(vmcf_walkers_t wk, vmcf_counters* out, void* stream);
 
@@ -227,51 +241,53 @@ int vmcf_probe_pipes(double* fp64_tflops, double* fp32_tflops, double* exp_gops,
 
 /* ---- Ragged batches of geometries.
  * Many independent geometries (different nuclei, electron and AO counts, walker counts) are
- * sampled together: each VMC sweep of the whole batch is one replay of a captured CUDA
- * graph that holds one persistent kernel per launch shape, plus a one-thread-block clock
- * kernel. Walker groups in the persistent kernels pull work items (one geometry, one range of
- * its walkers) from a device queue, longest first, so that small and large geometries share
- * the SMs; per walker a group runs the Metropolis sweep and, when measuring, the full
- * evaluation (E_L, forces, O) right after it. The method per walker is exactly that of
- * vmcf_sample (App. A, the MCMC sampling and the estimators of Eqs. hf, pulay and
- * fc-vmc-eval); batching changes neither a walker's chain nor its contributions, only where
- * and when they are computed. The paper batches nothing across geometries: this is the
- * deployment form for many molecules (or many displaced geometries) at once.
+ * sampled together: each VMC sweep of the whole batch is one replay of a captured CUDA graph
+ * with two phases, the Metropolis sweep of every walker and (when measuring) the evaluation
+ * of every walker (E_L, forces, O, walker sums). Each phase is one persistent kernel per
+ * launch shape, run side by side; a one-thread-block kernel then advances the chain clocks.
+ * Walker groups in the persistent kernels pull work items (one geometry, one range of its
+ * walkers) from a device queue, longest first, so that small and large geometries share the
+ * SMs. The method per walker is exactly that of vmcf_sample (App. A, the MCMC sampling and
+ * the estimators of Eqs. hf, pulay and fc-vmc-eval); batching changes neither a walker's chain
+ * nor its contributions, only where and when they are computed. The paper batches nothing
+ * across geometries: this is the deployment form for many molecules (or many displaced
+ * geometries) at once.
  *
  * vmcf_batch_create: systems[g], walkers[g] for g < G: each walker set belongs to its system;
  *   every system has the same precision and runs on the walker-group kernels (systems that
  *   qualify for the small-system kernels must be created with VMCF_FORCE_GROUP_PATH), else
  *   VMCF_ENOTSUP. The batch keeps the handles (the caller keeps ownership and must keep them
  *   alive until vmcf_batch_destroy) and allocates its own device tables. Geometries are put in
- *   buckets by (ceil(Ne / 16), ceil(M / 64)); every bucket starts with the default launch
- *   shape (32 threads per walker while n_up, n_dn <= 24, else 128; as many walker groups per
- *   CTA, up to 4, as fit shared memory). Synchronises `stream`.
- * vmcf_batch_autotune: for every bucket, time one sweep-plus-evaluation of the bucket's walkers
- *   with each feasible launch shape (threads per walker 32 or 128, walker groups per CTA 1, 2
- *   or 4) and keep the fastest; also records each geometry's measured cost for the
- *   longest-first order. Every timed sweep is a real sweep of the bucket's chains followed by
- *   a fresh inversion, exactly as vmcf_sample(..., measure = 0) plus an evaluation whose sums
- *   are discarded: call it during equilibration. Synchronises `stream`.
- * vmcf_batch_set_shape: force the launch shape of the bucket that holds geometry g
- *   (GS = 32 or 128 threads per walker, groups = walker groups per CTA); VMCF_EINVAL if it
- *   does not fit shared memory.
+ *   buckets by (ceil(Ne / 16), ceil(M / 64)); every bucket starts, per phase, with the default
+ *   launch shape (32 threads per walker while n_up, n_dn <= 24, with as many walker groups per
+ *   CTA, up to 4, as fit shared memory; else 128 threads per walker for the sweep and 256 for
+ *   the evaluation). Synchronises `stream`.
+ * vmcf_batch_autotune: for every bucket and phase, time one sweep (phase 0) or one evaluation
+ *   (phase 1) of the bucket's walkers with each feasible launch shape (threads per walker x
+ *   walker groups per CTA: 32 x 1, 2, 4, 8; 128 x 1, 2; 256 x 1) and keep the fastest; also
+ *   records each geometry's measured cost for the longest-first order. The timed sweeps are
+ *   real sweeps of the chains (as vmcf_sample with measure = 0) and the timed evaluations
+ *   rebuild the inverses and discard their sums: call it during equilibration. Synchronises
+ *   `stream`.
+ * vmcf_batch_set_shape: force the launch shape of `phase` (0 sweep, 1 evaluation) for the
+ *   bucket that holds geometry g; VMCF_EINVAL if unsupported or too large for shared memory.
  * vmcf_batch_sample: n_sweeps sweeps of every geometry, as vmcf_sample on each walker set
  *   (same arguments and meaning; measure != 0 adds each sweep's evaluation to each walker
  *   set's sums, read with vmcf_reduce_estimators / vmcf_block_sums on that walker set).
  *   The first call with a given (measure, refresh_k, step_sigma) captures the graph; later
  *   calls replay it. Asynchronous on `stream`.
- * vmcf_batch_info: number of buckets and of persistent kernels per sweep, and for geometry g
- *   (if 0 <= g < G) its bucket and launch shape; any output may be NULL. */
+ * vmcf_batch_info: number of buckets and of persistent kernels per measured sweep; for
+ *   geometry g (if 0 <= g < G) its bucket and shapes[4] = {sweep GS, sweep groups per CTA,
+ *   evaluation GS, evaluation groups per CTA}; any output may be NULL. */
 typedef struct vmcf_batch_s* vmcf_batch_t; /* opaque, library-owned */
 int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walkers, int G, void* stream,
                       vmcf_batch_t* out);
 int vmcf_batch_destroy(vmcf_batch_t batch);
 int vmcf_batch_autotune(vmcf_batch_t batch, double step_sigma, int refresh_k, void* stream);
-int vmcf_batch_set_shape(vmcf_batch_t batch, int g, int GS, int groups);
+int vmcf_batch_set_shape(vmcf_batch_t batch, int g, int phase, int GS, int groups);
 int vmcf_batch_sample(vmcf_batch_t batch, int n_sweeps, double step_sigma, int refresh_k, int measure,
                       void* stream);
-int vmcf_batch_info(vmcf_batch_t batch, int* n_buckets, int* n_launches, int g, int* bucket, int* GS,
-                    int* groups);
+int vmcf_batch_info(vmcf_batch_t batch, int* n_buckets, int* n_launches, int g, int* bucket, int* shapes);
 
 const char* vmcf_strerror(int status);
 const char* vmcf_last_error(void);

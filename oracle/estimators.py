@@ -73,3 +73,19 @@ def finish(sums: dict, e_ref: float):
     err = lambda a: np.sqrt(f * ((a - a.mean(axis=0)) ** 2).sum(axis=0))
     return {"E": E, "E_err": err(Ej), "F": F, "F_err": err(Fj), "dEdC": B, "dEdC_err": err(Bj),
             "var_EL": tot["sE2"] / tot["n"] - E * E}
+
+
+def jackknife_covariance(sums: dict, e_ref: float):
+    """Delete-one-block jackknife covariance matrices of the forces and of B = dE/dC (the
+    Cov(B) of the error-propagation appendix, "Error propagation"):
+    Cov = (nb - 1)/nb sum_b (theta_b - mean)(theta_b - mean)^T over the leave-one-out
+    estimates theta_b. Returns (Cov_F [3K][3K], Cov_B [nO][nO])."""
+    tot = {k: v.sum(axis=0) for k, v in sums.items()}
+    nb = sums["n"].shape[0]
+    jk = [_estimate({k: tot[k] - sums[k][b] for k in FIELDS}, e_ref) for b in range(nb)]
+    out = []
+    for idx in (1, 2):
+        th = np.array([x[idx] for x in jk])
+        d = th - th.mean(axis=0)
+        out.append((nb - 1) / nb * d.T @ d)
+    return out[0], out[1]

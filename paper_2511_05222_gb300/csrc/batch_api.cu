@@ -1,5 +1,6 @@
-// Host side of the ragged-batch entry points (vmcf_batch_*): buckets, launch shapes, the
-// autotuner, the longest-first work order and the captured sweep graph.
+// Host side of the ragged-batch entry points (vmcf_batch_*): buckets, launch shapes per
+// phase (Metropolis sweep, evaluation), the autotuner, the longest-first work order and the
+// captured sweep graph.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -39,6 +40,7 @@ struct Shape {
 };
 
 struct LaunchPlan {
+  int phase = 0;  // 0 Metropolis sweep, 1 evaluation
   Shape shape;
   int grid = 1;
   size_t smem = 0;
@@ -52,10 +54,11 @@ struct vmcf_batch_s {
   int G = 0, precision = 0, sms = 1;
   std::vector<vmcf_system_s*> sys;
   std::vector<vmcf_walkers_s*> wk;
-  std::vector<int> bucket;           // per geometry
-  std::vector<Shape> bucket_shape;   // per bucket
-  std::vector<double> cost;          // per geometry: relative cost of one walker-sweep
-  std::vector<LaunchPlan> launches;
+  std::vector<int> bucket;              // per geometry
+  std::vector<Shape> bucket_shape[2];   // per phase, per bucket
+  std::vector<double> cost[2];          // per phase, per geometry: relative cost of one walker
+  std::vector<LaunchPlan> launches;     // phase-0 launches first
+  int n_launch[2] = {0, 0};
   std::vector<BatchGeom> h_geo;
   std::vector<BatchClock> h_clk;
   BatchGeom* d_geo = nullptr;
@@ -76,67 +79,73 @@ struct vmcf_batch_s {
 
 namespace {
 
-int tsize(const vmcf_batch_s& b) { return b.precision == VMCF_FP64 ? 8 : 4; }
-
-// Bytes of one walker group's region for geometry g at group size GS.
-int region_bytes(const vmcf_batch_s& b, int g, int GS) {
-  const GroupLayout a = group_layout_rm(*b.sys[g], GS), m = group_layout_meas(*b.sys[g], GS);
-  return kHdr + align16(std::max(a.bytes, m.bytes));
+// Bytes of one walker group's region for geometry g in `phase` at group size GS.
+int region_bytes(const vmcf_batch_s& b, int phase, int g, int GS) {
+  const GroupLayout L = phase == 0 ? group_layout_rm(*b.sys[g], GS) : group_layout_meas(*b.sys[g], GS);
+  return kHdr + align16(L.bytes);
 }
 
-int bucket_region(const vmcf_batch_s& b, int bk, int GS) {
+int bucket_region(const vmcf_batch_s& b, int phase, int bk, int GS) {
   int r = 0;
   for (int g = 0; g < b.G; ++g)
-    if (b.bucket[g] == bk) r = std::max(r, region_bytes(b, g, GS));
+    if (b.bucket[g] == bk) r = std::max(r, region_bytes(b, phase, g, GS));
   return r;
 }
 
-int occupancy(const vmcf_batch_s& b, const Shape& sh, size_t smem, int* ctas) {
-  cudaError_t e = b.precision == VMCF_FP64 ? batch_occupancy<double>(sh.GS, sh.groups, smem, ctas)
-                                           : batch_occupancy<float>(sh.GS, sh.groups, smem, ctas);
+int occupancy(const vmcf_batch_s& b, int phase, const Shape& sh, size_t smem, int* ctas) {
+  cudaError_t e = b.precision == VMCF_FP64 ? batch_occupancy<double>(phase, sh.GS, sh.groups, smem, ctas)
+                                           : batch_occupancy<float>(phase, sh.GS, sh.groups, smem, ctas);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the batch kernel");
   return VMCF_OK;
 }
 
-bool shape_fits(const vmcf_batch_s& b, int bk, const Shape& sh) {
-  if (!((sh.GS == 32 && (sh.groups == 1 || sh.groups == 2 || sh.groups == 4)) || (sh.GS == 128 && sh.groups == 1)))
-    return false;
-  return (size_t)sh.groups * bucket_region(b, bk, sh.GS) <= (size_t)kSmemCapBytes;
+// Shapes the batch kernels support: 32 threads x 1, 2, 4 or 8 groups, 128 x 1 or 2, 256 x 1.
+bool shape_supported(const Shape& sh) {
+  return (sh.GS == 32 && (sh.groups == 1 || sh.groups == 2 || sh.groups == 4 || sh.groups == 8)) ||
+         (sh.GS == 128 && (sh.groups == 1 || sh.groups == 2)) || (sh.GS == 256 && sh.groups == 1);
 }
 
-Shape default_shape(const vmcf_batch_s& b, int bk) {
+bool shape_fits(const vmcf_batch_s& b, int phase, int bk, const Shape& sh) {
+  if (!shape_supported(sh)) return false;
+  return (size_t)sh.groups * bucket_region(b, phase, bk, sh.GS) <= (size_t)kSmemCapBytes;
+}
+
+const Shape kCandidates[] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {128, 1}, {128, 2}, {256, 1}};
+
+// Default shape: the single-geometry plan's group size (32 threads while n_up, n_dn <= 24;
+// else 128 for sweeps and 256 for evaluations), as many groups per CTA as fit (up to 4).
+Shape default_shape(const vmcf_batch_s& b, int phase, int bk) {
   int nmax = 0;
   for (int g = 0; g < b.G; ++g)
     if (b.bucket[g] == bk) nmax = std::max(nmax, b.sys[g]->nmax);
-  Shape sh;
-  sh.GS = nmax <= 24 ? 32 : 128;
-  sh.groups = 1;
+  Shape sh{nmax <= 24 ? 32 : (phase == 0 ? 128 : 256), 1};
   if (sh.GS == 32)
     for (int gr : {4, 2}) {
-      Shape t{32, gr};
-      if (shape_fits(b, bk, t)) {
+      const Shape t{32, gr};
+      if (shape_fits(b, phase, bk, t)) {
         sh = t;
         break;
       }
     }
-  if (!shape_fits(b, bk, sh)) sh = Shape{128, 1};
+  if (!shape_fits(b, phase, bk, sh)) sh = Shape{128, 1};
   return sh;
 }
 
-// Relative cost of one walker-sweep with evaluation, from the operation counts of the
-// method: AO/MO rows per move and per evaluation, inversions, Jastrow pairs.
-double heuristic_cost(const vmcf_system_s& s) {
+// Relative cost of one walker-sweep (phase 0) or evaluation (phase 1), from the operation
+// counts of the method: AO/MO rows per move and per evaluation, inversions, Jastrow pairs.
+double heuristic_cost(const vmcf_system_s& s, int phase) {
   const double Ne = s.Ne, M = s.M, n = s.nmax, K = s.K;
-  return Ne * (3.0 * M * n + 30.0 * M) + 4.0 * n * n * n * (1.0 + Ne / 26.0) + 60.0 * Ne * (Ne + K);
+  if (phase == 0) return Ne * (2.0 * M * n + 4.0 * n * n + 30.0 * (Ne + K)) + (Ne / 26.0) * (Ne * M * n + 4.0 * n * n * n);
+  return Ne * (12.0 * M * n + 40.0 * M) + 4.0 * n * n * n + 60.0 * Ne * (Ne + K);
 }
 
-void fill_geo(vmcf_batch_s& b, int g, int GS) {
+void fill_geo(vmcf_batch_s& b, int g) {
   const vmcf_system_s& s = *b.sys[g];
   const vmcf_walkers_s& w = *b.wk[g];
   BatchGeom G{};
   G.S = s.dev;
-  G.Lrm = group_layout_rm(s, GS);
-  G.Lmeas = group_layout_meas(s, GS);
+  G.Lrm = group_layout_rm(s, b.bucket_shape[0][b.bucket[g]].GS);
+  G.Lmeas = group_layout_meas(s, b.bucket_shape[1][b.bucket[g]].GS);
   G.P.pos = w.pos;
   G.P.B = w.B;
   G.P.nacc = w.nacc;
@@ -164,44 +173,49 @@ void invalidate_graph(vmcf_batch_s& b) {
   b.g_mode = -1;
 }
 
-// Launch list and work order for the current bucket shapes, restricted to the geometries
-// with take[g] (all when take is empty). Items of one launch are ordered by the cost of the
-// walkers they hold, largest first.
-int build_plan(vmcf_batch_s& b, const std::vector<char>& take, cudaStream_t st) {
-  std::map<Shape, std::vector<int>> by_shape;
-  for (int g = 0; g < b.G; ++g)
-    if (take.empty() || take[g]) by_shape[b.bucket_shape[b.bucket[g]]].push_back(g);
+// Launch list and work order for the current bucket shapes, for the phases in `phases`
+// (bit 0: sweep, bit 1: evaluation) and the geometries with take[g] (all when take is
+// empty). Items of one launch are ordered by the cost of the walkers they hold, largest first.
+int build_plan(vmcf_batch_s& b, const std::vector<char>& take, int phases, cudaStream_t st) {
   std::vector<int2> items;
   b.launches.clear();
-  for (auto& kv : by_shape) {
-    LaunchPlan lp;
-    lp.shape = kv.first;
-    int region = 0;
-    for (int g : kv.second) region = std::max(region, region_bytes(b, g, lp.shape.GS));
-    lp.region = region;
-    lp.smem = (size_t)lp.shape.groups * region;
-    if (lp.smem > (size_t)kSmemCapBytes) return fail(VMCF_ENOTSUP, "batch launch shape does not fit shared memory");
-    std::vector<std::pair<double, int2>> its;
-    for (int g : kv.second) {
-      fill_geo(b, g, lp.shape.GS);
-      const vmcf_walkers_s& w = *b.wk[g];
-      for (int c = 0; c < w.grid_meas; ++c) {
-        const long long n = (long long)w.W * (c + 1) / w.grid_meas - (long long)w.W * c / w.grid_meas;
-        its.push_back({b.cost[g] * (double)n, make_int2(g, c)});
+  b.n_launch[0] = b.n_launch[1] = 0;
+  for (int g = 0; g < b.G; ++g) fill_geo(b, g);
+  for (int phase = 0; phase < 2; ++phase) {
+    if (!(phases & (1 << phase))) continue;
+    std::map<Shape, std::vector<int>> by_shape;
+    for (int g = 0; g < b.G; ++g)
+      if (take.empty() || take[g]) by_shape[b.bucket_shape[phase][b.bucket[g]]].push_back(g);
+    for (auto& kv : by_shape) {
+      LaunchPlan lp;
+      lp.phase = phase;
+      lp.shape = kv.first;
+      int region = 0;
+      for (int g : kv.second) region = std::max(region, region_bytes(b, phase, g, lp.shape.GS));
+      lp.region = region;
+      lp.smem = (size_t)lp.shape.groups * region;
+      if (lp.smem > (size_t)kSmemCapBytes) return fail(VMCF_ENOTSUP, "batch launch shape does not fit shared memory");
+      std::vector<std::pair<double, int2>> its;
+      for (int g : kv.second) {
+        const vmcf_walkers_s& w = *b.wk[g];
+        for (int c = 0; c < w.grid_meas; ++c) {
+          const long long n = (long long)w.W * (c + 1) / w.grid_meas - (long long)w.W * c / w.grid_meas;
+          its.push_back({b.cost[phase][g] * (double)n, make_int2(g, c)});
+        }
       }
+      std::stable_sort(its.begin(), its.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+      lp.item0 = (int)items.size();
+      lp.n_items = (int)its.size();
+      for (auto& it : its) items.push_back(it.second);
+      int ctas = 0;
+      int rc = occupancy(b, phase, lp.shape, lp.smem, &ctas);
+      if (rc != VMCF_OK) return rc;
+      if (ctas < 1) return fail(VMCF_ENOTSUP, "batch kernel cannot be resident with this launch shape");
+      const long long grid_full = (long long)ctas * b.sms;
+      lp.grid = (int)std::max(1LL, std::min(grid_full, ((long long)lp.n_items + lp.shape.groups - 1) / lp.shape.groups));
+      b.launches.push_back(lp);
+      b.n_launch[phase] += 1;
     }
-    std::stable_sort(its.begin(), its.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-    lp.item0 = (int)items.size();
-    lp.n_items = (int)its.size();
-    for (auto& it : its) items.push_back(it.second);
-    int ctas = 0;
-    int rc = occupancy(b, lp.shape, lp.smem, &ctas);
-    if (rc != VMCF_OK) return rc;
-    if (ctas < 1) return fail(VMCF_ENOTSUP, "batch kernel cannot be resident with this launch shape");
-    const long long groups_needed = lp.n_items;
-    const long long grid_full = (long long)ctas * b.sms;
-    lp.grid = (int)std::max(1LL, std::min(grid_full, (groups_needed + lp.shape.groups - 1) / lp.shape.groups));
-    b.launches.push_back(lp);
   }
   if (items.size() > b.items_cap) {
     cudaFree(b.d_items);
@@ -218,7 +232,7 @@ int build_plan(vmcf_batch_s& b, const std::vector<char>& take, cudaStream_t st) 
   if (!items.empty())
     BATCH_CUDA(cudaMemcpyAsync(b.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
   BATCH_CUDA(cudaStreamSynchronize(st));
-  while (b.forks.size() + 1 < b.launches.size()) {
+  while (b.forks.size() < b.launches.size()) {
     cudaStream_t s2;
     cudaEvent_t ev;
     BATCH_CUDA(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
@@ -240,7 +254,7 @@ int upload_state(vmcf_batch_s& b, cudaStream_t st) {
   }
   BATCH_CUDA(cudaMemcpyAsync(b.d_geo, b.h_geo.data(), sizeof(BatchGeom) * b.G, cudaMemcpyHostToDevice, st));
   BATCH_CUDA(cudaMemcpyAsync(b.d_clk, b.h_clk.data(), sizeof(BatchClock) * b.G, cudaMemcpyHostToDevice, st));
-  BATCH_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(int) * b.launches.size(), st));
+  if (!b.launches.empty()) BATCH_CUDA(cudaMemsetAsync(b.d_queue, 0, sizeof(int) * b.launches.size(), st));
   return VMCF_OK;
 }
 
@@ -263,21 +277,28 @@ BatchArgs args_for(const vmcf_batch_s& b, int k, int mode, int kref, double sigm
 cudaError_t launch_k(const vmcf_batch_s& b, int k, int mode, int kref, double sigma, cudaStream_t st) {
   const LaunchPlan& lp = b.launches[k];
   const BatchArgs A = args_for(b, k, mode, kref, sigma);
-  return b.precision == VMCF_FP64 ? launch_batch<double>(lp.shape.GS, lp.shape.groups, lp.grid, lp.smem, A, st)
-                                  : launch_batch<float>(lp.shape.GS, lp.shape.groups, lp.grid, lp.smem, A, st);
+  return b.precision == VMCF_FP64
+             ? launch_batch<double>(lp.phase, lp.shape.GS, lp.shape.groups, lp.grid, lp.smem, A, st)
+             : launch_batch<float>(lp.phase, lp.shape.GS, lp.shape.groups, lp.grid, lp.smem, A, st);
 }
 
-// One sweep of the batch as a graph: fork one branch per launch, join, advance the clocks.
+// One sweep of the batch as a graph: per phase (the evaluation only when measuring), fork
+// one branch per persistent kernel and join; then advance the clocks and rewind the queues.
 int capture(vmcf_batch_s& b, int mode, int kref, double sigma) {
   invalidate_graph(b);
   BATCH_CUDA(cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaEventRecord(b.fork_ev, b.cap);
-  for (size_t k = 0; e == cudaSuccess && k < b.launches.size(); ++k) {
-    cudaStream_t sk = k == 0 ? b.cap : b.forks[k - 1];
-    if (k > 0) e = cudaStreamWaitEvent(sk, b.fork_ev, 0);
-    if (e == cudaSuccess) e = launch_k(b, (int)k, mode, kref, sigma, sk);
-    if (e == cudaSuccess && k > 0) e = cudaEventRecord(b.joins[k - 1], sk);
-    if (e == cudaSuccess && k > 0) e = cudaStreamWaitEvent(b.cap, b.joins[k - 1], 0);
+  cudaError_t e = cudaSuccess;
+  for (int phase = 0; phase < 2 && e == cudaSuccess; ++phase) {
+    if (phase == 1 && mode == 0) break;
+    e = cudaEventRecord(b.fork_ev, b.cap);
+    for (size_t k = 0; e == cudaSuccess && k < b.launches.size(); ++k) {
+      if (b.launches[k].phase != phase) continue;
+      cudaStream_t sk = b.forks[k];
+      e = cudaStreamWaitEvent(sk, b.fork_ev, 0);
+      if (e == cudaSuccess) e = launch_k(b, (int)k, mode, kref, sigma, sk);
+      if (e == cudaSuccess) e = cudaEventRecord(b.joins[k], sk);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b.cap, b.joins[k], 0);
+    }
   }
   if (e == cudaSuccess) e = launch_batch_advance(b.d_clk, b.G, mode, kref, b.d_queue, (int)b.launches.size(), b.cap);
   cudaGraph_t graph = nullptr;
@@ -351,7 +372,6 @@ int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walker
   b->wk.assign(walkers, walkers + G);
   b->h_geo.resize(G);
   b->h_clk.resize(G);
-  b->cost.resize(G);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -371,11 +391,13 @@ int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walker
     auto it = keys.find(k);
     if (it == keys.end()) it = keys.emplace(k, (int)keys.size()).first;
     b->bucket[g] = it->second;
-    b->cost[g] = heuristic_cost(*systems[g]);
+    for (int ph = 0; ph < 2; ++ph) b->cost[ph].push_back(heuristic_cost(*systems[g], ph));
   }
-  b->bucket_shape.resize(keys.size());
-  for (int bk = 0; bk < (int)keys.size(); ++bk) b->bucket_shape[bk] = default_shape(*b, bk);
-  int rc = build_plan(*b, {}, st);
+  for (int ph = 0; ph < 2; ++ph) {
+    b->bucket_shape[ph].resize(keys.size());
+    for (int bk = 0; bk < (int)keys.size(); ++bk) b->bucket_shape[ph][bk] = default_shape(*b, ph, bk);
+  }
+  int rc = build_plan(*b, {}, 3, st);
   if (rc != VMCF_OK) {
     vmcf_batch_destroy(b);
     return rc;
@@ -384,24 +406,27 @@ int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walker
   return VMCF_OK;
 }
 
-int vmcf_batch_set_shape(vmcf_batch_t b, int g, int GS, int groups) {
-  if (!b || g < 0 || g >= b->G) return fail(VMCF_EINVAL, "bad batch or geometry index");
+int vmcf_batch_set_shape(vmcf_batch_t b, int g, int phase, int GS, int groups) {
+  if (!b || g < 0 || g >= b->G || phase < 0 || phase > 1) return fail(VMCF_EINVAL, "bad batch, geometry or phase");
   const int bk = b->bucket[g];
   const Shape sh{GS, groups};
-  if (!shape_fits(*b, bk, sh)) return fail(VMCF_EINVAL, "launch shape not supported or does not fit shared memory");
-  b->bucket_shape[bk] = sh;
-  return build_plan(*b, {}, nullptr);
+  if (!shape_fits(*b, phase, bk, sh))
+    return fail(VMCF_EINVAL, "launch shape not supported or does not fit shared memory");
+  b->bucket_shape[phase][bk] = sh;
+  return build_plan(*b, {}, 3, nullptr);
 }
 
-int vmcf_batch_info(vmcf_batch_t b, int* n_buckets, int* n_launches, int g, int* bucket, int* GS, int* groups) {
+int vmcf_batch_info(vmcf_batch_t b, int* n_buckets, int* n_launches, int g, int* bucket, int* shapes) {
   if (!b) return fail(VMCF_EINVAL, "NULL batch");
-  if (n_buckets) *n_buckets = (int)b->bucket_shape.size();
+  if (n_buckets) *n_buckets = (int)b->bucket_shape[0].size();
   if (n_launches) *n_launches = (int)b->launches.size();
   if (g >= 0 && g < b->G) {
-    const Shape& sh = b->bucket_shape[b->bucket[g]];
     if (bucket) *bucket = b->bucket[g];
-    if (GS) *GS = sh.GS;
-    if (groups) *groups = sh.groups;
+    if (shapes)
+      for (int ph = 0; ph < 2; ++ph) {
+        shapes[2 * ph] = b->bucket_shape[ph][b->bucket[g]].GS;
+        shapes[2 * ph + 1] = b->bucket_shape[ph][b->bucket[g]].groups;
+      }
   }
   return VMCF_OK;
 }
@@ -432,56 +457,60 @@ int vmcf_batch_autotune(vmcf_batch_t b, double step_sigma, int refresh_k, void* 
   cudaEvent_t t0, t1;
   BATCH_CUDA(cudaEventCreate(&t0));
   BATCH_CUDA(cudaEventCreate(&t1));
-  const int nb = (int)b->bucket_shape.size();
+  const int nb = (int)b->bucket_shape[0].size();
   int rc = VMCF_OK;
-  for (int bk = 0; bk < nb && rc == VMCF_OK; ++bk) {
-    std::vector<char> take(b->G, 0);
-    long long walkers = 0;
-    for (int g = 0; g < b->G; ++g)
-      if (b->bucket[g] == bk) {
-        take[g] = 1;
-        walkers += b->wk[g]->W;
+  // per bucket and phase: one sweep (phase 0) or one evaluation without sums (phase 1) of
+  // the bucket's walkers per feasible shape
+  for (int phase = 0; phase < 2 && rc == VMCF_OK; ++phase)
+    for (int bk = 0; bk < nb && rc == VMCF_OK; ++bk) {
+      std::vector<char> take(b->G, 0);
+      for (int g = 0; g < b->G; ++g) take[g] = b->bucket[g] == bk;
+      Shape best = b->bucket_shape[phase][bk];
+      float best_ms = 1e30f;
+      for (const Shape& cand : kCandidates) {
+        if (!shape_fits(*b, phase, bk, cand)) continue;
+        b->bucket_shape[phase][bk] = cand;
+        rc = build_plan(*b, take, 1 << phase, st);
+        if (rc != VMCF_OK) break;
+        rc = upload_state(*b, st);
+        if (rc != VMCF_OK) break;
+        const int mode = phase == 0 ? 0 : 2;
+        cudaError_t e = cudaEventRecord(t0, st);
+        if (e == cudaSuccess) e = launch_k(*b, 0, mode, refresh_k, step_sigma, st);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e != cudaSuccess) {
+          rc = cuda_fail(e, "autotuning launch");
+          break;
+        }
+        if (phase == 0) {
+          advance_host(*b, take, 1, 0, refresh_k);
+        } else {
+          for (int g = 0; g < b->G; ++g)
+            if (take[g]) b->wk[g]->counter = 0;  // the evaluation rebuilt the inverses
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = cand;
+        }
       }
-    Shape best = b->bucket_shape[bk];
-    float best_ms = 1e30f;
-    for (const Shape cand : {Shape{32, 1}, Shape{32, 2}, Shape{32, 4}, Shape{128, 1}}) {
-      if (!shape_fits(*b, bk, cand)) continue;
-      b->bucket_shape[bk] = cand;
-      rc = build_plan(*b, take, st);
-      if (rc != VMCF_OK) break;
-      rc = upload_state(*b, st);
-      if (rc != VMCF_OK) break;
-      cudaError_t e = cudaEventRecord(t0, st);
-      if (e == cudaSuccess) e = launch_k(*b, 0, 2, refresh_k, step_sigma, st);
-      if (e == cudaSuccess) e = cudaEventRecord(t1, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-      if (e != cudaSuccess) {
-        rc = cuda_fail(e, "autotuning launch");
-        break;
-      }
-      advance_host(*b, take, 1, 2, refresh_k);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = cand;
+      b->bucket_shape[phase][bk] = best;
+      // measured cost per walker of this bucket, shared by its geometries in proportion to
+      // their operation counts
+      if (rc == VMCF_OK && best_ms < 1e29f) {
+        double hsum = 0.0;
+        for (int g = 0; g < b->G; ++g)
+          if (take[g]) hsum += heuristic_cost(*b->sys[g], phase) * b->wk[g]->W;
+        for (int g = 0; g < b->G; ++g)
+          if (take[g] && hsum > 0.0) b->cost[phase][g] = (double)best_ms * heuristic_cost(*b->sys[g], phase) / hsum;
       }
     }
-    b->bucket_shape[bk] = best;
-    // measured cost of one walker-sweep of this bucket, shared by its geometries in
-    // proportion to their operation counts
-    if (rc == VMCF_OK && best_ms < 1e29f && walkers > 0) {
-      double hsum = 0.0;
-      for (int g = 0; g < b->G; ++g)
-        if (take[g]) hsum += heuristic_cost(*b->sys[g]) * b->wk[g]->W;
-      for (int g = 0; g < b->G; ++g)
-        if (take[g]) b->cost[g] = (double)best_ms * heuristic_cost(*b->sys[g]) / hsum;
-    }
-  }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
   if (rc != VMCF_OK) return rc;
-  return build_plan(*b, {}, st);
+  return build_plan(*b, {}, 3, st);
 }
 
 }  // extern "C"

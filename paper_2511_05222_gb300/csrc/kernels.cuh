@@ -31,13 +31,13 @@ __device__ __forceinline__ void load_positions(const double* src, int n3, double
 
 // Rebuild the inverses of both spin blocks of one walker into B (T) from positions.
 template <typename T, int GS>
-__device__ void refresh_walker(const DevSys& S, const double* pos, T* B, double* A, T* ao, int* piv, double* f,
-                               int* flag) {
+__device__ void refresh_walker(const DevSys& S, const double* pos, T* B, double* A, T* ao, int ao_rows, int* piv,
+                               double* f, int* flag) {
   const int t = threadIdx.x % GS;
   for (int sg = 0; sg < 2; ++sg) {
     const int n = sg == 0 ? S.nup : S.ndn;
     if (n == 0) continue;
-    build_slater<T, GS>(S, pos, sg, A, ao);
+    build_slater<T, GS>(S, pos, sg, A, ao, ao_rows);
     double la = 0.0, sgn = 1.0;
     gj_inverse<GS>(A, n, piv, f, flag, &la, &sgn, false);
     T* Bs = B + (sg == 0 ? 0 : S.nup * S.nup);
@@ -48,7 +48,7 @@ __device__ void refresh_walker(const DevSys& S, const double* pos, T* B, double*
 
 // ---------------------------------------------------------------- refresh
 template <typename T, int GS>
-__global__ void __launch_bounds__(128) refresh_kernel(DevSys S, GroupLayout L, const double* __restrict__ pos_g,
+__global__ void __launch_bounds__(256) refresh_kernel(DevSys S, GroupLayout L, const double* __restrict__ pos_g,
                                                       T* __restrict__ B_g, int W, unsigned long long* counters) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gpb = blockDim.x / GS, gid = threadIdx.x / GS, t = threadIdx.x % GS;
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128) refresh_kernel(DevSys S, GroupLayout L, c
   for (int i = t; i < 3 * Ne; i += GS) pos[i] = pos_g[(size_t)w * 3 * Ne + i];
   if (t == 0) *flag = 0;
   gsync<GS>();
-  refresh_walker<T, GS>(S, pos, B, A, ao, piv, f, flag);
+  refresh_walker<T, GS>(S, pos, B, A, ao, L.ao_rows, piv, f, flag);
   for (int i = t; i < S.nB; i += GS) B_g[(size_t)w * S.nB + i] = B[i];
   if (t == 0) {
     if (*flag) atomicAdd(&counters[0], 1ull);
@@ -122,11 +122,32 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
       ao_point<T, GS, 0, false>(S, pn, ao, 0);
       gsync<GS>();
       double part[2] = {0.0, 0.0};
-      for (int i = t; i < n; i += GS) {
+      // new orbital row phi_i(r'): with GS >= 2n the mu sum is split in kp parts (partial
+      // sums of parts 1 and 2 go through wv and col) so that kp n threads share it
+      const int kp = GS >= 3 * n ? 3 : (GS >= 2 * n ? 2 : 1);
+      if (kp == 1) {
+        for (int i = t; i < n; i += GS) {
+          T v = 0;
+          for (int mu = 0; mu < S.M; ++mu) v += ao[mu] * __ldg(C + mu * n + i);
+          row[i] = v;
+          part[0] += (double)v * (double)Bs[i * n + el];
+        }
+      } else {
         T v = 0;
-        for (int mu = 0; mu < S.M; ++mu) v += ao[mu] * __ldg(C + mu * n + i);
-        row[i] = v;
-        part[0] += (double)v * (double)Bs[i * n + el];
+        const int i = t % n, pp = t / n;
+        if (pp < kp) {
+          const int m0 = S.M * pp / kp, m1 = S.M * (pp + 1) / kp;
+          for (int mu = m0; mu < m1; ++mu) v += ao[mu] * __ldg(C + mu * n + i);
+          if (pp == 1) wv[i] = v;
+          if (pp == 2) col[i] = v;
+        }
+        gsync<GS>();
+        if (pp == 0) {
+          v += wv[i];
+          if (kp == 3) v += col[i];
+          row[i] = v;
+          part[0] += (double)v * (double)Bs[i * n + el];
+        }
       }
       // Jastrow ratio: pairs with every other electron, and the e-n terms
       for (int q = t; q < Ne + K; q += GS) {
@@ -193,7 +214,7 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
       if (++c == P.kref) {
         const bool last = (sw == P.nsweeps - 1) && (e == Ne - 1);
         if (!(last && P.skip_final_refresh)) {
-          refresh_walker<T, GS>(S, pos, B, A, ao, piv, f, flag);
+          refresh_walker<T, GS>(S, pos, B, A, ao, L.ao_rows, piv, f, flag);
           ++nref;
         }
         c = 0;
@@ -213,7 +234,7 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
 }
 
 template <typename T, int GS>
-__global__ void __launch_bounds__(128) move_kernel(DevSys S, GroupLayout L, MoveParams P) {
+__global__ void __launch_bounds__(256) move_kernel(DevSys S, GroupLayout L, MoveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gpb = blockDim.x / GS, gid = threadIdx.x / GS;
   const int w = blockIdx.x * gpb + gid;
@@ -308,18 +329,20 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   gsync<GS>();
   group_sum<GS, 3>(vs, red);
 
-  // Pass 1: Slater matrices (T) and their FP64 inverses.
+  // Pass 1: Slater matrices (T) and their FP64 inverses. In FP64 mode Bt is Bd (both spin
+  // blocks); in mixed mode Bd holds one block at a time and each inverse is rounded into Bt.
   for (int sg = 0; sg < 2; ++sg) {
     const int n = sg == 0 ? nup : S.ndn;
     if (n == 0) continue;
-    double* A = Bd + (sg == 0 ? 0 : nup * nup);
-    build_slater<T, GS>(S, pos, sg, A, ao);
+    const int off = sg == 0 ? 0 : nup * nup;
+    double* A = sizeof(T) == 8 ? Bd + off : Bd;
+    build_slater<T, GS>(S, pos, sg, A, ao, L.ao_rows);
     gj_inverse<GS>(A, n, piv, f, flag, la, sgn, P.logpsi != nullptr);
+    if constexpr (sizeof(T) != 8) {
+      for (int i = t; i < n * n; i += GS) Bt[off + i] = (T)A[i];
+      gsync<GS>();
+    }
   }
-  if (static_cast<void*>(Bt) != static_cast<void*>(Bd)) {
-    for (int i = t; i < S.nB; i += GS) Bt[i] = (T)Bd[i];
-  }
-  gsync<GS>();
 
   // Pass 2: gradient and Laplacian rows of the MOs per electron; determinant drift
   // g_e = sum_i G_ei B_ie, l_e = sum_i L_ei B_ie; P_ei = L_ei + 2 gradJ_e . G_ei;
@@ -369,13 +392,15 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   // per AO; nuclear derivatives from the recomputed AO gradient, Hessian and gradient of
   // the Laplacian; O_{mu i} = sum_e psi_mu(r_e) B_ie.
   const int nO = M * (nup + S.ndn);
+  T* fa = sm_ptr<T>(base, L.fa);  // [6][M]: AO mu's share of the nuclear derivatives, owned by mu's thread
+  for (int i = t; i < 6 * M; i += GS) fa[i] = T(0);
   for (int sg = 0; sg < 2; ++sg) {
     const int n = sg == 0 ? nup : S.ndn;
     if (n == 0) continue;
     const int e0 = sg == 0 ? 0 : nup, off = sg == 0 ? 0 : nup * nup, ooff = sg == 0 ? 0 : M * nup;
     const T* Bs = Bt + off;
     T* Ps = Pm + off;
-    const T* C = coefC<T>(S, sg);
+    const T* CT = coefCT<T>(S, sg);
     for (int idx = t; idx < n * n; idx += GS) {  // Q = B P
       const int i = idx / n, j = idx - i * n;
       T v = 0;
@@ -402,9 +427,8 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       const T j0 = Jg[3 * e], j1 = Jg[3 * e + 1], j2 = Jg[3 * e + 2];
       for (int mu = t; mu < M; mu += GS) {
         T yA = 0, yL = 0;
-        const T* Cr = C + mu * n;
         for (int i = 0; i < n; ++i) {
-          const T cmi = __ldg(Cr + i);
+          const T cmi = __ldg(CT + i * M + mu);
           yA += cmi * Ps[el * n + i];
           yL += cmi * Bs[i * n + el];
         }
@@ -415,13 +439,12 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
         const T hj0 = hxx * j0 + hxy * j1 + hxz * j2;
         const T hj1 = hxy * j0 + hyy * j1 + hyz * j2;
         const T hj2 = hxz * j0 + hyz * j1 + hzz * j2;
-        const int I = __ldg(S.ao_center + mu);
-        atomicAdd(&frc[3 * I + 0], -g0 * yL);
-        atomicAdd(&frc[3 * I + 1], -g1 * yL);
-        atomicAdd(&frc[3 * I + 2], -g2 * yL);
-        atomicAdd(&frc[3 * K + 3 * I + 0], T(-0.5) * (g0 * yA - yL * (l0 + T(2) * hj0)));
-        atomicAdd(&frc[3 * K + 3 * I + 1], T(-0.5) * (g1 * yA - yL * (l1 + T(2) * hj1)));
-        atomicAdd(&frc[3 * K + 3 * I + 2], T(-0.5) * (g2 * yA - yL * (l2 + T(2) * hj2)));
+        fa[0 * M + mu] -= g0 * yL;
+        fa[1 * M + mu] -= g1 * yL;
+        fa[2 * M + mu] -= g2 * yL;
+        fa[3 * M + mu] += T(-0.5) * (g0 * yA - yL * (l0 + T(2) * hj0));
+        fa[4 * M + mu] += T(-0.5) * (g1 * yA - yL * (l1 + T(2) * hj1));
+        fa[5 * M + mu] += T(-0.5) * (g2 * yA - yL * (l2 + T(2) * hj2));
         const T tdc = lp + T(2) * (j0 * g0 + j1 * g1 + j2 * g2);
         for (int i = 0; i < n; ++i) {
           const T b = Bs[i * n + el];
@@ -478,6 +501,17 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
     gsync<GS>();
   }
 
+  // the AO shares of the nuclear derivatives, onto their centres
+  for (int mu = t; mu < M; mu += GS) {
+    const int I = __ldg(S.ao_center + mu);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      atomicAdd(&frc[3 * I + d], fa[d * M + mu]);
+      atomicAdd(&frc[3 * K + 3 * I + d], fa[(3 + d) * M + mu]);
+    }
+  }
+  gsync<GS>();
+
   // per-walker outputs and scalar / force sums
   for (int i = t; i < 3 * K; i += GS) {
     const double dl = (double)frc[i];
@@ -521,7 +555,7 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
 // In the shared accumulator, acc[1] and acc[2] hold sums of (E_L - E_ref) and its square;
 // they are turned into sums of E_L and E_L^2 when the CTA flushes.
 template <typename T, int GS>
-__global__ void __launch_bounds__(128) measure_kernel(DevSys S, GroupLayout L, MeasParams P, int acc_off) {
+__global__ void __launch_bounds__(256) measure_kernel(DevSys S, GroupLayout L, MeasParams P, int acc_off) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gpb = blockDim.x / GS, gid = threadIdx.x / GS;
   unsigned char* base = smem + gid * L.bytes;
@@ -558,6 +592,9 @@ cudaError_t set_smem_limits_impl() {
   if ((e = cudaFuncSetAttribute(move_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(measure_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(measure_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(refresh_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(move_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   return cudaSuccess;
 }
 
@@ -567,8 +604,12 @@ cudaError_t launch_refresh_impl(const DevSys& S, const Launch& lc, const double*
   const dim3 grid(lc.grid), block(lc.GS * lc.groups);
   if (lc.GS == 32)
     refresh_kernel<T, 32><<<grid, block, lc.smem, st>>>(S, lc.L, pos, reinterpret_cast<T*>(B), W, counters);
-  else
+  else if (lc.GS == 128)
     refresh_kernel<T, 128><<<grid, block, lc.smem, st>>>(S, lc.L, pos, reinterpret_cast<T*>(B), W, counters);
+  else if (lc.GS == 256)
+    refresh_kernel<T, 256><<<grid, block, lc.smem, st>>>(S, lc.L, pos, reinterpret_cast<T*>(B), W, counters);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
@@ -577,8 +618,12 @@ cudaError_t launch_move_impl(const DevSys& S, const Launch& lc, const MoveParams
   const dim3 grid(lc.grid), block(lc.GS * lc.groups);
   if (lc.GS == 32)
     move_kernel<T, 32><<<grid, block, lc.smem, st>>>(S, lc.L, P);
-  else
+  else if (lc.GS == 128)
     move_kernel<T, 128><<<grid, block, lc.smem, st>>>(S, lc.L, P);
+  else if (lc.GS == 256)
+    move_kernel<T, 256><<<grid, block, lc.smem, st>>>(S, lc.L, P);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
@@ -587,8 +632,12 @@ cudaError_t launch_measure_impl(const DevSys& S, const Launch& lc, const MeasPar
   const dim3 grid(lc.grid), block(lc.GS * lc.groups);
   if (lc.GS == 32)
     measure_kernel<T, 32><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
-  else
+  else if (lc.GS == 128)
     measure_kernel<T, 128><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
+  else if (lc.GS == 256)
+    measure_kernel<T, 256><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -88,12 +88,13 @@ GroupLayout layout_refresh_move(const vmcf_system_s& s, size_t tsz, int GS) {
   L.pl = take(4 * 3 * s.Ne);
   L.Bd = take(8 * s.nmax * s.nmax);
   L.Bt = take((int)tsz * s.nB);
-  L.ao = take((int)tsz * s.M);
+  L.ao_rows = 4;
+  L.ao = take((int)tsz * s.M * L.ao_rows);
   L.row = take((int)tsz * s.nmax);
   L.wv = take((int)tsz * s.nmax);
   L.col = take((int)tsz * s.nmax);
   L.piv = take(4 * s.nmax);
-  L.f = take(8 * (s.nmax + 1));
+  L.f = take(8 * (3 * s.nmax + 1));
   L.red = take(8 * 4 * std::max(1, GS / 32));
   L.scal = take(32);
   L.bytes = align16(o);
@@ -108,35 +109,36 @@ GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool with
   L.pos = take(8 * 3 * s.Ne);
   L.ph = take(4 * 3 * s.Ne);
   L.pl = take(4 * 3 * s.Ne);
-  L.Bd = take(8 * s.nB);
+  // FP64: Bd holds both inverses and is Bt. Mixed: Bd holds one block during the inversion;
+  // P (written after the last inversion) reuses its bytes (4 nB <= 8 nmax^2).
+  L.Bd = take(8 * (tsz == 8 ? s.nB : s.nmax * s.nmax));
   L.Bt = (tsz == 8) ? L.Bd : take((int)tsz * s.nB);
-  L.P = take((int)tsz * s.nB);
+  L.P = (tsz == 8) ? take((int)tsz * s.nB) : L.Bd;
   L.Q = take((int)tsz * s.nmax * s.nmax);
   L.Jg = take((int)tsz * 3 * s.Ne);
   L.Jl = take((int)tsz * s.Ne);
   L.gd = take((int)tsz * 3 * s.Ne);
+  L.ao_rows = 8;
   L.ao = take((int)tsz * 14 * s.M);
   L.mo = take((int)tsz * 4 * s.nmax);
   L.frc = take((int)tsz * 6 * s.K);
+  L.fa = take((int)tsz * 6 * s.M);
   L.Ow = take((int)tsz * s.M * s.nmax);
   L.D = withD ? take((int)tsz * s.M * s.nmax) : L.Ow;
   L.piv = take(4 * s.nmax);
-  L.f = take(8 * (s.nmax + 1));
+  L.f = take(8 * (3 * s.nmax + 1));
   L.red = take(8 * 4 * std::max(1, GS / 32));
   L.scal = take(32);
   L.bytes = align16(o);
   return L;
 }
 
-int plan(vmcf_system_s& s) {
+// Measurement-kernel plan for group size s.GSm: layouts, groups per CTA, accumulator placement.
+int plan_measure(vmcf_system_s& s) {
   const size_t tsz = s.precision == VMCF_FP64 ? 8 : 4;
-  s.GS = (s.nmax <= 24) ? 32 : 128;
-  s.Lrm = layout_refresh_move(s, tsz, s.GS);
-  s.Lmeas = layout_measure(s, tsz, s.GS, false);
-  s.LmeasD = layout_measure(s, tsz, s.GS, true);
-  const int maxg = s.GS == 32 ? 4 : 1;
-  s.gpb_rm = std::max(1, std::min(maxg, kSmemCap / std::max(1, s.Lrm.bytes)));
-  if (s.Lrm.bytes > kSmemCap) return fail(VMCF_ENOTSUP, "system too large for the shared-memory plan (sampling)");
+  s.Lmeas = layout_measure(s, tsz, s.GSm, false);
+  s.LmeasD = layout_measure(s, tsz, s.GSm, true);
+  const int maxg = s.GSm == 32 ? 4 : 1;
   if (s.Lmeas.bytes > kSmemCap) return fail(VMCF_ENOTSUP, "system too large for the shared-memory plan (measure)");
   s.gpb_measD = s.LmeasD.bytes > kSmemCap ? 0 : std::max(1, std::min(maxg, kSmemCap / s.LmeasD.bytes));
   s.accL = 3 + 9 * s.K + 2 * s.M * (s.nup + s.ndn);
@@ -153,6 +155,17 @@ int plan(vmcf_system_s& s) {
     s.acc_off = -1;
   }
   return VMCF_OK;
+}
+
+int plan(vmcf_system_s& s) {
+  const size_t tsz = s.precision == VMCF_FP64 ? 8 : 4;
+  s.GS = (s.nmax <= 24) ? 32 : 128;
+  s.GSm = (s.nmax <= 24) ? 32 : 256;
+  s.Lrm = layout_refresh_move(s, tsz, s.GS);
+  const int maxg = s.GS == 32 ? 4 : 1;
+  s.gpb_rm = std::max(1, std::min(maxg, kSmemCap / std::max(1, s.Lrm.bytes)));
+  if (s.Lrm.bytes > kSmemCap) return fail(VMCF_ENOTSUP, "system too large for the shared-memory plan (sampling)");
+  return plan_measure(s);
 }
 
 // Small-system path: one lane per electron in the measurement, one lane per walker in the
@@ -175,7 +188,7 @@ void plan_small(vmcf_system_s& s) {
   L.Pm = take(tsz * s.nB);
   L.Q = take(tsz * s.nmax * s.nmax);
   L.piv = take(4 * s.nmax);
-  L.f = take(8 * (s.nmax + 1));
+  L.f = take(8 * (3 * s.nmax + 1));
   L.frc = take(tsz * 6 * s.K);
   L.phi = take(tsz * s.Ne * L.chunk);
   L.red = take(16);
@@ -220,7 +233,7 @@ GroupLayout vmcf::group_layout_meas(const vmcf_system_s& s, int GS) {
 
 Launch vmcf::launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD) {
   Launch lc{};
-  lc.GS = s.GS;
+  lc.GS = s.GSm;
   if (withD) {
     lc.groups = s.gpb_measD;
     lc.L = s.LmeasD;
@@ -517,6 +530,19 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
     Rl[i] = (float)(s->R[i] - (double)Rh[i]);
   }
   std::vector<float> Cf0(s->C[0].begin(), s->C[0].end()), Cf1(s->C[1].begin(), s->C[1].end());
+  // C^s transposed, [n_s][M]: read along mu by consecutive threads
+  std::vector<double> CT[2];
+  std::vector<float> CfT[2];
+  for (int sg = 0; sg < 2; ++sg) {
+    const int n = sg == 0 ? n_up : n_dn;
+    CT[sg].assign((size_t)std::max(1, n * M), 0.0);
+    CfT[sg].assign((size_t)std::max(1, n * M), 0.f);
+    for (int mu = 0; mu < M; ++mu)
+      for (int i = 0; i < n; ++i) {
+        CT[sg][(size_t)i * M + mu] = s->C[sg][(size_t)mu * n + i];
+        CfT[sg][(size_t)i * M + mu] = (float)s->C[sg][(size_t)mu * n + i];
+      }
+  }
   size_t off = 0;
   auto slot = [&](size_t bytes) { size_t at = off; off = (off + bytes + 255) & ~size_t(255); return at; };
   const size_t oR = slot(8 * s->R.size()), oZ = slot(8 * s->Z.size()), oSh = slot(sizeof(int4) * shells.size()),
@@ -525,7 +551,8 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
                oC1 = slot(8 * std::max<size_t>(1, s->C[1].size())), oCf0 = slot(4 * Cf0.size()),
                oCf1 = slot(4 * std::max<size_t>(1, Cf1.size())), oDv = slot(8 * dVnn.size()), oCnt = slot(16),
                oRh = slot(4 * Rh.size()), oRl = slot(4 * Rl.size()), oSharp = slot(4 * sharp.size()),
-               oAlo = slot(4 * alpha_lo.size());
+               oAlo = slot(4 * alpha_lo.size()), oCT0 = slot(8 * CT[0].size()), oCT1 = slot(8 * CT[1].size()),
+               oCfT0 = slot(4 * CfT[0].size()), oCfT1 = slot(4 * CfT[1].size());
   cudaError_t e = cudaMalloc(&s->dmem, off);
   if (e != cudaSuccess) {
     delete s;
@@ -554,6 +581,10 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   ce = ce ? ce : up(oRl, Rl.data(), 4 * Rl.size());
   ce = ce ? ce : up(oSharp, sharp.data(), 4 * sharp.size());
   ce = ce ? ce : up(oAlo, alpha_lo.data(), 4 * alpha_lo.size());
+  ce = ce ? ce : up(oCT0, CT[0].data(), 8 * CT[0].size());
+  ce = ce ? ce : up(oCT1, CT[1].data(), 8 * CT[1].size());
+  ce = ce ? ce : up(oCfT0, CfT[0].data(), 4 * CfT[0].size());
+  ce = ce ? ce : up(oCfT1, CfT[1].data(), 4 * CfT[1].size());
   if (ce == cudaSuccess) ce = s->precision == VMCF_FP64 ? set_smem_limits<double>(s->GS) : set_smem_limits<float>(s->GS);
   if (ce == cudaSuccess && s->small)
     ce = s->precision == VMCF_FP64 ? set_smem_limits_small<double>() : set_smem_limits_small<float>();
@@ -590,6 +621,10 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   D.C[1] = reinterpret_cast<const double*>(b + oC1);
   D.Cf[0] = reinterpret_cast<const float*>(b + oCf0);
   D.Cf[1] = reinterpret_cast<const float*>(b + oCf1);
+  D.CT[0] = reinterpret_cast<const double*>(b + oCT0);
+  D.CT[1] = reinterpret_cast<const double*>(b + oCT1);
+  D.CfT[0] = reinterpret_cast<const float*>(b + oCfT0);
+  D.CfT[1] = reinterpret_cast<const float*>(b + oCfT1);
   D.Fa = jas->F_anti; D.Fp = jas->F_par; D.aa = jas->a_anti; D.ap = jas->a_par; D.ben = jas->b_en;
   D.J1 = jas->enable_J1 ? 1 : 0;
   D.J2 = jas->enable_J2 ? 1 : 0;
@@ -947,8 +982,12 @@ int vmcf_block_sums(vmcf_system_t s, vmcf_walkers_t wk, double* out, void* strea
   return VMCF_OK;
 }
 
-int vmcf_finish_estimators(const double* blk, int nb, int K, int M, int n_up, int n_dn, double er, double* E,
-                           double* E_err, double* F, double* F_err, double* dEdC, double* dEdC_err) {
+namespace {
+// Delete-one-block jackknife of the estimators from block sums: the full-sample estimates
+// (E, F, B) and the nb leave-one-out estimates (Ej [nb], Fj [nb][3K], Bj [nb][nO]).
+int jackknife_estimates(const double* blk, int nb, int K, int M, int n_up, int n_dn, double er, double* Ev,
+                        std::vector<double>& Fv, std::vector<double>& Bv, std::vector<double>& Ej,
+                        std::vector<double>& Fj, std::vector<double>& Bj) {
   if (!blk || nb < 2 || K < 1 || M < 1 || n_up < 0 || n_dn < 0) return fail(VMCF_EINVAL, "bad arguments");
   const int K3 = 3 * K, nO = M * (n_up + n_dn), L = 3 + 9 * K + 2 * nO;
   std::vector<double> tot(L, 0.0);
@@ -965,19 +1004,37 @@ int vmcf_finish_estimators(const double* blk, int nb, int K, int M, int n_up, in
     for (int i = 0; i < K3; ++i) Fo[i] = -(v[o_dEL + i] / n + 2.0 * (v[o_Ed + i] / n - (Em - er) * v[o_d + i] / n));
     for (int i = 0; i < nO; ++i) Bo[i] = 2.0 * (v[o_EO + i] / n - (Em - er) * v[o_O + i] / n);
   };
-  double Ev;
-  std::vector<double> Fv(K3), Bv(nO);
-  est(tot.data(), &Ev, Fv.data(), Bv.data());
-  // delete-one-block jackknife
-  std::vector<double> Ej(nb), Fj((size_t)nb * K3), Bj((size_t)nb * nO), loo(L);
+  Fv.assign(K3, 0.0);
+  Bv.assign(nO, 0.0);
+  est(tot.data(), Ev, Fv.data(), Bv.data());
+  Ej.assign(nb, 0.0);
+  Fj.assign((size_t)nb * K3, 0.0);
+  Bj.assign((size_t)nb * nO, 0.0);
+  std::vector<double> loo(L);
   for (int b = 0; b < nb; ++b) {
     for (int i = 0; i < L; ++i) loo[i] = tot[i] - blk[(size_t)b * L + i];
     est(loo.data(), &Ej[b], Fj.data() + (size_t)b * K3, Bj.data() + (size_t)b * nO);
   }
-  auto jk = [&](const double* th, int stride, int idx) {
-    double m = 0.0;
-    for (int b = 0; b < nb; ++b) m += th[(size_t)b * stride + idx];
-    m /= nb;
+  return VMCF_OK;
+}
+
+// Mean over the nb leave-one-out estimates of component idx (stride = components per block).
+double jk_mean(const std::vector<double>& th, int nb, int stride, int idx) {
+  double m = 0.0;
+  for (int b = 0; b < nb; ++b) m += th[(size_t)b * stride + idx];
+  return m / nb;
+}
+}  // namespace
+
+int vmcf_finish_estimators(const double* blk, int nb, int K, int M, int n_up, int n_dn, double er, double* E,
+                           double* E_err, double* F, double* F_err, double* dEdC, double* dEdC_err) {
+  double Ev = 0.0;
+  std::vector<double> Fv, Bv, Ej, Fj, Bj;
+  int rc = jackknife_estimates(blk, nb, K, M, n_up, n_dn, er, &Ev, Fv, Bv, Ej, Fj, Bj);
+  if (rc != VMCF_OK) return rc;
+  const int K3 = 3 * K, nO = M * (n_up + n_dn);
+  auto jk = [&](const std::vector<double>& th, int stride, int idx) {
+    const double m = jk_mean(th, nb, stride, idx);
     double v = 0.0;
     for (int b = 0; b < nb; ++b) {
       const double d = th[(size_t)b * stride + idx] - m;
@@ -986,15 +1043,36 @@ int vmcf_finish_estimators(const double* blk, int nb, int K, int M, int n_up, in
     return std::sqrt((nb - 1.0) / nb * v);
   };
   if (E) *E = Ev;
-  if (E_err) *E_err = jk(Ej.data(), 1, 0);
+  if (E_err) *E_err = jk(Ej, 1, 0);
   for (int i = 0; i < K3; ++i) {
     if (F) F[i] = Fv[i];
-    if (F_err) F_err[i] = jk(Fj.data(), K3, i);
+    if (F_err) F_err[i] = jk(Fj, K3, i);
   }
   for (int i = 0; i < nO; ++i) {
     if (dEdC) dEdC[i] = Bv[i];
-    if (dEdC_err) dEdC_err[i] = jk(Bj.data(), nO, i);
+    if (dEdC_err) dEdC_err[i] = jk(Bj, nO, i);
   }
+  return VMCF_OK;
+}
+
+int vmcf_finish_covariance(const double* blk, int nb, int K, int M, int n_up, int n_dn, double er,
+                           double* F_factor, double* B_factor) {
+  double Ev = 0.0;
+  std::vector<double> Fv, Bv, Ej, Fj, Bj;
+  int rc = jackknife_estimates(blk, nb, K, M, n_up, n_dn, er, &Ev, Fv, Bv, Ej, Fj, Bj);
+  if (rc != VMCF_OK) return rc;
+  const int K3 = 3 * K, nO = M * (n_up + n_dn);
+  const double scale = std::sqrt((nb - 1.0) / nb);
+  if (F_factor)
+    for (int i = 0; i < K3; ++i) {
+      const double m = jk_mean(Fj, nb, K3, i);
+      for (int b = 0; b < nb; ++b) F_factor[(size_t)i * nb + b] = scale * (Fj[(size_t)b * K3 + i] - m);
+    }
+  if (B_factor)
+    for (int i = 0; i < nO; ++i) {
+      const double m = jk_mean(Bj, nb, nO, i);
+      for (int b = 0; b < nb; ++b) B_factor[(size_t)i * nb + b] = scale * (Bj[(size_t)b * nO + i] - m);
+    }
   return VMCF_OK;
 }
 
@@ -1058,6 +1136,18 @@ int vmcf_set_tuning(vmcf_system_t s, const char* key, int value) {
       return fail(VMCF_EINVAL, "tensor-core walker sums need the mixed small-system path, M <= 128, 2n <= 32");
     s->tc_sums = want;
     return VMCF_OK;
+  }
+  if (k == "measure_group_size") {
+    if (s->small || (value != 32 && value != 128 && value != 256))
+      return fail(VMCF_EINVAL, "measure group size (walker-group kernels): 32, 128 or 256");
+    const int old = s->GSm;
+    s->GSm = value;
+    int rc = plan_measure(*s);
+    if (rc != VMCF_OK) {
+      s->GSm = old;
+      plan_measure(*s);
+    }
+    return rc;
   }
   if (k == "measure_warps") {
     if (!s->small || (value != 2 && value != 4 && value != 8)) return fail(VMCF_EINVAL, "measure warps: 2, 4 or 8");

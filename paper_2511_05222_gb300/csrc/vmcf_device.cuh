@@ -29,6 +29,8 @@ struct DevSys {
   const float* alpha_lo; // [nshell][kMaxPrim] alpha - (float)alpha, for float-float a r^2
   const double* C[2];    // [M][n_s]
   const float* Cf[2];
+  const double* CT[2];   // [n_s][M], the same coefficients transposed
+  const float* CfT[2];
   double Fa, Fp, aa, ap, ben;
   int J1, J2;
   double Vnn;
@@ -38,6 +40,9 @@ struct DevSys {
 template <typename T> __device__ __forceinline__ const T* coefC(const DevSys& S, int s);
 template <> __device__ __forceinline__ const double* coefC<double>(const DevSys& S, int s) { return S.C[s]; }
 template <> __device__ __forceinline__ const float* coefC<float>(const DevSys& S, int s) { return S.Cf[s]; }
+template <typename T> __device__ __forceinline__ const T* coefCT(const DevSys& S, int s);
+template <> __device__ __forceinline__ const double* coefCT<double>(const DevSys& S, int s) { return S.CT[s]; }
+template <> __device__ __forceinline__ const float* coefCT<float>(const DevSys& S, int s) { return S.CfT[s]; }
 
 template <typename T> __device__ __forceinline__ T dexp(T x);
 template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
@@ -305,12 +310,11 @@ __device__ __forceinline__ void disp_nuc<float>(const DevSys& S, const EPos& p, 
   for (int k = 0; k < 3; ++k) d[k] = (p.h[k] - __ldg(S.Rh + 3 * c + k)) + (p.l[k] - __ldg(S.Rl + 3 * c + k));
 }
 
-// AO components at one point for all shells, threads of the group over shells. SHARP:
-// in mixed mode, form a r^2 of sharp primitives in float-float arithmetic.
-template <typename T, int GS, int LEVEL, bool SHARP>
-__device__ __forceinline__ void ao_point(const DevSys& S, const EPos& p, T* out, int stride) {
-  const int t = threadIdx.x % GS;
-  for (int s = t; s < S.nshell; s += GS) {
+// AO components of shell s at one point. SHARP: in mixed mode, form a r^2 of sharp
+// primitives in float-float arithmetic.
+template <typename T, int LEVEL, bool SHARP>
+__device__ __forceinline__ void shell_point(const DevSys& S, const EPos& p, int s, T* out, int stride) {
+  {
     const int c = __ldg(S.shell + s).x;
     T d[3];
     R2FF r2ff{0.f, 0.f};
@@ -334,6 +338,12 @@ __device__ __forceinline__ void ao_point(const DevSys& S, const EPos& p, T* out,
     }
     shell_eval<T, LEVEL>(S, s, d[0], d[1], d[2], smask, r2ff, out, stride);
   }
+}
+
+template <typename T, int GS, int LEVEL, bool SHARP>
+__device__ __forceinline__ void ao_point(const DevSys& S, const EPos& p, T* out, int stride) {
+  const int t = threadIdx.x % GS;
+  for (int s = t; s < S.nshell; s += GS) shell_point<T, LEVEL, SHARP>(S, p, s, out, stride);
 }
 
 // Electron-electron displacement from the shared-memory position arrays.
@@ -365,13 +375,21 @@ __device__ __forceinline__ T pade_value(T a, T F, T r) {
 
 // ---------------------------------------------------------------- FP64 Gauss-Jordan inverse
 // In-place inversion of the n x n row-major matrix A (shared memory, double) with partial
-// row pivoting. piv: int[n], f: double[n + 1] scratch, flag: int (set to 1 if a pivot is zero
-// or not finite). logabs/sign are accumulated when want_logdet. Every thread of the group
-// must call it.
+// row pivoting. piv: int[n]; f: double[3 n + 1] scratch (column k, the pivot's reciprocal,
+// the scaled pivot row and the row it replaces); flag: int (set to 1 if a pivot is zero or
+// not finite). logabs/sign are accumulated when want_logdet. Every thread of the group must
+// call it. Per pivot: the first warp finds the pivot; the group copies the pivot row (scaled),
+// the row it displaces and column k; then every element is updated once, the row swap folded
+// into the update, so each pivot costs three group barriers.
 template <int GS>
 __device__ void gj_inverse(double* A, int n, int* piv, double* f, int* flag, double* logabs, double* sgn,
                            bool want_logdet) {
   const int t = threadIdx.x % GS;
+  double* rs = f + n + 1;      // scaled pivot row: the new row k
+  double* rk = f + 2 * n + 1;  // old row k: the new row p
+  // this thread's elements in row-major order: (i0, j0), then steps of GS elements
+  const int i0 = t / n, j0 = t - i0 * n;
+  const int di = GS / n, dj = GS - di * n;
   for (int k = 0; k < n; ++k) {
     // pivot search by the first warp of the group; |x| of doubles compared through their bit
     // patterns (monotone for non-negative values), so the search needs no FP64 instruction
@@ -402,53 +420,107 @@ __device__ void gj_inverse(double* A, int n, int* piv, double* f, int* flag, dou
     }
     gsync<GS>();
     const int p = piv[k];
-    if (p != k)
-      for (int j = t; j < n; j += GS) {
-        const double a = A[k * n + j];
-        A[k * n + j] = A[p * n + j];
-        A[p * n + j] = a;
-      }
-    gsync<GS>();
     const double pinv = f[n];
-    for (int i = t; i < n; i += GS) f[i] = A[i * n + k];
+    for (int j = t; j < n; j += GS) {
+      rs[j] = (j == k ? 1.0 : A[p * n + j]) * pinv;
+      rk[j] = A[k * n + j];
+    }
+    for (int i = t; i < n; i += GS) f[i] = A[i * n + k];  // column k before the swap
     gsync<GS>();
-    for (int j = t; j < n; j += GS) A[k * n + j] = (j == k ? 1.0 : A[k * n + j]) * pinv;
-    gsync<GS>();
-    for (int idx = t; idx < n * n; idx += GS) {
-      const int i = idx / n, j = idx - i * n;
-      if (i != k) A[idx] = (j == k ? 0.0 : A[idx]) - f[i] * A[k * n + j];
+    // after the swap, row p holds the old row k, whose column-k entry is f[k]
+    const double fp = f[k];
+    for (int i = i0, j = j0; i < n;) {
+      double v;
+      if (i == k) {
+        v = rs[j];
+      } else {
+        const double fi = i == p ? fp : f[i];
+        const double aij = i == p ? rk[j] : A[i * n + j];
+        v = (j == k ? 0.0 : aij) - fi * rs[j];
+      }
+      A[i * n + j] = v;
+      i += di;
+      j += dj;
+      if (j >= n) {
+        j -= n;
+        ++i;
+      }
     }
     gsync<GS>();
   }
-  // undo the row permutation as column swaps, last pivot first
-  for (int k = n - 1; k >= 0; --k) {
-    const int p = piv[k];
-    if (p != k)
-      for (int i = t; i < n; i += GS) {
+  // undo the row permutation as column swaps, last pivot first; a thread owns whole rows
+  for (int i = t; i < n; i += GS)
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = piv[k];
+      if (p != k) {
         const double a = A[i * n + k];
         A[i * n + k] = A[i * n + p];
         A[i * n + p] = a;
       }
-    gsync<GS>();
-  }
+    }
+  gsync<GS>();
 }
 
 // ---------------------------------------------------------------- Slater matrix build
+// R rows (rows row0, row0 + ng, ...) of one orbital column: independent accumulators that
+// share each coefficient load. Rows past nc are computed from a valid row and not stored.
+template <typename T, int R>
+__device__ __forceinline__ void slater_rows(const T* aobuf, const T* C, int M, int n, int col, int row0, int ng,
+                                            int nc, double* A) {
+  T v[R];
+  const T* a[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    v[r] = T(0);
+    const int row = row0 + r * ng;
+    a[r] = aobuf + (row < nc ? row : nc - 1) * M;
+  }
+  for (int mu = 0; mu < M; ++mu) {
+    const T c = __ldg(C + mu * n + col);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] += a[r][mu] * c;
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int row = row0 + r * ng;
+    if (row < nc) A[row * n + col] = (double)v[r];
+  }
+}
+
 // A^s_{el, i} = phi_i(r_e) = sum_mu psi_mu(r_e) C^s_{mu i} (Eq. restricted-C), computed
-// in T and stored in double for the inversion. aorow: T[M] scratch.
+// in T and stored in double for the inversion. aobuf: T[chunk * M] scratch. chunk electrons
+// at a time: their AO values over (electron, shell) pairs, then their rows of A, each thread
+// owning one orbital column and every ng-th row of the chunk.
 template <typename T, int GS>
-__device__ void build_slater(const DevSys& S, const double* pos, int sg, double* A, T* aorow) {
+__device__ void build_slater(const DevSys& S, const double* pos, int sg, double* A, T* aobuf, int chunk) {
   const int t = threadIdx.x % GS;
-  const int n = sg == 0 ? S.nup : S.ndn, e0 = sg == 0 ? 0 : S.nup;
+  const int n = sg == 0 ? S.nup : S.ndn, e0 = sg == 0 ? 0 : S.nup, M = S.M, ns = S.nshell;
   const T* C = coefC<T>(S, sg);
-  for (int el = 0; el < n; ++el) {
-    const EPos p = make_epos(pos + 3 * (e0 + el));
-    ao_point<T, GS, 0, true>(S, p, aorow, 0);
+  chunk = chunk < 1 ? 1 : (chunk > 8 ? 8 : chunk);
+  // GS >= n: thread t owns column t % n and row group t / n of GS / n groups;
+  // GS < n: thread t owns columns t, t + GS, ... and every row
+  const bool wide = GS >= n;
+  const int ng = wide ? GS / n : 1;
+  const int col0 = wide ? t % n : t, rg = wide ? t / n : 0, dcol = wide ? n : GS;
+  for (int c0 = 0; c0 < n; c0 += chunk) {
+    const int nc = n - c0 < chunk ? n - c0 : chunk;
+    for (int q = t; q < nc * ns; q += GS) {
+      const int r = q / ns, sh = q - r * ns;
+      shell_point<T, 0, true>(S, make_epos(pos + 3 * (e0 + c0 + r)), sh, aobuf + r * M, 0);
+    }
     gsync<GS>();
-    for (int i = t; i < n; i += GS) {
-      T v = 0;
-      for (int mu = 0; mu < S.M; ++mu) v += aorow[mu] * __ldg(C + mu * n + i);
-      A[el * n + i] = (double)v;
+    for (int col = col0; col < n && rg < ng && rg < nc; col += dcol) {
+      double* Ar = A + c0 * n;
+      switch ((nc - rg + ng - 1) / ng) {  // rows of this thread
+        case 1: slater_rows<T, 1>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
+        case 2: slater_rows<T, 2>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
+        case 3: slater_rows<T, 3>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
+        case 4: slater_rows<T, 4>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
+        case 5: slater_rows<T, 5>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
+        case 6: slater_rows<T, 6>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
+        case 7: slater_rows<T, 7>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
+        default: slater_rows<T, 8>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
+      }
     }
     gsync<GS>();
   }

@@ -18,7 +18,8 @@ struct vmcf_system_s {
   vmcf::DevSys dev{};
   void* dmem = nullptr;
   // launch planning
-  int GS = 32;
+  int GS = 32;   // threads per walker group: sweep and refresh kernels
+  int GSm = 32;  // threads per walker group: measurement kernel
   vmcf::GroupLayout Lrm{}, Lmeas{}, LmeasD{};
   int gpb_rm = 1, gpb_meas = 1, gpb_measD = 1;
   int accL = 0;

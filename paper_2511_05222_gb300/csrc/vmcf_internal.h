@@ -10,8 +10,9 @@ namespace vmcf {
 
 // Byte offsets of one walker group's shared-memory region; computed on the host.
 struct GroupLayout {
-  int pos, ph, pl, Bd, Bt, P, Q, Jg, Jl, gd, ao, mo, frc, Ow, D, piv, f, red, scal, row, wv, col;
-  int bytes;  // size of one group's region (16-byte multiple)
+  int pos, ph, pl, Bd, Bt, P, Q, Jg, Jl, gd, ao, mo, frc, fa, Ow, D, piv, f, red, scal, row, wv, col;
+  int ao_rows;  // AO rows of M values the ao buffer holds (electrons per Slater-build chunk)
+  int bytes;    // size of one group's region (16-byte multiple)
 };
 
 struct Launch {
@@ -145,10 +146,11 @@ struct BatchArgs {
   int hdr;            // header bytes (geometry copy and the group's scalars) at the start of a region
 };
 
+// phase 0: Metropolis sweep of each walker; phase 1: evaluation (and walker sums when mode 1)
 template <typename T>
-cudaError_t launch_batch(int GS, int groups, int grid, size_t smem, const BatchArgs& A, cudaStream_t st);
+cudaError_t launch_batch(int phase, int GS, int groups, int grid, size_t smem, const BatchArgs& A, cudaStream_t st);
 template <typename T>
-cudaError_t batch_occupancy(int GS, int groups, size_t smem, int* ctas_per_sm);
+cudaError_t batch_occupancy(int phase, int GS, int groups, size_t smem, int* ctas_per_sm);
 cudaError_t launch_batch_advance(BatchClock* clk, int G, int mode, int kref, int* queues, int nq, cudaStream_t st);
 
 cudaError_t run_probes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, cudaStream_t st);

@@ -43,6 +43,23 @@ def finish_estimators(blocks: np.ndarray, K: int, M: int, n_up: int, n_dn: int, 
             "dEdC_err": Be}
 
 
+def finish_covariance(blocks: np.ndarray, K: int, M: int, n_up: int, n_dn: int, e_ref: float):
+    """vmcf_finish_covariance on host block sums: factors (F [3K][nb], B [nO][nb]) with
+    Cov = factor @ factor.T (no GPU involved)."""
+    L = vmcf.lib()
+    L.vmcf_finish_covariance.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int] + [ctypes.c_int] * 4 + \
+        [ctypes.c_double] + [ctypes.POINTER(ctypes.c_double)] * 2
+    blocks = np.ascontiguousarray(blocks, dtype=np.float64)
+    nb = blocks.shape[0]
+    Ff = np.zeros((3 * K, nb))
+    Bf = np.zeros((M * (n_up + n_dn), nb))
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rc = L.vmcf_finish_covariance(dp(blocks), nb, K, M, n_up, n_dn, float(e_ref), dp(Ff), dp(Bf))
+    if rc != 0:
+        raise vmcf.VmcfError(rc, "vmcf_finish_covariance")
+    return Ff, Bf
+
+
 def sharded_estimators(walkers: "vmcf.Walkers", group=None) -> dict:
     """Estimators over the walkers of all ranks: gather block sums, finish on the host."""
     s = walkers.system

@@ -95,9 +95,9 @@ def lib(build_if_missing: bool = True):
                                         ctypes.POINTER(_vp)]
         L.vmcf_batch_destroy.argtypes = [_vp]
         L.vmcf_batch_autotune.argtypes = [_vp, ctypes.c_double, ctypes.c_int, _vp]
-        L.vmcf_batch_set_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.vmcf_batch_set_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.vmcf_batch_sample.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp]
-        L.vmcf_batch_info.argtypes = [_vp, _ip, _ip, ctypes.c_int, _ip, _ip, _ip]
+        L.vmcf_batch_info.argtypes = [_vp, _ip, _ip, ctypes.c_int, _ip, _ip]
         _lib = L
     return _lib
 
@@ -330,8 +330,9 @@ class Batch:
         _check(lib().vmcf_batch_autotune(self.h, float(step_sigma), int(refresh_k), _stream(stream)),
                "vmcf_batch_autotune")
 
-    def set_shape(self, g: int, GS: int, groups: int):
-        _check(lib().vmcf_batch_set_shape(self.h, int(g), int(GS), int(groups)), "vmcf_batch_set_shape")
+    def set_shape(self, g: int, phase: int, GS: int, groups: int):
+        """Launch shape of phase 0 (sweep) or 1 (evaluation) for geometry g's bucket."""
+        _check(lib().vmcf_batch_set_shape(self.h, int(g), int(phase), int(GS), int(groups)), "vmcf_batch_set_shape")
 
     def sample(self, n_sweeps: int, step_sigma: float = 0.3, refresh_k: int = 26, measure: bool = False,
                stream=None):
@@ -342,8 +343,9 @@ class Batch:
         nb, nl = ctypes.c_int(), ctypes.c_int()
         geo = []
         for g in range(self.G):
-            b, gs, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-            _check(lib().vmcf_batch_info(self.h, ctypes.byref(nb), ctypes.byref(nl), g, ctypes.byref(b),
-                                         ctypes.byref(gs), ctypes.byref(gr)), "vmcf_batch_info")
-            geo.append({"bucket": b.value, "GS": gs.value, "groups": gr.value})
+            b = ctypes.c_int()
+            sh = (ctypes.c_int * 4)()
+            _check(lib().vmcf_batch_info(self.h, ctypes.byref(nb), ctypes.byref(nl), g, ctypes.byref(b), sh),
+                   "vmcf_batch_info")
+            geo.append({"bucket": b.value, "sweep": (sh[0], sh[1]), "evaluation": (sh[2], sh[3])})
         return {"buckets": nb.value, "launches": nl.value, "geometries": geo}

@@ -105,3 +105,24 @@ def test_host_finish_matches_the_numpy_finish():
     np.testing.assert_allclose(got["F"].ravel(), ref["F"], rtol=1e-9, atol=1e-9 * np.abs(ref["F"]).max())
     np.testing.assert_allclose(got["dEdC"], ref["dEdC"], rtol=1e-9, atol=1e-9 * np.abs(ref["dEdC"]).max())
     np.testing.assert_allclose(got["F_err"].ravel(), ref["F_err"], rtol=1e-8)
+
+
+def test_host_covariance_factor_matches_the_numpy_covariance():
+    """vmcf_finish_covariance (C++ low-rank factor b, Cov = b b^T) against the oracle's
+    jackknife covariance matrices; the diagonal is the square of the error bars."""
+    from oracle import estimators
+    sysx = S.make_system(0)
+    o = oracle.Oracle(sysx, nthreads=1)
+    pos = S.initial_walkers(sysx, 64, seed=5)
+    nb = 8
+    blocks = block_sums(o, sysx, pos, 0, nb)
+    Ff, Bf = D.finish_covariance(blocks, sysx.K, sysx.M, sysx.n_up, sysx.n_dn, E_REF)
+    sums = estimators.new_sums(nb, sysx.K, o.nO)
+    out = o.eval(pos, want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+    estimators.accumulate(sums, np.arange(64) * nb // 64, out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], E_REF)
+    cF, cB = estimators.jackknife_covariance(sums, E_REF)
+    np.testing.assert_allclose(Ff @ Ff.T, cF, rtol=0, atol=1e-9 * np.abs(cF).max())
+    np.testing.assert_allclose(Bf @ Bf.T, cB, rtol=0, atol=1e-9 * np.abs(cB).max())
+    est = D.finish_estimators(blocks, sysx.K, sysx.M, sysx.n_up, sysx.n_dn, E_REF)
+    np.testing.assert_allclose(np.sqrt(np.diag(Bf @ Bf.T)), est["dEdC_err"], rtol=1e-9, atol=1e-300)
+    assert np.linalg.matrix_rank(Bf) <= nb - 1  # the deviations from their mean sum to zero

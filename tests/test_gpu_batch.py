@@ -48,8 +48,8 @@ def test_batch_follows_the_single_geometry_path(ragged, precision):
     wb = _walkers(systems, specs, 20)
     batch = vmcf.Batch(systems, wa)
     info = batch.info()
-    assert info["buckets"] == 3 and info["launches"] >= 2  # the 38- and 42-electron molecules share one
-    assert info["geometries"][2]["GS"] == 128
+    assert info["buckets"] == 3 and info["launches"] >= 4  # the 38- and 42-electron molecules share one
+    assert info["geometries"][2]["sweep"] == (128, 1) and info["geometries"][2]["evaluation"] == (256, 1)
     e_ref = [-76.0, -150.0, -160.0, -300.0]
     batch.sample(3, measure=False)
     for g, w in enumerate(wa):
@@ -112,8 +112,8 @@ def test_batch_estimators_match_the_oracle(ragged):
 
 def test_launch_shape_and_autotuning_leave_the_chains_unchanged(ragged):
     """Two batches over identical walker sets: one autotuned, one with every bucket forced to
-    one walker group of 128 threads per CTA. Autotuning runs the same number of sweeps
-    whatever it picks, and no shape changes a chain beyond FP64 rounding."""
+    one walker group per CTA (128 threads for sweeps, 256 for evaluations). Autotuning runs the
+    same number of sweeps whatever it picks, and no shape changes a chain beyond FP64 rounding."""
     specs = [(sx, W) for (sx, _), W in zip(ragged, (64, 40, 48, 24))]
     systems = [vmcf.System(sx, vmcf.FP64, force_group=True) for sx, _ in specs]
     wa = _walkers(systems, specs, 40)
@@ -123,10 +123,12 @@ def test_launch_shape_and_autotuning_leave_the_chains_unchanged(ragged):
     ba.autotune()
     bb.autotune()
     for g in range(len(specs)):
-        bb.set_shape(g, 128, 1)
+        bb.set_shape(g, 0, 128, 1)
+        bb.set_shape(g, 1, 256, 1)
     info = ba.info()
     for geo in info["geometries"]:
-        assert geo["GS"] in (32, 128) and geo["groups"] in (1, 2, 4)
+        for ph in ("sweep", "evaluation"):
+            assert geo[ph] in ((32, 1), (32, 2), (32, 4), (32, 8), (128, 1), (128, 2), (256, 1))
     for w in wa + wb:
         w.reset_accumulators(-100.0)
     ba.sample(2, measure=True)

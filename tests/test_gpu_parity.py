@@ -63,12 +63,17 @@ def test_evaluate_fp64_c2oh6(sys1, force_group):
             assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
 
 
-def test_evaluate_fp64_c9o4h8_sample():
+@pytest.mark.parametrize("group", [0, 32, 128, 256])
+def test_evaluate_fp64_c9o4h8_sample(group):
+    """94 electrons (47 orbitals per spin): walker groups narrower and wider than a spin block."""
     sys4 = S.make_system(4)
     pos = S.initial_walkers(sys4, 6, seed=7)
     want = ("EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O")
     ref = oracle.Oracle(sys4).eval(pos, want=want)
-    got = gpu_eval(vmcf.System(sys4, vmcf.FP64), pos, want)
+    g = vmcf.System(sys4, vmcf.FP64)
+    if group:
+        g.set_tuning("measure_group_size", group)
+    got = gpu_eval(g, pos, want)
     for k in want:
         assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
 

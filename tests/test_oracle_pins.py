@@ -457,3 +457,27 @@ def test_jackknife_of_a_mean_is_the_block_standard_error():
     bm = x.reshape(nb, per).mean(1)
     assert abs(res["E"] - x.mean()) < 1e-12
     assert abs(res["E_err"] - bm.std(ddof=1) / math.sqrt(nb)) < 1e-12
+
+
+def test_jackknife_covariance_of_means_is_the_block_covariance():
+    """When the estimators reduce to plain sample means (E_L averaging to E_ref inside every
+    block, so that F = -<dE_L/dR> and B = 2 <(E_L - E_ref) O>), the delete-one-block jackknife
+    covariance equals the textbook covariance of the block means divided by the block count."""
+    rng = np.random.default_rng(1)
+    nb, per, K, nO = 8, 40, 2, 5
+    e_ref = -1.5
+    n = nb * per
+    dEL = rng.normal(size=(n, K, 3))
+    O = rng.normal(size=(n, nO))
+    dev = rng.normal(size=n // 2)
+    EL = e_ref + np.stack([dev, -dev], 1).ravel()  # +d, -d pairs: every block averages to e_ref
+    blk = np.repeat(np.arange(nb), per)
+    sums = estimators.new_sums(nb, K, nO)
+    estimators.accumulate(sums, blk, EL, np.zeros((n, K, 3)), dEL, O, e_ref)
+    cF, cB = estimators.jackknife_covariance(sums, e_ref)
+    for x, c in ((-dEL.reshape(n, -1), cF), (2.0 * (EL - e_ref)[:, None] * O, cB)):
+        bm = x.reshape(nb, per, -1).mean(1)
+        ref = np.cov(bm, rowvar=False, ddof=1) / nb
+        np.testing.assert_allclose(c, ref, rtol=1e-10, atol=1e-14)
+    res = estimators.finish(sums, e_ref)
+    np.testing.assert_allclose(np.sqrt(np.diag(cB)), res["dEdC_err"], rtol=1e-12)
