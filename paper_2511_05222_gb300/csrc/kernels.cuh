@@ -121,7 +121,8 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
       const EPos po = make_epos(pos + 3 * e);
       ao_point<T, GS, 0, false>(S, pn, ao, 0);
       gsync<GS>();
-      double part[2] = {0.0, 0.0};
+      double part[1] = {0.0};  // determinant ratio (FP64)
+      T dJ = T(0);              // Jastrow exponent difference
       // new orbital row phi_i(r'): with GS >= 2n the mu sum is split in kp parts (partial
       // sums of parts 1 and 2 go through wv and col) so that kp n threads share it
       const int kp = GS >= 3 * n ? 3 : (GS >= 2 * n ? 2 : 1);
@@ -166,8 +167,8 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
               d0[k] = (po.h[k] - ph[3 * q + k]) + (po.l[k] - pl[3 * q + k]);
             }
           }
-          part[1] += (double)(pade_value<T>(a, F, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
-                              pade_value<T>(a, F, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2])));
+          dJ += pade_value<T>(a, F, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
+                pade_value<T>(a, F, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]));
         } else {
           if (!S.J1) continue;
           const int I = q - Ne;
@@ -175,17 +176,17 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
           T d1[3], d0[3];
           disp_nuc<T>(S, pn, I, d1);
           disp_nuc<T>(S, po, I, d0);
-          part[1] += (double)(pade_value<T>(mz, b, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
-                              pade_value<T>(mz, b, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2])));
+          dJ += pade_value<T>(mz, b, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
+                pade_value<T>(mz, b, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]));
         }
       }
       gsync<GS>();
-      group_sum<GS, 2>(part, red);
+      group_sum_dt<GS>(part[0], dJ, red);
       const double R = part[0];
       uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
       philox4x64_10(r2, P.k0, P.k1);
       const double u = u01(r2[0]);
-      const double pr = R * R * (double)dexp<T>((T)(2.0 * part[1]));
+      const double pr = R * R * (double)dexp<T>(T(2) * dJ);
       const bool ok = isfinite(pr) && R != 0.0;
       if (!ok) ++nrej;
       if (ok && u < pr) {
@@ -344,46 +345,60 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
     }
   }
 
-  // Pass 2: gradient and Laplacian rows of the MOs per electron; determinant drift
-  // g_e = sum_i G_ei B_ie, l_e = sum_i L_ei B_ie; P_ei = L_ei + 2 gradJ_e . G_ei;
+  // Pass 2: gradient and Laplacian rows of the MOs, a few electrons at a time; determinant
+  // drift g_e = sum_i G_ei B_ie, l_e = sum_i L_ei B_ie; P_ei = L_ei + 2 gradJ_e . G_ei;
   // kinetic term -1/2 (l_e + lap J_e + |grad J_e|^2 + 2 grad J_e . g_e).
-  double ekin = 0.0;
-  for (int e = 0; e < Ne; ++e) {
-    const int sg = e < nup ? 0 : 1;
-    const int n = sg == 0 ? nup : S.ndn, el = e - (sg == 0 ? 0 : nup), off = sg == 0 ? 0 : nup * nup;
-    const T* Bs = Bt + off;
-    const T* C = coefC<T>(S, sg);
-    ao_point<T, GS, 1, true>(S, make_epos(pos + 3 * e), ao, M);
-    gsync<GS>();
-    for (int q = t; q < 4 * n; q += GS) {
-      const int c = q / n, i = q - c * n;
-      const T* a = ao + c * M;
-      T v = 0;
-      for (int mu = 0; mu < M; ++mu) v += a[mu] * __ldg(C + mu * n + i);
-      mo[c * nmax + i] = v;
+  double ekin = 0.0;  // this thread's share
+  {
+    const int ns = S.nshell;
+    double* esum = red + 32;  // [4 chunk] per-electron sums, after the group-sum scratch
+    for (int sg = 0; sg < 2; ++sg) {
+      const int n = sg == 0 ? nup : S.ndn;
+      if (n == 0) continue;
+      const int e0 = sg == 0 ? 0 : nup, off = sg == 0 ? 0 : nup * nup;
+      const T* Bs = Bt + off;
+      const T* C = coefC<T>(S, sg);
+      const int ng = GS >= n ? GS / n : 1;
+      const int ch = L.p2_chunk < 2 * ng ? L.p2_chunk : 2 * ng;  // 4 ch rows, at most 8 per thread
+      for (int c0 = 0; c0 < n; c0 += ch) {
+        const int nc = n - c0 < ch ? n - c0 : ch;
+        for (int q = t; q < nc * ns; q += GS) {  // AO gradient and Laplacian rows: (electron, shell) pairs
+          const int r = q / ns, sh = q - r * ns;
+          shell_point<T, 1, true>(S, make_epos(pos + 3 * (e0 + c0 + r)), sh, ao + r * 4 * M, M);
+        }
+        gsync<GS>();
+        orbital_block<T, GS>(ao, 4 * nc, C, M, n, mo, nmax);  // mo row 4 r + c: component c of electron r
+        gsync<GS>();
+        for (int q = t; q < nc * n; q += GS) {
+          const int r = q / n, i = q - r * n, e = e0 + c0 + r;
+          const T* m = mo + 4 * r * nmax;
+          Pm[off + (c0 + r) * n + i] =
+              m[3 * nmax + i] + T(2) * (Jg[3 * e] * m[i] + Jg[3 * e + 1] * m[nmax + i] + Jg[3 * e + 2] * m[2 * nmax + i]);
+        }
+        if (t < 4 * nc) {  // sum_i (component c of electron r)_i B_{i, el}
+          const int r = t >> 2, el = c0 + r;
+          const T* m = mo + t * nmax;
+          double v = 0.0;
+          for (int i = 0; i < n; ++i) v += (double)(m[i] * Bs[i * n + el]);
+          esum[t] = v;
+        }
+        gsync<GS>();
+        if (t < nc) {
+          const int e = e0 + c0 + t;
+          const double g0 = esum[4 * t], g1 = esum[4 * t + 1], g2 = esum[4 * t + 2], lp = esum[4 * t + 3];
+          gd[3 * e] = (T)g0;
+          gd[3 * e + 1] = (T)g1;
+          gd[3 * e + 2] = (T)g2;
+          const double j0 = (double)Jg[3 * e], j1 = (double)Jg[3 * e + 1], j2 = (double)Jg[3 * e + 2];
+          const double jj = j0 * j0 + j1 * j1 + j2 * j2;
+          const double jgd = j0 * g0 + j1 * g1 + j2 * g2;
+          ekin += -0.5 * (lp + (double)Jl[e] + jj + 2.0 * jgd);
+        }
+      }
     }
-    gsync<GS>();
-    double part[4] = {0.0, 0.0, 0.0, 0.0};
-    const T j0 = Jg[3 * e], j1 = Jg[3 * e + 1], j2 = Jg[3 * e + 2];
-    for (int i = t; i < n; i += GS) {
-      const T b = Bs[i * n + el];
-      const T g0 = mo[i], g1 = mo[nmax + i], g2 = mo[2 * nmax + i], lp = mo[3 * nmax + i];
-      part[0] += (double)(g0 * b);
-      part[1] += (double)(g1 * b);
-      part[2] += (double)(g2 * b);
-      part[3] += (double)(lp * b);
-      Pm[off + el * n + i] = lp + T(2) * (j0 * g0 + j1 * g1 + j2 * g2);
-    }
-    group_sum<GS, 4>(part, red);
-    if (t == 0) {
-      gd[3 * e] = (T)part[0];
-      gd[3 * e + 1] = (T)part[1];
-      gd[3 * e + 2] = (T)part[2];
-    }
-    const double jj = (double)j0 * j0 + (double)j1 * j1 + (double)j2 * j2;
-    const double jgd = (double)j0 * part[0] + (double)j1 * part[1] + (double)j2 * part[2];
-    ekin += -0.5 * (part[3] + (double)Jl[e] + jj + 2.0 * jgd);
-    gsync<GS>();
+    double ek[1] = {ekin};
+    group_sum<GS, 1>(ek, red);
+    ekin = ek[0];
   }
   const double EL = ekin + vs[0] + vs[1] + S.Vnn;
   const double cw = EL - P.e_ref;

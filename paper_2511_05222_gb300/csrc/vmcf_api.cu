@@ -119,15 +119,16 @@ GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool with
   L.Jl = take((int)tsz * s.Ne);
   L.gd = take((int)tsz * 3 * s.Ne);
   L.ao_rows = 8;
+  L.p2_chunk = 3;
   L.ao = take((int)tsz * 14 * s.M);
-  L.mo = take((int)tsz * 4 * s.nmax);
+  L.mo = take((int)tsz * 4 * L.p2_chunk * s.nmax);
   L.frc = take((int)tsz * 6 * s.K);
   L.fa = take((int)tsz * 6 * s.M);
   L.Ow = take((int)tsz * s.M * s.nmax);
   L.D = withD ? take((int)tsz * s.M * s.nmax) : L.Ow;
   L.piv = take(4 * s.nmax);
   L.f = take(8 * (3 * s.nmax + 1));
-  L.red = take(8 * 4 * std::max(1, GS / 32));
+  L.red = take(8 * (32 + 4 * L.p2_chunk));  // group-sum scratch (<= 32 doubles), then per-electron sums
   L.scal = take(32);
   L.bytes = align16(o);
   return L;

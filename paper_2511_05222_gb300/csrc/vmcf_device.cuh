@@ -103,6 +103,32 @@ __device__ __forceinline__ void group_sum(double (&v)[NV], double* scratch) {
   }
 }
 
+// Group sums of one double and one value of type T (identical results in every thread).
+// scratch: >= 2 * GS/32 doubles.
+template <int GS, typename T>
+__device__ __forceinline__ void group_sum_dt(double& a, T& b, double* scratch) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if constexpr (GS > 32) {
+    constexpr int NW = GS / 32;
+    const int t = threadIdx.x % GS;
+    if ((t & 31) == 0) {
+      scratch[t >> 5] = a;
+      scratch[NW + (t >> 5)] = (double)b;
+    }
+    gsync<GS>();
+    double sa = 0.0;
+    T sb = T(0);
+    for (int w = 0; w < NW; ++w) {
+      sa += scratch[w];
+      sb += (T)scratch[NW + w];
+    }
+    a = sa;
+    b = sb;
+    gsync<GS>();
+  }
+}
+
 // ---------------------------------------------------------------- Philox4x64-10
 // Salmon et al., "Parallel random numbers: as easy as 1, 2, 3" (SC'11), 10 rounds.
 __device__ __forceinline__ void philox4x64_10(uint64_t x[4], uint64_t k0, uint64_t k1) {
@@ -461,19 +487,20 @@ __device__ void gj_inverse(double* A, int n, int* piv, double* f, int* flag, dou
   gsync<GS>();
 }
 
-// ---------------------------------------------------------------- Slater matrix build
-// R rows (rows row0, row0 + ng, ...) of one orbital column: independent accumulators that
-// share each coefficient load. Rows past nc are computed from a valid row and not stored.
-template <typename T, int R>
-__device__ __forceinline__ void slater_rows(const T* aobuf, const T* C, int M, int n, int col, int row0, int ng,
-                                            int nc, double* A) {
+// ---------------------------------------------------------------- orbital rows
+// out[r][col] = sum_mu rows[r][mu] C[mu][col] for the R rows row0, row0 + ng, ... of a chunk of
+// nrows rows (row stride M): independent accumulators that share each coefficient load. Rows
+// past nrows are computed from a valid row and not stored.
+template <typename T, int R, typename OutT>
+__device__ __forceinline__ void orbital_rows(const T* rows, const T* C, int M, int n, int col, int row0, int ng,
+                                             int nrows, OutT* out, int out_stride) {
   T v[R];
   const T* a[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     v[r] = T(0);
     const int row = row0 + r * ng;
-    a[r] = aobuf + (row < nc ? row : nc - 1) * M;
+    a[r] = rows + (row < nrows ? row : nrows - 1) * M;
   }
   for (int mu = 0; mu < M; ++mu) {
     const T c = __ldg(C + mu * n + col);
@@ -483,25 +510,45 @@ __device__ __forceinline__ void slater_rows(const T* aobuf, const T* C, int M, i
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int row = row0 + r * ng;
-    if (row < nc) A[row * n + col] = (double)v[r];
+    if (row < nrows) out[row * out_stride + col] = (OutT)v[r];
   }
 }
 
+// All columns of nrows (<= 8 ng) rows of AO values times C^s (n columns), over the group:
+// with GS >= n thread t owns column t % n and rows t / n + k ng (ng = GS / n); with GS < n it
+// owns columns t, t + GS, ... and every row.
+template <typename T, int GS, typename OutT>
+__device__ __forceinline__ void orbital_block(const T* rows, int nrows, const T* C, int M, int n, OutT* out,
+                                              int out_stride) {
+  const int t = threadIdx.x % GS;
+  const bool wide = GS >= n;
+  const int ng = wide ? GS / n : 1;
+  const int col0 = wide ? t % n : t, rg = wide ? t / n : 0, dcol = wide ? n : GS;
+  for (int col = col0; col < n && rg < ng && rg < nrows; col += dcol) {
+    switch ((nrows - rg + ng - 1) / ng) {  // rows of this thread
+      case 1: orbital_rows<T, 1>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 2: orbital_rows<T, 2>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 3: orbital_rows<T, 3>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 4: orbital_rows<T, 4>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 5: orbital_rows<T, 5>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 6: orbital_rows<T, 6>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 7: orbital_rows<T, 7>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      default: orbital_rows<T, 8>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Slater matrix build
 // A^s_{el, i} = phi_i(r_e) = sum_mu psi_mu(r_e) C^s_{mu i} (Eq. restricted-C), computed
-// in T and stored in double for the inversion. aobuf: T[chunk * M] scratch. chunk electrons
-// at a time: their AO values over (electron, shell) pairs, then their rows of A, each thread
-// owning one orbital column and every ng-th row of the chunk.
+// in T and stored in double for the inversion. aobuf: T[chunk * M] scratch; chunk electrons
+// at a time: their AO values over (electron, shell) pairs, then their rows of A.
 template <typename T, int GS>
 __device__ void build_slater(const DevSys& S, const double* pos, int sg, double* A, T* aobuf, int chunk) {
   const int t = threadIdx.x % GS;
   const int n = sg == 0 ? S.nup : S.ndn, e0 = sg == 0 ? 0 : S.nup, M = S.M, ns = S.nshell;
   const T* C = coefC<T>(S, sg);
-  chunk = chunk < 1 ? 1 : (chunk > 8 ? 8 : chunk);
-  // GS >= n: thread t owns column t % n and row group t / n of GS / n groups;
-  // GS < n: thread t owns columns t, t + GS, ... and every row
-  const bool wide = GS >= n;
-  const int ng = wide ? GS / n : 1;
-  const int col0 = wide ? t % n : t, rg = wide ? t / n : 0, dcol = wide ? n : GS;
+  const int ng = GS >= n ? GS / n : 1;
+  chunk = chunk < 1 ? 1 : (chunk > 8 * ng ? 8 * ng : chunk);
   for (int c0 = 0; c0 < n; c0 += chunk) {
     const int nc = n - c0 < chunk ? n - c0 : chunk;
     for (int q = t; q < nc * ns; q += GS) {
@@ -509,19 +556,7 @@ __device__ void build_slater(const DevSys& S, const double* pos, int sg, double*
       shell_point<T, 0, true>(S, make_epos(pos + 3 * (e0 + c0 + r)), sh, aobuf + r * M, 0);
     }
     gsync<GS>();
-    for (int col = col0; col < n && rg < ng && rg < nc; col += dcol) {
-      double* Ar = A + c0 * n;
-      switch ((nc - rg + ng - 1) / ng) {  // rows of this thread
-        case 1: slater_rows<T, 1>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
-        case 2: slater_rows<T, 2>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
-        case 3: slater_rows<T, 3>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
-        case 4: slater_rows<T, 4>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
-        case 5: slater_rows<T, 5>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
-        case 6: slater_rows<T, 6>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
-        case 7: slater_rows<T, 7>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
-        default: slater_rows<T, 8>(aobuf, C, M, n, col, rg, ng, nc, Ar); break;
-      }
-    }
+    orbital_block<T, GS>(aobuf, nc, C, M, n, A + c0 * n, n);
     gsync<GS>();
   }
 }

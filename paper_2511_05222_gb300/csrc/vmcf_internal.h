@@ -11,7 +11,8 @@ namespace vmcf {
 // Byte offsets of one walker group's shared-memory region; computed on the host.
 struct GroupLayout {
   int pos, ph, pl, Bd, Bt, P, Q, Jg, Jl, gd, ao, mo, frc, fa, Ow, D, piv, f, red, scal, row, wv, col;
-  int ao_rows;  // AO rows of M values the ao buffer holds (electrons per Slater-build chunk)
+  int ao_rows;   // AO rows of M values the ao buffer holds (electrons per Slater-build chunk)
+  int p2_chunk;  // electrons per chunk of the gradient/Laplacian pass (4 AO rows each)
   int bytes;    // size of one group's region (16-byte multiple)
 };
 
