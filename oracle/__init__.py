@@ -60,6 +60,8 @@ def lib():
         L.oracle_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
         L.osys_eval.restype = ctypes.c_int
         L.osys_eval.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int] + [_dp] * 10
+        L.osys_eval_warp.restype = ctypes.c_int
+        L.osys_eval_warp.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp]
         L.osys_refresh.restype = ctypes.c_int
         L.osys_refresh.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_int]
         L.osys_sample.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_uint64, ctypes.c_uint64,
@@ -146,6 +148,17 @@ class Oracle:
         order = ["EL", "logpsi", "sign", "dlnpsi_dR", "dEL_dR", "O", "dEL_dC", "grad_lnpsi", "lap_lnpsi", "parts"]
         nsing = lib().osys_eval(self.h, W, _p(pos), self.nthreads, *[_p(out.get(k)) for k in order])
         out["n_singular"] = nsing
+        return out
+
+    def eval_warp(self, pos: np.ndarray) -> dict:
+        """Electron derivatives dE_L/dr (W, Ne, 3) and the space-warp force vectors
+        dE_L^sw/dR, d ln Psi^sw/dR (W, K, 3) for positions (W, Ne, 3)."""
+        pos = _f64(pos)
+        W = pos.shape[0]
+        out = {"dEL_dr": np.zeros((W, self.Ne, 3)), "dEL_sw": np.zeros((W, self.K, 3)),
+               "dlnpsi_sw": np.zeros((W, self.K, 3))}
+        out["n_singular"] = lib().osys_eval_warp(self.h, W, _p(pos), self.nthreads, _p(out["dEL_dr"]),
+                                                 _p(out["dEL_sw"]), _p(out["dlnpsi_sw"]))
         return out
 
     def refresh(self, pos: np.ndarray) -> np.ndarray:

@@ -258,12 +258,14 @@ struct WalkerOut {
   std::vector<double> dlnpsi_dR, dEL_dR;     // [K][3]
   std::vector<double> O[2], dELdC[2];         // [M][n_s]
   std::vector<double> glnpsi, laplnpsi;       // [Ne][3], [Ne]
+  std::vector<double> dEL_dr;                 // [Ne][3] (want_electron)
+  std::vector<double> dEL_sw, dlnpsi_sw;      // [K][3] space-warp force vectors (want_electron)
   double Vee, Ven, Vnn, Ekin;
   int singular;
 };
 
 // ---------------------------------------------------------------- one walker, all outputs
-void eval_walker(const OSys& s, const double* pos, bool want_dC, WalkerOut& w) {
+void eval_walker(const OSys& s, const double* pos, bool want_dC, WalkerOut& w, bool want_electron = false) {
   const int Ne = s.nup + s.ndn, M = s.M, K = s.K;
   // AO table at every electron.
   std::vector<double> ao((size_t)Ne * M * NC);
@@ -472,6 +474,109 @@ void eval_walker(const OSys& s, const double* pos, bool want_dC, WalkerOut& w) {
       w.dlnpsi_dR[3 * I + d] = dlnpsi;
       w.dEL_dR[3 * I + d] = dEL;
     }
+
+  // ------------------------------------------------ electron derivatives, forward mode
+  // For each electron coordinate lambda = r_{q,d}: row q of A, G and L moves (d psi / d lambda
+  // = d_d psi at r_q, and likewise one order up); dB = -B dA B. In the Jastrow, every pair
+  // term u(r_q - r_j) and every chi_I(r_q - R_I) depends on r_q; V_ee and V_en directly.
+  if (want_electron) {
+    w.dEL_dr.assign((size_t)Ne * 3, 0.0);
+    for (int q = 0; q < Ne; ++q)
+      for (int d = 0; d < 3; ++d) {
+        const int sq = spin_of(s, q), n = nspin(s, sq), e0 = first_e(s, sq), elq = q - e0;
+        std::vector<double> dg((size_t)Ne * 3, 0.0), dl(Ne, 0.0);
+        // the moved rows: dA_{elq, i}, dG_{elq, i}, dL_{elq, i}
+        std::vector<double> dArow(n, 0.0), dLrow(n, 0.0), dGrow[3];
+        for (int c = 0; c < 3; ++c) dGrow[c].assign(n, 0.0);
+        for (int i = 0; i < n; ++i)
+          for (int mu = 0; mu < M; ++mu) {
+            double c = s.C[sq][(size_t)mu * n + i];
+            dArow[i] += AOv(q, mu, 1 + d) * c;
+            for (int cc = 0; cc < 3; ++cc) dGrow[cc][i] += AOv(q, mu, hidx(d, cc)) * c;
+            dLrow[i] += AOv(q, mu, 11 + d) * c;
+          }
+        // dB = -B dA B with dA nonzero in row elq only: dB_{i e} = -B_{i, elq} v_e,
+        // v_e = sum_k dA_{elq, k} B_{k e}
+        std::vector<double> v(n, 0.0);
+        for (int e = 0; e < n; ++e)
+          for (int k = 0; k < n; ++k) v[e] += dArow[k] * B[sq][(size_t)k * n + e];
+        for (int el = 0; el < n; ++el) {
+          int e = e0 + el;
+          for (int i = 0; i < n; ++i) {
+            double b = B[sq][(size_t)i * n + el], db = -B[sq][(size_t)i * n + elq] * v[el];
+            for (int c = 0; c < 3; ++c)
+              dg[3 * e + c] += (el == elq ? dGrow[c][i] : 0.0) * b + G[sq][c][(size_t)el * n + i] * db;
+            dl[e] += (el == elq ? dLrow[i] : 0.0) * b + L[sq][(size_t)el * n + i] * db;
+          }
+        }
+        double dEL = 0.0;
+        std::vector<double> dJg((size_t)Ne * 3, 0.0), dJl(Ne, 0.0);
+        for (int j = 0; j < Ne; ++j) {
+          if (j == q) continue;
+          double sv[3];
+          for (int c = 0; c < 3; ++c) sv[c] = pos[3 * q + c] - pos[3 * j + c];
+          double r = std::sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
+          dEL += -sv[d] / (r * r * r);  // V_ee
+          if (s.J2) {
+            bool par = spin_of(s, q) == spin_of(s, j);
+            RadDeriv du = radial_derivs(pade(par ? s.ap : s.aa, par ? s.Fp : s.Fa, r), sv);
+            for (int c = 0; c < 3; ++c) {
+              dJg[3 * q + c] += du.H[d][c];  // grad_q u(r_q - r_j) moves with r_q
+              dJg[3 * j + c] -= du.H[d][c];  // grad_j u = -grad_q u
+            }
+            dJl[q] += du.glap[d];  // both Laplacians of the pair term equal lap u(r_q - r_j)
+            dJl[j] += du.glap[d];
+          }
+        }
+        for (int I = 0; I < K; ++I) {
+          double sv[3];
+          for (int c = 0; c < 3; ++c) sv[c] = pos[3 * q + c] - s.R[3 * I + c];
+          double r = std::sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
+          dEL += s.Z[I] * sv[d] / (r * r * r);  // V_en
+          if (s.J1) {
+            RadDeriv df = radial_derivs(chi(s.Z[I], s.ben, r), sv);
+            for (int c = 0; c < 3; ++c) dJg[3 * q + c] += df.H[d][c];
+            dJl[q] += df.glap[d];
+          }
+        }
+        for (int e = 0; e < Ne; ++e) {
+          double t = dl[e] + dJl[e];
+          for (int c = 0; c < 3; ++c)
+            t += 2.0 * Jg[3 * e + c] * dJg[3 * e + c] + 2.0 * dJg[3 * e + c] * gdet[3 * e + c] +
+                 2.0 * Jg[3 * e + c] * dg[3 * e + c];
+          dEL += -0.5 * t;
+        }
+        w.dEL_dr[3 * q + d] = dEL;
+      }
+    // Space-warp coordinate transformation (force expression with omega, Sec. Methods /
+    // App.): electrons near nucleus a move with it, with weight
+    // omega_a(r) = kappa(|r - R_a|) / sum_b kappa(|r - R_b|), kappa(r) = 1 / r^4;
+    // dE_L^sw/dR_a = dE_L/dR_a + sum_e omega_a(r_e) dE_L/dr_e,
+    // d ln Psi^sw/dR_a = d ln Psi/dR_a + sum_e [omega_a(r_e) d ln Psi/dr_e + 1/2 grad omega_a(r_e)].
+    w.dEL_sw = w.dEL_dR;
+    w.dlnpsi_sw = w.dlnpsi_dR;
+    std::vector<double> kap(K), gk((size_t)K * 3);
+    for (int e = 0; e < Ne; ++e) {
+      double ks = 0.0, gks[3] = {0, 0, 0};
+      for (int b = 0; b < K; ++b) {
+        double sv[3];
+        for (int c = 0; c < 3; ++c) sv[c] = pos[3 * e + c] - s.R[3 * b + c];
+        double r2 = sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2];
+        kap[b] = 1.0 / (r2 * r2);
+        for (int c = 0; c < 3; ++c) gk[3 * b + c] = -4.0 * sv[c] / (r2 * r2 * r2);  // grad of r^-4
+        ks += kap[b];
+        for (int c = 0; c < 3; ++c) gks[c] += gk[3 * b + c];
+      }
+      for (int a = 0; a < K; ++a) {
+        double om = kap[a] / ks;
+        for (int c = 0; c < 3; ++c) {
+          double gom = (gk[3 * a + c] * ks - kap[a] * gks[c]) / (ks * ks);
+          w.dEL_sw[3 * a + c] += om * w.dEL_dr[3 * e + c];
+          w.dlnpsi_sw[3 * a + c] += om * w.glnpsi[3 * e + c] + 0.5 * gom;
+        }
+      }
+    }
+  }
 
   // ------------------------------------------------ orbital-coefficient derivatives
   // O^s_{mu i} = d ln Psi / d C^s_{mu i} = sum_{e in s} psi_mu(r_e) B_{i e}.
@@ -746,6 +851,28 @@ int osys_eval(void* p, int W, const double* pos, int nthreads, double* EL, doubl
       double* q = parts + (size_t)w * 5;
       q[0] = o.Ekin; q[1] = o.Vee; q[2] = o.Ven; q[3] = o.Vnn; q[4] = o.J;
     }
+  }
+  return nsing;
+}
+
+// Electron derivatives and space-warp force vectors per walker (any output may be NULL):
+// dEL_dr [W][Ne][3], dEL_sw and dlnpsi_sw [W][K][3].
+int osys_eval_warp(void* p, int W, const double* pos, int nthreads, double* dEL_dr, double* dEL_sw,
+                   double* dlnpsi_sw) {
+  OSys* s = static_cast<OSys*>(p);
+  const int Ne = s->nup + s->ndn, K = s->K;
+  int nsing = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 2) reduction(+ : nsing)
+#endif
+  for (int w = 0; w < W; ++w) {
+    WalkerOut o;
+    eval_walker(*s, pos + (size_t)w * Ne * 3, false, o, true);
+    nsing += o.singular;
+    if (dEL_dr) std::copy(o.dEL_dr.begin(), o.dEL_dr.end(), dEL_dr + (size_t)w * Ne * 3);
+    if (dEL_sw) std::copy(o.dEL_sw.begin(), o.dEL_sw.end(), dEL_sw + (size_t)w * K * 3);
+    if (dlnpsi_sw) std::copy(o.dlnpsi_sw.begin(), o.dlnpsi_sw.end(), dlnpsi_sw + (size_t)w * K * 3);
   }
   return nsing;
 }

@@ -36,7 +36,6 @@ constexpr int kHdr = (int)((sizeof(BatchGeom) + 16 + 15) / 16 * 16);
 struct Shape {
   int GS = 32, groups = 1;
   bool operator<(const Shape& o) const { return std::tie(GS, groups) < std::tie(o.GS, o.groups); }
-  bool operator==(const Shape& o) const { return GS == o.GS && groups == o.groups; }
 };
 
 struct LaunchPlan {

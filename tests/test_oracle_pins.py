@@ -481,3 +481,60 @@ def test_jackknife_covariance_of_means_is_the_block_covariance():
         np.testing.assert_allclose(c, ref, rtol=1e-10, atol=1e-14)
     res = estimators.finish(sums, e_ref)
     np.testing.assert_allclose(np.sqrt(np.diag(cB)), res["dEdC_err"], rtol=1e-12)
+
+
+# ------------------------------------------------------------------ space warp (SWCT)
+def test_electron_derivatives_of_EL_by_finite_differences(sys0):
+    """dE_L/dr_e against O(h^4) central differences of E_L, and the exact translational sum
+    rule sum_I dE_L/dR_I + sum_e dE_L/dr_e = 0."""
+    o = oracle.Oracle(sys0)
+    pos = S.initial_walkers(sys0, 6, seed=13)
+    w = o.eval_warp(pos)
+    for e, d in [(0, 0), (2, 1), (5, 2), (9, 0), (4, 1)]:
+        def f(t):
+            p = pos.copy()
+            p[:, e, d] += t
+            return o.eval(p, want=("EL",))["EL"]
+        fd = _rich(f, 1e-4)
+        np.testing.assert_allclose(w["dEL_dr"][:, e, d], fd, rtol=1e-6, atol=1e-6 * np.abs(fd).max())
+    out = o.eval(pos, want=("dEL_dR",))
+    tot = out["dEL_dR"].sum(1) + w["dEL_dr"].sum(1)
+    assert np.abs(tot).max() < 1e-9 * np.abs(w["dEL_dr"]).max()
+
+
+def _omega(R, r):
+    """Space-warp weights omega_a(r) = |r - R_a|^-4 / sum_b |r - R_b|^-4, (npts, K)."""
+    k = ((r[:, None, :] - R[None, :, :]) ** 2).sum(-1) ** -2
+    return k / k.sum(1, keepdims=True)
+
+
+def test_space_warp_vectors_are_derivatives_along_the_warp(sys0):
+    """dE_L^sw/dR_a and d ln Psi^sw/dR_a are the total derivatives when nucleus a moves by t e_d
+    and every electron by omega_a(r_e) t e_d (plus half the log-Jacobian of that electron map
+    for ln Psi); they sum to zero over the nuclei (the warp of every nucleus together is a rigid
+    translation)."""
+    o = oracle.Oracle(sys0)
+    pos = S.initial_walkers(sys0, 5, seed=14)
+    w = o.eval_warp(pos)
+    assert np.abs(w["dEL_sw"].sum(1)).max() < 1e-9 * np.abs(w["dEL_sw"]).max()
+    assert np.abs(w["dlnpsi_sw"].sum(1)).max() < 1e-9 * np.abs(w["dlnpsi_sw"]).max()
+    W, Ne = pos.shape[:2]
+    om = _omega(sys0.R, pos.reshape(-1, 3)).reshape(W, Ne, sys0.K)
+    for a, d in [(0, 0), (1, 2), (2, 1)]:
+        def dom(t):  # d omega_a / d r_d at each electron, by central differences of the weights
+            p = pos.reshape(-1, 3).copy()
+            p[:, d] += t
+            return _omega(sys0.R, p)[:, a].reshape(W, Ne)
+        gom = _rich(dom, 1e-5)
+
+        def moved(t, what):
+            p = pos.copy()
+            p[:, :, d] += om[:, :, a] * t
+            out = _with_R(sys0, a, d, t).eval(p, want=(what,))[what]
+            if what == "logpsi":
+                out = out + 0.5 * np.log1p(t * gom).sum(1)
+            return out
+        fdE = _rich(lambda t: moved(t, "EL"), 1e-4)
+        fdl = _rich(lambda t: moved(t, "logpsi"), 1e-4)
+        np.testing.assert_allclose(w["dEL_sw"][:, a, d], fdE, rtol=1e-5, atol=1e-5 * np.abs(fdE).max())
+        np.testing.assert_allclose(w["dlnpsi_sw"][:, a, d], fdl, rtol=1e-6, atol=1e-6 * np.abs(fdl).max())
