@@ -66,6 +66,13 @@ typedef enum {
  * other. */
 #define VMCF_FORCE_GROUP_PATH 0x100
 
+/* OR-ed into `precision` at vmcf_init_system: also accumulate the space-warp (SWCT) force
+ * estimator (the force expression with the warp weights omega, Methods/appendix: electrons
+ * near nucleus a move with it with weight omega_a(r) = kappa(|r - R_a|) / sum_b kappa(|r - R_b|),
+ * kappa(r) = r^-4). Its walker sums are appended to each block (see vmcf_block_sums); read the
+ * estimate with vmcf_reduce_warp. Same expectation as the plain forces, smaller variance. */
+#define VMCF_SPACE_WARP 0x200
+
 typedef struct vmcf_system_s* vmcf_system_t;   /* opaque, library-owned */
 typedef struct vmcf_walkers_s* vmcf_walkers_t; /* opaque, library-owned device state */
 
@@ -164,7 +171,8 @@ int vmcf_reduce_estimators(vmcf_system_t sys, vmcf_walkers_t wk, double* E, doub
                            double* F_err, double* dEdC, double* dEdC_err, double* rhs_BQ, void* stream);
 /* Raw block sums (synchronises): host [nblocks][vmcf_accumulator_length()] doubles, layout
  * n, sum E_L, sum E_L^2, sum dE_L/dR [3K], sum dlnPsi/dR [3K], sum (E_L-E_ref) dlnPsi/dR [3K],
- * sum O [nO], sum (E_L-E_ref) O [nO], with nO = M (n_up + n_dn). */
+ * sum O [nO], sum (E_L-E_ref) O [nO], with nO = M (n_up + n_dn); with VMCF_SPACE_WARP followed by
+ * sum dE_L^sw/dR [3K], sum dlnPsi^sw/dR [3K], sum (E_L-E_ref) dlnPsi^sw/dR [3K]. */
 int vmcf_block_sums(vmcf_system_t sys, vmcf_walkers_t wk, double* out, void* stream);
 int vmcf_accumulator_length(vmcf_system_t sys);
 
@@ -175,6 +183,23 @@ int vmcf_accumulator_length(vmcf_system_t sys);
  * Host outputs as in vmcf_reduce_estimators (any may be NULL). */
 int vmcf_finish_estimators(const double* blocks, int nblocks, int K, int M, int n_up, int n_dn, double e_ref,
                            double* E, double* E_err, double* F, double* F_err, double* dEdC, double* dEdC_err);
+
+/* Space-warp forces (VMCF_SPACE_WARP):
+ * F^sw_a = -<dE_L^sw/dR_a> - 2 <(E_L - E) dlnPsi^sw/dR_a>, with
+ *   dE_L^sw/dR_a = dE_L/dR_a + sum_e omega_a(r_e) dE_L/dr_e,
+ *   dlnPsi^sw/dR_a = dlnPsi/dR_a + sum_e [omega_a(r_e) dlnPsi/dr_e + 1/2 grad_{r_e} omega_a(r_e)]
+ * (the component of the gradient of omega along the force component), jackknife error bars.
+ * vmcf_finish_warp: host only, from block sums with row length `stride` = 3 + 18K + 2 M (n_up +
+ *   n_dn) (the layout above with the warped sums); F, F_err host [K][3] or NULL.
+ * vmcf_reduce_warp: the same from a walker set's own sums (synchronises).
+ * vmcf_evaluate_warp: per-walker values at device positions pos [W][Ne][3] (any output may be
+ *   NULL; device, caller-owned): dE_L/dr_e [W][Ne][3], dE_L^sw/dR [W][K][3], dlnPsi^sw/dR
+ *   [W][K][3]. Works with or without VMCF_SPACE_WARP. */
+int vmcf_finish_warp(const double* blocks, int nblocks, int stride, int K, int M, int n_up, int n_dn, double e_ref,
+                     double* F, double* F_err);
+int vmcf_reduce_warp(vmcf_system_t sys, vmcf_walkers_t wk, double* F, double* F_err, void* stream);
+int vmcf_evaluate_warp(vmcf_system_t sys, const double* pos, int W, double* dEL_dr, double* dEL_sw,
+                       double* dlnpsi_sw, void* stream);
 
 /* Host-only covariance of the estimators, as the low-rank factor that the error propagation
  * through the Z-vector equations needs (App. "Error propagation": Var(F^c) = R^T G Cov(B) G^T R,

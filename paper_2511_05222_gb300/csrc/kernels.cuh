@@ -409,6 +409,11 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   const int nO = M * (nup + S.ndn);
   T* fa = sm_ptr<T>(base, L.fa);  // [6][M]: AO mu's share of the nuclear derivatives, owned by mu's thread
   for (int i = t; i < 6 * M; i += GS) fa[i] = T(0);
+  // space warp: the electron derivatives of E_L are wanted (walker sums or outputs)
+  const bool warp = S.swct || P.dEL_dr || P.dEL_sw || P.dlnpsi_sw;
+  T* er = sm_ptr<T>(base, L.ew);  // [3 Ne]: orbital part of dE_L/dr_e, then all of it
+  if (warp)
+    for (int i = t; i < 3 * Ne; i += GS) er[i] = T(0);
   for (int sg = 0; sg < 2; ++sg) {
     const int n = sg == 0 ? nup : S.ndn;
     if (n == 0) continue;
@@ -440,6 +445,7 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       ao_point<T, GS, 2, true>(S, pe, ao, M);
       gsync<GS>();
       const T j0 = Jg[3 * e], j1 = Jg[3 * e + 1], j2 = Jg[3 * e + 2];
+      T ce[3] = {T(0), T(0), T(0)};  // this thread's share of sum_mu of the AO terms of electron e
       for (int mu = t; mu < M; mu += GS) {
         T yA = 0, yL = 0;
         for (int i = 0; i < n; ++i) {
@@ -457,15 +463,28 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
         fa[0 * M + mu] -= g0 * yL;
         fa[1 * M + mu] -= g1 * yL;
         fa[2 * M + mu] -= g2 * yL;
-        fa[3 * M + mu] += T(-0.5) * (g0 * yA - yL * (l0 + T(2) * hj0));
-        fa[4 * M + mu] += T(-0.5) * (g1 * yA - yL * (l1 + T(2) * hj1));
-        fa[5 * M + mu] += T(-0.5) * (g2 * yA - yL * (l2 + T(2) * hj2));
+        const T c0 = T(-0.5) * (g0 * yA - yL * (l0 + T(2) * hj0));
+        const T c1 = T(-0.5) * (g1 * yA - yL * (l1 + T(2) * hj1));
+        const T c2 = T(-0.5) * (g2 * yA - yL * (l2 + T(2) * hj2));
+        fa[3 * M + mu] += c0;
+        fa[4 * M + mu] += c1;
+        fa[5 * M + mu] += c2;
+        ce[0] += c0;
+        ce[1] += c1;
+        ce[2] += c2;
         const T tdc = lp + T(2) * (j0 * g0 + j1 * g1 + j2 * g2);
         for (int i = 0; i < n; ++i) {
           const T b = Bs[i * n + el];
           Ow[mu * n + i] += v * b;
           if (want_dC) D[mu * n + i] += b * tdc;
         }
+      }
+      if (warp) {  // an AO moves with its nucleus as -d/dr_e: the same terms, summed over every AO
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ce[k] = warp_sum(ce[k]);
+        if ((t & 31) == 0)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) atomicAdd(&er[3 * e + k], ce[k]);
       }
       gsync<GS>();
       // e-n Jastrow and V_en terms, one nucleus per thread
@@ -526,6 +545,120 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
     }
   }
   gsync<GS>();
+
+  // Space-warp force vectors (force expression with omega_a(r) = kappa(|r - R_a|) /
+  // sum_b kappa(|r - R_b|), kappa(r) = r^-4): dE_L/dr_e, then per nucleus a
+  //   dE_L^sw/dR_a = dE_L/dR_a + sum_e omega_a(r_e) dE_L/dr_e,
+  //   d ln Psi^sw/dR_a = d ln Psi/dR_a + sum_e [omega_a(r_e) d ln Psi/dr_e + 1/2 grad omega_a(r_e)].
+  if (warp) {
+    T* ks = er + 3 * Ne;   // [Ne] sum_b kappa_b(r_e)
+    T* gks = er + 4 * Ne;  // [3 Ne] sum_b grad kappa_b(r_e)
+    for (int e = t; e < Ne; e += GS) {
+      const bool up = e < nup;
+      const T ge[3] = {gd[3 * e] + Jg[3 * e], gd[3 * e + 1] + Jg[3 * e + 1], gd[3 * e + 2] + Jg[3 * e + 2]};
+      T dr[3] = {-er[3 * e], -er[3 * e + 1], -er[3 * e + 2]};
+      for (int j = 0; j < Ne; ++j) {  // e-e Jastrow pair terms and V_ee
+        if (j == e) continue;
+        const T sv[3] = {edisp<T>(pos, ph, pl, e, j, 0), edisp<T>(pos, ph, pl, e, j, 1), edisp<T>(pos, ph, pl, e, j, 2)};
+        const T r = dsqrt<T>(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]), ri = T(1) / r;
+        const T ri3 = ri * ri * ri;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dr[k] -= sv[k] * ri3;
+        if (S.J2) {
+          const bool par = (j < nup) == up;
+          const Rad3<T> u = pade<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), r);
+          const T nn[3] = {sv[0] * ri, sv[1] * ri, sv[2] * ri};
+          const T dl = u.h3 + T(2) * u.h2 * ri - T(2) * u.h1 * ri * ri;
+          const T vec[3] = {ge[0] - gd[3 * j] - Jg[3 * j], ge[1] - gd[3 * j + 1] - Jg[3 * j + 1],
+                            ge[2] - gd[3 * j + 2] - Jg[3 * j + 2]};
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            T hs = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              hs += (u.h2 * nn[k] * nn[c] + u.h1 * ri * ((k == c ? T(1) : T(0)) - nn[k] * nn[c])) * vec[c];
+            dr[k] -= dl * nn[k] + hs;
+          }
+        }
+      }
+      const EPos pe = make_epos(pos + 3 * e);
+      T k0 = T(0), gk[3] = {T(0), T(0), T(0)};
+      for (int I = 0; I < K; ++I) {  // e-n Jastrow, V_en and the warp weights
+        T sv[3];
+        disp_nuc<T>(S, pe, I, sv);
+        const T r2 = sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2];
+        const T r = dsqrt<T>(r2), ri = T(1) / r;
+        const T Z = (T)S.Z[I];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dr[k] += Z * sv[k] * ri * ri * ri;
+        if (S.J1) {
+          const Rad3<T> c = pade<T>(-Z, (T)S.ben, r);
+          const T nn[3] = {sv[0] * ri, sv[1] * ri, sv[2] * ri};
+          const T dl = c.h3 + T(2) * c.h2 * ri - T(2) * c.h1 * ri * ri;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            T hs = 0;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc)
+              hs += (c.h2 * nn[k] * nn[cc] + c.h1 * ri * ((k == cc ? T(1) : T(0)) - nn[k] * nn[cc])) * ge[cc];
+            dr[k] -= T(0.5) * dl * nn[k] + hs;
+          }
+        }
+        const T kap = T(1) / (r2 * r2);
+        k0 += kap;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gk[k] += T(-4) * sv[k] * kap / r2;
+      }
+      ks[e] = k0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        gks[3 * e + k] = gk[k];
+        er[3 * e + k] = dr[k];
+        if (P.dEL_dr) P.dEL_dr[((size_t)w * Ne + e) * 3 + k] = (double)dr[k];
+      }
+    }
+    gsync<GS>();
+    const int so = P.swct_off;  // offset of the warped sums in the accumulator (0: none)
+    for (int a = t; a < K; a += GS) {
+      double sE[3], sL[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        sE[k] = (double)frc[3 * K + 3 * a + k] + __ldg(S.dVnn + 3 * a + k);
+        sL[k] = (double)frc[3 * a + k];
+      }
+      for (int e = 0; e < Ne; ++e) {
+        T sv[3];
+        disp_nuc<T>(S, make_epos(pos + 3 * e), a, sv);
+        const T r2 = sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2];
+        const T kap = T(1) / (r2 * r2), kinv = T(1) / ks[e];
+        const T om = kap * kinv;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const T gom = (T(-4) * sv[k] * kap / r2 - om * gks[3 * e + k]) * kinv;
+          sE[k] += (double)(om * er[3 * e + k]);
+          sL[k] += (double)(om * (gd[3 * e + k] + Jg[3 * e + k]) + T(0.5) * gom);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int i = 3 * a + k;
+        if (P.dEL_sw) P.dEL_sw[(size_t)w * 3 * K + i] = sE[k];
+        if (P.dlnpsi_sw) P.dlnpsi_sw[(size_t)w * 3 * K + i] = sL[k];
+        if (so > 0) {
+          if (acc_s) {
+            atomicAdd(&acc_s[so + i], (T)sE[k]);
+            atomicAdd(&acc_s[so + 3 * K + i], (T)sL[k]);
+            atomicAdd(&acc_s[so + 6 * K + i], (T)(cw * sL[k]));
+          } else if (acc_g) {
+            acc_g[so + i] += sE[k];
+            acc_g[so + 3 * K + i] += sL[k];
+            acc_g[so + 6 * K + i] += cw * sL[k];
+          }
+        }
+      }
+    }
+    gsync<GS>();
+  }
 
   // per-walker outputs and scalar / force sums
   for (int i = t; i < 3 * K; i += GS) {

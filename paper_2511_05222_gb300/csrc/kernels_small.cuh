@@ -591,6 +591,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
 #pragma unroll
     for (int i = 0; i < NM; ++i) xr[i] = (has_e && i < n) ? Pm[off + el * n + i] : T(0);
     T fl[3] = {T(0), T(0), T(0)}, fe[3] = {T(0), T(0), T(0)};
+    T fr[3] = {T(0), T(0), T(0)};  // sum over every AO of the dE_L terms of this electron (space warp)
     int cur = -1;
     int chunk0 = 0, chunk_n = 0;  // AOs [chunk0, chunk0 + chunk_n) pending in phi
     const T* Csg = Cs + sg * M * NM;
@@ -693,7 +694,9 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
             const T gl = g[k] * rs.LF + Pa * d[k] * rs.T3;
             const T hj = hjv[k] * rs.R0 + g[k] * xjR1 + d[k] * (gjR1 + PxjR2) + jg[k] * PR1;
             fl[k] -= gv * yL;
-            fe[k] += T(-0.5) * (gv * yA - yL * (gl + T(2) * hj));
+            const T cde = T(-0.5) * (gv * yA - yL * (gl + T(2) * hj));
+            fe[k] += cde;
+            fr[k] += cde;
           }
           if (tc)
             reinterpret_cast<__nv_bfloat16*>(P.phiT[sg])[((size_t)w * P.Mp + sh.w + m) * 16 + el] =
@@ -715,7 +718,9 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
           y[(n + i) * 16 + el] = __float2bfloat16_rn((float)((T)cw * bc[i]));
         }
     }
-    // e-n Jastrow and V_en derivatives, one nucleus at a time
+    // e-n Jastrow and V_en derivatives, one nucleus at a time; an electron moving is the
+    // negative of the nucleus moving, so dE_L/dr_e collects minus every term
+    T dr[3] = {-fr[0], -fr[1], -fr[2]};
     for (int I = 0; I < K; ++I) {
       T c6[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
       if (has_e) {
@@ -745,6 +750,8 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
             c6[3 + k] += hs + T(0.5) * dl * nn[k];
           }
         }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dr[k] -= c6[3 + k];
       }
       if constexpr (sizeof(T) == 4) {
         float v6[6];
@@ -771,6 +778,87 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       }
     }
     __syncwarp();
+    // ---- space warp (force expression with omega_a(r) = kappa(|r - R_a|) / sum_b kappa(|r - R_b|),
+    // kappa(r) = r^-4): e-e pair terms of dE_L/dr_e, then per nucleus
+    //   dE_L^sw/dR_a = dE_L/dR_a + sum_e omega_a(r_e) dE_L/dr_e,
+    //   d ln Psi^sw/dR_a = d ln Psi/dR_a + sum_e [omega_a(r_e) d ln Psi/dr_e + 1/2 grad omega_a(r_e)].
+    if (accum && P.swct_off > 0) {
+      const T ge[3] = {gd[0] + jg[0], gd[1] + jg[1], gd[2] + jg[2]};
+      for (int j = 0; j < Ne; ++j) {  // every lane takes part in the shuffles
+        T gj[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gj[k] = __shfl_sync(0xffffffffu, ge[k], j);
+        if (!has_e || j == e) continue;
+        T sv[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if constexpr (sizeof(T) == 8) sv[k] = p[k] - pd[3 * j + k];
+          else sv[k] = (hh[k] - ph[3 * j + k]) + (ll[k] - pl[3 * j + k]);
+        }
+        const T r = dsqrt<T>(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]), ri = T(1) / r;
+        const T ri3 = ri * ri * ri;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dr[k] -= sv[k] * ri3;
+        if (S.J2) {
+          const bool par = (j < nup) == (e < nup);
+          const Rad3<T> u = pade<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), r);
+          const T nn[3] = {sv[0] * ri, sv[1] * ri, sv[2] * ri};
+          const T dl = u.h3 + T(2) * u.h2 * ri - T(2) * u.h1 * ri * ri;
+          const T vec[3] = {ge[0] - gj[0], ge[1] - gj[1], ge[2] - gj[2]};
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            T hs = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              hs += (u.h2 * nn[k] * nn[c] + u.h1 * ri * ((k == c ? T(1) : T(0)) - nn[k] * nn[c])) * vec[c];
+            dr[k] -= dl * nn[k] + hs;
+          }
+        }
+      }
+      T k0 = T(0), gk[3] = {T(0), T(0), T(0)};
+      if (has_e)
+        for (int I = 0; I < K; ++I) {
+          T sv[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            if constexpr (sizeof(T) == 8) sv[k] = p[k] - __ldg(S.R + 3 * I + k);
+            else sv[k] = (hh[k] - __ldg(S.Rh + 3 * I + k)) + (ll[k] - __ldg(S.Rl + 3 * I + k));
+          }
+          const T r2 = sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2], kap = T(1) / (r2 * r2);
+          k0 += kap;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) gk[k] += T(-4) * sv[k] * kap / r2;
+        }
+      const int so = P.swct_off;
+      for (int a = 0; a < K; ++a) {
+        T v6[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        if (has_e) {
+          T sv[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            if constexpr (sizeof(T) == 8) sv[k] = p[k] - __ldg(S.R + 3 * a + k);
+            else sv[k] = (hh[k] - __ldg(S.Rh + 3 * a + k)) + (ll[k] - __ldg(S.Rl + 3 * a + k));
+          }
+          const T r2 = sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2];
+          const T kap = T(1) / (r2 * r2), kinv = T(1) / k0, om = kap * kinv;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            v6[k] = om * dr[k];
+            v6[3 + k] = om * ge[k] + T(0.5) * (T(-4) * sv[k] * kap / r2 - om * gk[k]) * kinv;
+          }
+        }
+        warp_sum_f<6>(v6);
+        if (lane == 0)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const double sE = (double)v6[k] + (double)frc[3 * K + 3 * a + k] + __ldg(S.dVnn + 3 * a + k);
+            const double sL = (double)v6[3 + k] + (double)frc[3 * a + k];
+            atomicAdd(&acc_s[so + 3 * a + k], (T)sE);
+            atomicAdd(&acc_s[so + 3 * K + 3 * a + k], (T)sL);
+            atomicAdd(&acc_s[so + 6 * K + 3 * a + k], (T)(cw * sL));
+          }
+      }
+    }
     // ---- outputs and walker sums
     for (int i = lane; i < 3 * K; i += 32) {
       const double dl = (double)frc[i];

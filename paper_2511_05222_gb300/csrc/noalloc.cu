@@ -66,6 +66,7 @@ extern "C" int vmcf_evaluate_sums_noalloc(vmcf_system_t s, const double* pos, in
   vmcf::MeasParams M{};
   M.pos = pos;
   M.acc = scratch;
+  M.swct_off = vmcf::swct_offset(*s);
   M.accL = accL;
   M.acc_in_smem = s->acc_smem ? 1 : 0;
   M.e_ref = e_ref;

@@ -124,6 +124,7 @@ GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool with
   L.mo = take((int)tsz * 4 * L.p2_chunk * s.nmax);
   L.frc = take((int)tsz * 6 * s.K);
   L.fa = take((int)tsz * 6 * s.M);
+  L.ew = take((int)tsz * 7 * s.Ne);  // space warp: dE_L/dr_e [3 Ne], kappa sums [Ne], their gradients [3 Ne]
   L.Ow = take((int)tsz * s.M * s.nmax);
   L.D = withD ? take((int)tsz * s.M * s.nmax) : L.Ow;
   L.piv = take(4 * s.nmax);
@@ -142,7 +143,7 @@ int plan_measure(vmcf_system_s& s) {
   const int maxg = s.GSm == 32 ? 4 : 1;
   if (s.Lmeas.bytes > kSmemCap) return fail(VMCF_ENOTSUP, "system too large for the shared-memory plan (measure)");
   s.gpb_measD = s.LmeasD.bytes > kSmemCap ? 0 : std::max(1, std::min(maxg, kSmemCap / s.LmeasD.bytes));
-  s.accL = 3 + 9 * s.K + 2 * s.M * (s.nup + s.ndn);
+  s.accL = 3 + 9 * s.K + 2 * s.M * (s.nup + s.ndn) + (s.swct ? 9 * s.K : 0);
   const int accBytes = align16((int)tsz * s.accL);
   int g = maxg;
   while (g > 1 && g * s.Lmeas.bytes + accBytes > kSmemCap) --g;
@@ -370,6 +371,7 @@ int measure_state_small(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
   M.mode = 2;
   M.Bout = wk->B;
   M.acc = wk->acc;
+  M.swct_off = swct_offset(*s);
   M.e_ref = wk->e_ref;
   M.counters = wk->counters;
   const bool tc = wk->tc && s->tc_sums;
@@ -421,7 +423,8 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   *out = nullptr;
   if (!nuc || !bas || !jas || !C_up) return fail(VMCF_EINVAL, "NULL input");
   const bool force_group = (precision & VMCF_FORCE_GROUP_PATH) != 0;
-  precision &= ~VMCF_FORCE_GROUP_PATH;
+  const bool swct = (precision & VMCF_SPACE_WARP) != 0;
+  precision &= ~(VMCF_FORCE_GROUP_PATH | VMCF_SPACE_WARP);
   if (precision != VMCF_FP64 && precision != VMCF_MIXED) return fail(VMCF_EINVAL, "bad precision");
   if (nuc->K < 1 || !nuc->Z || !nuc->R) return fail(VMCF_EINVAL, "need at least one nucleus");
   if (!finite_all(nuc->R, 3 * (size_t)nuc->K)) return fail(VMCF_EINVAL, "nuclear positions not finite");
@@ -435,6 +438,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
 
   auto* s = new vmcf_system_s();
   s->precision = precision;
+  s->swct = swct;
   s->K = nuc->K;
   s->nshell = bas->nshell;
   s->nup = n_up;
@@ -629,6 +633,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   D.Fa = jas->F_anti; D.Fp = jas->F_par; D.aa = jas->a_anti; D.ap = jas->a_par; D.ben = jas->b_en;
   D.J1 = jas->enable_J1 ? 1 : 0;
   D.J2 = jas->enable_J2 ? 1 : 0;
+  D.swct = s->swct ? 1 : 0;
   D.Vnn = Vnn;
   D.dVnn = reinterpret_cast<const double*>(b + oDv);
   s->scratch_counters = reinterpret_cast<double*>(b + oCnt);
@@ -808,6 +813,7 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
     M.mode = 2;
     M.Bout = wk->B;
     M.acc = wk->acc;
+    M.swct_off = swct_offset(*s);
     M.e_ref = wk->e_ref;
     M.counters = wk->counters;
     for (int sw = 0; sw < n_sweeps; ++sw) {
@@ -878,6 +884,7 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
   M.pos = wk->pos;
   M.Bout = wk->B;
   M.acc = wk->acc;
+  M.swct_off = swct_offset(*s);
   M.accL = s->accL;
   M.acc_in_smem = s->acc_smem ? 1 : 0;
   M.e_ref = wk->e_ref;
@@ -907,6 +914,7 @@ int vmcf_measure(vmcf_system_t s, vmcf_walkers_t wk, void* stream) {
     M.pos = wk->pos;
     M.Bout = wk->B;
     M.acc = wk->acc;
+    M.swct_off = swct_offset(*s);
     M.accL = s->accL;
     M.acc_in_smem = s->acc_smem ? 1 : 0;
     M.e_ref = wk->e_ref;
@@ -989,7 +997,7 @@ namespace {
 int jackknife_estimates(const double* blk, int nb, int K, int M, int n_up, int n_dn, double er, double* Ev,
                         std::vector<double>& Fv, std::vector<double>& Bv, std::vector<double>& Ej,
                         std::vector<double>& Fj, std::vector<double>& Bj) {
-  if (!blk || nb < 2 || K < 1 || M < 1 || n_up < 0 || n_dn < 0) return fail(VMCF_EINVAL, "bad arguments");
+  if (!blk || nb < 2 || K < 1 || M < 0 || n_up < 0 || n_dn < 0) return fail(VMCF_EINVAL, "bad arguments");
   const int K3 = 3 * K, nO = M * (n_up + n_dn), L = 3 + 9 * K + 2 * nO;
   std::vector<double> tot(L, 0.0);
   for (int b = 0; b < nb; ++b)
@@ -1029,6 +1037,7 @@ double jk_mean(const std::vector<double>& th, int nb, int stride, int idx) {
 
 int vmcf_finish_estimators(const double* blk, int nb, int K, int M, int n_up, int n_dn, double er, double* E,
                            double* E_err, double* F, double* F_err, double* dEdC, double* dEdC_err) {
+  if (M < 1) return fail(VMCF_EINVAL, "bad arguments");
   double Ev = 0.0;
   std::vector<double> Fv, Bv, Ej, Fj, Bj;
   int rc = jackknife_estimates(blk, nb, K, M, n_up, n_dn, er, &Ev, Fv, Bv, Ej, Fj, Bj);
@@ -1058,6 +1067,7 @@ int vmcf_finish_estimators(const double* blk, int nb, int K, int M, int n_up, in
 
 int vmcf_finish_covariance(const double* blk, int nb, int K, int M, int n_up, int n_dn, double er,
                            double* F_factor, double* B_factor) {
+  if (M < 1) return fail(VMCF_EINVAL, "bad arguments");
   double Ev = 0.0;
   std::vector<double> Fv, Bv, Ej, Fj, Bj;
   int rc = jackknife_estimates(blk, nb, K, M, n_up, n_dn, er, &Ev, Fv, Bv, Ej, Fj, Bj);
@@ -1077,6 +1087,65 @@ int vmcf_finish_covariance(const double* blk, int nb, int K, int M, int n_up, in
   return VMCF_OK;
 }
 
+int vmcf_finish_warp(const double* blk, int nb, int stride, int K, int M, int n_up, int n_dn, double er, double* F,
+                     double* F_err) {
+  if (!blk || nb < 2 || K < 1 || M < 1 || n_up < 0 || n_dn < 0) return fail(VMCF_EINVAL, "bad arguments");
+  const int nO = M * (n_up + n_dn), Lb = 3 + 9 * K + 2 * nO;
+  if (stride != Lb + 9 * K) return fail(VMCF_EINVAL, "stride must be 3 + 18 K + 2 M (n_up + n_dn)");
+  // the base layout with the warped sums in place of the force fields, and no O sums
+  const int Lw = 3 + 9 * K;
+  std::vector<double> v((size_t)nb * Lw);
+  for (int b = 0; b < nb; ++b) {
+    const double* src = blk + (size_t)b * stride;
+    double* dst = v.data() + (size_t)b * Lw;
+    std::copy(src, src + 3, dst);
+    std::copy(src + Lb, src + Lb + 9 * K, dst + 3);
+  }
+  double Ev = 0.0;
+  std::vector<double> Fv, Bv, Ej, Fj, Bj;
+  int rc = jackknife_estimates(v.data(), nb, K, 0, 0, 0, er, &Ev, Fv, Bv, Ej, Fj, Bj);
+  if (rc != VMCF_OK) return rc;
+  for (int i = 0; i < 3 * K; ++i) {
+    if (F) F[i] = Fv[i];
+    if (F_err) {
+      const double m = jk_mean(Fj, nb, 3 * K, i);
+      double s2 = 0.0;
+      for (int b = 0; b < nb; ++b) s2 += (Fj[(size_t)b * 3 * K + i] - m) * (Fj[(size_t)b * 3 * K + i] - m);
+      F_err[i] = std::sqrt((nb - 1.0) / nb * s2);
+    }
+  }
+  return VMCF_OK;
+}
+
+int vmcf_reduce_warp(vmcf_system_t s, vmcf_walkers_t wk, double* F, double* F_err, void* stream) {
+  if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
+  if (!s->swct) return fail(VMCF_EINVAL, "the system was not created with VMCF_SPACE_WARP");
+  std::vector<double> blk((size_t)wk->nblocks * s->accL);
+  int rc = vmcf_block_sums(s, wk, blk.data(), stream);
+  if (rc != VMCF_OK) return rc;
+  return vmcf_finish_warp(blk.data(), wk->nblocks, s->accL, s->K, s->M, s->nup, s->ndn, wk->e_ref, F, F_err);
+}
+
+int vmcf_evaluate_warp(vmcf_system_t s, const double* pos, int W, double* dEL_dr, double* dEL_sw, double* dlnpsi_sw,
+                       void* stream) {
+  if (!s || !pos || W < 0) return fail(VMCF_EINVAL, "bad arguments");
+  if (W == 0) return VMCF_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MeasParams M{};
+  M.pos = pos;
+  M.dEL_dr = dEL_dr;
+  M.dEL_sw = dEL_sw;
+  M.dlnpsi_sw = dlnpsi_sw;
+  M.counters = reinterpret_cast<unsigned long long*>(s->scratch_counters);
+  M.W = W;
+  const int grid = (W + 2 * s->gpb_meas - 1) / (2 * s->gpb_meas);
+  const Launch lc = launch_meas(*s, grid, false, false);
+  cudaError_t e = s->precision == VMCF_FP64 ? launch_measure<double>(s->dev, lc, M, st)
+                                            : launch_measure<float>(s->dev, lc, M, st);
+  if (e != cudaSuccess) return cuda_fail(e, "measure kernel launch (space warp)");
+  return VMCF_OK;
+}
+
 int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double* E_err, double* F, double* F_err,
                            double* dEdC, double* dEdC_err, double* rhs_BQ, void* stream) {
   if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
@@ -1085,6 +1154,12 @@ int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double
   std::vector<double> blk((size_t)nb * L);
   int rc = vmcf_block_sums(s, wk, blk.data(), stream);
   if (rc != VMCF_OK) return rc;
+  const int Lb = 3 + 9 * s->K + 2 * nO;  // base fields; the space-warp sums (if any) follow
+  if (L != Lb) {
+    std::vector<double> base((size_t)nb * Lb);
+    for (int b = 0; b < nb; ++b) std::copy(&blk[(size_t)b * L], &blk[(size_t)b * L] + Lb, &base[(size_t)b * Lb]);
+    blk.swap(base);
+  }
   std::vector<double> Bv(nO);
   rc = vmcf_finish_estimators(blk.data(), nb, s->K, s->M, s->nup, s->ndn, wk->e_ref, E, E_err, F, F_err,
                               Bv.data(), dEdC_err);

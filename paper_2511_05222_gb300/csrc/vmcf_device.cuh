@@ -33,6 +33,7 @@ struct DevSys {
   const float* CfT[2];
   double Fa, Fp, aa, ap, ben;
   int J1, J2;
+  int swct;              // accumulate the space-warp force sums
   double Vnn;
   const double* dVnn;    // [K][3], derivative of V_nn
 };

@@ -15,6 +15,7 @@ struct vmcf_system_s {
   std::vector<double> R, Z, S, C[2];
   std::vector<int> ao_center;
   bool has_S = false;
+  bool swct = false;  // accumulate the space-warp force sums (VMCF_SPACE_WARP)
   vmcf::DevSys dev{};
   void* dmem = nullptr;
   // launch planning
@@ -73,6 +74,8 @@ struct vmcf_walkers_s {
 namespace vmcf {
 // Launch planning shared by the entry points (defined in vmcf_api.cu).
 Launch launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD);
+// Offset of the space-warp sums in an accumulator slot (after the base fields), 0 if off.
+inline int swct_offset(const vmcf_system_s& s) { return s.swct ? 3 + 9 * s.K + 2 * s.M * (s.nup + s.ndn) : 0; }
 // Walker-group shared-memory plans of the sweep and measurement kernels for group size GS.
 GroupLayout group_layout_rm(const vmcf_system_s& s, int GS);
 GroupLayout group_layout_meas(const vmcf_system_s& s, int GS);

@@ -10,7 +10,7 @@ namespace vmcf {
 
 // Byte offsets of one walker group's shared-memory region; computed on the host.
 struct GroupLayout {
-  int pos, ph, pl, Bd, Bt, P, Q, Jg, Jl, gd, ao, mo, frc, fa, Ow, D, piv, f, red, scal, row, wv, col;
+  int pos, ph, pl, Bd, Bt, P, Q, Jg, Jl, gd, ao, mo, frc, fa, ew, Ow, D, piv, f, red, scal, row, wv, col;
   int ao_rows;   // AO rows of M values the ao buffer holds (electrons per Slater-build chunk)
   int p2_chunk;  // electrons per chunk of the gradient/Laplacian pass (4 AO rows each)
   int bytes;    // size of one group's region (16-byte multiple)
@@ -41,8 +41,10 @@ struct MeasParams {
   const double* pos;  // [W][Ne][3]
   void* Bout;         // T [W][nB] or NULL
   double *EL, *logpsi, *dlnpsi, *dEL, *O, *dELdC;  // outputs or NULL
+  double *dEL_dr, *dEL_sw, *dlnpsi_sw;               // space-warp outputs ([W][Ne][3], [W][K][3]) or NULL
   double* acc;        // [grid][accL] FP64 slots, or NULL
   int accL, acc_in_smem;
+  int swct_off;       // offset (> 0) of the space-warp sums in a slot, 0 if none
   double e_ref;
   unsigned long long* counters;
   int W;
@@ -96,6 +98,7 @@ struct SmallMeasParams {
   double e_ref;
   unsigned long long* counters;
   int W;
+  int swct_off;  // offset (> 0) of the space-warp sums in a slot (accumulate mode), 0 if none
 };
 
 template <typename T>

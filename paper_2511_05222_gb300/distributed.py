@@ -60,6 +60,18 @@ def finish_covariance(blocks: np.ndarray, K: int, M: int, n_up: int, n_dn: int, 
     return Ff, Bf
 
 
+def finish_warp(blocks: np.ndarray, K: int, M: int, n_up: int, n_dn: int, e_ref: float) -> dict:
+    """vmcf_finish_warp on host block sums that carry the space-warp fields (no GPU involved)."""
+    L = vmcf.lib()
+    blocks = np.ascontiguousarray(blocks, dtype=np.float64)
+    F, Fe = np.zeros(3 * K), np.zeros(3 * K)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    rc = L.vmcf_finish_warp(dp(blocks), blocks.shape[0], blocks.shape[1], K, M, n_up, n_dn, float(e_ref), dp(F), dp(Fe))
+    if rc != 0:
+        raise vmcf.VmcfError(rc, "vmcf_finish_warp")
+    return {"F": F.reshape(K, 3), "F_err": Fe.reshape(K, 3)}
+
+
 def sharded_estimators(walkers: "vmcf.Walkers", group=None) -> dict:
     """Estimators over the walkers of all ranks: gather block sums, finish on the host."""
     s = walkers.system

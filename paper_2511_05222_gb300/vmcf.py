@@ -15,6 +15,7 @@ from . import build as _build
 
 FP64, MIXED = 0, 1
 FORCE_GROUP_PATH = 0x100
+SPACE_WARP = 0x200
 _STATUS = {0: "VMCF_OK", -1: "VMCF_EINVAL", -2: "VMCF_ENOMEM", -3: "VMCF_ECUDA", -4: "VMCF_ESINGULAR",
            -5: "VMCF_ETIMEOUT", -6: "VMCF_ENOTSUP"}
 
@@ -91,6 +92,10 @@ def lib(build_if_missing: bool = True):
         L.vmcf_set_tuning.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int]
         L.vmcf_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
         L.vmcf_probe_pipes.argtypes = [_dp, _dp, _dp, _vp]
+        L.vmcf_evaluate_warp.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.vmcf_reduce_warp.argtypes = [_vp, _vp, _dp, _dp, _vp]
+        L.vmcf_finish_warp.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_double, _dp, _dp]
         L.vmcf_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int, _vp,
                                         ctypes.POINTER(_vp)]
         L.vmcf_batch_destroy.argtypes = [_vp]
@@ -129,7 +134,7 @@ def _np(a, dt):
 class System:
     """vmcf_init_system: a molecule, its basis, frozen orbitals and Jastrow, on the GPU."""
 
-    def __init__(self, sys, precision: int = FP64, force_group: bool = False):
+    def __init__(self, sys, precision: int = FP64, force_group: bool = False, space_warp: bool = False):
         L = lib()
         j = sys.jastrow
         self._hold = dict(Z=_np(sys.Z, np.int32), R=_np(sys.R, np.float64), c=_np(sys.shell_center, np.int32),
@@ -145,7 +150,8 @@ class System:
         jas = _Jastrow(j.F_anti, j.F_par, j.a_anti, j.a_par, j.b_en, int(j.enable_J1), int(j.enable_J2))
         out = _vp()
         _check(L.vmcf_init_system(ctypes.byref(nuc), ctypes.byref(bas), dp(h["Cu"]), dp(h["Cd"]), sys.n_up, sys.n_dn,
-                                  ctypes.byref(jas), dp(h["S"]), precision | (FORCE_GROUP_PATH if force_group else 0),
+                                  ctypes.byref(jas), dp(h["S"]),
+                                  precision | (FORCE_GROUP_PATH if force_group else 0) | (SPACE_WARP if space_warp else 0),
                                   ctypes.byref(out)), "vmcf_init_system")
         self.h = out
         self.precision = precision
@@ -185,6 +191,19 @@ def vmcf_evaluate(system: System, pos, want=("EL",), stream=None):
     order = ["EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O", "dEL_dC"]
     _check(lib().vmcf_evaluate(system.h, _ptr(pos.contiguous()), W, *[_ptr(out.get(k)) for k in order],
                                _stream(stream)), "vmcf_evaluate")
+    return out
+
+
+def vmcf_evaluate_warp(system: System, pos, stream=None):
+    """vmcf_evaluate_warp on device positions (W, Ne, 3): dict of torch CUDA tensors dEL_dr
+    (W, Ne, 3), dEL_sw and dlnpsi_sw (W, K, 3)."""
+    import torch
+    W = pos.shape[0]
+    out = {"dEL_dr": torch.empty((W, system.Ne, 3), dtype=torch.float64, device=pos.device),
+           "dEL_sw": torch.empty((W, system.K, 3), dtype=torch.float64, device=pos.device),
+           "dlnpsi_sw": torch.empty((W, system.K, 3), dtype=torch.float64, device=pos.device)}
+    _check(lib().vmcf_evaluate_warp(system.h, _ptr(pos.contiguous()), W, _ptr(out["dEL_dr"]), _ptr(out["dEL_sw"]),
+                                    _ptr(out["dlnpsi_sw"]), _stream(stream)), "vmcf_evaluate_warp")
     return out
 
 
@@ -266,6 +285,14 @@ class Walkers:
         if with_rhs:
             out["rhs_BQ"] = rhs
         return out
+
+    def reduce_warp(self, stream=None) -> dict:
+        """Space-warp forces F^sw and their jackknife errors (system created with space_warp)."""
+        s = self.system
+        F, Fe = np.zeros(3 * s.K), np.zeros(3 * s.K)
+        _check(lib().vmcf_reduce_warp(s.h, self.h, F.ctypes.data_as(_dp), Fe.ctypes.data_as(_dp), _stream(stream)),
+               "vmcf_reduce_warp")
+        return {"F": F.reshape(s.K, 3), "F_err": Fe.reshape(s.K, 3)}
 
     def block_sums(self, stream=None) -> np.ndarray:
         s = self.system

@@ -126,3 +126,27 @@ def test_host_covariance_factor_matches_the_numpy_covariance():
     est = D.finish_estimators(blocks, sysx.K, sysx.M, sysx.n_up, sysx.n_dn, E_REF)
     np.testing.assert_allclose(np.sqrt(np.diag(Bf @ Bf.T)), est["dEdC_err"], rtol=1e-9, atol=1e-300)
     assert np.linalg.matrix_rank(Bf) <= nb - 1  # the deviations from their mean sum to zero
+
+
+def test_host_warp_finish_matches_the_numpy_finish():
+    """vmcf_finish_warp (C++) against the oracle's estimators fed the space-warp vectors."""
+    from oracle import estimators
+    sysx = S.make_system(0)
+    o = oracle.Oracle(sysx, nthreads=1)
+    W, nb = 64, 8
+    pos = S.initial_walkers(sysx, W, seed=6)
+    base = block_sums(o, sysx, pos, 0, nb)
+    out = o.eval(pos, want=("EL",))
+    wv = o.eval_warp(pos)
+    c = out["EL"] - E_REF
+    de, dl = wv["dEL_sw"].reshape(W, -1), wv["dlnpsi_sw"].reshape(W, -1)
+    extra = [np.concatenate([de[sl].sum(0), dl[sl].sum(0), (c[sl, None] * dl[sl]).sum(0)])
+             for sl in (slice(W * b // nb, W * (b + 1) // nb) for b in range(nb))]
+    blocks = np.concatenate([base, np.array(extra)], 1)
+    got = D.finish_warp(blocks, sysx.K, sysx.M, sysx.n_up, sysx.n_dn, E_REF)
+    sums = estimators.new_sums(nb, sysx.K, o.nO)
+    estimators.accumulate(sums, np.arange(W) * nb // W, out["EL"], wv["dlnpsi_sw"], wv["dEL_sw"],
+                          np.zeros((W, o.nO)), E_REF)
+    ref = estimators.finish(sums, E_REF)
+    np.testing.assert_allclose(got["F"].ravel(), ref["F"], rtol=1e-9, atol=1e-9 * np.abs(ref["F"]).max())
+    np.testing.assert_allclose(got["F_err"].ravel(), ref["F_err"], rtol=1e-8)
