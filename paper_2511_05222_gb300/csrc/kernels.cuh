@@ -411,7 +411,7 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   for (int i = t; i < 6 * M; i += GS) fa[i] = T(0);
   // space warp: the electron derivatives of E_L are wanted (walker sums or outputs)
   const bool warp = S.swct || P.dEL_dr || P.dEL_sw || P.dlnpsi_sw;
-  T* er = sm_ptr<T>(base, L.ew);  // [3 Ne]: orbital part of dE_L/dr_e, then all of it
+  T* er = sm_ptr<T>(base, L.ew);  // [3 Ne]: orbital part of dE_L/dr_e, then all of it (may share f)
   if (warp)
     for (int i = t; i < 3 * Ne; i += GS) er[i] = T(0);
   for (int sg = 0; sg < 2; ++sg) {
@@ -551,8 +551,8 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   //   dE_L^sw/dR_a = dE_L/dR_a + sum_e omega_a(r_e) dE_L/dr_e,
   //   d ln Psi^sw/dR_a = d ln Psi/dR_a + sum_e [omega_a(r_e) d ln Psi/dr_e + 1/2 grad omega_a(r_e)].
   if (warp) {
-    T* ks = er + 3 * Ne;   // [Ne] sum_b kappa_b(r_e)
-    T* gks = er + 4 * Ne;  // [3 Ne] sum_b grad kappa_b(r_e)
+    T* ks = ao;            // [Ne] sum_b kappa_b(r_e) (the AO buffer is free after pass 3)
+    T* gks = ao + Ne;      // [3 Ne] sum_b grad kappa_b(r_e)
     for (int e = t; e < Ne; e += GS) {
       const bool up = e < nup;
       const T ge[3] = {gd[3 * e] + Jg[3 * e], gd[3 * e + 1] + Jg[3 * e + 1], gd[3 * e + 2] + Jg[3 * e + 2]};

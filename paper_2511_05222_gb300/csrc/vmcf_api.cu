@@ -124,11 +124,13 @@ GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool with
   L.mo = take((int)tsz * 4 * L.p2_chunk * s.nmax);
   L.frc = take((int)tsz * 6 * s.K);
   L.fa = take((int)tsz * 6 * s.M);
-  L.ew = take((int)tsz * 7 * s.Ne);  // space warp: dE_L/dr_e [3 Ne], kappa sums [Ne], their gradients [3 Ne]
+  // space warp: dE_L/dr_e [3 Ne] (the kappa sums go to the AO buffer, free by then); in mixed mode
+  // it shares the Gauss-Jordan scratch f, which is only used before (3 Ne floats <= 3 nmax + 1 doubles)
   L.Ow = take((int)tsz * s.M * s.nmax);
   L.D = withD ? take((int)tsz * s.M * s.nmax) : L.Ow;
   L.piv = take(4 * s.nmax);
   L.f = take(8 * (3 * s.nmax + 1));
+  L.ew = tsz == 4 ? L.f : take((int)tsz * 3 * s.Ne);
   L.red = take(8 * (32 + 4 * L.p2_chunk));  // group-sum scratch (<= 32 doubles), then per-electron sums
   L.scal = take(32);
   L.bytes = align16(o);
