@@ -140,6 +140,16 @@ int vmcf_walkers_get_positions(vmcf_walkers_t wk, double* pos, int is_host, void
  * before it multiplies d ln Psi / dR or O (cancellation control; results do not depend
  * on it except by rounding). */
 int vmcf_reset_accumulators(vmcf_walkers_t wk, double e_ref, void* stream);
+/* Reweighted (guided) sampling (App., reweighting; the Attaccalite-Sorella scheme the paper uses to
+ * keep the force and dE/dC estimators finite-variance near the nodal surface). With eps > 0 the
+ * walker set samples |Psi_G|^2, Psi_G = Psi g, g = max(1, eps sqrt(S)), where S is the sum over
+ * both spin blocks of the squared entries of the inverse Slater matrices (1/sqrt(S) vanishes
+ * linearly on the nodal surface), and every measured sample enters the walker sums with weight
+ * |Psi/Psi_G|^2 = 1/g^2 (the sample count becomes the sum of the weights), so that every estimator
+ * is sum(W O) / sum(W). eps = 0 (the default) is plain |Psi|^2 sampling, bit for bit. The moves
+ * track S through each Sherman-Morrison update and recompute it at every refresh. Takes effect at
+ * the next vmcf_sample / vmcf_measure. */
+int vmcf_set_guiding(vmcf_walkers_t wk, double eps);
 
 /* Metropolis sweeps (App. A, MCMC). Each sweep moves every electron once, in order, with
  * a Gaussian proposal of width step_sigma; the Philox counter is (walker id, sweep index,

@@ -66,7 +66,9 @@ def lib():
         L.osys_refresh.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_int]
         L.osys_sample.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_uint64, ctypes.c_uint64,
                                   ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                  _ip, _u32p, _u32p, _dp, ctypes.c_int]
+                                  _ip, _u32p, _u32p, _dp, ctypes.c_int, ctypes.c_double]
+        L.osys_guide_weight.restype = ctypes.c_int
+        L.osys_guide_weight.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_double, _dp, ctypes.c_int]
     return _lib
 
 
@@ -161,21 +163,28 @@ class Oracle:
                                                  _p(out["dEL_sw"]), _p(out["dlnpsi_sw"]))
         return out
 
+    def guide_weight(self, pos: np.ndarray, eps: float) -> np.ndarray:
+        """Reweighting factors |Psi / Psi_G|^2 (W,) of the guided sampling at positions (W, Ne, 3)."""
+        pos = _f64(pos)
+        wt = np.zeros(pos.shape[0])
+        lib().osys_guide_weight(self.h, pos.shape[0], _p(pos), float(eps), _p(wt), self.nthreads)
+        return wt
+
     def refresh(self, pos: np.ndarray) -> np.ndarray:
         pos = _f64(pos)
         B = np.zeros((pos.shape[0], self.nB))
         lib().osys_refresh(self.h, pos.shape[0], _p(pos), _p(B), self.nthreads)
         return B
 
-    def sample(self, state: dict, n_sweeps: int, sigma: float = 0.3, refresh_k: int = 26):
+    def sample(self, state: dict, n_sweeps: int, sigma: float = 0.3, refresh_k: int = 26, eps: float = 0.0):
         """Advance a sampler state in place. state: pos (W,Ne,3), B (W,nB), wid0, key (k0,k1),
-        sweep, counter, nacc (W,), nsing (W,), margin (W,)."""
+        sweep, counter, nacc (W,), nsing (W,), margin (W,). eps > 0 samples |Psi_G|^2 (guided)."""
         W = state["pos"].shape[0]
         cnt = np.array([state["counter"]], np.int32)
         lib().osys_sample(self.h, W, _p(state["pos"]), _p(state["B"]), state["wid0"], state["key"][0],
                           state["key"][1], state["sweep"], n_sweeps, sigma, refresh_k, _p(cnt, _ip),
                           _p(state["nacc"], _u32p), _p(state["nsing"], _u32p), _p(state["margin"]),
-                          self.nthreads)
+                          self.nthreads, float(eps))
         state["counter"] = int(cnt[0])
         state["sweep"] += n_sweeps
 

@@ -25,22 +25,27 @@ def new_sums(nblocks: int, K: int, nO: int) -> dict:
             "sEd": np.zeros((nblocks, K * 3)), "sO": np.zeros((nblocks, nO)), "sEO": np.zeros((nblocks, nO))}
 
 
-def accumulate(sums: dict, block_of_walker: np.ndarray, EL, dlnpsi_dR, dEL_dR, O, e_ref: float) -> None:
-    """Add one measured sweep (one sample per walker) to the block sums."""
+def accumulate(sums: dict, block_of_walker: np.ndarray, EL, dlnpsi_dR, dEL_dR, O, e_ref: float,
+               weight=None) -> None:
+    """Add one measured sweep (one sample per walker) to the block sums. weight: per-walker
+    reweighting factors |Psi/Psi_G|^2 of a guided chain (App., reweighting: every average becomes
+    sum(W O) / sum(W), so each sum, the sample count included, takes the factor W); None: 1."""
     W = EL.shape[0]
     dl = dlnpsi_dR.reshape(W, -1)
     de = dEL_dR.reshape(W, -1)
     c = EL - e_ref
+    wt = np.ones(W) if weight is None else np.asarray(weight, dtype=np.float64)
     for w in range(W):
         b = block_of_walker[w]
-        sums["n"][b] += 1
-        sums["sE"][b] += EL[w]
-        sums["sE2"][b] += EL[w] * EL[w]
-        sums["sdEL"][b] += de[w]
-        sums["sd"][b] += dl[w]
-        sums["sEd"][b] += c[w] * dl[w]
-        sums["sO"][b] += O[w]
-        sums["sEO"][b] += c[w] * O[w]
+        q = wt[w]
+        sums["n"][b] += q
+        sums["sE"][b] += q * EL[w]
+        sums["sE2"][b] += q * EL[w] * EL[w]
+        sums["sdEL"][b] += q * de[w]
+        sums["sd"][b] += q * dl[w]
+        sums["sEd"][b] += q * c[w] * dl[w]
+        sums["sO"][b] += q * O[w]
+        sums["sEO"][b] += q * c[w] * O[w]
 
 
 def _estimate(t: dict, e_ref: float):

@@ -671,9 +671,22 @@ double u_pair(const OSys& s, int i, int j, double r) {
   return pade(par ? s.ap : s.aa, par ? s.Fp : s.Fa, r).h;
 }
 
+// Guiding function for reweighted sampling (App., reweighting: sample |Psi_G|^2 and weight each
+// sample by |Psi / Psi_G|^2). Reading of the Attaccalite-Sorella regularisation: Psi_G = Psi g with
+// g(x) = max(1, eps sqrt(S(x))), S = sum over both spin blocks of the squared entries of the inverse
+// Slater matrices; 1 / sqrt(S) vanishes linearly on the nodal surface of the determinants, so
+// Psi_G stays finite there. eps = 0 gives g = 1 (plain sampling).
+double frob2(const OSys& s, const double* Bst) {
+  const size_t nb = (size_t)s.nup * s.nup + (size_t)s.ndn * s.ndn;
+  double v = 0.0;
+  for (size_t k = 0; k < nb; ++k) v += Bst[k] * Bst[k];
+  return v;
+}
+double guide_g(double eps, double S) { return std::max(1.0, eps * std::sqrt(S)); }
+
 void sample_walker(const OSys& s, int wid, double* pos, double* Bst, uint64_t k0, uint64_t k1,
                    uint64_t sweep0, int nsweeps, double sigma, int kref, int* counter,
-                   uint32_t* nacc, uint32_t* nsing, double* margin) {
+                   uint32_t* nacc, uint32_t* nsing, double* margin, double eps = 0.0) {
   const int Ne = s.nup + s.ndn, M = s.M;
   std::vector<double> aov(M * NC), row(std::max(s.nup, s.ndn) + 1), w(std::max(s.nup, s.ndn) + 1);
   const uint64_t key[2] = {k0, k1};
@@ -719,6 +732,22 @@ void sample_walker(const OSys& s, int wid, double* pos, double* Bst, uint64_t k0
                 chi(s.Z[I], s.ben, std::sqrt(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2])).h;
         }
       double p = R * R * std::exp(2.0 * dJ);
+      if (eps > 0.0 && R != 0.0) {
+        // the guiding factor at the proposed configuration, from the updated inverse formed explicitly
+        const size_t nbst = (size_t)s.nup * s.nup + (size_t)s.ndn * s.ndn;
+        std::vector<double> Bn(Bst, Bst + nbst);
+        double* Bp = Bn.data() + (sg == 0 ? 0 : s.nup * s.nup);
+        std::vector<double> wt(n);
+        for (int j = 0; j < n; ++j) {
+          double v = 0;
+          for (int i = 0; i < n; ++i) v += row[i] * B[(size_t)i * n + j];
+          wt[j] = v - (j == el ? 1.0 : 0.0);
+        }
+        for (int k = 0; k < n; ++k)
+          for (int j = 0; j < n; ++j) Bp[(size_t)k * n + j] -= B[(size_t)k * n + el] * wt[j] / R;
+        const double g0 = guide_g(eps, frob2(s, Bst)), g1 = guide_g(eps, frob2(s, Bn.data()));
+        p *= (g1 / g0) * (g1 / g0);
+      }
       uint64_t ctr2[4] = {(uint64_t)wid, sweep, (uint64_t)e, 1};
       philox4x64_10(ctr2, key, rnd);
       double u = u01(rnd[0]);
@@ -877,6 +906,27 @@ int osys_eval_warp(void* p, int W, const double* pos, int nthreads, double* dEL_
   return nsing;
 }
 
+// Reweighting factor |Psi / Psi_G|^2 = 1 / g^2 of every walker from fresh inverses.
+int osys_guide_weight(void* p, int W, const double* pos, double eps, double* wt, int nthreads) {
+  OSys* s = static_cast<OSys*>(p);
+  const int Ne = s->nup + s->ndn;
+  const size_t nb = (size_t)s->nup * s->nup + (size_t)s->ndn * s->ndn;
+  int nsing = 0;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : nsing)
+#endif
+  for (int w = 0; w < W; ++w) {
+    std::vector<double> B(std::max<size_t>(nb, 1));
+    int sing = 0;
+    refresh(*s, pos + (size_t)w * Ne * 3, B.data(), &sing);
+    nsing += sing;
+    const double g = guide_g(eps, frob2(*s, B.data()));
+    wt[w] = 1.0 / (g * g);
+  }
+  return nsing;
+}
+
 // Fresh inverses for every walker: Bst [W][n_up^2 + n_dn^2].
 int osys_refresh(void* p, int W, const double* pos, double* Bst, int nthreads) {
   OSys* s = static_cast<OSys*>(p);
@@ -901,7 +951,7 @@ int osys_refresh(void* p, int W, const double* pos, double* Bst, int nthreads) {
 // margin: per-walker minimum of |u - p| / p over all decisions (in/out).
 void osys_sample(void* p, int W, double* pos, double* Bst, uint64_t wid0, uint64_t k0, uint64_t k1,
                  uint64_t sweep0, int nsweeps, double sigma, int kref, int* counter, uint32_t* nacc,
-                 uint32_t* nsing, double* margin, int nthreads) {
+                 uint32_t* nsing, double* margin, int nthreads, double eps) {
   OSys* s = static_cast<OSys*>(p);
   const int Ne = s->nup + s->ndn;
   const size_t nb = (size_t)s->nup * s->nup + (size_t)s->ndn * s->ndn;
@@ -914,7 +964,7 @@ void osys_sample(void* p, int W, double* pos, double* Bst, uint64_t wid0, uint64
   for (int w = 0; w < W; ++w) {
     int c = c0;
     sample_walker(*s, (int)(wid0 + w), pos + (size_t)w * Ne * 3, Bst + w * nb, k0, k1, sweep0, nsweeps,
-                  sigma, kref, &c, nacc + w, nsing + w, margin + w);
+                  sigma, kref, &c, nacc + w, nsing + w, margin + w, eps);
     if (w == 0) cend = c;
   }
   if (W == 0) cend = (int)((c0 + (long long)nsweeps * Ne) % kref);

@@ -158,6 +158,8 @@ void fill_geo(vmcf_batch_s& b, int g) {
   G.Mp.Bout = w.B;
   G.Mp.acc = w.acc;
   G.Mp.swct_off = swct_offset(s);
+  G.Mp.eps = w.eps;
+  G.P.eps = w.eps;
   G.Mp.accL = s.accL;
   G.Mp.acc_in_smem = 0;
   G.Mp.e_ref = w.e_ref;

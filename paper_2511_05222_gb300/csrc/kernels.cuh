@@ -29,6 +29,17 @@ __device__ __forceinline__ void load_positions(const double* src, int n3, double
   }
 }
 
+// Sum over both spin blocks of the squared entries of the inverses (the S of the guiding
+// function g = max(1, eps sqrt(S)) of reweighted sampling); identical in every thread.
+template <typename T, int GS>
+__device__ __forceinline__ double inverse_frob2(const DevSys& S, const T* B, double* red) {
+  const int t = threadIdx.x % GS;
+  double v[1] = {0.0};
+  for (int i = t; i < S.nB; i += GS) v[0] += (double)B[i] * (double)B[i];
+  group_sum<GS, 1>(v, red);
+  return v[0];
+}
+
 // Rebuild the inverses of both spin blocks of one walker into B (T) from positions.
 template <typename T, int GS>
 __device__ void refresh_walker(const DevSys& S, const double* pos, T* B, double* A, T* ao, int ao_rows, int* piv,
@@ -104,6 +115,9 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
   const uint64_t wid = P.wid0 + (uint64_t)w;
   int c = c0;
   uint32_t nacc = 0, nrej = 0, nref = 0;
+  // reweighted sampling of |Psi_G|^2, Psi_G = Psi max(1, eps sqrt(S)): S of the current inverses
+  const bool guide = P.eps > 0.0;
+  double Sg = guide ? inverse_frob2<T, GS>(S, B, red) : 0.0;
   for (int sw = 0; sw < P.nsweeps; ++sw) {
     const uint64_t sweep = sweep0 + (uint64_t)sw;
     for (int e = 0; e < Ne; ++e) {
@@ -186,18 +200,44 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
       uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
       philox4x64_10(r2, P.k0, P.k1);
       const double u = u01(r2[0]);
-      const double pr = R * R * (double)dexp<T>(T(2) * dJ);
+      double pr = R * R * (double)dexp<T>(T(2) * dJ);
+      double Sn = Sg;
+      if (guide && R != 0.0) {
+        // S after the Sherman-Morrison update B' = B - c w^T / R (c = column el of B):
+        // S' = S - (2/R) sum_j w_j (B^T c)_j + |c|^2 |w|^2 / R^2
+        double gs[3] = {0.0, 0.0, 0.0};
+        for (int j = t; j < n; j += GS) {
+          T v = 0, tj = 0;
+          for (int i = 0; i < n; ++i) {
+            v += row[i] * Bs[i * n + j];
+            tj += Bs[i * n + el] * Bs[i * n + j];
+          }
+          const T wj = v - (j == el ? T(1) : T(0));
+          wv[j] = wj;
+          col[j] = Bs[j * n + el];
+          gs[0] += (double)wj * (double)tj;
+          gs[1] += (double)wj * (double)wj;
+          gs[2] += (double)col[j] * (double)col[j];
+        }
+        group_sum<GS, 3>(gs, red);
+        Sn = Sg - 2.0 * gs[0] / R + gs[2] * gs[1] / (R * R);
+        const double g0 = fmax(1.0, P.eps * sqrt(Sg)), g1 = fmax(1.0, P.eps * sqrt(fmax(Sn, 0.0)));
+        pr *= (g1 / g0) * (g1 / g0);
+      }
       const bool ok = isfinite(pr) && R != 0.0;
       if (!ok) ++nrej;
       if (ok && u < pr) {
         // Sherman-Morrison: row el of A becomes `row`; with w_j = sum_i row_i B_ij - delta_j,el,
         // B_kj <- B_kj - B_k,el w_j / R.
-        for (int j = t; j < n; j += GS) {
-          T v = 0;
-          for (int i = 0; i < n; ++i) v += row[i] * Bs[i * n + j];
-          wv[j] = v - (j == el ? T(1) : T(0));
-          col[j] = Bs[j * n + el];
+        if (!guide) {
+          for (int j = t; j < n; j += GS) {
+            T v = 0;
+            for (int i = 0; i < n; ++i) v += row[i] * Bs[i * n + j];
+            wv[j] = v - (j == el ? T(1) : T(0));
+            col[j] = Bs[j * n + el];
+          }
         }
+        Sg = Sn;
         gsync<GS>();
         const T rinv = (T)(1.0 / R);
         for (int idx = t; idx < n * n; idx += GS) {
@@ -217,6 +257,7 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
         if (!(last && P.skip_final_refresh)) {
           refresh_walker<T, GS>(S, pos, B, A, ao, L.ao_rows, piv, f, flag);
           ++nref;
+          if (guide) Sg = inverse_frob2<T, GS>(S, B, red);
         }
         c = 0;
       }
@@ -343,6 +384,14 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       for (int i = t; i < n * n; i += GS) Bt[off + i] = (T)A[i];
       gsync<GS>();
     }
+  }
+
+  // Reweighting factor |Psi / Psi_G|^2 = 1 / g^2 of a guided chain, from the fresh inverses;
+  // every walker sum below carries it (the sample count included)
+  double wt = 1.0;
+  if (P.eps > 0.0) {
+    const double g = fmax(1.0, P.eps * sqrt(inverse_frob2<T, GS>(S, Bt, red)));
+    wt = 1.0 / (g * g);
   }
 
   // Pass 2: gradient and Laplacian rows of the MOs, a few electrons at a time; determinant
@@ -525,11 +574,11 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
         P.dELdC[(size_t)w * nO + ooff + idx] = -0.5 * ((double)D[idx] - (double)q);
       }
       if (acc_s) {
-        atomicAdd(&acc_s[oo + ooff + idx], o);
-        atomicAdd(&acc_s[oo + nO + ooff + idx], (T)cw * o);
+        atomicAdd(&acc_s[oo + ooff + idx], (T)wt * o);
+        atomicAdd(&acc_s[oo + nO + ooff + idx], (T)(wt * cw) * o);
       } else if (acc_g) {
-        acc_g[oo + ooff + idx] += (double)o;
-        acc_g[oo + nO + ooff + idx] += cw * (double)o;
+        acc_g[oo + ooff + idx] += wt * (double)o;
+        acc_g[oo + nO + ooff + idx] += wt * cw * (double)o;
       }
     }
     gsync<GS>();
@@ -646,13 +695,13 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
         if (P.dlnpsi_sw) P.dlnpsi_sw[(size_t)w * 3 * K + i] = sL[k];
         if (so > 0) {
           if (acc_s) {
-            atomicAdd(&acc_s[so + i], (T)sE[k]);
-            atomicAdd(&acc_s[so + 3 * K + i], (T)sL[k]);
-            atomicAdd(&acc_s[so + 6 * K + i], (T)(cw * sL[k]));
+            atomicAdd(&acc_s[so + i], (T)(wt * sE[k]));
+            atomicAdd(&acc_s[so + 3 * K + i], (T)(wt * sL[k]));
+            atomicAdd(&acc_s[so + 6 * K + i], (T)(wt * cw * sL[k]));
           } else if (acc_g) {
-            acc_g[so + i] += sE[k];
-            acc_g[so + 3 * K + i] += sL[k];
-            acc_g[so + 6 * K + i] += cw * sL[k];
+            acc_g[so + i] += wt * sE[k];
+            acc_g[so + 3 * K + i] += wt * sL[k];
+            acc_g[so + 6 * K + i] += wt * cw * sL[k];
           }
         }
       }
@@ -667,26 +716,26 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
     if (P.dlnpsi) P.dlnpsi[(size_t)w * 3 * K + i] = dl;
     if (P.dEL) P.dEL[(size_t)w * 3 * K + i] = de;
     if (acc_s) {
-      atomicAdd(&acc_s[3 + i], (T)de);
-      atomicAdd(&acc_s[3 + 3 * K + i], (T)dl);
-      atomicAdd(&acc_s[3 + 6 * K + i], (T)(cw * dl));
+      atomicAdd(&acc_s[3 + i], (T)(wt * de));
+      atomicAdd(&acc_s[3 + 3 * K + i], (T)(wt * dl));
+      atomicAdd(&acc_s[3 + 6 * K + i], (T)(wt * cw * dl));
     } else if (acc_g) {
-      acc_g[3 + i] += de;
-      acc_g[3 + 3 * K + i] += dl;
-      acc_g[3 + 6 * K + i] += cw * dl;
+      acc_g[3 + i] += wt * de;
+      acc_g[3 + 3 * K + i] += wt * dl;
+      acc_g[3 + 6 * K + i] += wt * cw * dl;
     }
   }
   if (t == 0) {
     if (P.EL) P.EL[w] = EL;
     if (P.logpsi) P.logpsi[w] = *la + vs[2];
     if (acc_s) {
-      atomicAdd(&acc_s[0], T(1));
-      atomicAdd(&acc_s[1], (T)cw);
-      atomicAdd(&acc_s[2], (T)(cw * cw));
+      atomicAdd(&acc_s[0], (T)wt);
+      atomicAdd(&acc_s[1], (T)(wt * cw));
+      atomicAdd(&acc_s[2], (T)(wt * cw * cw));
     } else if (acc_g) {
-      acc_g[0] += 1.0;
-      acc_g[1] += EL;
-      acc_g[2] += EL * EL;
+      acc_g[0] += wt;
+      acc_g[1] += wt * EL;
+      acc_g[2] += wt * EL * EL;
     }
     if (*flag) atomicAdd(&P.counters[0], 1ull);
   }

@@ -156,7 +156,7 @@ __device__ __forceinline__ V lane_group_sum(V v, unsigned mask) {
 // A run of single-electron Metropolis moves. LPW lanes cooperate on one walker: shells, ratio
 // terms, Jastrow pairs and Sherman-Morrison columns are split across them and combined with
 // butterfly sums, so the accept decision is identical in all of a walker's lanes.
-template <typename T, int NM, int LPW>
+template <typename T, int NM, int LPW, bool GUIDE>
 __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   // shared memory: C^up, C^dn [2][M][NM]; the CTA's inverses walker-interleaved [nB][WPC]; its
@@ -198,6 +198,13 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
   PosT* pp = Ps + ws;  // coordinate k of this walker's electrons at pp[k * WPC]
   const uint64_t wid = P.wid0 + (uint64_t)w;
   uint32_t nacc = 0, nrej = 0;
+  // reweighted sampling of |Psi_G|^2, Psi_G = Psi max(1, eps sqrt(S)): S of the current inverses
+  constexpr bool guide = GUIDE;  // P.eps > 0
+  double Sg = 0.0;
+  if (guide) {
+    for (int k = q; k < nB; k += LPW) Sg += (double)B[k * WPC] * (double)B[k * WPC];
+    Sg = lane_group_sum<LPW>(Sg, mask);
+  }
   for (int mv = 0; mv < P.nmoves; ++mv) {
     const uint64_t gm = P.move0 + (uint64_t)mv;
     const int e = (int)(gm % (uint64_t)Ne);
@@ -297,13 +304,11 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
     uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
     philox4x64_10(r2, P.k0, P.k1);
     const double u = u01(r2[0]);
-    const double pr = R * R * (double)dexp<T>((T)(2.0 * dJ));
-    const bool ok = isfinite(pr) && R != 0.0;
-    if (!ok) ++nrej;
-    if (ok && u < pr) {
-      // Sherman-Morrison: w_j = sum_i row_i B_ij - delta_j,el; B_kj <- B_kj - B_k,el w_j / R.
-      // This lane owns columns j = q, q + LPW, ...; every lane reads the whole column el first.
-      T wv[NM], col[NM];
+    double pr = R * R * (double)dexp<T>((T)(2.0 * dJ));
+    // Sherman-Morrison: w_j = sum_i row_i B_ij - delta_j,el; B_kj <- B_kj - B_k,el w_j / R.
+    // This lane owns columns j = q, q + LPW, ...; every lane reads the whole column el first.
+    T wv[NM], col[NM];
+    auto sm_vectors = [&]() {
 #pragma unroll
       for (int j = 0; j < NM; ++j) {
         wv[j] = T(0);
@@ -317,6 +322,36 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
         for (int j = 0; j < NM; ++j)
           if (j % LPW == q && j < n) wv[j] += ri * B[(off + i * n + j) * WPC];
       }
+    };
+    double Sn = Sg;
+    if constexpr (guide) if (R != 0.0) {
+      // S after the update B' = B - c w^T / R (c = column el): S - (2/R) w.(B^T c) + |c|^2 |w|^2 / R^2
+      sm_vectors();
+      double tw = 0.0, ww = 0.0, cc = 0.0;
+#pragma unroll
+      for (int j = 0; j < NM; ++j) {
+        if (j >= n) continue;
+        cc += (double)col[j] * (double)col[j];
+        if (j % LPW != q) continue;
+        T tj = 0;
+#pragma unroll
+        for (int i = 0; i < NM; ++i)
+          if (i < n) tj += col[i] * B[(off + i * n + j) * WPC];
+        const double wj = (double)((j == el) ? wv[j] - T(1) : wv[j]);
+        tw += wj * (double)tj;
+        ww += wj * wj;
+      }
+      tw = lane_group_sum<LPW>(tw, mask);
+      ww = lane_group_sum<LPW>(ww, mask);
+      Sn = Sg - 2.0 * tw / R + cc * ww / (R * R);
+      const double g0 = fmax(1.0, P.eps * sqrt(Sg)), g1 = fmax(1.0, P.eps * sqrt(fmax(Sn, 0.0)));
+      pr *= (g1 / g0) * (g1 / g0);
+    }
+    const bool ok = isfinite(pr) && R != 0.0;
+    if (!ok) ++nrej;
+    if (ok && u < pr) {
+      if constexpr (!guide) sm_vectors();
+      Sg = Sn;
       if (LPW > 1) __syncwarp(mask);  // column el is read by all lanes before its owner rewrites it
       const T rinv = (T)(1.0 / R);
 #pragma unroll
@@ -462,6 +497,17 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       for (int i = lane; i < S.nB; i += 32) Bg[(size_t)i * W + w] = Bf[i];
     }
     if (lane == 0 && *flag) atomicAdd(&P.counters[0], 1ull);
+    // reweighting factor |Psi / Psi_G|^2 = 1 / g^2 of a guided chain (g = max(1, eps sqrt(S)), S the
+    // sum of the squared entries of the fresh inverses); every walker sum below carries it
+    double wt = 1.0;
+    if (accum && P.eps > 0.0) {
+      double sq = 0.0;
+      for (int i = lane; i < S.nB; i += 32) sq += (double)Bf[i] * (double)Bf[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      const double g = fmax(1.0, P.eps * sqrt(sq));
+      wt = 1.0 / (g * g);
+    }
     if (P.mode == 0) {
       __syncwarp();
       continue;
@@ -652,8 +698,8 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
           const int mu = chunk0 + c;
           if (P.O) P.O[(size_t)w * nO + ooff + mu * ng + i] = (double)s;
           if (accum) {
-            atomicAdd(&acc_s[3 + 9 * K + ooff + mu * ng + i], s);
-            atomicAdd(&acc_s[3 + 9 * K + nO + ooff + mu * ng + i], (T)cw * s);
+            atomicAdd(&acc_s[3 + 9 * K + ooff + mu * ng + i], (T)wt * s);
+            atomicAdd(&acc_s[3 + 9 * K + nO + ooff + mu * ng + i], (T)(wt * cw) * s);
           }
         }
       }
@@ -714,8 +760,8 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
 #pragma unroll
       for (int i = 0; i < NM; ++i)
         if (i < n) {
-          y[i * 16 + el] = __float2bfloat16_rn((float)bc[i]);
-          y[(n + i) * 16 + el] = __float2bfloat16_rn((float)((T)cw * bc[i]));
+          y[i * 16 + el] = __float2bfloat16_rn((float)((T)wt * bc[i]));
+          y[(n + i) * 16 + el] = __float2bfloat16_rn((float)((T)(wt * cw) * bc[i]));
         }
     }
     // e-n Jastrow and V_en derivatives, one nucleus at a time; an electron moving is the
@@ -853,9 +899,9 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
           for (int k = 0; k < 3; ++k) {
             const double sE = (double)v6[k] + (double)frc[3 * K + 3 * a + k] + __ldg(S.dVnn + 3 * a + k);
             const double sL = (double)v6[3 + k] + (double)frc[3 * a + k];
-            atomicAdd(&acc_s[so + 3 * a + k], (T)sE);
-            atomicAdd(&acc_s[so + 3 * K + 3 * a + k], (T)sL);
-            atomicAdd(&acc_s[so + 6 * K + 3 * a + k], (T)(cw * sL));
+            atomicAdd(&acc_s[so + 3 * a + k], (T)(wt * sE));
+            atomicAdd(&acc_s[so + 3 * K + 3 * a + k], (T)(wt * sL));
+            atomicAdd(&acc_s[so + 6 * K + 3 * a + k], (T)(wt * cw * sL));
           }
       }
     }
@@ -866,18 +912,18 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       if (P.dlnpsi) P.dlnpsi[(size_t)w * 3 * K + i] = dl;
       if (P.dEL) P.dEL[(size_t)w * 3 * K + i] = de;
       if (accum) {
-        atomicAdd(&acc_s[3 + i], (T)de);
-        atomicAdd(&acc_s[3 + 3 * K + i], (T)dl);
-        atomicAdd(&acc_s[3 + 6 * K + i], (T)(cw * dl));
+        atomicAdd(&acc_s[3 + i], (T)(wt * de));
+        atomicAdd(&acc_s[3 + 3 * K + i], (T)(wt * dl));
+        atomicAdd(&acc_s[3 + 6 * K + i], (T)(wt * cw * dl));
       }
     }
     if (lane == 0) {
       if (P.EL) P.EL[w] = EL;
       if (P.logpsi) P.logpsi[w] = *la + vpart[3];
       if (accum) {
-        atomicAdd(&acc_s[0], T(1));
-        atomicAdd(&acc_s[1], (T)cw);
-        atomicAdd(&acc_s[2], (T)(cw * cw));
+        atomicAdd(&acc_s[0], (T)wt);
+        atomicAdd(&acc_s[1], (T)(wt * cw));
+        atomicAdd(&acc_s[2], (T)(wt * cw * cw));
       }
     }
     __syncwarp();
@@ -924,11 +970,16 @@ cudaError_t launch_move_small_lpw(int lpw, const DevSys& S, int W, size_t smem, 
   const int threads = (P.wpc * lpw + 31) / 32 * 32;
   smem += (sizeof(T) * (size_t)S.nB + (sizeof(T) == 4 ? 8 : 8) * (size_t)(3 * S.Ne)) * P.wpc;
   const dim3 grid((unsigned)((W + P.wpc - 1) / P.wpc));
+  if (P.eps > 0.0) {  // guided sampling: one lane-group width (the launch planned it with lpw = 2)
+    if (lpw != 2) return cudaErrorInvalidValue;
+    move_small<T, NM, 2, true><<<grid, threads, smem, st>>>(S, P);
+    return cudaGetLastError();
+  }
   switch (lpw) {
-    case 1: move_small<T, NM, 1><<<grid, threads, smem, st>>>(S, P); break;
-    case 2: move_small<T, NM, 2><<<grid, threads, smem, st>>>(S, P); break;
-    case 4: move_small<T, NM, 4><<<grid, threads, smem, st>>>(S, P); break;
-    default: move_small<T, NM, 8><<<grid, threads, smem, st>>>(S, P); break;
+    case 1: move_small<T, NM, 1, false><<<grid, threads, smem, st>>>(S, P); break;
+    case 2: move_small<T, NM, 2, false><<<grid, threads, smem, st>>>(S, P); break;
+    case 4: move_small<T, NM, 4, false><<<grid, threads, smem, st>>>(S, P); break;
+    default: move_small<T, NM, 8, false><<<grid, threads, smem, st>>>(S, P); break;
   }
   return cudaGetLastError();
 }
@@ -955,10 +1006,11 @@ template <typename T>
 cudaError_t set_smem_limits_small_impl() {
   const int lim = 227 * 1024;
   cudaError_t e;
-#define VMCF_MOVE_ATTR(NM, L)                                                                                   \
-  if ((e = cudaFuncSetAttribute(move_small<T, NM, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  VMCF_MOVE_ATTR(8, 1) VMCF_MOVE_ATTR(8, 2) VMCF_MOVE_ATTR(8, 4) VMCF_MOVE_ATTR(8, 8)
-  VMCF_MOVE_ATTR(16, 1) VMCF_MOVE_ATTR(16, 2) VMCF_MOVE_ATTR(16, 4) VMCF_MOVE_ATTR(16, 8)
+#define VMCF_MOVE_ATTR(NM, L, G)                                                                                  \
+  if ((e = cudaFuncSetAttribute(move_small<T, NM, L, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  VMCF_MOVE_ATTR(8, 1, false) VMCF_MOVE_ATTR(8, 2, false) VMCF_MOVE_ATTR(8, 4, false) VMCF_MOVE_ATTR(8, 8, false)
+  VMCF_MOVE_ATTR(16, 1, false) VMCF_MOVE_ATTR(16, 2, false) VMCF_MOVE_ATTR(16, 4, false) VMCF_MOVE_ATTR(16, 8, false)
+  VMCF_MOVE_ATTR(8, 2, true) VMCF_MOVE_ATTR(16, 2, true)
 #undef VMCF_MOVE_ATTR
   if ((e = cudaFuncSetAttribute(measure_small<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(measure_small<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;

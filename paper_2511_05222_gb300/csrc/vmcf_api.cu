@@ -292,11 +292,11 @@ int launch_small_measure(vmcf_system_s* s, int grid, const SmallMeasParams& P, c
 
 // Walkers per CTA of the move kernel: one CTA per SM when the walkers, their inverses and
 // positions fit shared memory, else as many as fit.
-int move_walkers_per_cta(const vmcf_system_s& s, int W) {
+int move_walkers_per_cta(const vmcf_system_s& s, int W, int lpw) {
   const size_t tsz = s.precision == VMCF_FP64 ? 8 : 4;
   const size_t per = tsz * s.nB + 8 * 3 * (size_t)s.Ne;
   const size_t room = (size_t)kSmemCap - s.small_move_smem;
-  int cap = (int)std::min<size_t>(room / per, (size_t)(256 / s.move_lpw));  // 256 threads per CTA at most
+  int cap = (int)std::min<size_t>(room / per, (size_t)(256 / lpw));  // 256 threads per CTA at most
   int want = (W + s.small_sms - 1) / s.small_sms;
   return std::max(1, std::min(cap, want));
 }
@@ -374,6 +374,7 @@ int measure_state_small(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
   M.Bout = wk->B;
   M.acc = wk->acc;
   M.swct_off = swct_offset(*s);
+  M.eps = wk->eps;
   M.e_ref = wk->e_ref;
   M.counters = wk->counters;
   const bool tc = wk->tc && s->tc_sums;
@@ -776,6 +777,12 @@ int vmcf_walkers_get_positions(vmcf_walkers_t wk, double* pos, int is_host, void
   return VMCF_OK;
 }
 
+int vmcf_set_guiding(vmcf_walkers_t wk, double eps) {
+  if (!wk || !(eps >= 0.0) || !std::isfinite(eps)) return fail(VMCF_EINVAL, "need eps >= 0");
+  wk->eps = eps;
+  return VMCF_OK;
+}
+
 int vmcf_reset_accumulators(vmcf_walkers_t wk, double e_ref, void* stream) {
   if (!wk || !std::isfinite(e_ref)) return fail(VMCF_EINVAL, "bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -807,7 +814,9 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
     P.k0 = wk->k0;
     P.k1 = wk->k1;
     P.sigma = step_sigma;
-    P.wpc = move_walkers_per_cta(*s, wk->W);
+    P.eps = wk->eps;
+    const int lpw = wk->eps > 0.0 ? 2 : s->move_lpw;  // guided moves use two lanes per walker
+    P.wpc = move_walkers_per_cta(*s, wk->W, lpw);
     SmallMeasParams M = small_params(*s, wk->W);
     M.pos = wk->pos;
     M.pos_sk = wk->W;
@@ -816,6 +825,7 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
     M.Bout = wk->B;
     M.acc = wk->acc;
     M.swct_off = swct_offset(*s);
+    M.eps = wk->eps;
     M.e_ref = wk->e_ref;
     M.counters = wk->counters;
     for (int sw = 0; sw < n_sweeps; ++sw) {
@@ -827,8 +837,8 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
         {
           Timed tm(wk, 0, st);
           cudaError_t e =
-              fp64 ? launch_move_small<double>(s->dev, s->small_nm, s->move_lpw, wk->W, s->small_move_smem, P, st)
-                   : launch_move_small<float>(s->dev, s->small_nm, s->move_lpw, wk->W, s->small_move_smem, P, st);
+              fp64 ? launch_move_small<double>(s->dev, s->small_nm, lpw, wk->W, s->small_move_smem, P, st)
+                   : launch_move_small<float>(s->dev, s->small_nm, lpw, wk->W, s->small_move_smem, P, st);
           if (e != cudaSuccess) return cuda_fail(e, "small move kernel launch");
         }
         done += chunk;
@@ -864,6 +874,7 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
   P.k1 = wk->k1;
   P.kref = refresh_k;
   P.sigma = step_sigma;
+  P.eps = wk->eps;
   const Launch lm = launch_rm(*s, wk->W);
   const bool fp64 = s->precision == VMCF_FP64;
   auto move = [&](int nsw, int skip) -> int {
@@ -887,6 +898,7 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
   M.Bout = wk->B;
   M.acc = wk->acc;
   M.swct_off = swct_offset(*s);
+  M.eps = wk->eps;
   M.accL = s->accL;
   M.acc_in_smem = s->acc_smem ? 1 : 0;
   M.e_ref = wk->e_ref;
@@ -917,6 +929,7 @@ int vmcf_measure(vmcf_system_t s, vmcf_walkers_t wk, void* stream) {
     M.Bout = wk->B;
     M.acc = wk->acc;
     M.swct_off = swct_offset(*s);
+    M.eps = wk->eps;
     M.accL = s->accL;
     M.acc_in_smem = s->acc_smem ? 1 : 0;
     M.e_ref = wk->e_ref;

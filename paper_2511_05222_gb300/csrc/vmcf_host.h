@@ -54,6 +54,7 @@ struct vmcf_walkers_s {
   uint64_t sweep = 0, measured = 0;
   int counter = 0;
   double e_ref = 0.0;
+  double eps = 0.0;  // guided sampling: Psi_G = Psi max(1, eps sqrt(S)); 0: plain |Psi|^2
   // small-system path state: positions and inverses walker-interleaved
   float2* posf = nullptr;   // float-float positions (mixed mode)
   void* phiT[2] = {nullptr, nullptr};  // tensor-core walker sums: [W][Mp][16] bf16 per spin

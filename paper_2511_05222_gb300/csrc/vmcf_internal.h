@@ -35,6 +35,7 @@ struct MoveParams {
   uint64_t wid0, k0, k1, sweep0;
   int nsweeps, kref, c0, skip_final_refresh;
   double sigma;
+  double eps;       // guiding function max(1, eps sqrt(S)) of reweighted sampling; 0: plain |Psi|^2
 };
 
 struct MeasParams {
@@ -45,6 +46,7 @@ struct MeasParams {
   double* acc;        // [grid][accL] FP64 slots, or NULL
   int accL, acc_in_smem;
   int swct_off;       // offset (> 0) of the space-warp sums in a slot, 0 if none
+  double eps;         // guided chain: weight the sums by |Psi / Psi_G|^2; 0: unweighted
   double e_ref;
   unsigned long long* counters;
   int W;
@@ -74,6 +76,7 @@ struct SmallMoveParams {
   int nmoves;
   int wpc;         // walkers per CTA
   double sigma;
+  double eps;      // guiding function max(1, eps sqrt(S)); 0: plain |Psi|^2
 };
 
 struct SmallLayout {
@@ -99,6 +102,7 @@ struct SmallMeasParams {
   unsigned long long* counters;
   int W;
   int swct_off;  // offset (> 0) of the space-warp sums in a slot (accumulate mode), 0 if none
+  double eps;    // guided chain: weight the sums by |Psi / Psi_G|^2; 0: unweighted
 };
 
 template <typename T>

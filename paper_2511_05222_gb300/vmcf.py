@@ -92,6 +92,7 @@ def lib(build_if_missing: bool = True):
         L.vmcf_set_tuning.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int]
         L.vmcf_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
         L.vmcf_probe_pipes.argtypes = [_dp, _dp, _dp, _vp]
+        L.vmcf_set_guiding.argtypes = [_vp, ctypes.c_double]
         L.vmcf_evaluate_warp.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.vmcf_reduce_warp.argtypes = [_vp, _vp, _dp, _dp, _vp]
         L.vmcf_finish_warp.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -257,6 +258,11 @@ class Walkers:
     def positions_into(self, dev_tensor, stream=None):
         _check(lib().vmcf_walkers_get_positions(self.h, _ptr(dev_tensor), 0, _stream(stream)),
                "vmcf_walkers_get_positions")
+
+    def set_guiding(self, eps: float):
+        """Guided sampling of |Psi_G|^2 with reweighted sums (eps = 0: plain |Psi|^2)."""
+        _check(lib().vmcf_set_guiding(self.h, float(eps)), "vmcf_set_guiding")
+        self.eps = float(eps)
 
     def reset_accumulators(self, e_ref: float, stream=None):
         _check(lib().vmcf_reset_accumulators(self.h, float(e_ref), _stream(stream)), "vmcf_reset_accumulators")

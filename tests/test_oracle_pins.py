@@ -538,3 +538,50 @@ def test_space_warp_vectors_are_derivatives_along_the_warp(sys0):
         fdl = _rich(lambda t: moved(t, "logpsi"), 1e-4)
         np.testing.assert_allclose(w["dEL_sw"][:, a, d], fdE, rtol=1e-5, atol=1e-5 * np.abs(fdE).max())
         np.testing.assert_allclose(w["dlnpsi_sw"][:, a, d], fdl, rtol=1e-6, atol=1e-6 * np.abs(fdl).max())
+
+
+# ------------------------------------------------------------------ reweighted (guided) sampling
+def test_guided_sampling_with_eps_zero_is_plain_sampling(sys0):
+    o = oracle.Oracle(sys0)
+    pos = S.initial_walkers(sys0, 32, seed=31)
+    a, b = o.new_state(pos, key=(5222, 0)), o.new_state(pos, key=(5222, 0))
+    o.sample(a, 5)
+    o.sample(b, 5, eps=0.0)
+    np.testing.assert_array_equal(a["pos"], b["pos"])
+    np.testing.assert_array_equal(o.guide_weight(a["pos"], 0.0), np.ones(32))
+
+
+def test_guided_weights_and_estimates(sys0):
+    """Weights |Psi/Psi_G|^2 = min(1, 1/(eps^2 S)) with S the summed squares of the inverse
+    Slater entries (S from an independent numpy inversion of the oracle's Slater matrices), and
+    the reweighted estimates from a |Psi_G|^2 chain agree with plain |Psi|^2 sampling within
+    their statistical errors (the reweighting identity of the appendix)."""
+    o = oracle.Oracle(sys0)
+    W, nb = 1024, 16
+    pos = S.initial_walkers(sys0, W, seed=32)
+    st0 = o.new_state(pos, key=(5222, 0))
+    o.sample(st0, 30)
+    ao = o.ao_eval(st0["pos"].reshape(-1, 3))[:, :, 0].reshape(W, sys0.Ne, -1)
+    Sx = (np.linalg.inv(ao[:, :sys0.n_up] @ sys0.C_up) ** 2).sum((1, 2)) + \
+         (np.linalg.inv(ao[:, sys0.n_up:] @ sys0.C_dn) ** 2).sum((1, 2))
+    eps = 1.0 / math.sqrt(np.quantile(Sx, 0.8))  # the guide is active on ~20% of |Psi|^2 samples
+    wt = o.guide_weight(st0["pos"], eps)
+    np.testing.assert_allclose(wt, np.minimum(1.0, 1.0 / (eps ** 2 * Sx)), rtol=1e-9)
+    assert 0.1 < (wt < 1).mean() < 0.3
+    e_ref = -76.0
+    blk = np.arange(W) * nb // W
+    res = {}
+    for name, e in (("plain", 0.0), ("guided", eps)):
+        st = o.new_state(pos, key=(5222, 7 if e else 8))
+        o.sample(st, 30, eps=e)
+        sums = estimators.new_sums(nb, sys0.K, o.nO)
+        for _ in range(8):
+            o.sample(st, 2, eps=e)
+            out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+            estimators.accumulate(sums, blk, out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], e_ref,
+                                  weight=o.guide_weight(st["pos"], e) if e else None)
+        res[name] = estimators.finish(sums, e_ref)
+    p, g = res["plain"], res["guided"]
+    assert abs(p["E"] - g["E"]) < 4.0 * math.hypot(p["E_err"], g["E_err"])
+    dF = np.abs(p["F"] - g["F"]) / np.hypot(p["F_err"], g["F_err"])
+    assert np.median(dF) < 1.5 and dF.max() < 5.0
