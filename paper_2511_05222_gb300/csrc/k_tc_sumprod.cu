@@ -3,11 +3,11 @@
 // For one spin block, the walker-weighted orbital-coefficient sums of App. A (Eq. fc-vmc-eval)
 //   S[mu][j] = sum over walkers w of the block, electrons el of the spin:
 //              psi_mu(r_{w,el}) * Y_{w,el,j},   Y = [B_{i,el} (j < n) | c_w B_{i,el} (n <= j < 2n)]
-// are one GEMM with K = walkers x 16 electron slots: D[mu][j] = sum_k PhiT[mu][k] Y[k][j]. The
-// measurement kernel writes, per walker, PhiT as [Mp][16] and YT as [Np][16] bf16 (electron
-// slots beyond n are zero). A CTA owns a range of walkers inside one jackknife block and one
-// spin, keeps D (128 lanes x Np columns, FP32) in tensor memory across the whole range, and adds
-// it to its FP64 slot at the end.
+// are one GEMM with K = walkers x electron slots: D[mu][j] = sum_k PhiT[mu][k] Y[k][j]. The
+// measurement kernels write, per walker and chunk of 16 electron slots, PhiT as [Mf][16] and YT as
+// [Nf][16] bf16 (slots beyond n, rows beyond M and columns beyond 2n are zero). A CTA owns a range
+// of walkers inside one jackknife block, one spin and one 128 x 32 tile of D, keeps the tile
+// (FP32) in tensor memory across the whole range, and adds it to its FP64 slot at the end.
 //
 // Operands are K-major without swizzle: 8-row x 16-byte core matrices, the K-adjacent core at
 // +128 bytes (leading byte offset), the M/N-adjacent core at +KC*128 bytes (stride byte offset),
@@ -70,12 +70,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 
 }  // namespace
 
-// grid.x = nblocks * cpb, grid.y = 2 spins. PhiT[s]: [W][Mp][16] bf16; YT[s]: [W][Np][16] bf16.
-// slots: [grid.y][grid.x][Mp][Np] FP64, added to. flag: set to 1 on a timed-out wait.
+// grid.x = nblocks * cpb CTAs (walker ranges), grid.y = 2 spins, grid.z = output tiles of 128 AO
+// rows x 32 Y columns (z = mt * Nt + nt). Each walker holds nch chunks of 16 electron slots:
+// PhiT[s]: [W][nch][Mf][16] bf16, YT[s]: [W][nch][Nf][16] bf16 (a chunk is one K step of 16).
+// slots: [2][gridDim.z][gridDim.x][128][32] FP64, added to. flag: set to 1 on a timed-out wait.
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_sumprod_kernel(const __nv_bfloat16* __restrict__ phiT_up, const __nv_bfloat16* __restrict__ phiT_dn,
-                      const __nv_bfloat16* __restrict__ yT_up, const __nv_bfloat16* __restrict__ yT_dn, int W, int Mp,
-                      int Np, int n_up, int n_dn, double* __restrict__ slots, int* flag) {
+                      const __nv_bfloat16* __restrict__ yT_up, const __nv_bfloat16* __restrict__ yT_dn, int W, int nch,
+                      int Mf, int Nf, int n_up, int n_dn, double* __restrict__ slots, int* flag) {
   __shared__ __align__(128) unsigned char sA[128 * kTcKC * 16];  // 128 rows (mu) x K stage
   __shared__ __align__(128) unsigned char sB[32 * kTcKC * 16];   // up to 32 rows (j) x K stage
   __shared__ __align__(8) uint64_t mbar;
@@ -85,7 +87,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const __nv_bfloat16* phiT = spin == 0 ? phiT_up : phiT_dn;
   const __nv_bfloat16* yT = spin == 0 ? yT_up : yT_dn;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const long long w0 = (long long)W * blockIdx.x / gridDim.x, w1 = (long long)W * (blockIdx.x + 1) / gridDim.x;
+  const int Nt = (Nf + 31) / 32, mt = blockIdx.z / Nt, nt = blockIdx.z - mt * Nt;
+  const int m0 = 128 * mt, j0 = 32 * nt;
+  const int Mp = Mf - m0 < 128 ? Mf - m0 : 128, Np = Nf - j0 < 32 ? Nf - j0 : 32;  // rows of this tile
+  // the CTA's walkers (never split between CTAs, so a jackknife block keeps whole walkers),
+  // as nch chunks each
+  const long long w0 = (long long)nch * ((long long)W * blockIdx.x / gridDim.x);
+  const long long w1 = (long long)nch * ((long long)W * (blockIdx.x + 1) / gridDim.x);
 
   // zero both tiles once: rows mu >= Mp and j >= Np stay zero for the whole kernel
   for (int i = tid; i < (int)(sizeof(sA) / 16); i += kTcThreads) reinterpret_cast<uint4*>(sA)[i] = make_uint4(0, 0, 0, 0);
@@ -115,14 +123,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int idx = tid; idx < kTcWalkersPerStage * Mp * 2; idx += kTcThreads) {
       const int s = idx / (Mp * 2), rem = idx - s * Mp * 2, mu = rem >> 1, h = rem & 1;
       uint4 v = make_uint4(0, 0, 0, 0);
-      if (s < nw) v = *reinterpret_cast<const uint4*>(phiT + ((size_t)(ws + s) * Mp + mu) * 16 + 8 * h);
+      if (s < nw) v = *reinterpret_cast<const uint4*>(phiT + ((size_t)(ws + s) * Mf + m0 + mu) * 16 + 8 * h);
       const int kc = 2 * s + h;
       *reinterpret_cast<uint4*>(sA + ((mu >> 3) * kTcKC + kc) * 128 + (mu & 7) * 16) = v;
     }
     for (int idx = tid; idx < kTcWalkersPerStage * Np * 2; idx += kTcThreads) {
       const int s = idx / (Np * 2), rem = idx - s * Np * 2, j = rem >> 1, h = rem & 1;
       uint4 v = make_uint4(0, 0, 0, 0);
-      if (s < nw) v = *reinterpret_cast<const uint4*>(yT + ((size_t)(ws + s) * Np + j) * 16 + 8 * h);
+      if (s < nw) v = *reinterpret_cast<const uint4*>(yT + ((size_t)(ws + s) * Nf + j0 + j) * 16 + 8 * h);
       const int kc = 2 * s + h;
       *reinterpret_cast<uint4*>(sB + ((j >> 3) * kTcKC + kc) * 128 + (j & 7) * 16) = v;
     }
@@ -172,7 +180,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
     if (row < Mp) {
-      double* slot = slots + (((size_t)spin * gridDim.x + blockIdx.x) * Mp + row) * Np;
+      double* slot = slots + ((((size_t)spin * gridDim.z + blockIdx.z) * gridDim.x + blockIdx.x) * 128 + row) * 32;
 #pragma unroll
       for (int j = 0; j < 32; ++j)
         if (j < Np) slot[j] += (double)__uint_as_float(r[j]);
@@ -184,13 +192,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 cudaError_t launch_tc_sumprod(const void* phiT_up, const void* phiT_dn, const void* yT_up, const void* yT_dn, int W,
-                              int Mp, int Np, int n_up, int n_dn, int grid_x, double* slots, int* flag,
+                              int nch, int Mf, int Nf, int n_up, int n_dn, int grid_x, double* slots, int* flag,
                               cudaStream_t st) {
-  if (Mp > 128 || Np > 32 || (Np % 16) != 0 || (Mp % 8) != 0) return cudaErrorInvalidValue;
-  tc_sumprod_kernel<<<dim3(grid_x, 2), kTcThreads, 0, st>>>(
+  if (nch < 1 || Mf < 8 || Nf < 16 || (Nf % 16) != 0 || (Mf % 8) != 0) return cudaErrorInvalidValue;
+  const int tiles = ((Mf + 127) / 128) * ((Nf + 31) / 32);
+  tc_sumprod_kernel<<<dim3(grid_x, 2, tiles), kTcThreads, 0, st>>>(
       static_cast<const __nv_bfloat16*>(phiT_up), static_cast<const __nv_bfloat16*>(phiT_dn),
-      static_cast<const __nv_bfloat16*>(yT_up), static_cast<const __nv_bfloat16*>(yT_dn), W, Mp, Np, n_up, n_dn, slots,
-      flag);
+      static_cast<const __nv_bfloat16*>(yT_up), static_cast<const __nv_bfloat16*>(yT_dn), W, nch, Mf, Nf, n_up, n_dn,
+      slots, flag);
   return cudaGetLastError();
 }
 

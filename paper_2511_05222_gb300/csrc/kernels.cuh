@@ -6,6 +6,8 @@
 //  measure_kernel  fresh inverse, E_L, adjoint nuclear derivatives, O = dlnPsi/dC, and
 //                  either per-walker outputs or the walker sums behind E, F and dE/dC
 #pragma once
+#include <cuda_bf16.h>
+
 #include "vmcf_device.cuh"
 #include "vmcf_internal.h"
 
@@ -456,6 +458,9 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   // per AO; nuclear derivatives from the recomputed AO gradient, Hessian and gradient of
   // the Laplacian; O_{mu i} = sum_e psi_mu(r_e) B_ie.
   const int nO = M * (nup + S.ndn);
+  // mixed accumulate with tensor-core O sums: AO values are staged as bf16 rows [Mf][8] (in place of O)
+  const bool tcs = sizeof(T) == 4 && P.phiT[0] != nullptr;
+  __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(base + L.Ow);
   T* fa = sm_ptr<T>(base, L.fa);  // [6][M]: AO mu's share of the nuclear derivatives, owned by mu's thread
   for (int i = t; i < 6 * M; i += GS) fa[i] = T(0);
   // space warp: the electron derivatives of E_L are wanted (walker sums or outputs)
@@ -476,9 +481,13 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       for (int e = 0; e < n; ++e) v += Bs[i * n + e] * Ps[e * n + j];
       Q[idx] = v;
     }
-    for (int idx = t; idx < M * n; idx += GS) {
-      Ow[idx] = T(0);
-      if (want_dC) D[idx] = T(0);
+    if (tcs) {  // the AO-value staging rows start empty: slots of absent electrons stay zero
+      for (int mu = t; mu < P.Mf; mu += GS) *reinterpret_cast<uint4*>(stg + 8 * mu) = make_uint4(0, 0, 0, 0);
+    } else {
+      for (int idx = t; idx < M * n; idx += GS) {
+        Ow[idx] = T(0);
+        if (want_dC) D[idx] = T(0);
+      }
     }
     gsync<GS>();
     for (int idx = t; idx < n * n; idx += GS) {  // X[e][i] = (B P B)_{i e}, over P
@@ -521,11 +530,26 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
         ce[0] += c0;
         ce[1] += c1;
         ce[2] += c2;
-        const T tdc = lp + T(2) * (j0 * g0 + j1 * g1 + j2 * g2);
-        for (int i = 0; i < n; ++i) {
-          const T b = Bs[i * n + el];
-          Ow[mu * n + i] += v * b;
-          if (want_dC) D[mu * n + i] += b * tdc;
+        if (tcs) {
+          stg[8 * mu + (el & 7)] = __float2bfloat16_rn((float)v);
+        } else {
+          const T tdc = lp + T(2) * (j0 * g0 + j1 * g1 + j2 * g2);
+          for (int i = 0; i < n; ++i) {
+            const T b = Bs[i * n + el];
+            Ow[mu * n + i] += v * b;
+            if (want_dC) D[mu * n + i] += b * tdc;
+          }
+        }
+      }
+      if (tcs && ((el & 7) == 7 || el == n - 1)) {
+        // eight electron slots of psi_mu: one 16-byte row of the K-major PhiT tile (chunk el / 16);
+        // each staging row is written and flushed by the same thread
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(P.phiT[sg]) +
+                             ((size_t)w * P.nch + (el >> 4)) * P.Mf * 16 + (el & 8);
+        for (int mu = t; mu < M; mu += GS) {
+          uint4* row = reinterpret_cast<uint4*>(stg + 8 * mu);
+          *reinterpret_cast<uint4*>(dst + (size_t)mu * 16) = *row;
+          *row = make_uint4(0, 0, 0, 0);
         }
       }
       if (warp) {  // an AO moves with its nucleus as -d/dr_e: the same terms, summed over every AO
@@ -562,9 +586,26 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       }
       gsync<GS>();
     }
+    if (tcs) {
+      // Y rows of the tensor-core sums: wt B_{j, el} (j < n) and wt (E_L - E_ref) B_{j - n, el},
+      // eight electron slots per 16-byte store
+      __nv_bfloat16* y = reinterpret_cast<__nv_bfloat16*>(P.yT[sg]) + (size_t)w * P.nch * P.Nf * 16;
+      for (int q = t; q < 2 * n * P.nch * 2; q += GS) {
+        const int j = q / (2 * P.nch), r = q - j * 2 * P.nch, c = r >> 1, h = r & 1;
+        const int i = j < n ? j : j - n;
+        const float f = (float)(j < n ? wt : wt * cw);
+        __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int e8 = 16 * c + 8 * h + k;
+          v8[k] = __float2bfloat16_rn(e8 < n ? f * (float)Bs[i * n + e8] : 0.f);
+        }
+        *reinterpret_cast<uint4*>(y + ((size_t)c * P.Nf + j) * 16 + 8 * h) = *reinterpret_cast<const uint4*>(v8);
+      }
+    }
     // this spin's O (and explicit dE_L/dC): outputs and walker sums
     const int oo = 3 + 9 * K;
-    for (int idx = t; idx < M * n; idx += GS) {
+    for (int idx = t; idx < (tcs ? 0 : M * n); idx += GS) {
       const T o = Ow[idx];
       if (P.O) P.O[(size_t)w * nO + ooff + idx] = (double)o;
       if (want_dC) {

@@ -102,7 +102,7 @@ GroupLayout layout_refresh_move(const vmcf_system_s& s, size_t tsz, int GS) {
 }
 
 // Shared-memory plan of one walker group for the measure kernel.
-GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool withD) {
+GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows = 0) {
   GroupLayout L{};
   int o = 0;
   auto take = [&](int bytes) { int at = o; o = align16(o + bytes); return at; };
@@ -126,7 +126,8 @@ GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool with
   L.fa = take((int)tsz * 6 * s.M);
   // space warp: dE_L/dr_e [3 Ne] (the kappa sums go to the AO buffer, free by then); in mixed mode
   // it shares the Gauss-Jordan scratch f, which is only used before (3 Ne floats <= 3 nmax + 1 doubles)
-  L.Ow = take((int)tsz * s.M * s.nmax);
+  // O per walker, or (tensor-core sums) a [tc_rows][8] bf16 staging tile of AO values
+  L.Ow = tc_rows > 0 ? take(16 * tc_rows) : take((int)tsz * s.M * s.nmax);
   L.D = withD ? take((int)tsz * s.M * s.nmax) : L.Ow;
   L.piv = take(4 * s.nmax);
   L.f = take(8 * (3 * s.nmax + 1));
@@ -142,6 +143,15 @@ int plan_measure(vmcf_system_s& s) {
   const size_t tsz = s.precision == VMCF_FP64 ? 8 : 4;
   s.Lmeas = layout_measure(s, tsz, s.GSm, false);
   s.LmeasD = layout_measure(s, tsz, s.GSm, true);
+  // mixed precision: the walker sums of O on the tensor cores (tiles of 128 AOs x 32 columns,
+  // chunks of 16 electrons); the measurement then stages AO values instead of holding O
+  s.LmeasTC = s.Lmeas;
+  if (s.precision == VMCF_MIXED) {
+    s.tcg_Mf = (s.M + 7) / 8 * 8;
+    s.tcg_Nf = (2 * s.nmax + 15) / 16 * 16;
+    s.tcg_nch = (s.nmax + 15) / 16;
+    s.LmeasTC = layout_measure(s, tsz, s.GSm, false, s.tcg_Mf);
+  }
   const int maxg = s.GSm == 32 ? 4 : 1;
   if (s.Lmeas.bytes > kSmemCap) return fail(VMCF_ENOTSUP, "system too large for the shared-memory plan (measure)");
   s.gpb_measD = s.LmeasD.bytes > kSmemCap ? 0 : std::max(1, std::min(maxg, kSmemCap / s.LmeasD.bytes));
@@ -211,7 +221,8 @@ void plan_small(vmcf_system_s& s) {
   s.small = true;
   s.tc_Mp = (s.M + 7) / 8 * 8;
   s.tc_Np = (2 * s.nmax + 15) / 16 * 16;
-  s.tc_sums = s.precision == VMCF_MIXED && s.tc_Mp <= 128 && s.tc_Np <= 32;
+  s.tc_nch = 1;
+  s.tc_sums = s.precision == VMCF_MIXED;
 }
 
 Launch launch_rm(const vmcf_system_s& s, int W) {
@@ -342,21 +353,30 @@ int load_positions_state(vmcf_system_s* s, vmcf_walkers_s* wk, const double* pos
   return VMCF_OK;
 }
 
-// Tensor-core walker sums: bf16 tiles (zero-filled: electron slots beyond n and Y columns
-// beyond 2n are never written and must stay zero), FP64 slots and an error flag.
+// FP64 slots of the tensor-core sums: [2 spins][tiles][nblocks * tc_cpb][128][32].
+size_t tc_slot_doubles(const vmcf_system_s& s, const vmcf_walkers_s& wk) {
+  const int Mf = s.small ? s.tc_Mp : s.tcg_Mf, Nf = s.small ? s.tc_Np : s.tcg_Nf;
+  const size_t tiles = (size_t)((Mf + 127) / 128) * ((Nf + 31) / 32);
+  return 2 * tiles * (size_t)wk.nblocks * wk.tc_cpb * 128 * 32;
+}
+
+// Tensor-core walker sums: bf16 tiles (zero-filled: electron slots beyond n, AO rows beyond M and
+// Y columns beyond 2n are never written and must stay zero), FP64 slots and an error flag.
 cudaError_t alloc_tc(vmcf_system_s* s, vmcf_walkers_s* wk) {
   const size_t W = wk->W;
+  const size_t Mf = s->small ? s->tc_Mp : s->tcg_Mf, Nf = s->small ? s->tc_Np : s->tcg_Nf;
+  const size_t nch = s->small ? s->tc_nch : s->tcg_nch;
   wk->tc_cpb = std::max(1, (int)(W / ((size_t)wk->nblocks * 64)));
-  const size_t nslot = 2 * (size_t)wk->nblocks * wk->tc_cpb * s->tc_Mp * s->tc_Np;
   cudaError_t e;
   for (int k = 0; k < 2; ++k) {
-    if ((e = cudaMalloc(&wk->phiT[k], 2 * W * s->tc_Mp * 16))) return e;
-    if ((e = cudaMalloc(&wk->yT[k], 2 * W * s->tc_Np * 16))) return e;
-    if ((e = cudaMemset(wk->phiT[k], 0, 2 * W * s->tc_Mp * 16))) return e;
-    if ((e = cudaMemset(wk->yT[k], 0, 2 * W * s->tc_Np * 16))) return e;
+    if ((e = cudaMalloc(&wk->phiT[k], 2 * W * nch * Mf * 16))) return e;
+    if ((e = cudaMalloc(&wk->yT[k], 2 * W * nch * Nf * 16))) return e;
+    if ((e = cudaMemset(wk->phiT[k], 0, 2 * W * nch * Mf * 16))) return e;
+    if ((e = cudaMemset(wk->yT[k], 0, 2 * W * nch * Nf * 16))) return e;
   }
-  if ((e = cudaMalloc(&wk->tc_slots, 8 * nslot))) return e;
-  if ((e = cudaMemset(wk->tc_slots, 0, 8 * nslot))) return e;
+  wk->tc_slot_doubles = tc_slot_doubles(*s, *wk);
+  if ((e = cudaMalloc(&wk->tc_slots, 8 * wk->tc_slot_doubles))) return e;
+  if ((e = cudaMemset(wk->tc_slots, 0, 8 * wk->tc_slot_doubles))) return e;
   if ((e = cudaMalloc(&wk->tc_flag, sizeof(int)))) return e;
   if ((e = cudaMemset(wk->tc_flag, 0, sizeof(int)))) return e;
   wk->tc = true;
@@ -393,13 +413,59 @@ int measure_state_small(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
   }
   if (tc) {
     Timed tm(wk, 3, st);
-    cudaError_t e = launch_tc_sumprod(wk->phiT[0], wk->phiT[1], wk->yT[0], wk->yT[1], wk->W, s->tc_Mp, s->tc_Np, s->nup,
-                                      s->ndn, wk->nblocks * wk->tc_cpb, wk->tc_slots, wk->tc_flag, st);
+    cudaError_t e = launch_tc_sumprod(wk->phiT[0], wk->phiT[1], wk->yT[0], wk->yT[1], wk->W, 1, s->tc_Mp, s->tc_Np,
+                                      s->nup, s->ndn, wk->nblocks * wk->tc_cpb, wk->tc_slots, wk->tc_flag, st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core walker-sum kernel launch");
   }
   return VMCF_OK;
 }
 
+// One accumulate-mode measurement on the walker-group kernels; with tensor-core sums the kernel
+// stages AO values and B rows as bf16 tiles and the GEMM kernel adds the O sums to its slots.
+int measure_state_group(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
+  MeasParams M{};
+  M.pos = wk->pos;
+  M.Bout = wk->B;
+  M.acc = wk->acc;
+  M.swct_off = swct_offset(*s);
+  M.eps = wk->eps;
+  M.accL = s->accL;
+  M.acc_in_smem = s->acc_smem ? 1 : 0;
+  M.e_ref = wk->e_ref;
+  M.counters = wk->counters;
+  M.W = wk->W;
+  const bool tc = wk->tc && s->tcg_sums;
+  Launch lme = launch_meas(*s, wk->grid_meas, true, false);
+  if (tc) {
+    for (int k = 0; k < 2; ++k) {
+      M.phiT[k] = wk->phiT[k];
+      M.yT[k] = wk->yT[k];
+    }
+    M.nch = s->tcg_nch;
+    M.Mf = s->tcg_Mf;
+    M.Nf = s->tcg_Nf;
+    // one walker group per CTA, its non-O sums straight to the CTA's FP64 slot
+    lme.L = s->LmeasTC;
+    lme.groups = 1;
+    lme.acc_off = -1;
+    lme.smem = s->LmeasTC.bytes;
+    M.acc_in_smem = 0;
+  }
+  {
+    Timed tm(wk, 1, st);
+    cudaError_t e = s->precision == VMCF_FP64 ? launch_measure<double>(s->dev, lme, M, st)
+                                              : launch_measure<float>(s->dev, lme, M, st);
+    if (e != cudaSuccess) return cuda_fail(e, "measure kernel launch");
+  }
+  if (tc) {
+    Timed tm(wk, 3, st);
+    cudaError_t e = launch_tc_sumprod(wk->phiT[0], wk->phiT[1], wk->yT[0], wk->yT[1], wk->W, s->tcg_nch, s->tcg_Mf,
+                                      s->tcg_Nf, s->nup, s->ndn, wk->nblocks * wk->tc_cpb, wk->tc_slots, wk->tc_flag,
+                                      st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core walker-sum kernel launch");
+  }
+  return VMCF_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -527,6 +593,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
     return rc;
   }
   if (!force_group) plan_small(*s);
+  s->tcg_sums = !s->small && s->precision == VMCF_MIXED;
 
   // one device allocation for all tables
   std::vector<float> alpha_f(alpha.begin(), alpha.end()), coef_f(coef.begin(), coef.end());
@@ -705,7 +772,7 @@ int vmcf_walkers_create(vmcf_system_t s, int W, const double* pos, int is_host, 
       (e = cudaMalloc(&wk->blocks, 8 * (size_t)nblocks * s->accL)) ||
       (s->small && (e = cudaMalloc(&wk->stage, 8 * npos))) ||
       (s->small && s->precision == VMCF_MIXED && (e = cudaMalloc(&wk->posf, sizeof(float2) * npos))) ||
-      (s->small && s->tc_sums && (e = alloc_tc(s, wk)))) {
+      (((s->small && s->tc_sums) || (!s->small && s->tcg_sums)) && (e = alloc_tc(s, wk)))) {
     vmcf_walkers_destroy(wk);
     return fail(VMCF_ENOMEM, std::string("walker state allocation: ") + cudaGetErrorString(e));
   }
@@ -788,8 +855,7 @@ int vmcf_reset_accumulators(vmcf_walkers_t wk, double e_ref, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   VMCF_CUDA(cudaMemsetAsync(wk->acc, 0, 8 * (size_t)wk->grid_meas * wk->sys->accL, st));
   if (wk->tc)
-    VMCF_CUDA(cudaMemsetAsync(wk->tc_slots, 0,
-                              8 * 2 * (size_t)wk->nblocks * wk->tc_cpb * wk->sys->tc_Mp * wk->sys->tc_Np, st));
+    VMCF_CUDA(cudaMemsetAsync(wk->tc_slots, 0, 8 * wk->tc_slot_doubles, st));
   wk->e_ref = e_ref;
   wk->measured = 0;
   return VMCF_OK;
@@ -893,29 +959,17 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
     if (n_sweeps > 0) return move(n_sweeps, 0);
     return VMCF_OK;
   }
-  MeasParams M{};
-  M.pos = wk->pos;
-  M.Bout = wk->B;
-  M.acc = wk->acc;
-  M.swct_off = swct_offset(*s);
-  M.eps = wk->eps;
-  M.accL = s->accL;
-  M.acc_in_smem = s->acc_smem ? 1 : 0;
-  M.e_ref = wk->e_ref;
-  M.counters = wk->counters;
-  M.W = wk->W;
-  const Launch lme = launch_meas(*s, wk->grid_meas, true, false);
   for (int k = 0; k < n_sweeps; ++k) {
     int rc = move(1, 1);
     if (rc != VMCF_OK) return rc;
-    Timed tm(wk, 1, st);
-    cudaError_t e = fp64 ? launch_measure<double>(s->dev, lme, M, st) : launch_measure<float>(s->dev, lme, M, st);
-    if (e != cudaSuccess) return cuda_fail(e, "measure kernel launch");
+    rc = measure_state_group(s, wk, st);
+    if (rc != VMCF_OK) return rc;
     wk->counter = 0;  // the measurement rebuilt the inverses
     wk->measured += 1;
   }
   return VMCF_OK;
 }
+
 
 int vmcf_measure(vmcf_system_t s, vmcf_walkers_t wk, void* stream) {
   if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
@@ -924,22 +978,8 @@ int vmcf_measure(vmcf_system_t s, vmcf_walkers_t wk, void* stream) {
     int rc = measure_state_small(s, wk, st);
     if (rc != VMCF_OK) return rc;
   } else {
-    MeasParams M{};
-    M.pos = wk->pos;
-    M.Bout = wk->B;
-    M.acc = wk->acc;
-    M.swct_off = swct_offset(*s);
-    M.eps = wk->eps;
-    M.accL = s->accL;
-    M.acc_in_smem = s->acc_smem ? 1 : 0;
-    M.e_ref = wk->e_ref;
-    M.counters = wk->counters;
-    M.W = wk->W;
-    const Launch lme = launch_meas(*s, wk->grid_meas, true, false);
-    Timed tm(wk, 1, st);
-    cudaError_t e = s->precision == VMCF_FP64 ? launch_measure<double>(s->dev, lme, M, st)
-                                              : launch_measure<float>(s->dev, lme, M, st);
-    if (e != cudaSuccess) return cuda_fail(e, "measure kernel launch");
+    int rc = measure_state_group(s, wk, st);
+    if (rc != VMCF_OK) return rc;
   }
   wk->counter = 0;
   wk->measured += 1;
@@ -993,8 +1033,8 @@ int vmcf_block_sums(vmcf_system_t s, vmcf_walkers_t wk, double* out, void* strea
   if (e != cudaSuccess) return cuda_fail(e, "block reduce launch");
   if (wk->tc) {
     const int nO = s->M * (s->nup + s->ndn);
-    e = launch_tc_fold(wk->tc_slots, wk->nblocks, wk->tc_cpb, s->tc_Mp, s->tc_Np, s->M, s->nup, s->ndn, 3 + 9 * s->K, nO,
-                       s->accL, wk->blocks, st);
+    e = launch_tc_fold(wk->tc_slots, wk->nblocks, wk->tc_cpb, s->small ? s->tc_Mp : s->tcg_Mf,
+                       s->small ? s->tc_Np : s->tcg_Nf, s->M, s->nup, s->ndn, 3 + 9 * s->K, nO, s->accL, wk->blocks, st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core fold launch");
     int flag = 0;
     VMCF_CUDA(cudaMemcpyAsync(&flag, wk->tc_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1223,9 +1263,9 @@ int vmcf_set_tuning(vmcf_system_t s, const char* key, int value) {
   }
   if (k == "tensor_core_sums") {
     const bool want = value != 0;
-    if (want && !(s->small && s->precision == VMCF_MIXED && s->tc_Mp <= 128 && s->tc_Np <= 32))
-      return fail(VMCF_EINVAL, "tensor-core walker sums need the mixed small-system path, M <= 128, 2n <= 32");
-    s->tc_sums = want;
+    if (want && s->precision != VMCF_MIXED) return fail(VMCF_EINVAL, "tensor-core walker sums need mixed precision");
+    if (s->small) s->tc_sums = want;
+    else s->tcg_sums = want;
     return VMCF_OK;
   }
   if (k == "measure_group_size") {

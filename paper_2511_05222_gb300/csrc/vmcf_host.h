@@ -38,6 +38,11 @@ struct vmcf_system_s {
   int move_lpw = 2;            // lanes per walker in the move kernel (1, 2, 4 or 8)
   bool tc_sums = false;        // mixed small path: walker sums of O on the tensor cores
   int tc_Mp = 0, tc_Np = 0;    // padded AO rows and Y columns of those tiles
+  int tc_nch = 1;              // chunks of 16 electron slots per walker
+  // walker-group path, mixed precision: the same sums on the tensor cores (tiles and chunks)
+  bool tcg_sums = false;
+  int tcg_Mf = 0, tcg_Nf = 0, tcg_nch = 1;
+  vmcf::GroupLayout LmeasTC{};  // measurement layout that stages AO values instead of holding O
 };
 
 struct vmcf_walkers_s {
@@ -62,6 +67,7 @@ struct vmcf_walkers_s {
   double* tc_slots = nullptr;          // [2][nblocks * tc_cpb][Mp][Np]
   int* tc_flag = nullptr;
   int tc_cpb = 1;
+  size_t tc_slot_doubles = 0;
   bool tc = false;
   double* stage = nullptr;  // [W][Ne][3] staging for layout conversion
   // per-kernel timing (kind 0 move, 1 measure, 2 refresh): event pairs around launches

@@ -43,6 +43,9 @@ struct MeasParams {
   void* Bout;         // T [W][nB] or NULL
   double *EL, *logpsi, *dlnpsi, *dEL, *O, *dELdC;  // outputs or NULL
   double *dEL_dr, *dEL_sw, *dlnpsi_sw;               // space-warp outputs ([W][Ne][3], [W][K][3]) or NULL
+  void* phiT[2];      // mixed accumulate: tensor-core tiles of the O sums ([W][nch][Mf][16] bf16 per spin), or NULL
+  void* yT[2];        // [W][nch][Nf][16] bf16 per spin
+  int nch, Mf, Nf;
   double* acc;        // [grid][accL] FP64 slots, or NULL
   int accL, acc_in_smem;
   int swct_off;       // offset (> 0) of the space-warp sums in a slot, 0 if none
@@ -116,10 +119,12 @@ cudaError_t set_smem_limits_small();
 cudaError_t launch_to_interleaved(const double* src, double* dst, float2* dstf, int W, int n3, cudaStream_t st);
 cudaError_t launch_from_interleaved(const double* src, double* dst, int W, int n3, cudaStream_t st);
 
+// Tensor-core walker sums of O: PhiT[s] [W][nch][Mf][16] and YT[s] [W][nch][Nf][16] bf16 per spin;
+// slots [2][tiles][grid_x][128][32] FP64 with tiles = ceil(Mf / 128) ceil(Nf / 32).
 cudaError_t launch_tc_sumprod(const void* phiT_up, const void* phiT_dn, const void* yT_up, const void* yT_dn, int W,
-                              int Mp, int Np, int n_up, int n_dn, int grid_x, double* slots, int* flag,
+                              int nch, int Mf, int Nf, int n_up, int n_dn, int grid_x, double* slots, int* flag,
                               cudaStream_t st);
-cudaError_t launch_tc_fold(const double* slots, int nblocks, int cpb, int Mp, int Np, int M, int n_up, int n_dn,
+cudaError_t launch_tc_fold(const double* slots, int nblocks, int cpb, int Mf, int Nf, int M, int n_up, int n_dn,
                            int oo, int nO, int accL, double* blocks, cudaStream_t st);
 
 // ---- ragged batch of geometries (k_batch.cu): one persistent kernel per launch shape
