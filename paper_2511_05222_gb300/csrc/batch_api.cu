@@ -78,9 +78,16 @@ struct vmcf_batch_s {
 
 namespace {
 
+// Geometry g forms its O sums on the tensor cores (its walker set holds the bf16 tiles).
+bool uses_tc(const vmcf_batch_s& b, int g) { return b.wk[g]->tc && b.sys[g]->tcg_sums; }
+
+GroupLayout meas_layout(const vmcf_batch_s& b, int g, int GS) {
+  return uses_tc(b, g) ? group_layout_meas_tc(*b.sys[g], GS) : group_layout_meas(*b.sys[g], GS);
+}
+
 // Bytes of one walker group's region for geometry g in `phase` at group size GS.
 int region_bytes(const vmcf_batch_s& b, int phase, int g, int GS) {
-  const GroupLayout L = phase == 0 ? group_layout_rm(*b.sys[g], GS) : group_layout_meas(*b.sys[g], GS);
+  const GroupLayout L = phase == 0 ? group_layout_rm(*b.sys[g], GS) : meas_layout(b, g, GS);
   return kHdr + align16(L.bytes);
 }
 
@@ -144,7 +151,7 @@ void fill_geo(vmcf_batch_s& b, int g) {
   BatchGeom G{};
   G.S = s.dev;
   G.Lrm = group_layout_rm(s, b.bucket_shape[0][b.bucket[g]].GS);
-  G.Lmeas = group_layout_meas(s, b.bucket_shape[1][b.bucket[g]].GS);
+  G.Lmeas = meas_layout(b, g, b.bucket_shape[1][b.bucket[g]].GS);
   G.P.pos = w.pos;
   G.P.B = w.B;
   G.P.nacc = w.nacc;
@@ -158,6 +165,15 @@ void fill_geo(vmcf_batch_s& b, int g) {
   G.Mp.Bout = w.B;
   G.Mp.acc = w.acc;
   G.Mp.swct_off = swct_offset(s);
+  if (uses_tc(b, g)) {
+    for (int k = 0; k < 2; ++k) {
+      G.Mp.phiT[k] = w.phiT[k];
+      G.Mp.yT[k] = w.yT[k];
+    }
+    G.Mp.nch = s.tcg_nch;
+    G.Mp.Mf = s.tcg_Mf;
+    G.Mp.Nf = s.tcg_Nf;
+  }
   G.Mp.eps = w.eps;
   G.P.eps = w.eps;
   G.Mp.accL = s.accL;
@@ -301,6 +317,14 @@ int capture(vmcf_batch_s& b, int mode, int kref, double sigma) {
       if (e == cudaSuccess) e = cudaEventRecord(b.joins[k], sk);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(b.cap, b.joins[k], 0);
     }
+  }
+  // measured sweeps: the tensor-core GEMM of each geometry's O sums over the tiles just written
+  for (int g = 0; e == cudaSuccess && mode == 1 && g < b.G; ++g) {
+    if (!uses_tc(b, g)) continue;
+    const vmcf_system_s& s = *b.sys[g];
+    const vmcf_walkers_s& w = *b.wk[g];
+    e = launch_tc_sumprod(w.phiT[0], w.phiT[1], w.yT[0], w.yT[1], w.W, s.tcg_nch, s.tcg_Mf, s.tcg_Nf, s.nup, s.ndn,
+                          w.nblocks * w.tc_cpb, w.tc_slots, w.tc_flag, b.cap);
   }
   if (e == cudaSuccess) e = launch_batch_advance(b.d_clk, b.G, mode, kref, b.d_queue, (int)b.launches.size(), b.cap);
   cudaGraph_t graph = nullptr;

@@ -246,6 +246,10 @@ GroupLayout vmcf::group_layout_meas(const vmcf_system_s& s, int GS) {
   return layout_measure(s, s.precision == VMCF_FP64 ? 8 : 4, GS, false);
 }
 
+GroupLayout vmcf::group_layout_meas_tc(const vmcf_system_s& s, int GS) {
+  return layout_measure(s, s.precision == VMCF_FP64 ? 8 : 4, GS, false, s.tcg_Mf);
+}
+
 Launch vmcf::launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD) {
   Launch lc{};
   lc.GS = s.GSm;

@@ -86,6 +86,8 @@ inline int swct_offset(const vmcf_system_s& s) { return s.swct ? 3 + 9 * s.K + 2
 // Walker-group shared-memory plans of the sweep and measurement kernels for group size GS.
 GroupLayout group_layout_rm(const vmcf_system_s& s, int GS);
 GroupLayout group_layout_meas(const vmcf_system_s& s, int GS);
+// the measurement plan that stages AO values for the tensor-core sums (mixed, walker-group path)
+GroupLayout group_layout_meas_tc(const vmcf_system_s& s, int GS);
 constexpr int kSmemCapBytes = 227 * 1024;
 int set_last_error(int code, const std::string& msg);
 }  // namespace vmcf

@@ -40,13 +40,10 @@ def _walkers(systems, specs, seed0, nb=4):
 @pytest.mark.parametrize("precision", [vmcf.FP64, vmcf.MIXED])
 def test_batch_follows_the_single_geometry_path(ragged, precision):
     """Same chains and sums as vmcf_sample on each walker set alone (positions bit for bit;
-    walker sums to rounding: FP64 1e-12, mixed 1e-5 since the single path sums in FP32 shared
-    memory before its FP64 slots)."""
+    walker sums to rounding: FP64 1e-12; mixed 1e-5; in mixed precision both form the O sums on
+    the tensor cores)."""
     specs = [(sx, W) for (sx, _), W in zip(ragged, (64, 40, 56, 24))]
     systems = [vmcf.System(sx, precision, force_group=True) for sx, _ in specs]
-    if precision == vmcf.MIXED:  # the batch forms the O sums on the SIMT pipes; so does the single path here
-        for g in systems:
-            g.set_tuning("tensor_core_sums", 0)
     wa = _walkers(systems, specs, 20)
     wb = _walkers(systems, specs, 20)
     batch = vmcf.Batch(systems, wa)
