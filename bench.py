@@ -385,7 +385,10 @@ def main():
     pipe_flops = {"fp32": work[dom]["fp32"], "fp64": work[dom]["fp64"], "sfu": work[dom]["exp"]}[bound]
     peak = {"fp32": peaks["fp32_tflops"], "fp64": peaks["fp64_tflops"], "sfu": peaks["exp_gops"] / 1e3}[bound]
     achieved = pipe_flops * W / t_launch / 1e12
-    roofline = {"bound": "alu", "pipe": bound, "kernel": f"{dom}_kernel<float>", "achieved": achieved, "peak": peak,
+    small = sysx.Ne <= 32 and max(sysx.n_up, sysx.n_dn) <= 16  # the one-warp-per-walker kernel family
+    kname = (f"{dom}_small<float, 16>" if small else
+             {"move": "move_kernel<float, 128>", "measure": "measure_kernel<float, 256>"}[dom])
+    roofline = {"bound": "alu", "pipe": bound, "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s" if bound != "sfu" else "Texp/s", "frac": achieved / peak,
                 "peak_source": "measured in this run by vmcf_probe_pipes (register-only FMA/exp kernels)",
                 "traffic": profiled_traffic() if dom == "measure" else None, "launch_ms": t_launch * 1e3,

@@ -98,6 +98,8 @@ typedef struct {
   double b_en;          /* one-body chi_I(r) = -Z_I r / (1 + b_en r); default 1.5 */
   int enable_J1;        /* one-body term on/off */
   int enable_J2;        /* two-body term on/off */
+  int two_body_exp;     /* two-body form: 0 Pade a r / (1 + F r) (Eq. twobody_v), 1 exponential
+                           (a / F)(1 - exp(-F r)) (Eq. twobody_v_exp); a is the cusp in both */
 } vmcf_jastrow;
 
 typedef struct {

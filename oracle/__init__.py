@@ -51,7 +51,8 @@ def lib():
         L = _lib
         L.osys_create.restype = ctypes.c_void_p
         L.osys_create.argtypes = [ctypes.c_int, _ip, _dp, ctypes.c_int, _ip, _ip, _ip, _dp, _dp, ctypes.c_int,
-                                  ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int]
+                                  ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int]
         L.osys_destroy.argtypes = [ctypes.c_void_p]
         L.osys_nao.argtypes = [ctypes.c_void_p]
         L.osys_norm_coefs.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int]
@@ -113,7 +114,7 @@ class Oracle:
         Z, R, c, l, npr, e, co, Cu, Cd, jp = self._keep
         self.h = L.osys_create(sys.K, _p(Z, _ip), _p(R), sys.nshell, _p(c, _ip), _p(l, _ip), _p(npr, _ip),
                                _p(e), _p(co), e.shape[1], sys.n_up, sys.n_dn, _p(Cu), _p(Cd), _p(jp),
-                               int(j.enable_J1), int(j.enable_J2))
+                               int(j.enable_J1), int(j.enable_J2), int(bool(getattr(j, "two_body_exp", False))))
         self.M = L.osys_nao(self.h)
         self.K, self.Ne = sys.K, sys.Ne
         self.nO = self.M * (sys.n_up + sys.n_dn)

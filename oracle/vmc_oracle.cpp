@@ -56,6 +56,7 @@ struct OSys {
   std::vector<double> C[2];  // [M][n_s]
   double Fa = 0.8, Fp = 0.8, aa = 0.5, ap = 0.25, ben = 1.5;
   int J1 = 1, J2 = 1;
+  int j2exp = 0;  // two-body form: 0 Pade (Eq. twobody_v), 1 exponential (Eq. twobody_v_exp)
 };
 
 // ---------------------------------------------------------------- basis (convention P1)
@@ -225,9 +226,22 @@ Rad pade(double a, double F, double r) {  // a r / (1 + F r)
   return {a * r * q, a * q * q, -2.0 * a * F * q * q * q, 6.0 * a * F * F * q * q * q * q};
 }
 
+// Exponential form (a / F) (1 - exp(-F r)) of Eq. twobody_v_exp, with the cusp a in place of 1/2.
+Rad expo(double a, double F, double r) {
+  double q = std::exp(-F * r);
+  return {-(a / F) * std::expm1(-F * r), a * q, -a * F * q, a * F * F * q};
+}
+
 Rad chi(double Z, double b, double r) {  // -Z r / (1 + b r)
   Rad p = pade(-Z, b, r);
   return p;
+}
+
+// The two-body term u_{s_i s_j}(r) of the pair: antiparallel or parallel cusp and F, in the
+// chosen form.
+Rad pair_u(const OSys& s, bool par, double r) {
+  const double a = par ? s.ap : s.aa, F = par ? s.Fp : s.Fa;
+  return s.j2exp ? expo(a, F, r) : pade(a, F, r);
 }
 
 // For a radial function h(|s|): gradient, Hessian, Laplacian and gradient of the Laplacian
@@ -331,7 +345,7 @@ void eval_walker(const OSys& s, const double* pos, bool want_dC, WalkerOut& w, b
       Vee += 1.0 / r;
       if (s.J2) {
         bool par = spin_of(s, i) == spin_of(s, j);
-        Rad u = pade(par ? s.ap : s.aa, par ? s.Fp : s.Fa, r);
+        Rad u = pair_u(s, par, r);
         J += u.h;
         RadDeriv du = radial_derivs(u, d);  // derivatives with respect to r_i
         for (int c = 0; c < 3; ++c) {
@@ -519,7 +533,7 @@ void eval_walker(const OSys& s, const double* pos, bool want_dC, WalkerOut& w, b
           dEL += -sv[d] / (r * r * r);  // V_ee
           if (s.J2) {
             bool par = spin_of(s, q) == spin_of(s, j);
-            RadDeriv du = radial_derivs(pade(par ? s.ap : s.aa, par ? s.Fp : s.Fa, r), sv);
+            RadDeriv du = radial_derivs(pair_u(s, par, r), sv);
             for (int c = 0; c < 3; ++c) {
               dJg[3 * q + c] += du.H[d][c];  // grad_q u(r_q - r_j) moves with r_q
               dJg[3 * j + c] -= du.H[d][c];  // grad_j u = -grad_q u
@@ -668,7 +682,7 @@ void refresh(const OSys& s, const double* pos, double* Bst, int* singular) {
 
 double u_pair(const OSys& s, int i, int j, double r) {
   bool par = spin_of(s, i) == spin_of(s, j);
-  return pade(par ? s.ap : s.aa, par ? s.Fp : s.Fa, r).h;
+  return pair_u(s, par, r).h;
 }
 
 // Guiding function for reweighted sampling (App., reweighting: sample |Psi_G|^2 and weight each
@@ -786,7 +800,7 @@ extern "C" {
 void* osys_create(int K, const int* Z, const double* R, int nshell, const int* center, const int* l,
                   const int* nprim, const double* exps, const double* coefs, int maxprim, int n_up,
                   int n_dn, const double* C_up, const double* C_dn, const double* jas, int enable_J1,
-                  int enable_J2) {
+                  int enable_J2, int j2exp) {
   OSys* s = new OSys();
   s->K = K;
   s->Z.assign(Z, Z + K);
@@ -819,6 +833,7 @@ void* osys_create(int K, const int* Z, const double* R, int nshell, const int* c
   s->Fa = jas[0]; s->Fp = jas[1]; s->aa = jas[2]; s->ap = jas[3]; s->ben = jas[4];
   s->J1 = enable_J1;
   s->J2 = enable_J2;
+  s->j2exp = j2exp;
   return s;
 }
 

@@ -171,7 +171,7 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
         if (q < Ne) {
           if (q == e || !S.J2) continue;
           const bool par = (q < nup) == (e < nup);
-          const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+
           T d1[3], d0[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
@@ -183,8 +183,8 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
               d0[k] = (po.h[k] - ph[3 * q + k]) + (po.l[k] - pl[3 * q + k]);
             }
           }
-          dJ += pade_value<T>(a, F, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
-                pade_value<T>(a, F, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]));
+          dJ += pair_value<T>(S, par, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
+                pair_value<T>(S, par, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]));
         } else {
           if (!S.J1) continue;
           const int I = q - Ne;
@@ -338,7 +338,7 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       if (j > e) vs[0] += (double)ri;
       if (S.J2) {
         const bool par = (j < nup) == up;
-        const Rad3<T> u = pade<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), r);
+        const Rad3<T> u = pair_rad<T>(S, par, r);
         const T gr = u.h1 * ri;
         jg0 += gr * dx;
         jg1 += gr * dy;
@@ -656,7 +656,7 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
         for (int k = 0; k < 3; ++k) dr[k] -= sv[k] * ri3;
         if (S.J2) {
           const bool par = (j < nup) == up;
-          const Rad3<T> u = pade<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), r);
+          const Rad3<T> u = pair_rad<T>(S, par, r);
           const T nn[3] = {sv[0] * ri, sv[1] * ri, sv[2] * ri};
           const T dl = u.h3 + T(2) * u.h2 * ri - T(2) * u.h1 * ri * ri;
           const T vec[3] = {ge[0] - gd[3 * j] - Jg[3 * j], ge[1] - gd[3 * j + 1] - Jg[3 * j + 1],

@@ -116,6 +116,14 @@ __device__ __forceinline__ T pade_at(T a, T F, const T d[3]) {
   }
 }
 
+// The two-body term of a pair at r = |d| for the Metropolis ratio, in the system's form.
+template <typename T>
+__device__ __forceinline__ T pair_at(const DevSys& S, bool par, const T d[3]) {
+  if (!S.j2exp) return pade_at<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), d);
+  const T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  return expo_value<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), dsqrt<T>(r2));
+}
+
 template <typename T, int NM>
 __device__ __forceinline__ void axpy_row(T (&acc)[NM], T a, const T* __restrict__ crow) {
 #pragma unroll
@@ -266,7 +274,6 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
       for (int j = q; j < Ne; j += LPW) {
         if (j == e) continue;
         const bool par = (j < nup) == (e < nup);
-        const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
         T d1[3], d0[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
             d0[k] = (oh[k] - f.x) + (ol[k] - f.y);
           }
         }
-        jacc += pade_at<T>(a, F, d1) - pade_at<T>(a, F, d0);
+        jacc += pair_at<T>(S, par, d1) - pair_at<T>(S, par, d0);
       }
     }
     if (S.J1) {
@@ -530,7 +537,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
         if (j > e) vee += ri;
         if (S.J2) {
           const bool par = (j < nup) == (e < nup);
-          const Rad3<T> u = pade<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), r);
+          const Rad3<T> u = pair_rad<T>(S, par, r);
           const T gr = u.h1 * ri;
 #pragma unroll
           for (int k = 0; k < 3; ++k) jg[k] += gr * d[k];
@@ -847,7 +854,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
         for (int k = 0; k < 3; ++k) dr[k] -= sv[k] * ri3;
         if (S.J2) {
           const bool par = (j < nup) == (e < nup);
-          const Rad3<T> u = pade<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), r);
+          const Rad3<T> u = pair_rad<T>(S, par, r);
           const T nn[3] = {sv[0] * ri, sv[1] * ri, sv[2] * ri};
           const T dl = u.h3 + T(2) * u.h2 * ri - T(2) * u.h1 * ri * ri;
           const T vec[3] = {ge[0] - gj[0], ge[1] - gj[1], ge[2] - gj[2]};

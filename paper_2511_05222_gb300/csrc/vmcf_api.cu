@@ -499,6 +499,8 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   const bool swct = (precision & VMCF_SPACE_WARP) != 0;
   precision &= ~(VMCF_FORCE_GROUP_PATH | VMCF_SPACE_WARP);
   if (precision != VMCF_FP64 && precision != VMCF_MIXED) return fail(VMCF_EINVAL, "bad precision");
+  if (jas->two_body_exp && jas->enable_J2 && !(jas->F_anti > 0.0 && jas->F_par > 0.0))
+    return fail(VMCF_EINVAL, "the exponential two-body form needs F_anti, F_par > 0");
   if (nuc->K < 1 || !nuc->Z || !nuc->R) return fail(VMCF_EINVAL, "need at least one nucleus");
   if (!finite_all(nuc->R, 3 * (size_t)nuc->K)) return fail(VMCF_EINVAL, "nuclear positions not finite");
   for (int I = 0; I < nuc->K; ++I)
@@ -708,6 +710,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   D.J1 = jas->enable_J1 ? 1 : 0;
   D.J2 = jas->enable_J2 ? 1 : 0;
   D.swct = s->swct ? 1 : 0;
+  D.j2exp = jas->two_body_exp ? 1 : 0;
   D.Vnn = Vnn;
   D.dVnn = reinterpret_cast<const double*>(b + oDv);
   s->scratch_counters = reinterpret_cast<double*>(b + oCnt);

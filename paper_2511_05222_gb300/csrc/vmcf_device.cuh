@@ -34,6 +34,7 @@ struct DevSys {
   double Fa, Fp, aa, ap, ben;
   int J1, J2;
   int swct;              // accumulate the space-warp force sums
+  int j2exp;             // two-body form: 0 Pade, 1 exponential
   double Vnn;
   const double* dVnn;    // [K][3], derivative of V_nn
 };
@@ -398,6 +399,32 @@ __device__ __forceinline__ Rad3<T> pade(T a, T F, T r) {
 template <typename T>
 __device__ __forceinline__ T pade_value(T a, T F, T r) {
   return a * r / (T(1) + F * r);
+}
+
+// Exponential form (a / F)(1 - exp(-F r)) (Eq. twobody_v_exp, cusp a) and its derivatives.
+template <typename T> __device__ __forceinline__ T dexpm1(T x);
+template <> __device__ __forceinline__ double dexpm1<double>(double x) { return expm1(x); }
+template <> __device__ __forceinline__ float dexpm1<float>(float x) { return expm1f(x); }
+template <typename T>
+__device__ __forceinline__ Rad3<T> expo(T a, T F, T r) {
+  const T q = dexp<T>(-F * r);
+  return {-(a / F) * dexpm1<T>(-F * r), a * q, -a * F * q, a * F * F * q};
+}
+template <typename T>
+__device__ __forceinline__ T expo_value(T a, T F, T r) {
+  return -(a / F) * dexpm1<T>(-F * r);
+}
+
+// The two-body term of a pair of electrons with parallel (par) or antiparallel spins.
+template <typename T>
+__device__ __forceinline__ Rad3<T> pair_rad(const DevSys& S, bool par, T r) {
+  const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+  return S.j2exp ? expo<T>(a, F, r) : pade<T>(a, F, r);
+}
+template <typename T>
+__device__ __forceinline__ T pair_value(const DevSys& S, bool par, T r) {
+  const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+  return S.j2exp ? expo_value<T>(a, F, r) : pade_value<T>(a, F, r);
 }
 
 // ---------------------------------------------------------------- FP64 Gauss-Jordan inverse

@@ -58,7 +58,8 @@ NCOMP = {0: 1, 1: 3, 2: 5}
 @dataclass
 class Jastrow:
     """One-body e-n cusp term chi_I(r) = -Z_I r / (1 + b_en r) and spin-dependent two-body
-    Pade u(r) = a r / (1 + F r) (a = 1/2 antiparallel, 1/4 parallel)."""
+    term with cusp a (1/2 antiparallel, 1/4 parallel): Pade u(r) = a r / (1 + F r), or with
+    two_body_exp the exponential form u(r) = (a / F) (1 - exp(-F r))."""
     F_anti: float = 0.8
     F_par: float = 0.8
     a_anti: float = 0.5
@@ -66,6 +67,7 @@ class Jastrow:
     b_en: float = 1.5
     enable_J1: bool = True
     enable_J2: bool = True
+    two_body_exp: bool = False
 
 
 @dataclass

@@ -44,7 +44,7 @@ class _Basis(ctypes.Structure):
 class _Jastrow(ctypes.Structure):
     _fields_ = [("F_anti", ctypes.c_double), ("F_par", ctypes.c_double), ("a_anti", ctypes.c_double),
                 ("a_par", ctypes.c_double), ("b_en", ctypes.c_double), ("enable_J1", ctypes.c_int),
-                ("enable_J2", ctypes.c_int)]
+                ("enable_J2", ctypes.c_int), ("two_body_exp", ctypes.c_int)]
 
 
 class Counters(ctypes.Structure):
@@ -148,7 +148,8 @@ class System:
         ip = lambda a: a.ctypes.data_as(_ip)
         nuc = _Nuclei(sys.K, ip(h["Z"]), dp(h["R"]))
         bas = _Basis(sys.nshell, h["e"].shape[1], ip(h["c"]), ip(h["l"]), ip(h["np"]), dp(h["e"]), dp(h["co"]))
-        jas = _Jastrow(j.F_anti, j.F_par, j.a_anti, j.a_par, j.b_en, int(j.enable_J1), int(j.enable_J2))
+        jas = _Jastrow(j.F_anti, j.F_par, j.a_anti, j.a_par, j.b_en, int(j.enable_J1), int(j.enable_J2),
+                       int(bool(getattr(j, "two_body_exp", False))))
         out = _vp()
         _check(L.vmcf_init_system(ctypes.byref(nuc), ctypes.byref(bas), dp(h["Cu"]), dp(h["Cd"]), sys.n_up, sys.n_dn,
                                   ctypes.byref(jas), dp(h["S"]),

@@ -276,3 +276,27 @@ def test_evaluate_mixed_local_energy_c9o4h8():
     assert well.mean() > 0.8
     assert r[well].max() < 1e-5, np.sort(r[well])[-5:]
     assert np.all(r[~well] < 1e-9 * kap[~well])
+
+
+@pytest.mark.parametrize("force_group", [False, True])
+def test_exponential_two_body_form_fp64(sys1, force_group):
+    """The exponential two-body form (Eq. twobody_v_exp): evaluation outputs and a short FP64
+    chain against the oracle on both kernel families."""
+    import copy
+    import dataclasses
+    sx = copy.deepcopy(sys1)
+    sx.jastrow = dataclasses.replace(sys1.jastrow, two_body_exp=True)
+    pos = S.initial_walkers(sx, 48, seed=51)
+    o = oracle.Oracle(sx)
+    ref = o.eval(pos, want=ALL)
+    g = vmcf.System(sx, vmcf.FP64, force_group=force_group)
+    got = gpu_eval(g, pos, ALL)
+    for k in ALL:
+        assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
+    st = o.new_state(pos, key=(5222, 5))
+    o.sample(st, 3)
+    wk = vmcf.Walkers(g, pos, key=(5222, 5), nblocks=4)
+    wk.sample(3)
+    ok = st["margin"] >= 1e-9
+    assert ok.sum() >= 46
+    assert np.abs(wk.positions()[ok] - st["pos"][ok]).max() < 1e-9

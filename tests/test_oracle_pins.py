@@ -7,6 +7,7 @@ differences (Richardson-extrapolated), correlated-sampling finite differences, i
 and numpy's own Philox generator.
 """
 import copy
+import dataclasses
 import itertools
 import math
 
@@ -585,3 +586,59 @@ def test_guided_weights_and_estimates(sys0):
     assert abs(p["E"] - g["E"]) < 4.0 * math.hypot(p["E_err"], g["E_err"])
     dF = np.abs(p["F"] - g["F"]) / np.hypot(p["F_err"], g["F_err"])
     assert np.median(dF) < 1.5 and dF.max() < 5.0
+
+
+# ------------------------------------------------------------------ exponential two-body form
+def _with_exp_j2(sysx):
+    s = copy.deepcopy(sysx)
+    s.jastrow = dataclasses.replace(sysx.jastrow, two_body_exp=True)
+    return s
+
+
+def test_exponential_two_body_term_cusp_and_derivatives(sys0):
+    """Eq. twobody_v_exp, u(r) = (a/F)(1 - exp(-F r)): its slope at coalescence is a, so the
+    e-e cusp keeps E_L finite; the gradient and Laplacian of ln Psi, E_L and dE_L/dr_e follow
+    from O(h^4) central differences; at F -> 0 the form tends to the linear a r, as the Pade
+    form does."""
+    # cusp: antiparallel pair
+    sx = two_electron(0.7, 0.9, S.Jastrow(enable_J1=False, two_body_exp=True))
+    p0 = np.array([0.2, 0.1, -0.1])
+    dirv = np.array([0.6, -0.8, 0.0])
+    o2 = oracle.Oracle(sx)
+    vals = [o2.eval(np.array([[p0, p0 + t * dirv]]), want=("EL",))["EL"][0] for t in (1e-3, 1e-5, 1e-7)]
+    assert abs(vals[-1] - vals[0]) < 1e-2
+    # small F: exponential and Pade forms agree to O(F)
+    for exp_form in (True, False):
+        s = two_electron(0.7, 0.9, S.Jastrow(enable_J1=False, F_anti=1e-7, two_body_exp=exp_form))
+        lp = oracle.Oracle(s).eval(np.array([[p0, p0 + 0.5 * dirv]]), want=("logpsi",))["logpsi"][0]
+        if exp_form:
+            lp_exp = lp
+        else:
+            assert abs(lp - lp_exp) < 1e-6
+    # derivatives by finite differences on water with the exponential form
+    sx = _with_exp_j2(sys0)
+    o = oracle.Oracle(sx)
+    pos = S.initial_walkers(sx, 4, seed=17)
+    out = o.eval(pos, want=("grad_lnpsi", "lap_lnpsi", "EL", "parts"))
+    wv = o.eval_warp(pos)
+    h = 1e-4
+    for e, d in [(0, 0), (3, 2), (8, 1)]:
+        def f(t, what):
+            p = pos.copy()
+            p[:, e, d] += t
+            return o.eval(p, want=(what,))[what]
+        np.testing.assert_allclose(_rich(lambda t: f(t, "logpsi"), h), out["grad_lnpsi"][:, e, d], rtol=1e-7, atol=1e-7)
+        fdE = _rich(lambda t: f(t, "EL"), h)
+        np.testing.assert_allclose(wv["dEL_dr"][:, e, d], fdE, rtol=1e-6, atol=1e-6 * np.abs(fdE).max())
+    lap_fd = np.zeros((4, sx.Ne))
+    for e in range(sx.Ne):
+        for d in range(3):
+            def gd(t):
+                p = pos.copy()
+                p[:, e, d] += t
+                return o.eval(p, want=("grad_lnpsi",))["grad_lnpsi"][:, e, d]
+            lap_fd[:, e] += _rich(gd, h)
+    np.testing.assert_allclose(lap_fd, out["lap_lnpsi"], rtol=1e-7, atol=1e-7)
+    V = out["parts"][:, 1] + out["parts"][:, 2] + out["parts"][:, 3]
+    EL = -0.5 * (lap_fd + (out["grad_lnpsi"] ** 2).sum(-1)).sum(1) + V
+    np.testing.assert_allclose(EL, out["EL"], rtol=1e-6)
