@@ -255,6 +255,13 @@ int vmcf_evaluate_sums_noalloc(vmcf_system_t sys, const double* pos, int W, doub
  *                            the small-system path (default 2);
  *   "measure_warps":         2, 4 or 8 walkers (one warp each) per CTA of the small-system
  *                            measurement kernel (default: the most that fit shared memory, up to 8);
+ *   "stagger_refresh":       1: on the walker-group kernels, walker wid counts its moves towards
+ *                            the next FP64 re-inversion from the common count plus (wid mod k), so
+ *                            that walkers re-invert at different moves (each still every k moves;
+ *                            a measurement still re-inverts every walker); the FP64 re-inversions
+ *                            then overlap the FP32 moves of other walkers. Chains change only by
+ *                            the rounding of the inverses between re-inversions. Default 0;
+ *                            VMCF_ENOTSUP on the small-system kernels;
  *   "tensor_core_sums":      1: in mixed precision, the walker sums of O and (E_L - E_ref) O are
  *                            one bf16 GEMM on the tensor cores (tcgen05, FP32 accumulation in
  *                            tensor memory, FP64 across CTAs); 0: FP32 SIMT sums (default 1 where

@@ -962,28 +962,29 @@ int osys_refresh(void* p, int W, const double* pos, double* Bst, int nthreads) {
 
 // Metropolis sweeps. pos [W][Ne][3] and Bst are updated in place. wid0 is the global id
 // of walker 0 (Philox counter word 0). counter: attempted moves since the last refresh,
-// the same for every walker (in/out). nacc, nsing: per-walker counts (added to).
+// the same for every walker (in/out; with stagger, walker wid's own count starts from counter +
+// wid mod kref). nacc, nsing: per-walker counts (added to).
 // margin: per-walker minimum of |u - p| / p over all decisions (in/out).
 void osys_sample(void* p, int W, double* pos, double* Bst, uint64_t wid0, uint64_t k0, uint64_t k1,
                  uint64_t sweep0, int nsweeps, double sigma, int kref, int* counter, uint32_t* nacc,
-                 uint32_t* nsing, double* margin, int nthreads, double eps) {
+                 uint32_t* nsing, double* margin, int nthreads, double eps, int stagger) {
   OSys* s = static_cast<OSys*>(p);
   const int Ne = s->nup + s->ndn;
   const size_t nb = (size_t)s->nup * s->nup + (size_t)s->ndn * s->ndn;
   const int c0 = *counter;
-  int cend = c0;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 4)
 #endif
   for (int w = 0; w < W; ++w) {
-    int c = c0;
-    sample_walker(*s, (int)(wid0 + w), pos + (size_t)w * Ne * 3, Bst + w * nb, k0, k1, sweep0, nsweeps,
-                  sigma, kref, &c, nacc + w, nsing + w, margin + w, eps);
-    if (w == 0) cend = c;
+    // staggered re-inversions: walker wid counts its moves from the common counter plus
+    // (wid mod kref), so that walkers re-invert at different moves (every kref moves each)
+    const uint64_t wid = wid0 + (uint64_t)w;
+    int c = stagger ? (int)((c0 + (int)(wid % (uint64_t)kref)) % kref) : c0;
+    sample_walker(*s, (int)wid, pos + (size_t)w * Ne * 3, Bst + w * nb, k0, k1, sweep0, nsweeps, sigma, kref,
+                  &c, nacc + w, nsing + w, margin + w, eps);
   }
-  if (W == 0) cend = (int)((c0 + (long long)nsweeps * Ne) % kref);
-  *counter = cend;
+  *counter = (int)((c0 + (long long)nsweeps * Ne) % kref);  // the common counter
 }
 
 }  // extern "C"

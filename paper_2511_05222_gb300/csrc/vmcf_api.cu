@@ -948,6 +948,7 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
   P.kref = refresh_k;
   P.sigma = step_sigma;
   P.eps = wk->eps;
+  P.stagger = s->stagger ? 1 : 0;
   const Launch lm = launch_rm(*s, wk->W);
   const bool fp64 = s->precision == VMCF_FP64;
   auto move = [&](int nsw, int skip) -> int {
@@ -1273,6 +1274,11 @@ int vmcf_set_tuning(vmcf_system_t s, const char* key, int value) {
     if (want && s->precision != VMCF_MIXED) return fail(VMCF_EINVAL, "tensor-core walker sums need mixed precision");
     if (s->small) s->tc_sums = want;
     else s->tcg_sums = want;
+    return VMCF_OK;
+  }
+  if (k == "stagger_refresh") {
+    if (s->small) return fail(VMCF_ENOTSUP, "staggered re-inversions need the walker-group kernels");
+    s->stagger = value != 0;
     return VMCF_OK;
   }
   if (k == "measure_group_size") {

@@ -300,3 +300,37 @@ def test_exponential_two_body_form_fp64(sys1, force_group):
     ok = st["margin"] >= 1e-9
     assert ok.sum() >= 46
     assert np.abs(wk.positions()[ok] - st["pos"][ok]).max() < 1e-9
+
+
+@pytest.mark.parametrize("kref", [26, 7])
+def test_staggered_refresh_chain_and_estimators_follow_the_oracle(sys0, kref):
+    """Walker-group moves with staggered FP64 re-inversions (walker wid counts from the common
+    count plus wid mod k): the FP64 chain and the measured estimators follow the oracle's chain
+    with the same schedule."""
+    W, nb, warm, meas, e_ref = 128, 8, 3, 2, -76.0
+    pos = S.initial_walkers(sys0, W, seed=61)
+    o = oracle.Oracle(sys0)
+    st = o.new_state(pos, key=(5222, 0))
+    o.sample(st, warm, refresh_k=kref, stagger=True)
+    g = vmcf.System(sys0, vmcf.FP64, force_group=True)
+    g.set_tuning("stagger_refresh", 1)
+    wk = vmcf.Walkers(g, pos, key=(5222, 0), nblocks=nb)
+    wk.sample(warm, 0.3, kref, measure=False)
+    wk.reset_accumulators(e_ref)
+    wk.sample(meas, 0.3, kref, measure=True)
+    sums = estimators.new_sums(nb, sys0.K, o.nO)
+    for _ in range(meas):
+        o.sample(st, 1, refresh_k=kref, stagger=True)
+        o.force_refresh(st)
+        out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+        estimators.accumulate(sums, block_map(W, nb), out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], e_ref)
+    ok = st["margin"] >= 1e-9
+    assert ok.sum() >= W - 2
+    assert np.abs(wk.positions()[ok] - st["pos"][ok]).max() < 1e-9
+    if ok.all():
+        ref = estimators.finish(sums, e_ref)
+        got = wk.reduce_estimators()
+        assert abs(got["E"] - ref["E"]) < 1e-10 * abs(ref["E"])
+        assert rel(got["F"].ravel(), ref["F"]) < 1e-9
+    with pytest.raises(vmcf.VmcfError):  # the small-system kernels re-invert all walkers together
+        vmcf.System(sys0, vmcf.FP64).set_tuning("stagger_refresh", 1)
