@@ -68,6 +68,11 @@ def lib():
         L.osys_sample.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_uint64, ctypes.c_uint64,
                                   ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                   _ip, _u32p, _u32p, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+        L.osys_set_jastrow_basis.restype = ctypes.c_int
+        L.osys_set_jastrow_basis.argtypes = [ctypes.c_void_p, ctypes.c_int, _ip, _ip, _ip, _dp, _dp, ctypes.c_int,
+                                             _dp, _dp]
+        L.osys_move_jastrow_diff.restype = ctypes.c_double
+        L.osys_move_jastrow_diff.argtypes = [ctypes.c_void_p, _dp, ctypes.c_int, _dp]
         L.osys_guide_weight.restype = ctypes.c_int
         L.osys_guide_weight.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, ctypes.c_double, _dp, ctypes.c_int]
     return _lib
@@ -115,6 +120,15 @@ class Oracle:
         self.h = L.osys_create(sys.K, _p(Z, _ip), _p(R), sys.nshell, _p(c, _ip), _p(l, _ip), _p(npr, _ip),
                                _p(e), _p(co), e.shape[1], sys.n_up, sys.n_dn, _p(Cu), _p(Cd), _p(jp),
                                int(j.enable_J1), int(j.enable_J2), int(bool(getattr(j, "two_body_exp", False))))
+        jb = getattr(j, "basis", None)
+        self.MJ = 0
+        if jb is not None:
+            jk = [np.ascontiguousarray(jb.shell_center, np.int32), np.ascontiguousarray(jb.shell_l, np.int32),
+                  np.ascontiguousarray(jb.shell_nprim, np.int32), _f64(jb.shell_exp), _f64(jb.shell_coef),
+                  _f64(jb.xi), _f64(jb.Xi)]
+            self._keep += jk
+            self.MJ = L.osys_set_jastrow_basis(self.h, jb.nshell, _p(jk[0], _ip), _p(jk[1], _ip), _p(jk[2], _ip),
+                                               _p(jk[3]), _p(jk[4]), jk[3].shape[1], _p(jk[5]), _p(jk[6]))
         self.M = L.osys_nao(self.h)
         self.K, self.Ne = sys.K, sys.Ne
         self.nO = self.M * (sys.n_up + sys.n_dn)
@@ -163,6 +177,13 @@ class Oracle:
         out["n_singular"] = lib().osys_eval_warp(self.h, W, _p(pos), self.nthreads, _p(out["dEL_dr"]),
                                                  _p(out["dEL_sw"]), _p(out["dlnpsi_sw"]))
         return out
+
+    def move_jastrow_diff(self, pos: np.ndarray, e: int, rn) -> float:
+        """The change of the Jastrow exponent that the sampler uses when electron e of the walker
+        at pos (Ne, 3) moves to rn (3,)."""
+        pos = _f64(pos)
+        rn = _f64(rn)
+        return float(lib().osys_move_jastrow_diff(self.h, _p(pos), int(e), _p(rn)))
 
     def guide_weight(self, pos: np.ndarray, eps: float) -> np.ndarray:
         """Reweighting factors |Psi / Psi_G|^2 (W,) of the guided sampling at positions (W, Ne, 3)."""

@@ -16,7 +16,10 @@
 // (Eq. restricted-C). Electrons 0..n_up-1 are spin up, n_up..Ne-1 spin down.
 // Jastrow: J = sum_{i<j} u_{s_i s_j}(r_ij) + sum_{e,I} chi_I(|r_e - R_I|), with the Pade
 // form a r / (1 + F r) of Eq. twobody_v made spin dependent (a = 1/2 antiparallel, 1/4
-// parallel) and the e-n cusp term chi_I(r) = -Z_I r / (1 + b r).
+// parallel) and the e-n cusp term chi_I(r) = -Z_I r / (1 + b r). Optionally, the AO-expanded
+// terms over a separate Jastrow basis psi^J (App., Eqs. onebody_J_inhom and threebody_jas):
+// sum_e sum_mu xi_mu psi^J_mu(r_e) + sum_{i<j} sum_{mu,nu} Xi_{mu nu} psi^J_mu(r_i) psi^J_nu(r_j),
+// read as further terms of the exponent J, with Xi symmetric.
 // Local energy (App. A, E_L = H Psi / Psi): E_L = -1/2 sum_e lap_e Psi / Psi + V_ee + V_en + V_nn.
 // Forces (Eqs. hf, pulay): total partial derivatives of E_L and ln|Psi| with respect to the
 // nuclear positions at fixed electron positions and fixed C.
@@ -57,6 +60,12 @@ struct OSys {
   double Fa = 0.8, Fp = 0.8, aa = 0.5, ap = 0.25, ben = 1.5;
   int J1 = 1, J2 = 1;
   int j2exp = 0;  // two-body form: 0 Pade (Eq. twobody_v), 1 exponential (Eq. twobody_v_exp)
+  // Jastrow basis of the AO-expanded terms (MJ = 0: none), its one-body coefficients xi [MJ] and
+  // its symmetric pair coefficients Xi [MJ][MJ]
+  std::vector<Shell> jshells;
+  std::vector<AO> jaos;
+  int MJ = 0;
+  std::vector<double> xi, Xi;
 };
 
 // ---------------------------------------------------------------- basis (convention P1)
@@ -123,13 +132,16 @@ void poly1d_derivs(int a, double al, double x, double out[4]) {
 // 11..13 gradient of the Laplacian.
 const int NC = 14;
 
-void ao_eval_point(const OSys& s, const double r[3], double* out /*[M][NC]*/) {
-  std::fill(out, out + (size_t)s.M * NC, 0.0);
-  for (int mu = 0; mu < s.M; ++mu) {
-    const AO& ao = s.aos[mu];
-    const Shell& sh = s.shells[ao.shell];
+// Every function of a basis (shells, functions) at the point r.
+void basis_eval_point(const std::vector<Shell>& shells, const std::vector<AO>& aos, const std::vector<double>& R,
+                      const double r[3], double* out /*[n][NC]*/) {
+  const int nf = (int)aos.size();
+  std::fill(out, out + (size_t)nf * NC, 0.0);
+  for (int mu = 0; mu < nf; ++mu) {
+    const AO& ao = aos[mu];
+    const Shell& sh = shells[ao.shell];
     double x[3];
-    for (int d = 0; d < 3; ++d) x[d] = r[d] - s.R[3 * sh.center + d];
+    for (int d = 0; d < 3; ++d) x[d] = r[d] - R[3 * sh.center + d];
     double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     double* o = out + (size_t)mu * NC;
     for (int k = 0; k < sh.nprim; ++k) {
@@ -159,6 +171,10 @@ void ao_eval_point(const OSys& s, const double r[3], double* out /*[M][NC]*/) {
       }
     }
   }
+}
+
+void ao_eval_point(const OSys& s, const double r[3], double* out /*[M][NC]*/) {
+  basis_eval_point(s.shells, s.aos, s.R, r, out);
 }
 
 // Index of the Hessian component (d, c) in the comps layout.
@@ -370,6 +386,37 @@ void eval_walker(const OSys& s, const double* pos, bool want_dC, WalkerOut& w, b
         Jl[e] += df.lap;
       }
     }
+  // AO-expanded Jastrow terms (Eqs. onebody_J_inhom, threebody_jas) by their definition:
+  // U = sum_e sum_mu xi_mu psi^J_mu(r_e) + sum_{i<j} sum_{mu,nu} Xi_{mu nu} psi^J_mu(r_i) psi^J_nu(r_j).
+  // U is linear in the functions of any one electron; with Xi symmetric its derivative with respect
+  // to psi^J_mu(r_e) is t_{e mu} = xi_mu + sum_{j != e} sum_nu Xi_{mu nu} psi^J_nu(r_j), so that
+  // grad_e U = sum_mu t_{e mu} grad psi^J_mu(r_e) and lap_e U = sum_mu t_{e mu} lap psi^J_mu(r_e).
+  const int MJ = s.MJ;
+  std::vector<double> jv, tJ;
+  auto JV = [&](int e, int mu, int c) { return jv[((size_t)e * MJ + mu) * NC + c]; };
+  auto XI = [&](int mu, int nu) { return s.Xi[(size_t)mu * MJ + nu]; };
+  if (MJ > 0) {
+    jv.resize((size_t)Ne * MJ * NC);
+    for (int e = 0; e < Ne; ++e) basis_eval_point(s.jshells, s.jaos, s.R, pos + 3 * e, jv.data() + (size_t)e * MJ * NC);
+    for (int e = 0; e < Ne; ++e)
+      for (int mu = 0; mu < MJ; ++mu) J += s.xi[mu] * JV(e, mu, 0);
+    for (int i = 0; i < Ne; ++i)
+      for (int j = i + 1; j < Ne; ++j)
+        for (int mu = 0; mu < MJ; ++mu)
+          for (int nu = 0; nu < MJ; ++nu) J += JV(i, mu, 0) * XI(mu, nu) * JV(j, nu, 0);
+    tJ.assign((size_t)Ne * MJ, 0.0);
+    for (int e = 0; e < Ne; ++e)
+      for (int mu = 0; mu < MJ; ++mu) {
+        double t = s.xi[mu];
+        for (int j = 0; j < Ne; ++j) {
+          if (j == e) continue;
+          for (int nu = 0; nu < MJ; ++nu) t += XI(mu, nu) * JV(j, nu, 0);
+        }
+        tJ[(size_t)e * MJ + mu] = t;
+        for (int c = 0; c < 3; ++c) Jg[3 * e + c] += t * JV(e, mu, 1 + c);
+        Jl[e] += t * JV(e, mu, 4);
+      }
+  }
   for (int I = 0; I < K; ++I)
     for (int Jn = I + 1; Jn < K; ++Jn) {
       double d[3];
@@ -460,9 +507,34 @@ void eval_walker(const OSys& s, const double* pos, bool want_dC, WalkerOut& w, b
           double r = std::sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
           RadDeriv df = radial_derivs(chi(s.Z[I], s.ben, r), sv);
           dlnpsi -= df.g[d];
-          for (int c = 0; c < 3; ++c) dJg[3 * e + c] = -df.H[d][c];
-          dJl[e] = -df.glap[d];
+          for (int c = 0; c < 3; ++c) dJg[3 * e + c] += -df.H[d][c];
+          dJl[e] += -df.glap[d];
         }
+      // AO-expanded terms: the Jastrow functions centred on I move with it, d psi^J_nu(r_j) =
+      // -d_d psi^J_nu(r_j) (and one order up for their gradients and Laplacians); d U =
+      // sum_{e,mu} t_{e mu} d psi^J_mu(r_e), and t_{e mu} changes by sum_{j != e} sum_nu Xi_{mu nu} d psi^J_nu(r_j).
+      if (MJ > 0) {
+        std::vector<double> dphi((size_t)Ne * MJ, 0.0);
+        std::vector<char> onI(MJ, 0);
+        for (int mu = 0; mu < MJ; ++mu) onI[mu] = s.jshells[s.jaos[mu].shell].center == I;
+        for (int e = 0; e < Ne; ++e)
+          for (int nu = 0; nu < MJ; ++nu)
+            if (onI[nu]) dphi[(size_t)e * MJ + nu] = -JV(e, nu, 1 + d);
+        for (int e = 0; e < Ne; ++e)
+          for (int mu = 0; mu < MJ; ++mu) {
+            double dt = 0.0;
+            for (int j = 0; j < Ne; ++j) {
+              if (j == e) continue;
+              for (int nu = 0; nu < MJ; ++nu)
+                if (onI[nu]) dt += XI(mu, nu) * dphi[(size_t)j * MJ + nu];
+            }
+            const double t = tJ[(size_t)e * MJ + mu];
+            dlnpsi += t * dphi[(size_t)e * MJ + mu];
+            for (int c = 0; c < 3; ++c)
+              dJg[3 * e + c] += (onI[mu] ? -JV(e, mu, hidx(d, c)) : 0.0) * t + JV(e, mu, 1 + c) * dt;
+            dJl[e] += (onI[mu] ? -JV(e, mu, 11 + d) : 0.0) * t + JV(e, mu, 4) * dt;
+          }
+      }
       for (int e = 0; e < Ne; ++e) {
         double t = dl[e] + dJl[e];
         for (int c = 0; c < 3; ++c)
@@ -553,6 +625,22 @@ void eval_walker(const OSys& s, const double* pos, bool want_dC, WalkerOut& w, b
             dJl[q] += df.glap[d];
           }
         }
+        // AO-expanded terms: only the functions at r_q move; t_q does not depend on r_q, and for
+        // e != q, t_{e mu} changes by sum_nu Xi_{mu nu} d_d psi^J_nu(r_q).
+        if (MJ > 0)
+          for (int e = 0; e < Ne; ++e)
+            for (int mu = 0; mu < MJ; ++mu) {
+              if (e == q) {
+                const double t = tJ[(size_t)q * MJ + mu];
+                for (int c = 0; c < 3; ++c) dJg[3 * q + c] += JV(q, mu, hidx(d, c)) * t;
+                dJl[q] += JV(q, mu, 11 + d) * t;
+              } else {
+                double dt = 0.0;
+                for (int nu = 0; nu < MJ; ++nu) dt += XI(mu, nu) * JV(q, nu, 1 + d);
+                for (int c = 0; c < 3; ++c) dJg[3 * e + c] += JV(e, mu, 1 + c) * dt;
+                dJl[e] += JV(e, mu, 4) * dt;
+              }
+            }
         for (int e = 0; e < Ne; ++e) {
           double t = dl[e] + dJl[e];
           for (int c = 0; c < 3; ++c)
@@ -698,6 +786,48 @@ double frob2(const OSys& s, const double* Bst) {
 }
 double guide_g(double eps, double S) { return std::max(1.0, eps * std::sqrt(S)); }
 
+// Change of the Jastrow exponent J when electron e moves from pos[e] to rn: the two-body terms
+// of its pairs, its e-n terms and the AO-expanded terms that hold it.
+double move_jastrow_diff(const OSys& s, const double* pos, int e, const double rn[3]) {
+  const int Ne = s.nup + s.ndn;
+  double dJ = 0.0;
+  if (s.J2)
+    for (int j = 0; j < Ne; ++j) {
+      if (j == e) continue;
+      double dn[3], d0[3];
+      for (int d = 0; d < 3; ++d) { dn[d] = rn[d] - pos[3 * j + d]; d0[d] = pos[3 * e + d] - pos[3 * j + d]; }
+      dJ += u_pair(s, e, j, std::sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2])) -
+            u_pair(s, e, j, std::sqrt(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]));
+    }
+  if (s.J1)
+    for (int I = 0; I < s.K; ++I) {
+      double dn[3], d0[3];
+      for (int d = 0; d < 3; ++d) { dn[d] = rn[d] - s.R[3 * I + d]; d0[d] = pos[3 * e + d] - s.R[3 * I + d]; }
+      dJ += chi(s.Z[I], s.ben, std::sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2])).h -
+            chi(s.Z[I], s.ben, std::sqrt(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2])).h;
+    }
+  if (s.MJ > 0) {
+    // AO-expanded terms (Eqs. onebody_J_inhom, threebody_jas): the terms that hold electron e,
+    // sum_mu xi_mu dphi_mu + sum_{j != e} sum_{mu,nu} dphi_mu Xi_{mu nu} psi^J_nu(r_j), with
+    // dphi = psi^J(r') - psi^J(r_e)
+    const int MJ = s.MJ;
+    std::vector<double> jn((size_t)MJ * NC), jo((size_t)MJ * NC), jj((size_t)MJ * NC), dphi(MJ);
+    basis_eval_point(s.jshells, s.jaos, s.R, rn, jn.data());
+    basis_eval_point(s.jshells, s.jaos, s.R, pos + 3 * e, jo.data());
+    for (int mu = 0; mu < MJ; ++mu) {
+      dphi[mu] = jn[(size_t)mu * NC] - jo[(size_t)mu * NC];
+      dJ += s.xi[mu] * dphi[mu];
+    }
+    for (int j = 0; j < Ne; ++j) {
+      if (j == e) continue;
+      basis_eval_point(s.jshells, s.jaos, s.R, pos + 3 * j, jj.data());
+      for (int mu = 0; mu < MJ; ++mu)
+        for (int nu = 0; nu < MJ; ++nu) dJ += dphi[mu] * s.Xi[(size_t)mu * MJ + nu] * jj[(size_t)nu * NC];
+    }
+  }
+  return dJ;
+}
+
 void sample_walker(const OSys& s, int wid, double* pos, double* Bst, uint64_t k0, uint64_t k1,
                    uint64_t sweep0, int nsweeps, double sigma, int kref, int* counter,
                    uint32_t* nacc, uint32_t* nsing, double* margin, double eps = 0.0) {
@@ -729,22 +859,7 @@ void sample_walker(const OSys& s, int wid, double* pos, double* Bst, uint64_t k0
         R += v * B[(size_t)i * n + el];
       }
       // Jastrow ratio
-      double dJ = 0.0;
-      if (s.J2)
-        for (int j = 0; j < Ne; ++j) {
-          if (j == e) continue;
-          double dn[3], d0[3];
-          for (int d = 0; d < 3; ++d) { dn[d] = rn[d] - pos[3 * j + d]; d0[d] = pos[3 * e + d] - pos[3 * j + d]; }
-          dJ += u_pair(s, e, j, std::sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2])) -
-                u_pair(s, e, j, std::sqrt(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]));
-        }
-      if (s.J1)
-        for (int I = 0; I < s.K; ++I) {
-          double dn[3], d0[3];
-          for (int d = 0; d < 3; ++d) { dn[d] = rn[d] - s.R[3 * I + d]; d0[d] = pos[3 * e + d] - s.R[3 * I + d]; }
-          dJ += chi(s.Z[I], s.ben, std::sqrt(dn[0] * dn[0] + dn[1] * dn[1] + dn[2] * dn[2])).h -
-                chi(s.Z[I], s.ben, std::sqrt(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2])).h;
-        }
+      const double dJ = move_jastrow_diff(s, pos, e, rn);
       double p = R * R * std::exp(2.0 * dJ);
       if (eps > 0.0 && R != 0.0) {
         // the guiding factor at the proposed configuration, from the updated inverse formed explicitly
@@ -794,6 +909,34 @@ void sample_walker(const OSys& s, int wid, double* pos, double* Bst, uint64_t k0
 
 }  // namespace
 
+// Shells of a basis: each primitive normalised, then the contraction renormalised (convention
+// P1); returns the number of functions added.
+static int add_shells(std::vector<Shell>& shells, std::vector<AO>& aos, int nshell, const int* center, const int* l,
+               const int* nprim, const double* exps, const double* coefs, int maxprim) {
+  int nf = 0;
+  for (int sh = 0; sh < nshell; ++sh) {
+    Shell x;
+    x.center = center[sh];
+    x.l = l[sh];
+    x.nprim = nprim[sh];
+    double d[8], S = 0.0;
+    for (int k = 0; k < x.nprim; ++k) {
+      x.alpha[k] = exps[sh * maxprim + k];
+      d[k] = coefs[sh * maxprim + k];
+    }
+    for (int a = 0; a < x.nprim; ++a)
+      for (int b = 0; b < x.nprim; ++b) S += d[a] * d[b] * prim_overlap(x.alpha[a], x.alpha[b], x.l);
+    for (int k = 0; k < x.nprim; ++k) x.coef[k] = d[k] * prim_norm(x.alpha[k], x.l) / std::sqrt(S);
+    const int first = (int)shells.size();
+    shells.push_back(x);
+    for (auto& poly : solid_harmonics(x.l)) {
+      aos.push_back({first, poly});
+      ++nf;
+    }
+  }
+  return nf;
+}
+
 // ==================================================================== C interface
 extern "C" {
 
@@ -805,27 +948,7 @@ void* osys_create(int K, const int* Z, const double* R, int nshell, const int* c
   s->K = K;
   s->Z.assign(Z, Z + K);
   s->R.assign(R, R + 3 * K);
-  s->M = 0;
-  for (int sh = 0; sh < nshell; ++sh) {
-    Shell x;
-    x.center = center[sh];
-    x.l = l[sh];
-    x.nprim = nprim[sh];
-    // Normalise each primitive, then renormalise the contraction (convention P1).
-    double d[8], S = 0.0;
-    for (int k = 0; k < x.nprim; ++k) {
-      x.alpha[k] = exps[sh * maxprim + k];
-      d[k] = coefs[sh * maxprim + k];
-    }
-    for (int a = 0; a < x.nprim; ++a)
-      for (int b = 0; b < x.nprim; ++b) S += d[a] * d[b] * prim_overlap(x.alpha[a], x.alpha[b], x.l);
-    for (int k = 0; k < x.nprim; ++k) x.coef[k] = d[k] * prim_norm(x.alpha[k], x.l) / std::sqrt(S);
-    s->shells.push_back(x);
-    for (auto& poly : solid_harmonics(x.l)) {
-      s->aos.push_back({sh, poly});
-      s->M++;
-    }
-  }
+  s->M = add_shells(s->shells, s->aos, nshell, center, l, nprim, exps, coefs, maxprim);
   s->nup = n_up;
   s->ndn = n_dn;
   s->C[0].assign(C_up, C_up + (size_t)s->M * n_up);
@@ -835,6 +958,30 @@ void* osys_create(int K, const int* Z, const double* R, int nshell, const int* c
   s->J2 = enable_J2;
   s->j2exp = j2exp;
   return s;
+}
+
+// Jastrow basis of the AO-expanded terms (same conventions as the determinant basis, centred on
+// the same nuclei), one-body coefficients xi [MJ] and symmetric pair coefficients Xi [MJ][MJ]
+// (either may be NULL: zero). Returns MJ.
+int osys_set_jastrow_basis(void* p, int nshell, const int* center, const int* l, const int* nprim,
+                           const double* exps, const double* coefs, int maxprim, const double* xi,
+                           const double* Xi) {
+  OSys* s = static_cast<OSys*>(p);
+  s->jshells.clear();
+  s->jaos.clear();
+  s->MJ = add_shells(s->jshells, s->jaos, nshell, center, l, nprim, exps, coefs, maxprim);
+  const size_t MJ = (size_t)s->MJ;
+  s->xi.assign(MJ, 0.0);
+  s->Xi.assign(MJ * MJ, 0.0);
+  if (xi) s->xi.assign(xi, xi + MJ);
+  if (Xi) s->Xi.assign(Xi, Xi + MJ * MJ);
+  return s->MJ;
+}
+
+// Change of the Jastrow exponent that the sampler uses when electron e of the walker at pos
+// [Ne][3] moves to rn [3].
+double osys_move_jastrow_diff(void* p, const double* pos, int e, const double* rn) {
+  return move_jastrow_diff(*static_cast<OSys*>(p), pos, e, rn);
 }
 
 void osys_destroy(void* p) { delete static_cast<OSys*>(p); }

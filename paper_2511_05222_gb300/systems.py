@@ -56,10 +56,33 @@ NCOMP = {0: 1, 1: 3, 2: 5}
 
 
 @dataclass
+class JastrowBasis:
+    """Jastrow basis of the AO-expanded Jastrow terms: shells on the system's nuclei (same
+    conventions as the determinant basis: real solid harmonics, raw coefficients of normalised
+    primitives), one-body coefficients xi (MJ,) and symmetric pair coefficients Xi (MJ, MJ)."""
+    shell_center: np.ndarray  # (nshell,) int32
+    shell_l: np.ndarray       # (nshell,) int32, 0..2
+    shell_nprim: np.ndarray   # (nshell,) int32
+    shell_exp: np.ndarray     # (nshell, MAXPRIM) float64
+    shell_coef: np.ndarray    # (nshell, MAXPRIM) float64, RAW coefficients
+    xi: np.ndarray            # (MJ,) float64
+    Xi: np.ndarray            # (MJ, MJ) float64, symmetric
+
+    @property
+    def MJ(self) -> int:
+        return int(sum(NCOMP[int(l)] for l in self.shell_l))
+
+    @property
+    def nshell(self) -> int:
+        return int(self.shell_l.shape[0])
+
+
+@dataclass
 class Jastrow:
     """One-body e-n cusp term chi_I(r) = -Z_I r / (1 + b_en r) and spin-dependent two-body
     term with cusp a (1/2 antiparallel, 1/4 parallel): Pade u(r) = a r / (1 + F r), or with
-    two_body_exp the exponential form u(r) = (a / F) (1 - exp(-F r))."""
+    two_body_exp the exponential form u(r) = (a / F) (1 - exp(-F r)); optionally the AO-expanded
+    one-body and pair terms over a Jastrow basis (basis, None for none)."""
     F_anti: float = 0.8
     F_par: float = 0.8
     a_anti: float = 0.5
@@ -68,6 +91,7 @@ class Jastrow:
     enable_J1: bool = True
     enable_J2: bool = True
     two_body_exp: bool = False
+    basis: JastrowBasis | None = None
 
 
 @dataclass
@@ -321,6 +345,50 @@ def make_ragged_batch(n_geom: int = 64, seed: int = 3, only=None):
         sys = make_molecule(f"ragged{g}", Z, R, np.random.default_rng([GEN_SEED_BASE + seed, 2, g]),
                             np.random.default_rng([GEN_SEED_BASE + seed, 3, g]))
         out.append((sys, W))
+    return out
+
+
+def jastrow_basis(sys: System, seed: int = 0, xi_scale: float = 0.1, same_scale: float = 0.03,
+                  pair_scale: float = 0.01) -> JastrowBasis:
+    """Seeded Jastrow basis and coefficients for the AO-expanded Jastrow terms: uncontracted
+    primitives, H [3s1p] and heavy atoms [4s2p1d] (the medium Jastrow basis); exponents log-uniform
+    in [0.1, 3] for s, [0.2, 2] for p, [0.3, 1.5] for d, sorted descending per l; xi_mu uniform in
+    +-xi_scale; Xi symmetric with Gaussian entries of standard deviation same_scale between functions
+    of one nucleus and pair_scale between nuclei (the inter-nuclear entries are kept)."""
+    rng = np.random.default_rng([GEN_SEED_BASE + 2000, seed])
+    centers, ls, exps = [], [], []
+    ranges = {0: (0.1, 3.0), 1: (0.2, 2.0), 2: (0.3, 1.5)}
+    for I, z in enumerate(sys.Z):
+        counts = {0: 3, 1: 1} if z == 1 else {0: 4, 1: 2, 2: 1}
+        for l, cnt in counts.items():
+            lo, hi = ranges[l]
+            for a in np.sort(np.exp(rng.uniform(math.log(lo), math.log(hi), size=cnt)))[::-1]:
+                centers.append(I)
+                ls.append(l)
+                exps.append(a)
+    ns = len(ls)
+    ex = np.zeros((ns, MAXPRIM))
+    co = np.zeros((ns, MAXPRIM))
+    ex[:, 0] = exps
+    co[:, 0] = 1.0
+    cen = np.array(centers, np.int32)
+    lv = np.array(ls, np.int32)
+    fcen = np.concatenate([[c] * NCOMP[int(l)] for c, l in zip(cen, lv)]).astype(np.int32)
+    MJ = fcen.shape[0]
+    xi = rng.uniform(-xi_scale, xi_scale, size=MJ)
+    same = fcen[:, None] == fcen[None, :]
+    G = rng.standard_normal((MJ, MJ)) * np.where(same, same_scale, pair_scale)
+    Xi = np.triu(G) + np.triu(G, 1).T
+    return JastrowBasis(cen, lv, np.ones(ns, np.int32), ex, co, xi, np.ascontiguousarray(Xi))
+
+
+def with_jastrow_basis(sys: System, jb: JastrowBasis | None = None, seed: int = 0) -> System:
+    """A copy of the system whose Jastrow also holds the AO-expanded terms (jb, or a seeded
+    jastrow_basis of the system)."""
+    import copy
+    out = copy.copy(sys)
+    out.jastrow = copy.copy(sys.jastrow)
+    out.jastrow.basis = jb if jb is not None else jastrow_basis(sys, seed)
     return out
 
 
