@@ -100,6 +100,17 @@ typedef struct {
   int enable_J2;        /* two-body term on/off */
   int two_body_exp;     /* two-body form: 0 Pade a r / (1 + F r) (Eq. twobody_v), 1 exponential
                            (a / F)(1 - exp(-F r)) (Eq. twobody_v_exp); a is the cusp in both */
+  /* AO-expanded Jastrow terms over a separate Jastrow basis psi^J (App., Eqs. onebody_J_inhom and
+   * threebody_jas), read as further terms of the Jastrow exponent:
+   *   sum_e sum_mu xi_mu psi^J_mu(r_e) + sum_{i<j} sum_{mu,nu} Xi_{mu nu} psi^J_mu(r_i) psi^J_nu(r_j)
+   * (the inhomogeneous one-body term and the three-body term; entries of Xi between functions of
+   * different nuclei are the four-body terms). NULL basis: none. The basis follows the conventions
+   * of the determinant basis, on the same nuclei, with at most 1024 functions (MJ); xi: host [MJ]
+   * or NULL (zero); Xi: host [MJ][MJ] or NULL (zero), symmetric to 1e-12 relative (else
+   * VMCF_EINVAL). Systems with these terms run on the walker-group kernels. */
+  const vmcf_basis* basis;
+  const double* xi;
+  const double* Xi;
 } vmcf_jastrow;
 
 typedef struct {

@@ -1,0 +1,115 @@
+// AO-expanded Jastrow terms over a separate Jastrow basis psi^J (arXiv:2511.05222, App.,
+// Eqs. onebody_J_inhom and threebody_jas), read as terms of the Jastrow exponent:
+//   U = sum_e sum_mu xi_mu psi^J_mu(r_e) + sum_{i<j} sum_{mu,nu} Xi_{mu nu} psi^J_mu(r_i) psi^J_nu(r_j)
+// with Xi symmetric. With s = sum_e psi^J(r_e), t0 = xi + Xi s and u_e = Xi psi^J(r_e):
+//   t_e = t0 - u_e = dU / d psi^J(r_e),  grad_e U = sum_mu t_{e mu} grad psi^J_mu(r_e),
+//   lap_e U = sum_mu t_{e mu} lap psi^J_mu(r_e),  U = sum_e psi^J(r_e) . (xi + t0 - u_e) / 2.
+// A move of electron e by dphi = psi^J(r') - psi^J(r_e) changes U by dphi . t0 - psi^J(r_e) . (Xi dphi).
+#pragma once
+#include "vmcf_device.cuh"
+
+namespace vmcf {
+
+template <typename T> __device__ __forceinline__ const T* jas_xi(const DevSys& S);
+template <> __device__ __forceinline__ const double* jas_xi<double>(const DevSys& S) { return S.jxi; }
+template <> __device__ __forceinline__ const float* jas_xi<float>(const DevSys& S) { return S.jxi_f; }
+template <typename T> __device__ __forceinline__ const T* jas_Xi(const DevSys& S);
+template <> __device__ __forceinline__ const double* jas_Xi<double>(const DevSys& S) { return S.jXi; }
+template <> __device__ __forceinline__ const float* jas_Xi<float>(const DevSys& S) { return S.jXi_f; }
+template <typename T> __device__ __forceinline__ T jas_alpha(const DevSys& S, int s, int k);
+template <> __device__ __forceinline__ double jas_alpha<double>(const DevSys& S, int s, int k) { return __ldg(S.jalpha + s * kMaxPrim + k); }
+template <> __device__ __forceinline__ float jas_alpha<float>(const DevSys& S, int s, int k) { return __ldg(S.jalpha_f + s * kMaxPrim + k); }
+template <typename T> __device__ __forceinline__ T jas_coef(const DevSys& S, int s, int k);
+template <> __device__ __forceinline__ double jas_coef<double>(const DevSys& S, int s, int k) { return __ldg(S.jcoef + s * kMaxPrim + k); }
+template <> __device__ __forceinline__ float jas_coef<float>(const DevSys& S, int s, int k) { return __ldg(S.jcoef_f + s * kMaxPrim + k); }
+
+// Index of the Hessian component (d, c) in the LEVEL-2 component layout below.
+__device__ __forceinline__ int jas_hidx(int d, int c) {
+  return d == c ? 5 + d : (d + c == 1 ? 8 : (d + c == 2 ? 9 : 10));
+}
+
+// The functions of Jastrow shell s at p, handed one by one to f(mu, v) with v[0] the value and,
+// for LEVEL >= 1, v[1..3] the gradient and v[4] the Laplacian; for LEVEL 2 also v[5..10] the
+// Hessian (xx yy zz xy xz yz) and v[11..13] the gradient of the Laplacian. Same radial sums as
+// the determinant basis: with e_k = c_k exp(-a_k r^2), R0 = sum e_k, R1 = sum -2 a_k e_k,
+// R2 = sum 4 a_k^2 e_k, lap F = sum -2 a_k e_k ((2l+3) - 2 a_k r^2), T3 = sum 4 a_k^2 e_k ((2l+5) - 2 a_k r^2).
+template <typename T, int LEVEL, typename F>
+__device__ __forceinline__ void jas_shell(const DevSys& S, int s, const EPos& p, F&& f) {
+  const int4 sh = __ldg(S.jshell + s);
+  const int l = sh.y, np = sh.z;
+  T d[3];
+  disp_nuc<T>(S, p, sh.x, d);
+  const T x = d[0], y = d[1], z = d[2];
+  const T r2 = x * x + y * y + z * z;
+  T R0 = 0, R1 = 0, R2 = 0, LF = 0, T3 = 0;
+  for (int k = 0; k < np; ++k) {
+    const T a = jas_alpha<T>(S, s, k);
+    const T xa = a * r2;
+    const T e = jas_coef<T>(S, s, k) * dexp<T>(-xa);
+    R0 += e;
+    if (LEVEL >= 1) {
+      const T m2ae = T(-2) * a * e;
+      R1 += m2ae;
+      LF += m2ae * (T(2 * l + 3) - T(2) * xa);
+      if (LEVEL >= 2) {
+        const T a4e = T(4) * a * a * e;
+        R2 += a4e;
+        T3 += a4e * (T(2 * l + 5) - T(2) * xa);
+      }
+    }
+  }
+  const T xs[3] = {x, y, z};
+  for (int m = 0; m < 2 * l + 1; ++m) {
+    T P, g[3], h[6];
+    angular<T>(l, m, x, y, z, P, g, h);
+    T v[LEVEL == 0 ? 1 : (LEVEL == 1 ? 5 : 14)];
+    v[0] = P * R0;
+    if (LEVEL >= 1) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v[1 + i] = g[i] * R0 + P * xs[i] * R1;
+      v[4] = P * LF;
+    }
+    if constexpr (LEVEL >= 2) {
+      const int hi[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const int i = hi[k][0], j = hi[k][1];
+        v[5 + k] = h[k] * R0 + (g[i] * xs[j] + g[j] * xs[i]) * R1 + P * (xs[i] * xs[j] * R2 + (i == j ? R1 : T(0)));
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[11 + k] = g[k] * LF + P * xs[k] * T3;
+    }
+    f(sh.w + m, v);
+  }
+}
+
+// y[mu] = b[mu] + sum_nu Xi_{nu mu} x[nu] for the group's functions mu (b may be NULL); consecutive
+// threads read consecutive entries of a row of Xi (Xi is symmetric).
+template <typename T, int GS>
+__device__ __forceinline__ void jas_matvec(const DevSys& S, const T* x, const T* b, T* y) {
+  const int t = threadIdx.x % GS, MJ = S.MJ;
+  const T* Xi = jas_Xi<T>(S);
+  for (int mu = t; mu < MJ; mu += GS) {
+    T v = b ? __ldg(b + mu) : T(0);
+    for (int nu = 0; nu < MJ; ++nu) v += __ldg(Xi + (size_t)nu * MJ + mu) * x[nu];
+    y[mu] = v;
+  }
+}
+
+// t0 = xi + Xi s with s = sum_e psi^J(r_e) for the walker at pos (every thread of the group
+// calls it). s: [MJ] scratch; a thread sums the functions of its shells over all electrons.
+template <typename T, int GS>
+__device__ void jas_refresh_t0(const DevSys& S, const double* pos, T* s, T* t0) {
+  const int t = threadIdx.x % GS;
+  for (int sh = t; sh < S.nJs; sh += GS) {
+    const int4 d = __ldg(S.jshell + sh);
+    for (int m = 0; m < 2 * d.y + 1; ++m) s[d.w + m] = T(0);
+    for (int e = 0; e < S.Ne; ++e)
+      jas_shell<T, 0>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) { s[mu] += v[0]; });
+  }
+  gsync<GS>();
+  jas_matvec<T, GS>(S, s, jas_xi<T>(S), t0);
+  gsync<GS>();
+}
+
+}  // namespace vmcf

@@ -1,6 +1,5 @@
 // Mixed-mode (FP32 arithmetic, FP64 inversion and sums) instantiations of the hot-path kernels.
 #include "kernels.cuh"
-#include "kernels_small.cuh"
 
 namespace vmcf {
 template <>
@@ -19,19 +18,5 @@ cudaError_t launch_measure<float>(const DevSys& S, const Launch& lc, const MeasP
 template <>
 cudaError_t set_smem_limits<float>(int) {
   return set_smem_limits_impl<float>();
-}
-template <>
-cudaError_t launch_move_small<float>(const DevSys& S, int nm, int lpw, int W, size_t smem,
-                                   const SmallMoveParams& P, cudaStream_t st) {
-  return launch_move_small_impl<float>(S, nm, lpw, W, smem, P, st);
-}
-template <>
-cudaError_t launch_measure_small<float>(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
-                                      const SmallMeasParams& P, cudaStream_t st) {
-  return launch_measure_small_impl<float>(S, nm, L, grid, warps, P, st);
-}
-template <>
-cudaError_t set_smem_limits_small<float>() {
-  return set_smem_limits_small_impl<float>();
 }
 }  // namespace vmcf

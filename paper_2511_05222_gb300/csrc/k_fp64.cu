@@ -2,7 +2,6 @@
 #include <algorithm>
 
 #include "kernels.cuh"
-#include "kernels_small.cuh"
 
 namespace vmcf {
 template <>
@@ -21,27 +20,5 @@ cudaError_t launch_measure<double>(const DevSys& S, const Launch& lc, const Meas
 template <>
 cudaError_t set_smem_limits<double>(int) {
   return set_smem_limits_impl<double>();
-}
-template <>
-cudaError_t launch_move_small<double>(const DevSys& S, int nm, int lpw, int W, size_t smem,
-                                   const SmallMoveParams& P, cudaStream_t st) {
-  return launch_move_small_impl<double>(S, nm, lpw, W, smem, P, st);
-}
-template <>
-cudaError_t launch_measure_small<double>(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
-                                      const SmallMeasParams& P, cudaStream_t st) {
-  return launch_measure_small_impl<double>(S, nm, L, grid, warps, P, st);
-}
-template <>
-cudaError_t set_smem_limits_small<double>() {
-  return set_smem_limits_small_impl<double>();
-}
-cudaError_t launch_to_interleaved(const double* src, double* dst, float2* dstf, int W, int n3, cudaStream_t st) {
-  to_interleaved<<<std::min(4096, (int)(((long long)W * n3 + 255) / 256)), 256, 0, st>>>(src, dst, dstf, W, n3);
-  return cudaGetLastError();
-}
-cudaError_t launch_from_interleaved(const double* src, double* dst, int W, int n3, cudaStream_t st) {
-  from_interleaved<<<std::min(4096, (int)(((long long)W * n3 + 255) / 256)), 256, 0, st>>>(src, dst, W, n3);
-  return cudaGetLastError();
 }
 }  // namespace vmcf

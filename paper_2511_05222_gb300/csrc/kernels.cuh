@@ -8,6 +8,7 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include "jastrow_basis.cuh"
 #include "vmcf_device.cuh"
 #include "vmcf_internal.h"
 
@@ -114,6 +115,15 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
   for (int i = t; i < S.nB; i += GS) B[i] = Bg[i];
   if (t == 0) *flag = 0;
   gsync<GS>();
+  // AO-expanded Jastrow terms: t0 = xi + Xi s, the Jastrow-basis values at r' and r_e, and
+  // y = Xi (psi^J(r') - psi^J(r_e)); t0 is rebuilt here and at every re-inversion, and moves by y
+  // on acceptance
+  const int MJ = S.MJ;
+  T* jt0 = MJ ? sm_ptr<T>(base, L.jw) : nullptr;
+  T* jpn = jt0 + MJ;
+  T* jpo = jpn + MJ;
+  T* jy = jpo + MJ;
+  if (MJ) jas_refresh_t0<T, GS>(S, pos, jy, jt0);
   const uint64_t wid = P.wid0 + (uint64_t)w;
   // staggered re-inversions: this walker counts from c0 + (wid mod kref), so that the walkers of an
   // SM re-invert at different moves and the FP64 work overlaps the FP32 moves of the others
@@ -138,6 +148,10 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
       const EPos pn = make_epos(rn);
       const EPos po = make_epos(pos + 3 * e);
       ao_point<T, GS, 0, false>(S, pn, ao, 0);
+      for (int sh = t; sh < S.nJs; sh += GS) {
+        jas_shell<T, 0>(S, sh, pn, [&](int mu, const T* v) { jpn[mu] = v[0]; });
+        jas_shell<T, 0>(S, sh, po, [&](int mu, const T* v) { jpo[mu] = v[0]; });
+      }
       gsync<GS>();
       double part[1] = {0.0};  // determinant ratio (FP64)
       T dJ = T(0);              // Jastrow exponent difference
@@ -198,6 +212,15 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
                 pade_value<T>(mz, b, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]));
         }
       }
+      if (MJ) {  // AO-expanded terms: dphi . t0 - psi^J(r_e) . (Xi dphi), dphi = psi^J(r') - psi^J(r_e)
+        const T* Xi = jas_Xi<T>(S);
+        for (int mu = t; mu < MJ; mu += GS) {
+          T y = T(0);
+          for (int nu = 0; nu < MJ; ++nu) y += __ldg(Xi + (size_t)nu * MJ + mu) * (jpn[nu] - jpo[nu]);
+          jy[mu] = y;
+          dJ += (jpn[mu] - jpo[mu]) * jt0[mu] - jpo[mu] * y;
+        }
+      }
       gsync<GS>();
       group_sum_dt<GS>(part[0], dJ, red);
       const double R = part[0];
@@ -253,6 +276,7 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
           ph[3 * e + t] = pn.h[t];
           pl[3 * e + t] = pn.l[t];
         }
+        for (int mu = t; mu < MJ; mu += GS) jt0[mu] += jy[mu];  // s moves by dphi
         ++nacc;
         gsync<GS>();
       }
@@ -262,6 +286,7 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
           refresh_walker<T, GS>(S, pos, B, A, ao, L.ao_rows, piv, f, flag);
           ++nref;
           if (guide) Sg = inverse_frob2<T, GS>(S, B, red);
+          if (MJ) jas_refresh_t0<T, GS>(S, pos, jy, jt0);
         }
         c = 0;
       }
@@ -373,6 +398,54 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
     Jl[e] = jl;
   }
   gsync<GS>();
+
+  // AO-expanded Jastrow terms (Eqs. onebody_J_inhom, threebody_jas). Work space (free from here to
+  // pass 1 and after pass 3): t0 = xi + Xi s, s (later sum_e w_e), P, the per-function force shares
+  // [6][MJ], and the products with Xi of jch electrons at a time (inputs and outputs [2 jch][MJ] each).
+  const int MJ = S.MJ, jch = L.jch;
+  T* jt0 = MJ ? sm_ptr<T>(base, L.jw) : nullptr;
+  T* js = jt0 + MJ;
+  T* jP = js + MJ;
+  T* jfa = jP + MJ;
+  T* jin = jfa + 6 * MJ;
+  T* jout = jin + 2 * jch * MJ;
+  if (MJ) {
+    jas_refresh_t0<T, GS>(S, pos, js, jt0);
+    const T* xi = jas_xi<T>(S);
+    // with u_e = Xi psi^J(r_e) and t_e = t0 - u_e: grad_e J += sum_mu t_e grad psi^J, lap_e J +=
+    // sum_mu t_e lap psi^J, J += sum_e psi^J(r_e) . (xi + t_e) / 2
+    for (int c0 = 0; c0 < Ne; c0 += jch) {
+      const int nc = Ne - c0 < jch ? Ne - c0 : jch;
+      for (int q = t; q < nc * S.nJs; q += GS) {
+        const int r = q / S.nJs, sh = q - r * S.nJs;
+        jas_shell<T, 0>(S, sh, make_epos(pos + 3 * (c0 + r)), [&](int mu, const T* v) { jin[r * MJ + mu] = v[0]; });
+      }
+      gsync<GS>();
+      orbital_block<T, GS>(jin, nc, jas_Xi<T>(S), MJ, MJ, jout, MJ);
+      gsync<GS>();
+      for (int r = 0; r < nc; ++r) {
+        const int e = c0 + r;
+        T a[4] = {T(0), T(0), T(0), T(0)};
+        for (int sh = t; sh < S.nJs; sh += GS)
+          jas_shell<T, 1>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) {
+            const T te = jt0[mu] - jout[r * MJ + mu];
+            a[0] += v[1] * te;
+            a[1] += v[2] * te;
+            a[2] += v[3] * te;
+            a[3] += v[4] * te;
+            vs[2] += 0.5 * (double)(v[0] * (__ldg(xi + mu) + te));
+          });
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = warp_sum(a[k]);
+        if ((t & 31) == 0) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) atomicAdd(&Jg[3 * e + k], a[k]);
+          atomicAdd(&Jl[e], a[3]);
+        }
+      }
+      gsync<GS>();
+    }
+  }
   group_sum<GS, 3>(vs, red);
 
   // Pass 1: Slater matrices (T) and their FP64 inverses. In FP64 mode Bt is Bd (both spin
@@ -625,6 +698,80 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       }
     }
     gsync<GS>();
+  }
+
+  // AO-expanded Jastrow terms: their shares of d ln Psi/dR, dE_L/dR and dE_L/dr_e. With
+  // h_e = grad ln D + grad J at r_e, w_e = h_e . grad psi^J(r_e) + lap psi^J(r_e) / 2, p_e = Xi w_e and
+  // P = sum_e p_e, function mu of nucleus a at electron e contributes -d_d psi^J_mu t_{e mu} to
+  // d ln Psi/dR_{a,d}, and c = (h_e . d_d grad psi^J_mu + d_d lap psi^J_mu / 2) t_{e mu} +
+  // (P - p_e)_mu d_d psi^J_mu to dE_L/dR_{a,d} and -c to dE_L/dr_{e,d}.
+  if (MJ) {
+    const int nJs = S.nJs;
+    jas_refresh_t0<T, GS>(S, pos, js, jt0);  // the work space may share the O buffer of pass 3
+    for (int i = t; i < 6 * MJ; i += GS) jfa[i] = T(0);
+    for (int sh = t; sh < nJs; sh += GS) {
+      const int4 d4 = __ldg(S.jshell + sh);
+      for (int m = 0; m < 2 * d4.y + 1; ++m) js[d4.w + m] = T(0);
+      for (int e = 0; e < Ne; ++e) {
+        const T h0 = gd[3 * e] + Jg[3 * e], h1 = gd[3 * e + 1] + Jg[3 * e + 1], h2 = gd[3 * e + 2] + Jg[3 * e + 2];
+        jas_shell<T, 1>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) {
+          js[mu] += h0 * v[1] + h1 * v[2] + h2 * v[3] + T(0.5) * v[4];
+        });
+      }
+    }
+    gsync<GS>();
+    jas_matvec<T, GS>(S, js, nullptr, jP);
+    gsync<GS>();
+    for (int c0 = 0; c0 < Ne; c0 += jch) {
+      const int nc = Ne - c0 < jch ? Ne - c0 : jch;
+      for (int q = t; q < nc * nJs; q += GS) {  // rows: psi^J at the chunk's electrons, then their w_e
+        const int r = q / nJs, sh = q - r * nJs, e = c0 + r;
+        const T h0 = gd[3 * e] + Jg[3 * e], h1 = gd[3 * e + 1] + Jg[3 * e + 1], h2 = gd[3 * e + 2] + Jg[3 * e + 2];
+        jas_shell<T, 1>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) {
+          jin[r * MJ + mu] = v[0];
+          jin[(nc + r) * MJ + mu] = h0 * v[1] + h1 * v[2] + h2 * v[3] + T(0.5) * v[4];
+        });
+      }
+      gsync<GS>();
+      orbital_block<T, GS>(jin, 2 * nc, jas_Xi<T>(S), MJ, MJ, jout, MJ);  // u_e, then p_e
+      gsync<GS>();
+      for (int r = 0; r < nc; ++r) {
+        const int e = c0 + r;
+        const T h[3] = {gd[3 * e] + Jg[3 * e], gd[3 * e + 1] + Jg[3 * e + 1], gd[3 * e + 2] + Jg[3 * e + 2]};
+        T ce[3] = {T(0), T(0), T(0)};
+        for (int sh = t; sh < nJs; sh += GS)
+          jas_shell<T, 2>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) {
+            const T te = jt0[mu] - jout[r * MJ + mu];
+            const T pd = jP[mu] - jout[(nc + r) * MJ + mu];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+              T hh = T(0);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) hh += h[c] * v[jas_hidx(d, c)];
+              const T cd = (hh + T(0.5) * v[11 + d]) * te + pd * v[1 + d];
+              jfa[d * MJ + mu] -= v[1 + d] * te;
+              jfa[(3 + d) * MJ + mu] += cd;
+              ce[d] += cd;
+            }
+          });
+        if (warp) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) ce[k] = warp_sum(ce[k]);
+          if ((t & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) atomicAdd(&er[3 * e + k], ce[k]);
+        }
+      }
+      gsync<GS>();
+    }
+    for (int mu = t; mu < MJ; mu += GS) {
+      const int I = __ldg(S.jcenter + mu);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        atomicAdd(&frc[3 * I + d], jfa[d * MJ + mu]);
+        atomicAdd(&frc[3 * K + 3 * I + d], jfa[(3 + d) * MJ + mu]);
+      }
+    }
   }
 
   // the AO shares of the nuclear derivatives, onto their centres

@@ -75,6 +75,55 @@ double same_centre_overlap(double a, double b, int l) {
   return radial_norm(a, l) * radial_norm(b, l) * std::tgamma(l + 1.5) / (2.0 * std::pow(a + b, l + 1.5));
 }
 
+// Device tables of a basis (determinant or Jastrow): per shell (centre, l, nprim, first function),
+// exponents and normalised contraction coefficients ([nshell][kMaxPrim]), the sharp-primitive
+// masks, and the centre of every function. False (with the reason) on a bad shell.
+bool shell_tables(const vmcf_basis& bas, int K, std::vector<int4>& shells, std::vector<int>& sharp,
+                  std::vector<double>& alpha, std::vector<double>& coef, std::vector<int>& center, int* nfun,
+                  std::string* why) {
+  shells.assign(bas.nshell, make_int4(0, 0, 0, 0));
+  sharp.assign(bas.nshell, 0);
+  alpha.assign((size_t)bas.nshell * kMaxPrim, 0.0);
+  coef.assign((size_t)bas.nshell * kMaxPrim, 0.0);
+  center.clear();
+  int M = 0;
+  for (int sh = 0; sh < bas.nshell; ++sh) {
+    const int c = bas.center[sh], l = bas.l[sh], np = bas.nprim[sh];
+    if (c < 0 || c >= K || l < 0 || l > 2 || np < 1 || np > bas.maxprim) {
+      *why = "bad shell (centre, l in 0..2, nprim)";
+      return false;
+    }
+    double d[kMaxPrim], a[kMaxPrim];
+    for (int k = 0; k < np; ++k) {
+      a[k] = bas.exps[sh * bas.maxprim + k];
+      d[k] = bas.coefs[sh * bas.maxprim + k];
+      if (!(a[k] > 0.0) || !std::isfinite(a[k]) || !std::isfinite(d[k])) {
+        *why = "exponents must be positive and finite";
+        return false;
+      }
+    }
+    double norm2 = 0.0;
+    for (int p = 0; p < np; ++p)
+      for (int q = 0; q < np; ++q) norm2 += d[p] * d[q] * same_centre_overlap(a[p], a[q], l);
+    if (!(norm2 > 0.0)) {
+      *why = "contraction has zero norm";
+      return false;
+    }
+    for (int k = 0; k < np; ++k) {
+      // In mixed mode a primitive this sharp has a r^2 and its Laplacian factors formed in
+      // double: the float rounding of a r^2 times a would dominate the local energy error.
+      if (a[k] > kSharpAlpha) sharp[sh] |= 1 << k;
+      alpha[sh * kMaxPrim + k] = a[k];
+      coef[sh * kMaxPrim + k] = d[k] * radial_norm(a[k], l) / std::sqrt(norm2);
+    }
+    shells[sh] = make_int4(c, l, np, M);
+    for (int m = 0; m < 2 * l + 1; ++m) center.push_back(c);
+    M += 2 * l + 1;
+  }
+  *nfun = M;
+  return true;
+}
+
 template <typename T>
 size_t tsize() { return sizeof(T); }
 
@@ -97,6 +146,9 @@ GroupLayout layout_refresh_move(const vmcf_system_s& s, size_t tsz, int GS) {
   L.f = take(8 * (3 * s.nmax + 1));
   L.red = take(8 * 4 * std::max(1, GS / 32));
   L.scal = take(32);
+  // AO-expanded Jastrow terms: t0 = xi + Xi s, the proposed and current Jastrow-basis values and
+  // Xi (psi^J(r') - psi^J(r_e)) (the sum s while t0 is rebuilt)
+  L.jw = s.MJ > 0 ? take((int)tsz * 4 * s.MJ) : 0;
   L.bytes = align16(o);
   return L;
 }
@@ -134,6 +186,13 @@ GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool with
   L.ew = tsz == 4 ? L.f : take((int)tsz * 3 * s.Ne);
   L.red = take(8 * (32 + 4 * L.p2_chunk));  // group-sum scratch (<= 32 doubles), then per-electron sums
   L.scal = take(32);
+  // AO-expanded Jastrow terms: t0, s (then sum_e w_e), P = Xi sum_e w_e, the per-function shares of
+  // the nuclear derivatives [6][MJ], and the products with Xi of jch electrons at a time: inputs
+  // [2 jch][MJ] and outputs [2 jch][MJ]. The work runs before the first and after the last use of
+  // the per-walker O buffer, so it shares that buffer when it fits there.
+  L.jch = tsz == 8 ? 2 : 4;
+  const int jneed = (int)tsz * (9 + 4 * L.jch) * s.MJ;
+  L.jw = s.MJ == 0 ? 0 : (tc_rows == 0 && jneed <= (int)tsz * s.M * s.nmax ? L.Ow : take(jneed));
   L.bytes = align16(o);
   return L;
 }
@@ -187,7 +246,7 @@ int plan(vmcf_system_s& s) {
 // register row, and the shared-memory plan fits.
 void plan_small(vmcf_system_s& s) {
   s.small = false;
-  if (s.Ne > 32 || s.nmax > 16) return;
+  if (s.Ne > 32 || s.nmax > 16 || s.MJ > 0) return;  // the AO-expanded Jastrow terms run on walker groups
   const int tsz = s.precision == VMCF_FP64 ? 8 : 4;
   s.small_nm = s.nmax <= 8 ? 8 : 16;
   SmallLayout L{};
@@ -525,47 +584,58 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   s->Z.resize(s->K);
   for (int I = 0; I < s->K; ++I) s->Z[I] = nuc->Z[I];
 
-  std::vector<int4> shells(s->nshell);
-  std::vector<int> sharp(s->nshell, 0);
-  std::vector<double> alpha(s->nshell * kMaxPrim, 0.0), coef(s->nshell * kMaxPrim, 0.0);
+  std::vector<int4> shells;
+  std::vector<int> sharp;
+  std::vector<double> alpha, coef;
   int M = 0;
-  for (int sh = 0; sh < s->nshell; ++sh) {
-    const int c = bas->center[sh], l = bas->l[sh], np = bas->nprim[sh];
-    if (c < 0 || c >= s->K || l < 0 || l > 2 || np < 1 || np > bas->maxprim) {
-      delete s;
-      return fail(VMCF_EINVAL, "bad shell (centre, l in 0..2, nprim)");
-    }
-    double d[kMaxPrim], a[kMaxPrim];
-    for (int k = 0; k < np; ++k) {
-      a[k] = bas->exps[sh * bas->maxprim + k];
-      d[k] = bas->coefs[sh * bas->maxprim + k];
-      if (!(a[k] > 0.0) || !std::isfinite(a[k]) || !std::isfinite(d[k])) {
-        delete s;
-        return fail(VMCF_EINVAL, "exponents must be positive and finite");
-      }
-    }
-    double norm2 = 0.0;
-    for (int p = 0; p < np; ++p)
-      for (int q = 0; q < np; ++q) norm2 += d[p] * d[q] * same_centre_overlap(a[p], a[q], l);
-    if (!(norm2 > 0.0)) {
-      delete s;
-      return fail(VMCF_EINVAL, "contraction has zero norm");
-    }
-    for (int k = 0; k < np; ++k) {
-      // In mixed mode a primitive this sharp has a r^2 and its Laplacian factors formed in
-      // double: the float rounding of a r^2 times a would dominate the local energy error.
-      if (a[k] > kSharpAlpha) sharp[sh] |= 1 << k;
-      alpha[sh * kMaxPrim + k] = a[k];
-      coef[sh * kMaxPrim + k] = d[k] * radial_norm(a[k], l) / std::sqrt(norm2);
-    }
-    shells[sh] = make_int4(c, l, np, M);
-    for (int m = 0; m < 2 * l + 1; ++m) s->ao_center.push_back(c);
-    M += 2 * l + 1;
+  std::string why;
+  if (!shell_tables(*bas, s->K, shells, sharp, alpha, coef, s->ao_center, &M, &why)) {
+    delete s;
+    return fail(VMCF_EINVAL, why);
   }
   s->M = M;
   if (M > 1024) {
     delete s;
     return fail(VMCF_ENOTSUP, "more than 1024 AOs");
+  }
+  // AO-expanded Jastrow terms: the Jastrow basis and its coefficients
+  std::vector<int4> jshells;
+  std::vector<int> jsharp, jcenter;
+  std::vector<double> jalpha, jcoef, jxi, jXi;
+  if (jas->basis) {
+    const vmcf_basis* jb = jas->basis;
+    if (jb->nshell < 1 || jb->maxprim < 1 || jb->maxprim > kMaxPrim || !jb->center || !jb->l || !jb->nprim ||
+        !jb->exps || !jb->coefs) {
+      delete s;
+      return fail(VMCF_EINVAL, "bad Jastrow basis description");
+    }
+    int MJ = 0;
+    if (!shell_tables(*jb, s->K, jshells, jsharp, jalpha, jcoef, jcenter, &MJ, &why)) {
+      delete s;
+      return fail(VMCF_EINVAL, "Jastrow basis: " + why);
+    }
+    if (MJ > 1024) {
+      delete s;
+      return fail(VMCF_ENOTSUP, "more than 1024 Jastrow basis functions");
+    }
+    jxi.assign(MJ, 0.0);
+    jXi.assign((size_t)MJ * MJ, 0.0);
+    if (jas->xi) jxi.assign(jas->xi, jas->xi + MJ);
+    if (jas->Xi) jXi.assign(jas->Xi, jas->Xi + (size_t)MJ * MJ);
+    if (!finite_all(jxi.data(), jxi.size()) || !finite_all(jXi.data(), jXi.size())) {
+      delete s;
+      return fail(VMCF_EINVAL, "Jastrow coefficients not finite");
+    }
+    double big = 0.0;
+    for (double v : jXi) big = std::max(big, std::fabs(v));
+    for (int a = 0; a < MJ; ++a)
+      for (int b = a + 1; b < MJ; ++b)
+        if (std::fabs(jXi[(size_t)a * MJ + b] - jXi[(size_t)b * MJ + a]) > 1e-12 * std::max(1.0, big)) {
+          delete s;
+          return fail(VMCF_EINVAL, "Xi must be symmetric");
+        }
+    s->MJ = MJ;
+    s->nJs = jb->nshell;
   }
   s->C[0].assign(C_up, C_up + (size_t)M * n_up);
   if (n_dn > 0) s->C[1].assign(C_dn, C_dn + (size_t)M * n_dn);
@@ -634,6 +704,13 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
                oRh = slot(4 * Rh.size()), oRl = slot(4 * Rl.size()), oSharp = slot(4 * sharp.size()),
                oAlo = slot(4 * alpha_lo.size()), oCT0 = slot(8 * CT[0].size()), oCT1 = slot(8 * CT[1].size()),
                oCfT0 = slot(4 * CfT[0].size()), oCfT1 = slot(4 * CfT[1].size());
+  // Jastrow basis tables (AO-expanded Jastrow terms), double and float copies
+  std::vector<float> jalpha_f(jalpha.begin(), jalpha.end()), jcoef_f(jcoef.begin(), jcoef.end());
+  std::vector<float> jxi_f(jxi.begin(), jxi.end()), jXi_f(jXi.begin(), jXi.end());
+  const size_t oJs = slot(sizeof(int4) * jshells.size()), oJa = slot(8 * jalpha.size()), oJc = slot(8 * jcoef.size()),
+               oJaf = slot(4 * jalpha.size()), oJcf = slot(4 * jcoef.size()), oJcen = slot(4 * jcenter.size()),
+               oJxi = slot(8 * jxi.size()), oJxif = slot(4 * jxi.size()), oJXi = slot(8 * jXi.size()),
+               oJXif = slot(4 * jXi.size());
   cudaError_t e = cudaMalloc(&s->dmem, off);
   if (e != cudaSuccess) {
     delete s;
@@ -666,6 +743,16 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   ce = ce ? ce : up(oCT1, CT[1].data(), 8 * CT[1].size());
   ce = ce ? ce : up(oCfT0, CfT[0].data(), 4 * CfT[0].size());
   ce = ce ? ce : up(oCfT1, CfT[1].data(), 4 * CfT[1].size());
+  ce = ce ? ce : up(oJs, jshells.data(), sizeof(int4) * jshells.size());
+  ce = ce ? ce : up(oJa, jalpha.data(), 8 * jalpha.size());
+  ce = ce ? ce : up(oJc, jcoef.data(), 8 * jcoef.size());
+  ce = ce ? ce : up(oJaf, jalpha_f.data(), 4 * jalpha_f.size());
+  ce = ce ? ce : up(oJcf, jcoef_f.data(), 4 * jcoef_f.size());
+  ce = ce ? ce : up(oJcen, jcenter.data(), 4 * jcenter.size());
+  ce = ce ? ce : up(oJxi, jxi.data(), 8 * jxi.size());
+  ce = ce ? ce : up(oJxif, jxi_f.data(), 4 * jxi_f.size());
+  ce = ce ? ce : up(oJXi, jXi.data(), 8 * jXi.size());
+  ce = ce ? ce : up(oJXif, jXi_f.data(), 4 * jXi_f.size());
   if (ce == cudaSuccess) ce = s->precision == VMCF_FP64 ? set_smem_limits<double>(s->GS) : set_smem_limits<float>(s->GS);
   if (ce == cudaSuccess && s->small)
     ce = s->precision == VMCF_FP64 ? set_smem_limits_small<double>() : set_smem_limits_small<float>();
@@ -713,6 +800,20 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   D.j2exp = jas->two_body_exp ? 1 : 0;
   D.Vnn = Vnn;
   D.dVnn = reinterpret_cast<const double*>(b + oDv);
+  D.nJs = s->nJs;
+  D.MJ = s->MJ;
+  if (s->MJ > 0) {
+    D.jshell = reinterpret_cast<const int4*>(b + oJs);
+    D.jalpha = reinterpret_cast<const double*>(b + oJa);
+    D.jcoef = reinterpret_cast<const double*>(b + oJc);
+    D.jalpha_f = reinterpret_cast<const float*>(b + oJaf);
+    D.jcoef_f = reinterpret_cast<const float*>(b + oJcf);
+    D.jcenter = reinterpret_cast<const int*>(b + oJcen);
+    D.jxi = reinterpret_cast<const double*>(b + oJxi);
+    D.jxi_f = reinterpret_cast<const float*>(b + oJxif);
+    D.jXi = reinterpret_cast<const double*>(b + oJXi);
+    D.jXi_f = reinterpret_cast<const float*>(b + oJXif);
+  }
   s->scratch_counters = reinterpret_cast<double*>(b + oCnt);
   *out = s;
   return VMCF_OK;

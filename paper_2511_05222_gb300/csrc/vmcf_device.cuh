@@ -37,6 +37,19 @@ struct DevSys {
   int j2exp;             // two-body form: 0 Pade, 1 exponential
   double Vnn;
   const double* dVnn;    // [K][3], derivative of V_nn
+  // AO-expanded Jastrow terms over a separate Jastrow basis (nJs = MJ = 0: none):
+  // U = sum_e sum_mu xi_mu psi^J_mu(r_e) + sum_{i<j} sum_{mu,nu} Xi_{mu nu} psi^J_mu(r_i) psi^J_nu(r_j)
+  int nJs, MJ;           // Jastrow-basis shells and functions
+  const int4* jshell;    // (center, l, nprim, index of the shell's first function)
+  const double* jalpha;  // [nJs][kMaxPrim]
+  const double* jcoef;   // [nJs][kMaxPrim], normalised contraction coefficients
+  const float* jalpha_f;
+  const float* jcoef_f;
+  const int* jcenter;    // [MJ] nucleus of each function
+  const double* jxi;     // [MJ] one-body coefficients xi_mu
+  const float* jxi_f;
+  const double* jXi;     // [MJ][MJ] pair coefficients Xi_{mu nu}, symmetric
+  const float* jXi_f;
 };
 
 template <typename T> __device__ __forceinline__ const T* coefC(const DevSys& S, int s);

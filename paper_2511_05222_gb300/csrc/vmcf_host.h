@@ -12,6 +12,7 @@
 struct vmcf_system_s {
   int precision = 0;
   int K = 0, M = 0, nup = 0, ndn = 0, Ne = 0, nshell = 0, nB = 0, nmax = 0;
+  int MJ = 0, nJs = 0;  // functions and shells of the Jastrow basis (AO-expanded Jastrow terms)
   std::vector<double> R, Z, S, C[2];
   std::vector<int> ao_center;
   bool has_S = false;

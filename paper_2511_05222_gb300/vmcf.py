@@ -44,7 +44,8 @@ class _Basis(ctypes.Structure):
 class _Jastrow(ctypes.Structure):
     _fields_ = [("F_anti", ctypes.c_double), ("F_par", ctypes.c_double), ("a_anti", ctypes.c_double),
                 ("a_par", ctypes.c_double), ("b_en", ctypes.c_double), ("enable_J1", ctypes.c_int),
-                ("enable_J2", ctypes.c_int), ("two_body_exp", ctypes.c_int)]
+                ("enable_J2", ctypes.c_int), ("two_body_exp", ctypes.c_int), ("basis", ctypes.POINTER(_Basis)),
+                ("xi", _dp), ("Xi", _dp)]
 
 
 class Counters(ctypes.Structure):
@@ -149,7 +150,17 @@ class System:
         nuc = _Nuclei(sys.K, ip(h["Z"]), dp(h["R"]))
         bas = _Basis(sys.nshell, h["e"].shape[1], ip(h["c"]), ip(h["l"]), ip(h["np"]), dp(h["e"]), dp(h["co"]))
         jas = _Jastrow(j.F_anti, j.F_par, j.a_anti, j.a_par, j.b_en, int(j.enable_J1), int(j.enable_J2),
-                       int(bool(getattr(j, "two_body_exp", False))))
+                       int(bool(getattr(j, "two_body_exp", False))), None, None, None)
+        jb = getattr(j, "basis", None)
+        if jb is not None:  # AO-expanded Jastrow terms over a Jastrow basis
+            h.update(jc=_np(jb.shell_center, np.int32), jl=_np(jb.shell_l, np.int32), jn=_np(jb.shell_nprim, np.int32),
+                     je=_np(jb.shell_exp, np.float64), jco=_np(jb.shell_coef, np.float64),
+                     xi=_np(jb.xi, np.float64), Xi=_np(jb.Xi, np.float64))
+            h["jbas"] = _Basis(jb.nshell, h["je"].shape[1], ip(h["jc"]), ip(h["jl"]), ip(h["jn"]), dp(h["je"]),
+                               dp(h["jco"]))
+            jas.basis = ctypes.pointer(h["jbas"])
+            jas.xi = dp(h["xi"])
+            jas.Xi = dp(h["Xi"])
         out = _vp()
         _check(L.vmcf_init_system(ctypes.byref(nuc), ctypes.byref(bas), dp(h["Cu"]), dp(h["Cd"]), sys.n_up, sys.n_dn,
                                   ctypes.byref(jas), dp(h["S"]),

@@ -1,0 +1,180 @@
+"""AO-expanded Jastrow terms (App., Eqs. onebody_J_inhom and threebody_jas: the inhomogeneous one-body
+term and the three/four-body pair term over a separate Jastrow basis) on the GPU against the oracle:
+per-walker outputs in FP64 (1e-10 normwise), space-warp vectors, FP64 chains and estimators following
+the oracle's chain, mixed-precision local energies (1e-5), and ragged batches."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import estimators
+from paper_2511_05222_gb300 import systems as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2511_05222_gb300 import vmcf  # noqa: E402
+
+TOL64 = 1e-10
+ALL = ("EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O", "dEL_dC")
+NO_DC = ("EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O")
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def gpu_eval(system, pos, want):
+    out = vmcf.vmcf_evaluate(system, dev(pos), want=want)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def with_jb(cfg, seed=3, scale=1.0):
+    """Workload cfg with a seeded medium Jastrow basis (coefficients scale x the defaults)."""
+    sx = S.make_system(cfg)
+    return S.with_jastrow_basis(sx, S.jastrow_basis(sx, seed, 0.1 * scale, 0.03 * scale, 0.01 * scale))
+
+
+@pytest.fixture(scope="module")
+def water_jb():
+    return with_jb(0, scale=3.0)
+
+
+@pytest.fixture(scope="module")
+def c2oh6_jb():
+    return with_jb(1)
+
+
+@pytest.mark.parametrize("W", [1, 37])
+def test_evaluate_fp64_water(water_jb, W):
+    pos = S.initial_walkers(water_jb, W, seed=5)
+    ref = oracle.Oracle(water_jb).eval(pos, want=ALL)
+    g = vmcf.System(water_jb, vmcf.FP64)
+    for want in (NO_DC, ALL):
+        got = gpu_eval(g, pos, want)
+        for k in want:
+            assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
+
+
+def test_evaluate_fp64_c2oh6(c2oh6_jb):
+    pos = S.initial_walkers(c2oh6_jb, 24, seed=6)
+    ref = oracle.Oracle(c2oh6_jb).eval(pos, want=ALL)
+    got = gpu_eval(vmcf.System(c2oh6_jb, vmcf.FP64), pos, ALL)
+    for k in ALL:
+        assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
+
+
+@pytest.mark.parametrize("group", [0, 32, 256])
+def test_evaluate_fp64_c9o4h8(group):
+    """94 electrons, 243 Jastrow-basis functions: more functions than threads per walker group
+    for 32- and 128-thread groups."""
+    sx = with_jb(4)
+    pos = S.initial_walkers(sx, 3, seed=7)
+    ref = oracle.Oracle(sx).eval(pos, want=NO_DC)
+    g = vmcf.System(sx, vmcf.FP64)
+    if group:
+        g.set_tuning("measure_group_size", group)
+    got = gpu_eval(g, pos, NO_DC)
+    for k in NO_DC:
+        assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_warp_vectors_fp64(cfg, water_jb, c2oh6_jb):
+    sx = water_jb if cfg == 0 else c2oh6_jb
+    pos = S.initial_walkers(sx, 17, seed=21)
+    ref = oracle.Oracle(sx).eval_warp(pos)
+    got = vmcf.vmcf_evaluate_warp(vmcf.System(sx, vmcf.FP64), dev(pos))
+    torch.cuda.synchronize()
+    for k in ("dEL_dr", "dEL_sw", "dlnpsi_sw"):
+        assert rel(got[k].cpu().numpy(), ref[k]) < TOL64, (k, rel(got[k].cpu().numpy(), ref[k]))
+
+
+@pytest.mark.parametrize("kref", [26, 7])
+def test_fp64_chain_and_estimators_follow_the_oracle(water_jb, kref):
+    W, nb, warm, meas, e_ref = 128, 8, 3, 2, -76.0
+    pos = S.initial_walkers(water_jb, W, seed=9)
+    o = oracle.Oracle(water_jb)
+    st = o.new_state(pos, key=(5222, 0))
+    o.sample(st, warm, refresh_k=kref)
+    g = vmcf.System(water_jb, vmcf.FP64)
+    wk = vmcf.Walkers(g, pos, key=(5222, 0), nblocks=nb)
+    wk.sample(warm, 0.3, kref, measure=False)
+    ok = st["margin"] >= 1e-9
+    assert ok.sum() >= W - 2
+    assert np.abs(wk.positions()[ok] - st["pos"][ok]).max() < 1e-9
+    wk.reset_accumulators(e_ref)
+    wk.sample(meas, 0.3, kref, measure=True)
+    sums = estimators.new_sums(nb, water_jb.K, o.nO)
+    blk = np.arange(W) * nb // W
+    for _ in range(meas):
+        o.sample(st, 1, refresh_k=kref)
+        o.force_refresh(st)
+        out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+        estimators.accumulate(sums, blk, out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], e_ref)
+    ok = st["margin"] >= 1e-9
+    assert np.abs(wk.positions()[ok] - st["pos"][ok]).max() < 1e-9
+    if ok.all():
+        ref = estimators.finish(sums, e_ref)
+        got = wk.reduce_estimators()
+        assert abs(got["E"] - ref["E"]) < 1e-10 * abs(ref["E"])
+        assert rel(got["F"].ravel(), ref["F"]) < 1e-9
+        assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
+
+
+def test_mixed_local_energy(c2oh6_jb):
+    """Mixed precision on walkers drawn from |Psi|^2 (20 oracle sweeps): per-walker E_L within 1e-5 of
+    max(|E_L|, |mean E_L|) for nearly every walker, median 1e-6."""
+    o = oracle.Oracle(c2oh6_jb)
+    st = o.new_state(S.initial_walkers(c2oh6_jb, 128, seed=8), key=(5222, 8))
+    o.sample(st, 20)
+    pos = st["pos"]
+    ref = o.eval(pos, want=("EL",))["EL"]
+    got = gpu_eval(vmcf.System(c2oh6_jb, vmcf.MIXED), pos, ("EL",))["EL"]
+    r = np.abs(got - ref) / np.maximum(np.abs(ref), abs(ref.mean()))
+    assert np.median(r) < 1e-6
+    assert np.mean(r < 1e-5) > 0.98, np.sort(r)[-8:]
+
+
+@pytest.mark.parametrize("precision", [vmcf.FP64, vmcf.MIXED])
+def test_batch_with_jastrow_basis_follows_the_single_path(water_jb, c2oh6_jb, precision):
+    """A ragged batch holding systems with and without the AO-expanded terms: same chains (bit for
+    bit) and walker sums (FP64 1e-12, mixed 1e-5) as each walker set sampled alone."""
+    specs = [(water_jb, 48), (c2oh6_jb, 32), (S.make_system(0), 24)]
+    systems = [vmcf.System(sx, precision, force_group=True) for sx, _ in specs]
+
+    def walkers():
+        return [vmcf.Walkers(systems[g], S.initial_walkers(sx, W, seed=30 + g), key=(5222, 400 + g), nblocks=4)
+                for g, (sx, W) in enumerate(specs)]
+    wa, wb = walkers(), walkers()
+    batch = vmcf.Batch(systems, wa)
+    batch.sample(2, measure=False)
+    for g, w in enumerate(wa):
+        w.reset_accumulators(-100.0)
+        wb[g].sample(2, measure=False)
+        wb[g].reset_accumulators(-100.0)
+    batch.sample(2, measure=True)
+    for w in wb:
+        w.sample(2, measure=True)
+    tol = 1e-12 if precision == vmcf.FP64 else 1e-5
+    for g in range(len(specs)):
+        np.testing.assert_array_equal(wa[g].positions(), wb[g].positions())
+        assert rel(wa[g].block_sums(), wb[g].block_sums()) < tol
+
+
+def test_invalid_jastrow_coefficients_are_rejected(water_jb):
+    jb = water_jb.jastrow.basis
+    bad = S.with_jastrow_basis(S.make_system(0), S.JastrowBasis(jb.shell_center, jb.shell_l, jb.shell_nprim,
+                                                                  jb.shell_exp, jb.shell_coef, jb.xi, jb.Xi + np.triu(
+                                                                      np.full_like(jb.Xi, 1e-3), 1)))
+    with pytest.raises(vmcf.VmcfError):
+        vmcf.System(bad, vmcf.FP64)
+    nan = S.with_jastrow_basis(S.make_system(0), S.JastrowBasis(jb.shell_center, jb.shell_l, jb.shell_nprim,
+                                                                  jb.shell_exp, jb.shell_coef, jb.xi * np.nan, jb.Xi))
+    with pytest.raises(vmcf.VmcfError):
+        vmcf.System(nan, vmcf.FP64)
