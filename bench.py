@@ -299,6 +299,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--jastrow-basis", action="store_true",
+                    help="add the AO-expanded Jastrow terms (seeded medium Jastrow basis) to the workload")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -320,6 +322,10 @@ def main():
     stream = torch.cuda.current_stream()
     W = args.walkers or wl["walkers"]
     sysx = S.make_system(wl["cfg"])
+    jb = None
+    if args.jastrow_basis:
+        sysx = S.with_jastrow_basis(sysx)
+        jb = sysx.jastrow.basis
     pos0 = S.initial_walkers(sysx, W, seed=rank)
     nb = 64
 
@@ -378,27 +384,32 @@ def main():
     acc = cnt["accepted"] / max(1, cnt["moves"])
     est = wk.reduce_estimators(stream=stream)
 
-    work = workmodel.per_walker_eval(sysx.K, g.M, sysx.n_up, sysx.n_dn, int(sysx.shell_nprim.sum()), acc)
+    work = workmodel.per_walker_eval(sysx.K, g.M, sysx.n_up, sysx.n_dn, int(sysx.shell_nprim.sum()), acc,
+                                     jb.MJ if jb else 0, int(jb.shell_nprim.sum()) if jb else 0)
     dom = max(("move", "measure"), key=lambda k: kt[k]["ms"])  # the tensor-core sums take ~2%
     t_launch = kt[dom]["ms"] / max(1, kt[dom]["launches"]) * 1e-3
     bound, t_roof_w = workmodel.roofline_time(work[dom], peaks)
     pipe_flops = {"fp32": work[dom]["fp32"], "fp64": work[dom]["fp64"], "sfu": work[dom]["exp"]}[bound]
     peak = {"fp32": peaks["fp32_tflops"], "fp64": peaks["fp64_tflops"], "sfu": peaks["exp_gops"] / 1e3}[bound]
     achieved = pipe_flops * W / t_launch / 1e12
-    small = sysx.Ne <= 32 and max(sysx.n_up, sysx.n_dn) <= 16  # the one-warp-per-walker kernel family
+    # the one-warp-per-walker kernel family, else walker groups (32 threads up to 24 orbitals per spin)
+    small = sysx.Ne <= 32 and max(sysx.n_up, sysx.n_dn) <= 16 and jb is None
+    wide = max(sysx.n_up, sysx.n_dn) > 24
     kname = (f"{dom}_small<float, 16>" if small else
-             {"move": "move_kernel<float, 128>", "measure": "measure_kernel<float, 256>"}[dom])
+             {"move": f"move_kernel<float, {128 if wide else 32}>",
+              "measure": f"measure_kernel<float, {256 if wide else 32}>"}[dom])
     roofline = {"bound": "alu", "pipe": bound, "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s" if bound != "sfu" else "Texp/s", "frac": achieved / peak,
                 "peak_source": "measured in this run by vmcf_probe_pipes (register-only FMA/exp kernels)",
-                "traffic": profiled_traffic() if dom == "measure" else None, "launch_ms": t_launch * 1e3,
+                "traffic": profiled_traffic() if dom == "measure" and small else None, "launch_ms": t_launch * 1e3,
                 "kernel_share": {k: kt[k]["ms"] / max(1e-9, sum(v["ms"] for v in kt.values())) for k in kt},
                 "whole_step_frac": workmodel.roofline_time(work["total"], peaks)[1] * W / (ms * 1e-3 / args.steps)}
 
     line = {"metric": METRIC, "value": value, "unit": "walker-evals/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": wl["name"], "walkers_per_gpu": W, "electrons": sysx.Ne, "aos": g.M,
+            "config": {"workload": wl["name"] + (f" + AO-expanded Jastrow ({jb.MJ} Jastrow-basis functions)" if jb else ""),
+                       "walkers_per_gpu": W, "electrons": sysx.Ne, "aos": g.M,
                        "step_sigma": 0.3, "refresh_every": 26, "precision": "mixed (FP32 + FP64 inverse/ratio/sums)",
                        "l2": "flushed (256 MB write) between timed steps"},
             "roofline": roofline, "gpu_launches": sum(v["launches"] for v in kt.values()), "clocks": clk.summary(),

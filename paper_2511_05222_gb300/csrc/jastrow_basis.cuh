@@ -83,17 +83,30 @@ __device__ __forceinline__ void jas_shell(const DevSys& S, int s, const EPos& p,
   }
 }
 
-// y[mu] = b[mu] + sum_nu Xi_{nu mu} x[nu] for the group's functions mu (b may be NULL); consecutive
-// threads read consecutive entries of a row of Xi (Xi is symmetric).
+// sum_nu Xi_{nu mu} x[nu] in order of nu; consecutive threads read consecutive entries of a row of Xi
+// (Xi is symmetric). The loads are issued eight rows ahead of their use: the rows come from L2, and
+// a product per move is latency-bound with one load in flight.
+template <typename T>
+__device__ __forceinline__ T jas_column(const T* __restrict__ Xi, int MJ, int mu, const T* x) {
+  T v = T(0);
+  int nu = 0;
+  for (; nu + 8 <= MJ; nu += 8) {
+    T a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = __ldg(Xi + (size_t)(nu + k) * MJ + mu);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v += a[k] * x[nu + k];
+  }
+  for (; nu < MJ; ++nu) v += __ldg(Xi + (size_t)nu * MJ + mu) * x[nu];
+  return v;
+}
+
+// y[mu] = b[mu] + sum_nu Xi_{nu mu} x[nu] for the group's functions mu (b may be NULL).
 template <typename T, int GS>
 __device__ __forceinline__ void jas_matvec(const DevSys& S, const T* x, const T* b, T* y) {
   const int t = threadIdx.x % GS, MJ = S.MJ;
   const T* Xi = jas_Xi<T>(S);
-  for (int mu = t; mu < MJ; mu += GS) {
-    T v = b ? __ldg(b + mu) : T(0);
-    for (int nu = 0; nu < MJ; ++nu) v += __ldg(Xi + (size_t)nu * MJ + mu) * x[nu];
-    y[mu] = v;
-  }
+  for (int mu = t; mu < MJ; mu += GS) y[mu] = (b ? __ldg(b + mu) : T(0)) + jas_column<T>(Xi, MJ, mu, x);
 }
 
 // t0 = xi + Xi s with s = sum_e psi^J(r_e) for the walker at pos (every thread of the group

@@ -213,12 +213,12 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
         }
       }
       if (MJ) {  // AO-expanded terms: dphi . t0 - psi^J(r_e) . (Xi dphi), dphi = psi^J(r') - psi^J(r_e)
-        const T* Xi = jas_Xi<T>(S);
+        for (int mu = t; mu < MJ; mu += GS) jpn[mu] -= jpo[mu];  // dphi in place of psi^J(r')
+        gsync<GS>();
         for (int mu = t; mu < MJ; mu += GS) {
-          T y = T(0);
-          for (int nu = 0; nu < MJ; ++nu) y += __ldg(Xi + (size_t)nu * MJ + mu) * (jpn[nu] - jpo[nu]);
+          const T y = jas_column<T>(jas_Xi<T>(S), MJ, mu, jpn);
+          dJ += jpn[mu] * jt0[mu] - jpo[mu] * y;
           jy[mu] = y;
-          dJ += (jpn[mu] - jpo[mu]) * jt0[mu] - jpo[mu] * y;
         }
       }
       gsync<GS>();

@@ -14,7 +14,12 @@ electron per pass) counted separately for the SFU.
 from __future__ import annotations
 
 
-def per_walker_eval(K: int, M: int, n_up: int, n_dn: int, nprim: int, acc: float = 0.5) -> dict:
+def per_walker_eval(K: int, M: int, n_up: int, n_dn: int, nprim: int, acc: float = 0.5, MJ: int = 0,
+                    nJprim: int = 0) -> dict:
+    """MJ, nJprim: functions and primitives of the Jastrow basis of the AO-expanded Jastrow terms
+    (0: none). Those add, per move, one Jastrow-basis evaluation at r' and the product Xi dphi with
+    its dot products; per evaluation, the basis with all derivatives at every electron, t0 = xi + Xi s,
+    u_e = Xi psi^J(r_e) and p_e = Xi w_e for every electron, and the force terms."""
     Ne = n_up + n_dn
     ns = [n_up] * n_up + [n_dn] * n_dn  # orbital count seen by each electron
     move = {
@@ -36,6 +41,11 @@ def per_walker_eval(K: int, M: int, n_up: int, n_dn: int, nprim: int, acc: float
                  + sum(4 * M * n for n in spins) + 18 * K),      # walker sums
         "fp64": sum(2 * n ** 3 for n in spins),                  # Gauss-Jordan inversion per spin
     }
+    if MJ:
+        move["exp"] += Ne * nJprim
+        move["fp32"] += Ne * (3 * nJprim + 3 * MJ + 2 * MJ * MJ + 4 * MJ)
+        measure["exp"] += Ne * nJprim
+        measure["fp32"] += Ne * (8 * nJprim + 40 * MJ) + 2 * MJ * MJ + 4 * Ne * MJ * MJ + Ne * 46 * MJ
     total = {k: move[k] + measure[k] for k in move}
     return {"move": move, "measure": measure, "total": total}
 
