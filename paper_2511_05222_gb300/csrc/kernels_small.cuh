@@ -393,6 +393,107 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
   for (int k = q; k < nB; k += LPW) Bg[(size_t)k * W + w] = B[k * WPC];
 }
 
+// ---------------------------------------------------------------- both spin blocks' FP64 inverses
+// The two Slater matrices of a walker inverted at once by one warp, half-warp h (lanes 16h..16h+15)
+// taking matrix h (A_h, n_h x n_h row-major, in place), with the steps of gj_inverse: partial row
+// pivoting (largest |x|, lowest row on ties, found over the half-warp), the scaled pivot row, the row
+// it displaces and column k copied, then every element updated once with the row swap folded in; the
+// row permutation is undone as column swaps at the end. The pivot sequence and every operation on an
+// element are those of gj_inverse, so the inverses are the same to the bit. piv: int[2][nmax];
+// f: double[2][3 nmax + 1]. flag is set to 1 on a zero or non-finite pivot; with want_logdet the
+// logarithm of |det A_0 det A_1| and the sign of the product are accumulated into logabs and sgn.
+static __device__ __forceinline__ void gj_inverse_pair(double* A0, int n0, double* A1, int n1, int nmax, int* piv, double* f, int* flag,
+                                double* logabs, double* sgn, bool want_logdet) {
+  const int lane = threadIdx.x & 31, h = lane >> 4, hl = lane & 15;
+  double* A = h ? A1 : A0;
+  const int n = h ? n1 : n0;
+  int* pv = piv + h * nmax;
+  double* ff = f + h * (3 * nmax + 1);
+  double* rs = ff + n + 1;      // scaled pivot row: the new row k
+  double* rk = ff + 2 * n + 1;  // old row k: the new row p
+  const int i0 = n > 0 ? hl / n : 0, j0 = n > 0 ? hl - i0 * n : 0;
+  const int di = n > 0 ? 16 / n : 0, dj = n > 0 ? 16 - di * n : 0;
+  double la = 0.0, sg = 1.0;
+  const int nk = n0 > n1 ? n0 : n1;
+  for (int k = 0; k < nk; ++k) {
+    const bool act = k < n;
+    long long best = -1;
+    int bi = k;
+    if (act)
+      for (int i = k + hl; i < n; i += 16) {
+        const long long v = __double_as_longlong(A[i * n + k]) & 0x7fffffffffffffffLL;
+        if (v > best) { best = v; bi = i; }
+      }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {  // within the half-warp
+      const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (act && hl == 0) {
+      pv[k] = bi;
+      const double p = A[bi * n + k];
+      if (!(p != 0.0) || !isfinite(p)) *flag = 1;
+      ff[n] = 1.0 / p;
+      if (want_logdet) {
+        la += log(fabs(p));
+        if (p < 0) sg = -sg;
+        if (bi != k) sg = -sg;
+      }
+    }
+    __syncwarp();
+    if (act) {
+      const int p = pv[k];
+      const double pinv = ff[n];
+      for (int j = hl; j < n; j += 16) {
+        rs[j] = (j == k ? 1.0 : A[p * n + j]) * pinv;
+        rk[j] = A[k * n + j];
+      }
+      for (int i = hl; i < n; i += 16) ff[i] = A[i * n + k];
+    }
+    __syncwarp();
+    if (act) {
+      const int p = pv[k];
+      const double fp = ff[k];
+      for (int i = i0, j = j0; i < n;) {
+        double v;
+        if (i == k) {
+          v = rs[j];
+        } else {
+          const double fi = i == p ? fp : ff[i];
+          const double aij = i == p ? rk[j] : A[i * n + j];
+          v = (j == k ? 0.0 : aij) - fi * rs[j];
+        }
+        A[i * n + j] = v;
+        i += di;
+        j += dj;
+        if (j >= n) {
+          j -= n;
+          ++i;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  for (int i = hl; i < n; i += 16)
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = pv[k];
+      if (p != k) {
+        const double a = A[i * n + k];
+        A[i * n + k] = A[i * n + p];
+        A[i * n + p] = a;
+      }
+    }
+  if (want_logdet) {
+    const double la1 = __shfl_sync(0xffffffffu, la, 16), sg1 = __shfl_sync(0xffffffffu, sg, 16);
+    if (lane == 0) {
+      *logabs += la + la1;
+      *sgn *= sg * sg1;
+    }
+  }
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------- measurement, one warp per walker
 
 
@@ -492,10 +593,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
         if (i < n) Ad[off + el * n + i] = (double)row[i];
     }
     __syncwarp();
-    for (int s2 = 0; s2 < 2; ++s2) {
-      const int ns = s2 == 0 ? nup : ndn;
-      if (ns > 0) gj_inverse<32>(Ad + (s2 == 0 ? 0 : nup * nup), ns, piv, f, flag, la, sgn, P.logpsi != nullptr);
-    }
+    gj_inverse_pair(Ad, nup, Ad + nup * nup, ndn, S.nmax, piv, f, flag, la, sgn, P.logpsi != nullptr);
     if (static_cast<void*>(Bf) != static_cast<void*>(Ad))
       for (int i = lane; i < S.nB; i += 32) Bf[i] = (T)Ad[i];
     __syncwarp();

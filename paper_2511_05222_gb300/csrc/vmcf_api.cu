@@ -260,8 +260,8 @@ void plan_small(vmcf_system_s& s) {
   L.Bf = (tsz == 8) ? L.Ad : take(tsz * s.nB);
   L.Pm = take(tsz * s.nB);
   L.Q = take(tsz * s.nmax * s.nmax);
-  L.piv = take(4 * s.nmax);
-  L.f = take(8 * (3 * s.nmax + 1));
+  L.piv = take(4 * 2 * s.nmax);           // both spin blocks are inverted at once
+  L.f = take(8 * 2 * (3 * s.nmax + 1));
   L.frc = take(tsz * 6 * s.K);
   L.phi = take(tsz * s.Ne * L.chunk);
   L.red = take(16);
