@@ -543,17 +543,7 @@ __device__ __forceinline__ void orbital_rows(const T* rows, const T* C, int M, i
     const int row = row0 + r * ng;
     a[r] = rows + (row < nrows ? row : nrows - 1) * M;
   }
-  int mu = 0;
-  for (; mu + 4 <= M; mu += 4) {  // four coefficient loads in flight (C comes from L2)
-    T c[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) c[k] = __ldg(C + (mu + k) * n + col);
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] += a[r][mu + k] * c[k];
-  }
-  for (; mu < M; ++mu) {
+  for (int mu = 0; mu < M; ++mu) {
     const T c = __ldg(C + mu * n + col);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] += a[r][mu] * c;

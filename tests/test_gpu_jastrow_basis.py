@@ -1,7 +1,8 @@
 """AO-expanded Jastrow terms (App., Eqs. onebody_J_inhom and threebody_jas: the inhomogeneous one-body
 term and the three/four-body pair term over a separate Jastrow basis) on the GPU against the oracle:
 per-walker outputs in FP64 (1e-10 normwise), space-warp vectors, FP64 chains and estimators following
-the oracle's chain, mixed-precision local energies (1e-5), and ragged batches."""
+the oracle's chain (plain, and guided with the space-warp estimator), mixed-precision local energies (1e-5)
+and estimators (within 0.1 of their error bars, paired with FP64), and ragged batches."""
 import numpy as np
 import pytest
 
@@ -178,3 +179,72 @@ def test_invalid_jastrow_coefficients_are_rejected(water_jb):
                                                                   jb.shell_exp, jb.shell_coef, jb.xi * np.nan, jb.Xi))
     with pytest.raises(vmcf.VmcfError):
         vmcf.System(nan, vmcf.FP64)
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_mixed_estimators_within_a_tenth_of_their_error_bars(cfg, water_jb, c2oh6_jb):
+    """Mixed-precision sampling with the AO-expanded terms; the FP64 path measures the same
+    configurations after every sweep (paired). E, every force component and every dE/dC element of
+    the mixed path lie within 0.1 x the FP64 path's jackknife error bar."""
+    sx = water_jb if cfg == 0 else c2oh6_jb
+    W = 4096
+    gm = vmcf.System(sx, vmcf.MIXED)
+    g64 = vmcf.System(sx, vmcf.FP64)
+    wm = vmcf.Walkers(gm, S.initial_walkers(sx, W, seed=12), key=(5222, 60 + cfg), nblocks=32)
+    wm.sample(20, measure=False)
+    w64 = vmcf.Walkers(g64, wm.positions(), key=(5222, 60 + cfg), nblocks=32)
+    e_ref = {0: -76.0, 1: -150.0}[cfg]
+    wm.reset_accumulators(e_ref)
+    w64.reset_accumulators(e_ref)
+    for _ in range(6):
+        wm.sample(1, measure=True)
+        w64.set_positions(wm.positions())
+        w64.measure()
+    em, e64 = wm.reduce_estimators(), w64.reduce_estimators()
+    assert abs(em["E"] - e64["E"]) <= 0.1 * e64["E_err"], (em["E"], e64["E"], e64["E_err"])
+    dF = np.abs(em["F"] - e64["F"]) / e64["F_err"]
+    assert dF.max() <= 0.1, dF.max()
+    ok = e64["dEdC_err"] > 0
+    dB = np.abs(em["dEdC"] - e64["dEdC"])[ok] / e64["dEdC_err"][ok]
+    assert dB.max() <= 0.1, dB.max()
+
+
+def test_guided_space_warp_chain_follows_the_oracle(water_jb):
+    """Reweighted (guided) FP64 sampling of a system with the AO-expanded terms and the space-warp
+    estimator on: the chain, the weighted plain estimators and the weighted space-warp forces as the
+    oracle's."""
+    W, nb, warm, meas, e_ref = 96, 8, 3, 2, -76.0
+    o = oracle.Oracle(water_jb)
+    st = o.new_state(S.initial_walkers(water_jb, W, seed=43), key=(5222, 0))
+    o.sample(st, 8)
+    pos = st["pos"].copy()
+    Bf = o.refresh(pos)
+    eps = 1.0 / np.sqrt(np.quantile((Bf ** 2).sum(1), 0.5))
+    st = o.new_state(pos, key=(5222, 0))
+    o.sample(st, warm, eps=eps)
+    g = vmcf.System(water_jb, vmcf.FP64, space_warp=True)
+    wk = vmcf.Walkers(g, pos, key=(5222, 0), nblocks=nb)
+    wk.set_guiding(eps)
+    wk.sample(warm, measure=False)
+    wk.reset_accumulators(e_ref)
+    wk.sample(meas, measure=True)
+    plain = estimators.new_sums(nb, water_jb.K, o.nO)
+    warp = estimators.new_sums(nb, water_jb.K, o.nO)
+    blk = np.arange(W) * nb // W
+    for _ in range(meas):
+        o.sample(st, 1, eps=eps)
+        o.force_refresh(st)
+        out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+        wv = o.eval_warp(st["pos"])
+        wt = o.guide_weight(st["pos"], eps)
+        estimators.accumulate(plain, blk, out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], e_ref, weight=wt)
+        estimators.accumulate(warp, blk, out["EL"], wv["dlnpsi_sw"], wv["dEL_sw"], out["O"], e_ref, weight=wt)
+    ok = st["margin"] >= 1e-9
+    assert np.abs(wk.positions()[ok] - st["pos"][ok]).max() < 1e-9
+    if ok.all():
+        ref, refw = estimators.finish(plain, e_ref), estimators.finish(warp, e_ref)
+        got, gotw = wk.reduce_estimators(), wk.reduce_warp()
+        assert abs(got["E"] - ref["E"]) < 1e-10 * abs(ref["E"])
+        assert rel(got["F"].ravel(), ref["F"]) < 1e-9
+        assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
+        assert rel(gotw["F"].ravel(), refw["F"]) < 1e-9
