@@ -138,11 +138,15 @@ Shape default_shape(const vmcf_batch_s& b, int phase, int bk) {
 }
 
 // Relative cost of one walker-sweep (phase 0) or evaluation (phase 1), from the operation
-// counts of the method: AO/MO rows per move and per evaluation, inversions, Jastrow pairs.
+// counts of the method: AO/MO rows per move and per evaluation, inversions, Jastrow pairs, and
+// the products with Xi of the AO-expanded Jastrow terms (one per move; three row blocks per
+// electron in an evaluation).
 double heuristic_cost(const vmcf_system_s& s, int phase) {
-  const double Ne = s.Ne, M = s.M, n = s.nmax, K = s.K;
-  if (phase == 0) return Ne * (2.0 * M * n + 4.0 * n * n + 30.0 * (Ne + K)) + (Ne / 26.0) * (Ne * M * n + 4.0 * n * n * n);
-  return Ne * (12.0 * M * n + 40.0 * M) + 4.0 * n * n * n + 60.0 * Ne * (Ne + K);
+  const double Ne = s.Ne, M = s.M, n = s.nmax, K = s.K, MJ = s.MJ;
+  if (phase == 0)
+    return Ne * (2.0 * M * n + 4.0 * n * n + 30.0 * (Ne + K) + 2.0 * MJ * MJ + 6.0 * MJ) +
+           (Ne / 26.0) * (Ne * M * n + 4.0 * n * n * n + Ne * MJ + 2.0 * MJ * MJ);
+  return Ne * (12.0 * M * n + 40.0 * M + 6.0 * MJ * MJ + 60.0 * MJ) + 4.0 * n * n * n + 60.0 * Ne * (Ne + K);
 }
 
 void fill_geo(vmcf_batch_s& b, int g) {
