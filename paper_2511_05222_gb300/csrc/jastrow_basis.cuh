@@ -6,6 +6,8 @@
 //   lap_e U = sum_mu t_{e mu} lap psi^J_mu(r_e),  U = sum_e psi^J(r_e) . (xi + t0 - u_e) / 2.
 // A move of electron e by dphi = psi^J(r') - psi^J(r_e) changes U by dphi . t0 - psi^J(r_e) . (Xi dphi).
 #pragma once
+#include <type_traits>
+
 #include "vmcf_device.cuh"
 
 namespace vmcf {
@@ -107,6 +109,95 @@ __device__ __forceinline__ void jas_matvec(const DevSys& S, const T* x, const T*
   const int t = threadIdx.x % GS, MJ = S.MJ;
   const T* Xi = jas_Xi<T>(S);
   for (int mu = t; mu < MJ; mu += GS) y[mu] = (b ? __ldg(b + mu) : T(0)) + jas_column<T>(Xi, MJ, mu, x);
+}
+
+// out[r][col] = sum_mu rows[r][mu] Xi_{mu col} for R rows row0, row0 + ng, ... of nrows rows with
+// row stride MJp (entries MJ..MJp-1 zero, as are the rows of Xi past MJ): four inputs of a row per
+// vector load, each output summed in order of mu. Rows past nrows are computed from a valid row and not
+// stored.
+template <typename T, int R>
+__device__ __forceinline__ void jas_rows(const T* rows, const T* __restrict__ Xi, int MJp, int MJ, int col, int row0,
+                                         int ng, int nrows, T* out, int out_stride) {
+  T v[R];
+  const T* a[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    v[r] = T(0);
+    const int row = row0 + r * ng;
+    a[r] = rows + (row < nrows ? row : nrows - 1) * MJp;
+  }
+  for (int mu = 0; mu < MJp; mu += 4) {
+    T c[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c[k] = __ldg(Xi + (size_t)(mu + k) * MJ + col);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T x[4];
+      if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(a[r] + mu);
+        x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+      } else {
+        const double2 q0 = *reinterpret_cast<const double2*>(a[r] + mu);
+        const double2 q1 = *reinterpret_cast<const double2*>(a[r] + mu + 2);
+        x[0] = q0.x; x[1] = q0.y; x[2] = q1.x; x[3] = q1.y;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[r] += x[k] * c[k];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int row = row0 + r * ng;
+    if (row < nrows) out[row * out_stride + col] = v[r];
+  }
+}
+
+// All MJ columns of nrows (<= 8 per thread) rows times Xi over the group, the thread mapping of
+// orbital_block: with GS >= MJ thread t owns column t % MJ and rows t / MJ + k ng (ng = GS / MJ); with
+// GS < MJ it owns columns t, t + GS, ... and every row.
+template <typename T, int GS>
+__device__ __forceinline__ void jas_block(const DevSys& S, const T* rows, int nrows, T* out, int out_stride) {
+  const int t = threadIdx.x % GS, MJ = S.MJ, MJp = S.MJp;
+  const T* Xi = jas_Xi<T>(S);
+  const bool wide = GS >= MJ;
+  const int ng = wide ? GS / MJ : 1;
+  const int col0 = wide ? t % MJ : t, rg = wide ? t / MJ : 0, dcol = wide ? MJ : GS;
+  for (int col = col0; col < MJ && rg < ng && rg < nrows; col += dcol) {
+    switch ((nrows - rg + ng - 1) / ng) {
+      case 1: jas_rows<T, 1>(rows, Xi, MJp, MJ, col, rg, ng, nrows, out, out_stride); break;
+      case 2: jas_rows<T, 2>(rows, Xi, MJp, MJ, col, rg, ng, nrows, out, out_stride); break;
+      case 3: jas_rows<T, 3>(rows, Xi, MJp, MJ, col, rg, ng, nrows, out, out_stride); break;
+      case 4: jas_rows<T, 4>(rows, Xi, MJp, MJ, col, rg, ng, nrows, out, out_stride); break;
+      case 5: jas_rows<T, 5>(rows, Xi, MJp, MJ, col, rg, ng, nrows, out, out_stride); break;
+      case 6: jas_rows<T, 6>(rows, Xi, MJp, MJ, col, rg, ng, nrows, out, out_stride); break;
+      case 7: jas_rows<T, 7>(rows, Xi, MJp, MJ, col, rg, ng, nrows, out, out_stride); break;
+      default: jas_rows<T, 8>(rows, Xi, MJp, MJ, col, rg, ng, nrows, out, out_stride); break;
+    }
+  }
+}
+
+// t0 = xi + Xi s with s = sum_e psi^J(r_e), by jng subgroups of GS / jng threads (whole warps): subgroup
+// g sums the electrons e = g, g + jng, ... into part[g][MJ], a thread covering whole shells; then the
+// parts are added in order of g. Every thread of the group calls it.
+template <typename T, int GS>
+__device__ void jas_refresh_t0_sub(const DevSys& S, const double* pos, int jng, T* part, T* s, T* t0) {
+  const int t = threadIdx.x % GS, MJ = S.MJ, gsz = GS / jng, g = t / gsz, tt = t - g * gsz;
+  T* pg = part + g * MJ;
+  for (int sh = tt; sh < S.nJs; sh += gsz) {
+    const int4 d = __ldg(S.jshell + sh);
+    for (int m = 0; m < 2 * d.y + 1; ++m) pg[d.w + m] = T(0);
+    for (int e = g; e < S.Ne; e += jng)
+      jas_shell<T, 0>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) { pg[mu] += v[0]; });
+  }
+  gsync<GS>();
+  for (int mu = t; mu < MJ; mu += GS) {
+    T v = T(0);
+    for (int k = 0; k < jng; ++k) v += part[k * MJ + mu];
+    s[mu] = v;
+  }
+  gsync<GS>();
+  jas_matvec<T, GS>(S, s, jas_xi<T>(S), t0);
+  gsync<GS>();
 }
 
 // t0 = xi + Xi s with s = sum_e psi^J(r_e) for the walker at pos (every thread of the group

@@ -400,17 +400,22 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   gsync<GS>();
 
   // AO-expanded Jastrow terms (Eqs. onebody_J_inhom, threebody_jas). Work space (free from here to
-  // pass 1 and after pass 3): t0 = xi + Xi s, s (later sum_e w_e), P, the per-function force shares
-  // [6][MJ], and the products with Xi of jch electrons at a time (inputs and outputs [2 jch][MJ] each).
-  const int MJ = S.MJ, jch = L.jch;
-  T* jt0 = MJ ? sm_ptr<T>(base, L.jw) : nullptr;
+  // pass 1 and after pass 3): inputs of the products with Xi [2 jch][MJp] (jch electrons at a time),
+  // their outputs [2 jch][MJ], t0 = xi + Xi s, s (later sum_e w_e), P, and the per-function force
+  // shares [jng][6][MJ]. The per-electron loops run in jng subgroups of whole warps, each covering
+  // every Jastrow-basis shell for its own electrons.
+  const int MJ = S.MJ, MJp = S.MJp, jch = L.jch, jng = L.jng > 0 ? L.jng : 1;
+  T* jin = MJ ? sm_ptr<T>(base, L.jw) : nullptr;
+  T* jout = jin + 2 * jch * MJp;
+  T* jt0 = jout + 2 * jch * MJ;
   T* js = jt0 + MJ;
   T* jP = js + MJ;
   T* jfa = jP + MJ;
-  T* jin = jfa + 6 * MJ;
-  T* jout = jin + 2 * jch * MJ;
+  const int jgsz = GS / jng, jg = t / jgsz, jt = t - jg * jgsz;
   if (MJ) {
-    jas_refresh_t0<T, GS>(S, pos, js, jt0);
+    jas_refresh_t0_sub<T, GS>(S, pos, jng, jin, js, jt0);  // the input rows hold the partial sums meanwhile
+    if (MJp > MJ)  // row padding of the inputs (the staging writes mu < MJ)
+      for (int q = t; q < 2 * jch * (MJp - MJ); q += GS) jin[(q / (MJp - MJ)) * MJp + MJ + q % (MJp - MJ)] = T(0);
     const T* xi = jas_xi<T>(S);
     // with u_e = Xi psi^J(r_e) and t_e = t0 - u_e: grad_e J += sum_mu t_e grad psi^J, lap_e J +=
     // sum_mu t_e lap psi^J, J += sum_e psi^J(r_e) . (xi + t_e) / 2
@@ -418,26 +423,27 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       const int nc = Ne - c0 < jch ? Ne - c0 : jch;
       for (int q = t; q < nc * S.nJs; q += GS) {
         const int r = q / S.nJs, sh = q - r * S.nJs;
-        jas_shell<T, 0>(S, sh, make_epos(pos + 3 * (c0 + r)), [&](int mu, const T* v) { jin[r * MJ + mu] = v[0]; });
+        jas_shell<T, 0>(S, sh, make_epos(pos + 3 * (c0 + r)), [&](int mu, const T* v) { jin[r * MJp + mu] = v[0]; });
       }
       gsync<GS>();
-      orbital_block<T, GS>(jin, nc, jas_Xi<T>(S), MJ, MJ, jout, MJ);
+      jas_block<T, GS>(S, jin, nc, jout, MJ);
       gsync<GS>();
-      for (int r = 0; r < nc; ++r) {
-        const int e = c0 + r;
+      for (int r0 = 0; r0 < nc; r0 += jng) {
+        const int r = r0 + jg, e = c0 + r;
         T a[4] = {T(0), T(0), T(0), T(0)};
-        for (int sh = t; sh < S.nJs; sh += GS)
-          jas_shell<T, 1>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) {
-            const T te = jt0[mu] - jout[r * MJ + mu];
-            a[0] += v[1] * te;
-            a[1] += v[2] * te;
-            a[2] += v[3] * te;
-            a[3] += v[4] * te;
-            vs[2] += 0.5 * (double)(v[0] * (__ldg(xi + mu) + te));
-          });
+        if (r < nc)
+          for (int sh = jt; sh < S.nJs; sh += jgsz)
+            jas_shell<T, 1>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) {
+              const T te = jt0[mu] - jout[r * MJ + mu];
+              a[0] += v[1] * te;
+              a[1] += v[2] * te;
+              a[2] += v[3] * te;
+              a[3] += v[4] * te;
+              vs[2] += 0.5 * (double)(v[0] * (__ldg(xi + mu) + te));
+            });
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a[k] = warp_sum(a[k]);
-        if ((t & 31) == 0) {
+        for (int k = 0; k < 4; ++k) a[k] = warp_sum(a[k]);  // a warp belongs to one subgroup
+        if ((t & 31) == 0 && r < nc) {
 #pragma unroll
           for (int k = 0; k < 3; ++k) atomicAdd(&Jg[3 * e + k], a[k]);
           atomicAdd(&Jl[e], a[3]);
@@ -707,17 +713,26 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   // (P - p_e)_mu d_d psi^J_mu to dE_L/dR_{a,d} and -c to dE_L/dr_{e,d}.
   if (MJ) {
     const int nJs = S.nJs;
-    jas_refresh_t0<T, GS>(S, pos, js, jt0);  // the work space may share the O buffer of pass 3
-    for (int i = t; i < 6 * MJ; i += GS) jfa[i] = T(0);
-    for (int sh = t; sh < nJs; sh += GS) {
+    jas_refresh_t0_sub<T, GS>(S, pos, jng, jin, js, jt0);  // the work space may share the O buffer of pass 3
+    if (MJp > MJ)
+      for (int q = t; q < 2 * jch * (MJp - MJ); q += GS) jin[(q / (MJp - MJ)) * MJp + MJ + q % (MJp - MJ)] = T(0);
+    for (int i = t; i < 6 * jng * MJ; i += GS) jfa[i] = T(0);
+    T* wpart = jout;  // sum_e w_e by subgroup (electrons e = g, g + jng, ...) before the products
+    for (int sh = jt; sh < nJs; sh += jgsz) {
       const int4 d4 = __ldg(S.jshell + sh);
-      for (int m = 0; m < 2 * d4.y + 1; ++m) js[d4.w + m] = T(0);
-      for (int e = 0; e < Ne; ++e) {
+      for (int m = 0; m < 2 * d4.y + 1; ++m) wpart[jg * MJ + d4.w + m] = T(0);
+      for (int e = jg; e < Ne; e += jng) {
         const T h0 = gd[3 * e] + Jg[3 * e], h1 = gd[3 * e + 1] + Jg[3 * e + 1], h2 = gd[3 * e + 2] + Jg[3 * e + 2];
         jas_shell<T, 1>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) {
-          js[mu] += h0 * v[1] + h1 * v[2] + h2 * v[3] + T(0.5) * v[4];
+          wpart[jg * MJ + mu] += h0 * v[1] + h1 * v[2] + h2 * v[3] + T(0.5) * v[4];
         });
       }
+    }
+    gsync<GS>();
+    for (int mu = t; mu < MJ; mu += GS) {
+      T v = T(0);
+      for (int k = 0; k < jng; ++k) v += wpart[k * MJ + mu];
+      js[mu] = v;
     }
     gsync<GS>();
     jas_matvec<T, GS>(S, js, nullptr, jP);
@@ -728,36 +743,39 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
         const int r = q / nJs, sh = q - r * nJs, e = c0 + r;
         const T h0 = gd[3 * e] + Jg[3 * e], h1 = gd[3 * e + 1] + Jg[3 * e + 1], h2 = gd[3 * e + 2] + Jg[3 * e + 2];
         jas_shell<T, 1>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) {
-          jin[r * MJ + mu] = v[0];
-          jin[(nc + r) * MJ + mu] = h0 * v[1] + h1 * v[2] + h2 * v[3] + T(0.5) * v[4];
+          jin[r * MJp + mu] = v[0];
+          jin[(nc + r) * MJp + mu] = h0 * v[1] + h1 * v[2] + h2 * v[3] + T(0.5) * v[4];
         });
       }
       gsync<GS>();
-      orbital_block<T, GS>(jin, 2 * nc, jas_Xi<T>(S), MJ, MJ, jout, MJ);  // u_e, then p_e
+      jas_block<T, GS>(S, jin, 2 * nc, jout, MJ);  // u_e, then p_e
       gsync<GS>();
-      for (int r = 0; r < nc; ++r) {
-        const int e = c0 + r;
-        const T h[3] = {gd[3 * e] + Jg[3 * e], gd[3 * e + 1] + Jg[3 * e + 1], gd[3 * e + 2] + Jg[3 * e + 2]};
+      for (int r0 = 0; r0 < nc; r0 += jng) {
+        const int r = r0 + jg, e = c0 + r;
         T ce[3] = {T(0), T(0), T(0)};
-        for (int sh = t; sh < nJs; sh += GS)
-          jas_shell<T, 2>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) {
-            const T te = jt0[mu] - jout[r * MJ + mu];
-            const T pd = jP[mu] - jout[(nc + r) * MJ + mu];
+        if (r < nc) {
+          const T h[3] = {gd[3 * e] + Jg[3 * e], gd[3 * e + 1] + Jg[3 * e + 1], gd[3 * e + 2] + Jg[3 * e + 2]};
+          T* fa_g = jfa + jg * 6 * MJ;
+          for (int sh = jt; sh < nJs; sh += jgsz)
+            jas_shell<T, 2>(S, sh, make_epos(pos + 3 * e), [&](int mu, const T* v) {
+              const T te = jt0[mu] - jout[r * MJ + mu];
+              const T pd = jP[mu] - jout[(nc + r) * MJ + mu];
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-              T hh = T(0);
+              for (int d = 0; d < 3; ++d) {
+                T hh = T(0);
 #pragma unroll
-              for (int c = 0; c < 3; ++c) hh += h[c] * v[jas_hidx(d, c)];
-              const T cd = (hh + T(0.5) * v[11 + d]) * te + pd * v[1 + d];
-              jfa[d * MJ + mu] -= v[1 + d] * te;
-              jfa[(3 + d) * MJ + mu] += cd;
-              ce[d] += cd;
-            }
-          });
+                for (int c = 0; c < 3; ++c) hh += h[c] * v[jas_hidx(d, c)];
+                const T cd = (hh + T(0.5) * v[11 + d]) * te + pd * v[1 + d];
+                fa_g[d * MJ + mu] -= v[1 + d] * te;
+                fa_g[(3 + d) * MJ + mu] += cd;
+                ce[d] += cd;
+              }
+            });
+        }
         if (warp) {
 #pragma unroll
           for (int k = 0; k < 3; ++k) ce[k] = warp_sum(ce[k]);
-          if ((t & 31) == 0)
+          if ((t & 31) == 0 && r < nc)
 #pragma unroll
             for (int k = 0; k < 3; ++k) atomicAdd(&er[3 * e + k], ce[k]);
         }
@@ -768,8 +786,13 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       const int I = __ldg(S.jcenter + mu);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        atomicAdd(&frc[3 * I + d], jfa[d * MJ + mu]);
-        atomicAdd(&frc[3 * K + 3 * I + d], jfa[(3 + d) * MJ + mu]);
+        T sl = T(0), se = T(0);
+        for (int k = 0; k < jng; ++k) {
+          sl += jfa[(k * 6 + d) * MJ + mu];
+          se += jfa[(k * 6 + 3 + d) * MJ + mu];
+        }
+        atomicAdd(&frc[3 * I + d], sl);
+        atomicAdd(&frc[3 * K + 3 * I + d], se);
       }
     }
   }

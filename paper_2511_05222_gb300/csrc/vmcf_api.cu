@@ -191,7 +191,13 @@ GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool with
   // [2 jch][MJ] and outputs [2 jch][MJ]. The work runs before the first and after the last use of
   // the per-walker O buffer, so it shares that buffer when it fits there.
   L.jch = tsz == 8 ? 2 : 4;
-  const int jneed = (int)tsz * (9 + 4 * L.jch) * s.MJ;
+  // whole-warp subgroups, each covering every Jastrow-basis shell, for different electrons
+  const int wpg = std::max(1, (s.nJs + 31) / 32), nw = std::max(1, GS / 32);
+  L.jng = 1;
+  while (L.jng < 4 && 2 * L.jng * wpg <= nw) L.jng *= 2;
+  const int MJp = (s.MJ + 3) / 4 * 4;
+  // inputs [2 jch][MJp] first (rows start on 16 bytes), outputs [2 jch][MJ], t0, s, P, shares [jng][6][MJ]
+  const int jneed = (int)tsz * (2 * L.jch * MJp + 2 * L.jch * s.MJ + 3 * s.MJ + 6 * L.jng * s.MJ);
   L.jw = s.MJ == 0 ? 0 : (tc_rows == 0 && jneed <= (int)tsz * s.M * s.nmax ? L.Ow : take(jneed));
   L.bytes = align16(o);
   return L;
@@ -622,6 +628,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
     jXi.assign((size_t)MJ * MJ, 0.0);
     if (jas->xi) jxi.assign(jas->xi, jas->xi + MJ);
     if (jas->Xi) jXi.assign(jas->Xi, jas->Xi + (size_t)MJ * MJ);
+    jXi.resize((size_t)((MJ + 3) / 4 * 4) * MJ, 0.0);  // zero rows up to a multiple of 4
     if (!finite_all(jxi.data(), jxi.size()) || !finite_all(jXi.data(), jXi.size())) {
       delete s;
       return fail(VMCF_EINVAL, "Jastrow coefficients not finite");
@@ -802,6 +809,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   D.dVnn = reinterpret_cast<const double*>(b + oDv);
   D.nJs = s->nJs;
   D.MJ = s->MJ;
+  D.MJp = (s->MJ + 3) / 4 * 4;
   if (s->MJ > 0) {
     D.jshell = reinterpret_cast<const int4*>(b + oJs);
     D.jalpha = reinterpret_cast<const double*>(b + oJa);

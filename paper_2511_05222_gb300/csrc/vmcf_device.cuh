@@ -40,6 +40,7 @@ struct DevSys {
   // AO-expanded Jastrow terms over a separate Jastrow basis (nJs = MJ = 0: none):
   // U = sum_e sum_mu xi_mu psi^J_mu(r_e) + sum_{i<j} sum_{mu,nu} Xi_{mu nu} psi^J_mu(r_i) psi^J_nu(r_j)
   int nJs, MJ;           // Jastrow-basis shells and functions
+  int MJp;               // MJ rounded up to a multiple of 4 (rows of the row-block products with Xi)
   const int4* jshell;    // (center, l, nprim, index of the shell's first function)
   const double* jalpha;  // [nJs][kMaxPrim]
   const double* jcoef;   // [nJs][kMaxPrim], normalised contraction coefficients
@@ -48,7 +49,7 @@ struct DevSys {
   const int* jcenter;    // [MJ] nucleus of each function
   const double* jxi;     // [MJ] one-body coefficients xi_mu
   const float* jxi_f;
-  const double* jXi;     // [MJ][MJ] pair coefficients Xi_{mu nu}, symmetric
+  const double* jXi;     // [MJp][MJ] pair coefficients Xi_{mu nu}, symmetric; rows MJ..MJp-1 are zero
   const float* jXi_f;
 };
 

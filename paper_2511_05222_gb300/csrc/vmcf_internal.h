@@ -15,6 +15,7 @@ struct GroupLayout {
   int p2_chunk;  // electrons per chunk of the gradient/Laplacian pass (4 AO rows each)
   int jw;        // AO-expanded Jastrow work space (systems with a Jastrow basis, else 0)
   int jch;       // electrons per chunk of the Jastrow-basis products (measurement)
+  int jng;       // subgroups of whole warps that take different electrons in the Jastrow-basis loops
   int bytes;    // size of one group's region (16-byte multiple)
 };
 
