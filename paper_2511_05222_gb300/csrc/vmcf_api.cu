@@ -154,7 +154,7 @@ GroupLayout layout_refresh_move(const vmcf_system_s& s, size_t tsz, int GS) {
 }
 
 // Shared-memory plan of one walker group for the measure kernel.
-GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows = 0) {
+GroupLayout layout_measure_p2(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows, int p2) {
   GroupLayout L{};
   int o = 0;
   auto take = [&](int bytes) { int at = o; o = align16(o + bytes); return at; };
@@ -171,8 +171,8 @@ GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool with
   L.Jl = take((int)tsz * s.Ne);
   L.gd = take((int)tsz * 3 * s.Ne);
   L.ao_rows = 8;
-  L.p2_chunk = 3;
-  L.ao = take((int)tsz * 14 * s.M);
+  L.p2_chunk = p2;  // electrons per chunk of the gradient/Laplacian pass: 4 AO rows each
+  L.ao = take((int)tsz * std::max(14, 4 * L.p2_chunk) * s.M);
   L.mo = take((int)tsz * 4 * L.p2_chunk * s.nmax);
   L.frc = take((int)tsz * 6 * s.K);
   L.fa = take((int)tsz * 6 * s.M);
@@ -201,6 +201,17 @@ GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool with
   L.jw = s.MJ == 0 ? 0 : (tc_rows == 0 && jneed <= (int)tsz * s.M * s.nmax ? L.Ow : take(jneed));
   L.bytes = align16(o);
   return L;
+}
+
+// Six electrons per chunk of the gradient/Laplacian pass (half the chunks of three, each coefficient
+// load shared by twice the rows) when that layout fits and keeps as many walker groups per SM as
+// chunks of three do; else three.
+GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows = 0) {
+  const GroupLayout L3 = layout_measure_p2(s, tsz, GS, withD, tc_rows, 3);
+  const GroupLayout L6 = layout_measure_p2(s, tsz, GS, withD, tc_rows, 6);
+  const int per_sm = 228 * 1024;
+  if (L6.bytes <= kSmemCap && per_sm / (L6.bytes + 1024) >= per_sm / (L3.bytes + 1024)) return L6;
+  return L3;
 }
 
 // Measurement-kernel plan for group size s.GSm: layouts, groups per CTA, accumulator placement.
