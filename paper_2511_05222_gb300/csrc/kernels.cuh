@@ -578,55 +578,71 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       Ps[idx] = v;
     }
     gsync<GS>();
-    for (int el = 0; el < n; ++el) {
-      const int e = e0 + el;
-      const EPos pe = make_epos(pos + 3 * e);
-      ao_point<T, GS, 2, true>(S, pe, ao, M);
+    // one or two electrons per step (L.p3_chunk): their level-2 AO rows over (electron, shell) pairs,
+    // then each AO's thread takes the electrons in order, sharing every coefficient load
+    for (int el = 0; el < n; el += L.p3_chunk) {
+      const int nr = n - el < L.p3_chunk ? n - el : L.p3_chunk;
+      for (int q = t; q < nr * S.nshell; q += GS) {
+        const int r = q / S.nshell, sh = q - r * S.nshell;
+        shell_point<T, 2, true>(S, make_epos(pos + 3 * (e0 + el + r)), sh, ao + r * 14 * M, M);
+      }
       gsync<GS>();
-      const T j0 = Jg[3 * e], j1 = Jg[3 * e + 1], j2 = Jg[3 * e + 2];
-      T ce[3] = {T(0), T(0), T(0)};  // this thread's share of sum_mu of the AO terms of electron e
+      T ce[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};  // this thread's share of sum_mu of the AO terms
       for (int mu = t; mu < M; mu += GS) {
-        T yA = 0, yL = 0;
+        T yA[2] = {T(0), T(0)}, yL[2] = {T(0), T(0)};
         for (int i = 0; i < n; ++i) {
           const T cmi = __ldg(CT + i * M + mu);
-          yA += cmi * Ps[el * n + i];
-          yL += cmi * Bs[i * n + el];
+          yA[0] += cmi * Ps[el * n + i];
+          yL[0] += cmi * Bs[i * n + el];
+          if (nr > 1) {
+            yA[1] += cmi * Ps[(el + 1) * n + i];
+            yL[1] += cmi * Bs[i * n + el + 1];
+          }
         }
-        const T v = ao[mu], g0 = ao[M + mu], g1 = ao[2 * M + mu], g2 = ao[3 * M + mu], lp = ao[4 * M + mu];
-        const T hxx = ao[5 * M + mu], hyy = ao[6 * M + mu], hzz = ao[7 * M + mu];
-        const T hxy = ao[8 * M + mu], hxz = ao[9 * M + mu], hyz = ao[10 * M + mu];
-        const T l0 = ao[11 * M + mu], l1 = ao[12 * M + mu], l2 = ao[13 * M + mu];
-        const T hj0 = hxx * j0 + hxy * j1 + hxz * j2;
-        const T hj1 = hxy * j0 + hyy * j1 + hyz * j2;
-        const T hj2 = hxz * j0 + hyz * j1 + hzz * j2;
-        fa[0 * M + mu] -= g0 * yL;
-        fa[1 * M + mu] -= g1 * yL;
-        fa[2 * M + mu] -= g2 * yL;
-        const T c0 = T(-0.5) * (g0 * yA - yL * (l0 + T(2) * hj0));
-        const T c1 = T(-0.5) * (g1 * yA - yL * (l1 + T(2) * hj1));
-        const T c2 = T(-0.5) * (g2 * yA - yL * (l2 + T(2) * hj2));
-        fa[3 * M + mu] += c0;
-        fa[4 * M + mu] += c1;
-        fa[5 * M + mu] += c2;
-        ce[0] += c0;
-        ce[1] += c1;
-        ce[2] += c2;
-        if (tcs) {
-          stg[8 * mu + (el & 7)] = __float2bfloat16_rn((float)v);
-        } else {
-          const T tdc = lp + T(2) * (j0 * g0 + j1 * g1 + j2 * g2);
-          for (int i = 0; i < n; ++i) {
-            const T b = Bs[i * n + el];
-            Ow[mu * n + i] += v * b;
-            if (want_dC) D[mu * n + i] += b * tdc;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (r >= nr) break;
+          const int e = e0 + el + r;
+          const T* a = ao + r * 14 * M;
+          const T j0 = Jg[3 * e], j1 = Jg[3 * e + 1], j2 = Jg[3 * e + 2];
+          const T v = a[mu], g0 = a[M + mu], g1 = a[2 * M + mu], g2 = a[3 * M + mu], lp = a[4 * M + mu];
+          const T hxx = a[5 * M + mu], hyy = a[6 * M + mu], hzz = a[7 * M + mu];
+          const T hxy = a[8 * M + mu], hxz = a[9 * M + mu], hyz = a[10 * M + mu];
+          const T l0 = a[11 * M + mu], l1 = a[12 * M + mu], l2 = a[13 * M + mu];
+          const T hj0 = hxx * j0 + hxy * j1 + hxz * j2;
+          const T hj1 = hxy * j0 + hyy * j1 + hyz * j2;
+          const T hj2 = hxz * j0 + hyz * j1 + hzz * j2;
+          const T ya = r == 0 ? yA[0] : yA[1], yl = r == 0 ? yL[0] : yL[1];
+          fa[0 * M + mu] -= g0 * yl;
+          fa[1 * M + mu] -= g1 * yl;
+          fa[2 * M + mu] -= g2 * yl;
+          const T c0 = T(-0.5) * (g0 * ya - yl * (l0 + T(2) * hj0));
+          const T c1 = T(-0.5) * (g1 * ya - yl * (l1 + T(2) * hj1));
+          const T c2 = T(-0.5) * (g2 * ya - yl * (l2 + T(2) * hj2));
+          fa[3 * M + mu] += c0;
+          fa[4 * M + mu] += c1;
+          fa[5 * M + mu] += c2;
+          ce[r][0] += c0;
+          ce[r][1] += c1;
+          ce[r][2] += c2;
+          if (tcs) {
+            stg[8 * mu + ((el + r) & 7)] = __float2bfloat16_rn((float)v);
+          } else {
+            const T tdc = lp + T(2) * (j0 * g0 + j1 * g1 + j2 * g2);
+            for (int i = 0; i < n; ++i) {
+              const T b = Bs[i * n + el + r];
+              Ow[mu * n + i] += v * b;
+              if (want_dC) D[mu * n + i] += b * tdc;
+            }
           }
         }
       }
-      if (tcs && ((el & 7) == 7 || el == n - 1)) {
-        // eight electron slots of psi_mu: one 16-byte row of the K-major PhiT tile (chunk el / 16);
+      const int ell = el + nr - 1;  // the step's last electron (steps start on even electrons)
+      if (tcs && ((ell & 7) == 7 || ell == n - 1)) {
+        // eight electron slots of psi_mu: one 16-byte row of the K-major PhiT tile (chunk ell / 16);
         // each staging row is written and flushed by the same thread
         __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(P.phiT[sg]) +
-                             ((size_t)w * P.nch + (el >> 4)) * P.Mf * 16 + (el & 8);
+                             ((size_t)w * P.nch + (ell >> 4)) * P.Mf * 16 + (ell & 8);
         for (int mu = t; mu < M; mu += GS) {
           uint4* row = reinterpret_cast<uint4*>(stg + 8 * mu);
           *reinterpret_cast<uint4*>(dst + (size_t)mu * 16) = *row;
@@ -635,33 +651,41 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       }
       if (warp) {  // an AO moves with its nucleus as -d/dr_e: the same terms, summed over every AO
 #pragma unroll
-        for (int k = 0; k < 3; ++k) ce[k] = warp_sum(ce[k]);
-        if ((t & 31) == 0)
+        for (int r = 0; r < 2; ++r) {
+          if (r >= nr) break;
 #pragma unroll
-          for (int k = 0; k < 3; ++k) atomicAdd(&er[3 * e + k], ce[k]);
+          for (int k = 0; k < 3; ++k) ce[r][k] = warp_sum(ce[r][k]);
+          if ((t & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) atomicAdd(&er[3 * (e0 + el + r) + k], ce[r][k]);
+        }
       }
       gsync<GS>();
-      // e-n Jastrow and V_en terms, one nucleus per thread
+      // e-n Jastrow and V_en terms, one nucleus per thread, the step's electrons in order
       for (int I = t; I < K; I += GS) {
-        T sd[3];
-        disp_nuc<T>(S, pe, I, sd);
-        const T sx = sd[0], sy = sd[1], sz = sd[2];
-        const T r = dsqrt<T>(sx * sx + sy * sy + sz * sz), ri = T(1) / r;
-        const T Z = (T)S.Z[I];
-        const T sv[3] = {sx, sy, sz};
-        const T nn[3] = {sx * ri, sy * ri, sz * ri};
-        const T ven = -Z * ri * ri * ri;
-        for (int d = 0; d < 3; ++d) frc[3 * K + 3 * I + d] += ven * sv[d];
-        if (S.J1) {
-          const Rad3<T> c = pade<T>(-Z, (T)S.ben, r);
-          const T gsum[3] = {gd[3 * e] + Jg[3 * e], gd[3 * e + 1] + Jg[3 * e + 1], gd[3 * e + 2] + Jg[3 * e + 2]};
-          const T dl = c.h3 + T(2) * c.h2 * ri - T(2) * c.h1 * ri * ri;
-          for (int d = 0; d < 3; ++d) {
-            T hs = 0;
-            for (int cc = 0; cc < 3; ++cc)
-              hs += (c.h2 * nn[d] * nn[cc] + c.h1 * ri * ((d == cc ? T(1) : T(0)) - nn[d] * nn[cc])) * gsum[cc];
-            frc[3 * I + d] += -c.h1 * nn[d];
-            frc[3 * K + 3 * I + d] += hs + T(0.5) * dl * nn[d];
+        for (int r = 0; r < nr; ++r) {
+          const int e = e0 + el + r;
+          const EPos pe = make_epos(pos + 3 * e);
+          T sd[3];
+          disp_nuc<T>(S, pe, I, sd);
+          const T sx = sd[0], sy = sd[1], sz = sd[2];
+          const T rr = dsqrt<T>(sx * sx + sy * sy + sz * sz), ri = T(1) / rr;
+          const T Z = (T)S.Z[I];
+          const T sv[3] = {sx, sy, sz};
+          const T nn[3] = {sx * ri, sy * ri, sz * ri};
+          const T ven = -Z * ri * ri * ri;
+          for (int d = 0; d < 3; ++d) frc[3 * K + 3 * I + d] += ven * sv[d];
+          if (S.J1) {
+            const Rad3<T> c = pade<T>(-Z, (T)S.ben, rr);
+            const T gsum[3] = {gd[3 * e] + Jg[3 * e], gd[3 * e + 1] + Jg[3 * e + 1], gd[3 * e + 2] + Jg[3 * e + 2]};
+            const T dl = c.h3 + T(2) * c.h2 * ri - T(2) * c.h1 * ri * ri;
+            for (int d = 0; d < 3; ++d) {
+              T hs = 0;
+              for (int cc = 0; cc < 3; ++cc)
+                hs += (c.h2 * nn[d] * nn[cc] + c.h1 * ri * ((d == cc ? T(1) : T(0)) - nn[d] * nn[cc])) * gsum[cc];
+              frc[3 * I + d] += -c.h1 * nn[d];
+              frc[3 * K + 3 * I + d] += hs + T(0.5) * dl * nn[d];
+            }
           }
         }
       }

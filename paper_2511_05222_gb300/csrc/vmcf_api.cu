@@ -154,7 +154,8 @@ GroupLayout layout_refresh_move(const vmcf_system_s& s, size_t tsz, int GS) {
 }
 
 // Shared-memory plan of one walker group for the measure kernel.
-GroupLayout layout_measure_p2(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows, int p2) {
+GroupLayout layout_measure_p2(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows, int p2,
+                              int p3) {
   GroupLayout L{};
   int o = 0;
   auto take = [&](int bytes) { int at = o; o = align16(o + bytes); return at; };
@@ -172,7 +173,8 @@ GroupLayout layout_measure_p2(const vmcf_system_s& s, size_t tsz, int GS, bool w
   L.gd = take((int)tsz * 3 * s.Ne);
   L.ao_rows = 8;
   L.p2_chunk = p2;  // electrons per chunk of the gradient/Laplacian pass: 4 AO rows each
-  L.ao = take((int)tsz * std::max(14, 4 * L.p2_chunk) * s.M);
+  L.p3_chunk = p3;  // electrons per step of the adjoint/force pass: 14 AO rows each
+  L.ao = take((int)tsz * std::max(14 * L.p3_chunk, 4 * L.p2_chunk) * s.M);
   L.mo = take((int)tsz * 4 * L.p2_chunk * s.nmax);
   L.frc = take((int)tsz * 6 * s.K);
   L.fa = take((int)tsz * 6 * s.M);
@@ -203,15 +205,21 @@ GroupLayout layout_measure_p2(const vmcf_system_s& s, size_t tsz, int GS, bool w
   return L;
 }
 
-// Six electrons per chunk of the gradient/Laplacian pass (half the chunks of three, each coefficient
-// load shared by twice the rows) when that layout fits and keeps as many walker groups per SM as
-// chunks of three do; else three.
+// Larger electron chunks where the layout fits and keeps as many walker groups per SM as the smallest
+// (three electrons per gradient/Laplacian chunk, one per adjoint/force step): six per gradient/Laplacian
+// chunk (half the chunks, each coefficient load shared by twice the rows) and two per adjoint/force step
+// (half the steps and barriers, each coefficient load shared by both electrons), in that order of
+// preference.
 GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows = 0) {
-  const GroupLayout L3 = layout_measure_p2(s, tsz, GS, withD, tc_rows, 3);
-  const GroupLayout L6 = layout_measure_p2(s, tsz, GS, withD, tc_rows, 6);
+  const GroupLayout L0 = layout_measure_p2(s, tsz, GS, withD, tc_rows, 3, 1);
   const int per_sm = 228 * 1024;
-  if (L6.bytes <= kSmemCap && per_sm / (L6.bytes + 1024) >= per_sm / (L3.bytes + 1024)) return L6;
-  return L3;
+  const int want = per_sm / (L0.bytes + 1024);
+  const int cand[3][2] = {{6, 2}, {6, 1}, {3, 2}};
+  for (const auto& c : cand) {
+    const GroupLayout L = layout_measure_p2(s, tsz, GS, withD, tc_rows, c[0], c[1]);
+    if (L.bytes <= kSmemCap && per_sm / (L.bytes + 1024) >= want) return L;
+  }
+  return L0;
 }
 
 // Measurement-kernel plan for group size s.GSm: layouts, groups per CTA, accumulator placement.

@@ -13,6 +13,7 @@ struct GroupLayout {
   int pos, ph, pl, Bd, Bt, P, Q, Jg, Jl, gd, ao, mo, frc, fa, ew, Ow, D, piv, f, red, scal, row, wv, col;
   int ao_rows;   // AO rows of M values the ao buffer holds (electrons per Slater-build chunk)
   int p2_chunk;  // electrons per chunk of the gradient/Laplacian pass (4 AO rows each)
+  int p3_chunk;  // electrons per step of the adjoint/force pass (14 AO rows each): 1 or 2
   int jw;        // AO-expanded Jastrow work space (systems with a Jastrow basis, else 0)
   int jch;       // electrons per chunk of the Jastrow-basis products (measurement)
   int jng;       // subgroups of whole warps that take different electrons in the Jastrow-basis loops
