@@ -15,11 +15,14 @@ from __future__ import annotations
 
 
 def per_walker_eval(K: int, M: int, n_up: int, n_dn: int, nprim: int, acc: float = 0.5, MJ: int = 0,
-                    nJprim: int = 0) -> dict:
+                    nJprim: int = 0, kref: int = 26) -> dict:
     """MJ, nJprim: functions and primitives of the Jastrow basis of the AO-expanded Jastrow terms
     (0: none). Those add, per move, one Jastrow-basis evaluation at r' and the product Xi dphi with
     its dot products; per evaluation, the basis with all derivatives at every electron, t0 = xi + Xi s,
-    u_e = Xi psi^J(r_e) and p_e = Xi w_e for every electron, and the force terms."""
+    u_e = Xi psi^J(r_e) and p_e = Xi w_e for every electron, and the force terms.
+    kref: moves between FP64 re-inversions. A measured sweep re-inverts (Ne - 1) // kref times during its
+    moves (a re-inversion that would fall on the last move is the evaluation's own, counted there):
+    each rebuilds the Slater matrices (AO values and MO rows of every electron) and inverts both blocks."""
     Ne = n_up + n_dn
     ns = [n_up] * n_up + [n_dn] * n_dn  # orbital count seen by each electron
     move = {
@@ -41,6 +44,11 @@ def per_walker_eval(K: int, M: int, n_up: int, n_dn: int, nprim: int, acc: float
                  + sum(4 * M * n for n in spins) + 18 * K),      # walker sums
         "fp64": sum(2 * n ** 3 for n in spins),                  # Gauss-Jordan inversion per spin
     }
+    n_ref = (Ne - 1) // kref
+    spins0 = [n for n in (n_up, n_dn) if n > 0]
+    move["exp"] += n_ref * Ne * nprim
+    move["fp32"] += n_ref * sum(3 * nprim + 3 * M + 2 * M * n for n in ns)
+    move["fp64"] += n_ref * sum(2 * n ** 3 for n in spins0)
     if MJ:
         move["exp"] += Ne * nJprim
         move["fp32"] += Ne * (3 * nJprim + 3 * MJ + 2 * MJ * MJ + 4 * MJ)
