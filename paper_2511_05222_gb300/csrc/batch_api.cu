@@ -51,6 +51,7 @@ struct LaunchPlan {
 
 struct vmcf_batch_s {
   int G = 0, precision = 0, sms = 1;
+  bool jb = false;  // some geometry has AO-expanded Jastrow terms: the kernels that hold their code
   std::vector<vmcf_system_s*> sys;
   std::vector<vmcf_walkers_s*> wk;
   std::vector<int> bucket;              // per geometry
@@ -99,8 +100,8 @@ int bucket_region(const vmcf_batch_s& b, int phase, int bk, int GS) {
 }
 
 int occupancy(const vmcf_batch_s& b, int phase, const Shape& sh, size_t smem, int* ctas) {
-  cudaError_t e = b.precision == VMCF_FP64 ? batch_occupancy<double>(phase, sh.GS, sh.groups, smem, ctas)
-                                           : batch_occupancy<float>(phase, sh.GS, sh.groups, smem, ctas);
+  cudaError_t e = b.precision == VMCF_FP64 ? batch_occupancy<double>(phase, sh.GS, sh.groups, smem, b.jb, ctas)
+                                           : batch_occupancy<float>(phase, sh.GS, sh.groups, smem, b.jb, ctas);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the batch kernel");
   return VMCF_OK;
 }
@@ -301,8 +302,8 @@ cudaError_t launch_k(const vmcf_batch_s& b, int k, int mode, int kref, double si
   const LaunchPlan& lp = b.launches[k];
   const BatchArgs A = args_for(b, k, mode, kref, sigma);
   return b.precision == VMCF_FP64
-             ? launch_batch<double>(lp.phase, lp.shape.GS, lp.shape.groups, lp.grid, lp.smem, A, st)
-             : launch_batch<float>(lp.phase, lp.shape.GS, lp.shape.groups, lp.grid, lp.smem, A, st);
+             ? launch_batch<double>(lp.phase, lp.shape.GS, lp.shape.groups, lp.grid, lp.smem, A, b.jb, st)
+             : launch_batch<float>(lp.phase, lp.shape.GS, lp.shape.groups, lp.grid, lp.smem, A, b.jb, st);
 }
 
 // One sweep of the batch as a graph: per phase (the evaluation only when measuring), fork
@@ -401,6 +402,7 @@ int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walker
   b->precision = systems[0]->precision;
   b->sys.assign(systems, systems + G);
   b->wk.assign(walkers, walkers + G);
+  for (int g = 0; g < G; ++g) b->jb = b->jb || systems[g]->MJ > 0;
   b->h_geo.resize(G);
   b->h_clk.resize(G);
   int dev = 0;

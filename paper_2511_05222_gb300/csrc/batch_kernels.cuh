@@ -10,7 +10,8 @@
 
 namespace vmcf {
 
-template <typename T, int GS, int PHASE>
+// JB: some geometry of the batch has AO-expanded Jastrow terms (else their code is compiled out).
+template <typename T, int GS, int PHASE, bool JB>
 __global__ void __launch_bounds__(256) batch_kernel(BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gid = threadIdx.x / GS, t = threadIdx.x % GS;
@@ -47,37 +48,38 @@ __global__ void __launch_bounds__(256) batch_kernel(BatchArgs A) {
     const int W = G->P.W;
     const long long w0 = (long long)W * item.y / G->grid_meas, w1 = (long long)W * (item.y + 1) / G->grid_meas;
     if constexpr (PHASE == 0) {
-      for (long long w = w0; w < w1; ++w) move_walker<T, GS>(G->S, G->Lrm, G->P, base, (int)w, G->P.c0, G->P.sweep0);
+      for (long long w = w0; w < w1; ++w) move_walker<T, GS, JB>(G->S, G->Lrm, G->P, base, (int)w, G->P.c0, G->P.sweep0);
     } else {
       double* slot = A.mode == 1 ? G->Mp.acc + (size_t)item.y * G->Mp.accL : nullptr;
-      for (long long w = w0; w < w1; ++w) measure_walker<T, GS>(G->S, G->Lmeas, G->Mp, base, nullptr, slot, (int)w);
+      for (long long w = w0; w < w1; ++w) measure_walker<T, GS, JB>(G->S, G->Lmeas, G->Mp, base, nullptr, slot, (int)w);
     }
     gsync<GS>();  // cur[1] is read by every thread before it is overwritten
   }
 }
 
-template <typename T, int PHASE>
+template <typename T, int PHASE, bool JB>
 const void* batch_fn(int GS) {
   switch (GS) {
-    case 32: return reinterpret_cast<const void*>(batch_kernel<T, 32, PHASE>);
-    case 128: return reinterpret_cast<const void*>(batch_kernel<T, 128, PHASE>);
-    case 256: return reinterpret_cast<const void*>(batch_kernel<T, 256, PHASE>);
+    case 32: return reinterpret_cast<const void*>(batch_kernel<T, 32, PHASE, JB>);
+    case 128: return reinterpret_cast<const void*>(batch_kernel<T, 128, PHASE, JB>);
+    case 256: return reinterpret_cast<const void*>(batch_kernel<T, 256, PHASE, JB>);
     default: return nullptr;
   }
 }
 
-template <typename T>
-cudaError_t launch_batch(int phase, int GS, int groups, int grid, size_t smem, const BatchArgs& A, cudaStream_t st) {
-  const void* fn = phase == 0 ? batch_fn<T, 0>(GS) : batch_fn<T, 1>(GS);
+template <typename T, bool JB>
+cudaError_t launch_batch_impl(int phase, int GS, int groups, int grid, size_t smem, const BatchArgs& A,
+                              cudaStream_t st) {
+  const void* fn = phase == 0 ? batch_fn<T, 0, JB>(GS) : batch_fn<T, 1, JB>(GS);
   if (!fn || GS * groups > 256) return cudaErrorInvalidValue;
   BatchArgs a = A;
   void* args[] = {&a};
   return cudaLaunchKernel(fn, dim3(grid), dim3(GS * groups), args, smem, st);
 }
 
-template <typename T>
-cudaError_t batch_occupancy(int phase, int GS, int groups, size_t smem, int* ctas_per_sm) {
-  const void* fn = phase == 0 ? batch_fn<T, 0>(GS) : batch_fn<T, 1>(GS);
+template <typename T, bool JB>
+cudaError_t batch_occupancy_impl(int phase, int GS, int groups, size_t smem, int* ctas_per_sm) {
+  const void* fn = phase == 0 ? batch_fn<T, 0, JB>(GS) : batch_fn<T, 1, JB>(GS);
   if (!fn || GS * groups > 256) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;

@@ -1,4 +1,5 @@
-// Ragged batches: the batch-clock kernel and the mixed-mode (FP32) persistent batch kernels.
+// Ragged batches: the batch-clock kernel and the mixed-mode (FP32) persistent batch kernels (the instances
+// for batches with AO-expanded Jastrow terms are in k_batch_jb.cu).
 #include "batch_kernels.cuh"
 
 namespace vmcf {
@@ -19,7 +20,19 @@ cudaError_t launch_batch_advance(BatchClock* clk, int G, int mode, int kref, int
   return cudaGetLastError();
 }
 
-template cudaError_t launch_batch<float>(int, int, int, int, size_t, const BatchArgs&, cudaStream_t);
-template cudaError_t batch_occupancy<float>(int, int, int, size_t, int*);
+extern template cudaError_t launch_batch_impl<float, true>(int, int, int, int, size_t, const BatchArgs&, cudaStream_t);
+extern template cudaError_t batch_occupancy_impl<float, true>(int, int, int, size_t, int*);
+
+template <>
+cudaError_t launch_batch<float>(int phase, int GS, int groups, int grid, size_t smem, const BatchArgs& A, bool jb,
+                                cudaStream_t st) {
+  return jb ? launch_batch_impl<float, true>(phase, GS, groups, grid, smem, A, st)
+            : launch_batch_impl<float, false>(phase, GS, groups, grid, smem, A, st);
+}
+template <>
+cudaError_t batch_occupancy<float>(int phase, int GS, int groups, size_t smem, bool jb, int* ctas) {
+  return jb ? batch_occupancy_impl<float, true>(phase, GS, groups, smem, ctas)
+            : batch_occupancy_impl<float, false>(phase, GS, groups, smem, ctas);
+}
 
 }  // namespace vmcf

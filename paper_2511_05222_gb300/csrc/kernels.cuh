@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(256) refresh_kernel(DevSys S, GroupLayout L, c
 // ---------------------------------------------------------------- Metropolis sweeps
 // All sweeps of one walker (index w of P's arrays) by one group. c0: attempted moves since
 // the last refresh when the launch starts; sweep0: global sweep index of the first sweep.
-template <typename T, int GS>
+// JB: the system has AO-expanded Jastrow terms; without them the terms' code is compiled out.
+template <typename T, int GS, bool JB>
 __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MoveParams& P, unsigned char* base, int w,
                             int c0, uint64_t sweep0) {
   const int t = threadIdx.x % GS;
@@ -118,7 +119,7 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
   // AO-expanded Jastrow terms: t0 = xi + Xi s, the Jastrow-basis values at r' and r_e, and
   // y = Xi (psi^J(r') - psi^J(r_e)); t0 is rebuilt here and at every re-inversion, and moves by y
   // on acceptance
-  const int MJ = S.MJ;
+  const int MJ = JB ? S.MJ : 0;
   T* jt0 = MJ ? sm_ptr<T>(base, L.jw) : nullptr;
   T* jpn = jt0 + MJ;
   T* jpo = jpn + MJ;
@@ -148,7 +149,7 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
       const EPos pn = make_epos(rn);
       const EPos po = make_epos(pos + 3 * e);
       ao_point<T, GS, 0, false>(S, pn, ao, 0);
-      for (int sh = t; sh < S.nJs; sh += GS) {
+      for (int sh = t; sh < (JB ? S.nJs : 0); sh += GS) {
         jas_shell<T, 0>(S, sh, pn, [&](int mu, const T* v) { jpn[mu] = v[0]; });
         jas_shell<T, 0>(S, sh, po, [&](int mu, const T* v) { jpo[mu] = v[0]; });
       }
@@ -304,18 +305,18 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
   gsync<GS>();
 }
 
-template <typename T, int GS>
+template <typename T, int GS, bool JB>
 __global__ void __launch_bounds__(256) move_kernel(DevSys S, GroupLayout L, MoveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gpb = blockDim.x / GS, gid = threadIdx.x / GS;
   const int w = blockIdx.x * gpb + gid;
   if (w >= P.W) return;  // the whole group leaves together; only group barriers are used
-  move_walker<T, GS>(S, L, P, smem + gid * L.bytes, w, P.c0, P.sweep0);
+  move_walker<T, GS, JB>(S, L, P, smem + gid * L.bytes, w, P.c0, P.sweep0);
 }
 
 
 // ---------------------------------------------------------------- measurement
-template <typename T, int GS>
+template <typename T, int GS, bool JB>
 __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const MeasParams& P, unsigned char* base,
                                T* acc_s, double* acc_g, int w) {
   const int t = threadIdx.x % GS;
@@ -404,7 +405,7 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   // their outputs [2 jch][MJ], t0 = xi + Xi s, s (later sum_e w_e), P, and the per-function force
   // shares [jng][6][MJ]. The per-electron loops run in jng subgroups of whole warps, each covering
   // every Jastrow-basis shell for its own electrons.
-  const int MJ = S.MJ, MJp = S.MJp, jch = L.jch, jng = L.jng > 0 ? L.jng : 1;
+  const int MJ = JB ? S.MJ : 0, MJp = S.MJp, jch = L.jch, jng = L.jng > 0 ? L.jng : 1;
   T* jin = MJ ? sm_ptr<T>(base, L.jw) : nullptr;
   T* jout = jin + 2 * jch * MJp;
   T* jt0 = jout + 2 * jch * MJ;
@@ -988,7 +989,7 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
 // CTA's FP64 slot (one group per CTA), and the slot is only ever touched by its CTA.
 // In the shared accumulator, acc[1] and acc[2] hold sums of (E_L - E_ref) and its square;
 // they are turned into sums of E_L and E_L^2 when the CTA flushes.
-template <typename T, int GS>
+template <typename T, int GS, bool JB>
 __global__ void __launch_bounds__(256) measure_kernel(DevSys S, GroupLayout L, MeasParams P, int acc_off) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gpb = blockDim.x / GS, gid = threadIdx.x / GS;
@@ -1001,7 +1002,7 @@ __global__ void __launch_bounds__(256) measure_kernel(DevSys S, GroupLayout L, M
   }
   const long long w0 = (long long)P.W * blockIdx.x / gridDim.x;
   const long long w1 = (long long)P.W * (blockIdx.x + 1) / gridDim.x;
-  for (long long w = w0 + gid; w < w1; w += gpb) measure_walker<T, GS>(S, L, P, base, acc_s, acc_g, (int)w);
+  for (long long w = w0 + gid; w < w1; w += gpb) measure_walker<T, GS, JB>(S, L, P, base, acc_s, acc_g, (int)w);
   if (acc_s) {
     __syncthreads();
     double* slot = P.acc + (size_t)blockIdx.x * P.accL;
@@ -1016,19 +1017,22 @@ __global__ void __launch_bounds__(256) measure_kernel(DevSys S, GroupLayout L, M
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename T>
+// Instances with the AO-expanded Jastrow terms (JB = true) live in their own translation units.
+template <typename T, bool JB>
 cudaError_t set_smem_limits_impl() {
   const int lim = 227 * 1024;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(refresh_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(refresh_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(move_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(move_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(measure_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(measure_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(refresh_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(move_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(measure_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if (!JB) {
+    if ((e = cudaFuncSetAttribute(refresh_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(refresh_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(refresh_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  }
+  if ((e = cudaFuncSetAttribute(move_kernel<T, 32, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(move_kernel<T, 128, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(move_kernel<T, 256, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_kernel<T, 32, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_kernel<T, 128, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_kernel<T, 256, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   return cudaSuccess;
 }
 
@@ -1047,29 +1051,29 @@ cudaError_t launch_refresh_impl(const DevSys& S, const Launch& lc, const double*
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool JB>
 cudaError_t launch_move_impl(const DevSys& S, const Launch& lc, const MoveParams& P, cudaStream_t st) {
   const dim3 grid(lc.grid), block(lc.GS * lc.groups);
   if (lc.GS == 32)
-    move_kernel<T, 32><<<grid, block, lc.smem, st>>>(S, lc.L, P);
+    move_kernel<T, 32, JB><<<grid, block, lc.smem, st>>>(S, lc.L, P);
   else if (lc.GS == 128)
-    move_kernel<T, 128><<<grid, block, lc.smem, st>>>(S, lc.L, P);
+    move_kernel<T, 128, JB><<<grid, block, lc.smem, st>>>(S, lc.L, P);
   else if (lc.GS == 256)
-    move_kernel<T, 256><<<grid, block, lc.smem, st>>>(S, lc.L, P);
+    move_kernel<T, 256, JB><<<grid, block, lc.smem, st>>>(S, lc.L, P);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool JB>
 cudaError_t launch_measure_impl(const DevSys& S, const Launch& lc, const MeasParams& P, cudaStream_t st) {
   const dim3 grid(lc.grid), block(lc.GS * lc.groups);
   if (lc.GS == 32)
-    measure_kernel<T, 32><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
+    measure_kernel<T, 32, JB><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
   else if (lc.GS == 128)
-    measure_kernel<T, 128><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
+    measure_kernel<T, 128, JB><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
   else if (lc.GS == 256)
-    measure_kernel<T, 256><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
+    measure_kernel<T, 256, JB><<<grid, block, lc.smem, st>>>(S, lc.L, P, lc.acc_off);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

@@ -166,9 +166,10 @@ struct BatchArgs {
 
 // phase 0: Metropolis sweep of each walker; phase 1: evaluation (and walker sums when mode 1)
 template <typename T>
-cudaError_t launch_batch(int phase, int GS, int groups, int grid, size_t smem, const BatchArgs& A, cudaStream_t st);
+cudaError_t launch_batch(int phase, int GS, int groups, int grid, size_t smem, const BatchArgs& A, bool jb,
+                         cudaStream_t st);
 template <typename T>
-cudaError_t batch_occupancy(int phase, int GS, int groups, size_t smem, int* ctas_per_sm);
+cudaError_t batch_occupancy(int phase, int GS, int groups, size_t smem, bool jb, int* ctas_per_sm);
 cudaError_t launch_batch_advance(BatchClock* clk, int G, int mode, int kref, int* queues, int nq, cudaStream_t st);
 
 cudaError_t run_probes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, cudaStream_t st);
