@@ -395,9 +395,10 @@ def main():
     # the one-warp-per-walker kernel family, else walker groups (32 threads up to 24 orbitals per spin)
     small = sysx.Ne <= 32 and max(sysx.n_up, sysx.n_dn) <= 16 and jb is None
     wide = max(sysx.n_up, sysx.n_dn) > 24
+    jbf = "true" if jb else "false"  # walker-group kernels: instance with or without the AO-expanded Jastrow terms
     kname = (f"{dom}_small<float, 16>" if small else
-             {"move": f"move_kernel<float, {128 if wide else 32}>",
-              "measure": f"measure_kernel<float, {256 if wide else 32}>"}[dom])
+             {"move": f"move_kernel<float, {128 if wide else 32}, {jbf}>",
+              "measure": f"measure_kernel<float, {256 if wide else 32}, {jbf}>"}[dom])
     roofline = {"bound": "alu", "pipe": bound, "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s" if bound != "sfu" else "Texp/s", "frac": achieved / peak,
                 "peak_source": "measured in this run by vmcf_probe_pipes (register-only FMA/exp kernels)",
