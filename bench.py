@@ -396,7 +396,9 @@ def main():
     small = sysx.Ne <= 32 and max(sysx.n_up, sysx.n_dn) <= 16 and jb is None
     wide = max(sysx.n_up, sysx.n_dn) > 24
     jbf = "true" if jb else "false"  # walker-group kernels: instance with or without the AO-expanded Jastrow terms
-    kname = (f"{dom}_small<float, 16>" if small else
+    nmx = max(sysx.n_up, sysx.n_dn)
+    nm = 8 if nmx <= 8 else (14 if nmx <= 14 else 16)  # register-row width of the one-warp-per-walker kernels
+    kname = (f"{dom}_small<float, {nm}>" if small else
              {"move": f"move_kernel<float, {128 if wide else 32}, {jbf}>",
               "measure": f"measure_kernel<float, {256 if wide else 32}, {jbf}>"}[dom])
     roofline = {"bound": "alu", "pipe": bound, "kernel": kname, "achieved": achieved, "peak": peak,

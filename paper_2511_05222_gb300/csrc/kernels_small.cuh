@@ -141,11 +141,17 @@ __device__ __forceinline__ T dot_row(const T (&x)[NM], const T* __restrict__ cro
   return s0 + s1;
 }
 
-// Stage C^up and C^dn into shared memory as [2][M][NM], zero-padded beyond n_s.
+// Row stride of the staged coefficients for register rows of NM orbitals: a multiple of 4, so that
+// every row starts on 16 bytes.
+template <int NM>
+__host__ __device__ constexpr int c_stride() { return (NM + 3) / 4 * 4; }
+
+// Stage C^up and C^dn into shared memory as [2][M][c_stride<NM>()], zero-padded beyond n_s.
 template <typename T, int NM>
 __device__ __forceinline__ void stage_C(const DevSys& S, T* Cs) {
-  for (int idx = threadIdx.x; idx < 2 * S.M * NM; idx += blockDim.x) {
-    const int sg = idx / (S.M * NM), r = idx - sg * S.M * NM, mu = r / NM, i = r - mu * NM;
+  constexpr int NMS = c_stride<NM>();
+  for (int idx = threadIdx.x; idx < 2 * S.M * NMS; idx += blockDim.x) {
+    const int sg = idx / (S.M * NMS), r = idx - sg * S.M * NMS, mu = r / NMS, i = r - mu * NMS;
     const int n = sg == 0 ? S.nup : S.ndn;
     Cs[idx] = (i < n) ? __ldg(coefC<T>(S, sg) + mu * n + i) : T(0);
   }
@@ -167,11 +173,11 @@ __device__ __forceinline__ V lane_group_sum(V v, unsigned mask) {
 template <typename T, int NM, int LPW, bool GUIDE>
 __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // shared memory: C^up, C^dn [2][M][NM]; the CTA's inverses walker-interleaved [nB][WPC]; its
+  // shared memory: C^up, C^dn [2][M][c_stride<NM>()]; the CTA's inverses walker-interleaved [nB][WPC]; its
   // positions [3 Ne][WPC] (float-float pairs in mixed mode, double in FP64 mode)
   T* Cs = reinterpret_cast<T*>(smem);
   const int WPC = P.wpc;
-  T* Bs = Cs + 2 * S.M * NM;
+  T* Bs = Cs + 2 * S.M * c_stride<NM>();
   using PosT = typename std::conditional<sizeof(T) == 4, float2, double>::type;
   PosT* Ps = reinterpret_cast<PosT*>(Bs + (size_t)S.nB * WPC);
   stage_C<T, NM>(S, Cs);
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
     const int sg = e < nup ? 0 : 1;
     const int n = sg == 0 ? nup : S.ndn, el = e - (sg == 0 ? 0 : nup);
     const int off = sg == 0 ? 0 : nup * nup;
-    const T* Csg = Cs + sg * S.M * NM;
+    const T* Csg = Cs + sg * S.M * c_stride<NM>();
     uint64_t r[4] = {wid, sweep, (uint64_t)e, 0};
     philox4x64_10(r, P.k0, P.k1);
     double xi[3];
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
       for (int m = 0; m < 2 * sh.y + 1; ++m) {
         T Pa, g[3], h[6];
         angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
-        axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * NM);
+        axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * c_stride<NM>());
       }
     }
 #pragma unroll
@@ -575,7 +581,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       T row[NM];
 #pragma unroll
       for (int i = 0; i < NM; ++i) row[i] = T(0);
-      const T* Csg = Cs + sg * M * NM;
+      const T* Csg = Cs + sg * M * c_stride<NM>();
       for (int s = 0; s < S.nshell; ++s) {
         const int4 sh = __ldg(S.shell + s);
         T d[3];
@@ -585,7 +591,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
         for (int m = 0; m < 2 * sh.y + 1; ++m) {
           T Pa, g[3], h[6];
           angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
-          axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * NM);
+          axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * c_stride<NM>());
         }
       }
 #pragma unroll
@@ -676,7 +682,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       T G0[NM], G1[NM], G2[NM], Lr[NM];
 #pragma unroll
       for (int i = 0; i < NM; ++i) G0[i] = G1[i] = G2[i] = Lr[i] = T(0);
-      const T* Csg = Cs + sg * M * NM;
+      const T* Csg = Cs + sg * M * c_stride<NM>();
       for (int s = 0; s < S.nshell; ++s) {
         const int4 sh = __ldg(S.shell + s);
         T d[3];
@@ -686,7 +692,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
         for (int m = 0; m < 2 * sh.y + 1; ++m) {
           T Pa, g[3], h[6];
           angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
-          const T* cr = Csg + (sh.w + m) * NM;
+          const T* cr = Csg + (sh.w + m) * c_stride<NM>();
           axpy_row<T, NM>(G0, g[0] * rs.R0 + Pa * d[0] * rs.R1, cr);
           axpy_row<T, NM>(G1, g[1] * rs.R0 + Pa * d[1] * rs.R1, cr);
           axpy_row<T, NM>(G2, g[2] * rs.R0 + Pa * d[2] * rs.R1, cr);
@@ -745,7 +751,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
     T fr[3] = {T(0), T(0), T(0)};  // sum over every AO of the dE_L terms of this electron (space warp)
     int cur = -1;
     int chunk0 = 0, chunk_n = 0;  // AOs [chunk0, chunk0 + chunk_n) pending in phi
-    const T* Csg = Cs + sg * M * NM;
+    const T* Csg = Cs + sg * M * c_stride<NM>();
     auto flush_centre = [&](int I) {
       float v6f[6];
       double v6d[6];
@@ -829,7 +835,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
         for (int m = 0; m < ncomp; ++m) {
           T Pa, g[3], h[6];
           angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
-          const T* cr = Csg + (sh.w + m) * NM;
+          const T* cr = Csg + (sh.w + m) * c_stride<NM>();
           const T yA = dot_row<T, NM>(xr, cr), yL = dot_row<T, NM>(bc, cr);
           // Hessian of the AO contracted with grad J without forming it:
           // (H j)_a = (h j)_a R0 + g_a (x.j) R1 + (g.j) x_a R1 + P x_a (x.j) R2 + P j_a R1
@@ -1093,6 +1099,7 @@ template <typename T>
 cudaError_t launch_move_small_impl(const DevSys& S, int nm, int lpw, int W, size_t smem, const SmallMoveParams& P,
                                    cudaStream_t st) {
   if (nm <= 8) return launch_move_small_lpw<T, 8>(lpw, S, W, smem, P, st);
+  if (nm <= 14) return launch_move_small_lpw<T, 14>(lpw, S, W, smem, P, st);
   return launch_move_small_lpw<T, 16>(lpw, S, W, smem, P, st);
 }
 
@@ -1102,6 +1109,8 @@ cudaError_t launch_measure_small_impl(const DevSys& S, int nm, const SmallLayout
   const size_t smem = (size_t)L.cta_bytes + (size_t)warps * L.bytes;
   if (nm <= 8)
     measure_small<T, 8><<<grid, 32 * warps, smem, st>>>(S, L, P);
+  else if (nm <= 14)
+    measure_small<T, 14><<<grid, 32 * warps, smem, st>>>(S, L, P);
   else
     measure_small<T, 16><<<grid, 32 * warps, smem, st>>>(S, L, P);
   return cudaGetLastError();
@@ -1114,10 +1123,12 @@ cudaError_t set_smem_limits_small_impl() {
 #define VMCF_MOVE_ATTR(NM, L, G)                                                                                  \
   if ((e = cudaFuncSetAttribute(move_small<T, NM, L, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   VMCF_MOVE_ATTR(8, 1, false) VMCF_MOVE_ATTR(8, 2, false) VMCF_MOVE_ATTR(8, 4, false) VMCF_MOVE_ATTR(8, 8, false)
+  VMCF_MOVE_ATTR(14, 1, false) VMCF_MOVE_ATTR(14, 2, false) VMCF_MOVE_ATTR(14, 4, false) VMCF_MOVE_ATTR(14, 8, false)
   VMCF_MOVE_ATTR(16, 1, false) VMCF_MOVE_ATTR(16, 2, false) VMCF_MOVE_ATTR(16, 4, false) VMCF_MOVE_ATTR(16, 8, false)
-  VMCF_MOVE_ATTR(8, 2, true) VMCF_MOVE_ATTR(16, 2, true)
+  VMCF_MOVE_ATTR(8, 2, true) VMCF_MOVE_ATTR(14, 2, true) VMCF_MOVE_ATTR(16, 2, true)
 #undef VMCF_MOVE_ATTR
   if ((e = cudaFuncSetAttribute(measure_small<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_small<T, 14>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(measure_small<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   return cudaSuccess;
 }

@@ -273,7 +273,7 @@ void plan_small(vmcf_system_s& s) {
   s.small = false;
   if (s.Ne > 32 || s.nmax > 16 || s.MJ > 0) return;  // the AO-expanded Jastrow terms run on walker groups
   const int tsz = s.precision == VMCF_FP64 ? 8 : 4;
-  s.small_nm = s.nmax <= 8 ? 8 : 16;
+  s.small_nm = s.nmax <= 8 ? 8 : (s.nmax <= 14 ? 14 : 16);  // register-row width; staged rows padded to 4
   SmallLayout L{};
   L.chunk = 21;  // odd row stride: lanes writing phi[e][c] fall in distinct banks
   int o = 0;
@@ -293,14 +293,14 @@ void plan_small(vmcf_system_s& s) {
   L.scal = take(32);
   L.bytes = align16(o);
   L.cta_C = 0;
-  L.cta_acc = align16(tsz * 2 * s.M * s.small_nm);
+  L.cta_acc = align16(tsz * 2 * s.M * ((s.small_nm + 3) / 4 * 4));
   L.cta_bytes = L.cta_acc + align16(tsz * s.accL);
   int warps = 8;
   while (warps > 2 && L.cta_bytes + warps * L.bytes > kSmemCap) warps /= 2;
   if (L.cta_bytes + warps * L.bytes > kSmemCap) return;
   s.SL = L;
   s.small_warps = warps;
-  s.small_move_smem = (size_t)tsz * 2 * s.M * s.small_nm;
+  s.small_move_smem = (size_t)tsz * 2 * s.M * ((s.small_nm + 3) / 4 * 4);
   if (s.small_move_smem > (size_t)kSmemCap) return;
   s.small = true;
   s.tc_Mp = (s.M + 7) / 8 * 8;
