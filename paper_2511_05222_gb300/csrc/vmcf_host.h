@@ -30,7 +30,7 @@ struct vmcf_system_s {
   double* scratch_counters = nullptr;  // device [2] for evaluate
   // small-system path (at most 32 electrons and 16 orbitals per spin)
   bool small = false;
-  int small_nm = 16;          // register row width: 8 or 16
+  int small_nm = 16;          // register row width: 8, 14 or 16 (staged coefficient rows padded to 4)
   int small_warps = 8;        // warps per CTA of the measurement kernel
   int small_res = 1;          // resident measurement CTAs on the device
   int small_sms = 1;          // SMs on the device
