@@ -395,7 +395,7 @@ def main():
     # the one-warp-per-walker kernel family, else walker groups (32 threads up to 24 orbitals per spin)
     small = sysx.Ne <= 32 and max(sysx.n_up, sysx.n_dn) <= 16 and jb is None
     wide = max(sysx.n_up, sysx.n_dn) > 24
-    jbf = "true" if jb else "false"  # walker-group kernels: instance with or without the AO-expanded Jastrow terms
+    jbf = "1" if jb else "0"  # walker-group kernels: instance with (1) or without (0) the AO-expanded Jastrow terms
     nmx = max(sysx.n_up, sysx.n_dn)
     nm = 8 if nmx <= 8 else (14 if nmx <= 14 else 16)  # register-row width of the one-warp-per-walker kernels
     kname = (f"{dom}_small<float, {nm}>" if small else
