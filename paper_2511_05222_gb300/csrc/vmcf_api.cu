@@ -154,7 +154,7 @@ GroupLayout layout_refresh_move(const vmcf_system_s& s, size_t tsz, int GS) {
 }
 
 // Shared-memory plan of one walker group for the measure kernel.
-GroupLayout layout_measure_p2(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows, int p2,
+GroupLayout layout_measure_chunks(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows, int p2,
                               int p3) {
   GroupLayout L{};
   int o = 0;
@@ -211,12 +211,12 @@ GroupLayout layout_measure_p2(const vmcf_system_s& s, size_t tsz, int GS, bool w
 // (half the steps and barriers, each coefficient load shared by both electrons), in that order of
 // preference.
 GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows = 0) {
-  const GroupLayout L0 = layout_measure_p2(s, tsz, GS, withD, tc_rows, 3, 1);
+  const GroupLayout L0 = layout_measure_chunks(s, tsz, GS, withD, tc_rows, 3, 1);
   const int per_sm = 228 * 1024;
   const int want = per_sm / (L0.bytes + 1024);
   const int cand[3][2] = {{6, 2}, {6, 1}, {3, 2}};
   for (const auto& c : cand) {
-    const GroupLayout L = layout_measure_p2(s, tsz, GS, withD, tc_rows, c[0], c[1]);
+    const GroupLayout L = layout_measure_chunks(s, tsz, GS, withD, tc_rows, c[0], c[1]);
     if (L.bytes <= kSmemCap && per_sm / (L.bytes + 1024) >= want) return L;
   }
   return L0;
