@@ -59,15 +59,18 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             print(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        objs = list(ex.map(compile_unit, UNITS))
+    objs = [OUT_DIR / (Path(u).stem + f".{tag}.o") for u in UNITS]
     tmp = OUT_DIR / f"libvmcf.{tag}.so"
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs)], capture_output=True, text=True)
-    for o in objs:
-        o.unlink(missing_ok=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    try:
+        with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+            list(ex.map(compile_unit, UNITS))
+        r = subprocess.run([cc, *ARCH, "-shared", "-o", str(tmp), *map(str, objs)], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, LIB)
+    finally:  # no objects or partial library are left behind, whether or not the build succeeded
+        for o in objs + [tmp]:
+            o.unlink(missing_ok=True)
     return LIB
 
 

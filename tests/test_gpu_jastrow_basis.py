@@ -248,3 +248,27 @@ def test_guided_space_warp_chain_follows_the_oracle(water_jb):
         assert rel(got["F"].ravel(), ref["F"]) < 1e-9
         assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
         assert rel(gotw["F"].ravel(), refw["F"]) < 1e-9
+
+
+@pytest.mark.parametrize("case", ["one electron, one s function", "water, one p shell"])
+def test_smallest_jastrow_bases(case):
+    """Jastrow bases of 1 and 3 functions (rows padded to 4 in the products with Xi), in FP64 against the
+    oracle: the one-electron case on a proton and water with a single p shell on oxygen."""
+    if case.startswith("one"):
+        sx = S.custom_system("H", [1], [[0.0, 0.0, 0.0]], [(0, 0, [0.6], [1.0])], 1, 0, [[1.0]], None,
+                             S.Jastrow(enable_J1=False, enable_J2=False))
+        jb = S.JastrowBasis(np.array([0], np.int32), np.array([0], np.int32), np.array([1], np.int32),
+                            np.array([[0.5, 0.0, 0.0]]), np.array([[1.0, 0.0, 0.0]]), np.array([0.4]), np.array([[0.0]]))
+    else:
+        sx = S.make_system(0)
+        rng = np.random.default_rng(5)
+        G = rng.standard_normal((3, 3)) * 0.2
+        jb = S.JastrowBasis(np.array([0], np.int32), np.array([1], np.int32), np.array([1], np.int32),
+                            np.array([[0.8, 0.0, 0.0]]), np.array([[1.0, 0.0, 0.0]]), rng.uniform(-0.3, 0.3, 3),
+                            G + G.T)
+    sx = S.with_jastrow_basis(sx, jb)
+    pos = S.initial_walkers(sx, 9, seed=3)
+    ref = oracle.Oracle(sx).eval(pos, want=NO_DC)
+    got = gpu_eval(vmcf.System(sx, vmcf.FP64), pos, NO_DC)
+    for k in NO_DC:
+        assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
