@@ -1,9 +1,10 @@
 // Small-system kernels (at most 32 electrons, 16 orbitals per spin): the VMC hot path of
 // arXiv:2511.05222, App. A, laid out so that every lane does independent work.
 //
-//  move_small     one lane per walker: a run of single-electron Metropolis moves with the
-//                 MO row in registers and the walker's inverse in walker-interleaved global
-//                 memory (coalesced across the warp)
+//  move_small     LPW lanes per walker (1, 2, 4 or 8): a run of single-electron Metropolis
+//                 moves with the MO row in registers and the CTA's inverses and positions
+//                 staged walker-interleaved in shared memory (read from and written back to
+//                 walker-interleaved global memory once per launch)
 //  measure_small  one warp per walker, one lane per electron: AOs evaluated shell by shell
 //                 and contracted straight into register MO rows (C rows broadcast from shared
 //                 memory); FP64 Gauss-Jordan inversion and B P B cooperatively in the warp;
