@@ -320,7 +320,7 @@ template <typename T, int GS, bool JB>
 __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const MeasParams& P, unsigned char* base,
                                T* acc_s, double* acc_g, int w) {
   const int t = threadIdx.x % GS;
-  const int Ne = S.Ne, nup = S.nup, K = S.K, M = S.M, nmax = S.nmax;
+  const int Ne = S.Ne, nup = S.nup, K = S.K, M = S.M;
   double* pos = sm_ptr<double>(base, L.pos);
   float* ph = sm_ptr<float>(base, L.ph);
   float* pl = sm_ptr<float>(base, L.pl);
@@ -332,7 +332,6 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   T* Jl = sm_ptr<T>(base, L.Jl);
   T* gd = sm_ptr<T>(base, L.gd);
   T* ao = sm_ptr<T>(base, L.ao);
-  T* mo = sm_ptr<T>(base, L.mo);
   T* frc = sm_ptr<T>(base, L.frc);  // [0,3K) d ln Psi/dR, [3K,6K) dE_L/dR
   T* Ow = sm_ptr<T>(base, L.Ow);
   T* D = sm_ptr<T>(base, L.D);
@@ -478,13 +477,14 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
     wt = 1.0 / (g * g);
   }
 
-  // Pass 2: gradient and Laplacian rows of the MOs, a few electrons at a time; determinant
-  // drift g_e = sum_i G_ei B_ie, l_e = sum_i L_ei B_ie; P_ei = L_ei + 2 gradJ_e . G_ei;
-  // kinetic term -1/2 (l_e + lap J_e + |grad J_e|^2 + 2 grad J_e . g_e).
+  // Pass 2: rows of P = lap(phi) + 2 grad J . grad(phi), a few electrons at a time. P is linear in
+  // C, so each electron needs one AO row, lap psi_mu + 2 grad J_e . grad psi_mu, and one row of the
+  // contraction with C. Kinetic term of electron e: -1/2 (sum_i P_ei B_ie + lap J_e + |grad J_e|^2).
+  // (The determinant drift sum_i grad phi_i(r_e) B_ie is summed in pass 3, from the AO gradients
+  // that the nuclear derivatives need.)
   double ekin = 0.0;  // this thread's share
   {
     const int ns = S.nshell;
-    double* esum = red + 32;  // [4 chunk] per-electron sums, after the group-sum scratch
     for (int sg = 0; sg < 2; ++sg) {
       const int n = sg == 0 ? nup : S.ndn;
       if (n == 0) continue;
@@ -492,40 +492,23 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       const T* Bs = Bt + off;
       const T* C = coefC<T>(S, sg);
       const int ng = GS >= n ? GS / n : 1;
-      const int ch = L.p2_chunk < 2 * ng ? L.p2_chunk : 2 * ng;  // 4 ch rows, at most 8 per thread
+      const int ch = 4 * L.p2_chunk < 8 * ng ? 4 * L.p2_chunk : 8 * ng;  // one AO row each, at most 8 rows per thread
       for (int c0 = 0; c0 < n; c0 += ch) {
         const int nc = n - c0 < ch ? n - c0 : ch;
-        for (int q = t; q < nc * ns; q += GS) {  // AO gradient and Laplacian rows: (electron, shell) pairs
-          const int r = q / ns, sh = q - r * ns;
-          shell_point<T, 1, true>(S, make_epos(pos + 3 * (e0 + c0 + r)), sh, ao + r * 4 * M, M);
+        for (int q = t; q < nc * ns; q += GS) {  // (electron, shell) pairs
+          const int r = q / ns, sh = q - r * ns, e = e0 + c0 + r;
+          shell_point<T, kAoLevelP, true>(S, make_epos(pos + 3 * e), sh, ao + r * M, 0, Jg + 3 * e);
         }
         gsync<GS>();
-        orbital_block<T, GS>(ao, 4 * nc, C, M, n, mo, nmax);  // mo row 4 r + c: component c of electron r
-        gsync<GS>();
-        for (int q = t; q < nc * n; q += GS) {
-          const int r = q / n, i = q - r * n, e = e0 + c0 + r;
-          const T* m = mo + 4 * r * nmax;
-          Pm[off + (c0 + r) * n + i] =
-              m[3 * nmax + i] + T(2) * (Jg[3 * e] * m[i] + Jg[3 * e + 1] * m[nmax + i] + Jg[3 * e + 2] * m[2 * nmax + i]);
-        }
-        if (t < 4 * nc) {  // sum_i (component c of electron r)_i B_{i, el}
-          const int r = t >> 2, el = c0 + r;
-          const T* m = mo + t * nmax;
-          double v = 0.0;
-          for (int i = 0; i < n; ++i) v += (double)(m[i] * Bs[i * n + el]);
-          esum[t] = v;
-        }
+        orbital_block<T, GS>(ao, nc, C, M, n, Pm + off + c0 * n, n);
         gsync<GS>();
         if (t < nc) {
-          const int e = e0 + c0 + t;
-          const double g0 = esum[4 * t], g1 = esum[4 * t + 1], g2 = esum[4 * t + 2], lp = esum[4 * t + 3];
-          gd[3 * e] = (T)g0;
-          gd[3 * e + 1] = (T)g1;
-          gd[3 * e + 2] = (T)g2;
+          const int el = c0 + t, e = e0 + el;
+          const T* pr = Pm + off + el * n;
+          double v = 0.0;
+          for (int i = 0; i < n; ++i) v += (double)(pr[i] * Bs[i * n + el]);
           const double j0 = (double)Jg[3 * e], j1 = (double)Jg[3 * e + 1], j2 = (double)Jg[3 * e + 2];
-          const double jj = j0 * j0 + j1 * j1 + j2 * j2;
-          const double jgd = j0 * g0 + j1 * g1 + j2 * g2;
-          ekin += -0.5 * (lp + (double)Jl[e] + jj + 2.0 * jgd);
+          ekin += -0.5 * (v + (double)Jl[e] + j0 * j0 + j1 * j1 + j2 * j2);
         }
       }
     }
@@ -545,6 +528,8 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   __nv_bfloat16* stg = reinterpret_cast<__nv_bfloat16*>(base + L.Ow);
   T* fa = sm_ptr<T>(base, L.fa);  // [6][M]: AO mu's share of the nuclear derivatives, owned by mu's thread
   for (int i = t; i < 6 * M; i += GS) fa[i] = T(0);
+  // determinant drift grad_e D / D = sum_mu grad psi_mu(r_e) (C B)_{mu e}, summed with the AO terms below
+  for (int i = t; i < 3 * Ne; i += GS) gd[i] = T(0);
   // space warp: the electron derivatives of E_L are wanted (walker sums or outputs)
   const bool warp = S.swct || P.dEL_dr || P.dEL_sw || P.dlnpsi_sw;
   T* er = sm_ptr<T>(base, L.ew);  // [3 Ne]: orbital part of dE_L/dr_e, then all of it (may share f)
@@ -589,6 +574,7 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       }
       gsync<GS>();
       T ce[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};  // this thread's share of sum_mu of the AO terms
+      T gp[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};  // and of the determinant drift
       for (int mu = t; mu < M; mu += GS) {
         T yA[2] = {T(0), T(0)}, yL[2] = {T(0), T(0)};
         for (int i = 0; i < n; ++i) {
@@ -614,9 +600,13 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
           const T hj1 = hxy * j0 + hyy * j1 + hyz * j2;
           const T hj2 = hxz * j0 + hyz * j1 + hzz * j2;
           const T ya = r == 0 ? yA[0] : yA[1], yl = r == 0 ? yL[0] : yL[1];
-          fa[0 * M + mu] -= g0 * yl;
-          fa[1 * M + mu] -= g1 * yl;
-          fa[2 * M + mu] -= g2 * yl;
+          const T gy0 = g0 * yl, gy1 = g1 * yl, gy2 = g2 * yl;
+          fa[0 * M + mu] -= gy0;
+          fa[1 * M + mu] -= gy1;
+          fa[2 * M + mu] -= gy2;
+          gp[r][0] += gy0;
+          gp[r][1] += gy1;
+          gp[r][2] += gy2;
           const T c0 = T(-0.5) * (g0 * ya - yl * (l0 + T(2) * hj0));
           const T c1 = T(-0.5) * (g1 * ya - yl * (l1 + T(2) * hj1));
           const T c2 = T(-0.5) * (g2 * ya - yl * (l2 + T(2) * hj2));
@@ -649,6 +639,15 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
           *reinterpret_cast<uint4*>(dst + (size_t)mu * 16) = *row;
           *row = make_uint4(0, 0, 0, 0);
         }
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (r >= nr) break;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gp[r][k] = warp_sum(gp[r][k]);
+        if ((t & 31) == 0)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) atomicAdd(&gd[3 * (e0 + el + r) + k], gp[r][k]);
       }
       if (warp) {  // an AO moves with its nucleus as -d/dr_e: the same terms, summed over every AO
 #pragma unroll
@@ -990,7 +989,7 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
 // In the shared accumulator, acc[1] and acc[2] hold sums of (E_L - E_ref) and its square;
 // they are turned into sums of E_L and E_L^2 when the CTA flushes.
 template <typename T, int GS, bool JB>
-__global__ void __launch_bounds__(256) measure_kernel(DevSys S, GroupLayout L, MeasParams P, int acc_off) {
+__global__ void __launch_bounds__(256, 2) measure_kernel(DevSys S, GroupLayout L, MeasParams P, int acc_off) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int gpb = blockDim.x / GS, gid = threadIdx.x / GS;
   unsigned char* base = smem + gid * L.bytes;

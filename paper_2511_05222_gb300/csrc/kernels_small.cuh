@@ -5,10 +5,12 @@
 //                 moves with the MO row in registers and the CTA's inverses and positions
 //                 staged walker-interleaved in shared memory (read from and written back to
 //                 walker-interleaved global memory once per launch)
-//  measure_small  one warp per walker, one lane per electron: AOs evaluated shell by shell
-//                 and contracted straight into register MO rows (C rows broadcast from shared
-//                 memory); FP64 Gauss-Jordan inversion and B P B cooperatively in the warp;
-//                 E_L, adjoint nuclear derivatives, O and the walker sums
+//  measure_small  one warp per walker, one lane per electron: two sweeps over the AOs, shell
+//                 by shell, contracted straight into register rows (C rows broadcast from
+//                 shared memory): the Slater row and the row of P = lap(phi) + 2 grad J .
+//                 grad(phi), then (after the FP64 Gauss-Jordan inversion and B P B,
+//                 cooperatively in the warp) the adjoint nuclear derivatives, the determinant
+//                 drift and O; E_L and the walker sums
 //
 // Walker state on this path: positions [3 Ne][W] (double, plus a float-float copy in mixed
 // mode) and inverses [n_up^2 + n_dn^2][W], walker index fastest.
@@ -577,58 +579,12 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       *la = 0.0;
       *sgn = 1.0;
     }
-    // ---- pass 1: Slater rows (one per lane) -> FP64 -> Gauss-Jordan per spin
-    if (has_e) {
-      T row[NM];
-#pragma unroll
-      for (int i = 0; i < NM; ++i) row[i] = T(0);
-      const T* Csg = Cs + sg * M * c_stride<NM>();
-      for (int s = 0; s < S.nshell; ++s) {
-        const int4 sh = __ldg(S.shell + s);
-        T d[3];
-        R2FF r2ff{0.f, 0.f};
-        const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
-        const Radial<T> rs = radial_sums<T, 0>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
-        for (int m = 0; m < 2 * sh.y + 1; ++m) {
-          T Pa, g[3], h[6];
-          angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
-          axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * c_stride<NM>());
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < NM; ++i)
-        if (i < n) Ad[off + el * n + i] = (double)row[i];
-    }
-    __syncwarp();
-    gj_inverse_pair(Ad, nup, Ad + nup * nup, ndn, S.nmax, piv, f, flag, la, sgn, P.logpsi != nullptr);
-    if (static_cast<void*>(Bf) != static_cast<void*>(Ad))
-      for (int i = lane; i < S.nB; i += 32) Bf[i] = (T)Ad[i];
-    __syncwarp();
-    if (P.Bout && P.mode != 1) {
-      T* Bg = reinterpret_cast<T*>(P.Bout);
-      for (int i = lane; i < S.nB; i += 32) Bg[(size_t)i * W + w] = Bf[i];
-    }
-    if (lane == 0 && *flag) atomicAdd(&P.counters[0], 1ull);
-    // reweighting factor |Psi / Psi_G|^2 = 1 / g^2 of a guided chain (g = max(1, eps sqrt(S)), S the
-    // sum of the squared entries of the fresh inverses); every walker sum below carries it
-    double wt = 1.0;
-    if (accum && P.eps > 0.0) {
-      double sq = 0.0;
-      for (int i = lane; i < S.nB; i += 32) sq += (double)Bf[i] * (double)Bf[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-      const double g = fmax(1.0, P.eps * sqrt(sq));
-      wt = 1.0 / (g * g);
-    }
-    if (P.mode == 0) {
-      __syncwarp();
-      continue;
-    }
-
+    __syncwarp();  // every electron's position visible to the warp
+    const bool full = P.mode != 0;  // mode 0 only rebuilds the inverses
     // ---- Jastrow and potentials (lane = electron)
     T jg[3] = {T(0), T(0), T(0)}, jl = T(0);
     double vpart[4] = {0.0, 0.0, 0.0, 0.0};  // kinetic, V_ee, V_en, J
-    if (has_e) {
+    if (full && has_e) {
       T vee = 0, ven = 0, jv = 0;
       for (int j = 0; j < Ne; ++j) {
         if (j == e) continue;
@@ -674,45 +630,93 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       vpart[3] = (double)jv;
     }
 
-    // ---- pass 2: gradient and Laplacian rows; drift g_e, l_e; P row; kinetic term
-    T bc[NM];  // column el of B^s: B_{i, el}
-#pragma unroll
-    for (int i = 0; i < NM; ++i) bc[i] = (has_e && i < n) ? Bf[off + i * n + el] : T(0);
-    T gd[3] = {T(0), T(0), T(0)};
+    // ---- pass 1: the Slater row (one per lane) -> FP64 -> Gauss-Jordan per spin; when measuring, in
+    // the same sweep over the AOs, the row of P = lap(phi) + 2 grad(J) . grad(phi) that the adjoint
+    // weights B P B and the kinetic term need (linear in C, so one coefficient per AO:
+    // P_{e i} = sum_mu C_{mu i} (lap psi_mu + 2 grad J . grad psi_mu))
     if (has_e) {
-      T G0[NM], G1[NM], G2[NM], Lr[NM];
+      T row[NM];
 #pragma unroll
-      for (int i = 0; i < NM; ++i) G0[i] = G1[i] = G2[i] = Lr[i] = T(0);
+      for (int i = 0; i < NM; ++i) row[i] = T(0);
       const T* Csg = Cs + sg * M * c_stride<NM>();
-      for (int s = 0; s < S.nshell; ++s) {
-        const int4 sh = __ldg(S.shell + s);
-        T d[3];
-        R2FF r2ff{0.f, 0.f};
-        const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
-        const Radial<T> rs = radial_sums<T, 1>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
-        for (int m = 0; m < 2 * sh.y + 1; ++m) {
-          T Pa, g[3], h[6];
-          angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
-          const T* cr = Csg + (sh.w + m) * c_stride<NM>();
-          axpy_row<T, NM>(G0, g[0] * rs.R0 + Pa * d[0] * rs.R1, cr);
-          axpy_row<T, NM>(G1, g[1] * rs.R0 + Pa * d[1] * rs.R1, cr);
-          axpy_row<T, NM>(G2, g[2] * rs.R0 + Pa * d[2] * rs.R1, cr);
-          axpy_row<T, NM>(Lr, Pa * rs.LF, cr);
+      if (!full) {
+        for (int s = 0; s < S.nshell; ++s) {
+          const int4 sh = __ldg(S.shell + s);
+          T d[3];
+          R2FF r2ff{0.f, 0.f};
+          const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
+          const Radial<T> rs = radial_sums<T, 0>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
+          for (int m = 0; m < 2 * sh.y + 1; ++m) {
+            T Pa, g[3], h[6];
+            angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
+            axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * c_stride<NM>());
+          }
         }
-      }
-      T lsum = 0;
+      } else {
+        T prow[NM];
 #pragma unroll
-      for (int i = 0; i < NM; ++i) {
-        gd[0] += G0[i] * bc[i];
-        gd[1] += G1[i] * bc[i];
-        gd[2] += G2[i] * bc[i];
-        lsum += Lr[i] * bc[i];
+        for (int i = 0; i < NM; ++i) prow[i] = T(0);
+        for (int s = 0; s < S.nshell; ++s) {
+          const int4 sh = __ldg(S.shell + s);
+          T d[3];
+          R2FF r2ff{0.f, 0.f};
+          const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
+          const Radial<T> rs = radial_sums<T, 1>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
+          const T xjR1 = T(2) * (d[0] * jg[0] + d[1] * jg[1] + d[2] * jg[2]) * rs.R1;
+          for (int m = 0; m < 2 * sh.y + 1; ++m) {
+            T Pa, g[3], h[6];
+            angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
+            const T* cr = Csg + (sh.w + m) * c_stride<NM>();
+            axpy_row<T, NM>(row, Pa * rs.R0, cr);
+            // lap psi = P LF; grad psi = g R0 + P d R1
+            const T gj2 = T(2) * (g[0] * jg[0] + g[1] * jg[1] + g[2] * jg[2]);
+            axpy_row<T, NM>(prow, Pa * (rs.LF + xjR1) + gj2 * rs.R0, cr);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < NM; ++i)
+          if (i < n) Pm[off + el * n + i] = prow[i];
       }
 #pragma unroll
       for (int i = 0; i < NM; ++i)
-        if (i < n) Pm[off + el * n + i] = Lr[i] + T(2) * (jg[0] * G0[i] + jg[1] * G1[i] + jg[2] * G2[i]);
-      const T te = lsum + jl + (jg[0] * jg[0] + jg[1] * jg[1] + jg[2] * jg[2]) +
-                   T(2) * (jg[0] * gd[0] + jg[1] * gd[1] + jg[2] * gd[2]);
+        if (i < n) Ad[off + el * n + i] = (double)row[i];
+    }
+    __syncwarp();
+    gj_inverse_pair(Ad, nup, Ad + nup * nup, ndn, S.nmax, piv, f, flag, la, sgn, P.logpsi != nullptr);
+    if (static_cast<void*>(Bf) != static_cast<void*>(Ad))
+      for (int i = lane; i < S.nB; i += 32) Bf[i] = (T)Ad[i];
+    __syncwarp();
+    if (P.Bout && P.mode != 1) {
+      T* Bg = reinterpret_cast<T*>(P.Bout);
+      for (int i = lane; i < S.nB; i += 32) Bg[(size_t)i * W + w] = Bf[i];
+    }
+    if (lane == 0 && *flag) atomicAdd(&P.counters[0], 1ull);
+    // reweighting factor |Psi / Psi_G|^2 = 1 / g^2 of a guided chain (g = max(1, eps sqrt(S)), S the
+    // sum of the squared entries of the fresh inverses); every walker sum below carries it
+    double wt = 1.0;
+    if (accum && P.eps > 0.0) {
+      double sq = 0.0;
+      for (int i = lane; i < S.nB; i += 32) sq += (double)Bf[i] * (double)Bf[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      const double g = fmax(1.0, P.eps * sqrt(sq));
+      wt = 1.0 / (g * g);
+    }
+    if (P.mode == 0) {
+      __syncwarp();
+      continue;
+    }
+
+    // ---- kinetic term: -1/2 (lap Psi / Psi) of electron e = -1/2 (sum_i P_{e i} B_{i e} + lap J + |grad J|^2)
+    T bc[NM];  // column el of B^s: B_{i, el}
+#pragma unroll
+    for (int i = 0; i < NM; ++i) bc[i] = (has_e && i < n) ? Bf[off + i * n + el] : T(0);
+    if (has_e) {
+      T ps = 0;
+#pragma unroll
+      for (int i = 0; i < NM; ++i)
+        if (i < n) ps += Pm[off + el * n + i] * bc[i];
+      const T te = ps + jl + (jg[0] * jg[0] + jg[1] * jg[1] + jg[2] * jg[2]);
       vpart[0] = -0.5 * (double)te;
     }
     warp_sum_f<4>(vpart);
@@ -749,13 +753,21 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
 #pragma unroll
     for (int i = 0; i < NM; ++i) xr[i] = (has_e && i < n) ? Pm[off + el * n + i] : T(0);
     T fl[3] = {T(0), T(0), T(0)}, fe[3] = {T(0), T(0), T(0)};
-    T fr[3] = {T(0), T(0), T(0)};  // sum over every AO of the dE_L terms of this electron (space warp)
+    T fr[3] = {T(0), T(0), T(0)};  // sum over every AO of the dE_L terms of this electron (space warp): fe summed over nuclei
+    // determinant drift grad_e D / D = sum_i grad phi_i(r_e) B_{i e} = sum_mu grad psi_mu(r_e) (C B)_{mu e}:
+    // the sum over every AO of the products that fl collects per nucleus (with the opposite sign)
+    T gd[3] = {T(0), T(0), T(0)};
     int cur = -1;
     int chunk0 = 0, chunk_n = 0;  // AOs [chunk0, chunk0 + chunk_n) pending in phi
     const T* Csg = Cs + sg * M * c_stride<NM>();
     auto flush_centre = [&](int I) {
       float v6f[6];
       double v6d[6];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        gd[k] -= fl[k];
+        fr[k] += fe[k];
+      }
       if constexpr (sizeof(T) == 4) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -854,7 +866,6 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
             fl[k] -= gv * yL;
             const T cde = T(-0.5) * (gv * yA - yL * (gl + T(2) * hj));
             fe[k] += cde;
-            fr[k] += cde;
           }
           if (tc)
             reinterpret_cast<__nv_bfloat16*>(P.phiT[sg])[((size_t)w * P.Mp + sh.w + m) * 16 + el] =

@@ -172,10 +172,9 @@ GroupLayout layout_measure_chunks(const vmcf_system_s& s, size_t tsz, int GS, bo
   L.Jl = take((int)tsz * s.Ne);
   L.gd = take((int)tsz * 3 * s.Ne);
   L.ao_rows = 8;
-  L.p2_chunk = p2;  // electrons per chunk of the gradient/Laplacian pass: 4 AO rows each
+  L.p2_chunk = p2;  // 4 p2 electrons per chunk of the P-row pass: one AO row each
   L.p3_chunk = p3;  // electrons per step of the adjoint/force pass: 14 AO rows each
   L.ao = take((int)tsz * std::max(14 * L.p3_chunk, 4 * L.p2_chunk) * s.M);
-  L.mo = take((int)tsz * 4 * L.p2_chunk * s.nmax);
   L.frc = take((int)tsz * 6 * s.K);
   L.fa = take((int)tsz * 6 * s.M);
   // space warp: dE_L/dr_e [3 Ne] (the kappa sums go to the AO buffer, free by then); in mixed mode
@@ -206,10 +205,9 @@ GroupLayout layout_measure_chunks(const vmcf_system_s& s, size_t tsz, int GS, bo
 }
 
 // Larger electron chunks where the layout fits and keeps as many walker groups per SM as the smallest
-// (three electrons per gradient/Laplacian chunk, one per adjoint/force step): six per gradient/Laplacian
-// chunk (half the chunks, each coefficient load shared by twice the rows) and two per adjoint/force step
-// (half the steps and barriers, each coefficient load shared by both electrons), in that order of
-// preference.
+// (twelve electrons per P-row chunk, one per adjoint/force step): 24 per P-row chunk (half the chunks,
+// each coefficient load shared by twice the rows) and two per adjoint/force step (half the steps and
+// barriers, each coefficient load shared by both electrons), in that order of preference.
 GroupLayout layout_measure(const vmcf_system_s& s, size_t tsz, int GS, bool withD, int tc_rows = 0) {
   const GroupLayout L0 = layout_measure_chunks(s, tsz, GS, withD, tc_rows, 3, 1);
   const int per_sm = 228 * 1024;

@@ -258,16 +258,20 @@ __device__ __forceinline__ EPos make_epos(const double* r) {
 
 // Shell s at displacement (x, y, z) = r - R_center. LEVEL 0: value. LEVEL 1: gradient (3)
 // and Laplacian. LEVEL 2: value, gradient (3), Laplacian, Hessian (xx yy zz xy xz yz),
-// gradient of the Laplacian (3). out[c * stride + ao] for component c.
+// gradient of the Laplacian (3). LEVEL kAoLevelP: the one row lap psi + 2 j . grad psi for the
+// vector j (jv), the AO coefficients of a row of P = lap(phi) + 2 grad J . grad(phi), which is
+// linear in C. out[c * stride + ao] for component c.
 // With e_k = c_k exp(-a_k r^2), R0 = sum e_k, R1 = sum -2a_k e_k, R2 = sum 4a_k^2 e_k:
 //   d_i F = x_i R1, d_i d_j F = x_i x_j R2 + delta_ij R1; for a harmonic homogeneous P of
 //   degree l: lap(P F) = P sum_k -2a_k e_k ((2l+3) - 2 a_k r^2) and
 //   d_k lap(P F) = P_k lap F + P x_k sum_k 4a_k^2 e_k ((2l+5) - 2 a_k r^2).
 // Each primitive's factor (2l+3) - 2 a r^2 is where the Laplacian cancels; for primitives
 // marked sharp (mixed mode only) a r^2 and the factors are formed in double from r2d.
+constexpr int kAoLevelP = 3;
+
 template <typename T, int LEVEL>
 __device__ __forceinline__ void shell_eval(const DevSys& S, int s, T x, T y, T z, int smask, R2FF r2ff, T* out,
-                                           int stride) {
+                                           int stride, const T* jv = nullptr) {
   const int4 sh = __ldg(S.shell + s);
   const int l = sh.y, np = sh.z, ao0 = sh.w;
   const T r2 = x * x + y * y + z * z;
@@ -293,7 +297,7 @@ __device__ __forceinline__ void shell_eval(const DevSys& S, int s, T x, T y, T z
       const T m2ae = T(-2) * a * e;
       R1 += m2ae;
       LF += m2ae * f3;
-      if (LEVEL >= 2) {
+      if (LEVEL == 2) {
         const T a4e = T(4) * a * a * e;
         R2 += a4e;
         T3 += a4e * f5;
@@ -312,7 +316,9 @@ __device__ __forceinline__ void shell_eval(const DevSys& S, int s, T x, T y, T z
       T grad[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) grad[i] = g[i] * R0 + P * xs[i] * R1;
-      if (LEVEL == 1) {
+      if (LEVEL == kAoLevelP) {
+        out[ao] = P * LF + T(2) * (jv[0] * grad[0] + jv[1] * grad[1] + jv[2] * grad[2]);
+      } else if (LEVEL == 1) {
         out[0 * stride + ao] = grad[0];
         out[1 * stride + ao] = grad[1];
         out[2 * stride + ao] = grad[2];
@@ -355,7 +361,8 @@ __device__ __forceinline__ void disp_nuc<float>(const DevSys& S, const EPos& p, 
 // AO components of shell s at one point. SHARP: in mixed mode, form a r^2 of sharp
 // primitives in float-float arithmetic.
 template <typename T, int LEVEL, bool SHARP>
-__device__ __forceinline__ void shell_point(const DevSys& S, const EPos& p, int s, T* out, int stride) {
+__device__ __forceinline__ void shell_point(const DevSys& S, const EPos& p, int s, T* out, int stride,
+                                            const T* jv = nullptr) {
   {
     const int c = __ldg(S.shell + s).x;
     T d[3];
@@ -378,7 +385,7 @@ __device__ __forceinline__ void shell_point(const DevSys& S, const EPos& p, int 
     } else {
       disp_nuc<T>(S, p, c, d);
     }
-    shell_eval<T, LEVEL>(S, s, d[0], d[1], d[2], smask, r2ff, out, stride);
+    shell_eval<T, LEVEL>(S, s, d[0], d[1], d[2], smask, r2ff, out, stride, jv);
   }
 }
 

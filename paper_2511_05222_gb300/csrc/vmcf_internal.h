@@ -10,9 +10,9 @@ namespace vmcf {
 
 // Byte offsets of one walker group's shared-memory region; computed on the host.
 struct GroupLayout {
-  int pos, ph, pl, Bd, Bt, P, Q, Jg, Jl, gd, ao, mo, frc, fa, ew, Ow, D, piv, f, red, scal, row, wv, col;
+  int pos, ph, pl, Bd, Bt, P, Q, Jg, Jl, gd, ao, frc, fa, ew, Ow, D, piv, f, red, scal, row, wv, col;
   int ao_rows;   // AO rows of M values the ao buffer holds (electrons per Slater-build chunk)
-  int p2_chunk;  // electrons per chunk of the gradient/Laplacian pass (4 AO rows each)
+  int p2_chunk;  // the P-row pass takes 4 p2_chunk electrons per chunk (one AO row each)
   int p3_chunk;  // electrons per step of the adjoint/force pass (14 AO rows each): 1 or 2
   int jw;        // AO-expanded Jastrow work space (systems with a Jastrow basis, else 0)
   int jch;       // electrons per chunk of the Jastrow-basis products (measurement)

@@ -6,7 +6,11 @@ followed by one evaluation of E_L, d ln Psi/dR, dE_L/dR and O with its walker su
 
 Only what the method has to compute is counted (one AO evaluation per electron with all
 derivatives, one MO contraction, one inversion per spin, one adjoint sweep); recomputation
-done by an implementation is not counted, so it lowers the achieved fraction. Counts are
+done by an implementation is not counted, so it lowers the achieved fraction. The MO
+contraction of the evaluation is two rows per electron: the Slater row and the row of
+P = lap(phi) + 2 grad J . grad(phi), which is linear in C (one AO coefficient per function);
+the gradient and Laplacian rows themselves are never needed, since the kinetic term is
+sum_i P_ei B_ie + lap J + |grad J|^2 and the determinant drift comes out of the force terms. Counts are
 flops (an FMA is 2) split by the pipe that executes them in mixed mode: FP64 (inversion,
 ratio dot products) and FP32 (everything else), plus exponentials (one per primitive per
 electron per pass) counted separately for the SFU.
@@ -34,11 +38,12 @@ def per_walker_eval(K: int, M: int, n_up: int, n_dn: int, nprim: int, acc: float
     measure = {
         "exp": Ne * nprim,
         "fp32": (Ne * (8 * nprim + 40 * M)                       # AO value, gradient, Laplacian, Hessian, grad-Laplacian
-                 + sum(10 * M * n for n in ns)                   # MO rows: value, gradient (3), Laplacian
+                 + Ne * 8 * M                                    # AO coefficients lap psi + 2 grad J . grad psi of the P row
+                 + sum(4 * M * n for n in ns)                    # MO rows: Slater row and P = lap phi + 2 grad J . grad phi
                  + 25 * (Ne * (Ne - 1) // 2) + 25 * Ne * K       # Jastrow and potentials
-                 + sum(8 * n for n in ns)                        # drift and Laplacian ratios
+                 + sum(2 * n for n in ns)                        # kinetic ratio sum_i P_ei B_ie
                  + sum(4 * n ** 3 for n in spins)                # adjoint weights B P B
-                 + sum(4 * M * n for n in ns) + 30 * Ne * M      # back-projection and force contraction
+                 + sum(4 * M * n for n in ns) + 36 * Ne * M      # back-projection, force contraction, determinant drift
                  + 40 * Ne * K                                   # e-n Jastrow and V_en derivatives
                  + sum(2 * M * n for n in ns)                    # O
                  + sum(4 * M * n for n in spins) + 18 * K),      # walker sums
