@@ -489,7 +489,10 @@ int vmcf_batch_autotune(vmcf_batch_t b, double step_sigma, int refresh_k, void* 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaEvent_t t0, t1;
   BATCH_CUDA(cudaEventCreate(&t0));
-  BATCH_CUDA(cudaEventCreate(&t1));
+  if (cudaError_t e = cudaEventCreate(&t1); e != cudaSuccess) {
+    cudaEventDestroy(t0);
+    return cuda_fail(e, "cudaEventCreate(&t1)");
+  }
   const int nb = (int)b->bucket_shape[0].size();
   int rc = VMCF_OK;
   // per bucket and phase: one sweep (phase 0) or one evaluation without sums (phase 1) of
