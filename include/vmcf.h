@@ -179,8 +179,9 @@ int vmcf_sample(vmcf_system_t sys, vmcf_walkers_t wk, int n_sweeps, double step_
  * one measured sweep of vmcf_sample does). Used for estimators on fixed configurations. */
 int vmcf_measure(vmcf_system_t sys, vmcf_walkers_t wk, void* stream);
 
-/* Fixed-walker evaluation (no sampling). pos: device [W][Ne][3]. Outputs are device
- * buffers owned by the caller; any may be NULL:
+/* Fixed-walker evaluation (no sampling). pos: device [W][Ne][3], W >= 0 (W = 0: nothing is
+ * read or written and pos may be NULL). Outputs are device buffers owned by the caller; any may
+ * be NULL:
  *   EL [W], logpsi [W] (ln|Psi|), dlnpsi_dR [W][K][3], dEL_dR [W][K][3],
  *   O [W][M*(n_up+n_dn)], dEL_dC [W][M*(n_up+n_dn)] (the explicit dE_L/dC, for tests). */
 int vmcf_evaluate(vmcf_system_t sys, const double* pos, int W, double* EL, double* logpsi,
@@ -217,7 +218,7 @@ int vmcf_finish_estimators(const double* blocks, int nblocks, int K, int M, int 
  * vmcf_reduce_warp: the same from a walker set's own sums (synchronises).
  * vmcf_evaluate_warp: per-walker values at device positions pos [W][Ne][3] (any output may be
  *   NULL; device, caller-owned): dE_L/dr_e [W][Ne][3], dE_L^sw/dR [W][K][3], dlnPsi^sw/dR
- *   [W][K][3]. Works with or without VMCF_SPACE_WARP. */
+ *   [W][K][3]. Works with or without VMCF_SPACE_WARP. W = 0: nothing is read or written. */
 int vmcf_finish_warp(const double* blocks, int nblocks, int stride, int K, int M, int n_up, int n_dn, double e_ref,
                      double* F, double* F_err);
 int vmcf_reduce_warp(vmcf_system_t sys, vmcf_walkers_t wk, double* F, double* F_err, void* stream);

@@ -1122,8 +1122,9 @@ int vmcf_measure(vmcf_system_t s, vmcf_walkers_t wk, void* stream) {
 
 int vmcf_evaluate(vmcf_system_t s, const double* pos, int W, double* EL, double* logpsi, double* dlnpsi_dR,
                   double* dEL_dR, double* O, double* dEL_dC, void* stream) {
-  if (!s || !pos || W < 0) return fail(VMCF_EINVAL, "bad arguments");
-  if (W == 0) return VMCF_OK;
+  if (!s || W < 0) return fail(VMCF_EINVAL, "bad arguments");
+  if (W == 0) return VMCF_OK;  // nothing to read or write (pos may be NULL)
+  if (!pos) return fail(VMCF_EINVAL, "NULL positions");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool withD = dEL_dC != nullptr;
   if (s->small && !withD) {
@@ -1317,8 +1318,9 @@ int vmcf_reduce_warp(vmcf_system_t s, vmcf_walkers_t wk, double* F, double* F_er
 
 int vmcf_evaluate_warp(vmcf_system_t s, const double* pos, int W, double* dEL_dr, double* dEL_sw, double* dlnpsi_sw,
                        void* stream) {
-  if (!s || !pos || W < 0) return fail(VMCF_EINVAL, "bad arguments");
-  if (W == 0) return VMCF_OK;
+  if (!s || W < 0) return fail(VMCF_EINVAL, "bad arguments");
+  if (W == 0) return VMCF_OK;  // nothing to read or write (pos may be NULL)
+  if (!pos) return fail(VMCF_EINVAL, "NULL positions");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   MeasParams M{};
   M.pos = pos;

@@ -1,0 +1,99 @@
+"""Edge cases of the CUDA path, through the C ABI, against the FP64 oracle: an empty walker set
+(no work and no error), the largest system the one-warp-per-walker kernels take (32 electrons
+and 16 orbitals per spin: every lane holds an electron and the register rows are full), an
+open-shell system (n_up = n_dn + 1) in both kernel families, and a run of zero sweeps."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_05222_gb300 import systems as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2511_05222_gb300 import vmcf  # noqa: E402
+
+KEYS = ("EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O")
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def gpu_eval(system, pos, want=KEYS):
+    out = vmcf.vmcf_evaluate(system, torch.as_tensor(np.ascontiguousarray(pos), device="cuda"), want=want)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def molecule(name, Z, n_up, n_dn, seed):
+    """A covalent-walk molecule of the seeded recipe with the given spin split."""
+    Z = np.asarray(Z, np.int32)
+    R = S.covalent_walk(list(Z), np.random.default_rng([7000, seed, 0]))
+    c, l, npr, e, co = S.basis_rule(Z, np.random.default_rng([7000, seed, 1]))
+    sx = S.System(name, Z, R, c, l, npr, e, co, n_up, n_dn, np.zeros((0, 0)), np.zeros((0, 0)), S.Jastrow())
+    Sm = S.overlap_matrix(sx)
+    rng = np.random.default_rng([7000, seed, 2])
+    sx.C_up = S.orthonormal_orbitals(Sm, n_up, rng)
+    sx.C_dn = S.orthonormal_orbitals(Sm, n_dn, rng)
+    sx.S = Sm
+    return sx
+
+
+@pytest.mark.parametrize("force_group", [False, True])
+def test_empty_walker_set_is_no_work(sys0, force_group):
+    g = vmcf.System(sys0, vmcf.FP64, force_group=force_group)
+    out = gpu_eval(g, np.zeros((0, sys0.Ne, 3)), want=KEYS)
+    for k in KEYS:
+        assert out[k].shape[0] == 0
+    warp = vmcf.vmcf_evaluate_warp(g, torch.zeros((0, sys0.Ne, 3), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    assert all(v.shape[0] == 0 for v in warp.values())
+
+
+def test_full_warp_system_matches_the_oracle():
+    """C2O2H4: 32 electrons, 16 orbitals per spin, 76 AOs."""
+    sx = molecule("C2O2H4", [6, 6, 8, 8, 1, 1, 1, 1], 16, 16, seed=1)
+    assert (sx.Ne, sx.n_up) == (32, 16)
+    o = oracle.Oracle(sx)
+    st = o.new_state(S.initial_walkers(sx, 96, seed=3), key=(5222, 11))
+    o.sample(st, 10)
+    pos = st["pos"]
+    ref = o.eval(pos, want=KEYS)
+    for force_group in (False, True):
+        got = gpu_eval(vmcf.System(sx, vmcf.FP64, force_group=force_group), pos)
+        for k in KEYS:
+            assert rel(got[k], ref[k]) < 1e-10, (force_group, k, rel(got[k], ref[k]))
+    got = gpu_eval(vmcf.System(sx, vmcf.MIXED), pos, ("EL",))["EL"]
+    r = np.abs(got - ref["EL"]) / np.maximum(np.abs(ref["EL"]), abs(ref["EL"].mean()))
+    assert np.median(r) < 1e-6
+    assert np.mean(r < 1e-5) > 0.95, np.sort(r)[-10:]
+    # a short FP64 chain on the small-system kernels follows the oracle's
+    wk = vmcf.Walkers(vmcf.System(sx, vmcf.FP64), pos, key=(5222, 12), nblocks=4)
+    wk.sample(2, 0.3, 26)
+    st2 = o.new_state(pos, key=(5222, 12))
+    o.sample(st2, 2, sigma=0.3, refresh_k=26)
+    ok = st2["margin"] >= 1e-9
+    assert ok.sum() >= 94
+    assert np.abs(wk.positions()[ok] - st2["pos"][ok]).max() < 1e-9
+
+
+@pytest.mark.parametrize("force_group", [False, True])
+def test_open_shell_system_matches_the_oracle(force_group):
+    """CH3 radical: 9 electrons, 5 up and 4 down (spin blocks of different size)."""
+    sx = molecule("CH3", [6, 1, 1, 1], 5, 4, seed=2)
+    pos = S.initial_walkers(sx, 48, seed=4)
+    ref = oracle.Oracle(sx).eval(pos, want=KEYS)
+    got = gpu_eval(vmcf.System(sx, vmcf.FP64, force_group=force_group), pos)
+    for k in KEYS:
+        assert rel(got[k], ref[k]) < 1e-10, (k, rel(got[k], ref[k]))
+
+
+def test_zero_sweeps_leave_the_walkers_unchanged(sys0):
+    pos = S.initial_walkers(sys0, 32, seed=6)
+    wk = vmcf.Walkers(vmcf.System(sys0, vmcf.MIXED), pos, nblocks=4)
+    before = wk.counters()
+    wk.sample(0, 0.3, 26)
+    np.testing.assert_array_equal(wk.positions(), pos)
+    assert wk.counters() == before
