@@ -1,7 +1,8 @@
 """Edge cases of the CUDA path, through the C ABI, against the FP64 oracle: an empty walker set
 (no work and no error), the largest system the one-warp-per-walker kernels take (32 electrons
 and 16 orbitals per spin: every lane holds an electron and the register rows are full), an
-open-shell system (n_up = n_dn + 1) in both kernel families, and a run of zero sweeps."""
+open-shell system (n_up = n_dn + 1) in both kernel families, a run of zero sweeps, and a walker
+count that fills no CTA, warp or jackknife block evenly."""
 import numpy as np
 import pytest
 
@@ -97,3 +98,43 @@ def test_zero_sweeps_leave_the_walkers_unchanged(sys0):
     wk.sample(0, 0.3, 26)
     np.testing.assert_array_equal(wk.positions(), pos)
     assert wk.counters() == before
+
+
+def _block_map(W, nb):
+    blk = np.zeros(W, int)
+    for b in range(nb):
+        blk[(W * b) // nb:(W * (b + 1)) // nb] = b
+    return blk
+
+
+@pytest.mark.parametrize("force_group", [False, True])
+def test_ragged_walker_count_chain_and_estimators(sys0, force_group):
+    """37 walkers in 5 jackknife blocks of 7 or 8 (a count that fills no CTA, warp or block evenly):
+    the FP64 chain and the measured estimators follow the oracle."""
+    from oracle import estimators
+
+    W, nb, warm, meas, e_ref = 37, 5, 2, 2, -76.0
+    pos = S.initial_walkers(sys0, W, seed=12)
+    o = oracle.Oracle(sys0)
+    st = o.new_state(pos, key=(5222, 13))
+    o.sample(st, warm)
+    wk = vmcf.Walkers(vmcf.System(sys0, vmcf.FP64, force_group=force_group), pos, key=(5222, 13), nblocks=nb)
+    wk.sample(warm, measure=False)
+    wk.reset_accumulators(e_ref)
+    wk.sample(meas, measure=True)
+    sums = estimators.new_sums(nb, sys0.K, o.nO)
+    blk = _block_map(W, nb)
+    for _ in range(meas):
+        o.sample(st, 1)
+        o.force_refresh(st)
+        out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+        estimators.accumulate(sums, blk, out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], e_ref)
+    assert st["margin"].min() >= 1e-9
+    assert np.abs(wk.positions() - st["pos"]).max() < 1e-9
+    np.testing.assert_array_equal(wk.block_sums()[:, 0], sums["n"])
+    ref = estimators.finish(sums, e_ref)
+    got = wk.reduce_estimators()
+    assert abs(got["E"] - ref["E"]) < 1e-10 * abs(ref["E"])
+    assert rel(got["F"].ravel(), ref["F"]) < 1e-9
+    assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
+    assert abs(got["E_err"] - ref["E_err"]) < 1e-8 * ref["E_err"]
