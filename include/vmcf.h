@@ -242,6 +242,40 @@ int vmcf_finish_covariance(const double* blocks, int nblocks, int K, int M, int 
 /* Counters (synchronises the stream). */
 int vmcf_status_counters(vmcf_walkers_t wk, vmcf_counters* out, void* stream);
 
+/* Checkpoint and resume of a walker set, between library calls. A checkpoint holds everything
+ * the chains and the accumulated sums depend on: positions, the current inverses (as the
+ * Sherman-Morrison updates left them, so a chain resumes anywhere, not only after a
+ * re-inversion), accepted and rejected move counts, the status counters, the per-CTA walker sums
+ * (and the tensor-core sum slots of the mixed path), the chain clock, E_ref, the guiding
+ * threshold and the Philox key and walker-id base. The Philox counter of a move is (walker id,
+ * sweep, electron, draw), so a walker set that loads a checkpoint draws exactly the numbers the
+ * saved one would have drawn: its chains continue bit for bit; its sums continue to within the
+ * ordering of the in-CTA accumulation.
+ * Layout of the host buffer: one vmcf_walkers_state header, then its segments back to back in
+ * the order of `bytes` (raw device contents, in layouts private to the library; 0 bytes: segment
+ * absent). The header is public so that callers can read the chain clock and E_ref.
+ * vmcf_walkers_state_bytes: the buffer size for this walker set.
+ * vmcf_walkers_save: writes the checkpoint into host buf [bytes] (synchronises the stream).
+ * vmcf_walkers_load: restores it into a walker set created for the same system with the same W
+ *   and nblocks (VMCF_EINVAL if the header or any segment size differs; nothing is changed
+ *   then); synchronises the stream. */
+typedef struct {
+  char magic[8];        /* "vmcfwk1" (NUL-terminated) */
+  int32_t W, nblocks;   /* walkers, jackknife blocks */
+  int32_t Ne, n_up, n_dn, M, K, precision; /* the system (precision without flags) */
+  int32_t counter;      /* attempted moves since the last re-inversion */
+  int32_t reserved;
+  uint64_t sweep;       /* sweeps done (the Philox counter's sweep word) */
+  uint64_t measured;    /* sweeps accumulated into the sums */
+  uint64_t key0, key1, wid0;
+  double e_ref, eps;
+  uint64_t bytes[8];    /* positions, inverses, accepted, rejected, status counters, per-CTA sums,
+                           float-float positions, tensor-core sum slots */
+} vmcf_walkers_state;
+int vmcf_walkers_state_bytes(vmcf_walkers_t wk, uint64_t* bytes);
+int vmcf_walkers_save(vmcf_walkers_t wk, void* buf, uint64_t bytes, void* stream);
+int vmcf_walkers_load(vmcf_walkers_t wk, const void* buf, uint64_t bytes, void* stream);
+
 /* Fixed-walker evaluation reduced to walker sums, allocating nothing (the paper has no
  * counterpart; this is a deployment variant of vmcf_evaluate plus vmcf_block_sums).
  * It is for callers that must not allocate GPU memory while they run, for example code

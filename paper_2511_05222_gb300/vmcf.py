@@ -48,6 +48,16 @@ class _Jastrow(ctypes.Structure):
                 ("xi", _dp), ("Xi", _dp)]
 
 
+class WalkersState(ctypes.Structure):
+    """vmcf_walkers_state: the public header of a walker-set checkpoint."""
+    _fields_ = [("magic", ctypes.c_char * 8), ("W", ctypes.c_int32), ("nblocks", ctypes.c_int32),
+                ("Ne", ctypes.c_int32), ("n_up", ctypes.c_int32), ("n_dn", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("precision", ctypes.c_int32), ("counter", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("sweep", ctypes.c_uint64), ("measured", ctypes.c_uint64),
+                ("key0", ctypes.c_uint64), ("key1", ctypes.c_uint64), ("wid0", ctypes.c_uint64),
+                ("e_ref", ctypes.c_double), ("eps", ctypes.c_double), ("bytes", ctypes.c_uint64 * 8)]
+
+
 class Counters(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("moves", "accepted", "rejected_nonfinite", "singular", "refreshes", "sweeps", "measured_sweeps")]
@@ -105,6 +115,9 @@ def lib(build_if_missing: bool = True):
         L.vmcf_batch_set_shape.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.vmcf_batch_sample.argtypes = [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp]
         L.vmcf_batch_info.argtypes = [_vp, _ip, _ip, ctypes.c_int, _ip, _ip]
+        L.vmcf_walkers_state_bytes.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.vmcf_walkers_save.argtypes = [_vp, _vp, ctypes.c_uint64, _vp]
+        L.vmcf_walkers_load.argtypes = [_vp, _vp, ctypes.c_uint64, _vp]
         _lib = L
     return _lib
 
@@ -332,6 +345,23 @@ class Walkers:
         c = Counters()
         _check(lib().vmcf_status_counters(self.h, ctypes.byref(c), _stream(stream)), "vmcf_status_counters")
         return c.as_dict()
+
+    def save(self, stream=None) -> bytes:
+        """vmcf_walkers_save: a checkpoint of this walker set (header plus device state)."""
+        n = ctypes.c_uint64()
+        _check(lib().vmcf_walkers_state_bytes(self.h, ctypes.byref(n)), "vmcf_walkers_state_bytes")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(lib().vmcf_walkers_save(self.h, buf, n.value, _stream(stream)), "vmcf_walkers_save")
+        return buf.raw
+
+    def load(self, state: bytes, stream=None):
+        """vmcf_walkers_load: continue from a checkpoint of a walker set of the same system, W and
+        nblocks."""
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        _check(lib().vmcf_walkers_load(self.h, buf, len(state), _stream(stream)), "vmcf_walkers_load")
+        h = WalkersState.from_buffer_copy(bytes(state)[:ctypes.sizeof(WalkersState)])
+        self.e_ref = h.e_ref
+        self.eps = h.eps
 
 
 def vmcf_probe_pipes(stream=None) -> dict:

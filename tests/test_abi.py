@@ -33,3 +33,21 @@ def test_invalid_arguments_are_rejected_without_touching_the_gpu():
     assert b"NULL" in L.vmcf_last_error()
     assert L.vmcf_sample(None, None, 1, 0.3, 26, 0, None) == -1
     assert L.vmcf_evaluate(None, None, 1, None, None, None, None, None, None, None) == -1
+
+
+def test_checkpoint_header_layout_matches_the_c_struct(tmp_path):
+    """The ctypes mirror of vmcf_walkers_state has the C struct's size and field offsets."""
+    import ctypes
+    import subprocess
+
+    fields = [f[0] for f in vmcf.WalkersState._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "vmcf.h"\nint main(void) {\n'
+                   '  printf("%zu\\n", sizeof(vmcf_walkers_state));\n' +
+                   "".join(f'  printf("%zu\\n", offsetof(vmcf_walkers_state, {f}));\n' for f in fields) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", str(HEADER.parent), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(vmcf.WalkersState)
+    assert got[1:] == [getattr(vmcf.WalkersState, f).offset for f in fields]
