@@ -127,6 +127,11 @@ typedef struct {
  * C_up [M][n_up], C_dn [M][n_dn]: host, double, row-major [mu][i] (M = number of AOs).
  * S: host [M][M] AO overlap, or NULL (then rhs_BQ is unavailable).
  * n_up >= n_dn >= 0, n_up >= 1, n_up <= 64, M <= 1024.
+ * Rejected with VMCF_EINVAL before any CUDA call: NULL inputs, non-finite nuclear positions or
+ * coefficients, charges < 1, two nuclei at the same position, invalid shells (l > 2, exponents
+ * <= 0, centres out of range, a contraction of zero norm), and a C_up or C_dn with linearly
+ * dependent columns (every Slater matrix would be singular). Walker positions are not scanned:
+ * a non-finite position makes that walker's moves rejected (counted in rejected_nonfinite).
  * The call synchronises the current device. */
 int vmcf_init_system(const vmcf_nuclei* nuclei, const vmcf_basis* basis, const double* C_up,
                      const double* C_dn, int n_up, int n_dn, const vmcf_jastrow* jastrow,

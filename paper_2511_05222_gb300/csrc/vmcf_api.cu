@@ -124,6 +124,34 @@ bool shell_tables(const vmcf_basis& bas, int K, std::vector<int4>& shells, std::
   return true;
 }
 
+// Whether the n columns of C [M][n] (row-major) are linearly independent: Gram-Schmidt, twice per
+// column, against the columns before it; a column whose remainder is below 1e-10 of its own norm
+// lies in their span.
+bool independent_columns(const std::vector<double>& C, int M, int n) {
+  std::vector<double> Q((size_t)M * n);
+  for (int j = 0; j < n; ++j) {
+    double n0 = 0.0;
+    for (int mu = 0; mu < M; ++mu) {
+      Q[(size_t)j * M + mu] = C[(size_t)mu * n + j];
+      n0 += C[(size_t)mu * n + j] * C[(size_t)mu * n + j];
+    }
+    double* q = &Q[(size_t)j * M];
+    for (int pass = 0; pass < 2; ++pass)
+      for (int k = 0; k < j; ++k) {
+        const double* qk = &Q[(size_t)k * M];
+        double d = 0.0;
+        for (int mu = 0; mu < M; ++mu) d += qk[mu] * q[mu];
+        for (int mu = 0; mu < M; ++mu) q[mu] -= d * qk[mu];
+      }
+    double nr = 0.0;
+    for (int mu = 0; mu < M; ++mu) nr += q[mu] * q[mu];
+    if (!(nr > 1e-20 * n0) || !(n0 > 0.0)) return false;
+    const double inv = 1.0 / std::sqrt(nr);
+    for (int mu = 0; mu < M; ++mu) q[mu] *= inv;
+  }
+  return true;
+}
+
 template <typename T>
 size_t tsize() { return sizeof(T); }
 
@@ -667,6 +695,12 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
     delete s;
     return fail(VMCF_EINVAL, "C not finite");
   }
+  for (int sg = 0; sg < 2; ++sg)
+    if (!independent_columns(s->C[sg], M, sg == 0 ? n_up : n_dn)) {
+      delete s;
+      return fail(VMCF_EINVAL, std::string("the columns of C_") + (sg == 0 ? "up" : "dn") +
+                                   " are linearly dependent (every Slater matrix would be singular)");
+    }
   if (S) {
     s->S.assign(S, S + (size_t)M * M);
     s->has_S = true;
@@ -681,6 +715,10 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
       for (int k = 0; k < 3; ++k) {
         d[k] = s->R[3 * I + k] - s->R[3 * J + k];
         r2 += d[k] * d[k];
+      }
+      if (!(r2 > 1e-12)) {
+        delete s;
+        return fail(VMCF_EINVAL, "two nuclei at the same position");
       }
       const double r = std::sqrt(r2);
       if (J > I) Vnn += s->Z[I] * s->Z[J] / r;
