@@ -1118,7 +1118,13 @@ void osys_sample(void* p, int W, double* pos, double* Bst, uint64_t wid0, uint64
   OSys* s = static_cast<OSys*>(p);
   const int Ne = s->nup + s->ndn;
   const size_t nb = (size_t)s->nup * s->nup + (size_t)s->ndn * s->ndn;
-  const int c0 = *counter;
+  int c0 = *counter;
+  if (nsweeps > 0 && c0 >= kref) {
+    // k lowered since the last call: the attempted moves since the last re-inversion already
+    // reach it, so the inverses are rebuilt before the first move
+    osys_refresh(p, W, pos, Bst, nthreads);
+    c0 = 0;
+  }
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 4)

@@ -470,6 +470,11 @@ int vmcf_batch_sample(vmcf_batch_t b, int n_sweeps, double step_sigma, int refre
     return fail(VMCF_EINVAL, "need n_sweeps >= 0, step_sigma > 0, refresh_k >= 1");
   if (n_sweeps == 0) return VMCF_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int g = 0; g < b->G; ++g)
+    if (b->wk[g]->counter >= refresh_k) {  // k lowered since the last call: re-invert before the first move
+      int rc = vmcf::refresh_walker_set(b->sys[g], b->wk[g], st);
+      if (rc != VMCF_OK) return rc;
+    }
   const int mode = measure ? 1 : 0;
   if (!b->exec || b->g_mode != mode || b->g_kref != refresh_k || b->g_sigma != step_sigma) {
     int rc = capture(*b, mode, refresh_k, step_sigma);

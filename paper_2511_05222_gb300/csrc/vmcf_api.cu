@@ -582,6 +582,9 @@ int measure_state_group(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
 }
 }  // namespace
 
+// Re-inversion of a walker set from its positions (chain clock reset), for the batch entry points.
+int vmcf::refresh_walker_set(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) { return do_refresh(s, wk, st); }
+
 extern "C" {
 
 const char* vmcf_strerror(int status) {
@@ -1038,6 +1041,11 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
   if (n_sweeps < 0 || !(step_sigma > 0.0) || !std::isfinite(step_sigma) || refresh_k < 1)
     return fail(VMCF_EINVAL, "need n_sweeps >= 0, step_sigma > 0, refresh_k >= 1");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n_sweeps > 0 && wk->counter >= refresh_k) {
+    // k lowered since the last call: the moves since the last re-inversion already reach it
+    int rc = do_refresh(s, wk, st);
+    if (rc != VMCF_OK) return rc;
+  }
   if (s->small) {
     const bool fp64 = s->precision == VMCF_FP64;
     SmallMoveParams P{};

@@ -92,4 +92,6 @@ GroupLayout group_layout_meas(const vmcf_system_s& s, int GS);
 GroupLayout group_layout_meas_tc(const vmcf_system_s& s, int GS);
 constexpr int kSmemCapBytes = 227 * 1024;
 int set_last_error(int code, const std::string& msg);
+// Rebuild a walker set's inverses from its positions and reset its re-inversion count (vmcf_api.cu).
+int refresh_walker_set(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st);
 }  // namespace vmcf

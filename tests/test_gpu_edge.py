@@ -1,8 +1,9 @@
 """Edge cases of the CUDA path, through the C ABI, against the FP64 oracle: an empty walker set
 (no work and no error), the largest system the one-warp-per-walker kernels take (32 electrons
 and 16 orbitals per spin: every lane holds an electron and the register rows are full), an
-open-shell system (n_up = n_dn + 1) in both kernel families, a run of zero sweeps, and a walker
-count that fills no CTA, warp or jackknife block evenly."""
+open-shell system (n_up = n_dn + 1) in both kernel families, a run of zero sweeps, a walker count
+that fills no CTA, warp or jackknife block evenly, and a re-inversion interval k lowered between
+calls below the moves already made since the last re-inversion (single path and batch)."""
 import numpy as np
 import pytest
 
@@ -138,3 +139,36 @@ def test_ragged_walker_count_chain_and_estimators(sys0, force_group):
     assert rel(got["F"].ravel(), ref["F"]) < 1e-9
     assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
     assert abs(got["E_err"] - ref["E_err"]) < 1e-8 * ref["E_err"]
+
+
+@pytest.mark.parametrize("force_group", [False, True])
+def test_lowering_k_between_calls_follows_the_oracle(sys0, force_group):
+    """k = 26 for one sweep (10 moves since the re-inversion), then k = 7: both the library and the
+    oracle re-invert before the first move of the second call."""
+    W = 48
+    pos = S.initial_walkers(sys0, W, seed=14)
+    o = oracle.Oracle(sys0)
+    st = o.new_state(pos, key=(5222, 15))
+    o.sample(st, 1, refresh_k=26)
+    o.sample(st, 2, refresh_k=7)
+    wk = vmcf.Walkers(vmcf.System(sys0, vmcf.FP64, force_group=force_group), pos, key=(5222, 15), nblocks=4)
+    wk.sample(1, 0.3, 26)
+    wk.sample(2, 0.3, 7)
+    ok = st["margin"] >= 1e-9
+    assert ok.sum() >= W - 1
+    assert np.abs(wk.positions()[ok] - st["pos"][ok]).max() < 1e-9
+
+
+def test_batch_lowering_k_between_calls_follows_the_single_path(sys0):
+    systems = [vmcf.System(sys0, vmcf.FP64, force_group=True) for _ in range(2)]
+    pos = [S.initial_walkers(sys0, 32, seed=30 + g) for g in range(2)]
+    wa = [vmcf.Walkers(systems[g], pos[g], key=(5222, 40 + g), nblocks=4) for g in range(2)]
+    wb = [vmcf.Walkers(systems[g], pos[g], key=(5222, 40 + g), nblocks=4) for g in range(2)]
+    batch = vmcf.Batch(systems, wa)
+    batch.sample(1, 0.3, 26)
+    batch.sample(2, 0.3, 7)
+    for w in wb:
+        w.sample(1, 0.3, 26)
+        w.sample(2, 0.3, 7)
+    for g in range(2):
+        np.testing.assert_array_equal(wa[g].positions(), wb[g].positions())

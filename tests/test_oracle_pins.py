@@ -445,6 +445,25 @@ def test_refresh_cadence_and_counter(sys0):
     np.testing.assert_allclose(st["B"], o.refresh(st["pos"]), rtol=0, atol=0)
 
 
+def test_lowering_k_between_calls_re_inverts_first(sys0):
+    """A call whose k is at or below the moves already made since the last re-inversion starts
+    with one: the chain is the one of an explicit re-inversion before the call."""
+    o = oracle.Oracle(sys0)
+    pos = S.initial_walkers(sys0, 6, seed=2)
+    a = o.new_state(pos, key=(5222, 3))
+    b = o.new_state(pos, key=(5222, 3))
+    for st in (a, b):
+        o.sample(st, 1, refresh_k=26)
+    assert a["counter"] == sys0.Ne >= 7
+    o.force_refresh(b)
+    o.sample(a, 2, refresh_k=7)
+    o.sample(b, 2, refresh_k=7)
+    np.testing.assert_array_equal(a["pos"], b["pos"])
+    np.testing.assert_array_equal(a["B"], b["B"])
+    np.testing.assert_array_equal(a["nacc"], b["nacc"])
+    assert a["counter"] == b["counter"] == (2 * sys0.Ne) % 7
+
+
 # ------------------------------------------------------------------ jackknife
 def test_jackknife_of_a_mean_is_the_block_standard_error():
     rng = np.random.default_rng(0)
