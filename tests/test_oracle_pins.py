@@ -464,6 +464,50 @@ def test_lowering_k_between_calls_re_inverts_first(sys0):
     assert a["counter"] == b["counter"] == (2 * sys0.Ne) % 7
 
 
+def test_kinetic_energy_from_the_P_rows(sys0):
+    """The kinetic energy as sum_i P_ei B_ie + lap J_e + |grad J_e|^2 with P = lap(phi) + 2 grad J .
+    grad(phi) contracted from the AO rows, the Jastrow derivatives written out in closed form here
+    (Pade pairs and e-n cusp terms), the AO values and derivatives from the oracle's AO evaluation
+    (pinned by quadrature and finite differences): equal to the oracle's kinetic energy."""
+    o = oracle.Oracle(sys0)
+    j = sys0.jastrow
+    pos = S.initial_walkers(sys0, 5, seed=21)
+    ekin = o.eval(pos, want=("parts",))["parts"][:, 0]
+    R, Z = sys0.R, np.asarray(sys0.Z, float)
+    for w in range(pos.shape[0]):
+        r = pos[w]
+        ao = o.ao_eval(r)  # (Ne, M, 14): value, gradient, Laplacian, ...
+        gJ = np.zeros((sys0.Ne, 3))
+        lJ = np.zeros(sys0.Ne)
+        for e in range(sys0.Ne):
+            for q in range(sys0.Ne):
+                if q == e:
+                    continue
+                par = (q < sys0.n_up) == (e < sys0.n_up)
+                a, F = (j.a_par, j.F_par) if par else (j.a_anti, j.F_anti)
+                d = r[e] - r[q]
+                x = np.linalg.norm(d)
+                u1, u2 = a / (1 + F * x) ** 2, -2 * a * F / (1 + F * x) ** 3
+                gJ[e] += u1 * d / x
+                lJ[e] += u2 + 2 * u1 / x
+            for I in range(sys0.K):
+                d = r[e] - R[I]
+                x = np.linalg.norm(d)
+                c1, c2 = -Z[I] / (1 + j.b_en * x) ** 2, 2 * Z[I] * j.b_en / (1 + j.b_en * x) ** 3
+                gJ[e] += c1 * d / x
+                lJ[e] += c2 + 2 * c1 / x
+        total = 0.0
+        for sg, C in ((0, sys0.C_up), (1, sys0.C_dn)):
+            es = range(0, sys0.n_up) if sg == 0 else range(sys0.n_up, sys0.Ne)
+            v = ao[list(es)]
+            A = v[:, :, 0] @ C
+            B = np.linalg.inv(A)  # B[i, el]
+            P = v[:, :, 4] @ C + 2 * np.einsum("ek,emk->em", gJ[list(es)], v[:, :, 1:4]) @ C
+            total += np.einsum("ei,ie->", P, B)
+        total += lJ.sum() + (gJ ** 2).sum()
+        assert abs(-0.5 * total - ekin[w]) < 1e-10 * max(1.0, abs(ekin[w])), (w, -0.5 * total, ekin[w])
+
+
 # ------------------------------------------------------------------ jackknife
 def test_jackknife_of_a_mean_is_the_block_standard_error():
     rng = np.random.default_rng(0)
