@@ -37,3 +37,21 @@ def test_reference_arm_is_silent_on_other_ranks():
     r = _run({"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_ragged_geometries_are_sharded_once_and_balanced():
+    """Longest-processing-time-first sharding of the 64 ragged geometries by N_e^3 W: every
+    geometry on exactly one rank, and no rank above the mean load by more than the largest item
+    (the greedy bound)."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    from paper_2511_05222_gb300 import systems as S
+
+    plan = S.ragged_batch_plan()
+    cost = [sum(Z) ** 3 * W for Z, W in plan]
+    for ws in (1, 2, 3, 4, 8):
+        own = bench.shard_geometries(plan, ws)
+        flat = sorted(g for o in own for g in o)
+        assert flat == list(range(len(plan)))
+        loads = [sum(cost[g] for g in o) for o in own]
+        assert max(loads) <= sum(cost) / ws + max(cost)
