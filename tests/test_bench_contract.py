@@ -1,6 +1,6 @@
 """bench.py's reference arm on the CPU: one JSON line with the keys the measurement contract names
 (the oracle timed on the host cores on a bounded sample), and silence with exit status 0 on ranks
-other than 0 of a multi-process launch."""
+other than 0 of a multi-process launch; the sharding of the ragged batch's geometries over ranks."""
 import json
 import os
 import subprocess
