@@ -150,3 +150,34 @@ def test_host_warp_finish_matches_the_numpy_finish():
     ref = estimators.finish(sums, E_REF)
     np.testing.assert_allclose(got["F"].ravel(), ref["F"], rtol=1e-9, atol=1e-9 * np.abs(ref["F"]).max())
     np.testing.assert_allclose(got["F_err"].ravel(), ref["F_err"], rtol=1e-8)
+
+
+def _gather_or_die(rank, world, port, q):
+    """Rank 1 fails before the exchange (an exception on the host, no GPU involved); rank 0's
+    gather must end with an error instead of waiting forever."""
+    import datetime
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        q.put((1, "failed"))
+        raise SystemExit(3)  # leaves between steps, before the collective
+    try:
+        D.gather_block_sums(np.zeros((NB_LOCAL, 8)))
+        q.put((0, "gathered"))
+    except Exception as e:  # noqa: BLE001 - any error is the detection we want
+        q.put((0, "error: " + type(e).__name__))
+
+
+def test_a_rank_that_fails_before_the_exchange_ends_the_gather_with_an_error():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_gather_or_die, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+    assert res[1] == "failed" and procs[1].exitcode == 3
+    assert res[0].startswith("error"), res[0]
