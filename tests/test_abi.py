@@ -51,3 +51,13 @@ def test_checkpoint_header_layout_matches_the_c_struct(tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert got[0] == ctypes.sizeof(vmcf.WalkersState)
     assert got[1:] == [getattr(vmcf.WalkersState, f).offset for f in fields]
+
+
+def test_a_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without libvmcf.so the binding raises instead of computing anything."""
+    import pytest
+
+    monkeypatch.setattr(vmcf, "_lib", None)
+    monkeypatch.setattr(vmcf._build, "LIB", tmp_path / "libvmcf.so")
+    with pytest.raises(RuntimeError, match="libvmcf.so not found"):
+        vmcf.lib(build_if_missing=False)
