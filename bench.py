@@ -10,6 +10,11 @@ Default workload: C2OH6 (26 electrons, 72 AOs, 9 nuclei), 16384 walkers per GPU,
 step 0.3 bohr, re-inversion every 26 moves, mixed precision; the FP64 GPU path is timed on
 the same workload for comparison. Inputs are synthetic (seeded generator). L2 is flushed
 between timed steps (the walker state, 32 MB, would otherwise stay in the 129 MB L2).
+The headline steps are timed without per-kernel instrumentation; the kernel split and the
+roofline of the dominant kernel come from a second timed region of the same length with an
+event pair around every kernel. The default line also carries a "c9o4h8" block: the
+94-electron workload (C9O4H8, 222 AOs, 65536 walkers per GPU) measured the same way, mixed and
+FP64 (--no-large skips it).
 
 --impl reference times the CPU oracle (the plain FP64 C++ reference implementation) on
 the host cores, on a bounded sample of the same workload.
@@ -296,9 +301,14 @@ def main():
     ap.add_argument("--workload", default="c2oh6", choices=sorted(WORKLOADS))
     ap.add_argument("--walkers", type=int, default=0, help="walkers per GPU (default: the workload's)")
     ap.add_argument("--equil", type=int, default=10, help="unmeasured sweeps before the warm-up steps")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of the headline measurement (default mixed)")
+    ap.add_argument("--group-path", action="store_true", help="run a small system on the walker-group kernels")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the C9O4H8 (94 e-, 65536 walkers) block of the default line")
     ap.add_argument("--jastrow-basis", action="store_true",
                     help="add the AO-expanded Jastrow terms (seeded medium Jastrow basis) to the workload")
     args = ap.parse_args()
@@ -320,13 +330,6 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    W = args.walkers or wl["walkers"]
-    sysx = S.make_system(wl["cfg"])
-    jb = None
-    if args.jastrow_basis:
-        sysx = S.with_jastrow_basis(sysx)
-        jb = sysx.jastrow.basis
-    pos0 = S.initial_walkers(sysx, W, seed=rank)
     nb = 64
 
     def barrier():
@@ -345,7 +348,11 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def timed_steps(wk, K, profile=False):
+        """K measured sweeps, each bracketed by CUDA events on the launching stream, L2 flushed
+        before each. With profile, the library also records an event pair around every kernel it
+        launches (a second timed region, used only for the per-kernel split)."""
         if profile:
+            wk.kernel_times(reset=True)
             wk.profile(True)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         barrier()
@@ -356,84 +363,116 @@ def main():
             b.record(stream)
         barrier()
         ms = sum(a.elapsed_time(b) for a, b in ev)
-        kt = wk.kernel_times(reset=True) if profile else None
+        kt = None
         if profile:
+            kt = wk.kernel_times(reset=True)
             wk.profile(False)
         return ms, kt
 
-    def prepare(precision):
-        g = vmcf.System(sysx, precision)
+    peaks = vmcf.vmcf_probe_pipes(stream=stream)
+
+    def workload_line(sysx, W, steps, warmup, fp64_steps, jb=None, prec=vmcf.MIXED, group=False, seed=0):
+        """Headline measurement of one workload: the precision's walker-evals/s over `steps` timed
+        sweeps without instrumentation, then the same number of sweeps with per-kernel events for
+        the kernel split and the roofline of the dominant kernel; the FP64 GPU path on the same
+        (equilibrated) configurations."""
+        pos0 = S.initial_walkers(sysx, W, seed=seed)
+        g = vmcf.System(sysx, prec, force_group=group)
         wk = vmcf.Walkers(g, pos0, key=(5222, 1), wid0=rank * W, nblocks=nb, stream=stream)
         wk.sample(args.equil, 0.3, 26, measure=False, stream=stream)
         wk.reset_accumulators(0.0, stream=stream)
         wk.measure(stream=stream)  # E_ref: the mean local energy after equilibration
-        wk.reset_accumulators(wk.reduce_estimators(stream=stream)["E"], stream=stream)
-        return g, wk
+        e_ref = wk.reduce_estimators(stream=stream)["E"]
+        wk.reset_accumulators(e_ref, stream=stream)
+        for _ in range(warmup):
+            wk.sample(1, 0.3, 26, measure=True, stream=stream)
+        with ClockSampler(local) as clk:
+            ms, _ = timed_steps(wk, steps)
+        ms = max_over_ranks(ms)
+        ms_prof, kt = timed_steps(wk, steps, profile=True)
+        value = ws * W * steps / (ms * 1e-3)
+        cnt = wk.counters(stream=stream)
+        acc = cnt["accepted"] / max(1, cnt["moves"])
+        est = wk.reduce_estimators(stream=stream)
+        work = workmodel.per_walker_eval(sysx.K, g.M, sysx.n_up, sysx.n_dn, int(sysx.shell_nprim.sum()), acc,
+                                         jb.MJ if jb else 0, int(jb.shell_nprim.sum()) if jb else 0)
+        dom = max(("move", "measure"), key=lambda k: kt[k]["ms"])
+        t_launch = kt[dom]["ms"] / max(1, kt[dom]["launches"]) * 1e-3
+        bound, _ = workmodel.roofline_time(work[dom], peaks)
+        pipe_flops = {"fp32": work[dom]["fp32"], "fp64": work[dom]["fp64"], "sfu": work[dom]["exp"]}[bound]
+        peak = {"fp32": peaks["fp32_tflops"], "fp64": peaks["fp64_tflops"], "sfu": peaks["exp_gops"] / 1e3}[bound]
+        achieved = pipe_flops * W / t_launch / 1e12
+        # the one-warp-per-walker kernel family, else walker groups (32 threads up to 24 orbitals per spin)
+        small = sysx.Ne <= 32 and max(sysx.n_up, sysx.n_dn) <= 16 and jb is None and not group
+        wide = max(sysx.n_up, sysx.n_dn) > 24
+        jbf = "1" if jb else "0"  # walker-group kernels: instance with (1) or without (0) the AO-expanded Jastrow terms
+        nmx = max(sysx.n_up, sysx.n_dn)
+        nm = 8 if nmx <= 8 else (14 if nmx <= 14 else 16)  # register-row width of the one-warp-per-walker kernels
+        tn = "float" if prec == vmcf.MIXED else "double"
+        kname = (f"{dom}_small<{tn}, {nm}>" if small else
+                 {"move": f"move_kernel<{tn}, {128 if wide else 32}, {jbf}>",
+                  "measure": f"measure_kernel<{tn}, {256 if wide else 32}, {jbf}>"}[dom])
+        traffic = profiled_traffic() if (dom == "measure" and small and prec == vmcf.MIXED and W == 16384) else None
+        roofline = {"bound": "alu", "pipe": bound, "kernel": kname, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s" if bound != "sfu" else "Texp/s", "frac": achieved / peak,
+                    "peak_source": "measured in this run by vmcf_probe_pipes (register-only FMA/exp kernels)",
+                    "traffic": traffic,
+                    "traffic_source": ("DRAM bytes of the committed ncu capture profiles/measure_small_c2oh6.md "
+                                       "(its kernel-source hash matches this build)") if traffic else None,
+                    "launch_ms": t_launch * 1e3,
+                    "kernel_times_source": "per-kernel CUDA events over a second timed region of the same "
+                                           f"{steps} steps ({ms_prof / steps:.3f} ms per step with the events)",
+                    "kernel_share": {k: kt[k]["ms"] / max(1e-9, sum(v["ms"] for v in kt.values())) for k in kt},
+                    "whole_step_frac": workmodel.roofline_time(work["total"], peaks)[1] * W / (ms * 1e-3 / steps)}
+        out = {"value": value, "ms_per_step": ms / steps, "steps": steps, "warmup": warmup, "roofline": roofline,
+               "gpu_launches": sum(v["launches"] for v in kt.values()), "clocks": clk.summary(),
+               "acceptance": acc, "estimates": {"E": est["E"], "E_err": est["E_err"]}, "walkers_per_gpu": W,
+               "electrons": sysx.Ne, "aos": g.M}
+        if fp64_steps and prec == vmcf.MIXED:
+            pos_eq = wk.positions(stream=stream)
+            del wk, g
+            g64 = vmcf.System(sysx, vmcf.FP64, force_group=group)
+            wk64 = vmcf.Walkers(g64, pos_eq, key=(5222, 1), wid0=rank * W, nblocks=nb, stream=stream)
+            wk64.reset_accumulators(e_ref, stream=stream)
+            wk64.sample(1, 0.3, 26, measure=True, stream=stream)
+            ms64, _ = timed_steps(wk64, fp64_steps)
+            ms64 = max_over_ranks(ms64)
+            v64 = ws * W * fp64_steps / (ms64 * 1e-3)
+            out["fp64_gpu"] = {"value": v64, "ms_per_step": ms64 / fp64_steps, "steps": fp64_steps}
+            out["mixed_over_fp64"] = value / v64
+            del wk64, g64
+        return out
 
-    peaks = vmcf.vmcf_probe_pipes(stream=stream)
-
-    # ---- mixed precision (headline)
-    g, wk = prepare(vmcf.MIXED)
-    for _ in range(args.warmup):
-        wk.sample(1, 0.3, 26, measure=True, stream=stream)
-    with ClockSampler(local) as clk:
-        ms, kt = timed_steps(wk, args.steps, profile=True)
-    ms = max_over_ranks(ms)
-    value = ws * W * args.steps / (ms * 1e-3)
-    cnt = wk.counters(stream=stream)
-    acc = cnt["accepted"] / max(1, cnt["moves"])
-    est = wk.reduce_estimators(stream=stream)
-
-    work = workmodel.per_walker_eval(sysx.K, g.M, sysx.n_up, sysx.n_dn, int(sysx.shell_nprim.sum()), acc,
-                                     jb.MJ if jb else 0, int(jb.shell_nprim.sum()) if jb else 0)
-    dom = max(("move", "measure"), key=lambda k: kt[k]["ms"])  # the tensor-core sums take ~2%
-    t_launch = kt[dom]["ms"] / max(1, kt[dom]["launches"]) * 1e-3
-    bound, t_roof_w = workmodel.roofline_time(work[dom], peaks)
-    pipe_flops = {"fp32": work[dom]["fp32"], "fp64": work[dom]["fp64"], "sfu": work[dom]["exp"]}[bound]
-    peak = {"fp32": peaks["fp32_tflops"], "fp64": peaks["fp64_tflops"], "sfu": peaks["exp_gops"] / 1e3}[bound]
-    achieved = pipe_flops * W / t_launch / 1e12
-    # the one-warp-per-walker kernel family, else walker groups (32 threads up to 24 orbitals per spin)
-    small = sysx.Ne <= 32 and max(sysx.n_up, sysx.n_dn) <= 16 and jb is None
-    wide = max(sysx.n_up, sysx.n_dn) > 24
-    jbf = "1" if jb else "0"  # walker-group kernels: instance with (1) or without (0) the AO-expanded Jastrow terms
-    nmx = max(sysx.n_up, sysx.n_dn)
-    nm = 8 if nmx <= 8 else (14 if nmx <= 14 else 16)  # register-row width of the one-warp-per-walker kernels
-    kname = (f"{dom}_small<float, {nm}>" if small else
-             {"move": f"move_kernel<float, {128 if wide else 32}, {jbf}>",
-              "measure": f"measure_kernel<float, {256 if wide else 32}, {jbf}>"}[dom])
-    roofline = {"bound": "alu", "pipe": bound, "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s" if bound != "sfu" else "Texp/s", "frac": achieved / peak,
-                "peak_source": "measured in this run by vmcf_probe_pipes (register-only FMA/exp kernels)",
-                "traffic": profiled_traffic() if dom == "measure" and small else None, "launch_ms": t_launch * 1e3,
-                "kernel_share": {k: kt[k]["ms"] / max(1e-9, sum(v["ms"] for v in kt.values())) for k in kt},
-                "whole_step_frac": workmodel.roofline_time(work["total"], peaks)[1] * W / (ms * 1e-3 / args.steps)}
-
-    line = {"metric": METRIC, "value": value, "unit": "walker-evals/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+    W = args.walkers or wl["walkers"]
+    sysx = S.make_system(wl["cfg"])
+    jb = None
+    if args.jastrow_basis:
+        sysx = S.with_jastrow_basis(sysx)
+        jb = sysx.jastrow.basis
+    prec = vmcf.MIXED if args.precision == "mixed" else vmcf.FP64
+    head = workload_line(sysx, W, args.steps, args.warmup, 0 if args.no_fp64 else args.steps, jb, prec,
+                         args.group_path, seed=rank)
+    line = {"metric": METRIC, "value": head["value"], "unit": "walker-evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if prec == vmcf.MIXED else "f64", "data": "synthetic",
             "config": {"workload": wl["name"] + (f" + AO-expanded Jastrow ({jb.MJ} Jastrow-basis functions)" if jb else ""),
-                       "walkers_per_gpu": W, "electrons": sysx.Ne, "aos": g.M,
-                       "step_sigma": 0.3, "refresh_every": 26, "precision": "mixed (FP32 + FP64 inverse/ratio/sums)",
+                       "walkers_per_gpu": W, "electrons": sysx.Ne, "aos": head["aos"],
+                       "step_sigma": 0.3, "refresh_every": 26,
+                       "precision": "mixed (FP32 + FP64 inverse/ratio/sums)" if prec == vmcf.MIXED else "fp64",
                        "l2": "flushed (256 MB write) between timed steps"},
-            "roofline": roofline, "gpu_launches": sum(v["launches"] for v in kt.values()), "clocks": clk.summary(),
-            "acceptance": acc, "estimates": {"E": est["E"], "E_err": est["E_err"]}}
-
-    # ---- FP64 GPU path on the same workload
-    if not args.no_fp64:
-        del wk, g
-        g64, wk64 = prepare(vmcf.FP64)
-        wk64.sample(1, 0.3, 26, measure=True, stream=stream)
-        k64 = max(2, args.steps // 4)
-        ms64, _ = timed_steps(wk64, k64)
-        ms64 = max_over_ranks(ms64)
-        v64 = ws * W * k64 / (ms64 * 1e-3)
-        line["fp64_gpu"] = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64}
-        line["mixed_over_fp64"] = value / v64
-        del wk64, g64
+            "roofline": head["roofline"], "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+            "acceptance": head["acceptance"], "estimates": head["estimates"]}
+    if "fp64_gpu" in head:
+        line["fp64_gpu"] = head["fp64_gpu"]
+        line["mixed_over_fp64"] = head["mixed_over_fp64"]
 
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e:
-        g, wk = prepare(vmcf.MIXED)
+        g = vmcf.System(sysx, prec, force_group=args.group_path)
+        pos0 = S.initial_walkers(sysx, W, seed=rank)
+        wk = vmcf.Walkers(g, pos0, key=(5222, 1), wid0=rank * W, nblocks=nb, stream=stream)
+        wk.sample(args.equil, 0.3, 26, measure=False, stream=stream)
+        wk.reset_accumulators(head["estimates"]["E"], stream=stream)
         host = torch.empty((W, sysx.Ne, 3), dtype=torch.float64, pin_memory=True).numpy()
         host[:] = wk.positions(stream=stream)
         ke = max(2, args.steps // 2)
@@ -450,6 +489,14 @@ def main():
         d2h = W * sysx.Ne * 3 * 8 + nb * g.accL * 8
         line["e2e"] = {"value": ws * W * ke / te, "unit": "walker-evals/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "steps": ke}
+        del wk, g
+
+    # ---- the 94-electron workload (C9O4H8, 65536 walkers per GPU), mixed and FP64, beside the headline
+    if args.workload == "c2oh6" and not args.no_large and not args.jastrow_basis and not args.walkers:
+        big = WORKLOADS["c9o4h8"]
+        blk = workload_line(S.make_system(big["cfg"]), big["walkers"], 5, 3, 0 if args.no_fp64 else 2, seed=rank)
+        blk["workload"] = big["name"]
+        line["c9o4h8"] = blk
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     if not args.no_cpu and ws == 1:

@@ -124,6 +124,13 @@ typedef struct {
 } vmcf_counters;
 
 /* Build a system: validates the input, normalises the basis, uploads tables and C.
+ * Defines the wavefunction of App. A ("Wavefunction Ansatz"): the JAGP expanded over the n_up,
+ * n_dn occupied orbitals, i.e. the Jastrow-Slater determinant Psi = exp(J) det A_up det A_dn with
+ * A^s_{ei} = phi^s_i(r_e) and phi^s_i = sum_mu C^s_{mu i} psi_mu (Eqs. agp_expansion, restricted-C,
+ * occ-expansion); psi_mu are the contracted GTOs of `basis` on `nuclei`; J is the one-body and
+ * two-body Jastrow of `jastrow` (Eqs. twobody_v, twobody_v_exp, onebody_J_inhom, threebody_jas).
+ * C is frozen (the paper's coefficients come from DFT and stay fixed in VMC); R and C are the two
+ * parameter sets the forces and dE/dC differentiate.
  * C_up [M][n_up], C_dn [M][n_dn]: host, double, row-major [mu][i] (M = number of AOs).
  * S: host [M][M] AO overlap, or NULL (then rhs_BQ is unavailable).
  * n_up >= n_dn >= 0, n_up >= 1, n_up <= 64, M <= 1024.
@@ -140,7 +147,10 @@ int vmcf_system_destroy(vmcf_system_t sys);
 /* Sizes of a system: number of nuclei, AOs, up and down electrons (any pointer may be NULL). */
 int vmcf_system_info(vmcf_system_t sys, int* K, int* M, int* n_up, int* n_dn);
 
-/* Walker state for sampling: positions, Slater inverses, counters, accumulators.
+/* Walker state for sampling: positions, Slater inverses, counters, accumulators. The walkers are
+ * the set {x_i} of App. A ("Variational Monte Carlo Methods") that the Markov chain draws from
+ * pi(x) = Psi^2 / int Psi^2; each walker is one independent chain, and the estimators are the
+ * averages over walkers and measured sweeps (Eq. eq-eval-observable).
  * pos: [W][Ne][3] double, device (is_host = 0) or host (is_host = 1) memory.
  * key0, key1: Philox4x64-10 key; wid0: global id of walker 0 (Philox counter word 0), so
  * that shards of one walker set on several GPUs draw the same streams as one GPU would.
@@ -184,7 +194,12 @@ int vmcf_sample(vmcf_system_t sys, vmcf_walkers_t wk, int n_sweeps, double step_
  * one measured sweep of vmcf_sample does). Used for estimators on fixed configurations. */
 int vmcf_measure(vmcf_system_t sys, vmcf_walkers_t wk, void* stream);
 
-/* Fixed-walker evaluation (no sampling). pos: device [W][Ne][3], W >= 0 (W = 0: nothing is
+/* Fixed-walker evaluation (no sampling): the per-sample quantities whose averages make up the
+ * estimators. E_L = H Psi / Psi (App. A, the local energy of Eq. eq-eval-observable); d ln Psi/dR and
+ * dE_L/dR, the per-sample terms of the Pulay and Hellmann-Feynman forces (Eqs. pulay, hf), as total
+ * derivatives at fixed electron positions (AOs and one-body terms move with their nucleus, C fixed);
+ * O = d ln Psi / dC (App. A, "Computing derivatives", Eq. fc-vmc-eval).
+ * pos: device [W][Ne][3], W >= 0 (W = 0: nothing is
  * read or written and pos may be NULL). Outputs are device buffers owned by the caller; any may
  * be NULL:
  *   EL [W], logpsi [W] (ln|Psi|), dlnpsi_dR [W][K][3], dEL_dR [W][K][3],
@@ -192,7 +207,11 @@ int vmcf_measure(vmcf_system_t sys, vmcf_walkers_t wk, void* stream);
 int vmcf_evaluate(vmcf_system_t sys, const double* pos, int W, double* EL, double* logpsi,
                   double* dlnpsi_dR, double* dEL_dR, double* O, double* dEL_dC, void* stream);
 
-/* Finish the estimators from the accumulated sums (synchronises the stream). Host outputs
+/* Finish the estimators from the accumulated sums (synchronises the stream): E = <E_L>
+ * (Eq. eq-eval-observable), F = -<dE_L/dR> - 2 (<E_L d ln Psi/dR> - E <d ln Psi/dR>) (Eqs. hf,
+ * pulay, with E the same-sample mean), dEdC = 2 (<E_L O> - E <O>) (Eq. fc-vmc-eval, as dE/dC), and
+ * rhs_BQ, the right-hand side of the Z-vector equations projected on the virtual space (Eqs.
+ * Q_projector, AZ_eq_B_elements). Host outputs
  * (any may be NULL): E, E_err (scalars), F, F_err [K][3], dEdC, dEdC_err [M*(n_up+n_dn)],
  * rhs_BQ [M*(n_up+n_dn)] = -sum_mu B_{mu i} Q_{mu nu} (needs S at init, else VMCF_EINVAL).
  * Error bars: delete-one-block jackknife over the walker blocks. */
@@ -244,7 +263,10 @@ int vmcf_evaluate_warp(vmcf_system_t sys, const double* pos, int W, double* dEL_
 int vmcf_finish_covariance(const double* blocks, int nblocks, int K, int M, int n_up, int n_dn, double e_ref,
                            double* F_factor, double* B_factor);
 
-/* Counters (synchronises the stream). */
+/* Counters of the Markov chain of App. A ("Variational Monte Carlo Methods"): attempted and
+ * accepted Metropolis moves, moves rejected on a zero or non-finite ratio, Slater inversions that
+ * met a zero pivot, FP64 re-inversions, sweeps (synchronises the stream). Not part of the paper's
+ * estimators; they show whether the chain is healthy (acceptance rate, walkers on a node). */
 int vmcf_status_counters(vmcf_walkers_t wk, vmcf_counters* out, void* stream);
 
 /* Checkpoint and resume of a walker set, between library calls. A checkpoint holds everything
@@ -286,18 +308,24 @@ int vmcf_walkers_load(vmcf_walkers_t wk, const void* buf, uint64_t bytes, void* 
  * It is for callers that must not allocate GPU memory while they run, for example code
  * embedded in a host application that hands the library only buffers it already owns, or
  * a loop that cannot afford the device-wide synchronisation a cudaMalloc or cudaFree can
- * cause. The system must already exist (vmcf_init_system allocates once, at set-up).
+ * cause. The system must already exist (vmcf_init_system allocates once, at set-up), and its
+ * device (the device current at vmcf_init_system) must be the current device (else VMCF_EINVAL).
  *   pos: device [W][Ne][3]; e_ref: reference energy, as in vmcf_reset_accumulators;
  *   sums: device [vmcf_accumulator_length()] doubles, written (not added to) with the sums
  *   over all W walkers in the vmcf_block_sums layout for one block.
+ *   W = 0: only the once-per-device set-up below (pos and sums may be NULL, nothing launches).
  * Scratch: a fixed array of 2^21 doubles (16 MiB) in this library's device memory holds the
  * per-CTA partial sums; every GPU that loads the library keeps it until the process exits.
- * A system whose sum vector is longer than 2^21 doubles is rejected with VMCF_EINVAL.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture. All calls share the array: each call
- * clears the part it uses, and calls whose kernels overlap on the GPU race with each other
- * (serialise them, e.g. on one stream). The call calls no cudaMalloc, cudaFree or other
- * allocating routine. */
+ * A system whose sum vector is longer than 2^21 doubles is rejected with VMCF_EINVAL. Every
+ * walker sum is accumulated in FP64 (in mixed precision each walker's terms go straight to its
+ * CTA's FP64 partial sum).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress). With
+ * CUDA's lazy module loading that lookup may load the library's device code and commit the
+ * 16 MiB array at that moment, so the first call can synchronise or fail for lack of memory:
+ * make it at set-up (a call with W = 0 does only this), and before any stream capture.
+ * All calls share the array: each call clears the part it uses, and calls whose kernels
+ * overlap on the GPU race with each other (serialise them, e.g. on one stream). The call
+ * calls no cudaMalloc, cudaFree or other allocating routine. */
 int vmcf_evaluate_sums_noalloc(vmcf_system_t sys, const double* pos, int W, double e_ref, double* sums,
                                void* stream);
 
@@ -306,13 +334,6 @@ int vmcf_evaluate_sums_noalloc(vmcf_system_t sys, const double* pos, int W, doub
  *                            the small-system path (default 2);
  *   "measure_warps":         2, 4 or 8 walkers (one warp each) per CTA of the small-system
  *                            measurement kernel (default: the most that fit shared memory, up to 8);
- *   "stagger_refresh":       1: on the walker-group kernels, walker wid counts its moves towards
- *                            the next FP64 re-inversion from the common count plus (wid mod k), so
- *                            that walkers re-invert at different moves (each still every k moves;
- *                            a measurement still re-inverts every walker); the FP64 re-inversions
- *                            then overlap the FP32 moves of other walkers. Chains change only by
- *                            the rounding of the inverses between re-inversions. Default 0;
- *                            VMCF_ENOTSUP on the small-system kernels;
  *   "tensor_core_sums":      1: in mixed precision, the walker sums of O and (E_L - E_ref) O are
  *                            one bf16 GEMM on the tensor cores (tcgen05, FP32 accumulation in
  *                            tensor memory, FP64 across CTAs); 0: FP32 SIMT sums (default 1 where
@@ -320,19 +341,6 @@ int vmcf_evaluate_sums_noalloc(vmcf_system_t sys, const double* pos, int W, doub
  * Takes effect for walker sets created afterwards (measure_warps) or at the next call. */
 int vmcf_set_tuning(vmcf_system_t sys, const char* key, int value);
 
-/* Diagnostics (not part of the paper's method).
- * vmcf_profile: record a CUDA event pair around every kernel this walker set launches from
- * now on (enable != 0) or stop recording (0).
- * vmcf_kernel_times: synchronise on the recorded events and return the summed device time
- * in ms and the launch count per kernel kind: [0] Metropolis sweep kernel, [1] measurement
- * kernel, [2] refresh kernel, [3] tensor-core walker-sum kernel (host arrays of 4; either may
- * be NULL); reset != 0 zeroes the totals afterwards.
- * vmcf_probe_pipes: measure this GPU's FP64 FMA and FP32 FMA throughput (TFLOP/s) and FP32
- * expf throughput (G/s) with short register-only kernels on `stream` (synchronises; about
- * 30 ms). Used as the measured ALU peaks of the roofline. */
-int vmcf_profile(vmcf_walkers_t wk, int enable);
-int vmcf_kernel_times(vmcf_walkers_t wk, double* ms, long long* count, int reset);
-int vmcf_probe_pipes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, void* stream);
 
 /* ---- Ragged batches of geometries.
  * Many independent geometries (different nuclei, electron and AO counts, walker counts) are

@@ -67,7 +67,7 @@ def lib():
         L.osys_refresh.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_int]
         L.osys_sample.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp, _dp, ctypes.c_uint64, ctypes.c_uint64,
                                   ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                  _ip, _u32p, _u32p, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+                                  _ip, _u32p, _u32p, _dp, ctypes.c_int, ctypes.c_double]
         L.osys_set_jastrow_basis.restype = ctypes.c_int
         L.osys_set_jastrow_basis.argtypes = [ctypes.c_void_p, ctypes.c_int, _ip, _ip, _ip, _dp, _dp, ctypes.c_int,
                                              _dp, _dp]
@@ -198,17 +198,15 @@ class Oracle:
         lib().osys_refresh(self.h, pos.shape[0], _p(pos), _p(B), self.nthreads)
         return B
 
-    def sample(self, state: dict, n_sweeps: int, sigma: float = 0.3, refresh_k: int = 26, eps: float = 0.0,
-               stagger: bool = False):
+    def sample(self, state: dict, n_sweeps: int, sigma: float = 0.3, refresh_k: int = 26, eps: float = 0.0):
         """Advance a sampler state in place. state: pos (W,Ne,3), B (W,nB), wid0, key (k0,k1),
-        sweep, counter, nacc (W,), nsing (W,), margin (W,). eps > 0 samples |Psi_G|^2 (guided);
-        stagger offsets walker wid's re-inversion count by wid mod refresh_k."""
+        sweep, counter, nacc (W,), nsing (W,), margin (W,). eps > 0 samples |Psi_G|^2 (guided)."""
         W = state["pos"].shape[0]
         cnt = np.array([state["counter"]], np.int32)
         lib().osys_sample(self.h, W, _p(state["pos"]), _p(state["B"]), state["wid0"], state["key"][0],
                           state["key"][1], state["sweep"], n_sweeps, sigma, refresh_k, _p(cnt, _ip),
                           _p(state["nacc"], _u32p), _p(state["nsing"], _u32p), _p(state["margin"]),
-                          self.nthreads, float(eps), int(bool(stagger)))
+                          self.nthreads, float(eps))
         state["counter"] = int(cnt[0])
         state["sweep"] += n_sweeps
 

@@ -1109,12 +1109,11 @@ int osys_refresh(void* p, int W, const double* pos, double* Bst, int nthreads) {
 
 // Metropolis sweeps. pos [W][Ne][3] and Bst are updated in place. wid0 is the global id
 // of walker 0 (Philox counter word 0). counter: attempted moves since the last refresh,
-// the same for every walker (in/out; with stagger, walker wid's own count starts from counter +
-// wid mod kref). nacc, nsing: per-walker counts (added to).
+// the same for every walker (in/out). nacc, nsing: per-walker counts (added to).
 // margin: per-walker minimum of |u - p| / p over all decisions (in/out).
 void osys_sample(void* p, int W, double* pos, double* Bst, uint64_t wid0, uint64_t k0, uint64_t k1,
                  uint64_t sweep0, int nsweeps, double sigma, int kref, int* counter, uint32_t* nacc,
-                 uint32_t* nsing, double* margin, int nthreads, double eps, int stagger) {
+                 uint32_t* nsing, double* margin, int nthreads, double eps) {
   OSys* s = static_cast<OSys*>(p);
   const int Ne = s->nup + s->ndn;
   const size_t nb = (size_t)s->nup * s->nup + (size_t)s->ndn * s->ndn;
@@ -1130,10 +1129,8 @@ void osys_sample(void* p, int W, double* pos, double* Bst, uint64_t wid0, uint64
 #pragma omp parallel for schedule(dynamic, 4)
 #endif
   for (int w = 0; w < W; ++w) {
-    // staggered re-inversions: walker wid counts its moves from the common counter plus
-    // (wid mod kref), so that walkers re-invert at different moves (every kref moves each)
     const uint64_t wid = wid0 + (uint64_t)w;
-    int c = stagger ? (int)((c0 + (int)(wid % (uint64_t)kref)) % kref) : c0;
+    int c = c0;
     sample_walker(*s, (int)wid, pos + (size_t)w * Ne * 3, Bst + w * nb, k0, k1, sweep0, nsweeps, sigma, kref,
                   &c, nacc + w, nsing + w, margin + w, eps);
   }

@@ -181,7 +181,6 @@ void fill_geo(vmcf_batch_s& b, int g) {
   }
   G.Mp.eps = w.eps;
   G.P.eps = w.eps;
-  G.P.stagger = s.stagger ? 1 : 0;
   G.Mp.accL = s.accL;
   G.Mp.acc_in_smem = 0;
   G.Mp.e_ref = w.e_ref;

@@ -126,9 +126,7 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
   T* jy = jpo + MJ;
   if (MJ) jas_refresh_t0<T, GS>(S, pos, jy, jt0);
   const uint64_t wid = P.wid0 + (uint64_t)w;
-  // staggered re-inversions: this walker counts from c0 + (wid mod kref), so that the walkers of an
-  // SM re-invert at different moves and the FP64 work overlaps the FP32 moves of the others
-  int c = P.stagger ? (int)(((uint64_t)c0 + wid % (uint64_t)P.kref) % (uint64_t)P.kref) : c0;
+  int c = c0;
   uint32_t nacc = 0, nrej = 0, nref = 0;
   // reweighted sampling of |Psi_G|^2, Psi_G = Psi max(1, eps sqrt(S)): S of the current inverses
   const bool guide = P.eps > 0.0;

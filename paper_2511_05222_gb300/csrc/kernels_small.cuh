@@ -722,6 +722,14 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
     warp_sum_f<4>(vpart);
     const double EL = vpart[0] + vpart[1] + vpart[2] + S.Vnn;
     const double cw = EL - P.e_ref;
+    if (P.mode == 1 && !P.dlnpsi && !P.dEL && !P.O) {  // E_L and ln|Psi| only: no adjoint pass
+      if (lane == 0) {
+        if (P.EL) P.EL[w] = EL;
+        if (P.logpsi) P.logpsi[w] = *la + vpart[3];
+      }
+      __syncwarp();
+      continue;
+    }
     __syncwarp();
 
     // ---- adjoint weights per spin: Q = B P, X = Q B (X[e][i] = (B P B)_{i e}, over P)

@@ -25,15 +25,13 @@ constexpr int kMaxDevices = 64;
 double* g_scratch_dev[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
-int scratch_for_current_device(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return vmcf::set_last_error(VMCF_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+// The scratch of device `dev`, which must be the current device (the system's own device).
+int scratch_for_device(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return vmcf::set_last_error(VMCF_ENOTSUP, "device index beyond 63");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_dev[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
       return vmcf::set_last_error(VMCF_ECUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") +
                                                   cudaGetErrorString(e));
@@ -47,32 +45,49 @@ int scratch_for_current_device(double** out) {
 
 extern "C" int vmcf_evaluate_sums_noalloc(vmcf_system_t s, const double* pos, int W, double e_ref, double* sums,
                                           void* stream) {
-  if (!s || !pos || !sums || W < 1) return vmcf::set_last_error(VMCF_EINVAL, "need a system, positions, W >= 1 and an output");
+  if (!s || W < 0 || (W > 0 && (!pos || !sums)))
+    return vmcf::set_last_error(VMCF_EINVAL, "need a system, W >= 0, and positions and an output when W > 0");
   const int accL = s->accL;
   const size_t fit = kScratchDoubles / (size_t)accL;  // CTAs whose partial sums fit the scratch
   if (fit < 1)
     return vmcf::set_last_error(VMCF_EINVAL, "the system's walker-sum vector exceeds the no-alloc scratch of 2^21 doubles");
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return vmcf::set_last_error(VMCF_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != s->device)
+    return vmcf::set_last_error(VMCF_EINVAL, "the system's device must be the current device");
   double* scratch = nullptr;
-  int rc = scratch_for_current_device(&scratch);
-  if (rc != VMCF_OK) return rc;
+  int rc = scratch_for_device(dev, &scratch);
+  if (rc != VMCF_OK || W == 0) return rc;  // W = 0: the once-per-device set-up only
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int per_cta = 4 * (s->acc_smem ? s->gpb_meas : 1);
+  vmcf::MeasParams M{};
+  vmcf::Launch lc = vmcf::launch_meas(*s, 1, true, false);
+  M.acc_in_smem = s->acc_smem ? 1 : 0;
+  if (s->precision != VMCF_FP64 && s->acc_smem) {
+    // Mixed precision: the shared-memory accumulator is FP32 and is meant for the few walkers of
+    // one CTA; with the grid capped by the scratch a CTA may take many, so every walker goes
+    // straight to its CTA's FP64 slot instead (one walker group per CTA).
+    lc.groups = 1;
+    lc.L = s->Lmeas;
+    lc.smem = s->Lmeas.bytes;
+    lc.acc_off = -1;
+    M.acc_in_smem = 0;
+  }
+  const int per_cta = 4 * (M.acc_in_smem ? s->gpb_meas : 1);
   long long grid = (W + per_cta - 1) / per_cta;
   if (grid > (long long)fit) grid = (long long)fit;
   if (grid > W) grid = W;
+  lc.grid = (int)grid;
   // every call reuses the scratch: clear the slots this call accumulates into
-  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(double) * (size_t)grid * accL, st);
+  e = cudaMemsetAsync(scratch, 0, sizeof(double) * (size_t)grid * accL, st);
   if (e != cudaSuccess) return vmcf::set_last_error(VMCF_ECUDA, std::string("clearing scratch: ") + cudaGetErrorString(e));
-  vmcf::MeasParams M{};
   M.pos = pos;
   M.acc = scratch;
   M.swct_off = vmcf::swct_offset(*s);
   M.accL = accL;
-  M.acc_in_smem = s->acc_smem ? 1 : 0;
   M.e_ref = e_ref;
   M.counters = reinterpret_cast<unsigned long long*>(s->scratch_counters);
   M.W = W;
-  const vmcf::Launch lc = vmcf::launch_meas(*s, (int)grid, true, false);
   e = s->precision == VMCF_FP64 ? vmcf::launch_measure<double>(s->dev, lc, M, st)
                                 : vmcf::launch_measure<float>(s->dev, lc, M, st);
   if (e != cudaSuccess) return vmcf::set_last_error(VMCF_ECUDA, std::string("measure kernel launch: ") + cudaGetErrorString(e));

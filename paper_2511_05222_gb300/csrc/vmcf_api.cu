@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/vmcf.h"
+#include "../../include/vmcf_diag.h"
 #include "vmcf_host.h"
 
 using namespace vmcf;
@@ -781,6 +782,11 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
     delete s;
     return cuda_fail(e, "cudaMalloc(system tables)");
   }
+  if ((e = cudaGetDevice(&s->device)) != cudaSuccess) {
+    cudaFree(s->dmem);
+    delete s;
+    return cuda_fail(e, "cudaGetDevice");
+  }
   char* b = static_cast<char*>(s->dmem);
   auto up = [&](size_t at, const void* src, size_t bytes) {
     return bytes ? cudaMemcpy(b + at, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
@@ -1120,7 +1126,6 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
   P.kref = refresh_k;
   P.sigma = step_sigma;
   P.eps = wk->eps;
-  P.stagger = s->stagger ? 1 : 0;
   const Launch lm = launch_rm(*s, wk->W);
   const bool fp64 = s->precision == VMCF_FP64;
   auto move = [&](int nsw, int skip) -> int {
@@ -1448,11 +1453,6 @@ int vmcf_set_tuning(vmcf_system_t s, const char* key, int value) {
     if (want && s->precision != VMCF_MIXED) return fail(VMCF_EINVAL, "tensor-core walker sums need mixed precision");
     if (s->small) s->tc_sums = want;
     else s->tcg_sums = want;
-    return VMCF_OK;
-  }
-  if (k == "stagger_refresh") {
-    if (s->small) return fail(VMCF_ENOTSUP, "staggered re-inversions need the walker-group kernels");
-    s->stagger = value != 0;
     return VMCF_OK;
   }
   if (k == "measure_group_size") {

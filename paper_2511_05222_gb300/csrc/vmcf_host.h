@@ -11,6 +11,7 @@
 
 struct vmcf_system_s {
   int precision = 0;
+  int device = -1;      // the CUDA device the system's tables live on (current at vmcf_init_system)
   int K = 0, M = 0, nup = 0, ndn = 0, Ne = 0, nshell = 0, nB = 0, nmax = 0;
   int MJ = 0, nJs = 0;  // functions and shells of the Jastrow basis (AO-expanded Jastrow terms)
   std::vector<double> R, Z, S, C[2];
@@ -37,7 +38,6 @@ struct vmcf_system_s {
   vmcf::SmallLayout SL{};
   size_t small_move_smem = 0;  // C staging of the move kernel
   int move_lpw = 2;            // lanes per walker in the move kernel (1, 2, 4 or 8)
-  bool stagger = false;        // walker-group moves: re-inversion counts offset by the walker id
   bool tc_sums = false;        // mixed small path: walker sums of O on the tensor cores
   int tc_Mp = 0, tc_Np = 0;    // padded AO rows and Y columns of those tiles
   int tc_nch = 1;              // chunks of 16 electron slots per walker

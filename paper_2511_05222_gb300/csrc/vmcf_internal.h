@@ -40,7 +40,6 @@ struct MoveParams {
   int nsweeps, kref, c0, skip_final_refresh;
   double sigma;
   double eps;       // guiding function max(1, eps sqrt(S)) of reweighted sampling; 0: plain |Psi|^2
-  int stagger;      // walker wid counts its moves from c0 + wid mod kref
 };
 
 struct MeasParams {

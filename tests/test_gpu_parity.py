@@ -174,12 +174,12 @@ def test_fp64_measured_estimators_match_the_oracle(sys0, force_group):
     np.testing.assert_array_equal(wk.block_sums()[:, 0], sums["n"])
     ref = estimators.finish(sums, e_ref)
     got = wk.reduce_estimators()
-    assert abs(got["E"] - ref["E"]) < 1e-10 * abs(ref["E"])
-    assert rel(got["F"].ravel(), ref["F"]) < 1e-9
-    assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
-    assert abs(got["E_err"] - ref["E_err"]) < 1e-8 * ref["E_err"]
-    assert rel(got["F_err"].ravel(), ref["F_err"]) < 1e-7
-    assert rel(got["dEdC_err"], ref["dEdC_err"]) < 1e-7
+    assert abs(got["E"] - ref["E"]) < TOL64 * abs(ref["E"])
+    assert rel(got["F"].ravel(), ref["F"]) < TOL64
+    assert rel(got["dEdC"], ref["dEdC"]) < TOL64
+    assert abs(got["E_err"] - ref["E_err"]) < TOL64 * ref["E_err"]
+    assert rel(got["F_err"].ravel(), ref["F_err"]) < TOL64
+    assert rel(got["dEdC_err"], ref["dEdC_err"]) < TOL64
 
 
 def test_counters_and_singular_free_run(sys1):
@@ -192,13 +192,20 @@ def test_counters_and_singular_free_run(sys1):
     assert c["singular"] == 0
 
 
+# walkers and measured sweeps of the paired mixed-vs-FP64 estimator check: the configs' own walker
+# counts (water 1024, C2OH6 16384) and, for C9O4H8, the 1024-walker subset the FP64 GPU path is
+# compared on; a mixed-precision bias does not shrink with the sample count while the error bar
+# does, so the check runs at the full sample counts
+PAIRED = {0: (1024, 100), 1: (16384, 100), 4: (1024, 40)}
+
+
 @pytest.mark.parametrize("cfg", [0, 1, 4])
 def test_mixed_estimators_within_a_tenth_of_their_error_bars(cfg):
     """Mixed-precision sampling; the FP64 path measures the same configurations after every
     sweep (paired). Every walker-averaged estimator (E, each force component, each dE/dC
     element) of the mixed path lies within 0.1 x its own jackknife error bar of the FP64 one."""
     sysx = S.make_system(cfg)
-    W = 4096 if cfg != 4 else 512
+    W, nmeas = PAIRED[cfg]
     pos = S.initial_walkers(sysx, W, seed=12)
     gm = vmcf.System(sysx, vmcf.MIXED)
     g64 = vmcf.System(sysx, vmcf.FP64)
@@ -208,11 +215,12 @@ def test_mixed_estimators_within_a_tenth_of_their_error_bars(cfg):
     e_ref = {0: -76.0, 1: -150.0, 4: -600.0}[cfg]
     wm.reset_accumulators(e_ref)
     w64.reset_accumulators(e_ref)
-    for _ in range(6):
+    for _ in range(nmeas):
         wm.sample(1, measure=True)
         w64.set_positions(wm.positions())
         w64.measure()
     em, e64 = wm.reduce_estimators(), w64.reduce_estimators()
+    assert wm.block_sums()[:, 0].sum() == W * nmeas
     assert abs(em["E"] - e64["E"]) <= 0.1 * e64["E_err"], (em["E"], e64["E"], e64["E_err"])
     dF = np.abs(em["F"] - e64["F"]) / e64["F_err"]
     assert dF.max() <= 0.1, dF.max()
@@ -260,20 +268,54 @@ def test_tensor_core_walker_sums_match_simt(cfg, force_group):
 
 
 
-def test_evaluate_mixed_local_energy_c9o4h8():
-    """94 electrons (general kernels): per-walker mixed-mode E_L on walkers drawn from |Psi|^2
-    within 1e-5 of max(|E_L|, |mean E_L|) for Slater condition numbers <= 1e4."""
+@pytest.fixture(scope="module")
+def c9o4h8_subset():
+    """1024 C9O4H8 walkers drawn from |Psi|^2 by the oracle's chain (3 sweeps from the
+    round-robin start) and the oracle's FP64 outputs on them."""
     sys4 = S.make_system(4)
     o = oracle.Oracle(sys4)
-    st = o.new_state(S.initial_walkers(sys4, 48, seed=8), key=(5222, 4))
-    o.sample(st, 20)
+    st = o.new_state(S.initial_walkers(sys4, 1024, seed=8), key=(5222, 4))
+    o.sample(st, 3)
     pos = st["pos"]
-    ref = o.eval(pos, want=("EL",))["EL"]
+    ref = o.eval(pos, want=("EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O"))
+    return sys4, pos, ref
+
+
+def test_evaluate_fp64_c9o4h8_subset(c9o4h8_subset):
+    """94 electrons, 222 AOs: every FP64 output of the 1024-walker subset within 1e-10 of the
+    oracle (normwise per tensor), and the estimators of the fixed walkers (F on all 21 nuclei,
+    dE/dC 222 x 47 per spin) within 1e-10 of the oracle's."""
+    sys4, pos, ref = c9o4h8_subset
+    g = vmcf.System(sys4, vmcf.FP64)
+    got = gpu_eval(g, pos, ("EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O"))
+    for k in ("EL", "logpsi", "dlnpsi_dR", "dEL_dR", "O"):
+        assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
+    nb, e_ref = 16, -600.0
+    wk = vmcf.Walkers(g, pos, nblocks=nb)
+    wk.reset_accumulators(e_ref)
+    wk.measure()
+    sums = estimators.new_sums(nb, sys4.K, sys4.M * sys4.Ne)
+    estimators.accumulate(sums, block_map(1024, nb), ref["EL"], ref["dlnpsi_dR"], ref["dEL_dR"], ref["O"], e_ref)
+    fin, est = estimators.finish(sums, e_ref), wk.reduce_estimators()
+    assert abs(est["E"] - fin["E"]) < TOL64 * abs(fin["E"])
+    assert rel(est["F"].ravel(), fin["F"]) < TOL64, rel(est["F"].ravel(), fin["F"])
+    assert rel(est["dEdC"], fin["dEdC"]) < TOL64, rel(est["dEdC"], fin["dEdC"])
+
+
+def test_evaluate_mixed_local_energy_c9o4h8(c9o4h8_subset):
+    """94 electrons (walker-group kernels), the 1024-walker subset drawn from |Psi|^2: per-walker
+    mixed-mode E_L within 1e-5 of max(|E_L|, |mean E_L|) for Slater condition numbers <= 1e4,
+    which at least 99% of the walkers have (as for the smaller workloads); the rest within
+    1e-9 kappa. The number of walkers beyond kappa = 1e4 is reported."""
+    sys4, pos, ref = c9o4h8_subset
     got = gpu_eval(vmcf.System(sys4, vmcf.MIXED), pos, ("EL",))["EL"]
-    r = np.abs(got - ref) / np.maximum(np.abs(ref), abs(ref.mean()))
+    r = np.abs(got - ref["EL"]) / np.maximum(np.abs(ref["EL"]), abs(ref["EL"].mean()))
     kap = slater_condition(sys4, pos)
     well = kap <= 1e4
-    assert well.mean() > 0.8
+    print(f"C9O4H8 subset: {int((~well).sum())} of {len(well)} walkers beyond kappa = 1e4; "
+          f"median rel. error {np.median(r):.2e}, max over the rest {r[well].max():.2e}")
+    assert well.mean() >= 0.99
+    assert np.median(r) < 1e-6
     assert r[well].max() < 1e-5, np.sort(r[well])[-5:]
     assert np.all(r[~well] < 1e-9 * kap[~well])
 
@@ -302,35 +344,31 @@ def test_exponential_two_body_form_fp64(sys1, force_group):
     assert np.abs(wk.positions()[ok] - st["pos"][ok]).max() < 1e-9
 
 
-@pytest.mark.parametrize("kref", [26, 7])
-def test_staggered_refresh_chain_and_estimators_follow_the_oracle(sys0, kref):
-    """Walker-group moves with staggered FP64 re-inversions (walker wid counts from the common
-    count plus wid mod k): the FP64 chain and the measured estimators follow the oracle's chain
-    with the same schedule."""
-    W, nb, warm, meas, e_ref = 128, 8, 3, 2, -76.0
-    pos = S.initial_walkers(sys0, W, seed=61)
+def test_covariance_factor_from_gpu_block_sums_matches_the_oracle(sys0):
+    """The error-propagation input (App. "Error propagation": Cov(B) = b b^T, and the same for the
+    forces) from block sums the GPU accumulated along an FP64 chain: vmcf_finish_covariance on
+    those sums against the oracle's jackknife covariance of the oracle's own chain on the same
+    walkers (same Philox streams), to 1e-10 of the largest entry."""
+    from paper_2511_05222_gb300 import distributed as D
+    W, nb, warm, meas, e_ref = 512, 16, 3, 3, -76.0
+    pos = S.initial_walkers(sys0, W, seed=71)
     o = oracle.Oracle(sys0)
     st = o.new_state(pos, key=(5222, 0))
-    o.sample(st, warm, refresh_k=kref, stagger=True)
-    g = vmcf.System(sys0, vmcf.FP64, force_group=True)
-    g.set_tuning("stagger_refresh", 1)
-    wk = vmcf.Walkers(g, pos, key=(5222, 0), nblocks=nb)
-    wk.sample(warm, 0.3, kref, measure=False)
+    o.sample(st, warm)
+    wk = vmcf.Walkers(vmcf.System(sys0, vmcf.FP64), pos, key=(5222, 0), nblocks=nb)
+    wk.sample(warm, measure=False)
     wk.reset_accumulators(e_ref)
-    wk.sample(meas, 0.3, kref, measure=True)
+    wk.sample(meas, measure=True)
     sums = estimators.new_sums(nb, sys0.K, o.nO)
     for _ in range(meas):
-        o.sample(st, 1, refresh_k=kref, stagger=True)
+        o.sample(st, 1)
         o.force_refresh(st)
         out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
         estimators.accumulate(sums, block_map(W, nb), out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], e_ref)
-    ok = st["margin"] >= 1e-9
-    assert ok.sum() >= W - 2
-    assert np.abs(wk.positions()[ok] - st["pos"][ok]).max() < 1e-9
-    if ok.all():
-        ref = estimators.finish(sums, e_ref)
-        got = wk.reduce_estimators()
-        assert abs(got["E"] - ref["E"]) < 1e-10 * abs(ref["E"])
-        assert rel(got["F"].ravel(), ref["F"]) < 1e-9
-    with pytest.raises(vmcf.VmcfError):  # the small-system kernels re-invert all walkers together
-        vmcf.System(sys0, vmcf.FP64).set_tuning("stagger_refresh", 1)
+    assert st["margin"].min() >= 1e-9  # every decision clear of a tie: the chains are the same
+    Ff, Bf = D.finish_covariance(wk.block_sums(), sys0.K, sys0.M, sys0.n_up, sys0.n_dn, e_ref)
+    cF, cB = estimators.jackknife_covariance(sums, e_ref)
+    np.testing.assert_allclose(Ff @ Ff.T, cF, rtol=0, atol=TOL64 * np.abs(cF).max())
+    np.testing.assert_allclose(Bf @ Bf.T, cB, rtol=0, atol=TOL64 * np.abs(cB).max())
+    est = wk.reduce_estimators()
+    np.testing.assert_allclose(np.sqrt(np.diag(Ff @ Ff.T)), est["F_err"].ravel(), rtol=1e-12)

@@ -651,6 +651,59 @@ def test_guided_weights_and_estimates(sys0):
     assert np.median(dF) < 1.5 and dF.max() < 5.0
 
 
+def _u01(x):
+    return float(int(x) >> 11) * (1.0 / 9007199254740992.0)
+
+
+def test_guided_chain_replayed_from_log_psi_and_fresh_inverses(sys0):
+    """Two sweeps of the oracle's guided chain equal a replay that draws the proposal and the
+    acceptance uniform from Philox4x64-10 (counter (wid, sweep, e, 0 or 1), pinned to numpy's
+    generator) and accepts when u < |Psi(r')/Psi(r)|^2 (g'/g)^2, with ln|Psi| from the oracle's
+    evaluation and g = max(1, eps sqrt(S)), S the summed squares of inverses taken afresh by numpy
+    from the oracle's Slater matrices at both configurations. The chain itself tracks S through
+    its Sherman-Morrison updates, so a dropped term of that update, or of (g'/g)^2, changes a
+    decision here."""
+    o = oracle.Oracle(sys0)
+    W, key, sigma, sweeps = 6, (5222, 91), 0.45, 2
+
+    def s_inv(x):  # (n, Ne, 3) -> S per configuration
+        n = x.shape[0]
+        ao = o.ao_eval(x.reshape(-1, 3))[:, :, 0].reshape(n, sys0.Ne, -1)
+        return (np.linalg.inv(ao[:, :sys0.n_up] @ sys0.C_up) ** 2).sum((1, 2)) + \
+               (np.linalg.inv(ao[:, sys0.n_up:] @ sys0.C_dn) ** 2).sum((1, 2))
+
+    pos0 = S.initial_walkers(sys0, W, seed=33)
+    eps = 3.0 / math.sqrt(np.median(s_inv(pos0)))  # the guide is active on many of the configurations
+    st = o.new_state(pos0, key=key)
+    o.sample(st, sweeps, sigma=sigma, refresh_k=10 ** 9, eps=eps)
+    rep = pos0.copy()
+    nacc, active = 0, 0
+    for w in range(W):
+        for sw in range(sweeps):
+            for e in range(sys0.Ne):
+                r = oracle.philox4x64_10(np.array([w, sw, e, 0], np.uint64), key)
+                u1, u2, u3, u4 = (_u01(x) for x in r)
+                a = math.sqrt(-2.0 * math.log(1.0 - u1))
+                b = math.sqrt(-2.0 * math.log(1.0 - u3))
+                xi3 = np.array([a * math.cos(2 * math.pi * u2), a * math.sin(2 * math.pi * u2),
+                                b * math.cos(2 * math.pi * u4)])
+                new = rep[w].copy()
+                new[e] += sigma * xi3
+                both = np.stack([rep[w], new])
+                lp = o.eval(both, want=("logpsi",))["logpsi"]
+                g = np.maximum(1.0, eps * np.sqrt(s_inv(both)))
+                active += int(g[0] > 1.0 or g[1] > 1.0)
+                p = math.exp(2.0 * (lp[1] - lp[0])) * (g[1] / g[0]) ** 2
+                u = _u01(oracle.philox4x64_10(np.array([w, sw, e, 1], np.uint64), key)[0])
+                assert abs(u - p) > 1e-8 * p  # the decision is not a tie at this precision
+                if u < p:
+                    rep[w] = new
+                    nacc += 1
+    np.testing.assert_allclose(st["pos"], rep, rtol=0, atol=1e-12)
+    assert 0 < nacc < W * sweeps * sys0.Ne
+    assert active > W * sweeps * sys0.Ne // 4  # the guiding factor took part in many decisions
+
+
 # ------------------------------------------------------------------ exponential two-body form
 def _with_exp_j2(sysx):
     s = copy.deepcopy(sysx)
