@@ -8,6 +8,11 @@ cudaError_t launch_move_small<float>(const DevSys& S, int nm, int lpw, int W, si
   return launch_move_small_impl<float>(S, nm, lpw, W, smem, P, st);
 }
 template <>
+cudaError_t launch_propose_small<float>(const DevSys& S, int nm, int grid, size_t smem, const SmallProposeParams& P,
+                                        cudaStream_t st) {
+  return launch_propose_small_impl<float>(S, nm, grid, smem, P, st);
+}
+template <>
 cudaError_t launch_measure_small<float>(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
                                       const SmallMeasParams& P, cudaStream_t st) {
   return launch_measure_small_impl<float>(S, nm, L, grid, warps, P, st);

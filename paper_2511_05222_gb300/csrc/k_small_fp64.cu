@@ -8,6 +8,11 @@ cudaError_t launch_move_small<double>(const DevSys& S, int nm, int lpw, int W, s
   return launch_move_small_impl<double>(S, nm, lpw, W, smem, P, st);
 }
 template <>
+cudaError_t launch_propose_small<double>(const DevSys& S, int nm, int grid, size_t smem, const SmallProposeParams& P,
+                                        cudaStream_t st) {
+  return launch_propose_small_impl<double>(S, nm, grid, smem, P, st);
+}
+template <>
 cudaError_t launch_measure_small<double>(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
                                       const SmallMeasParams& P, cudaStream_t st) {
   return launch_measure_small_impl<double>(S, nm, L, grid, warps, P, st);

@@ -1,10 +1,15 @@
 // Small-system kernels (at most 32 electrons, 16 orbitals per spin): the VMC hot path of
 // arXiv:2511.05222, App. A, laid out so that every lane does independent work.
 //
-//  move_small     LPW lanes per walker (1, 2, 4 or 8): a run of single-electron Metropolis
-//                 moves with the MO row in registers and the CTA's inverses and positions
-//                 staged walker-interleaved in shared memory (read from and written back to
-//                 walker-interleaved global memory once per launch)
+//  propose_small  one warp per walker, one lane per electron: everything of a sweep's moves that
+//                 depends only on the electron's own start-of-sweep position and its proposal
+//                 (the Philox draws, the orbital row at the proposal, the electron-nucleus Jastrow
+//                 change), for all electrons at once
+//  move_small     LPW lanes per walker (1, 2, 4 or 8): the sequential part of a run of
+//                 single-electron Metropolis moves (determinant ratio, electron-electron Jastrow
+//                 change, acceptance, Sherman-Morrison update) with the CTA's inverses and
+//                 positions staged walker-interleaved in shared memory (read from and written back
+//                 to walker-interleaved global memory once per launch)
 //  measure_small  one warp per walker, one lane per electron: two sweeps over the AOs, shell
 //                 by shell, contracted straight into register rows (C rows broadcast from
 //                 shared memory): the Slater row and the row of P = lap(phi) + 2 grad J .
@@ -100,6 +105,52 @@ __device__ __forceinline__ int shell_disp(const DevSys& S, int s, int c, const d
   }
 }
 
+// Displacement of the electron from nucleus c (double in FP64 mode; float from the float-float
+// positions in mixed mode) and, in mixed mode when ff is set, the squared distance as a float-float
+// pair (for the shells of a group with sharp primitives).
+template <typename T>
+__device__ __forceinline__ void centre_disp(const DevSys& S, int c, const double p[3], const float ph[3],
+                                            const float pl[3], bool ff, T d[3], R2FF& r2ff) {
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = p[k] - __ldg(S.R + 3 * c + k);
+  } else if (!ff) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = (ph[k] - __ldg(S.Rh + 3 * c + k)) + (pl[k] - __ldg(S.Rl + 3 * c + k));
+  } else {
+    float hsum = 0.f, lsum = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float dh, dl, sdiff, eh;
+      two_sum(ph[k], -__ldg(S.Rh + 3 * c + k), sdiff, eh);
+      fast_two_sum(sdiff, (pl[k] - __ldg(S.Rl + 3 * c + k)) + eh, dh, dl);
+      d[k] = dh;
+      const float pp = dh * dh, pe = fmaf(dh, dh, -pp);
+      float t;
+      two_sum(hsum, pp, hsum, t);
+      lsum += t + pe + 2.0f * dh * dl;
+    }
+    fast_two_sum(hsum, lsum, r2ff.h, r2ff.l);
+  }
+}
+
+// Runs f(std::integral_constant<int, l>, group, d, r2ff) for every shell group, with the displacement
+// from the group's centre taken once per group and the angular momentum a compile-time constant.
+template <typename T, typename F>
+__device__ __forceinline__ void for_each_group(const DevSys& S, const double p[3], const float ph[3], const float pl[3],
+                                               F&& f) {
+  for (int gi = 0; gi < S.ngrp; ++gi) {
+    const int4 gr = __ldg(S.shgrp + gi);
+    T d[3];
+    R2FF r2ff{0.f, 0.f};
+    centre_disp<T>(S, gr.w, p, ph, pl, (gr.z & 256) != 0, d, r2ff);
+    const int l = gr.z & 255;
+    if (l == 0) f(std::integral_constant<int, 0>{}, gr, d, r2ff);
+    else if (l == 1) f(std::integral_constant<int, 1>{}, gr, d, r2ff);
+    else f(std::integral_constant<int, 2>{}, gr, d, r2ff);
+  }
+}
+
 __device__ __forceinline__ void split_ff(double v, float& h, float& l) {
   h = (float)v;
   l = (float)(v - (double)h);
@@ -127,19 +178,78 @@ __device__ __forceinline__ T pair_at(const DevSys& S, bool par, const T d[3]) {
   return expo_value<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), dsqrt<T>(r2));
 }
 
+// A staged coefficient row (16-byte aligned, padded to a multiple of 4 entries) into registers with
+// 16-byte shared-memory loads.
+template <typename T, int NM>
+__device__ __forceinline__ void crow_load(const T* __restrict__ crow, T (&c)[NM]) {
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int i = 0; i < NM; i += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(crow + i);
+      c[i] = v.x;
+      if (i + 1 < NM) c[i + 1] = v.y;
+      if (i + 2 < NM) c[i + 2] = v.z;
+      if (i + 3 < NM) c[i + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NM; i += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(crow + i);
+      c[i] = v.x;
+      if (i + 1 < NM) c[i + 1] = v.y;
+    }
+  }
+}
+
 template <typename T, int NM>
 __device__ __forceinline__ void axpy_row(T (&acc)[NM], T a, const T* __restrict__ crow) {
+  T c[NM];
+  crow_load<T, NM>(crow, c);
 #pragma unroll
-  for (int i = 0; i < NM; ++i) acc[i] += a * crow[i];
+  for (int i = 0; i < NM; ++i) acc[i] += a * c[i];
+}
+
+// Two rows updated from one coefficient row: acc0 += a0 c, acc1 += a1 c.
+template <typename T, int NM>
+__device__ __forceinline__ void axpy2_row(T (&acc0)[NM], T a0, T (&acc1)[NM], T a1, const T* __restrict__ crow) {
+  T c[NM];
+  crow_load<T, NM>(crow, c);
+#pragma unroll
+  for (int i = 0; i < NM; ++i) {
+    acc0[i] += a0 * c[i];
+    acc1[i] += a1 * c[i];
+  }
+}
+
+// Two dot products with one coefficient row: (x0 . c, x1 . c).
+template <typename T, int NM>
+__device__ __forceinline__ void dot2_row(const T (&x0)[NM], const T (&x1)[NM], const T* __restrict__ crow, T& d0,
+                                         T& d1) {
+  T c[NM];
+  crow_load<T, NM>(crow, c);
+  T s0 = 0, s1 = 0, t0 = 0, t1 = 0;
+#pragma unroll
+  for (int i = 0; i < NM; i += 2) {
+    s0 += x0[i] * c[i];
+    t0 += x1[i] * c[i];
+    if (i + 1 < NM) {
+      s1 += x0[i + 1] * c[i + 1];
+      t1 += x1[i + 1] * c[i + 1];
+    }
+  }
+  d0 = s0 + s1;
+  d1 = t0 + t1;
 }
 
 template <typename T, int NM>
 __device__ __forceinline__ T dot_row(const T (&x)[NM], const T* __restrict__ crow) {
+  T c[NM];
+  crow_load<T, NM>(crow, c);
   T s0 = 0, s1 = 0;  // two chains for instruction-level parallelism
 #pragma unroll
   for (int i = 0; i < NM; i += 2) {
-    s0 += x[i] * crow[i];
-    if (i + 1 < NM) s1 += x[i + 1] * crow[i + 1];
+    s0 += x[i] * c[i];
+    if (i + 1 < NM) s1 += x[i + 1] * c[i + 1];
   }
   return s0 + s1;
 }
@@ -148,6 +258,29 @@ __device__ __forceinline__ T dot_row(const T (&x)[NM], const T* __restrict__ cro
 // every row starts on 16 bytes.
 template <int NM>
 __host__ __device__ constexpr int c_stride() { return (NM + 3) / 4 * 4; }
+
+// A row of c_stride<NM>() values (16-byte aligned) into NM registers with vector loads.
+template <typename T, int NM>
+__device__ __forceinline__ void load_row(const T* __restrict__ src, T (&row)[NM]) {
+  constexpr int NMS = c_stride<NM>();
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int i = 0; i < NMS; i += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(src + i));
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (i + k < NM) row[i + k] = vv[k];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NMS; i += 2) {
+      const double2 v = __ldg(reinterpret_cast<const double2*>(src + i));
+      if (i < NM) row[i] = v.x;
+      if (i + 1 < NM) row[i + 1] = v.y;
+    }
+  }
+}
 
 // Stage C^up and C^dn into shared memory as [2][M][c_stride<NM>()], zero-padded beyond n_s.
 template <typename T, int NM>
@@ -160,6 +293,109 @@ __device__ __forceinline__ void stage_C(const DevSys& S, T* Cs) {
   }
 }
 
+
+// ---------------------------------------------------------------- proposals of one sweep
+// In sweep s electron e of walker w is proposed r'_e = r_e + sigma xi, xi from the Philox counter
+// (wid, s, e, 0), and accepted against the uniform of counter (wid, s, e, 1) (App. A, MCMC). Every
+// electron moves once per sweep, so r_e is its position at the start of the sweep, and whatever
+// depends only on r_e and r'_e is the same however the sweep's earlier moves went: the draws, the
+// orbital row phi^s(r'_e) = sum_mu psi_mu(r'_e) C^s_mu of the electron's spin, and the change of the
+// electron-nucleus Jastrow terms. This kernel computes them for every electron of every walker at
+// once (one warp per walker, one lane per electron); the move kernel keeps only what depends on the
+// order of the moves.
+template <typename T, int NM>
+__global__ void __launch_bounds__(256) propose_small(DevSys S, SmallProposeParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* Cs = reinterpret_cast<T*>(smem);  // C^up, C^dn [2][M][c_stride<NM>()]
+  stage_C<T, NM>(S, Cs);
+  __syncthreads();
+  constexpr int NMS = c_stride<NM>();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int Ne = S.Ne, W = P.W, e = lane;
+  if (e >= Ne) return;  // no warp-wide operation follows
+  const int sg = e < S.nup ? 0 : 1;
+  const T* Csg = Cs + sg * S.M * NMS;
+  for (long long w = (long long)blockIdx.x * nwarps + warp; w < W; w += (long long)gridDim.x * nwarps) {
+    const uint64_t wid = P.wid0 + (uint64_t)w;
+    uint64_t r[4] = {wid, P.sweep, (uint64_t)e, 0};
+    philox4x64_10(r, P.k0, P.k1);
+    uint64_t r2[4] = {wid, P.sweep, (uint64_t)e, 1};
+    philox4x64_10(r2, P.k0, P.k1);
+    // r'_e = r_e + sigma xi: in double in FP64 mode; in mixed mode a float-float sum of the float-float
+    // position and a float step, so that no FP64 instruction is needed
+    double po[3] = {0.0, 0.0, 0.0}, rn[3] = {0.0, 0.0, 0.0};
+    float nh[3], nl[3], oh[3], ol[3];
+    if constexpr (sizeof(T) == 8) {
+      double xi[3];
+      normals3(r, xi, 0.0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        po[k] = P.pos[(size_t)(3 * e + k) * W + w];
+        rn[k] = po[k] + P.sigma * xi[k];
+      }
+    } else {
+      float xi[3];
+      normals3_f(r, xi);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float2 f = P.posf[(size_t)(3 * e + k) * W + w];
+        oh[k] = f.x;
+        ol[k] = f.y;
+        float sh, se;
+        two_sum(oh[k], P.sigma_f * xi[k], sh, se);
+        fast_two_sum(sh, se + ol[k], nh[k], nl[k]);
+      }
+    }
+    T row[NM];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) row[i] = T(0);
+    // the row at r'_e; a move's row takes no float-float a r^2 for sharp primitives (its error enters only
+    // the acceptance ratio, and the measurement rebuilds every row)
+    for_each_group<T>(S, rn, nh, nl, [&](auto Lc, const int4 gr, const T (&d)[3], const R2FF) {
+      constexpr int LA = decltype(Lc)::value;
+      const T r2s = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      for (int s = gr.x; s < gr.x + gr.y; ++s) {
+        const int4 sh = __ldg(S.shell + s);
+        const Radial<T> rs = radial_sums<T, 0>(S, s, LA, sh.z, r2s, 0, R2FF{0.f, 0.f});
+#pragma unroll
+        for (int m = 0; m < 2 * LA + 1; ++m) {
+          T Pa, g[3], h[6];
+          angular<T>(LA, m, d[0], d[1], d[2], Pa, g, h);
+          axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * NMS);
+        }
+      }
+    });
+    T dchi = T(0);
+    if (S.J1) {
+      for (int I = 0; I < S.K; ++I) {
+        const T mz = (T)(-__ldg(S.Z + I)), b = (T)S.ben;
+        T d1[3], d0[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if constexpr (sizeof(T) == 8) {
+            d1[k] = rn[k] - __ldg(S.R + 3 * I + k);
+            d0[k] = po[k] - __ldg(S.R + 3 * I + k);
+          } else {
+            d1[k] = (nh[k] - __ldg(S.Rh + 3 * I + k)) + (nl[k] - __ldg(S.Rl + 3 * I + k));
+            d0[k] = (oh[k] - __ldg(S.Rh + 3 * I + k)) + (ol[k] - __ldg(S.Rl + 3 * I + k));
+          }
+        }
+        dchi += pade_at<T>(mz, b, d1) - pade_at<T>(mz, b, d0);
+      }
+    }
+    const size_t pe = (size_t)w * Ne + e;
+    T* rw = reinterpret_cast<T*>(P.pr.rows) + pe * NMS;
+#pragma unroll
+    for (int i = 0; i < NMS; ++i) rw[i] = i < NM ? row[i] : T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if constexpr (sizeof(T) == 8) P.pr.rnew[pe * 3 + k] = rn[k];
+      else reinterpret_cast<float2*>(P.pr.rnew)[pe * 3 + k] = make_float2(nh[k], nl[k]);
+    }
+    P.pr.u[pe] = u01_bits(r2[0]);
+    reinterpret_cast<T*>(P.pr.dchi)[pe] = dchi;
+  }
+}
 
 // ---------------------------------------------------------------- moves, LPW lanes per walker
 // Sum over the LPW lanes of a walker (xor butterfly: every lane receives the same bits).
@@ -176,15 +412,13 @@ __device__ __forceinline__ V lane_group_sum(V v, unsigned mask) {
 template <typename T, int NM, int LPW, bool GUIDE>
 __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  // shared memory: C^up, C^dn [2][M][c_stride<NM>()]; the CTA's inverses walker-interleaved [nB][WPC]; its
-  // positions [3 Ne][WPC] (float-float pairs in mixed mode, double in FP64 mode)
-  T* Cs = reinterpret_cast<T*>(smem);
+  // shared memory: the CTA's inverses walker-interleaved [nB][WPC]; its positions [3 Ne][WPC]
+  // (float-float pairs in mixed mode, double in FP64 mode)
   const int WPC = P.wpc;
-  T* Bs = Cs + 2 * S.M * c_stride<NM>();
+  T* Bs = reinterpret_cast<T*>(smem);
   using PosT = typename std::conditional<sizeof(T) == 4, float2, double>::type;
-  PosT* Ps = reinterpret_cast<PosT*>(Bs + (size_t)S.nB * WPC);
-  stage_C<T, NM>(S, Cs);
-  const int W = P.W, Ne = S.Ne, nup = S.nup, K = S.K, nB = S.nB;
+  PosT* Ps = reinterpret_cast<PosT*>(smem + (sizeof(T) * (size_t)S.nB * WPC + 7) / 8 * 8);  // move_small_smem
+  const int W = P.W, Ne = S.Ne, nup = S.nup, nB = S.nB;
   const int wbase = blockIdx.x * WPC;
   T* Bg = reinterpret_cast<T*>(P.B);
   for (int idx = threadIdx.x; idx < nB * WPC; idx += blockDim.x) {
@@ -194,14 +428,8 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
   for (int idx = threadIdx.x; idx < 3 * Ne * WPC; idx += blockDim.x) {
     const int k = idx / WPC, ws = idx - k * WPC;
     if (wbase + ws < W) {
-      const double v = P.pos[(size_t)k * W + wbase + ws];
-      if constexpr (sizeof(T) == 4) {
-        float h, l;
-        split_ff(v, h, l);
-        Ps[idx] = make_float2(h, l);
-      } else {
-        Ps[idx] = v;
-      }
+      if constexpr (sizeof(T) == 4) Ps[idx] = P.posf[(size_t)k * W + wbase + ws];
+      else Ps[idx] = P.pos[(size_t)k * W + wbase + ws];
     }
   }
   __syncthreads();
@@ -213,7 +441,6 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
   const unsigned mask = (LPW == 32) ? 0xffffffffu : (((1u << LPW) - 1u) << ((threadIdx.x & 31) & ~(LPW - 1)));
   T* B = Bs + ws;     // element k of this walker's inverses at B[k * WPC]
   PosT* pp = Ps + ws;  // coordinate k of this walker's electrons at pp[k * WPC]
-  const uint64_t wid = P.wid0 + (uint64_t)w;
   uint32_t nacc = 0, nrej = 0;
   // reweighted sampling of |Psi_G|^2, Psi_G = Psi max(1, eps sqrt(S)): S of the current inverses
   constexpr bool guide = GUIDE;  // P.eps > 0
@@ -222,62 +449,68 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
     for (int k = q; k < nB; k += LPW) Sg += (double)B[k * WPC] * (double)B[k * WPC];
     Sg = lane_group_sum<LPW>(Sg, mask);
   }
+  // a launch never crosses a sweep: its moves are electrons e0, e0 + 1, ... of one sweep
+  const int e0 = (int)(P.move0 % (uint64_t)Ne);
+  // this sweep's proposals, one move ahead: the loads of move mv + 1 are in flight while move mv runs
+  T rowc[NM], rown[NM];
+  double rnc[3], rnn[3], uc = 0.0, un = 0.0;
+  T dcc = T(0), dcn = T(0);
+  auto fetch = [&](int mv) {
+    const size_t pe = (size_t)w * Ne + e0 + mv;
+    load_row<T, NM>(reinterpret_cast<const T*>(P.pr.rows) + pe * c_stride<NM>(), rown);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rnn[k] = __ldg(P.pr.rnew + pe * 3 + k);
+    un = __ldg(P.pr.u + pe);
+    dcn = __ldg(reinterpret_cast<const T*>(P.pr.dchi) + pe);
+  };
+  if (P.nmoves > 0) fetch(0);
   for (int mv = 0; mv < P.nmoves; ++mv) {
-    const uint64_t gm = P.move0 + (uint64_t)mv;
-    const int e = (int)(gm % (uint64_t)Ne);
-    const uint64_t sweep = gm / (uint64_t)Ne;
+    const int e = e0 + mv;
     const int sg = e < nup ? 0 : 1;
     const int n = sg == 0 ? nup : S.ndn, el = e - (sg == 0 ? 0 : nup);
     const int off = sg == 0 ? 0 : nup * nup;
-    const T* Csg = Cs + sg * S.M * c_stride<NM>();
-    uint64_t r[4] = {wid, sweep, (uint64_t)e, 0};
-    philox4x64_10(r, P.k0, P.k1);
-    double xi[3];
-    normals3(r, xi, T(0));
-    double po[3], rn[3];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) rowc[i] = rown[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rnc[k] = rnn[k];
+    uc = un;
+    dcc = dcn;
+    if (mv + 1 < P.nmoves) fetch(mv + 1);
+    const T (&row)[NM] = rowc;
+    double po[3] = {0.0, 0.0, 0.0}, rn[3] = {0.0, 0.0, 0.0};
     float nh[3], nl[3], oh[3], ol[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      po[k] = P.pos[(size_t)(3 * e + k) * W + w];
-      rn[k] = po[k] + P.sigma * xi[k];
-      split_ff(rn[k], nh[k], nl[k]);
-      if constexpr (sizeof(T) == 4) {
+      if constexpr (sizeof(T) == 8) {
+        po[k] = P.pos[(size_t)(3 * e + k) * W + w];
+        rn[k] = rnc[k];
+      } else {  // r'_e as a float-float pair in the proposal's bytes; r_e from shared memory
+        nh[k] = __int_as_float(__double2loint(rnc[k]));
+        nl[k] = __int_as_float(__double2hiint(rnc[k]));
         const float2 f = pp[(3 * e + k) * WPC];
         oh[k] = f.x;
         ol[k] = f.y;
       }
     }
-    // new orbital row: this lane's shells, then the group sum
-    T row[NM];
-#pragma unroll
-    for (int i = 0; i < NM; ++i) row[i] = T(0);
-    for (int s = q; s < S.nshell; s += LPW) {
-      const int4 sh = __ldg(S.shell + s);
-      T d[3];
-      if constexpr (sizeof(T) == 8) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) d[k] = rn[k] - __ldg(S.R + 3 * sh.x + k);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) d[k] = (nh[k] - __ldg(S.Rh + 3 * sh.x + k)) + (nl[k] - __ldg(S.Rl + 3 * sh.x + k));
-      }
-      const T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-      const Radial<T> rs = radial_sums<T, 0>(S, s, sh.y, sh.z, r2, 0, R2FF{0.f, 0.f});
-      for (int m = 0; m < 2 * sh.y + 1; ++m) {
-        T Pa, g[3], h[6];
-        angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
-        axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * c_stride<NM>());
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < NM; ++i) row[i] = lane_group_sum<LPW>(row[i], mask);
-    // determinant ratio (FP64): this lane's orbitals i = q, q + LPW, ...
+    // determinant ratio (FP64): this lane's orbitals i = q, q + LPW, ...; the lane's row entry is picked
+    // by selects so that each FP64 FMA is issued once per LPW orbitals (the FP64 pipe charges a whole
+    // warp instruction whatever the number of active lanes)
     double R = 0.0;
 #pragma unroll
-    for (int i = 0; i < NM; ++i)
-      if (i % LPW == q && i < n) R += (double)row[i] * (double)B[(off + i * n + el) * WPC];
+    for (int ii = 0; ii < (NM + LPW - 1) / LPW; ++ii) {
+      T rv = row[ii * LPW];
+#pragma unroll
+      for (int k = 1; k < LPW; ++k)
+        if (ii * LPW + k < NM && q == k) rv = row[ii * LPW + k];
+      const int i = ii * LPW + q;
+      if (i < n) {
+        if constexpr (sizeof(T) == 8) R += rv * B[(off + i * n + el) * WPC];
+        else R += f2d_bits(rv) * f2d_bits(B[(off + i * n + el) * WPC]);
+      }
+    }
     R = lane_group_sum<LPW>(R, mask);
-    // Jastrow ratio: this lane's partners j = q, q + LPW, ... and nuclei I = q, q + LPW, ...
+    // electron-electron Jastrow ratio: this lane's partners j = q, q + LPW, ... at their current
+    // positions; the electron-nucleus change came with the proposal
     T jacc = 0;
     if (S.J2) {
       for (int j = q; j < Ne; j += LPW) {
@@ -299,44 +532,35 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
         jacc += pair_at<T>(S, par, d1) - pair_at<T>(S, par, d0);
       }
     }
-    if (S.J1) {
-      for (int I = q; I < K; I += LPW) {
-        const T mz = (T)(-__ldg(S.Z + I)), b = (T)S.ben;
-        T d1[3], d0[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          if constexpr (sizeof(T) == 8) {
-            d1[k] = rn[k] - __ldg(S.R + 3 * I + k);
-            d0[k] = po[k] - __ldg(S.R + 3 * I + k);
-          } else {
-            d1[k] = (nh[k] - __ldg(S.Rh + 3 * I + k)) + (nl[k] - __ldg(S.Rl + 3 * I + k));
-            d0[k] = (oh[k] - __ldg(S.Rh + 3 * I + k)) + (ol[k] - __ldg(S.Rl + 3 * I + k));
-          }
-        }
-        jacc += pade_at<T>(mz, b, d1) - pade_at<T>(mz, b, d0);
-      }
+    const double u = uc;
+    // |R exp(dJ)|^2 with R in FP64; in mixed mode the Jastrow factor is formed in float
+    double pr;
+    if constexpr (sizeof(T) == 8) {
+      const double dJ = lane_group_sum<LPW>(jacc, mask) + dcc;
+      pr = R * R * exp(2.0 * dJ);
+    } else {
+      const float dJ = lane_group_sum<LPW>(jacc, mask) + dcc;
+      pr = R * R * f2d_bits(expf(2.0f * dJ));
     }
-    const double dJ = (double)lane_group_sum<LPW>(jacc, mask);
-    uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
-    philox4x64_10(r2, P.k0, P.k1);
-    const double u = u01(r2[0]);
-    double pr = R * R * (double)dexp<T>((T)(2.0 * dJ));
     // Sherman-Morrison: w_j = sum_i row_i B_ij - delta_j,el; B_kj <- B_kj - B_k,el w_j / R.
     // This lane owns columns j = q, q + LPW, ...; every lane reads the whole column el first.
-    T wv[NM], col[NM];
+    // This lane owns columns j = jj LPW + q; its vector entries sit at wv[jj] (compile-time index).
+    constexpr int NJ = (NM + LPW - 1) / LPW;
+    T wv[NJ], col[NM];
     auto sm_vectors = [&]() {
 #pragma unroll
-      for (int j = 0; j < NM; ++j) {
-        wv[j] = T(0);
-        col[j] = (j < n) ? B[(off + j * n + el) * WPC] : T(0);
-      }
+      for (int j = 0; j < NM; ++j) col[j] = (j < n) ? B[(off + j * n + el) * WPC] : T(0);
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj) wv[jj] = T(0);
 #pragma unroll
       for (int i = 0; i < NM; ++i) {
         if (i >= n) continue;
         const T ri = row[i];
 #pragma unroll
-        for (int j = 0; j < NM; ++j)
-          if (j % LPW == q && j < n) wv[j] += ri * B[(off + i * n + j) * WPC];
+        for (int jj = 0; jj < NJ; ++jj) {
+          const int j = jj * LPW + q;
+          if (j < n) wv[jj] += ri * B[(off + i * n + j) * WPC];
+        }
       }
     };
     double Sn = Sg;
@@ -345,15 +569,17 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
       sm_vectors();
       double tw = 0.0, ww = 0.0, cc = 0.0;
 #pragma unroll
-      for (int j = 0; j < NM; ++j) {
+      for (int j = 0; j < NM; ++j)
+        if (j < n) cc += (double)col[j] * (double)col[j];
+#pragma unroll
+      for (int jj = 0; jj < NJ; ++jj) {
+        const int j = jj * LPW + q;
         if (j >= n) continue;
-        cc += (double)col[j] * (double)col[j];
-        if (j % LPW != q) continue;
         T tj = 0;
 #pragma unroll
         for (int i = 0; i < NM; ++i)
           if (i < n) tj += col[i] * B[(off + i * n + j) * WPC];
-        const double wj = (double)((j == el) ? wv[j] - T(1) : wv[j]);
+        const double wj = (double)((j == el) ? wv[jj] - T(1) : wv[jj]);
         tw += wj * (double)tj;
         ww += wj * wj;
       }
@@ -363,17 +589,21 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
       const double g0 = fmax(1.0, P.eps * sqrt(Sg)), g1 = fmax(1.0, P.eps * sqrt(fmax(Sn, 0.0)));
       pr *= (g1 / g0) * (g1 / g0);
     }
-    const bool ok = isfinite(pr) && R != 0.0;
+    // finite and non-zero, tested on the bits (no FP64 compare)
+    const bool ok = ((__double2hiint(pr) >> 20) & 0x7ff) != 0x7ff && (__double_as_longlong(R) << 1) != 0;
     if (!ok) ++nrej;
     if (ok && u < pr) {
       if constexpr (!guide) sm_vectors();
       Sg = Sn;
       if (LPW > 1) __syncwarp(mask);  // column el is read by all lanes before its owner rewrites it
-      const T rinv = (T)(1.0 / R);
+      T rinv;
+      if constexpr (sizeof(T) == 8) rinv = 1.0 / R;
+      else rinv = __frcp_rn(d2f_trunc(R));  // the update itself is FP32
 #pragma unroll
-      for (int j = 0; j < NM; ++j) {
-        if (j % LPW != q || j >= n) continue;
-        const T wj = (j == el) ? wv[j] - T(1) : wv[j];
+      for (int jj = 0; jj < NJ; ++jj) {
+        const int j = jj * LPW + q;
+        if (j >= n) continue;
+        const T wj = (j == el) ? wv[jj] - T(1) : wv[jj];
 #pragma unroll
         for (int k = 0; k < NM; ++k) {
           if (k >= n) continue;
@@ -384,9 +614,13 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
       if (q == 0) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          P.pos[(size_t)(3 * e + k) * W + w] = rn[k];
-          if constexpr (sizeof(T) == 4) pp[(3 * e + k) * WPC] = make_float2(nh[k], nl[k]);
-          else pp[(3 * e + k) * WPC] = rn[k];
+          if constexpr (sizeof(T) == 4) {
+            pp[(3 * e + k) * WPC] = make_float2(nh[k], nl[k]);
+            P.pos[(size_t)(3 * e + k) * W + w] = f2d_bits(nh[k]) + f2d_bits(nl[k]);  // exact
+          } else {
+            pp[(3 * e + k) * WPC] = rn[k];
+            P.pos[(size_t)(3 * e + k) * W + w] = rn[k];
+          }
         }
       }
       ++nacc;
@@ -397,9 +631,12 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
     P.nacc[w] += nacc;
     P.nrej[w] += nrej;
   }
-  // this walker's inverses back to global memory (its lanes share the copy)
+  // this walker's inverses (and, in mixed mode, float-float positions) back to global memory (its lanes
+  // share the copy)
   if (LPW > 1) __syncwarp(mask);
   for (int k = q; k < nB; k += LPW) Bg[(size_t)k * W + w] = B[k * WPC];
+  if constexpr (sizeof(T) == 4)
+    for (int k = q; k < 3 * Ne; k += LPW) P.posf[(size_t)k * W + w] = pp[k * WPC];
 }
 
 // ---------------------------------------------------------------- both spin blocks' FP64 inverses
@@ -442,7 +679,8 @@ static __device__ __forceinline__ void gj_inverse_pair(double* A0, int n0, doubl
     if (act && hl == 0) {
       pv[k] = bi;
       const double p = A[bi * n + k];
-      if (!(p != 0.0) || !isfinite(p)) *flag = 1;
+      const long long pb = __double_as_longlong(p);  // zero or not finite: tested on the bits
+      if ((pb << 1) == 0 || ((pb >> 52) & 0x7ff) == 0x7ff) *flag = 1;
       ff[n] = 1.0 / p;
       if (want_logdet) {
         la += log(fabs(p));
@@ -581,11 +819,17 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
     }
     __syncwarp();  // every electron's position visible to the warp
     const bool full = P.mode != 0;  // mode 0 only rebuilds the inverses
-    // ---- Jastrow and potentials (lane = electron)
+    // ---- Jastrow and potentials (lane = electron). E_L takes the 1/r parts of -1/2 lap J per pair and per
+    // nucleus together with the Coulomb terms they cancel at coalescence (the cusps), in forms without
+    // that cancellation. With q = 1/(1 + F r): a nucleus of charge Z with chi = -Z r q gives
+    //   -1/2 (2 chi'/r) - Z/r = -Z (1 - q^2)/r = -Z F q (q + 1);
+    // a pair with u = a r q gives, per electron (half the pair's 1/r),
+    //   -1/2 (2 u'/r) + 1/(2 r) = (1/2 - a)/r + a F q (q + 1)
+    // (exponential form u = (a/F)(1 - exp(-F r)): (1/2 - a)/r - a expm1(-F r)/r). The remaining Jastrow
+    // Laplacian terms u'', chi'' go to jl.
     T jg[3] = {T(0), T(0), T(0)}, jl = T(0);
-    double vpart[4] = {0.0, 0.0, 0.0, 0.0};  // kinetic, V_ee, V_en, J
+    T vee = 0, ven = 0, jv = 0, te = 0;  // pair and nucleus terms as above, J, and the kinetic term of this electron
     if (full && has_e) {
-      T vee = 0, ven = 0, jv = 0;
       for (int j = 0; j < Ne; ++j) {
         if (j == e) continue;
         T d[3];
@@ -594,16 +838,33 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
           if constexpr (sizeof(T) == 8) d[k] = p[k] - pd[3 * j + k];
           else d[k] = (hh[k] - ph[3 * j + k]) + (ll[k] - pl[3 * j + k]);
         }
-        const T r = dsqrt<T>(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), ri = T(1) / r;
-        if (j > e) vee += ri;
+        T r, ri;
+        dist_inv<T>(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r, ri);
         if (S.J2) {
           const bool par = (j < nup) == (e < nup);
-          const Rad3<T> u = pair_rad<T>(S, par, r);
-          const T gr = u.h1 * ri;
+          const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+          T h, h1, h2, reg;
+          if (!S.j2exp) {
+            const T q = fast_rcp<T>(T(1) + F * r), q2 = q * q;
+            h = a * r * q;
+            h1 = a * q2;
+            h2 = T(-2) * a * F * q2 * q;
+            reg = a * F * q * (q + T(1));
+          } else {
+            const T ex = dexp<T>(-F * r), em1 = dexpm1<T>(-F * r);
+            h = -(a / F) * em1;
+            h1 = a * ex;
+            h2 = -a * F * ex;
+            reg = -a * em1 * ri;
+          }
+          const T gr = h1 * ri;
 #pragma unroll
           for (int k = 0; k < 3; ++k) jg[k] += gr * d[k];
-          jl += u.h2 + T(2) * gr;
-          if (j > e) jv += u.h;
+          jl += h2;
+          vee += (T(0.5) - a) * ri + reg;
+          if (j > e) jv += h;
+        } else {
+          vee += T(0.5) * ri;
         }
       }
       for (int I = 0; I < K; ++I) {
@@ -613,21 +874,21 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
           if constexpr (sizeof(T) == 8) d[k] = p[k] - __ldg(S.R + 3 * I + k);
           else d[k] = (hh[k] - __ldg(S.Rh + 3 * I + k)) + (ll[k] - __ldg(S.Rl + 3 * I + k));
         }
-        const T r = dsqrt<T>(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]), ri = T(1) / r;
-        const T Z = (T)__ldg(S.Z + I);
-        ven -= Z * ri;
+        T r, ri;
+        dist_inv<T>(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r, ri);
+        const T Z = to_T<T>(__ldg(S.Z + I));
         if (S.J1) {
-          const Rad3<T> c = pade<T>(-Z, (T)S.ben, r);
-          const T gr = c.h1 * ri;
+          const T b = (T)S.ben, q = fast_rcp<T>(T(1) + b * r), q2 = q * q;
+          const T gr = -Z * q2 * ri;  // chi'/r
 #pragma unroll
           for (int k = 0; k < 3; ++k) jg[k] += gr * d[k];
-          jl += c.h2 + T(2) * gr;
-          jv += c.h;
+          jl += T(2) * Z * b * q2 * q;  // chi''
+          ven -= Z * b * q * (q + T(1));
+          jv -= Z * r * q;
+        } else {
+          ven -= Z * ri;
         }
       }
-      vpart[1] = (double)vee;
-      vpart[2] = (double)ven;
-      vpart[3] = (double)jv;
     }
 
     // ---- pass 1: the Slater row (one per lane) -> FP64 -> Gauss-Jordan per spin; when measuring, in
@@ -640,51 +901,60 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       for (int i = 0; i < NM; ++i) row[i] = T(0);
       const T* Csg = Cs + sg * M * c_stride<NM>();
       if (!full) {
-        for (int s = 0; s < S.nshell; ++s) {
-          const int4 sh = __ldg(S.shell + s);
-          T d[3];
-          R2FF r2ff{0.f, 0.f};
-          const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
-          const Radial<T> rs = radial_sums<T, 0>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
-          for (int m = 0; m < 2 * sh.y + 1; ++m) {
-            T Pa, g[3], h[6];
-            angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
-            axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * c_stride<NM>());
+        for_each_group<T>(S, p, hh, ll, [&](auto Lc, const int4 gr, const T (&d)[3], const R2FF r2ff) {
+          constexpr int LA = decltype(Lc)::value;
+          const T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+          for (int s = gr.x; s < gr.x + gr.y; ++s) {
+            const int4 sh = __ldg(S.shell + s);
+            const int smask = sizeof(T) == 4 ? __ldg(S.sharp + s) : 0;
+            const Radial<T> rs = radial_sums<T, 0>(S, s, LA, sh.z, r2, smask, r2ff);
+#pragma unroll
+            for (int m = 0; m < 2 * LA + 1; ++m) {
+              T Pa, g[3], h[6];
+              angular<T>(LA, m, d[0], d[1], d[2], Pa, g, h);
+              axpy_row<T, NM>(row, Pa * rs.R0, Csg + (sh.w + m) * c_stride<NM>());
+            }
           }
-        }
+        });
       } else {
         T prow[NM];
 #pragma unroll
         for (int i = 0; i < NM; ++i) prow[i] = T(0);
-        for (int s = 0; s < S.nshell; ++s) {
-          const int4 sh = __ldg(S.shell + s);
-          T d[3];
-          R2FF r2ff{0.f, 0.f};
-          const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
-          const Radial<T> rs = radial_sums<T, 1>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
-          const T xjR1 = T(2) * (d[0] * jg[0] + d[1] * jg[1] + d[2] * jg[2]) * rs.R1;
-          for (int m = 0; m < 2 * sh.y + 1; ++m) {
-            T Pa, g[3], h[6];
-            angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
-            const T* cr = Csg + (sh.w + m) * c_stride<NM>();
-            axpy_row<T, NM>(row, Pa * rs.R0, cr);
-            // lap psi = P LF; grad psi = g R0 + P d R1
-            const T gj2 = T(2) * (g[0] * jg[0] + g[1] * jg[1] + g[2] * jg[2]);
-            axpy_row<T, NM>(prow, Pa * (rs.LF + xjR1) + gj2 * rs.R0, cr);
+        for_each_group<T>(S, p, hh, ll, [&](auto Lc, const int4 gr, const T (&d)[3], const R2FF r2ff) {
+          constexpr int LA = decltype(Lc)::value;
+          const T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+          const T xj2 = T(2) * (d[0] * jg[0] + d[1] * jg[1] + d[2] * jg[2]);
+          for (int s = gr.x; s < gr.x + gr.y; ++s) {
+            const int4 sh = __ldg(S.shell + s);
+            const int smask = sizeof(T) == 4 ? __ldg(S.sharp + s) : 0;
+            const Radial<T> rs = radial_sums<T, 1>(S, s, LA, sh.z, r2, smask, r2ff);
+            const T xjR1 = xj2 * rs.R1;
+#pragma unroll
+            for (int m = 0; m < 2 * LA + 1; ++m) {
+              T Pa, g[3], h[6];
+              angular<T>(LA, m, d[0], d[1], d[2], Pa, g, h);
+              // lap psi = P LF; grad psi = g R0 + P d R1
+              const T gj2 = T(2) * (g[0] * jg[0] + g[1] * jg[1] + g[2] * jg[2]);
+              axpy2_row<T, NM>(row, Pa * rs.R0, prow, Pa * (rs.LF + xjR1) + gj2 * rs.R0,
+                               Csg + (sh.w + m) * c_stride<NM>());
+            }
           }
-        }
+        });
 #pragma unroll
         for (int i = 0; i < NM; ++i)
           if (i < n) Pm[off + el * n + i] = prow[i];
       }
 #pragma unroll
       for (int i = 0; i < NM; ++i)
-        if (i < n) Ad[off + el * n + i] = (double)row[i];
+        if (i < n) {
+          if constexpr (sizeof(T) == 8) Ad[off + el * n + i] = row[i];
+          else Ad[off + el * n + i] = f2d_bits(row[i]);  // exact, no FP64 conversion instruction
+        }
     }
     __syncwarp();
     gj_inverse_pair(Ad, nup, Ad + nup * nup, ndn, S.nmax, piv, f, flag, la, sgn, P.logpsi != nullptr);
     if (static_cast<void*>(Bf) != static_cast<void*>(Ad))
-      for (int i = lane; i < S.nB; i += 32) Bf[i] = (T)Ad[i];
+      for (int i = lane; i < S.nB; i += 32) Bf[i] = to_T<T>(Ad[i]);
     __syncwarp();
     if (P.Bout && P.mode != 1) {
       T* Bg = reinterpret_cast<T*>(P.Bout);
@@ -716,16 +986,32 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
 #pragma unroll
       for (int i = 0; i < NM; ++i)
         if (i < n) ps += Pm[off + el * n + i] * bc[i];
-      const T te = ps + jl + (jg[0] * jg[0] + jg[1] * jg[1] + jg[2] * jg[2]);
-      vpart[0] = -0.5 * (double)te;
+      te = ps + jl + (jg[0] * jg[0] + jg[1] * jg[1] + jg[2] * jg[2]);
     }
-    warp_sum_f<4>(vpart);
-    const double EL = vpart[0] + vpart[1] + vpart[2] + S.Vnn;
+    // E_L = sum over electrons of -te/2 + V_ee + V_en, plus V_nn: summed in FP64 (in mixed mode as
+    // float-float pairs, about 44 bits, on the FP32 pipe)
+    double EL;
+    if constexpr (sizeof(T) == 8) {
+      EL = warp_sum(-0.5 * te + vee + ven) + S.Vnn;
+    } else {
+      float h, l;
+      two_sum(-0.5f * te, vee, h, l);
+      ff_add(h, l, ven, 0.0f, h, l);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+        ff_add(h, l, h2, l2, h, l);
+      }
+      EL = (f2d_bits(h) + f2d_bits(l)) + S.Vnn;
+    }
+    const double jsum = P.logpsi ? warp_sum((double)jv) : 0.0;  // ln|Psi| wanted (evaluation only)
     const double cw = EL - P.e_ref;
+    // the weights of this walker's sums in the working precision
+    const T wtT = to_T<T>(wt), wcwT = to_T<T>(wt * cw), wcw2T = to_T<T>(wt * cw * cw);
     if (P.mode == 1 && !P.dlnpsi && !P.dEL && !P.O) {  // E_L and ln|Psi| only: no adjoint pass
       if (lane == 0) {
         if (P.EL) P.EL[w] = EL;
-        if (P.logpsi) P.logpsi[w] = *la + vpart[3];
+        if (P.logpsi) P.logpsi[w] = *la + jsum;
       }
       __syncwarp();
       continue;
@@ -830,8 +1116,8 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
           const int mu = chunk0 + c;
           if (P.O) P.O[(size_t)w * nO + ooff + mu * ng + i] = (double)s;
           if (accum) {
-            atomicAdd(&acc_s[3 + 9 * K + ooff + mu * ng + i], (T)wt * s);
-            atomicAdd(&acc_s[3 + 9 * K + nO + ooff + mu * ng + i], (T)(wt * cw) * s);
+            atomicAdd(&acc_s[3 + 9 * K + ooff + mu * ng + i], wtT * s);
+            atomicAdd(&acc_s[3 + 9 * K + nO + ooff + mu * ng + i], wcwT * s);
           }
         }
       }
@@ -839,51 +1125,64 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       chunk0 += chunk_n;
       chunk_n = 0;
     };
-    for (int s = 0; s < S.nshell; ++s) {
-      const int4 sh = __ldg(S.shell + s);
-      const int ncomp = 2 * sh.y + 1;
-      if (chunk_n + ncomp > L.chunk) flush_chunk();
-      if (sh.x != cur) {
+    for_each_group<T>(S, p, hh, ll, [&](auto Lc, const int4 gr, const T (&d)[3], const R2FF r2ff) {
+      constexpr int LA = decltype(Lc)::value, ncomp = 2 * LA + 1;
+      if (gr.w != cur) {
         if (cur >= 0) flush_centre(cur);
-        cur = sh.x;
+        cur = gr.w;
       }
-      if (has_e) {
-        T d[3];
-        R2FF r2ff{0.f, 0.f};
-        const int smask = shell_disp<T>(S, s, sh.x, p, hh, ll, d, r2ff);
-        const Radial<T> rs = radial_sums<T, 2>(S, s, sh.y, sh.z, d[0] * d[0] + d[1] * d[1] + d[2] * d[2], smask, r2ff);
-        const T xj = d[0] * jg[0] + d[1] * jg[1] + d[2] * jg[2];
-        for (int m = 0; m < ncomp; ++m) {
-          T Pa, g[3], h[6];
-          angular<T>(sh.y, m, d[0], d[1], d[2], Pa, g, h);
-          const T* cr = Csg + (sh.w + m) * c_stride<NM>();
-          const T yA = dot_row<T, NM>(xr, cr), yL = dot_row<T, NM>(bc, cr);
-          // Hessian of the AO contracted with grad J without forming it:
-          // (H j)_a = (h j)_a R0 + g_a (x.j) R1 + (g.j) x_a R1 + P x_a (x.j) R2 + P j_a R1
-          const T hj0 = h[0] * jg[0] + h[3] * jg[1] + h[4] * jg[2];
-          const T hj1 = h[3] * jg[0] + h[1] * jg[1] + h[5] * jg[2];
-          const T hj2 = h[4] * jg[0] + h[5] * jg[1] + h[2] * jg[2];
-          const T hjv[3] = {hj0, hj1, hj2};
-          const T gj = g[0] * jg[0] + g[1] * jg[1] + g[2] * jg[2];
-          const T PxjR2 = Pa * xj * rs.R2, gjR1 = gj * rs.R1, PR1 = Pa * rs.R1, xjR1 = xj * rs.R1;
+      const T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+      const T xj = d[0] * jg[0] + d[1] * jg[1] + d[2] * jg[2];
+      for (int s = gr.x; s < gr.x + gr.y; ++s) {
+        const int4 sh = __ldg(S.shell + s);
+        if (chunk_n + ncomp > L.chunk) flush_chunk();
+        if (has_e) {
+          const int smask = sizeof(T) == 4 ? __ldg(S.sharp + s) : 0;
+          const Radial<T> rs = radial_sums<T, 2>(S, s, LA, sh.z, r2, smask, r2ff);
+          // Every force term of an AO is linear in its harmonic P_m, its gradient g_m and its constant Hessian
+          // h_m, so the weights y_A, y_L (back-projected adjoint weights C X and C B of this electron) are folded
+          // over the shell's components first, and the radial factors applied once per shell:
+          //   sum_m y_m grad psi_m = R0 G + d R1 S, sum_m y_m grad lap psi_m = LF G + d T3 S,
+          //   sum_m y_m (Hess psi_m) j = R0 H + G (d.j) R1 + d (G.j) R1 + S d (d.j) R2 + S j R1,
+          // with S = sum_m y_m P_m, G = sum_m y_m g_m, H = sum_m y_m h_m j.
+          T SA = T(0), SL = T(0), GA[3] = {T(0), T(0), T(0)}, GL[3] = {T(0), T(0), T(0)}, HL[3] = {T(0), T(0), T(0)};
+#pragma unroll
+          for (int m = 0; m < ncomp; ++m) {
+            T Pa, g[3], h[6];
+            angular<T>(LA, m, d[0], d[1], d[2], Pa, g, h);
+            T yA, yL;
+            dot2_row<T, NM>(xr, bc, Csg + (sh.w + m) * c_stride<NM>(), yA, yL);
+            SA += yA * Pa;
+            SL += yL * Pa;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              GA[k] += yA * g[k];
+              GL[k] += yL * g[k];
+            }
+            HL[0] += yL * (h[0] * jg[0] + h[3] * jg[1] + h[4] * jg[2]);
+            HL[1] += yL * (h[3] * jg[0] + h[1] * jg[1] + h[5] * jg[2]);
+            HL[2] += yL * (h[4] * jg[0] + h[5] * jg[1] + h[2] * jg[2]);
+            if (tc)
+              reinterpret_cast<__nv_bfloat16*>(P.phiT[sg])[((size_t)w * P.Mp + sh.w + m) * 16 + el] =
+                  __float2bfloat16_rn((float)(Pa * rs.R0));
+            else
+              phi[e * L.chunk + chunk_n + m] = Pa * rs.R0;
+          }
+          const T GLj = GL[0] * jg[0] + GL[1] * jg[1] + GL[2] * jg[2];
+          const T xjR1 = xj * rs.R1, SLR1 = SL * rs.R1, cR = GLj * rs.R1 + SL * xj * rs.R2;
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            const T gv = g[k] * rs.R0 + Pa * d[k] * rs.R1;
-            const T gl = g[k] * rs.LF + Pa * d[k] * rs.T3;
-            const T hj = hjv[k] * rs.R0 + g[k] * xjR1 + d[k] * (gjR1 + PxjR2) + jg[k] * PR1;
-            fl[k] -= gv * yL;
-            const T cde = T(-0.5) * (gv * yA - yL * (gl + T(2) * hj));
-            fe[k] += cde;
+            const T gvL = GL[k] * rs.R0 + d[k] * SLR1;
+            const T gvA = GA[k] * rs.R0 + d[k] * (SA * rs.R1);
+            const T glL = GL[k] * rs.LF + d[k] * (SL * rs.T3);
+            const T hjL = HL[k] * rs.R0 + GL[k] * xjR1 + d[k] * cR + jg[k] * SLR1;
+            fl[k] -= gvL;
+            fe[k] += T(-0.5) * (gvA - (glL + T(2) * hjL));
           }
-          if (tc)
-            reinterpret_cast<__nv_bfloat16*>(P.phiT[sg])[((size_t)w * P.Mp + sh.w + m) * 16 + el] =
-                __float2bfloat16_rn((float)(Pa * rs.R0));
-          else
-            phi[e * L.chunk + chunk_n + m] = Pa * rs.R0;
         }
+        chunk_n += ncomp;
       }
-      chunk_n += ncomp;
-    }
+    });
     if (cur >= 0) flush_centre(cur);
     flush_chunk();
     if (tc && has_e) {  // Y rows: B_{i, el} and (E_L - E_ref) B_{i, el}
@@ -891,8 +1190,8 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
 #pragma unroll
       for (int i = 0; i < NM; ++i)
         if (i < n) {
-          y[i * 16 + el] = __float2bfloat16_rn((float)((T)wt * bc[i]));
-          y[(n + i) * 16 + el] = __float2bfloat16_rn((float)((T)(wt * cw) * bc[i]));
+          y[i * 16 + el] = __float2bfloat16_rn((float)(wtT * bc[i]));
+          y[(n + i) * 16 + el] = __float2bfloat16_rn((float)(wcwT * bc[i]));
         }
     }
     // e-n Jastrow and V_en derivatives, one nucleus at a time; an electron moving is the
@@ -907,14 +1206,15 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
           if constexpr (sizeof(T) == 8) sd[k] = p[k] - __ldg(S.R + 3 * I + k);
           else sd[k] = (hh[k] - __ldg(S.Rh + 3 * I + k)) + (ll[k] - __ldg(S.Rl + 3 * I + k));
         }
-        const T r = dsqrt<T>(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]), ri = T(1) / r;
-        const T Z = (T)__ldg(S.Z + I);
+        T r, ri;
+        dist_inv<T>(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2], r, ri);
+        const T Z = to_T<T>(__ldg(S.Z + I));
         const T nn[3] = {sd[0] * ri, sd[1] * ri, sd[2] * ri};
         const T ven = -Z * ri * ri * ri;
 #pragma unroll
         for (int k = 0; k < 3; ++k) c6[3 + k] = ven * sd[k];
         if (S.J1) {
-          const Rad3<T> c = pade<T>(-Z, (T)S.ben, r);
+          const Rad3<T> c = pade_fast<T>(-Z, (T)S.ben, r);
           const T gs[3] = {gd[0] + jg[0], gd[1] + jg[1], gd[2] + jg[2]};
           const T dl = c.h3 + T(2) * c.h2 * ri - T(2) * c.h1 * ri * ri;
 #pragma unroll
@@ -1038,23 +1338,22 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
     }
     // ---- outputs and walker sums
     for (int i = lane; i < 3 * K; i += 32) {
-      const double dl = (double)frc[i];
-      const double de = (double)frc[3 * K + i] + __ldg(S.dVnn + i);
-      if (P.dlnpsi) P.dlnpsi[(size_t)w * 3 * K + i] = dl;
-      if (P.dEL) P.dEL[(size_t)w * 3 * K + i] = de;
-      if (accum) {
-        atomicAdd(&acc_s[3 + i], (T)(wt * de));
-        atomicAdd(&acc_s[3 + 3 * K + i], (T)(wt * dl));
-        atomicAdd(&acc_s[3 + 6 * K + i], (T)(wt * cw * dl));
+      if (P.dlnpsi) P.dlnpsi[(size_t)w * 3 * K + i] = (double)frc[i];
+      if (P.dEL) P.dEL[(size_t)w * 3 * K + i] = (double)frc[3 * K + i] + __ldg(S.dVnn + i);
+      if (accum) {  // the CTA's accumulator is in the working precision
+        const T dl = frc[i], de = frc[3 * K + i] + to_T<T>(__ldg(S.dVnn + i));
+        atomicAdd(&acc_s[3 + i], wtT * de);
+        atomicAdd(&acc_s[3 + 3 * K + i], wtT * dl);
+        atomicAdd(&acc_s[3 + 6 * K + i], wcwT * dl);
       }
     }
     if (lane == 0) {
       if (P.EL) P.EL[w] = EL;
-      if (P.logpsi) P.logpsi[w] = *la + vpart[3];
+      if (P.logpsi) P.logpsi[w] = *la + jsum;
       if (accum) {
-        atomicAdd(&acc_s[0], (T)wt);
-        atomicAdd(&acc_s[1], (T)(wt * cw));
-        atomicAdd(&acc_s[2], (T)(wt * cw * cw));
+        atomicAdd(&acc_s[0], wtT);
+        atomicAdd(&acc_s[1], wcwT);
+        atomicAdd(&acc_s[2], wcw2T);
       }
     }
     __syncwarp();
@@ -1095,11 +1394,17 @@ static __global__ void from_interleaved(const double* __restrict__ src, double* 
   }
 }
 
+// Shared memory of the move kernel for wpc walkers per CTA: inverses (padded to 8 bytes) and positions.
+template <typename T>
+size_t move_small_smem(const DevSys& S, int wpc) {
+  return ((sizeof(T) * (size_t)S.nB * wpc + 7) / 8 * 8) + 8 * (size_t)(3 * S.Ne) * wpc;
+}
+
 template <typename T, int NM>
 cudaError_t launch_move_small_lpw(int lpw, const DevSys& S, int W, size_t smem, const SmallMoveParams& P,
                                   cudaStream_t st) {
   const int threads = (P.wpc * lpw + 31) / 32 * 32;
-  smem += (sizeof(T) * (size_t)S.nB + (sizeof(T) == 4 ? 8 : 8) * (size_t)(3 * S.Ne)) * P.wpc;
+  smem += move_small_smem<T>(S, P.wpc);
   const dim3 grid((unsigned)((W + P.wpc - 1) / P.wpc));
   if (P.eps > 0.0) {  // guided sampling: one lane-group width (the launch planned it with lpw = 2)
     if (lpw != 2) return cudaErrorInvalidValue;
@@ -1121,6 +1426,18 @@ cudaError_t launch_move_small_impl(const DevSys& S, int nm, int lpw, int W, size
   if (nm <= 8) return launch_move_small_lpw<T, 8>(lpw, S, W, smem, P, st);
   if (nm <= 14) return launch_move_small_lpw<T, 14>(lpw, S, W, smem, P, st);
   return launch_move_small_lpw<T, 16>(lpw, S, W, smem, P, st);
+}
+
+template <typename T>
+cudaError_t launch_propose_small_impl(const DevSys& S, int nm, int grid, size_t smem, const SmallProposeParams& P,
+                                      cudaStream_t st) {
+  if (nm <= 8)
+    propose_small<T, 8><<<grid, 256, smem, st>>>(S, P);
+  else if (nm <= 14)
+    propose_small<T, 14><<<grid, 256, smem, st>>>(S, P);
+  else
+    propose_small<T, 16><<<grid, 256, smem, st>>>(S, P);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -1147,6 +1464,9 @@ cudaError_t set_smem_limits_small_impl() {
   VMCF_MOVE_ATTR(16, 1, false) VMCF_MOVE_ATTR(16, 2, false) VMCF_MOVE_ATTR(16, 4, false) VMCF_MOVE_ATTR(16, 8, false)
   VMCF_MOVE_ATTR(8, 2, true) VMCF_MOVE_ATTR(14, 2, true) VMCF_MOVE_ATTR(16, 2, true)
 #undef VMCF_MOVE_ATTR
+  if ((e = cudaFuncSetAttribute(propose_small<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(propose_small<T, 14>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(propose_small<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(measure_small<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(measure_small<T, 14>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(measure_small<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;

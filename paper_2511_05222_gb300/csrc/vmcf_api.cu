@@ -421,7 +421,7 @@ int launch_small_measure(vmcf_system_s* s, int grid, const SmallMeasParams& P, c
 int move_walkers_per_cta(const vmcf_system_s& s, int W, int lpw) {
   const size_t tsz = s.precision == VMCF_FP64 ? 8 : 4;
   const size_t per = tsz * s.nB + 8 * 3 * (size_t)s.Ne;
-  const size_t room = (size_t)kSmemCap - s.small_move_smem;
+  const size_t room = (size_t)kSmemCap - 8;  // inverses and positions only (8 bytes of alignment padding)
   int cap = (int)std::min<size_t>(room / per, (size_t)(256 / lpw));  // 256 threads per CTA at most
   int want = (W + s.small_sms - 1) / s.small_sms;
   return std::max(1, std::min(cap, want));
@@ -760,8 +760,22 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
         CfT[sg][(size_t)i * M + mu] = (float)s->C[sg][(size_t)mu * n + i];
       }
   }
+  // shell groups: maximal runs of consecutive shells with one centre and one angular momentum,
+  // (first shell, count, l + 256 if a shell of the run has sharp primitives, centre)
+  std::vector<int4> groups;
+  for (int sh = 0; sh < (int)shells.size(); ++sh) {
+    const int sflag = sharp[sh] ? 256 : 0;
+    if (!groups.empty() && groups.back().w == shells[sh].x && (groups.back().z & 255) == shells[sh].y &&
+        groups.back().x + groups.back().y == sh) {
+      ++groups.back().y;
+      groups.back().z |= sflag;
+    } else {
+      groups.push_back(make_int4(sh, 1, shells[sh].y | sflag, shells[sh].x));
+    }
+  }
   size_t off = 0;
   auto slot = [&](size_t bytes) { size_t at = off; off = (off + bytes + 255) & ~size_t(255); return at; };
+  const size_t oGrp = slot(sizeof(int4) * groups.size());
   const size_t oR = slot(8 * s->R.size()), oZ = slot(8 * s->Z.size()), oSh = slot(sizeof(int4) * shells.size()),
                oA = slot(8 * alpha.size()), oC = slot(8 * coef.size()), oAf = slot(4 * alpha.size()),
                oCf = slot(4 * coef.size()), oAoc = slot(4 * (size_t)M), oC0 = slot(8 * s->C[0].size()),
@@ -795,6 +809,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   ce = ce ? ce : up(oR, s->R.data(), 8 * s->R.size());
   ce = ce ? ce : up(oZ, s->Z.data(), 8 * s->Z.size());
   ce = ce ? ce : up(oSh, shells.data(), sizeof(int4) * shells.size());
+  ce = ce ? ce : up(oGrp, groups.data(), sizeof(int4) * groups.size());
   ce = ce ? ce : up(oA, alpha.data(), 8 * alpha.size());
   ce = ce ? ce : up(oC, coef.data(), 8 * coef.size());
   ce = ce ? ce : up(oAf, alpha_f.data(), 4 * alpha_f.size());
@@ -847,6 +862,8 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   D.R = reinterpret_cast<const double*>(b + oR);
   D.Z = reinterpret_cast<const double*>(b + oZ);
   D.shell = reinterpret_cast<const int4*>(b + oSh);
+  D.shgrp = reinterpret_cast<const int4*>(b + oGrp);
+  D.ngrp = (int)groups.size();
   D.alpha = reinterpret_cast<const double*>(b + oA);
   D.coef = reinterpret_cast<const double*>(b + oC);
   D.alpha_f = reinterpret_cast<const float*>(b + oAf);
@@ -909,6 +926,25 @@ int vmcf_system_info(vmcf_system_t s, int* K, int* M, int* n_up, int* n_dn) {
 
 int vmcf_accumulator_length(vmcf_system_t s) { return s ? s->accL : VMCF_EINVAL; }
 
+// One sweep's proposals of every walker (small-system path): orbital rows, proposed positions,
+// acceptance uniforms and electron-nucleus Jastrow changes, in one allocation.
+static cudaError_t alloc_proposals(const vmcf_system_s* s, vmcf_walkers_s* wk) {
+  const size_t tsz = s->precision == VMCF_FP64 ? 8 : 4, n = (size_t)wk->W * s->Ne;
+  const int nms = (s->small_nm + 3) / 4 * 4;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t o_rows = 0, o_rnew = o_rows + al(tsz * n * nms), o_u = o_rnew + al(24 * n), o_dchi = o_u + al(8 * n),
+               bytes = o_dchi + al(tsz * n);
+  cudaError_t e = cudaMalloc(&wk->prop, bytes);
+  if (e != cudaSuccess) return e;
+  char* b = static_cast<char*>(wk->prop);
+  wk->pr.rows = b + o_rows;
+  wk->pr.rnew = reinterpret_cast<double*>(b + o_rnew);
+  wk->pr.u = reinterpret_cast<double*>(b + o_u);
+  wk->pr.dchi = b + o_dchi;
+  wk->pr.nms = nms;
+  return cudaSuccess;
+}
+
 int vmcf_walkers_create(vmcf_system_t s, int W, const double* pos, int is_host, uint64_t key0, uint64_t key1,
                         uint64_t wid0, int nblocks, void* stream, vmcf_walkers_t* out) {
   if (!out) return fail(VMCF_EINVAL, "out is NULL");
@@ -952,6 +988,7 @@ int vmcf_walkers_create(vmcf_system_t s, int W, const double* pos, int is_host, 
       (e = cudaMalloc(&wk->blocks, 8 * (size_t)nblocks * s->accL)) ||
       (s->small && (e = cudaMalloc(&wk->stage, 8 * npos))) ||
       (s->small && s->precision == VMCF_MIXED && (e = cudaMalloc(&wk->posf, sizeof(float2) * npos))) ||
+      (s->small && (e = alloc_proposals(s, wk))) ||
       (((s->small && s->tc_sums) || (!s->small && s->tcg_sums)) && (e = alloc_tc(s, wk)))) {
     vmcf_walkers_destroy(wk);
     return fail(VMCF_ENOMEM, std::string("walker state allocation: ") + cudaGetErrorString(e));
@@ -991,6 +1028,7 @@ int vmcf_walkers_destroy(vmcf_walkers_t wk) {
   cudaFree(wk->blocks);
   cudaFree(wk->stage);
   cudaFree(wk->posf);
+  cudaFree(wk->prop);
   for (int k = 0; k < 2; ++k) {
     cudaFree(wk->phiT[k]);
     cudaFree(wk->yT[k]);
@@ -1079,7 +1117,26 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
     M.eps = wk->eps;
     M.e_ref = wk->e_ref;
     M.counters = wk->counters;
+    P.pr = wk->pr;
+    SmallProposeParams Q{};
+    Q.pos = wk->pos;
+    Q.posf = wk->posf;
+    Q.pr = wk->pr;
+    Q.W = wk->W;
+    Q.wid0 = wk->wid0;
+    Q.k0 = wk->k0;
+    Q.k1 = wk->k1;
+    Q.sigma = step_sigma;
+    Q.sigma_f = (float)step_sigma;
+    const int qgrid = std::max(1, std::min((wk->W + 7) / 8, 8 * s->small_sms));
     for (int sw = 0; sw < n_sweeps; ++sw) {
+      {  // the sweep's proposals, from the positions at its start
+        Timed tm(wk, 0, st);
+        Q.sweep = wk->sweep;
+        cudaError_t e = fp64 ? launch_propose_small<double>(s->dev, s->small_nm, qgrid, s->small_move_smem, Q, st)
+                             : launch_propose_small<float>(s->dev, s->small_nm, qgrid, s->small_move_smem, Q, st);
+        if (e != cudaSuccess) return cuda_fail(e, "small proposal kernel launch");
+      }
       int done = 0;
       while (done < s->Ne) {
         const int chunk = std::min(s->Ne - done, refresh_k - wk->counter);
@@ -1088,8 +1145,8 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
         {
           Timed tm(wk, 0, st);
           cudaError_t e =
-              fp64 ? launch_move_small<double>(s->dev, s->small_nm, lpw, wk->W, s->small_move_smem, P, st)
-                   : launch_move_small<float>(s->dev, s->small_nm, lpw, wk->W, s->small_move_smem, P, st);
+              fp64 ? launch_move_small<double>(s->dev, s->small_nm, lpw, wk->W, 0, P, st)
+                   : launch_move_small<float>(s->dev, s->small_nm, lpw, wk->W, 0, P, st);
           if (e != cudaSuccess) return cuda_fail(e, "small move kernel launch");
         }
         done += chunk;

@@ -18,6 +18,9 @@ struct DevSys {
   const double* R;       // [K][3]
   const double* Z;       // [K]
   const int4* shell;     // (center, l, nprim, ao0)
+  const int4* shgrp;     // runs of consecutive shells with one centre and one l: (first shell, count,
+                         // l + 256 if a shell of the run has sharp primitives, center)
+  int ngrp;
   const double* alpha;   // [nshell][kMaxPrim]
   const double* coef;    // [nshell][kMaxPrim], normalised contraction coefficients
   const float* alpha_f;
@@ -168,6 +171,64 @@ __device__ __forceinline__ void philox4x64_10(uint64_t x[4], uint64_t k0, uint64
 // 53 random bits -> [0, 1)
 __device__ __forceinline__ double u01(uint64_t x) { return (double)(x >> 11) * 0x1.0p-53; }
 
+// The same value as u01(x), (x >> 11) 2^-53, assembled from its bits with integer instructions: on
+// this GPU every FP64 instruction (the integer-to-double conversion and the scaling of u01 included)
+// takes the FP64 pipe for a whole warp, whatever the number of active lanes.
+__device__ __forceinline__ double u01_bits(uint64_t x) {
+  const uint64_t v = x >> 11;  // 53 bits
+  if (v == 0) return 0.0;
+  const int n = __clzll(v);   // 11 ... 63; v = 2^(63 - n) (1.f), value 2^(10 - n) (1.f)
+  const uint64_t mant = ((v << n) << 1) >> 12;
+  return __longlong_as_double((long long)(((uint64_t)(1033 - n) << 52) | mant));
+}
+
+// float -> double, exact, with integer instructions only (zeros, denormals, infinities and NaNs
+// included), so that no conversion instruction reaches the FP64 pipe.
+__device__ __forceinline__ double f2d_bits(float x) {
+  const unsigned u = __float_as_uint(x), sgn = u & 0x80000000u, a = u & 0x7fffffffu;
+  // normal numbers, infinities, NaNs: rebias the exponent (127 -> 1023; 255 -> 2047)
+  const unsigned hn = sgn | ((a >> 3) + (a >= 0x7f800000u ? 0x70000000u : 0x38000000u)), ln = a << 29;
+  // denormals a 2^-149, normalised (the leading bit of a at 31 - n); zeros keep their sign
+  const int n = __clz(a | 1u);
+  const unsigned m = (a << n) << 1;
+  const unsigned hd = a ? (sgn | ((unsigned)(905 - n) << 20) | (m >> 12)) : sgn, ld = a ? (m << 20) : 0u;
+  const bool normal = a >= 0x00800000u;
+  return __hiloint2double((int)(normal ? hn : hd), (int)(normal ? ln : ld));
+}
+
+// double -> float, truncated toward zero, with integer instructions only: magnitudes below the
+// normal floats give a signed zero, those beyond the float range a signed infinity (NaN: a NaN).
+// Within the normal range the result is at most one float ulp from the rounded conversion.
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sgn = hi & 0x80000000u, e = (hi >> 20) & 0x7ffu;
+  const unsigned nrm = sgn | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const bool nan = e == 0x7ffu && (((hi & 0xfffffu) | lo) != 0u);
+  const unsigned big = nan ? 0x7fc00000u : (sgn | 0x7f800000u);
+  return __uint_as_float(e < 897u ? sgn : (e > 1150u ? big : nrm));
+}
+
+// double -> float, rounded to nearest (ties to even), with integer instructions only; outside the
+// normal float range as d2f_trunc (signed zero below, signed infinity above).
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned sgn = hi & 0x80000000u, e = (hi >> 20) & 0x7ffu;
+  unsigned nrm = sgn | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;  // the 29 discarded bits
+  nrm += (rest > 0x10000000u || (rest == 0x10000000u && (nrm & 1u))) ? 1u : 0u;  // a carry bumps the exponent
+  const bool nan = e == 0x7ffu && (((hi & 0xfffffu) | lo) != 0u);
+  const unsigned big = nan ? 0x7fc00000u : (sgn | 0x7f800000u);
+  return __uint_as_float(e < 897u ? sgn : (e > 1150u ? big : nrm));
+}
+
+// A double operand in the working precision: itself in FP64 mode, rounded to float with integer
+// instructions in mixed mode (no FP64 conversion instruction).
+template <typename T>
+__device__ __forceinline__ T to_T(double x) {
+  if constexpr (sizeof(T) == 8) return x;
+  else return d2f_rn(x);
+}
+
 // Three standard normals (Box-Muller on 4 uniforms) for one proposal.
 __device__ __forceinline__ void normals3(const uint64_t r[4], double xi[3], double) {
   const double twopi = 6.283185307179586;
@@ -189,6 +250,20 @@ __device__ __forceinline__ void normals3(const uint64_t r[4], double xi[3], floa
   xi[2] = (double)(b * cosf(twopi * (float)u01(r[3])));
 }
 
+// Three standard normals in float (Box-Muller on 24-bit uniforms k 2^-24, 1 - u inside the log):
+// the proposals of the mixed-precision chains, drawn from the same Philox outputs as normals3.
+__device__ __forceinline__ void normals3_f(const uint64_t r[4], float xi[3]) {
+  const float twopi = 6.2831853071795865f;
+  const float v1 = 1.0f - (float)(unsigned)(r[0] >> 40) * 0x1.0p-24f;
+  const float v3 = 1.0f - (float)(unsigned)(r[2] >> 40) * 0x1.0p-24f;
+  const float a = sqrtf(-2.0f * logf(v1)), b = sqrtf(-2.0f * logf(v3));
+  float sn, cs;
+  sincosf(twopi * ((float)(unsigned)(r[1] >> 40) * 0x1.0p-24f), &sn, &cs);
+  xi[0] = a * cs;
+  xi[1] = a * sn;
+  xi[2] = b * cosf(twopi * ((float)(unsigned)(r[3] >> 40) * 0x1.0p-24f));
+}
+
 // Error-free float transformations (Knuth two-sum; Dekker fast two-sum, |a| >= |b|).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -198,6 +273,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   e = b - (s - a);
+}
+
+// Float-float addition (h1 + l1) + (h2 + l2) -> (h + l), about 44 significant bits.
+__device__ __forceinline__ void ff_add(float h1, float l1, float h2, float l2, float& h, float& l) {
+  float s, e;
+  two_sum(h1, h2, s, e);
+  e += l1 + l2;
+  fast_two_sum(s, e, h, l);
 }
 
 // Squared distance of a shell's centre as a float-float pair (r2h + r2l), formed from the
@@ -421,6 +504,34 @@ template <typename T>
 __device__ __forceinline__ T pade_value(T a, T F, T r) {
   return a * r / (T(1) + F * r);
 }
+// The same in mixed mode with the approximate reciprocal (a few float ulp; these terms are summed
+// in float with many others) and, for a pair at squared distance r2, 1/r and r from the approximate
+// reciprocal square root; in FP64 mode the exact operations.
+template <typename T>
+__device__ __forceinline__ Rad3<T> pade_fast(T a, T F, T r) {
+  if constexpr (sizeof(T) == 8) {
+    return pade<T>(a, F, r);
+  } else {
+    const float q = __fdividef(1.0f, 1.0f + F * r);
+    const float q2 = q * q;
+    return {a * r * q, a * q2, -2.0f * a * F * q2 * q, 6.0f * a * F * F * q2 * q2};
+  }
+}
+template <typename T>
+__device__ __forceinline__ T fast_rcp(T x) {
+  if constexpr (sizeof(T) == 8) return 1.0 / x;
+  else return __fdividef(1.0f, x);
+}
+template <typename T>
+__device__ __forceinline__ void dist_inv(T r2, T& r, T& ri) {
+  if constexpr (sizeof(T) == 8) {
+    r = sqrt(r2);
+    ri = 1.0 / r;
+  } else {
+    ri = rsqrtf(r2);
+    r = r2 * ri;
+  }
+}
 
 // Exponential form (a / F)(1 - exp(-F r)) (Eq. twobody_v_exp, cusp a) and its derivatives.
 template <typename T> __device__ __forceinline__ T dexpm1(T x);
@@ -441,6 +552,11 @@ template <typename T>
 __device__ __forceinline__ Rad3<T> pair_rad(const DevSys& S, bool par, T r) {
   const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
   return S.j2exp ? expo<T>(a, F, r) : pade<T>(a, F, r);
+}
+template <typename T>
+__device__ __forceinline__ Rad3<T> pair_rad_fast(const DevSys& S, bool par, T r) {
+  const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+  return S.j2exp ? expo<T>(a, F, r) : pade_fast<T>(a, F, r);
 }
 template <typename T>
 __device__ __forceinline__ T pair_value(const DevSys& S, bool par, T r) {

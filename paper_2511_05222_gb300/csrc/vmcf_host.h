@@ -36,7 +36,7 @@ struct vmcf_system_s {
   int small_res = 1;          // resident measurement CTAs on the device
   int small_sms = 1;          // SMs on the device
   vmcf::SmallLayout SL{};
-  size_t small_move_smem = 0;  // C staging of the move kernel
+  size_t small_move_smem = 0;  // C staging of the proposal kernel
   int move_lpw = 2;            // lanes per walker in the move kernel (1, 2, 4 or 8)
   bool tc_sums = false;        // mixed small path: walker sums of O on the tensor cores
   int tc_Mp = 0, tc_Np = 0;    // padded AO rows and Y columns of those tiles
@@ -72,6 +72,8 @@ struct vmcf_walkers_s {
   size_t tc_slot_doubles = 0;
   bool tc = false;
   double* stage = nullptr;  // [W][Ne][3] staging for layout conversion
+  void* prop = nullptr;     // small-system path: one sweep's proposals (see pr)
+  vmcf::SmallProposals pr{};
   // per-kernel timing (kind 0 move, 1 measure, 2 refresh): event pairs around launches
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;

@@ -71,10 +71,32 @@ template <typename T>
 cudaError_t set_smem_limits(int GS);
 
 // ---- small-system path (kernels_small.cuh)
+// The proposals of one sweep for every walker and electron (filled by propose_small before the
+// sweep's moves): electron e of walker w at index w * Ne + e.
+struct SmallProposals {
+  void* rows;    // T [W][Ne][nms]: orbital row phi(r'_e) of the electron's spin (zero beyond n_s)
+  double* rnew;  // [W][Ne][3]: proposed position r'_e (FP64 mode); mixed mode: the same bytes hold
+                 // float2 [W][Ne][3], r'_e as float-float pairs (high, low)
+  double* u;     // [W][Ne]: acceptance uniform
+  void* dchi;    // T [W][Ne]: change of the electron-nucleus Jastrow terms, chi(r'_e) - chi(r_e)
+  int nms;       // row stride (c_stride of the register-row width)
+};
+
+struct SmallProposeParams {
+  const double* pos;   // [3 Ne][W], positions at the start of the sweep (FP64 mode)
+  const float2* posf;  // [3 Ne][W], the same as float-float pairs (mixed mode)
+  SmallProposals pr;
+  int W;
+  uint64_t wid0, k0, k1, sweep;
+  double sigma;
+  float sigma_f;
+};
+
 struct SmallMoveParams {
   double* pos;   // [3 Ne][W]
   float2* posf;  // [3 Ne][W] float-float (mixed mode) or NULL
   void* B;       // T [nB][W]
+  SmallProposals pr;  // this sweep's proposals
   uint32_t* nacc;
   uint32_t* nrej;
   int W;
@@ -115,6 +137,9 @@ struct SmallMeasParams {
 template <typename T>
 cudaError_t launch_move_small(const DevSys& S, int nm, int lpw, int W, size_t smem, const SmallMoveParams& P,
                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_propose_small(const DevSys& S, int nm, int grid, size_t smem, const SmallProposeParams& P,
+                                 cudaStream_t st);
 template <typename T>
 cudaError_t launch_measure_small(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
                                  const SmallMeasParams& P, cudaStream_t st);

@@ -7,7 +7,10 @@ The cases cover a grid the scratch does not cap (water, C2OH6 at a few hundred w
 grids it does (C2OH6 at 16384 walkers, C9O4H8 at 1024 walkers: more CTAs than the 2^21-double
 scratch holds partial sums for, so each CTA takes many walkers), in FP64 and in mixed
 precision. Both entry points run the walker-group kernels here (the systems are built with
-the group path), so the per-walker values are the same and the sums agree to FP64 rounding."""
+the group path). In FP64 the sums agree to 1e-10 (the FP64 tolerance of the parity tests). In
+mixed precision a wide walker group (C9O4H8: 256 threads per walker) adds the per-walker force
+partials with FP32 shared-memory atomics whose order changes from launch to launch, so two calls
+differ by FP32 rounding of those terms; the sums are held to 1e-6 there."""
 import ctypes
 
 import numpy as np
@@ -69,14 +72,15 @@ def test_noalloc_sums_match_evaluate_on_two_calls(cfg, precision, calls):
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert got[0] == W, (call, got[0])
+        tol = 1e-10 if precision == vmcf.FP64 else 1e-6
         scale = np.abs(EL).sum()
-        assert abs(got[1] - ref[1]) < 1e-10 * scale, (call, got[1], ref[1])
+        assert abs(got[1] - ref[1]) < tol * scale, (call, got[1], ref[1])
         K3, nO = 3 * g.K, g.nO
         seg = [(0, 3), (3, 3 + K3), (3 + K3, 3 + 2 * K3), (3 + 2 * K3, 3 + 3 * K3), (3 + 3 * K3, 3 + 3 * K3 + nO),
                (3 + 3 * K3 + nO, 3 + 3 * K3 + 2 * nO)]
-        for a, b in seg:  # 1e-10 relative, normwise per segment (the FP64 tolerance of the parity tests)
+        for a, b in seg:  # relative, normwise per segment
             err = np.abs(got[a:b] - ref[a:b]).max() / max(np.abs(ref[a:b]).max(), 1e-300)
-            assert err < 1e-10, (call, a, b, err)
+            assert err < tol, (call, a, b, err)
 
 
 def test_noalloc_rejects_another_current_device_and_bad_sizes():
