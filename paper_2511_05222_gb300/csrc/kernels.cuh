@@ -26,9 +26,7 @@ __device__ __forceinline__ void load_positions(const double* src, int n3, double
   for (int i = t; i < n3; i += GS) {
     const double v = src[i];
     pos[i] = v;
-    const float h = (float)v;
-    ph[i] = h;
-    pl[i] = (float)(v - (double)h);
+    split_ff_bits(v, ph[i], pl[i]);
   }
 }
 
@@ -203,7 +201,7 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
         } else {
           if (!S.J1) continue;
           const int I = q - Ne;
-          const T mz = (T)(-__ldg(S.Z + I)), b = (T)S.ben;
+          const T mz = -nuc_Z<T>(S, I), b = jas_b<T>(S);
           T d1[3], d0[3];
           disp_nuc<T>(S, pn, I, d1);
           disp_nuc<T>(S, po, I, d0);
@@ -350,8 +348,12 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
   }
   gsync<GS>();
 
-  // Jastrow gradient/Laplacian per electron, Jastrow value and potentials.
-  double vs[3] = {0.0, 0.0, 0.0};  // V_ee, V_en, J
+  // Jastrow gradient/Laplacian per electron, Jastrow value and potentials. The 1/r parts of -1/2 lap J
+  // per pair and per nucleus are taken together with the Coulomb terms they cancel at coalescence, in
+  // forms without that cancellation: with q = 1/(1 + F r), -1/2 (2 chi'/r) - Z/r = -Z F q (q + 1) for
+  // chi = -Z r q, and per electron of a pair with u = a r q, -1/2 (2 u'/r) + 1/(2 r) = (1/2 - a)/r +
+  // a F q (q + 1) (exponential form: (1/2 - a)/r - a expm1(-F r)/r); jl keeps u'' and chi''.
+  double vs[3] = {0.0, 0.0, 0.0};  // pair terms, nucleus terms, J
   for (int e = t; e < Ne; e += GS) {
     T jg0 = 0, jg1 = 0, jg2 = 0, jl = 0;
     const bool up = e < nup;
@@ -360,16 +362,32 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       const T dx = edisp<T>(pos, ph, pl, e, j, 0), dy = edisp<T>(pos, ph, pl, e, j, 1),
               dz = edisp<T>(pos, ph, pl, e, j, 2);
       const T r = dsqrt<T>(dx * dx + dy * dy + dz * dz), ri = T(1) / r;
-      if (j > e) vs[0] += (double)ri;
       if (S.J2) {
         const bool par = (j < nup) == up;
-        const Rad3<T> u = pair_rad<T>(S, par, r);
-        const T gr = u.h1 * ri;
+        const T a = jas_a<T>(S, par), F = jas_F<T>(S, par);
+        T h, h1, h2, reg;
+        if (!S.j2exp) {
+          const T q = T(1) / (T(1) + F * r), q2 = q * q;
+          h = a * r * q;
+          h1 = a * q2;
+          h2 = T(-2) * a * F * q2 * q;
+          reg = a * F * q * (q + T(1));
+        } else {
+          const T ex = dexp<T>(-F * r), em1 = dexpm1<T>(-F * r);
+          h = -(a / F) * em1;
+          h1 = a * ex;
+          h2 = -a * F * ex;
+          reg = -a * em1 * ri;
+        }
+        const T gr = h1 * ri;
         jg0 += gr * dx;
         jg1 += gr * dy;
         jg2 += gr * dz;
-        jl += u.h2 + T(2) * u.h1 * ri;
-        if (j > e) vs[2] += (double)u.h;
+        jl += h2;
+        vs[0] += (double)((T(0.5) - a) * ri + reg);
+        if (j > e) vs[2] += (double)h;
+      } else {
+        vs[0] += (double)(T(0.5) * ri);
       }
     }
     const EPos pe = make_epos(pos + 3 * e);
@@ -378,16 +396,18 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       disp_nuc<T>(S, pe, I, dd);
       const T dx = dd[0], dy = dd[1], dz = dd[2];
       const T r = dsqrt<T>(dx * dx + dy * dy + dz * dz), ri = T(1) / r;
-      const T Z = (T)S.Z[I];
-      vs[1] -= (double)(Z * ri);
+      const T Z = nuc_Z<T>(S, I);
       if (S.J1) {
-        const Rad3<T> c = pade<T>(-Z, (T)S.ben, r);
-        const T gr = c.h1 * ri;
+        const T b = jas_b<T>(S), q = T(1) / (T(1) + b * r), q2 = q * q;
+        const T gr = -Z * q2 * ri;  // chi'/r
         jg0 += gr * dx;
         jg1 += gr * dy;
         jg2 += gr * dz;
-        jl += c.h2 + T(2) * c.h1 * ri;
-        vs[2] += (double)c.h;
+        jl += T(2) * Z * b * q2 * q;  // chi''
+        vs[1] -= (double)(Z * b * q * (q + T(1)));
+        vs[2] -= (double)(Z * r * q);
+      } else {
+        vs[1] -= (double)(Z * ri);
       }
     }
     Jg[3 * e] = jg0;
@@ -459,7 +479,7 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
     if (n == 0) continue;
     const int off = sg == 0 ? 0 : nup * nup;
     double* A = sizeof(T) == 8 ? Bd + off : Bd;
-    build_slater<T, GS>(S, pos, sg, A, ao, L.ao_rows);
+    build_slater<T, GS, true>(S, pos, sg, A, ao, L.ao_rows);
     gj_inverse<GS>(A, n, piv, f, flag, la, sgn, P.logpsi != nullptr);
     if constexpr (sizeof(T) != 8) {
       for (int i = t; i < n * n; i += GS) Bt[off + i] = (T)A[i];
@@ -668,13 +688,13 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
           disp_nuc<T>(S, pe, I, sd);
           const T sx = sd[0], sy = sd[1], sz = sd[2];
           const T rr = dsqrt<T>(sx * sx + sy * sy + sz * sz), ri = T(1) / rr;
-          const T Z = (T)S.Z[I];
+          const T Z = nuc_Z<T>(S, I);
           const T sv[3] = {sx, sy, sz};
           const T nn[3] = {sx * ri, sy * ri, sz * ri};
           const T ven = -Z * ri * ri * ri;
           for (int d = 0; d < 3; ++d) frc[3 * K + 3 * I + d] += ven * sv[d];
           if (S.J1) {
-            const Rad3<T> c = pade<T>(-Z, (T)S.ben, rr);
+            const Rad3<T> c = pade<T>(-Z, jas_b<T>(S), rr);
             const T gsum[3] = {gd[3 * e] + Jg[3 * e], gd[3 * e + 1] + Jg[3 * e + 1], gd[3 * e + 2] + Jg[3 * e + 2]};
             const T dl = c.h3 + T(2) * c.h2 * ri - T(2) * c.h1 * ri * ri;
             for (int d = 0; d < 3; ++d) {
@@ -872,11 +892,11 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
         disp_nuc<T>(S, pe, I, sv);
         const T r2 = sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2];
         const T r = dsqrt<T>(r2), ri = T(1) / r;
-        const T Z = (T)S.Z[I];
+        const T Z = nuc_Z<T>(S, I);
 #pragma unroll
         for (int k = 0; k < 3; ++k) dr[k] += Z * sv[k] * ri * ri * ri;
         if (S.J1) {
-          const Rad3<T> c = pade<T>(-Z, (T)S.ben, r);
+          const Rad3<T> c = pade<T>(-Z, jas_b<T>(S), r);
           const T nn[3] = {sv[0] * ri, sv[1] * ri, sv[2] * ri};
           const T dl = c.h3 + T(2) * c.h2 * ri - T(2) * c.h1 * ri * ri;
 #pragma unroll

@@ -151,10 +151,7 @@ __device__ __forceinline__ void for_each_group(const DevSys& S, const double p[3
   }
 }
 
-__device__ __forceinline__ void split_ff(double v, float& h, float& l) {
-  h = (float)v;
-  l = (float)(v - (double)h);
-}
+__device__ __forceinline__ void split_ff(double v, float& h, float& l) { split_ff_bits(v, h, l); }
 
 // a r / (1 + F r) at r = |d| for the Metropolis ratio: in mixed mode with the approximate
 // reciprocal square root and division (a few ulp; the ratio feeds an acceptance test only).
@@ -173,9 +170,9 @@ __device__ __forceinline__ T pade_at(T a, T F, const T d[3]) {
 // The two-body term of a pair at r = |d| for the Metropolis ratio, in the system's form.
 template <typename T>
 __device__ __forceinline__ T pair_at(const DevSys& S, bool par, const T d[3]) {
-  if (!S.j2exp) return pade_at<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), d);
+  if (!S.j2exp) return pade_at<T>(jas_a<T>(S, par), jas_F<T>(S, par), d);
   const T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  return expo_value<T>((T)(par ? S.ap : S.aa), (T)(par ? S.Fp : S.Fa), dsqrt<T>(r2));
+  return expo_value<T>(jas_a<T>(S, par), jas_F<T>(S, par), dsqrt<T>(r2));
 }
 
 // A staged coefficient row (16-byte aligned, padded to a multiple of 4 entries) into registers with
@@ -368,7 +365,7 @@ __global__ void __launch_bounds__(256) propose_small(DevSys S, SmallProposeParam
     T dchi = T(0);
     if (S.J1) {
       for (int I = 0; I < S.K; ++I) {
-        const T mz = (T)(-__ldg(S.Z + I)), b = (T)S.ben;
+        const T mz = -nuc_Z<T>(S, I), b = jas_b<T>(S);
         T d1[3], d0[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -842,7 +839,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
         dist_inv<T>(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r, ri);
         if (S.J2) {
           const bool par = (j < nup) == (e < nup);
-          const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+          const T a = jas_a<T>(S, par), F = jas_F<T>(S, par);
           T h, h1, h2, reg;
           if (!S.j2exp) {
             const T q = fast_rcp<T>(T(1) + F * r), q2 = q * q;
@@ -876,9 +873,9 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
         }
         T r, ri;
         dist_inv<T>(d[0] * d[0] + d[1] * d[1] + d[2] * d[2], r, ri);
-        const T Z = to_T<T>(__ldg(S.Z + I));
+        const T Z = nuc_Z<T>(S, I);
         if (S.J1) {
-          const T b = (T)S.ben, q = fast_rcp<T>(T(1) + b * r), q2 = q * q;
+          const T b = jas_b<T>(S), q = fast_rcp<T>(T(1) + b * r), q2 = q * q;
           const T gr = -Z * q2 * ri;  // chi'/r
 #pragma unroll
           for (int k = 0; k < 3; ++k) jg[k] += gr * d[k];
@@ -1208,13 +1205,13 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
         }
         T r, ri;
         dist_inv<T>(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2], r, ri);
-        const T Z = to_T<T>(__ldg(S.Z + I));
+        const T Z = nuc_Z<T>(S, I);
         const T nn[3] = {sd[0] * ri, sd[1] * ri, sd[2] * ri};
         const T ven = -Z * ri * ri * ri;
 #pragma unroll
         for (int k = 0; k < 3; ++k) c6[3 + k] = ven * sd[k];
         if (S.J1) {
-          const Rad3<T> c = pade_fast<T>(-Z, (T)S.ben, r);
+          const Rad3<T> c = pade_fast<T>(-Z, jas_b<T>(S), r);
           const T gs[3] = {gd[0] + jg[0], gd[1] + jg[1], gd[2] + jg[2]};
           const T dl = c.h3 + T(2) * c.h2 * ri - T(2) * c.h1 * ri * ri;
 #pragma unroll

@@ -776,6 +776,8 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   size_t off = 0;
   auto slot = [&](size_t bytes) { size_t at = off; off = (off + bytes + 255) & ~size_t(255); return at; };
   const size_t oGrp = slot(sizeof(int4) * groups.size());
+  std::vector<float> Zf(s->Z.begin(), s->Z.end());
+  const size_t oZf = slot(4 * Zf.size());
   const size_t oR = slot(8 * s->R.size()), oZ = slot(8 * s->Z.size()), oSh = slot(sizeof(int4) * shells.size()),
                oA = slot(8 * alpha.size()), oC = slot(8 * coef.size()), oAf = slot(4 * alpha.size()),
                oCf = slot(4 * coef.size()), oAoc = slot(4 * (size_t)M), oC0 = slot(8 * s->C[0].size()),
@@ -810,6 +812,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   ce = ce ? ce : up(oZ, s->Z.data(), 8 * s->Z.size());
   ce = ce ? ce : up(oSh, shells.data(), sizeof(int4) * shells.size());
   ce = ce ? ce : up(oGrp, groups.data(), sizeof(int4) * groups.size());
+  ce = ce ? ce : up(oZf, Zf.data(), 4 * Zf.size());
   ce = ce ? ce : up(oA, alpha.data(), 8 * alpha.size());
   ce = ce ? ce : up(oC, coef.data(), 8 * coef.size());
   ce = ce ? ce : up(oAf, alpha_f.data(), 4 * alpha_f.size());
@@ -882,6 +885,8 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   D.CfT[0] = reinterpret_cast<const float*>(b + oCfT0);
   D.CfT[1] = reinterpret_cast<const float*>(b + oCfT1);
   D.Fa = jas->F_anti; D.Fp = jas->F_par; D.aa = jas->a_anti; D.ap = jas->a_par; D.ben = jas->b_en;
+  D.Fa_f = (float)D.Fa; D.Fp_f = (float)D.Fp; D.aa_f = (float)D.aa; D.ap_f = (float)D.ap; D.ben_f = (float)D.ben;
+  D.Zf = reinterpret_cast<const float*>(b + oZf);
   D.J1 = jas->enable_J1 ? 1 : 0;
   D.J2 = jas->enable_J2 ? 1 : 0;
   D.swct = s->swct ? 1 : 0;

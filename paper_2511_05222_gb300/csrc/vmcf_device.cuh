@@ -35,6 +35,8 @@ struct DevSys {
   const double* CT[2];   // [n_s][M], the same coefficients transposed
   const float* CfT[2];
   double Fa, Fp, aa, ap, ben;
+  float Fa_f, Fp_f, aa_f, ap_f, ben_f;  // the same in float (mixed mode reads these: no conversion per use)
+  const float* Zf;                     // [K] nuclear charges in float
   int J1, J2;
   int swct;              // accumulate the space-warp force sums
   int j2exp;             // two-body form: 0 Pade, 1 exponential
@@ -62,6 +64,25 @@ template <> __device__ __forceinline__ const float* coefC<float>(const DevSys& S
 template <typename T> __device__ __forceinline__ const T* coefCT(const DevSys& S, int s);
 template <> __device__ __forceinline__ const double* coefCT<double>(const DevSys& S, int s) { return S.CT[s]; }
 template <> __device__ __forceinline__ const float* coefCT<float>(const DevSys& S, int s) { return S.CfT[s]; }
+
+// Jastrow parameters and nuclear charges in the working precision, read from the copy of that type:
+// a conversion from double would take the FP64 pipe (a whole warp instruction) at every use.
+template <typename T> __device__ __forceinline__ T jas_a(const DevSys& S, bool par) {
+  if constexpr (sizeof(T) == 8) return par ? S.ap : S.aa;
+  else return par ? S.ap_f : S.aa_f;
+}
+template <typename T> __device__ __forceinline__ T jas_F(const DevSys& S, bool par) {
+  if constexpr (sizeof(T) == 8) return par ? S.Fp : S.Fa;
+  else return par ? S.Fp_f : S.Fa_f;
+}
+template <typename T> __device__ __forceinline__ T jas_b(const DevSys& S) {
+  if constexpr (sizeof(T) == 8) return S.ben;
+  else return S.ben_f;
+}
+template <typename T> __device__ __forceinline__ T nuc_Z(const DevSys& S, int I) {
+  if constexpr (sizeof(T) == 8) return __ldg(S.Z + I);
+  else return __ldg(S.Zf + I);
+}
 
 template <typename T> __device__ __forceinline__ T dexp(T x);
 template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
@@ -221,6 +242,14 @@ __device__ __forceinline__ float d2f_rn(double x) {
   return __uint_as_float(e < 897u ? sgn : (e > 1150u ? big : nrm));
 }
 
+// v as a float-float pair (h + l, h the rounded float, l the rounded remainder) with one FP64
+// instruction (the exact subtraction) instead of three; coordinates below the normal float range
+// become zero.
+__device__ __forceinline__ void split_ff_bits(double v, float& h, float& l) {
+  h = d2f_rn(v);
+  l = d2f_rn(v - f2d_bits(h));
+}
+
 // A double operand in the working precision: itself in FP64 mode, rounded to float with integer
 // instructions in mixed mode (no FP64 conversion instruction).
 template <typename T>
@@ -333,8 +362,7 @@ __device__ __forceinline__ EPos make_epos(const double* r) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     p.d[c] = r[c];
-    p.h[c] = (float)r[c];
-    p.l[c] = (float)(r[c] - (double)p.h[c]);
+    split_ff_bits(r[c], p.h[c], p.l[c]);
   }
   return p;
 }
@@ -550,17 +578,17 @@ __device__ __forceinline__ T expo_value(T a, T F, T r) {
 // The two-body term of a pair of electrons with parallel (par) or antiparallel spins.
 template <typename T>
 __device__ __forceinline__ Rad3<T> pair_rad(const DevSys& S, bool par, T r) {
-  const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+  const T a = jas_a<T>(S, par), F = jas_F<T>(S, par);
   return S.j2exp ? expo<T>(a, F, r) : pade<T>(a, F, r);
 }
 template <typename T>
 __device__ __forceinline__ Rad3<T> pair_rad_fast(const DevSys& S, bool par, T r) {
-  const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+  const T a = jas_a<T>(S, par), F = jas_F<T>(S, par);
   return S.j2exp ? expo<T>(a, F, r) : pade_fast<T>(a, F, r);
 }
 template <typename T>
 __device__ __forceinline__ T pair_value(const DevSys& S, bool par, T r) {
-  const T a = (T)(par ? S.ap : S.aa), F = (T)(par ? S.Fp : S.Fa);
+  const T a = jas_a<T>(S, par), F = jas_F<T>(S, par);
   return S.j2exp ? expo_value<T>(a, F, r) : pade_value<T>(a, F, r);
 }
 
@@ -679,6 +707,63 @@ __device__ __forceinline__ void orbital_rows(const T* rows, const T* C, int M, i
   }
 }
 
+// The same rows of a float contraction with compensated accumulation, for the Slater matrix of a
+// measurement in mixed mode: each product's rounding error (from an FMA) and each addition's (a
+// two-sum) are carried in a second float and the result is assembled in double. Plain float
+// accumulation over a few hundred AOs, with the cancellation between terms of both signs, leaves
+// errors several times the rounding of the inputs, and the inverse of an ill-conditioned Slater
+// matrix amplifies them by its condition number.
+template <int R>
+__device__ __forceinline__ void orbital_rows_comp(const float* rows, const float* C, int M, int n, int col, int row0,
+                                                  int ng, int nrows, double* out, int out_stride) {
+  float v[R], cmp[R];
+  const float* a[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    v[r] = 0.f;
+    cmp[r] = 0.f;
+    const int row = row0 + r * ng;
+    a[r] = rows + (row < nrows ? row : nrows - 1) * M;
+  }
+  for (int mu = 0; mu < M; ++mu) {
+    const float c = __ldg(C + mu * n + col);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float x = a[r][mu], p = x * c, pe = fmaf(x, c, -p);
+      float sv, se;
+      two_sum(v[r], p, sv, se);
+      v[r] = sv;
+      cmp[r] += se + pe;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int row = row0 + r * ng;
+    if (row < nrows) out[row * out_stride + col] = f2d_bits(v[r]) + f2d_bits(cmp[r]);
+  }
+}
+
+template <int GS>
+__device__ __forceinline__ void orbital_block_comp(const float* rows, int nrows, const float* C, int M, int n,
+                                                   double* out, int out_stride) {
+  const int t = threadIdx.x % GS;
+  const bool wide = GS >= n;
+  const int ng = wide ? GS / n : 1;
+  const int col0 = wide ? t % n : t, rg = wide ? t / n : 0, dcol = wide ? n : GS;
+  for (int col = col0; col < n && rg < ng && rg < nrows; col += dcol) {
+    switch ((nrows - rg + ng - 1) / ng) {  // rows of this thread
+      case 1: orbital_rows_comp<1>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 2: orbital_rows_comp<2>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 3: orbital_rows_comp<3>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 4: orbital_rows_comp<4>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 5: orbital_rows_comp<5>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 6: orbital_rows_comp<6>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      case 7: orbital_rows_comp<7>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+      default: orbital_rows_comp<8>(rows, C, M, n, col, rg, ng, nrows, out, out_stride); break;
+    }
+  }
+}
+
 // All columns of nrows (<= 8 ng) rows of AO values times C^s (n columns), over the group:
 // with GS >= n thread t owns column t % n and rows t / n + k ng (ng = GS / n); with GS < n it
 // owns columns t, t + GS, ... and every row.
@@ -707,7 +792,8 @@ __device__ __forceinline__ void orbital_block(const T* rows, int nrows, const T*
 // A^s_{el, i} = phi_i(r_e) = sum_mu psi_mu(r_e) C^s_{mu i} (Eq. restricted-C), computed
 // in T and stored in double for the inversion. aobuf: T[chunk * M] scratch; chunk electrons
 // at a time: their AO values over (electron, shell) pairs, then their rows of A.
-template <typename T, int GS>
+// COMP: in mixed mode, accumulate the contraction with compensation (orbital_rows_comp).
+template <typename T, int GS, bool COMP = false>
 __device__ void build_slater(const DevSys& S, const double* pos, int sg, double* A, T* aobuf, int chunk) {
   const int t = threadIdx.x % GS;
   const int n = sg == 0 ? S.nup : S.ndn, e0 = sg == 0 ? 0 : S.nup, M = S.M, ns = S.nshell;
@@ -721,7 +807,8 @@ __device__ void build_slater(const DevSys& S, const double* pos, int sg, double*
       shell_point<T, 0, true>(S, make_epos(pos + 3 * (e0 + c0 + r)), sh, aobuf + r * M, 0);
     }
     gsync<GS>();
-    orbital_block<T, GS>(aobuf, nc, C, M, n, A + c0 * n, n);
+    if constexpr (COMP && sizeof(T) == 4) orbital_block_comp<GS>(aobuf, nc, C, M, n, A + c0 * n, n);
+    else orbital_block<T, GS>(aobuf, nc, C, M, n, A + c0 * n, n);
     gsync<GS>();
   }
 }
