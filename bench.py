@@ -14,7 +14,8 @@ The headline steps are timed without per-kernel instrumentation; the kernel spli
 roofline of the dominant kernel come from a second timed region of the same length with an
 event pair around every kernel. The default line also carries a "c9o4h8" block: the
 94-electron workload (C9O4H8, 222 AOs, 65536 walkers per GPU) measured the same way, mixed and
-FP64 (--no-large skips it).
+FP64, and a "ragged64" block: the ragged batch of 64 geometries (10-94 electrons, 148608 walkers)
+sampled together, one captured graph per sweep (--no-large skips both).
 
 --impl reference times the CPU oracle (the plain FP64 C++ reference implementation) on
 the host cores, on a bounded sample of the same workload.
@@ -207,15 +208,17 @@ def shard_geometries(plan, ws):
     return [sorted(o) for o in own]
 
 
-def run_ragged(args, wl):
+def run_ragged(args, wl, embedded=False):
     """One step = one measured sweep of every geometry of the ragged batch, as one replay of
-    the batch's captured graph (persistent kernels, autotuned launch shapes)."""
+    the batch's captured graph (persistent kernels, autotuned launch shapes). embedded: called
+    from the default measurement (process group and device already set up); the line is
+    returned instead of printed."""
     import torch
     from paper_2511_05222_gb300 import systems as S
     from paper_2511_05222_gb300 import vmcf, workmodel
 
     rank, ws, local = dist_env()
-    if ws > 1:
+    if ws > 1 and not embedded:
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -285,6 +288,8 @@ def run_ragged(args, wl):
                          if ws == 1 else None, "peak_source": "measured in this run by vmcf_probe_pipes"},
             "gpu_launches": args.steps * (info["launches"] + 1), "clocks": clk.summary(),
             "acceptance": acc_n / max(1, acc_d)}
+    if embedded:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -497,6 +502,14 @@ def main():
         blk = workload_line(S.make_system(big["cfg"]), big["walkers"], 5, 3, 0 if args.no_fp64 else 2, seed=rank)
         blk["workload"] = big["name"]
         line["c9o4h8"] = blk
+
+    # ---- the ragged batch (64 geometries of 10-94 electrons, one captured graph per sweep), beside the headline
+    if args.workload == "c2oh6" and not args.no_large and not args.jastrow_basis and not args.walkers:
+        rg = run_ragged(argparse.Namespace(steps=3, warmup=1, equil=args.equil), WORKLOADS["ragged64"], embedded=True)
+        line["ragged64"] = {k: rg[k] for k in ("value", "ms_per_step", "steps", "warmup", "roofline", "gpu_launches",
+                                               "clocks", "acceptance")}
+        line["ragged64"]["workload"] = rg["config"]["workload"]
+        line["ragged64"]["walkers_total"] = rg["config"]["walkers_total"]
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     if not args.no_cpu and ws == 1:
