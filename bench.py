@@ -52,22 +52,70 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    """SM clocks and throttle reasons sampled in the background during a timed region: through the
+    driver's NVML library every 10 ms (read-only queries), else nvidia-smi every 200 ms."""
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # nvmlClocksEventReason bits (nvml.h): SwPowerCap, HwSlowdown, SwThermalSlowdown, HwThermalSlowdown
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, period_s: float = 0.01):
         self.index = index
+        self.period = period_s
         self.lines: list[str] = []
+        self.samples: list[tuple[float, float, int]] = []
         self.proc = None
+        self.th = None
+        self.stop_ev = threading.Event()
+        self.source = None
+
+    def _nvml(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        bus = None
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.index)
+            bus = "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        except Exception:
+            bus = None
+        if bus is None or lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), ctypes.byref(h)) != 0:
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+                return None
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, reasons
+
+    def _poll(self, lib, h, reasons):
+        import ctypes
+        cur, mx, r = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop_ev.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(cur)) == 0 and      # NVML_CLOCK_SM
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    reasons(h, ctypes.byref(r)) == 0):
+                self.samples.append((float(cur.value), float(mx.value), int(r.value)))
+            self.stop_ev.wait(self.period)
 
     def __enter__(self):
+        try:
+            nv = self._nvml()
+        except (OSError, AttributeError):
+            nv = None
+        if nv is not None:
+            self.source = "nvml, every %g ms" % (self.period * 1e3)
+            self.th = threading.Thread(target=self._poll, args=nv, daemon=True)
+            self.th.start()
+            return self
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            self.source = "nvidia-smi, every 200 ms"
         except OSError:
             self.proc = None
         return self
@@ -77,15 +125,22 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *a):
+        self.stop_ev.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        elif self.th is not None:
+            self.th.join(timeout=5)
 
     def summary(self):
         sm, mx, reasons = [], [], set()
+        for c, m, r in self.samples:
+            sm.append(c)
+            mx.append(m)
+            reasons.update(n for n, b in self.BITS.items() if r & b)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -102,7 +157,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": self.source}
 
 
 def oracle_steps(sysx, walkers: int, budget_s: float, max_s: float, key=(5222, 1)):
@@ -228,7 +283,7 @@ def run_ragged(args, wl, embedded=False):
     plan = S.ragged_batch_plan(64)
     mine = shard_geometries(plan, ws)[rank]
     geos = S.make_ragged_batch(64, only=set(mine))
-    systems = [vmcf.System(sx, vmcf.MIXED, force_group=True) for sx, _ in geos]
+    systems = [vmcf.System(sx, vmcf.MIXED) for sx, _ in geos]  # small geometries on the small-system kernels
     walkers = [vmcf.Walkers(systems[i], S.initial_walkers(sx, W, seed=g), key=(5222, 3000 + g), nblocks=64,
                             stream=stream) for i, ((sx, W), g) in enumerate(zip(geos, mine))]
     batch = vmcf.Batch(systems, walkers, stream=stream)

@@ -347,7 +347,11 @@ int vmcf_set_tuning(vmcf_system_t sys, const char* key, int value);
  * sampled together: each VMC sweep of the whole batch is one replay of a captured CUDA graph
  * with two phases, the Metropolis sweep of every walker and (when measuring) the evaluation
  * of every walker (E_L, forces, O, walker sums). Each phase is one persistent kernel per
- * launch shape, run side by side; a one-thread-block kernel then advances the chain clocks.
+ * launch shape, run side by side; geometries that fit the small-system kernels (at most 32
+ * electrons and 16 orbitals per spin, created without VMCF_FORCE_GROUP_PATH) run in branches of
+ * their own beside them (proposals, runs of moves with the re-inversions, the evaluation), their
+ * launches reading the sweep's schedule from the geometry's chain clock on the device; a
+ * one-thread-block kernel then advances the chain clocks.
  * Walker groups in the persistent kernels pull work items (one geometry, one range of its
  * walkers) from a device queue, longest first, so that small and large geometries share the
  * SMs. The method per walker is exactly that of vmcf_sample (App. A, the MCMC sampling and
@@ -357,11 +361,9 @@ int vmcf_set_tuning(vmcf_system_t sys, const char* key, int value);
  * geometries) at once.
  *
  * vmcf_batch_create: systems[g], walkers[g] for g < G: each walker set belongs to its system;
- *   every system has the same precision and runs on the walker-group kernels (systems that
- *   qualify for the small-system kernels must be created with VMCF_FORCE_GROUP_PATH), else
- *   VMCF_ENOTSUP. The batch keeps the handles (the caller keeps ownership and must keep them
- *   alive until vmcf_batch_destroy) and allocates its own device tables. Geometries are put in
- *   buckets by (ceil(Ne / 16), ceil(M / 64)); every bucket starts, per phase, with the default
+ *   every system has the same precision (else VMCF_EINVAL). The batch keeps the handles (the caller keeps ownership and must keep them
+ *   alive until vmcf_batch_destroy) and allocates its own device tables. Geometries on the
+ *   walker-group kernels are put in buckets by (ceil(Ne / 16), ceil(M / 64)); every bucket starts, per phase, with the default
  *   launch shape (32 threads per walker while n_up, n_dn <= 24, with as many walker groups per
  *   CTA, up to 4, as fit shared memory; else 128 threads per walker for the sweep and 256 for
  *   the evaluation). Synchronises `stream`.
@@ -373,7 +375,8 @@ int vmcf_set_tuning(vmcf_system_t sys, const char* key, int value);
  *   rebuild the inverses and discard their sums: call it during equilibration. Synchronises
  *   `stream`.
  * vmcf_batch_set_shape: force the launch shape of `phase` (0 sweep, 1 evaluation) for the
- *   bucket that holds geometry g; VMCF_EINVAL if unsupported or too large for shared memory.
+ *   bucket that holds geometry g; VMCF_EINVAL if unsupported, too large for shared memory, or g
+ *   runs on the small-system kernels.
  * vmcf_batch_sample: n_sweeps sweeps of every geometry, as vmcf_sample on each walker set
  *   (same arguments and meaning; measure != 0 adds each sweep's evaluation to each walker
  *   set's sums, read with vmcf_reduce_estimators / vmcf_block_sums on that walker set).
@@ -381,7 +384,11 @@ int vmcf_set_tuning(vmcf_system_t sys, const char* key, int value);
  *   calls replay it. Asynchronous on `stream`.
  * vmcf_batch_info: number of buckets and of persistent kernels per measured sweep; for
  *   geometry g (if 0 <= g < G) its bucket and shapes[4] = {sweep GS, sweep groups per CTA,
- *   evaluation GS, evaluation groups per CTA}; any output may be NULL. */
+ *   evaluation GS, evaluation groups per CTA}; a geometry on the small-system kernels has bucket
+ *   -1 and shapes {lanes per walker of its moves, 0, 32 (one warp per walker), walkers per
+ *   evaluation CTA}; any output may be NULL.
+ * A small-system geometry's launches are captured with its walker set's E_ref and guiding
+ * threshold; vmcf_batch_sample captures the graph again when either has changed. */
 typedef struct vmcf_batch_s* vmcf_batch_t; /* opaque, library-owned */
 int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walkers, int G, void* stream,
                       vmcf_batch_t* out);

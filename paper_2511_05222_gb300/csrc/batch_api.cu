@@ -75,6 +75,12 @@ struct vmcf_batch_s {
   std::vector<cudaStream_t> forks;
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork_ev = nullptr;
+  // geometries on the small-system kernels: their own branch of the graph each, with the E_ref and
+  // guiding threshold their launches were captured with
+  std::vector<int> small_g;
+  std::vector<cudaStream_t> sforks;
+  std::vector<cudaEvent_t> sjoins;
+  std::vector<double> s_eref, s_eps;
 };
 
 namespace {
@@ -155,8 +161,9 @@ void fill_geo(vmcf_batch_s& b, int g) {
   const vmcf_walkers_s& w = *b.wk[g];
   BatchGeom G{};
   G.S = s.dev;
-  G.Lrm = group_layout_rm(s, b.bucket_shape[0][b.bucket[g]].GS);
-  G.Lmeas = meas_layout(b, g, b.bucket_shape[1][b.bucket[g]].GS);
+  // (a geometry on the small-system kernels keeps a table the persistent kernels never read)
+  G.Lrm = group_layout_rm(s, b.bucket[g] >= 0 ? b.bucket_shape[0][b.bucket[g]].GS : 32);
+  G.Lmeas = meas_layout(b, g, b.bucket[g] >= 0 ? b.bucket_shape[1][b.bucket[g]].GS : 32);
   G.P.pos = w.pos;
   G.P.B = w.B;
   G.P.nacc = w.nacc;
@@ -208,7 +215,7 @@ int build_plan(vmcf_batch_s& b, const std::vector<char>& take, int phases, cudaS
     if (!(phases & (1 << phase))) continue;
     std::map<Shape, std::vector<int>> by_shape;
     for (int g = 0; g < b.G; ++g)
-      if (take.empty() || take[g]) by_shape[b.bucket_shape[phase][b.bucket[g]]].push_back(g);
+      if (b.bucket[g] >= 0 && (take.empty() || take[g])) by_shape[b.bucket_shape[phase][b.bucket[g]]].push_back(g);
     for (auto& kv : by_shape) {
       LaunchPlan lp;
       lp.phase = phase;
@@ -311,6 +318,17 @@ int capture(vmcf_batch_s& b, int mode, int kref, double sigma) {
   invalidate_graph(b);
   BATCH_CUDA(cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
+  // small-system geometries: each a branch of its own for the whole sweep (proposals, runs of moves and
+  // re-inversions, the measurement), beside the persistent kernels of both phases
+  if (!b.small_g.empty()) e = cudaEventRecord(b.fork_ev, b.cap);
+  for (size_t i = 0; e == cudaSuccess && i < b.small_g.size(); ++i) {
+    const int g = b.small_g[i];
+    e = cudaStreamWaitEvent(b.sforks[i], b.fork_ev, 0);
+    if (e == cudaSuccess) e = small_sweep_launches(b.sys[g], b.wk[g], b.d_clk + g, mode, kref, sigma, b.sforks[i]);
+    if (e == cudaSuccess) e = cudaEventRecord(b.sjoins[i], b.sforks[i]);
+    b.s_eref[i] = b.wk[g]->e_ref;
+    b.s_eps[i] = b.wk[g]->eps;
+  }
   for (int phase = 0; phase < 2 && e == cudaSuccess; ++phase) {
     if (phase == 1 && mode == 0) break;
     e = cudaEventRecord(b.fork_ev, b.cap);
@@ -323,6 +341,7 @@ int capture(vmcf_batch_s& b, int mode, int kref, double sigma) {
       if (e == cudaSuccess) e = cudaStreamWaitEvent(b.cap, b.joins[k], 0);
     }
   }
+  for (size_t i = 0; e == cudaSuccess && i < b.small_g.size(); ++i) e = cudaStreamWaitEvent(b.cap, b.sjoins[i], 0);
   // measured sweeps: the tensor-core GEMM of each geometry's O sums over the tiles just written
   for (int g = 0; e == cudaSuccess && mode == 1 && g < b.G; ++g) {
     if (!uses_tc(b, g)) continue;
@@ -370,6 +389,8 @@ int vmcf_batch_destroy(vmcf_batch_t b) {
   invalidate_graph(*b);
   for (auto s : b->forks) cudaStreamDestroy(s);
   for (auto e : b->joins) cudaEventDestroy(e);
+  for (auto s : b->sforks) cudaStreamDestroy(s);
+  for (auto e : b->sjoins) cudaEventDestroy(e);
   if (b->fork_ev) cudaEventDestroy(b->fork_ev);
   if (b->cap) cudaStreamDestroy(b->cap);
   cudaFree(b->d_geo);
@@ -390,10 +411,6 @@ int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walker
       return fail(VMCF_EINVAL, "geometry " + std::to_string(g) + ": walker set does not belong to its system");
     if (systems[g]->precision != systems[0]->precision)
       return fail(VMCF_EINVAL, "all systems of a batch must have the same precision");
-    if (systems[g]->small)
-      return fail(VMCF_ENOTSUP, "geometry " + std::to_string(g) +
-                                    ": batches run on the walker-group kernels; create the system with "
-                                    "VMCF_FORCE_GROUP_PATH");
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   auto* b = new vmcf_batch_s();
@@ -415,16 +432,36 @@ int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walker
     vmcf_batch_destroy(b);
     return cuda_fail(e, "batch set-up");
   }
-  // buckets by (ceil(Ne / 16), ceil(M / 64))
+  // buckets by (ceil(Ne / 16), ceil(M / 64)) for the walker-group kernels; geometries on the
+  // small-system kernels get a graph branch each instead (bucket -1)
   std::map<std::pair<int, int>, int> keys;
   b->bucket.resize(G);
   for (int g = 0; g < G; ++g) {
+    b->cost[0].push_back(0.0);
+    b->cost[1].push_back(0.0);
+    if (systems[g]->small) {
+      b->bucket[g] = -1;
+      b->small_g.push_back(g);
+      cudaStream_t s2 = nullptr;
+      cudaEvent_t ev = nullptr;
+      cudaError_t e2 = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+      if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (s2) b->sforks.push_back(s2);
+      if (ev) b->sjoins.push_back(ev);
+      if (e2 != cudaSuccess) {
+        vmcf_batch_destroy(b);
+        return cuda_fail(e2, "batch set-up");
+      }
+      continue;
+    }
     const std::pair<int, int> k{(systems[g]->Ne + 15) / 16, (systems[g]->M + 63) / 64};
     auto it = keys.find(k);
     if (it == keys.end()) it = keys.emplace(k, (int)keys.size()).first;
     b->bucket[g] = it->second;
-    for (int ph = 0; ph < 2; ++ph) b->cost[ph].push_back(heuristic_cost(*systems[g], ph));
+    for (int ph = 0; ph < 2; ++ph) b->cost[ph][g] = heuristic_cost(*systems[g], ph);
   }
+  b->s_eref.assign(b->small_g.size(), 0.0);
+  b->s_eps.assign(b->small_g.size(), 0.0);
   for (int ph = 0; ph < 2; ++ph) {
     b->bucket_shape[ph].resize(keys.size());
     for (int bk = 0; bk < (int)keys.size(); ++bk) b->bucket_shape[ph][bk] = default_shape(*b, ph, bk);
@@ -441,6 +478,7 @@ int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walker
 int vmcf_batch_set_shape(vmcf_batch_t b, int g, int phase, int GS, int groups) {
   if (!b || g < 0 || g >= b->G || phase < 0 || phase > 1) return fail(VMCF_EINVAL, "bad batch, geometry or phase");
   const int bk = b->bucket[g];
+  if (bk < 0) return fail(VMCF_EINVAL, "geometry runs on the small-system kernels (no launch shape to set)");
   const Shape sh{GS, groups};
   if (!shape_fits(*b, phase, bk, sh))
     return fail(VMCF_EINVAL, "launch shape not supported or does not fit shared memory");
@@ -454,11 +492,20 @@ int vmcf_batch_info(vmcf_batch_t b, int* n_buckets, int* n_launches, int g, int*
   if (n_launches) *n_launches = (int)b->launches.size();
   if (g >= 0 && g < b->G) {
     if (bucket) *bucket = b->bucket[g];
-    if (shapes)
-      for (int ph = 0; ph < 2; ++ph) {
-        shapes[2 * ph] = b->bucket_shape[ph][b->bucket[g]].GS;
-        shapes[2 * ph + 1] = b->bucket_shape[ph][b->bucket[g]].groups;
+    if (shapes) {
+      if (b->bucket[g] < 0) {  // small-system kernels: lanes per walker of the moves, warps per evaluation CTA
+        const vmcf_system_s& s = *b->sys[g];
+        shapes[0] = s.move_lpw;
+        shapes[1] = 0;
+        shapes[2] = 32;
+        shapes[3] = s.small_warps;
+      } else {
+        for (int ph = 0; ph < 2; ++ph) {
+          shapes[2 * ph] = b->bucket_shape[ph][b->bucket[g]].GS;
+          shapes[2 * ph + 1] = b->bucket_shape[ph][b->bucket[g]].groups;
+        }
       }
+    }
   }
   return VMCF_OK;
 }
@@ -475,7 +522,10 @@ int vmcf_batch_sample(vmcf_batch_t b, int n_sweeps, double step_sigma, int refre
       if (rc != VMCF_OK) return rc;
     }
   const int mode = measure ? 1 : 0;
-  if (!b->exec || b->g_mode != mode || b->g_kref != refresh_k || b->g_sigma != step_sigma) {
+  bool stale = false;  // a small-system geometry's launches were captured with another E_ref or threshold
+  for (size_t i = 0; i < b->small_g.size(); ++i)
+    stale = stale || b->s_eref[i] != b->wk[b->small_g[i]]->e_ref || b->s_eps[i] != b->wk[b->small_g[i]]->eps;
+  if (!b->exec || stale || b->g_mode != mode || b->g_kref != refresh_k || b->g_sigma != step_sigma) {
     int rc = capture(*b, mode, refresh_k, step_sigma);
     if (rc != VMCF_OK) return rc;
   }

@@ -291,6 +291,35 @@ __device__ __forceinline__ void stage_C(const DevSys& S, T* Cs) {
 }
 
 
+// ---------------------------------------------------------------- sweep schedule in a batch graph
+// The moves of one sweep, in the order vmcf_sample issues them: runs of at most k moves separated by
+// the FP64 re-inversion every k attempted moves (none after the sweep's last move when the sweep is
+// measured, because the measurement re-inverts). c0 = moves since the last re-inversion at the start
+// of the sweep (< k). Segment s: its first move (start) and count (0 if the sweep has fewer segments),
+// and whether a re-inversion follows it.
+__device__ __forceinline__ void sweep_segment(int c0, int Ne, int kref, int measure, int s, int& start, int& count,
+                                              bool& refresh_after) {
+  int done = 0, c = c0;
+  start = 0;
+  count = 0;
+  refresh_after = false;
+  for (int k = 0; k <= s && done < Ne; ++k) {
+    const int chunk = min(Ne - done, kref - c);
+    done += chunk;
+    c += chunk;
+    bool ref = false;
+    if (c >= kref) {
+      ref = !(measure && done == Ne);
+      c = 0;
+    }
+    if (k == s) {
+      start = done - chunk;
+      count = chunk;
+      refresh_after = ref;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- proposals of one sweep
 // In sweep s electron e of walker w is proposed r'_e = r_e + sigma xi, xi from the Philox counter
 // (wid, s, e, 0), and accepted against the uniform of counter (wid, s, e, 1) (App. A, MCMC). Every
@@ -313,10 +342,10 @@ __global__ void __launch_bounds__(256) propose_small(DevSys S, SmallProposeParam
   const int sg = e < S.nup ? 0 : 1;
   const T* Csg = Cs + sg * S.M * NMS;
   for (long long w = (long long)blockIdx.x * nwarps + warp; w < W; w += (long long)gridDim.x * nwarps) {
-    const uint64_t wid = P.wid0 + (uint64_t)w;
-    uint64_t r[4] = {wid, P.sweep, (uint64_t)e, 0};
+    const uint64_t wid = P.wid0 + (uint64_t)w, sweep = P.clk ? P.clk->sweep : P.sweep;
+    uint64_t r[4] = {wid, sweep, (uint64_t)e, 0};
     philox4x64_10(r, P.k0, P.k1);
-    uint64_t r2[4] = {wid, P.sweep, (uint64_t)e, 1};
+    uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
     philox4x64_10(r2, P.k0, P.k1);
     // r'_e = r_e + sigma xi: in double in FP64 mode; in mixed mode a float-float sum of the float-float
     // position and a float step, so that no FP64 instruction is needed
@@ -412,6 +441,16 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
   // shared memory: the CTA's inverses walker-interleaved [nB][WPC]; its positions [3 Ne][WPC]
   // (float-float pairs in mixed mode, double in FP64 mode)
   const int WPC = P.wpc;
+  uint64_t move0 = P.move0;
+  int nmoves = P.nmoves;
+  if (P.clk) {  // batch graph: this launch's segment of the sweep (uniform over the grid)
+    int start, count;
+    bool ref;
+    sweep_segment(P.clk->c, S.Ne, P.kref, P.measure, P.seg, start, count, ref);
+    if (count == 0) return;
+    move0 = P.clk->sweep * (uint64_t)S.Ne + (uint64_t)start;
+    nmoves = count;
+  }
   T* Bs = reinterpret_cast<T*>(smem);
   using PosT = typename std::conditional<sizeof(T) == 4, float2, double>::type;
   PosT* Ps = reinterpret_cast<PosT*>(smem + (sizeof(T) * (size_t)S.nB * WPC + 7) / 8 * 8);  // move_small_smem
@@ -447,7 +486,7 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
     Sg = lane_group_sum<LPW>(Sg, mask);
   }
   // a launch never crosses a sweep: its moves are electrons e0, e0 + 1, ... of one sweep
-  const int e0 = (int)(P.move0 % (uint64_t)Ne);
+  const int e0 = (int)(move0 % (uint64_t)Ne);
   // this sweep's proposals, one move ahead: the loads of move mv + 1 are in flight while move mv runs
   T rowc[NM], rown[NM];
   double rnc[3], rnn[3], uc = 0.0, un = 0.0;
@@ -460,8 +499,8 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
     un = __ldg(P.pr.u + pe);
     dcn = __ldg(reinterpret_cast<const T*>(P.pr.dchi) + pe);
   };
-  if (P.nmoves > 0) fetch(0);
-  for (int mv = 0; mv < P.nmoves; ++mv) {
+  if (nmoves > 0) fetch(0);
+  for (int mv = 0; mv < nmoves; ++mv) {
     const int e = e0 + mv;
     const int sg = e < nup ? 0 : 1;
     const int n = sg == 0 ? nup : S.ndn, el = e - (sg == 0 ? 0 : nup);
@@ -472,7 +511,7 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
     for (int k = 0; k < 3; ++k) rnc[k] = rnn[k];
     uc = un;
     dcc = dcn;
-    if (mv + 1 < P.nmoves) fetch(mv + 1);
+    if (mv + 1 < nmoves) fetch(mv + 1);
     const T (&row)[NM] = rowc;
     double po[3] = {0.0, 0.0, 0.0}, rn[3] = {0.0, 0.0, 0.0};
     float nh[3], nl[3], oh[3], ol[3];
@@ -783,6 +822,12 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
   const bool accum = P.mode == 2;
   // mixed-mode walker sums of O through the tensor-core kernel: emit PhiT and YT tiles
   const bool tc = accum && sizeof(T) == 4 && P.phiT[0] != nullptr;
+  if (P.mode == 0 && P.clk) {  // batch graph: re-invert only where the sweep's schedule has a re-inversion
+    int start, count;
+    bool ref;
+    sweep_segment(P.clk->c, S.Ne, P.kref, P.measure, P.seg, start, count, ref);
+    if (!ref) return;  // uniform over the grid
+  }
   stage_C<T, NM>(S, Cs);
   if (accum)
     for (int i = threadIdx.x; i < P.accL; i += blockDim.x) acc_s[i] = T(0);
@@ -958,6 +1003,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       for (int i = lane; i < S.nB; i += 32) Bg[(size_t)i * W + w] = Bf[i];
     }
     if (lane == 0 && *flag) atomicAdd(&P.counters[0], 1ull);
+    if (lane == 0 && P.mode == 0) atomicAdd(&P.counters[1], 1ull);  // a re-inversion between moves
     // reweighting factor |Psi / Psi_G|^2 = 1 / g^2 of a guided chain (g = max(1, eps sqrt(S)), S the
     // sum of the squared entries of the fresh inverses); every walker sum below carries it
     double wt = 1.0;

@@ -586,6 +586,92 @@ int measure_state_group(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
 // Re-inversion of a walker set from its positions (chain clock reset), for the batch entry points.
 int vmcf::refresh_walker_set(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) { return do_refresh(s, wk, st); }
 
+cudaError_t vmcf::small_sweep_launches(vmcf_system_s* s, vmcf_walkers_s* wk, const BatchClock* clk, int mode, int kref,
+                                       double sigma, cudaStream_t st) {
+  const bool fp64 = s->precision == VMCF_FP64;
+  SmallProposeParams Q{};
+  Q.pos = wk->pos;
+  Q.posf = wk->posf;
+  Q.pr = wk->pr;
+  Q.W = wk->W;
+  Q.wid0 = wk->wid0;
+  Q.k0 = wk->k0;
+  Q.k1 = wk->k1;
+  Q.sigma = sigma;
+  Q.sigma_f = (float)sigma;
+  Q.clk = clk;
+  const int qgrid = std::max(1, std::min((wk->W + 7) / 8, 8 * s->small_sms));
+  cudaError_t e = fp64 ? launch_propose_small<double>(s->dev, s->small_nm, qgrid, s->small_move_smem, Q, st)
+                       : launch_propose_small<float>(s->dev, s->small_nm, qgrid, s->small_move_smem, Q, st);
+  SmallMoveParams P{};
+  P.pos = wk->pos;
+  P.posf = wk->posf;
+  P.B = wk->B;
+  P.pr = wk->pr;
+  P.nacc = wk->nacc;
+  P.nrej = wk->nrej;
+  P.W = wk->W;
+  P.wid0 = wk->wid0;
+  P.k0 = wk->k0;
+  P.k1 = wk->k1;
+  P.sigma = sigma;
+  P.eps = wk->eps;
+  P.clk = clk;
+  P.kref = kref;
+  P.measure = mode != 0;
+  const int lpw = wk->eps > 0.0 ? 2 : s->move_lpw;
+  P.wpc = move_walkers_per_cta(*s, wk->W, lpw);
+  SmallMeasParams R = small_params(*s, wk->W);
+  R.pos = wk->pos;
+  R.pos_sk = wk->W;
+  R.pos_sw = 1;
+  R.mode = 0;
+  R.Bout = wk->B;
+  R.counters = wk->counters;
+  R.clk = clk;
+  R.kref = kref;
+  R.measure = mode != 0;
+  // at most ceil(Ne / k) + 1 runs of moves per sweep (the first run is shorter when the sweep starts
+  // part-way to a re-inversion); launches past the sweep's schedule do nothing
+  const int nseg = (s->Ne + kref - 1) / kref + 1;
+  for (int seg = 0; seg < nseg && e == cudaSuccess; ++seg) {
+    P.seg = seg;
+    R.seg = seg;
+    e = fp64 ? launch_move_small<double>(s->dev, s->small_nm, lpw, wk->W, 0, P, st)
+             : launch_move_small<float>(s->dev, s->small_nm, lpw, wk->W, 0, P, st);
+    if (e == cudaSuccess)
+      e = fp64 ? launch_measure_small<double>(s->dev, s->small_nm, s->SL, eval_grid(*s, wk->W), s->small_warps, R, st)
+               : launch_measure_small<float>(s->dev, s->small_nm, s->SL, eval_grid(*s, wk->W), s->small_warps, R, st);
+  }
+  if (e != cudaSuccess || mode != 1) return e;
+  SmallMeasParams M = small_params(*s, wk->W);
+  M.pos = wk->pos;
+  M.pos_sk = wk->W;
+  M.pos_sw = 1;
+  M.mode = 2;
+  M.Bout = wk->B;
+  M.acc = wk->acc;
+  M.swct_off = swct_offset(*s);
+  M.eps = wk->eps;
+  M.e_ref = wk->e_ref;
+  M.counters = wk->counters;
+  const bool tc = wk->tc && s->tc_sums;
+  if (tc) {
+    for (int k = 0; k < 2; ++k) {
+      M.phiT[k] = wk->phiT[k];
+      M.yT[k] = wk->yT[k];
+    }
+    M.Mp = s->tc_Mp;
+    M.Np = s->tc_Np;
+  }
+  e = fp64 ? launch_measure_small<double>(s->dev, s->small_nm, s->SL, wk->grid_meas, s->small_warps, M, st)
+           : launch_measure_small<float>(s->dev, s->small_nm, s->SL, wk->grid_meas, s->small_warps, M, st);
+  if (e == cudaSuccess && tc)
+    e = launch_tc_sumprod(wk->phiT[0], wk->phiT[1], wk->yT[0], wk->yT[1], wk->W, 1, s->tc_Mp, s->tc_Np, s->nup, s->ndn,
+                          wk->nblocks * wk->tc_cpb, wk->tc_slots, wk->tc_flag, st);
+  return e;
+}
+
 extern "C" {
 
 const char* vmcf_strerror(int status) {

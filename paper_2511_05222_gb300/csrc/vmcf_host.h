@@ -96,4 +96,9 @@ constexpr int kSmemCapBytes = 227 * 1024;
 int set_last_error(int code, const std::string& msg);
 // Rebuild a walker set's inverses from its positions and reset its re-inversion count (vmcf_api.cu).
 int refresh_walker_set(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st);
+// The launches of one sweep of a small-system walker set (proposals, runs of moves with the
+// re-inversions between them, and for mode 1 the measurement and its tensor-core sums) onto st, with
+// the sweep's schedule read from the geometry's device clock clk, for capture into a batch graph.
+cudaError_t small_sweep_launches(vmcf_system_s* s, vmcf_walkers_s* wk, const BatchClock* clk, int mode, int kref,
+                                 double sigma, cudaStream_t st);
 }  // namespace vmcf

@@ -71,6 +71,8 @@ template <typename T>
 cudaError_t set_smem_limits(int GS);
 
 // ---- small-system path (kernels_small.cuh)
+struct BatchClock;
+
 // The proposals of one sweep for every walker and electron (filled by propose_small before the
 // sweep's moves): electron e of walker w at index w * Ne + e.
 struct SmallProposals {
@@ -90,6 +92,7 @@ struct SmallProposeParams {
   uint64_t wid0, k0, k1, sweep;
   double sigma;
   float sigma_f;
+  const BatchClock* clk;  // in a batch graph: the sweep index comes from the geometry's device clock
 };
 
 struct SmallMoveParams {
@@ -103,6 +106,10 @@ struct SmallMoveParams {
   uint64_t wid0, k0, k1;
   uint64_t move0;  // global index of the first move: sweep = move0 / Ne, electron = move0 % Ne
   int nmoves;
+  // in a batch graph: move0 and nmoves come from segment seg of the sweep's schedule, replayed from
+  // the geometry's device clock with re-inversions every kref moves (measure: the sweep is measured)
+  const BatchClock* clk;
+  int seg, kref, measure;
   int wpc;         // walkers per CTA
   double sigma;
   double eps;      // guiding function max(1, eps sqrt(S)); 0: plain |Psi|^2
@@ -132,6 +139,10 @@ struct SmallMeasParams {
   int W;
   int swct_off;  // offset (> 0) of the space-warp sums in a slot (accumulate mode), 0 if none
   double eps;    // guided chain: weight the sums by |Psi / Psi_G|^2; 0: unweighted
+  // refresh mode in a batch graph: the re-inversion after segment seg of the sweep's schedule (replayed
+  // from the geometry's device clock, as for the moves); the launch does nothing when there is none
+  const BatchClock* clk;
+  int seg, kref, measure;
 };
 
 template <typename T>

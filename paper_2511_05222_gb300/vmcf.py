@@ -373,9 +373,10 @@ def vmcf_probe_pipes(stream=None) -> dict:
 
 
 class Batch:
-    """vmcf_batch_create: a ragged batch of geometries, each a (System, Walkers) pair whose
-    system was created with force_group=True; every sweep of the whole batch is one replay of
-    a captured CUDA graph of persistent kernels. Each Walkers object keeps its own sums."""
+    """vmcf_batch_create: a ragged batch of geometries, each a (System, Walkers) pair; every sweep
+    of the whole batch is one replay of a captured CUDA graph: persistent walker-group kernels for
+    the geometries on that path, a branch of small-system kernels for each geometry that fits them.
+    Each Walkers object keeps its own sums."""
 
     def __init__(self, systems, walkers, stream=None):
         L = lib()

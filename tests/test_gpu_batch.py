@@ -1,5 +1,6 @@
 """Ragged batches of geometries (vmcf_batch_*): every sweep of several molecules of different
-sizes is one replay of a captured graph of persistent kernels. Batching must not change any
+sizes is one replay of a captured graph of persistent kernels (walker-group kernels) and, for the
+geometries that fit them, branches of the small-system kernels. Batching must not change any
 walker's chain or contribution: positions follow the single-geometry path and the oracle's
 Markov chain, and the per-geometry walker sums give the same estimators."""
 import numpy as np
@@ -73,12 +74,14 @@ def test_batch_follows_the_single_geometry_path(ragged, precision):
         assert np.all(np.abs(ea["F"] - eb["F"]) <= 0.01 * eb["F_err"] + 1e-12)
 
 
-def test_batch_estimators_match_the_oracle(ragged):
-    """The water geometry inside a ragged FP64 batch: chain and estimators as the oracle's."""
+@pytest.mark.parametrize("small", [False, True])
+def test_batch_estimators_match_the_oracle(ragged, small):
+    """The water geometry inside a ragged FP64 batch, on the walker-group kernels or (small) on the
+    small-system kernels in a branch of the batch graph: chain and estimators as the oracle's."""
     specs = [(ragged[0][0], 128), (ragged[1][0], 32), (ragged[2][0], 16)]
     sys0 = specs[0][0]
     W, nb, warm, meas, e_ref = 128, 8, 3, 3, -76.0
-    systems = [vmcf.System(sx, vmcf.FP64, force_group=True) for sx, _ in specs]
+    systems = [vmcf.System(sx, vmcf.FP64, force_group=not (small and g == 0)) for g, (sx, _) in enumerate(specs)]
     pos = S.initial_walkers(sys0, W, seed=10)
     wk = [vmcf.Walkers(systems[0], pos, key=(5222, 0), nblocks=nb)]
     wk += [vmcf.Walkers(systems[g], S.initial_walkers(specs[g][0], specs[g][1], seed=g), key=(5222, 9 + g),
@@ -108,6 +111,47 @@ def test_batch_estimators_match_the_oracle(ragged):
     assert rel(got["F"].ravel(), ref["F"]) < 1e-9
     assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
     assert abs(got["E_err"] - ref["E_err"]) < 1e-8 * ref["E_err"]
+    if small:
+        assert batch.info()["geometries"][0]["bucket"] == -1
+
+
+@pytest.mark.parametrize("kref", [26, 7])
+@pytest.mark.parametrize("precision", [vmcf.FP64, vmcf.MIXED])
+def test_small_path_geometries_in_a_batch_follow_the_single_path(ragged, precision, kref):
+    """Water and C2OH6 on the small-system kernels (one graph branch each: proposals, runs of moves
+    with the re-inversions every k moves read from the device chain clock, the measurement) beside
+    two walker-group geometries: every chain bit for bit as vmcf_sample on the walker set alone, the
+    walker sums to rounding. k = 7 puts re-inversions inside sweeps at positions that change from
+    sweep to sweep."""
+    specs = [(ragged[0][0], 64), (S.make_system(1), 48), (ragged[1][0], 40), (ragged[3][0], 24)]
+    systems = [vmcf.System(sx, precision, force_group=g >= 2) for g, (sx, _) in enumerate(specs)]
+    wa = _walkers(systems, specs, 60)
+    wb = _walkers(systems, specs, 60)
+    batch = vmcf.Batch(systems, wa)
+    info = batch.info()
+    assert [geo["bucket"] for geo in info["geometries"]][:2] == [-1, -1]
+    e_ref = [-76.0, -150.0, -150.0, -300.0]
+    batch.sample(3, 0.3, kref, measure=False)
+    for g, w in enumerate(wb):
+        w.sample(3, 0.3, kref, measure=False)
+        w.reset_accumulators(e_ref[g])
+        wa[g].reset_accumulators(e_ref[g])
+    batch.sample(2, 0.3, kref, measure=True)
+    batch.sample(1, 0.3, kref, measure=False)
+    batch.sample(1, 0.3, kref, measure=True)
+    for w in wb:
+        w.sample(2, 0.3, kref, measure=True)
+        w.sample(1, 0.3, kref, measure=False)
+        w.sample(1, 0.3, kref, measure=True)
+    tol = 1e-12 if precision == vmcf.FP64 else 1e-5
+    for g in range(len(specs)):
+        np.testing.assert_array_equal(wa[g].positions(), wb[g].positions())
+        ca, cb = wa[g].counters(), wb[g].counters()
+        assert ca["accepted"] == cb["accepted"] and ca["moves"] == cb["moves"]
+        assert ca["refreshes"] == cb["refreshes"] and ca["sweeps"] == cb["sweeps"]
+        sa, sb = wa[g].block_sums(), wb[g].block_sums()
+        np.testing.assert_array_equal(sa[:, 0], sb[:, 0])
+        assert rel(sa, sb) < tol, (g, rel(sa, sb))
 
 
 def test_launch_shape_and_autotuning_leave_the_chains_unchanged(ragged):
@@ -139,11 +183,7 @@ def test_launch_shape_and_autotuning_leave_the_chains_unchanged(ragged):
         assert rel(wa[g].block_sums(), wb[g].block_sums()) < 1e-11
 
 
-def test_batch_rejects_small_path_systems_and_mixed_precisions(ragged):
-    s_small = vmcf.System(ragged[0][0], vmcf.FP64)  # qualifies for the small-system kernels
-    w_small = vmcf.Walkers(s_small, S.initial_walkers(ragged[0][0], 16, seed=1), nblocks=2)
-    with pytest.raises(vmcf.VmcfError):
-        vmcf.Batch([s_small], [w_small])
+def test_batch_rejects_mixed_precisions(ragged):
     a = vmcf.System(ragged[0][0], vmcf.FP64, force_group=True)
     b = vmcf.System(ragged[1][0], vmcf.MIXED, force_group=True)
     wa = vmcf.Walkers(a, S.initial_walkers(ragged[0][0], 16, seed=1), nblocks=2)
