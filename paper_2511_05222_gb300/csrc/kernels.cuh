@@ -650,11 +650,10 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
       if (tcs && ((ell & 7) == 7 || ell == n - 1)) {
         // eight electron slots of psi_mu: one 16-byte row of the K-major PhiT tile (chunk ell / 16);
         // each staging row is written and flushed by the same thread
-        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(P.phiT[sg]) +
-                             ((size_t)w * P.nch + (ell >> 4)) * P.Mf * 16 + (ell & 8);
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(P.phiT[sg]) + ((size_t)w * P.nch + (ell >> 4)) * P.Mf * 16;
         for (int mu = t; mu < M; mu += GS) {
           uint4* row = reinterpret_cast<uint4*>(stg + 8 * mu);
-          *reinterpret_cast<uint4*>(dst + (size_t)mu * 16) = *row;
+          *reinterpret_cast<uint4*>(dst + tc_tile_index(mu, ell & 8)) = *row;
           *row = make_uint4(0, 0, 0, 0);
         }
       }
@@ -723,7 +722,8 @@ __device__ void measure_walker(const DevSys& S, const GroupLayout& L, const Meas
           const int e8 = 16 * c + 8 * h + k;
           v8[k] = __float2bfloat16_rn(e8 < n ? f * (float)Bs[i * n + e8] : 0.f);
         }
-        *reinterpret_cast<uint4*>(y + ((size_t)c * P.Nf + j) * 16 + 8 * h) = *reinterpret_cast<const uint4*>(v8);
+        *reinterpret_cast<uint4*>(y + (size_t)c * P.Nf * 16 + tc_tile_index(j, 8 * h)) =
+            *reinterpret_cast<const uint4*>(v8);
       }
     }
     // this spin's O (and explicit dE_L/dC): outputs and walker sums
@@ -1013,8 +1013,12 @@ __global__ void __launch_bounds__(256, 2) measure_kernel(DevSys S, GroupLayout L
   unsigned char* base = smem + gid * L.bytes;
   T* acc_s = (P.acc && P.acc_in_smem) ? sm_ptr<T>(smem, acc_off) : nullptr;
   double* acc_g = (P.acc && !P.acc_in_smem) ? P.acc + (size_t)blockIdx.x * P.accL : nullptr;
+  // with the tensor-core sums the O range [3 + 9K, 3 + 9K + 2 nO) of the accumulator stays zero and is
+  // skipped: entry k < oskip is entry k, the rest entry k + olen
+  const int olen = (sizeof(T) == 4 && P.phiT[0] != nullptr) ? 2 * S.M * S.Ne : 0, oskip = 3 + 9 * S.K;
+  const int accn = P.accL - olen;
   if (acc_s) {
-    for (int i = threadIdx.x; i < P.accL; i += blockDim.x) acc_s[i] = T(0);
+    for (int k = threadIdx.x; k < accn; k += blockDim.x) acc_s[k < oskip ? k : k + olen] = T(0);
     __syncthreads();
   }
   const long long w0 = (long long)P.W * blockIdx.x / gridDim.x;
@@ -1024,7 +1028,8 @@ __global__ void __launch_bounds__(256, 2) measure_kernel(DevSys S, GroupLayout L
     __syncthreads();
     double* slot = P.acc + (size_t)blockIdx.x * P.accL;
     const double cnt = (double)acc_s[0];
-    for (int i = threadIdx.x; i < P.accL; i += blockDim.x) {
+    for (int k = threadIdx.x; k < accn; k += blockDim.x) {
+      const int i = k < oskip ? k : k + olen;
       double v = (double)acc_s[i];
       if (i == 2) v = v + 2.0 * P.e_ref * (double)acc_s[1] + cnt * P.e_ref * P.e_ref;
       if (i == 1) v = v + cnt * P.e_ref;

@@ -829,8 +829,11 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
     if (!ref) return;  // uniform over the grid
   }
   stage_C<T, NM>(S, Cs);
+  // with the tensor-core sums the slot's O range [3 + 9K, 3 + 9K + 2 nO) stays zero and is skipped:
+  // accumulator entry i < oskip is slot entry i, the rest slot entry i + olen
+  const int olen = tc ? 2 * S.M * S.Ne : 0, oskip = 3 + 9 * S.K, accn = P.accL - olen;
   if (accum)
-    for (int i = threadIdx.x; i < P.accL; i += blockDim.x) acc_s[i] = T(0);
+    for (int i = threadIdx.x; i < accn; i += blockDim.x) acc_s[i < oskip ? i : i + olen] = T(0);
   __syncthreads();
 
   const long long w0 = (long long)W * blockIdx.x / gridDim.x, w1 = (long long)W * (blockIdx.x + 1) / gridDim.x;
@@ -1206,7 +1209,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
             HL[1] += yL * (h[3] * jg[0] + h[1] * jg[1] + h[5] * jg[2]);
             HL[2] += yL * (h[4] * jg[0] + h[5] * jg[1] + h[2] * jg[2]);
             if (tc)
-              reinterpret_cast<__nv_bfloat16*>(P.phiT[sg])[((size_t)w * P.Mp + sh.w + m) * 16 + el] =
+              reinterpret_cast<__nv_bfloat16*>(P.phiT[sg])[(size_t)w * P.Mp * 16 + tc_tile_index(sh.w + m, el)] =
                   __float2bfloat16_rn((float)(Pa * rs.R0));
             else
               phi[e * L.chunk + chunk_n + m] = Pa * rs.R0;
@@ -1233,8 +1236,8 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
 #pragma unroll
       for (int i = 0; i < NM; ++i)
         if (i < n) {
-          y[i * 16 + el] = __float2bfloat16_rn((float)(wtT * bc[i]));
-          y[(n + i) * 16 + el] = __float2bfloat16_rn((float)(wcwT * bc[i]));
+          y[tc_tile_index(i, el)] = __float2bfloat16_rn((float)(wtT * bc[i]));
+          y[tc_tile_index(n + i, el)] = __float2bfloat16_rn((float)(wcwT * bc[i]));
         }
     }
     // e-n Jastrow and V_en derivatives, one nucleus at a time; an electron moving is the
@@ -1405,7 +1408,8 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
     __syncthreads();
     double* slot = P.acc + (size_t)blockIdx.x * P.accL;
     const double cnt = (double)acc_s[0];
-    for (int i = threadIdx.x; i < P.accL; i += blockDim.x) {
+    for (int k = threadIdx.x; k < accn; k += blockDim.x) {
+      const int i = k < oskip ? k : k + olen;
       double v = (double)acc_s[i];
       if (i == 2) v = v + 2.0 * P.e_ref * (double)acc_s[1] + cnt * P.e_ref * P.e_ref;
       if (i == 1) v = v + cnt * P.e_ref;
@@ -1475,11 +1479,11 @@ template <typename T>
 cudaError_t launch_propose_small_impl(const DevSys& S, int nm, int grid, size_t smem, const SmallProposeParams& P,
                                       cudaStream_t st) {
   if (nm <= 8)
-    propose_small<T, 8><<<grid, 256, smem, st>>>(S, P);
+    propose_small<T, 8><<<grid, 32 * kProposeWarps, smem, st>>>(S, P);
   else if (nm <= 14)
-    propose_small<T, 14><<<grid, 256, smem, st>>>(S, P);
+    propose_small<T, 14><<<grid, 32 * kProposeWarps, smem, st>>>(S, P);
   else
-    propose_small<T, 16><<<grid, 256, smem, st>>>(S, P);
+    propose_small<T, 16><<<grid, 32 * kProposeWarps, smem, st>>>(S, P);
   return cudaGetLastError();
 }
 

@@ -327,7 +327,7 @@ void plan_small(vmcf_system_s& s) {
   if (L.cta_bytes + warps * L.bytes > kSmemCap) return;
   s.SL = L;
   s.small_warps = warps;
-  s.small_move_smem = (size_t)tsz * 2 * s.M * ((s.small_nm + 3) / 4 * 4);
+  s.small_move_smem = vmcf::propose_c_bytes(s.M, (s.small_nm + 3) / 4 * 4, tsz);
   if (s.small_move_smem > (size_t)kSmemCap) return;
   s.small = true;
   s.tc_Mp = (s.M + 7) / 8 * 8;
@@ -481,7 +481,18 @@ cudaError_t alloc_tc(vmcf_system_s* s, vmcf_walkers_s* wk) {
   const size_t W = wk->W;
   const size_t Mf = s->small ? s->tc_Mp : s->tcg_Mf, Nf = s->small ? s->tc_Np : s->tcg_Nf;
   const size_t nch = s->small ? s->tc_nch : s->tcg_nch;
-  wk->tc_cpb = std::max(1, (int)(W / ((size_t)wk->nblocks * 64)));
+  // CTAs per jackknife block of the walker-sum GEMM: as many as fit one wave of resident CTAs (a second,
+  // partial wave would double the kernel's time), at most one per 16 walkers
+  {
+    int per_sm = 1, dev = 0, sms = 1;
+    cudaError_t e0 = tc_sumprod_ctas_per_sm((int)Mf, (int)Nf, &per_sm);
+    if (e0 == cudaSuccess) e0 = cudaGetDevice(&dev);
+    if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e0 != cudaSuccess) return e0;
+    const size_t tiles = ((Mf + 127) / 128) * ((Nf + 31) / 32);
+    const size_t wave = (size_t)std::max(1, per_sm) * sms / (2 * tiles * wk->nblocks);
+    wk->tc_cpb = (int)std::max<size_t>(1, std::min<size_t>(wave, W / ((size_t)wk->nblocks * 16)));
+  }
   cudaError_t e;
   for (int k = 0; k < 2; ++k) {
     if ((e = cudaMalloc(&wk->phiT[k], 2 * W * nch * Mf * 16))) return e;
@@ -931,6 +942,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   if (ce == cudaSuccess) ce = s->precision == VMCF_FP64 ? set_smem_limits<double>(s->GS) : set_smem_limits<float>(s->GS);
   if (ce == cudaSuccess && s->small)
     ce = s->precision == VMCF_FP64 ? set_smem_limits_small<double>() : set_smem_limits_small<float>();
+  if (ce == cudaSuccess && s->precision == VMCF_MIXED) ce = set_smem_limits_tc();
   if (ce == cudaSuccess && s->small) {
     int dev = 0, sms = 0;
     ce = cudaGetDevice(&dev);

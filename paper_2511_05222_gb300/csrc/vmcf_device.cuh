@@ -11,6 +11,13 @@
 
 namespace vmcf {
 
+// Position (in bf16 elements) of row r, electron slot k (0..15) in one chunk of the tensor-core
+// walker-sum tiles: K-major 8-row x 16-byte core matrices without swizzle, slots 8..15 of a row
+// group 128 bytes after slots 0..7, the next 8 rows 256 bytes on.
+__host__ __device__ __forceinline__ int tc_tile_index(int r, int k) {
+  return ((r >> 3) * 2 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
 constexpr int kMaxPrim = 8;
 
 struct DevSys {

@@ -36,7 +36,7 @@ struct vmcf_system_s {
   int small_res = 1;          // resident measurement CTAs on the device
   int small_sms = 1;          // SMs on the device
   vmcf::SmallLayout SL{};
-  size_t small_move_smem = 0;  // C staging of the proposal kernel
+  size_t small_move_smem = 0;  // shared memory of the proposal kernel (C staging)
   int move_lpw = 2;            // lanes per walker in the move kernel (1, 2, 4 or 8)
   bool tc_sums = false;        // mixed small path: walker sums of O on the tensor cores
   int tc_Mp = 0, tc_Np = 0;    // padded AO rows and Y columns of those tiles

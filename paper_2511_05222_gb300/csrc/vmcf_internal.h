@@ -84,6 +84,13 @@ struct SmallProposals {
   int nms;       // row stride (c_stride of the register-row width)
 };
 
+// Shared memory of the proposal kernel: the staged coefficient rows C^up, C^dn ([2][M][nms] of the
+// working type).
+__host__ __device__ inline size_t propose_c_bytes(int M, int nms, size_t tsz) {
+  return (tsz * 2 * (size_t)M * nms + 15) / 16 * 16;
+}
+constexpr int kProposeWarps = 8;  // warps per CTA of the proposal kernel
+
 struct SmallProposeParams {
   const double* pos;   // [3 Ne][W], positions at the start of the sweep (FP64 mode)
   const float2* posf;  // [3 Ne][W], the same as float-float pairs (mixed mode)
@@ -159,11 +166,14 @@ cudaError_t set_smem_limits_small();
 cudaError_t launch_to_interleaved(const double* src, double* dst, float2* dstf, int W, int n3, cudaStream_t st);
 cudaError_t launch_from_interleaved(const double* src, double* dst, int W, int n3, cudaStream_t st);
 
-// Tensor-core walker sums of O: PhiT[s] [W][nch][Mf][16] and YT[s] [W][nch][Nf][16] bf16 per spin;
+// Tensor-core walker sums of O: PhiT[s] [W][nch] chunks of Mf x 16 and YT[s] [W][nch] chunks of Nf x 16
+// bf16 per spin, element (row r, electron slot k) of a chunk at tc_tile_index(r, k);
 // slots [2][tiles][grid_x][128][32] FP64 with tiles = ceil(Mf / 128) ceil(Nf / 32).
 cudaError_t launch_tc_sumprod(const void* phiT_up, const void* phiT_dn, const void* yT_up, const void* yT_dn, int W,
                               int nch, int Mf, int Nf, int n_up, int n_dn, int grid_x, double* slots, int* flag,
                               cudaStream_t st);
+cudaError_t set_smem_limits_tc();
+cudaError_t tc_sumprod_ctas_per_sm(int Mf, int Nf, int* n);
 cudaError_t launch_tc_fold(const double* slots, int nblocks, int cpb, int Mf, int Nf, int M, int n_up, int n_dn,
                            int oo, int nO, int accL, double* blocks, cudaStream_t st);
 
