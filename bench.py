@@ -195,7 +195,7 @@ def measure_source_sha1() -> str:
     """Hash of the measurement kernel's source (its function text and the shared device header)."""
     import hashlib
     ks = open(os.path.join(ROOT, "paper_2511_05222_gb300/csrc/kernels_small.cuh")).read()
-    a = ks.index("__global__ void __launch_bounds__(256, 2) measure_small(")
+    a = ks.index("template <typename T, int NM, bool JB>\n__global__ void __launch_bounds__(256, 2) measure_small(")
     b = ks.index("// Layout conversion between the ABI")
     dev = open(os.path.join(ROOT, "paper_2511_05222_gb300/csrc/vmcf_device.cuh")).read()
     return hashlib.sha1((ks[a:b] + dev).encode()).hexdigest()
@@ -463,16 +463,18 @@ def main():
         peak = {"fp32": peaks["fp32_tflops"], "fp64": peaks["fp64_tflops"], "sfu": peaks["exp_gops"] / 1e3}[bound]
         achieved = pipe_flops * W / t_launch / 1e12
         # the one-warp-per-walker kernel family, else walker groups (32 threads up to 24 orbitals per spin)
-        small = sysx.Ne <= 32 and max(sysx.n_up, sysx.n_dn) <= 16 and jb is None and not group
+        small = sysx.Ne <= 32 and max(sysx.n_up, sysx.n_dn) <= 16 and not group
         wide = max(sysx.n_up, sysx.n_dn) > 24
         jbf = "1" if jb else "0"  # walker-group kernels: instance with (1) or without (0) the AO-expanded Jastrow terms
         nmx = max(sysx.n_up, sysx.n_dn)
         nm = 8 if nmx <= 8 else (14 if nmx <= 14 else 16)  # register-row width of the one-warp-per-walker kernels
         tn = "float" if prec == vmcf.MIXED else "double"
-        kname = (f"{dom}_small<{tn}, {nm}>" if small else
+        kname = ({"move": f"move_small<{tn}, {nm}, 2, 0>",
+                  "measure": f"measure_small<{tn}, {nm}, {jbf}>"}[dom] if small else
                  {"move": f"move_kernel<{tn}, {128 if wide else 32}, {jbf}>",
                   "measure": f"measure_kernel<{tn}, {256 if wide else 32}, {jbf}>"}[dom])
-        traffic = profiled_traffic() if (dom == "measure" and small and prec == vmcf.MIXED and W == 16384) else None
+        traffic = (profiled_traffic() if (dom == "measure" and small and jb is None and prec == vmcf.MIXED and W == 16384)
+                   else None)
         roofline = {"bound": "alu", "pipe": bound, "kernel": kname, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s" if bound != "sfu" else "Texp/s", "frac": achieved / peak,
                     "peak_source": "measured in this run by vmcf_probe_pipes (register-only FMA/exp kernels)",
@@ -542,7 +544,7 @@ def main():
             wk.set_positions(host, stream=stream)          # H2D, inverses rebuilt
             wk.sample(1, 0.3, 26, measure=True, stream=stream)
             _ = wk.reduce_estimators(stream=stream)         # D2H block sums + host finish
-            host[:] = wk.positions(stream=stream)           # D2H positions for the next step
+            wk.positions(stream=stream, out=host)           # D2H positions (pinned) for the next step
         barrier()
         te = max_over_ranks(time.perf_counter() - t0)
         h2d = W * sysx.Ne * 3 * 8

@@ -8,17 +8,20 @@ cudaError_t launch_move_small<float>(const DevSys& S, int nm, int lpw, int W, si
   return launch_move_small_impl<float>(S, nm, lpw, W, smem, P, st);
 }
 template <>
-cudaError_t launch_propose_small<float>(const DevSys& S, int nm, int grid, size_t smem, const SmallProposeParams& P,
-                                        cudaStream_t st) {
-  return launch_propose_small_impl<float>(S, nm, grid, smem, P, st);
+cudaError_t launch_propose_small<float>(const DevSys& S, int nm, int grid, int warps, size_t smem,
+                                        const SmallProposeParams& P, cudaStream_t st) {
+  if (S.MJ > 0) return launch_propose_small_jb<float>(S, nm, grid, warps, smem, P, st);
+  return launch_propose_small_impl<float, false>(S, nm, grid, warps, smem, P, st);
 }
 template <>
 cudaError_t launch_measure_small<float>(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
                                       const SmallMeasParams& P, cudaStream_t st) {
-  return launch_measure_small_impl<float>(S, nm, L, grid, warps, P, st);
+  if (S.MJ > 0) return launch_measure_small_jb<float>(S, nm, L, grid, warps, P, st);
+  return launch_measure_small_impl<float, false>(S, nm, L, grid, warps, P, st);
 }
 template <>
 cudaError_t set_smem_limits_small<float>() {
-  return set_smem_limits_small_impl<float>();
+  cudaError_t e = set_smem_limits_small_impl<float, false>();
+  return e == cudaSuccess ? set_smem_limits_small_jb<float>() : e;
 }
 }  // namespace vmcf

@@ -248,14 +248,28 @@ cudaError_t set_smem_limits_tc() {
   return e;
 }
 
-// CTAs of the walker-sum kernel resident per SM for a launch over tiles of at most Mf x Nf: the
-// occupancy calculator's answer, or, if it reports none, the count that the SM's shared memory holds
-// (228 KB, less 1 KB reserved and the static part per CTA).
+// CTAs of the walker-sum kernel resident per SM for a launch over tiles of at most Mf x Nf, from the kernel's
+// registers and shared memory against the SM's (the kernel is always launched with the largest shared-memory
+// carve-out, which set_smem_limits_tc requests).
 cudaError_t tc_sumprod_ctas_per_sm(int Mf, int Nf, int* n) {
   const size_t smem = tc_sumprod_smem(Mf < 128 ? Mf : 128, Nf < 32 ? Nf : 32);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(n, tc_sumprod_kernel, kTcThreads, smem);
-  if (e == cudaSuccess && *n < 1) *n = (int)((228 * 1024) / (smem + 2048));
-  return e;
+  cudaFuncAttributes fa{};
+  int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0, thr_sm = 0;
+  cudaError_t e = cudaFuncGetAttributes(&fa, tc_sumprod_kernel);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  if (e != cudaSuccess) return e;
+  const size_t per_cta = smem + fa.sharedSizeBytes + (size_t)reserved;
+  const int by_smem = (int)((size_t)smem_sm / per_cta);
+  const int by_regs = fa.numRegs > 0 ? regs_sm / (fa.numRegs * kTcThreads) : by_smem;
+  const int by_thr = thr_sm / kTcThreads;
+  int v = by_smem < by_regs ? by_smem : by_regs;
+  v = v < by_thr ? v : by_thr;
+  *n = v > 0 ? v : 1;
+  return cudaSuccess;
 }
 
 cudaError_t launch_tc_sumprod(const void* phiT_up, const void* phiT_dn, const void* yT_up, const void* yT_dn, int W,

@@ -26,6 +26,7 @@
 
 #include "vmcf_device.cuh"
 #include "vmcf_internal.h"
+#include "kernels_small_jb.cuh"
 
 namespace vmcf {
 
@@ -326,10 +327,12 @@ __device__ __forceinline__ void sweep_segment(int c0, int Ne, int kref, int meas
 // electron moves once per sweep, so r_e is its position at the start of the sweep, and whatever
 // depends only on r_e and r'_e is the same however the sweep's earlier moves went: the draws, the
 // orbital row phi^s(r'_e) = sum_mu psi_mu(r'_e) C^s_mu of the electron's spin, and the change of the
-// electron-nucleus Jastrow terms. This kernel computes them for every electron of every walker at
-// once (one warp per walker, one lane per electron); the move kernel keeps only what depends on the
-// order of the moves.
-template <typename T, int NM>
+// electron-nucleus Jastrow terms. With AO-expanded Jastrow terms (JB) also their change, which depends on
+// the earlier moves only through which of them were accepted: the part that does not (added to the
+// electron-nucleus change) and a pair term for each accepted earlier electron. This kernel computes them
+// for every electron of every walker at once (one warp per walker, one lane per electron); the move kernel
+// keeps only what depends on the order of the moves.
+template <typename T, int NM, bool JB>
 __global__ void __launch_bounds__(256) propose_small(DevSys S, SmallProposeParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* Cs = reinterpret_cast<T*>(smem);  // C^up, C^dn [2][M][c_stride<NM>()]
@@ -338,10 +341,26 @@ __global__ void __launch_bounds__(256) propose_small(DevSys S, SmallProposeParam
   constexpr int NMS = c_stride<NM>();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int Ne = S.Ne, W = P.W, e = lane;
-  if (e >= Ne) return;  // no warp-wide operation follows
+  if (!JB && e >= Ne) return;  // no warp-wide operation follows
+  const bool has_e = e < Ne;
+  // with the Jastrow-basis terms: Xi's rows [MJ][MJp] staged once, then this warp's rows dphi [Ne][JS] and
+  // vectors s and t0 [2][MJp]
+  const int JS = P.jJS;
+  T* jXs = reinterpret_cast<T*>(smem + propose_c_bytes(S.M, NMS, sizeof(T)));
+  T* jD = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(jXs) + propose_xi_bytes(S.MJ, sizeof(T)) +
+                               warp * propose_jb_bytes(Ne, S.MJ, JS, sizeof(T)));
+  if constexpr (JB) {
+    const T* Xr = jas_Xr<T>(S);
+    for (int i = threadIdx.x; i < S.MJ * S.MJp; i += blockDim.x) jXs[i] = __ldg(Xr + i);
+    __syncthreads();
+  }
   const int sg = e < S.nup ? 0 : 1;
   const T* Csg = Cs + sg * S.M * NMS;
   for (long long w = (long long)blockIdx.x * nwarps + warp; w < W; w += (long long)gridDim.x * nwarps) {
+   EPos epo{}, epn{};  // start-of-sweep position and proposal (Jastrow-basis terms)
+   T dchi = T(0);
+   size_t pe = 0;
+   if (has_e) {
     const uint64_t wid = P.wid0 + (uint64_t)w, sweep = P.clk ? P.clk->sweep : P.sweep;
     uint64_t r[4] = {wid, sweep, (uint64_t)e, 0};
     philox4x64_10(r, P.k0, P.k1);
@@ -391,7 +410,6 @@ __global__ void __launch_bounds__(256) propose_small(DevSys S, SmallProposeParam
         }
       }
     });
-    T dchi = T(0);
     if (S.J1) {
       for (int I = 0; I < S.K; ++I) {
         const T mz = -nuc_Z<T>(S, I), b = jas_b<T>(S);
@@ -409,7 +427,7 @@ __global__ void __launch_bounds__(256) propose_small(DevSys S, SmallProposeParam
         dchi += pade_at<T>(mz, b, d1) - pade_at<T>(mz, b, d0);
       }
     }
-    const size_t pe = (size_t)w * Ne + e;
+    pe = (size_t)w * Ne + e;
     T* rw = reinterpret_cast<T*>(P.pr.rows) + pe * NMS;
 #pragma unroll
     for (int i = 0; i < NMS; ++i) rw[i] = i < NM ? row[i] : T(0);
@@ -419,7 +437,26 @@ __global__ void __launch_bounds__(256) propose_small(DevSys S, SmallProposeParam
       else reinterpret_cast<float2*>(P.pr.rnew)[pe * 3 + k] = make_float2(nh[k], nl[k]);
     }
     P.pr.u[pe] = u01_bits(r2[0]);
-    reinterpret_cast<T*>(P.pr.dchi)[pe] = dchi;
+    if constexpr (JB) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        epo.d[k] = po[k];
+        epn.d[k] = rn[k];
+        if constexpr (sizeof(T) == 4) {
+          epo.h[k] = oh[k];
+          epo.l[k] = ol[k];
+          epn.h[k] = nh[k];
+          epn.l[k] = nl[k];
+        }
+      }
+    }
+   }
+    if constexpr (JB) {
+      T* js = jD + Ne * JS;
+      jb_propose_small<T>(S, JS, jXs, jD, js, js + S.MJp, lane, has_e, epo, epn, P.pr.npair,
+                          reinterpret_cast<T*>(P.pr.dpair) + (size_t)w * P.pr.npair, dchi);
+    }
+    if (has_e) reinterpret_cast<T*>(P.pr.dchi)[pe] = dchi;
   }
 }
 
@@ -487,6 +524,10 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
   }
   // a launch never crosses a sweep: its moves are electrons e0, e0 + 1, ... of one sweep
   const int e0 = (int)(move0 % (uint64_t)Ne);
+  // AO-expanded Jastrow pair terms: which of the sweep's earlier moves were accepted (a run after a
+  // re-inversion continues the sweep's mask)
+  const bool jbp = P.pr.npair > 0;
+  uint32_t am = (jbp && e0 > 0) ? P.pr.amask[w] : 0u;
   // this sweep's proposals, one move ahead: the loads of move mv + 1 are in flight while move mv runs
   T rowc[NM], rown[NM];
   double rnc[3], rnn[3], uc = 0.0, un = 0.0;
@@ -567,6 +608,11 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
         }
         jacc += pair_at<T>(S, par, d1) - pair_at<T>(S, par, d0);
       }
+    }
+    if (jbp) {  // the Jastrow-basis pair terms of the accepted earlier electrons j = q, q + LPW, ... < e
+      const T* dpe = reinterpret_cast<const T*>(P.pr.dpair) + (size_t)w * P.pr.npair + e * (e - 1) / 2;
+      for (int j = q; j < e; j += LPW)
+        if ((am >> j) & 1u) jacc += __ldg(dpe + j);
     }
     const double u = uc;
     // |R exp(dJ)|^2 with R in FP64; in mixed mode the Jastrow factor is formed in float
@@ -660,12 +706,14 @@ __global__ void __launch_bounds__(256) move_small(DevSys S, SmallMoveParams P) {
         }
       }
       ++nacc;
+      am |= 1u << e;
     }
     if (LPW > 1) __syncwarp(mask);  // the new position is visible to the group's next move
   }
   if (q == 0) {
     P.nacc[w] += nacc;
     P.nrej[w] += nrej;
+    if (jbp) P.pr.amask[w] = am;
   }
   // this walker's inverses (and, in mixed mode, float-float positions) back to global memory (its lanes
   // share the copy)
@@ -795,13 +843,18 @@ __device__ __forceinline__ void warp_sum_f(double (&v)[NV]) {
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
 }
 
-template <typename T, int NM>
+template <typename T, int NM, bool JB>
 __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L, SmallMeasParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   T* Cs = reinterpret_cast<T*>(smem + L.cta_C);
   T* acc_s = reinterpret_cast<T*>(smem + L.cta_acc);
-  unsigned char* base = smem + L.cta_bytes + warp * L.bytes;
+  // mixed-mode walker sums of O through the tensor-core kernel: the kernel emits PhiT and YT tiles, and the
+  // CTA's accumulator leaves out the O range [3 + 9K, 3 + 9K + 2 nO) of the slot (which stays zero): accumulator
+  // entry k is slot entry k < oskip ? k : k + olen
+  const bool tc = P.mode == 2 && sizeof(T) == 4 && P.phiT[0] != nullptr;
+  const int olen = tc ? 2 * S.M * S.Ne : 0, oskip = 3 + 9 * S.K, accn = P.accL - olen;
+  unsigned char* base = smem + (tc ? L.cta_bytes_tc : L.cta_bytes) + warp * L.bytes;
   double* pd = reinterpret_cast<double*>(base + L.pd);
   float* ph = reinterpret_cast<float*>(base + L.ph);
   float* pl = reinterpret_cast<float*>(base + L.pl);
@@ -820,8 +873,6 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
   const int Ne = S.Ne, nup = S.nup, ndn = S.ndn, K = S.K, M = S.M, W = P.W;
   const int nO = M * Ne;
   const bool accum = P.mode == 2;
-  // mixed-mode walker sums of O through the tensor-core kernel: emit PhiT and YT tiles
-  const bool tc = accum && sizeof(T) == 4 && P.phiT[0] != nullptr;
   if (P.mode == 0 && P.clk) {  // batch graph: re-invert only where the sweep's schedule has a re-inversion
     int start, count;
     bool ref;
@@ -829,11 +880,8 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
     if (!ref) return;  // uniform over the grid
   }
   stage_C<T, NM>(S, Cs);
-  // with the tensor-core sums the slot's O range [3 + 9K, 3 + 9K + 2 nO) stays zero and is skipped:
-  // accumulator entry i < oskip is slot entry i, the rest slot entry i + olen
-  const int olen = tc ? 2 * S.M * S.Ne : 0, oskip = 3 + 9 * S.K, accn = P.accL - olen;
   if (accum)
-    for (int i = threadIdx.x; i < accn; i += blockDim.x) acc_s[i < oskip ? i : i + olen] = T(0);
+    for (int k = threadIdx.x; k < accn; k += blockDim.x) acc_s[k] = T(0);
   __syncthreads();
 
   const long long w0 = (long long)W * blockIdx.x / gridDim.x, w1 = (long long)W * (blockIdx.x + 1) / gridDim.x;
@@ -933,6 +981,17 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
         } else {
           ven -= Z * ri;
         }
+      }
+    }
+
+    // ---- AO-expanded Jastrow terms (JB): their shares of grad J, lap J and J; t0 stays in the vector region
+    EPos jep{};
+    if constexpr (JB) {
+      jep = make_epos(p);
+      if (full) {
+        T* jv0 = reinterpret_cast<T*>(base + L.jv);
+        jb_eval_small<T>(S, L.JS, reinterpret_cast<T*>(base + L.jA), jv0, jv0 + S.MJp, lane, has_e, jep, jg, jl, jv);
+        __syncwarp();  // the rows are in the work space of the passes below
       }
     }
 
@@ -1301,6 +1360,14 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
       }
     }
     __syncwarp();
+    // AO-expanded Jastrow terms (JB): their shares of the nuclear derivatives and of dE_L/dr_e, with
+    // h = grad ln D + grad J of this electron
+    if constexpr (JB) {
+      const T h[3] = {gd[0] + jg[0], gd[1] + jg[1], gd[2] + jg[2]};
+      T* jv0 = reinterpret_cast<T*>(base + L.jv);
+      jb_force_small<T>(S, L.JS, reinterpret_cast<T*>(base + L.jA), jv0, jv0 + 2 * S.MJp, jv0 + S.MJp, lane, has_e, jep,
+                        h, frc, dr);
+    }
     // ---- space warp (force expression with omega_a(r) = kappa(|r - R_a|) / sum_b kappa(|r - R_b|),
     // kappa(r) = r^-4): e-e pair terms of dE_L/dr_e, then per nucleus
     //   dE_L^sw/dR_a = dE_L/dR_a + sum_e omega_a(r_e) dE_L/dr_e,
@@ -1352,7 +1419,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
 #pragma unroll
           for (int k = 0; k < 3; ++k) gk[k] += T(-4) * sv[k] * kap / r2;
         }
-      const int so = P.swct_off;
+      const int so = P.swct_off - olen;  // in the accumulator
       for (int a = 0; a < K; ++a) {
         T v6[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
         if (has_e) {
@@ -1410,7 +1477,7 @@ __global__ void __launch_bounds__(256, 2) measure_small(DevSys S, SmallLayout L,
     const double cnt = (double)acc_s[0];
     for (int k = threadIdx.x; k < accn; k += blockDim.x) {
       const int i = k < oskip ? k : k + olen;
-      double v = (double)acc_s[i];
+      double v = (double)acc_s[k];
       if (i == 2) v = v + 2.0 * P.e_ref * (double)acc_s[1] + cnt * P.e_ref * P.e_ref;
       if (i == 1) v = v + cnt * P.e_ref;
       slot[i] += v;
@@ -1475,48 +1542,53 @@ cudaError_t launch_move_small_impl(const DevSys& S, int nm, int lpw, int W, size
   return launch_move_small_lpw<T, 16>(lpw, S, W, smem, P, st);
 }
 
-template <typename T>
-cudaError_t launch_propose_small_impl(const DevSys& S, int nm, int grid, size_t smem, const SmallProposeParams& P,
-                                      cudaStream_t st) {
+template <typename T, bool JB>
+cudaError_t launch_propose_small_impl(const DevSys& S, int nm, int grid, int warps, size_t smem,
+                                      const SmallProposeParams& P, cudaStream_t st) {
   if (nm <= 8)
-    propose_small<T, 8><<<grid, 32 * kProposeWarps, smem, st>>>(S, P);
+    propose_small<T, 8, JB><<<grid, 32 * warps, smem, st>>>(S, P);
   else if (nm <= 14)
-    propose_small<T, 14><<<grid, 32 * kProposeWarps, smem, st>>>(S, P);
+    propose_small<T, 14, JB><<<grid, 32 * warps, smem, st>>>(S, P);
   else
-    propose_small<T, 16><<<grid, 32 * kProposeWarps, smem, st>>>(S, P);
+    propose_small<T, 16, JB><<<grid, 32 * warps, smem, st>>>(S, P);
   return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, bool JB>
 cudaError_t launch_measure_small_impl(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
                                       const SmallMeasParams& P, cudaStream_t st) {
-  const size_t smem = (size_t)L.cta_bytes + (size_t)warps * L.bytes;
+  const bool tc = P.mode == 2 && sizeof(T) == 4 && P.phiT[0] != nullptr;
+  const size_t smem = (size_t)(tc ? L.cta_bytes_tc : L.cta_bytes) + (size_t)warps * L.bytes;
   if (nm <= 8)
-    measure_small<T, 8><<<grid, 32 * warps, smem, st>>>(S, L, P);
+    measure_small<T, 8, JB><<<grid, 32 * warps, smem, st>>>(S, L, P);
   else if (nm <= 14)
-    measure_small<T, 14><<<grid, 32 * warps, smem, st>>>(S, L, P);
+    measure_small<T, 14, JB><<<grid, 32 * warps, smem, st>>>(S, L, P);
   else
-    measure_small<T, 16><<<grid, 32 * warps, smem, st>>>(S, L, P);
+    measure_small<T, 16, JB><<<grid, 32 * warps, smem, st>>>(S, L, P);
   return cudaGetLastError();
 }
 
-template <typename T>
+// Shared-memory limits of the proposal and measurement instances of one Jastrow flag (and, without the
+// terms, of the move kernels).
+template <typename T, bool JB>
 cudaError_t set_smem_limits_small_impl() {
   const int lim = 227 * 1024;
   cudaError_t e;
+  if constexpr (!JB) {
 #define VMCF_MOVE_ATTR(NM, L, G)                                                                                  \
   if ((e = cudaFuncSetAttribute(move_small<T, NM, L, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  VMCF_MOVE_ATTR(8, 1, false) VMCF_MOVE_ATTR(8, 2, false) VMCF_MOVE_ATTR(8, 4, false) VMCF_MOVE_ATTR(8, 8, false)
-  VMCF_MOVE_ATTR(14, 1, false) VMCF_MOVE_ATTR(14, 2, false) VMCF_MOVE_ATTR(14, 4, false) VMCF_MOVE_ATTR(14, 8, false)
-  VMCF_MOVE_ATTR(16, 1, false) VMCF_MOVE_ATTR(16, 2, false) VMCF_MOVE_ATTR(16, 4, false) VMCF_MOVE_ATTR(16, 8, false)
-  VMCF_MOVE_ATTR(8, 2, true) VMCF_MOVE_ATTR(14, 2, true) VMCF_MOVE_ATTR(16, 2, true)
+    VMCF_MOVE_ATTR(8, 1, false) VMCF_MOVE_ATTR(8, 2, false) VMCF_MOVE_ATTR(8, 4, false) VMCF_MOVE_ATTR(8, 8, false)
+    VMCF_MOVE_ATTR(14, 1, false) VMCF_MOVE_ATTR(14, 2, false) VMCF_MOVE_ATTR(14, 4, false) VMCF_MOVE_ATTR(14, 8, false)
+    VMCF_MOVE_ATTR(16, 1, false) VMCF_MOVE_ATTR(16, 2, false) VMCF_MOVE_ATTR(16, 4, false) VMCF_MOVE_ATTR(16, 8, false)
+    VMCF_MOVE_ATTR(8, 2, true) VMCF_MOVE_ATTR(14, 2, true) VMCF_MOVE_ATTR(16, 2, true)
 #undef VMCF_MOVE_ATTR
-  if ((e = cudaFuncSetAttribute(propose_small<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(propose_small<T, 14>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(propose_small<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(measure_small<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(measure_small<T, 14>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-  if ((e = cudaFuncSetAttribute(measure_small<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  }
+  if ((e = cudaFuncSetAttribute(propose_small<T, 8, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(propose_small<T, 14, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(propose_small<T, 16, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_small<T, 8, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_small<T, 14, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+  if ((e = cudaFuncSetAttribute(measure_small<T, 16, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   return cudaSuccess;
 }
 

@@ -298,7 +298,7 @@ int plan(vmcf_system_s& s) {
 // register row, and the shared-memory plan fits.
 void plan_small(vmcf_system_s& s) {
   s.small = false;
-  if (s.Ne > 32 || s.nmax > 16 || s.MJ > 0) return;  // the AO-expanded Jastrow terms run on walker groups
+  if (s.Ne > 32 || s.nmax > 16) return;
   const int tsz = s.precision == VMCF_FP64 ? 8 : 4;
   s.small_nm = s.nmax <= 8 ? 8 : (s.nmax <= 14 ? 14 : 16);  // register-row width; staged rows padded to 4
   SmallLayout L{};
@@ -308,27 +308,48 @@ void plan_small(vmcf_system_s& s) {
   L.pd = take(8 * 3 * s.Ne);
   L.ph = take(4 * 3 * s.Ne);
   L.pl = take(4 * 3 * s.Ne);
+  L.frc = take(tsz * 6 * s.K);
+  L.red = take(16);
+  L.scal = take(32);
+  // from here to phi's end: work space that is dead before pass 1 and after pass 3
+  const int dead0 = o;
   L.Ad = take(8 * s.nB);
   L.Bf = (tsz == 8) ? L.Ad : take(tsz * s.nB);
   L.Pm = take(tsz * s.nB);
   L.Q = take(tsz * s.nmax * s.nmax);
   L.piv = take(4 * 2 * s.nmax);           // both spin blocks are inverted at once
   L.f = take(8 * 2 * (3 * s.nmax + 1));
-  L.frc = take(tsz * 6 * s.K);
   L.phi = take(tsz * s.Ne * L.chunk);
-  L.red = take(16);
-  L.scal = take(32);
+  const int dead1 = o;
+  if (s.MJ > 0) {  // AO-expanded Jastrow terms: [Ne][JS] rows (in the dead block when they fit), [3][MJp] vectors
+    const int MJp = (s.MJ + 3) / 4 * 4;
+    int JS = MJp;
+    while ((JS * tsz / 16) % 2 == 0) JS += 16 / tsz;  // 16-byte row loads of a warp's lanes in distinct banks
+    L.JS = JS;
+    L.jv = take(tsz * 3 * MJp);
+    const int need = tsz * s.Ne * JS;
+    L.jA = need <= dead1 - dead0 ? dead0 : take(need);
+  }
   L.bytes = align16(o);
   L.cta_C = 0;
   L.cta_acc = align16(tsz * 2 * s.M * ((s.small_nm + 3) / 4 * 4));
   L.cta_bytes = L.cta_acc + align16(tsz * s.accL);
+  // with the tensor-core walker sums the accumulator leaves out the O range (2 M Ne entries)
+  L.cta_bytes_tc = L.cta_acc + align16(tsz * (s.accL - 2 * s.M * s.Ne));
   int warps = 8;
   while (warps > 2 && L.cta_bytes + warps * L.bytes > kSmemCap) warps /= 2;
   if (L.cta_bytes + warps * L.bytes > kSmemCap) return;
   s.SL = L;
   s.small_warps = warps;
-  s.small_move_smem = vmcf::propose_c_bytes(s.M, (s.small_nm + 3) / 4 * 4, tsz);
-  if (s.small_move_smem > (size_t)kSmemCap) return;
+  // proposal kernel: staged C, and with the Jastrow-basis terms Xi and per warp the rows dphi_e and vectors s, t0
+  const size_t cbytes = vmcf::propose_c_bytes(s.M, (s.small_nm + 3) / 4 * 4, tsz);
+  const size_t pw = vmcf::propose_jb_bytes(s.Ne, s.MJ, L.JS, tsz);
+  int pwarps = vmcf::kProposeWarps;
+  const size_t xbytes = vmcf::propose_xi_bytes(s.MJ, tsz);
+  while (pwarps > 1 && cbytes + xbytes + pwarps * pw > (size_t)kSmemCap) pwarps /= 2;
+  if (cbytes + xbytes + pwarps * pw > (size_t)kSmemCap) return;
+  s.propose_warps = pwarps;
+  s.small_move_smem = cbytes + vmcf::propose_xi_bytes(s.MJ, tsz) + pwarps * pw;
   s.small = true;
   s.tc_Mp = (s.M + 7) / 8 * 8;
   s.tc_Np = (2 * s.nmax + 15) / 16 * 16;
@@ -610,10 +631,11 @@ cudaError_t vmcf::small_sweep_launches(vmcf_system_s* s, vmcf_walkers_s* wk, con
   Q.k1 = wk->k1;
   Q.sigma = sigma;
   Q.sigma_f = (float)sigma;
+  Q.jJS = s->SL.JS;
   Q.clk = clk;
-  const int qgrid = std::max(1, std::min((wk->W + 7) / 8, 8 * s->small_sms));
-  cudaError_t e = fp64 ? launch_propose_small<double>(s->dev, s->small_nm, qgrid, s->small_move_smem, Q, st)
-                       : launch_propose_small<float>(s->dev, s->small_nm, qgrid, s->small_move_smem, Q, st);
+  const int qgrid = std::max(1, std::min((wk->W + s->propose_warps - 1) / s->propose_warps, 8 * s->small_sms));
+  cudaError_t e = fp64 ? launch_propose_small<double>(s->dev, s->small_nm, qgrid, s->propose_warps, s->small_move_smem, Q, st)
+                       : launch_propose_small<float>(s->dev, s->small_nm, qgrid, s->propose_warps, s->small_move_smem, Q, st);
   SmallMoveParams P{};
   P.pos = wk->pos;
   P.posf = wk->posf;
@@ -886,10 +908,15 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   // Jastrow basis tables (AO-expanded Jastrow terms), double and float copies
   std::vector<float> jalpha_f(jalpha.begin(), jalpha.end()), jcoef_f(jcoef.begin(), jcoef.end());
   std::vector<float> jxi_f(jxi.begin(), jxi.end()), jXi_f(jXi.begin(), jXi.end());
+  const int MJp = (s->MJ + 3) / 4 * 4;
+  std::vector<double> jXr((size_t)s->MJ * MJp, 0.0);  // rows of Xi padded to MJp
+  for (int a = 0; a < s->MJ; ++a)
+    for (int c = 0; c < s->MJ; ++c) jXr[(size_t)a * MJp + c] = jXi[(size_t)a * s->MJ + c];
+  std::vector<float> jXr_f(jXr.begin(), jXr.end());
   const size_t oJs = slot(sizeof(int4) * jshells.size()), oJa = slot(8 * jalpha.size()), oJc = slot(8 * jcoef.size()),
                oJaf = slot(4 * jalpha.size()), oJcf = slot(4 * jcoef.size()), oJcen = slot(4 * jcenter.size()),
                oJxi = slot(8 * jxi.size()), oJxif = slot(4 * jxi.size()), oJXi = slot(8 * jXi.size()),
-               oJXif = slot(4 * jXi.size());
+               oJXif = slot(4 * jXi.size()), oJXr = slot(8 * jXr.size()), oJXrf = slot(4 * jXr.size());
   cudaError_t e = cudaMalloc(&s->dmem, off);
   if (e != cudaSuccess) {
     delete s;
@@ -939,6 +966,8 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   ce = ce ? ce : up(oJxif, jxi_f.data(), 4 * jxi_f.size());
   ce = ce ? ce : up(oJXi, jXi.data(), 8 * jXi.size());
   ce = ce ? ce : up(oJXif, jXi_f.data(), 4 * jXi_f.size());
+  ce = ce ? ce : up(oJXr, jXr.data(), 8 * jXr.size());
+  ce = ce ? ce : up(oJXrf, jXr_f.data(), 4 * jXr_f.size());
   if (ce == cudaSuccess) ce = s->precision == VMCF_FP64 ? set_smem_limits<double>(s->GS) : set_smem_limits<float>(s->GS);
   if (ce == cudaSuccess && s->small)
     ce = s->precision == VMCF_FP64 ? set_smem_limits_small<double>() : set_smem_limits_small<float>();
@@ -947,7 +976,7 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
     int dev = 0, sms = 0;
     ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t cta = (size_t)s->SL.cta_bytes + (size_t)s->small_warps * s->SL.bytes;
+    const size_t cta = (size_t)(s->tc_sums ? s->SL.cta_bytes_tc : s->SL.cta_bytes) + (size_t)s->small_warps * s->SL.bytes;
     const int by_smem = (int)((228 * 1024) / (cta + 1024));
     const int by_regs = 65536 / (32 * s->small_warps * 128);
     s->small_res = std::max(1, sms * std::max(1, std::min(by_smem, by_regs)));
@@ -1005,6 +1034,8 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
     D.jxi_f = reinterpret_cast<const float*>(b + oJxif);
     D.jXi = reinterpret_cast<const double*>(b + oJXi);
     D.jXi_f = reinterpret_cast<const float*>(b + oJXif);
+    D.jXr = reinterpret_cast<const double*>(b + oJXr);
+    D.jXr_f = reinterpret_cast<const float*>(b + oJXrf);
   }
   s->scratch_counters = reinterpret_cast<double*>(b + oCnt);
   *out = s;
@@ -1035,8 +1066,10 @@ static cudaError_t alloc_proposals(const vmcf_system_s* s, vmcf_walkers_s* wk) {
   const size_t tsz = s->precision == VMCF_FP64 ? 8 : 4, n = (size_t)wk->W * s->Ne;
   const int nms = (s->small_nm + 3) / 4 * 4;
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t npair = s->MJ > 0 ? (size_t)s->Ne * (s->Ne - 1) / 2 : 0;
   const size_t o_rows = 0, o_rnew = o_rows + al(tsz * n * nms), o_u = o_rnew + al(24 * n), o_dchi = o_u + al(8 * n),
-               bytes = o_dchi + al(tsz * n);
+               o_dpair = o_dchi + al(tsz * n), o_amask = o_dpair + al(tsz * npair * wk->W),
+               bytes = o_amask + al(4 * (size_t)wk->W);
   cudaError_t e = cudaMalloc(&wk->prop, bytes);
   if (e != cudaSuccess) return e;
   char* b = static_cast<char*>(wk->prop);
@@ -1044,6 +1077,9 @@ static cudaError_t alloc_proposals(const vmcf_system_s* s, vmcf_walkers_s* wk) {
   wk->pr.rnew = reinterpret_cast<double*>(b + o_rnew);
   wk->pr.u = reinterpret_cast<double*>(b + o_u);
   wk->pr.dchi = b + o_dchi;
+  wk->pr.dpair = npair ? b + o_dpair : nullptr;
+  wk->pr.amask = reinterpret_cast<uint32_t*>(b + o_amask);
+  wk->pr.npair = (int)npair;
   wk->pr.nms = nms;
   return cudaSuccess;
 }
@@ -1089,6 +1125,7 @@ int vmcf_walkers_create(vmcf_system_t s, int W, const double* pos, int is_host, 
       (e = cudaMalloc(&wk->counters, 16)) ||
       (e = cudaMalloc(&wk->acc, 8 * (size_t)wk->grid_meas * s->accL)) ||
       (e = cudaMalloc(&wk->blocks, 8 * (size_t)nblocks * s->accL)) ||
+      (e = cudaMallocHost(&wk->h_blocks, 8 * (size_t)nblocks * s->accL)) ||
       (s->small && (e = cudaMalloc(&wk->stage, 8 * npos))) ||
       (s->small && s->precision == VMCF_MIXED && (e = cudaMalloc(&wk->posf, sizeof(float2) * npos))) ||
       (s->small && (e = alloc_proposals(s, wk))) ||
@@ -1129,6 +1166,7 @@ int vmcf_walkers_destroy(vmcf_walkers_t wk) {
   cudaFree(wk->counters);
   cudaFree(wk->acc);
   cudaFree(wk->blocks);
+  cudaFreeHost(wk->h_blocks);
   cudaFree(wk->stage);
   cudaFree(wk->posf);
   cudaFree(wk->prop);
@@ -1231,13 +1269,14 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
     Q.k1 = wk->k1;
     Q.sigma = step_sigma;
     Q.sigma_f = (float)step_sigma;
-    const int qgrid = std::max(1, std::min((wk->W + 7) / 8, 8 * s->small_sms));
+    Q.jJS = s->SL.JS;
+    const int qgrid = std::max(1, std::min((wk->W + s->propose_warps - 1) / s->propose_warps, 8 * s->small_sms));
     for (int sw = 0; sw < n_sweeps; ++sw) {
       {  // the sweep's proposals, from the positions at its start
         Timed tm(wk, 0, st);
         Q.sweep = wk->sweep;
-        cudaError_t e = fp64 ? launch_propose_small<double>(s->dev, s->small_nm, qgrid, s->small_move_smem, Q, st)
-                             : launch_propose_small<float>(s->dev, s->small_nm, qgrid, s->small_move_smem, Q, st);
+        cudaError_t e = fp64 ? launch_propose_small<double>(s->dev, s->small_nm, qgrid, s->propose_warps, s->small_move_smem, Q, st)
+                             : launch_propose_small<float>(s->dev, s->small_nm, qgrid, s->propose_warps, s->small_move_smem, Q, st);
         if (e != cudaSuccess) return cuda_fail(e, "small proposal kernel launch");
       }
       int done = 0;
@@ -1408,18 +1447,19 @@ int jackknife_estimates(const double* blk, int nb, int K, int M, int n_up, int n
     if (!(tot[0] - blk[(size_t)b * L] > 0.0)) return fail(VMCF_EINVAL, "a jackknife block holds every sample");
   const int o_dEL = 3, o_d = 3 + K3, o_Ed = 3 + 2 * K3, o_O = 3 + 3 * K3, o_EO = 3 + 3 * K3 + nO;
   // estimates from a sum vector v (all blocks, or all but one); E_ref cancels algebraically
+  // (the means of the force and orbital fields as products with 1/n: one division per vector, not two per entry)
   auto est = [&](const double* v, double* Eo, double* Fo, double* Bo) {
-    const double n = v[0], Em = v[1] / n;
+    const double n = v[0], Em = v[1] / n, in = 1.0 / n, c = Em - er;
     *Eo = Em;
-    for (int i = 0; i < K3; ++i) Fo[i] = -(v[o_dEL + i] / n + 2.0 * (v[o_Ed + i] / n - (Em - er) * v[o_d + i] / n));
-    for (int i = 0; i < nO; ++i) Bo[i] = 2.0 * (v[o_EO + i] / n - (Em - er) * v[o_O + i] / n);
+    for (int i = 0; i < K3; ++i) Fo[i] = -(v[o_dEL + i] * in + 2.0 * (v[o_Ed + i] * in - c * (v[o_d + i] * in)));
+    for (int i = 0; i < nO; ++i) Bo[i] = 2.0 * (v[o_EO + i] * in - c * (v[o_O + i] * in));
   };
   Fv.assign(K3, 0.0);
   Bv.assign(nO, 0.0);
   est(tot.data(), Ev, Fv.data(), Bv.data());
-  Ej.assign(nb, 0.0);
-  Fj.assign((size_t)nb * K3, 0.0);
-  Bj.assign((size_t)nb * nO, 0.0);
+  Ej.resize(nb);  // every entry is written below
+  Fj.resize((size_t)nb * K3);
+  Bj.resize((size_t)nb * nO);
   std::vector<double> loo(L);
   for (int b = 0; b < nb; ++b) {
     for (int i = 0; i < L; ++i) loo[i] = tot[i] - blk[(size_t)b * L + i];
@@ -1440,29 +1480,32 @@ int vmcf_finish_estimators(const double* blk, int nb, int K, int M, int n_up, in
                            double* E_err, double* F, double* F_err, double* dEdC, double* dEdC_err) {
   if (M < 1) return fail(VMCF_EINVAL, "bad arguments");
   double Ev = 0.0;
-  std::vector<double> Fv, Bv, Ej, Fj, Bj;
+  // per-thread work space, kept between calls (no fresh pages every call)
+  thread_local std::vector<double> Fv, Bv, Ej, Fj, Bj, mean, var;
   int rc = jackknife_estimates(blk, nb, K, M, n_up, n_dn, er, &Ev, Fv, Bv, Ej, Fj, Bj);
   if (rc != VMCF_OK) return rc;
   const int K3 = 3 * K, nO = M * (n_up + n_dn);
-  auto jk = [&](const std::vector<double>& th, int stride, int idx) {
-    const double m = jk_mean(th, nb, stride, idx);
-    double v = 0.0;
-    for (int b = 0; b < nb; ++b) {
-      const double d = th[(size_t)b * stride + idx] - m;
-      v += d * d;
-    }
-    return std::sqrt((nb - 1.0) / nb * v);
+  // jackknife errors of the components of th ([nb][n]): for each component the mean over the blocks, then the
+  // sum of squared deviations, both summed over the blocks in order, a block's row at a time
+  auto jk_all = [&](const std::vector<double>& th, int n, double* err) {
+    mean.assign(n, 0.0);
+    var.assign(n, 0.0);
+    for (int b = 0; b < nb; ++b)
+      for (int i = 0; i < n; ++i) mean[i] += th[(size_t)b * n + i];
+    for (int i = 0; i < n; ++i) mean[i] /= nb;
+    for (int b = 0; b < nb; ++b)
+      for (int i = 0; i < n; ++i) {
+        const double d = th[(size_t)b * n + i] - mean[i];
+        var[i] += d * d;
+      }
+    for (int i = 0; i < n; ++i) err[i] = std::sqrt((nb - 1.0) / nb * var[i]);
   };
   if (E) *E = Ev;
-  if (E_err) *E_err = jk(Ej, 1, 0);
-  for (int i = 0; i < K3; ++i) {
-    if (F) F[i] = Fv[i];
-    if (F_err) F_err[i] = jk(Fj, K3, i);
-  }
-  for (int i = 0; i < nO; ++i) {
-    if (dEdC) dEdC[i] = Bv[i];
-    if (dEdC_err) dEdC_err[i] = jk(Bj, nO, i);
-  }
+  if (E_err) jk_all(Ej, 1, E_err);
+  if (F) std::copy(Fv.begin(), Fv.end(), F);
+  if (F_err) jk_all(Fj, K3, F_err);
+  if (dEdC) std::copy(Bv.begin(), Bv.end(), dEdC);
+  if (dEdC_err) jk_all(Bj, nO, dEdC_err);
   return VMCF_OK;
 }
 
@@ -1521,10 +1564,9 @@ int vmcf_finish_warp(const double* blk, int nb, int stride, int K, int M, int n_
 int vmcf_reduce_warp(vmcf_system_t s, vmcf_walkers_t wk, double* F, double* F_err, void* stream) {
   if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
   if (!s->swct) return fail(VMCF_EINVAL, "the system was not created with VMCF_SPACE_WARP");
-  std::vector<double> blk((size_t)wk->nblocks * s->accL);
-  int rc = vmcf_block_sums(s, wk, blk.data(), stream);
+  int rc = vmcf_block_sums(s, wk, wk->h_blocks, stream);
   if (rc != VMCF_OK) return rc;
-  return vmcf_finish_warp(blk.data(), wk->nblocks, s->accL, s->K, s->M, s->nup, s->ndn, wk->e_ref, F, F_err);
+  return vmcf_finish_warp(wk->h_blocks, wk->nblocks, s->accL, s->K, s->M, s->nup, s->ndn, wk->e_ref, F, F_err);
 }
 
 int vmcf_evaluate_warp(vmcf_system_t s, const double* pos, int W, double* dEL_dr, double* dEL_sw, double* dlnpsi_sw,
@@ -1553,17 +1595,20 @@ int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double
   if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
   if (rhs_BQ && !s->has_S) return fail(VMCF_EINVAL, "rhs_BQ needs the AO overlap S at init");
   const int L = s->accL, nb = wk->nblocks, nO = s->M * (s->nup + s->ndn);
-  std::vector<double> blk((size_t)nb * L);
-  int rc = vmcf_block_sums(s, wk, blk.data(), stream);
+  // the block sums land in the walker set's pinned host buffer (a direct copy, no staging)
+  int rc = vmcf_block_sums(s, wk, wk->h_blocks, stream);
   if (rc != VMCF_OK) return rc;
   const int Lb = 3 + 9 * s->K + 2 * nO;  // base fields; the space-warp sums (if any) follow
+  const double* blk = wk->h_blocks;
+  std::vector<double> base;
   if (L != Lb) {
-    std::vector<double> base((size_t)nb * Lb);
-    for (int b = 0; b < nb; ++b) std::copy(&blk[(size_t)b * L], &blk[(size_t)b * L] + Lb, &base[(size_t)b * Lb]);
-    blk.swap(base);
+    base.resize((size_t)nb * Lb);
+    for (int b = 0; b < nb; ++b) std::copy(blk + (size_t)b * L, blk + (size_t)b * L + Lb, &base[(size_t)b * Lb]);
+    blk = base.data();
   }
-  std::vector<double> Bv(nO);
-  rc = vmcf_finish_estimators(blk.data(), nb, s->K, s->M, s->nup, s->ndn, wk->e_ref, E, E_err, F, F_err,
+  thread_local std::vector<double> Bv;
+  Bv.resize(nO);
+  rc = vmcf_finish_estimators(blk, nb, s->K, s->M, s->nup, s->ndn, wk->e_ref, E, E_err, F, F_err,
                               Bv.data(), dEdC_err);
   if (rc != VMCF_OK) return rc;
   if (dEdC) std::copy(Bv.begin(), Bv.end(), dEdC);

@@ -63,6 +63,8 @@ struct DevSys {
   const float* jxi_f;
   const double* jXi;     // [MJp][MJ] pair coefficients Xi_{mu nu}, symmetric; rows MJ..MJp-1 are zero
   const float* jXi_f;
+  const double* jXr;     // [MJ][MJp] the same with rows padded to MJp (zero), 16-byte aligned rows
+  const float* jXr_f;
 };
 
 template <typename T> __device__ __forceinline__ const T* coefC(const DevSys& S, int s);

@@ -36,7 +36,8 @@ struct vmcf_system_s {
   int small_res = 1;          // resident measurement CTAs on the device
   int small_sms = 1;          // SMs on the device
   vmcf::SmallLayout SL{};
-  size_t small_move_smem = 0;  // shared memory of the proposal kernel (C staging)
+  size_t small_move_smem = 0;  // shared memory of the proposal kernel (C staging, Jastrow-basis rows)
+  int propose_warps = 8;       // warps per CTA of the proposal kernel
   int move_lpw = 2;            // lanes per walker in the move kernel (1, 2, 4 or 8)
   bool tc_sums = false;        // mixed small path: walker sums of O on the tensor cores
   int tc_Mp = 0, tc_Np = 0;    // padded AO rows and Y columns of those tiles
@@ -58,6 +59,7 @@ struct vmcf_walkers_s {
   unsigned long long* counters = nullptr;  // [0] singular, [1] refreshes
   double* acc = nullptr;                   // [grid_meas][accL]
   double* blocks = nullptr;                // [nblocks][accL]
+  double* h_blocks = nullptr;              // pinned host copy of the block sums [nblocks][accL] (reductions)
   uint64_t sweep = 0, measured = 0;
   int counter = 0;
   double e_ref = 0.0;

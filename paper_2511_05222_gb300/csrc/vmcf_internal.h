@@ -80,7 +80,14 @@ struct SmallProposals {
   double* rnew;  // [W][Ne][3]: proposed position r'_e (FP64 mode); mixed mode: the same bytes hold
                  // float2 [W][Ne][3], r'_e as float-float pairs (high, low)
   double* u;     // [W][Ne]: acceptance uniform
-  void* dchi;    // T [W][Ne]: change of the electron-nucleus Jastrow terms, chi(r'_e) - chi(r_e)
+  void* dchi;    // T [W][Ne]: change of the electron-nucleus Jastrow terms, chi(r'_e) - chi(r_e), plus (with
+                 // AO-expanded Jastrow terms) the part of their change that does not depend on earlier moves
+  // AO-expanded Jastrow pair terms of a sweep: the move of e changes U by dphi_e . (t0 - Xi psi_e) plus, for every
+  // accepted j < e, dphi_e . Xi dphi_j (dphi: psi^J(r') - psi^J(r) of the electron's own proposal; t0, psi: at the
+  // start of the sweep)
+  void* dpair;       // T [W][npair]: dphi_e . Xi dphi_j at pair index e (e - 1) / 2 + j, j < e (NULL without the terms)
+  uint32_t* amask;   // [W]: bit j set when electron j's move of the current sweep was accepted
+  int npair;         // Ne (Ne - 1) / 2 with the terms, else 0
   int nms;       // row stride (c_stride of the register-row width)
 };
 
@@ -89,7 +96,15 @@ struct SmallProposals {
 __host__ __device__ inline size_t propose_c_bytes(int M, int nms, size_t tsz) {
   return (tsz * 2 * (size_t)M * nms + 15) / 16 * 16;
 }
-constexpr int kProposeWarps = 8;  // warps per CTA of the proposal kernel
+// With AO-expanded Jastrow terms: per CTA, Xi's rows padded to MJp ([MJ][MJp]); per warp, the rows dphi_e of every
+// electron ([Ne][JS]) and the vectors s and t0 ([2][MJp]). Nothing without them.
+__host__ __device__ inline size_t propose_xi_bytes(int MJ, size_t tsz) {
+  return MJ > 0 ? (tsz * (size_t)MJ * ((MJ + 3) / 4 * 4) + 15) / 16 * 16 : 0;
+}
+__host__ __device__ inline size_t propose_jb_bytes(int Ne, int MJ, int JS, size_t tsz) {
+  return MJ > 0 ? (tsz * ((size_t)Ne * JS + 2 * (size_t)((MJ + 3) / 4 * 4)) + 15) / 16 * 16 : 0;
+}
+constexpr int kProposeWarps = 8;  // most warps per CTA of the proposal kernel
 
 struct SmallProposeParams {
   const double* pos;   // [3 Ne][W], positions at the start of the sweep (FP64 mode)
@@ -100,6 +115,7 @@ struct SmallProposeParams {
   double sigma;
   float sigma_f;
   const BatchClock* clk;  // in a batch graph: the sweep index comes from the geometry's device clock
+  int jJS;                // row stride of the Jastrow-basis rows (SmallLayout::JS)
 };
 
 struct SmallMoveParams {
@@ -124,8 +140,10 @@ struct SmallMoveParams {
 
 struct SmallLayout {
   int pd, ph, pl, Ad, Bf, Pm, Q, piv, f, frc, phi, red, scal;
+  int jA, jv, JS;  // AO-expanded Jastrow terms: [Ne][JS] rows (may share Ad..phi), vectors [3][MJp]; JS row stride
   int bytes;  // per warp
   int cta_C, cta_acc, cta_bytes;
+  int cta_bytes_tc;  // the CTA region with the tensor-core walker sums (no O range in the accumulator)
   int chunk;  // AOs per O chunk (Phi buffer width)
 };
 
@@ -156,8 +174,17 @@ template <typename T>
 cudaError_t launch_move_small(const DevSys& S, int nm, int lpw, int W, size_t smem, const SmallMoveParams& P,
                               cudaStream_t st);
 template <typename T>
-cudaError_t launch_propose_small(const DevSys& S, int nm, int grid, size_t smem, const SmallProposeParams& P,
+cudaError_t launch_propose_small(const DevSys& S, int nm, int grid, int warps, size_t smem, const SmallProposeParams& P,
                                  cudaStream_t st);
+// the instances for systems with AO-expanded Jastrow terms (k_small_fp32_jb.cu, k_small_fp64_jb.cu)
+template <typename T>
+cudaError_t launch_propose_small_jb(const DevSys& S, int nm, int grid, int warps, size_t smem,
+                                    const SmallProposeParams& P, cudaStream_t st);
+template <typename T>
+cudaError_t launch_measure_small_jb(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
+                                    const SmallMeasParams& P, cudaStream_t st);
+template <typename T>
+cudaError_t set_smem_limits_small_jb();
 template <typename T>
 cudaError_t launch_measure_small(const DevSys& S, int nm, const SmallLayout& L, int grid, int warps,
                                  const SmallMeasParams& P, cudaStream_t st);

@@ -274,8 +274,14 @@ class Walkers:
             _check(lib().vmcf_walkers_set_positions(self.system.h, self.h, _ptr(pos.contiguous()), 0,
                                                     _stream(stream)), "vmcf_walkers_set_positions")
 
-    def positions(self, stream=None) -> np.ndarray:
-        out = np.empty((self.W, self.system.Ne, 3))
+    def positions(self, stream=None, out=None) -> np.ndarray:
+        """Positions [W][Ne][3] into a new array, or into `out` (C-contiguous float64 host array of that shape;
+        pinned memory makes the copy a direct one)."""
+        if out is None:
+            out = np.empty((self.W, self.system.Ne, 3))
+        elif (not isinstance(out, np.ndarray) or out.dtype != np.float64 or not out.flags.c_contiguous
+              or out.shape != (self.W, self.system.Ne, 3)):
+            raise ValueError("out must be a C-contiguous float64 array of shape (W, Ne, 3)")
         _check(lib().vmcf_walkers_get_positions(self.h, ctypes.c_void_p(out.ctypes.data), 1, _stream(stream)),
                "vmcf_walkers_get_positions")
         return out

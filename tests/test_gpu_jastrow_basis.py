@@ -2,7 +2,8 @@
 term and the three/four-body pair term over a separate Jastrow basis) on the GPU against the oracle:
 per-walker outputs in FP64 (1e-10 normwise), space-warp vectors, FP64 chains and estimators following
 the oracle's chain (plain, and guided with the space-warp estimator), mixed-precision local energies (1e-5)
-and estimators (within 0.1 of their error bars, paired with FP64), and ragged batches."""
+and estimators (within 0.1 of their error bars, paired with FP64), and ragged batches. Water and C2OH6 run
+on the one-warp-per-walker kernels unless a test forces the walker-group kernels (group=True)."""
 import numpy as np
 import pytest
 
@@ -51,11 +52,11 @@ def c2oh6_jb():
     return with_jb(1)
 
 
-@pytest.mark.parametrize("W", [1, 37])
-def test_evaluate_fp64_water(water_jb, W):
+@pytest.mark.parametrize("W,group", [(1, False), (37, False), (37, True)])
+def test_evaluate_fp64_water(water_jb, W, group):
     pos = S.initial_walkers(water_jb, W, seed=5)
     ref = oracle.Oracle(water_jb).eval(pos, want=ALL)
-    g = vmcf.System(water_jb, vmcf.FP64)
+    g = vmcf.System(water_jb, vmcf.FP64, force_group=group)
     for want in (NO_DC, ALL):
         got = gpu_eval(g, pos, want)
         for k in want:
@@ -85,25 +86,25 @@ def test_evaluate_fp64_c9o4h8(group):
         assert rel(got[k], ref[k]) < TOL64, (k, rel(got[k], ref[k]))
 
 
-@pytest.mark.parametrize("cfg", [0, 1])
-def test_warp_vectors_fp64(cfg, water_jb, c2oh6_jb):
+@pytest.mark.parametrize("cfg,group", [(0, False), (1, False), (1, True)])
+def test_warp_vectors_fp64(cfg, group, water_jb, c2oh6_jb):
     sx = water_jb if cfg == 0 else c2oh6_jb
     pos = S.initial_walkers(sx, 17, seed=21)
     ref = oracle.Oracle(sx).eval_warp(pos)
-    got = vmcf.vmcf_evaluate_warp(vmcf.System(sx, vmcf.FP64), dev(pos))
+    got = vmcf.vmcf_evaluate_warp(vmcf.System(sx, vmcf.FP64, force_group=group), dev(pos))
     torch.cuda.synchronize()
     for k in ("dEL_dr", "dEL_sw", "dlnpsi_sw"):
         assert rel(got[k].cpu().numpy(), ref[k]) < TOL64, (k, rel(got[k].cpu().numpy(), ref[k]))
 
 
-@pytest.mark.parametrize("kref", [26, 7])
-def test_fp64_chain_and_estimators_follow_the_oracle(water_jb, kref):
+@pytest.mark.parametrize("kref,group", [(26, False), (7, False), (26, True)])
+def test_fp64_chain_and_estimators_follow_the_oracle(water_jb, kref, group):
     W, nb, warm, meas, e_ref = 128, 8, 3, 2, -76.0
     pos = S.initial_walkers(water_jb, W, seed=9)
     o = oracle.Oracle(water_jb)
     st = o.new_state(pos, key=(5222, 0))
     o.sample(st, warm, refresh_k=kref)
-    g = vmcf.System(water_jb, vmcf.FP64)
+    g = vmcf.System(water_jb, vmcf.FP64, force_group=group)
     wk = vmcf.Walkers(g, pos, key=(5222, 0), nblocks=nb)
     wk.sample(warm, 0.3, kref, measure=False)
     ok = st["margin"] >= 1e-9
@@ -128,7 +129,8 @@ def test_fp64_chain_and_estimators_follow_the_oracle(water_jb, kref):
         assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
 
 
-def test_mixed_local_energy(c2oh6_jb):
+@pytest.mark.parametrize("group", [False, True])
+def test_mixed_local_energy(c2oh6_jb, group):
     """Mixed precision on walkers drawn from |Psi|^2 (20 oracle sweeps): per-walker E_L within 1e-5 of
     max(|E_L|, |mean E_L|) for nearly every walker, median 1e-6."""
     o = oracle.Oracle(c2oh6_jb)
@@ -136,18 +138,19 @@ def test_mixed_local_energy(c2oh6_jb):
     o.sample(st, 20)
     pos = st["pos"]
     ref = o.eval(pos, want=("EL",))["EL"]
-    got = gpu_eval(vmcf.System(c2oh6_jb, vmcf.MIXED), pos, ("EL",))["EL"]
+    got = gpu_eval(vmcf.System(c2oh6_jb, vmcf.MIXED, force_group=group), pos, ("EL",))["EL"]
     r = np.abs(got - ref) / np.maximum(np.abs(ref), abs(ref.mean()))
     assert np.median(r) < 1e-6
     assert np.mean(r < 1e-5) > 0.98, np.sort(r)[-8:]
 
 
-@pytest.mark.parametrize("precision", [vmcf.FP64, vmcf.MIXED])
-def test_batch_with_jastrow_basis_follows_the_single_path(water_jb, c2oh6_jb, precision):
-    """A ragged batch holding systems with and without the AO-expanded terms: same chains (bit for
-    bit) and walker sums (FP64 1e-12, mixed 1e-5) as each walker set sampled alone."""
+@pytest.mark.parametrize("precision,group", [(vmcf.FP64, True), (vmcf.MIXED, True), (vmcf.FP64, False),
+                                             (vmcf.MIXED, False)])
+def test_batch_with_jastrow_basis_follows_the_single_path(water_jb, c2oh6_jb, precision, group):
+    """A ragged batch holding systems with and without the AO-expanded terms, on either kernel family: same
+    chains (bit for bit) and walker sums (FP64 1e-12, mixed 1e-5) as each walker set sampled alone."""
     specs = [(water_jb, 48), (c2oh6_jb, 32), (S.make_system(0), 24)]
-    systems = [vmcf.System(sx, precision, force_group=True) for sx, _ in specs]
+    systems = [vmcf.System(sx, precision, force_group=group) for sx, _ in specs]
 
     def walkers():
         return [vmcf.Walkers(systems[g], S.initial_walkers(sx, W, seed=30 + g), key=(5222, 400 + g), nblocks=4)
