@@ -146,6 +146,19 @@ int vmcf_init_system(const vmcf_nuclei* nuclei, const vmcf_basis* basis, const d
 int vmcf_system_destroy(vmcf_system_t sys);
 /* Sizes of a system: number of nuclei, AOs, up and down electrons (any pointer may be NULL). */
 int vmcf_system_info(vmcf_system_t sys, int* K, int* M, int* n_up, int* n_dn);
+/* Replaces the nuclear positions R [K][3] (bohr) and the frozen orbital coefficients C_up [M][n_up], C_dn [M][n_dn]
+ * (row-major, host memory, copied) of an existing system, keeping its basis, charges, Jastrow factor, precision and
+ * kernel plans: the wavefunction of App. "Wavefunction Ansatz" at another geometry, e.g. for the forces of Eqs. hf,
+ * pulay along a trajectory or for derivatives with respect to R and C. S: the AO overlap at the new geometry
+ * ([M][M], host) for vmcf_reduce_estimators' rhs_BQ, or NULL (rhs_BQ is then refused until S is given again).
+ * Validated as at creation (VMCF_EINVAL before any CUDA call: non-finite values, two nuclei at one position,
+ * linearly dependent columns of C); the system is unchanged on error. The call synchronises the system's device and
+ * must not overlap kernels that use this system. Walker sets of the system keep their positions, but their inverses
+ * and accumulated sums belong to the old wavefunction: re-invert them (vmcf_walkers_set_positions) and reset their
+ * sums (vmcf_reset_accumulators) before sampling or reducing. Batches notice the change at their next
+ * vmcf_batch_sample. */
+int vmcf_system_set_geometry(vmcf_system_t sys, const double* R, const double* C_up, const double* C_dn,
+                             const double* S);
 
 /* Walker state for sampling: positions, Slater inverses, counters, accumulators. The walkers are
  * the set {x_i} of App. A ("Variational Monte Carlo Methods") that the Markov chain draws from

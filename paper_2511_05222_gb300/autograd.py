@@ -11,16 +11,35 @@ read as dE/dC): the derivative of the reweighted energy minus <dE_L/dC>, a term 
 expectation is zero.
 
 Every number comes out of libvmcf's kernels and its estimator finish; torch only carries the
-tensors.
+tensors. The library objects are kept between calls for the same template, precision, block count and
+walker count: each call moves the system to the given R and C (vmcf_system_set_geometry) and re-inverts
+the walker set at the given positions instead of building both again.
 """
 from __future__ import annotations
 
-import copy
+from collections import OrderedDict
 
 import numpy as np
 import torch
 
 from . import vmcf
+
+_STATE: "OrderedDict[tuple, tuple]" = OrderedDict()  # (id(template), precision, nblocks, W) -> (template, System, Walkers)
+_STATE_MAX = 4
+
+
+def _state(template, precision, nblocks, pos):
+    key = (id(template), precision, nblocks, int(pos.shape[0]))
+    ent = _STATE.get(key)
+    if ent is None or ent[0] is not template:
+        g = vmcf.System(template, precision)
+        ent = (template, g, vmcf.Walkers(g, pos, nblocks=nblocks))
+        _STATE[key] = ent
+        while len(_STATE) > _STATE_MAX:
+            _STATE.popitem(last=False)
+    else:
+        _STATE.move_to_end(key)
+    return ent[1], ent[2]
 
 
 class VMCForces(torch.autograd.Function):
@@ -29,12 +48,9 @@ class VMCForces(torch.autograd.Function):
         """R (K, 3), C_up (M, n_up), C_dn (M, n_dn): float64 tensors (any device).
         template: a systems.System giving the basis, charges and Jastrow.
         pos: (W, Ne, 3) float64 CUDA tensor of fixed walker positions."""
-        sysx = copy.copy(template)
-        sysx.R = np.ascontiguousarray(R.detach().cpu().numpy(), dtype=np.float64)
-        sysx.C_up = np.ascontiguousarray(C_up.detach().cpu().numpy(), dtype=np.float64)
-        sysx.C_dn = np.ascontiguousarray(C_dn.detach().cpu().numpy(), dtype=np.float64)
-        g = vmcf.System(sysx, precision)
-        wk = vmcf.Walkers(g, pos, nblocks=nblocks)
+        g, wk = _state(template, precision, nblocks, pos)
+        g.set_geometry(R.detach().cpu().numpy(), C_up.detach().cpu().numpy(), C_dn.detach().cpu().numpy())
+        wk.set_positions(pos)  # re-inverts at the new geometry
         wk.reset_accumulators(0.0)
         wk.measure()
         est = wk.reduce_estimators()

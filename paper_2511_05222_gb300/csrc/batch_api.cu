@@ -81,6 +81,7 @@ struct vmcf_batch_s {
   std::vector<cudaStream_t> sforks;
   std::vector<cudaEvent_t> sjoins;
   std::vector<double> s_eref, s_eps;
+  std::vector<int> geo_version;  // each system's geometry version when its descriptors were last filled
 };
 
 namespace {
@@ -461,6 +462,8 @@ int vmcf_batch_create(const vmcf_system_t* systems, const vmcf_walkers_t* walker
     for (int ph = 0; ph < 2; ++ph) b->cost[ph][g] = heuristic_cost(*systems[g], ph);
   }
   b->s_eref.assign(b->small_g.size(), 0.0);
+  b->geo_version.resize(G);
+  for (int g = 0; g < G; ++g) b->geo_version[g] = systems[g]->geometry_version;
   b->s_eps.assign(b->small_g.size(), 0.0);
   for (int ph = 0; ph < 2; ++ph) {
     b->bucket_shape[ph].resize(keys.size());
@@ -523,6 +526,12 @@ int vmcf_batch_sample(vmcf_batch_t b, int n_sweeps, double step_sigma, int refre
     }
   const int mode = measure ? 1 : 0;
   bool stale = false;  // a small-system geometry's launches were captured with another E_ref or threshold
+  for (int g = 0; g < b->G; ++g)
+    if (b->geo_version[g] != b->sys[g]->geometry_version) {  // vmcf_system_set_geometry since: new descriptors
+      fill_geo(*b, g);
+      b->geo_version[g] = b->sys[g]->geometry_version;
+      stale = true;
+    }
   for (size_t i = 0; i < b->small_g.size(); ++i)
     stale = stale || b->s_eref[i] != b->wk[b->small_g[i]]->e_ref || b->s_eps[i] != b->wk[b->small_g[i]]->eps;
   if (!b->exec || stale || b->g_mode != mode || b->g_kref != refresh_k || b->g_sigma != step_sigma) {

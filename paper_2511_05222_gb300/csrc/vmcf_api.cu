@@ -1042,6 +1042,79 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
   return VMCF_OK;
 }
 
+int vmcf_system_set_geometry(vmcf_system_t s, const double* R, const double* C_up, const double* C_dn,
+                              const double* S) {
+  if (!s || !R || !C_up) return fail(VMCF_EINVAL, "NULL input");
+  if (s->ndn > 0 && !C_dn) return fail(VMCF_EINVAL, "C_dn is NULL");
+  const int K = s->K, M = s->M, n_up = s->nup, n_dn = s->ndn;
+  if (!finite_all(R, 3 * (size_t)K)) return fail(VMCF_EINVAL, "nuclear positions not finite");
+  std::vector<double> C[2];
+  C[0].assign(C_up, C_up + (size_t)M * n_up);
+  if (n_dn > 0) C[1].assign(C_dn, C_dn + (size_t)M * n_dn);
+  if (!finite_all(C[0].data(), C[0].size()) || !finite_all(C[1].data(), C[1].size()))
+    return fail(VMCF_EINVAL, "C not finite");
+  for (int sg = 0; sg < 2; ++sg)
+    if (!independent_columns(C[sg], M, sg == 0 ? n_up : n_dn))
+      return fail(VMCF_EINVAL, std::string("the columns of C_") + (sg == 0 ? "up" : "dn") +
+                                   " are linearly dependent (every Slater matrix would be singular)");
+  // nuclear repulsion and its derivative, as at creation
+  double Vnn = 0.0;
+  std::vector<double> dVnn(3 * K, 0.0);
+  for (int I = 0; I < K; ++I)
+    for (int J = 0; J < K; ++J) {
+      if (I == J) continue;
+      double d[3], r2 = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        d[k] = R[3 * I + k] - R[3 * J + k];
+        r2 += d[k] * d[k];
+      }
+      if (!(r2 > 1e-12)) return fail(VMCF_EINVAL, "two nuclei at the same position");
+      const double r = std::sqrt(r2);
+      if (J > I) Vnn += s->Z[I] * s->Z[J] / r;
+      for (int k = 0; k < 3; ++k) dVnn[3 * I + k] -= s->Z[I] * s->Z[J] * d[k] / (r2 * r);
+    }
+  std::vector<float> Rh(3 * K), Rl(3 * K);
+  for (int i = 0; i < 3 * K; ++i) {
+    Rh[i] = (float)R[i];
+    Rl[i] = (float)(R[i] - (double)Rh[i]);
+  }
+  DevSys& D = s->dev;
+  cudaError_t e = cudaSetDevice(s->device);
+  auto up = [&](const void* dst, const void* src, size_t bytes) {
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice);
+  };
+  up(D.R, R, 8 * 3 * (size_t)K);
+  up(D.Rh, Rh.data(), 4 * Rh.size());
+  up(D.Rl, Rl.data(), 4 * Rl.size());
+  up(D.dVnn, dVnn.data(), 8 * dVnn.size());
+  for (int sg = 0; sg < 2; ++sg) {
+    const int n = sg == 0 ? n_up : n_dn;
+    if (n == 0) continue;
+    std::vector<float> Cf(C[sg].begin(), C[sg].end());
+    std::vector<double> CT((size_t)n * M);
+    std::vector<float> CfT((size_t)n * M);
+    for (int mu = 0; mu < M; ++mu)
+      for (int i = 0; i < n; ++i) {
+        CT[(size_t)i * M + mu] = C[sg][(size_t)mu * n + i];
+        CfT[(size_t)i * M + mu] = (float)C[sg][(size_t)mu * n + i];
+      }
+    up(D.C[sg], C[sg].data(), 8 * C[sg].size());
+    up(D.Cf[sg], Cf.data(), 4 * Cf.size());
+    up(D.CT[sg], CT.data(), 8 * CT.size());
+    up(D.CfT[sg], CfT.data(), 4 * CfT.size());
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "uploading the new geometry");
+  s->R.assign(R, R + 3 * (size_t)K);
+  s->C[0].swap(C[0]);
+  s->C[1].swap(C[1]);
+  D.Vnn = Vnn;
+  ++s->geometry_version;
+  s->has_S = S != nullptr;
+  if (S) s->S.assign(S, S + (size_t)M * M);
+  else s->S.clear();
+  return VMCF_OK;
+}
+
 int vmcf_system_destroy(vmcf_system_t s) {
   if (!s) return VMCF_OK;
   if (s->dmem) cudaFree(s->dmem);

@@ -11,7 +11,8 @@
 
 struct vmcf_system_s {
   int precision = 0;
-  int device = -1;      // the CUDA device the system's tables live on (current at vmcf_init_system)
+  int device = -1;
+  int geometry_version = 0;  // incremented by vmcf_system_set_geometry      // the CUDA device the system's tables live on (current at vmcf_init_system)
   int K = 0, M = 0, nup = 0, ndn = 0, Ne = 0, nshell = 0, nB = 0, nmax = 0;
   int MJ = 0, nJs = 0;  // functions and shells of the Jastrow basis (AO-expanded Jastrow terms)
   std::vector<double> R, Z, S, C[2];

@@ -86,6 +86,7 @@ def lib(build_if_missing: bool = True):
                                        ctypes.c_int, ctypes.POINTER(_Jastrow), _dp, ctypes.c_int, ctypes.POINTER(_vp)]
         L.vmcf_system_destroy.argtypes = [_vp]
         L.vmcf_system_info.argtypes = [_vp, _ip, _ip, _ip, _ip]
+        L.vmcf_system_set_geometry.argtypes = [_vp, _dp, _dp, _dp, _dp]
         L.vmcf_accumulator_length.argtypes = [_vp]
         L.vmcf_walkers_create.argtypes = [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
                                           ctypes.c_uint64, ctypes.c_int, _vp, ctypes.POINTER(_vp)]
@@ -192,6 +193,18 @@ class System:
 
     def set_tuning(self, key: str, value: int):
         _check(lib().vmcf_set_tuning(self.h, key.encode(), int(value)), "vmcf_set_tuning")
+
+    def set_geometry(self, R, C_up, C_dn, S=None):
+        """vmcf_system_set_geometry: new nuclear positions (K, 3) and orbital coefficients (M, n_up), (M, n_dn)
+        for this system (host arrays); walker sets must be re-inverted (Walkers.set_positions) afterwards."""
+        dp = lambda a: None if a is None else a.ctypes.data_as(_dp)
+        R, C_up, C_dn = _np(R, np.float64), _np(C_up, np.float64), _np(C_dn, np.float64)
+        S = None if S is None else _np(S, np.float64)
+        if R.shape != (self.K, 3) or C_up.shape != (self.M, self.n_up) or C_dn.size != self.M * self.n_dn:
+            raise ValueError("R must be (K, 3), C_up (M, n_up), C_dn (M, n_dn)")
+        if S is not None and S.shape != (self.M, self.M):
+            raise ValueError("S must be (M, M)")
+        _check(lib().vmcf_system_set_geometry(self.h, dp(R), dp(C_up), dp(C_dn), dp(S)), "vmcf_system_set_geometry")
 
     def close(self):
         if getattr(self, "h", None):
