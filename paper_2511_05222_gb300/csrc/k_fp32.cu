@@ -13,6 +13,10 @@ cudaError_t launch_refresh<float>(const DevSys& S, const Launch& lc, const doubl
   return launch_refresh_impl<float>(S, lc, pos, B, W, counters, st);
 }
 template <>
+cudaError_t launch_propose_group<float>(const DevSys& S, const GroupProposeParams& P, cudaStream_t st) {
+  return launch_propose_group_impl<float>(S, P, st);
+}
+template <>
 cudaError_t launch_move<float>(const DevSys& S, const Launch& lc, const MoveParams& P, cudaStream_t st) {
   return S.MJ > 0 ? launch_move_impl<float, true>(S, lc, P, st) : launch_move_impl<float, false>(S, lc, P, st);
 }

@@ -13,6 +13,10 @@ cudaError_t launch_refresh<double>(const DevSys& S, const Launch& lc, const doub
   return launch_refresh_impl<double>(S, lc, pos, B, W, counters, st);
 }
 template <>
+cudaError_t launch_propose_group<double>(const DevSys& S, const GroupProposeParams& P, cudaStream_t st) {
+  return launch_propose_group_impl<double>(S, P, st);
+}
+template <>
 cudaError_t launch_move<double>(const DevSys& S, const Launch& lc, const MoveParams& P, cudaStream_t st) {
   return S.MJ > 0 ? launch_move_impl<double, true>(S, lc, P, st) : launch_move_impl<double, false>(S, lc, P, st);
 }

@@ -89,6 +89,37 @@ __global__ void __launch_bounds__(256) refresh_kernel(DevSys S, GroupLayout L, c
 // ---------------------------------------------------------------- Metropolis sweeps
 // All sweeps of one walker (index w of P's arrays) by one group. c0: attempted moves since
 // the last refresh when the launch starts; sweep0: global sweep index of the first sweep.
+// Change of the electron-nucleus Jastrow terms when an electron moves from po to pn, summed over the nuclei by
+// one whole warp: lane l takes nuclei l, l + 32, ... in order, then an xor butterfly, so every lane holds the same
+// bits whichever kernel calls it (the sweep kernel or the proposal pass).
+template <typename T>
+__device__ __forceinline__ T en_change_warp(const DevSys& S, const EPos& pn, const EPos& po, int lane) {
+  T v = T(0);
+  if (S.J1) {
+    const T b = jas_b<T>(S);
+    for (int I = lane; I < S.K; I += 32) {
+      const T mz = -nuc_Z<T>(S, I);
+      T d1[3], d0[3];
+      disp_nuc<T>(S, pn, I, d1);
+      disp_nuc<T>(S, po, I, d0);
+      v += pade_value<T>(mz, b, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
+           pade_value<T>(mz, b, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// sum_{mu in [m0, m1)} ao[mu] C[mu][i], in order of mu: one half of an orbital-row entry (the entry is the sum of
+// the halves [0, M/2) and [M/2, M), in that order, in every kernel that forms it).
+template <typename T>
+__device__ __forceinline__ T orbital_half(const T* ao, const T* __restrict__ C, int n, int i, int m0, int m1) {
+  T v = T(0);
+  for (int mu = m0; mu < m1; ++mu) v += ao[mu] * __ldg(C + mu * n + i);
+  return v;
+}
+
 // JB: the system has AO-expanded Jastrow terms; without them the terms' code is compiled out.
 template <typename T, int GS, bool JB>
 __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MoveParams& P, unsigned char* base, int w,
@@ -136,15 +167,24 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
       const int n = sg == 0 ? nup : S.ndn, el = e - (sg == 0 ? 0 : nup);
       T* Bs = B + (sg == 0 ? 0 : nup * nup);
       const T* C = coefC<T>(S, sg);
-      uint64_t r[4] = {wid, sweep, (uint64_t)e, 0};
-      philox4x64_10(r, P.k0, P.k1);
-      double xi[3];
-      normals3(r, xi, T(0));
-      const double rn[3] = {pos[3 * e] + P.sigma * xi[0], pos[3 * e + 1] + P.sigma * xi[1],
-                            pos[3 * e + 2] + P.sigma * xi[2]};
+      // the proposal: from the proposal pass when given, else drawn here (the same arithmetic)
+      const bool pre = P.prn != nullptr;
+      const size_t pidx = (size_t)w * Ne + e;
+      double rn[3];
+      if (pre) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) rn[k] = __ldg(P.prn + 3 * pidx + k);
+      } else {
+        uint64_t r[4] = {wid, sweep, (uint64_t)e, 0};
+        philox4x64_10(r, P.k0, P.k1);
+        double xi[3];
+        normals3(r, xi, T(0));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) rn[k] = pos[3 * e + k] + P.sigma * xi[k];
+      }
       const EPos pn = make_epos(rn);
       const EPos po = make_epos(pos + 3 * e);
-      ao_point<T, GS, 0, false>(S, pn, ao, 0);
+      if (!pre) ao_point<T, GS, 0, false>(S, pn, ao, 0);
       for (int sh = t; sh < (JB ? S.nJs : 0); sh += GS) {
         jas_shell<T, 0>(S, sh, pn, [&](int mu, const T* v) { jpn[mu] = v[0]; });
         jas_shell<T, 0>(S, sh, po, [&](int mu, const T* v) { jpo[mu] = v[0]; });
@@ -152,36 +192,45 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
       gsync<GS>();
       double part[1] = {0.0};  // determinant ratio (FP64)
       T dJ = T(0);              // Jastrow exponent difference
-      // new orbital row phi_i(r'): with GS >= 2n the mu sum is split in kp parts (partial
-      // sums of parts 1 and 2 go through wv and col) so that kp n threads share it
-      const int kp = GS >= 3 * n ? 3 : (GS >= 2 * n ? 2 : 1);
-      if (kp == 1) {
+      // new orbital row phi_i(r'), each entry the sum of its halves over [0, M/2) and [M/2, M); with GS >= 2n
+      // the halves go to different threads (the second through wv)
+      const int mh = S.M / 2;
+      if (pre) {
+        const T* pr = reinterpret_cast<const T*>(P.prow) + pidx * S.nmax;
         for (int i = t; i < n; i += GS) {
-          T v = 0;
-          for (int mu = 0; mu < S.M; ++mu) v += ao[mu] * __ldg(C + mu * n + i);
+          const T v = __ldg(pr + i);
+          row[i] = v;
+          part[0] += (double)v * (double)Bs[i * n + el];
+        }
+      } else if (GS < 2 * n) {
+        for (int i = t; i < n; i += GS) {
+          const T v = orbital_half<T>(ao, C, n, i, 0, mh) + orbital_half<T>(ao, C, n, i, mh, S.M);
           row[i] = v;
           part[0] += (double)v * (double)Bs[i * n + el];
         }
       } else {
         T v = 0;
         const int i = t % n, pp = t / n;
-        if (pp < kp) {
-          const int m0 = S.M * pp / kp, m1 = S.M * (pp + 1) / kp;
-          for (int mu = m0; mu < m1; ++mu) v += ao[mu] * __ldg(C + mu * n + i);
+        if (pp < 2) {
+          v = orbital_half<T>(ao, C, n, i, pp == 0 ? 0 : mh, pp == 0 ? mh : S.M);
           if (pp == 1) wv[i] = v;
-          if (pp == 2) col[i] = v;
         }
         gsync<GS>();
         if (pp == 0) {
-          v += wv[i];
-          if (kp == 3) v += col[i];
+          v = v + wv[i];
           row[i] = v;
           part[0] += (double)v * (double)Bs[i * n + el];
         }
       }
-      // Jastrow ratio: pairs with every other electron, and the e-n terms
-      for (int q = t; q < Ne + K; q += GS) {
-        if (q < Ne) {
+      // the electron-nucleus change: from the proposal pass, else from the group's first warp (into f[0], which
+      // is free between re-inversions)
+      if (!pre && t < 32) {
+        const T en = en_change_warp<T>(S, pn, po, t);
+        if (t == 0) f[0] = (double)en;
+      }
+      // Jastrow ratio: pairs with every other electron
+      for (int q = t; q < Ne; q += GS) {
+        {
           if (q == e || !S.J2) continue;
           const bool par = (q < nup) == (e < nup);
 
@@ -198,15 +247,6 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
           }
           dJ += pair_value<T>(S, par, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
                 pair_value<T>(S, par, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]));
-        } else {
-          if (!S.J1) continue;
-          const int I = q - Ne;
-          const T mz = -nuc_Z<T>(S, I), b = jas_b<T>(S);
-          T d1[3], d0[3];
-          disp_nuc<T>(S, pn, I, d1);
-          disp_nuc<T>(S, po, I, d0);
-          dJ += pade_value<T>(mz, b, dsqrt<T>(d1[0] * d1[0] + d1[1] * d1[1] + d1[2] * d1[2])) -
-                pade_value<T>(mz, b, dsqrt<T>(d0[0] * d0[0] + d0[1] * d0[1] + d0[2] * d0[2]));
         }
       }
       if (MJ) {  // AO-expanded terms: dphi . t0 - psi^J(r_e) . (Xi dphi), dphi = psi^J(r') - psi^J(r_e)
@@ -220,10 +260,16 @@ __device__ void move_walker(const DevSys& S, const GroupLayout& L, const MovePar
       }
       gsync<GS>();
       group_sum_dt<GS>(part[0], dJ, red);
+      dJ += pre ? __ldg(reinterpret_cast<const T*>(P.pdchi) + pidx) : (T)f[0];
       const double R = part[0];
-      uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
-      philox4x64_10(r2, P.k0, P.k1);
-      const double u = u01(r2[0]);
+      double u;
+      if (pre) {
+        u = __ldg(P.pu + pidx);
+      } else {
+        uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
+        philox4x64_10(r2, P.k0, P.k1);
+        u = u01(r2[0]);
+      }
       double pr = R * R * (double)dexp<T>(T(2) * dJ);
       double Sn = Sg;
       if (guide && R != 0.0) {
@@ -1038,6 +1084,69 @@ __global__ void __launch_bounds__(256, 2) measure_kernel(DevSys S, GroupLayout L
   }
 }
 
+// ---------------------------------------------------------------- proposals of a walker-group sweep
+// Every electron moves once per sweep, from its position at the start of the sweep, so its proposal r'_e (Philox
+// counter (wid, sweep, e, 0)), its acceptance uniform (counter (wid, sweep, e, 1)), the orbital row of its spin at
+// r'_e and the change of the electron-nucleus Jastrow terms do not depend on the sweep's earlier moves and are
+// formed here for every (walker, electron) at once (App. A, MCMC): one warp per pair, the AO values at r'_e in the
+// warp's shared buffer. The arithmetic is that of move_walker's own path (orbital_half, en_change_warp), so the
+// chain is the same bit for bit either way.
+template <typename T>
+__global__ void __launch_bounds__(256) propose_group(DevSys S, GroupProposeParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  T* ao = reinterpret_cast<T*>(smem) + (size_t)warp * ((S.M + 3) / 4 * 4);
+  const int Ne = S.Ne, nup = S.nup, mh = S.M / 2;
+  const long long nitem = (long long)P.W * Ne;
+  for (long long it = (long long)blockIdx.x * nwarps + warp; it < nitem; it += (long long)gridDim.x * nwarps) {
+    const int w = (int)(it / Ne), e = (int)(it - (long long)w * Ne);
+    const uint64_t wid = P.wid0 + (uint64_t)w;
+    uint64_t r[4] = {wid, P.sweep, (uint64_t)e, 0};
+    philox4x64_10(r, P.k0, P.k1);
+    double xi[3];
+    normals3(r, xi, T(0));
+    double po3[3], rn[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      po3[k] = P.pos[(size_t)it * 3 + k];
+      rn[k] = po3[k] + P.sigma * xi[k];
+    }
+    const EPos pn = make_epos(rn);
+    const EPos po = make_epos(po3);
+    ao_point<T, 32, 0, false>(S, pn, ao, 0);
+    __syncwarp();
+    const int sg = e < nup ? 0 : 1, n = sg == 0 ? nup : S.ndn;
+    const T* C = coefC<T>(S, sg);
+    T* prow = reinterpret_cast<T*>(P.prow) + (size_t)it * S.nmax;
+    for (int i = lane; i < n; i += 32)
+      prow[i] = orbital_half<T>(ao, C, n, i, 0, mh) + orbital_half<T>(ao, C, n, i, mh, S.M);
+    const T en = en_change_warp<T>(S, pn, po, lane);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) P.prn[(size_t)it * 3 + k] = rn[k];
+      reinterpret_cast<T*>(P.pdchi)[it] = en;
+      uint64_t r2[4] = {wid, P.sweep, (uint64_t)e, 1};
+      philox4x64_10(r2, P.k0, P.k1);
+      P.pu[it] = u01(r2[0]);
+    }
+    __syncwarp();  // the AO buffer is reused for the warp's next pair
+  }
+}
+
+template <typename T>
+size_t propose_group_smem(const DevSys& S) {
+  return (size_t)8 * ((S.M + 3) / 4 * 4) * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_propose_group_impl(const DevSys& S, const GroupProposeParams& P, cudaStream_t st) {
+  const long long items = (long long)P.W * S.Ne;
+  if (items == 0) return cudaSuccess;
+  const int grid = (int)std::min<long long>((items + 7) / 8, 8192);
+  propose_group<T><<<grid, 256, propose_group_smem<T>(S), st>>>(S, P);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- launchers
 // Instances with the AO-expanded Jastrow terms (JB = true) live in their own translation units.
 template <typename T, bool JB>
@@ -1048,6 +1157,7 @@ cudaError_t set_smem_limits_impl() {
     if ((e = cudaFuncSetAttribute(refresh_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(refresh_kernel<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(refresh_kernel<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(propose_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   }
   if ((e = cudaFuncSetAttribute(move_kernel<T, 32, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
   if ((e = cudaFuncSetAttribute(move_kernel<T, 128, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;

@@ -1135,6 +1135,23 @@ int vmcf_accumulator_length(vmcf_system_t s) { return s ? s->accL : VMCF_EINVAL;
 
 // One sweep's proposals of every walker (small-system path): orbital rows, proposed positions,
 // acceptance uniforms and electron-nucleus Jastrow changes, in one allocation.
+// Proposals of one walker-group sweep: r' [W][Ne][3], the orbital rows [W][Ne][nmax], the uniforms and the
+// electron-nucleus Jastrow changes [W][Ne].
+static cudaError_t alloc_group_proposals(const vmcf_system_s* s, vmcf_walkers_s* wk) {
+  const size_t tsz = s->precision == VMCF_FP64 ? 8 : 4, n = (size_t)wk->W * s->Ne;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t o_rn = 0, o_row = o_rn + al(24 * n), o_u = o_row + al(tsz * n * s->nmax), o_dchi = o_u + al(8 * n),
+               bytes = o_dchi + al(tsz * n);
+  cudaError_t e = cudaMalloc(&wk->gprop, bytes);
+  if (e != cudaSuccess) return e;
+  char* b = static_cast<char*>(wk->gprop);
+  wk->g_rn = reinterpret_cast<double*>(b + o_rn);
+  wk->g_row = b + o_row;
+  wk->g_u = reinterpret_cast<double*>(b + o_u);
+  wk->g_dchi = b + o_dchi;
+  return cudaSuccess;
+}
+
 static cudaError_t alloc_proposals(const vmcf_system_s* s, vmcf_walkers_s* wk) {
   const size_t tsz = s->precision == VMCF_FP64 ? 8 : 4, n = (size_t)wk->W * s->Ne;
   const int nms = (s->small_nm + 3) / 4 * 4;
@@ -1202,6 +1219,7 @@ int vmcf_walkers_create(vmcf_system_t s, int W, const double* pos, int is_host, 
       (s->small && (e = cudaMalloc(&wk->stage, 8 * npos))) ||
       (s->small && s->precision == VMCF_MIXED && (e = cudaMalloc(&wk->posf, sizeof(float2) * npos))) ||
       (s->small && (e = alloc_proposals(s, wk))) ||
+      (!s->small && (e = alloc_group_proposals(s, wk))) ||
       (((s->small && s->tc_sums) || (!s->small && s->tcg_sums)) && (e = alloc_tc(s, wk)))) {
     vmcf_walkers_destroy(wk);
     return fail(VMCF_ENOMEM, std::string("walker state allocation: ") + cudaGetErrorString(e));
@@ -1243,6 +1261,7 @@ int vmcf_walkers_destroy(vmcf_walkers_t wk) {
   cudaFree(wk->stage);
   cudaFree(wk->posf);
   cudaFree(wk->prop);
+  cudaFree(wk->gprop);
   for (int k = 0; k < 2; ++k) {
     cudaFree(wk->phiT[k]);
     cudaFree(wk->yT[k]);
@@ -1401,15 +1420,48 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
   const Launch lm = launch_rm(*s, wk->W);
   const bool fp64 = s->precision == VMCF_FP64;
   auto move = [&](int nsw, int skip) -> int {
-    P.sweep0 = wk->sweep;
-    P.nsweeps = nsw;
-    P.c0 = wk->counter;
-    P.skip_final_refresh = skip;
-    Timed tm(wk, 0, st);
-    cudaError_t e = fp64 ? launch_move<double>(s->dev, lm, P, st) : launch_move<float>(s->dev, lm, P, st);
-    if (e != cudaSuccess) return cuda_fail(e, "move kernel launch");
-    wk->sweep += nsw;
-    wk->counter = (int)((wk->counter + (long long)nsw * s->Ne) % refresh_k);
+    if (!s->group_prepass || !wk->gprop) {  // every sweep's proposals drawn inside the move kernel
+      P.sweep0 = wk->sweep;
+      P.nsweeps = nsw;
+      P.c0 = wk->counter;
+      P.skip_final_refresh = skip;
+      Timed tm(wk, 0, st);
+      cudaError_t e = fp64 ? launch_move<double>(s->dev, lm, P, st) : launch_move<float>(s->dev, lm, P, st);
+      if (e != cudaSuccess) return cuda_fail(e, "move kernel launch");
+      wk->sweep += nsw;
+      wk->counter = (int)((wk->counter + (long long)nsw * s->Ne) % refresh_k);
+      return VMCF_OK;
+    }
+    // one sweep per launch, its proposals formed ahead for every (walker, electron) by propose_group
+    GroupProposeParams Q{};
+    Q.pos = wk->pos;
+    Q.prn = wk->g_rn;
+    Q.prow = wk->g_row;
+    Q.pu = wk->g_u;
+    Q.pdchi = wk->g_dchi;
+    Q.W = wk->W;
+    Q.wid0 = wk->wid0;
+    Q.k0 = wk->k0;
+    Q.k1 = wk->k1;
+    Q.sigma = step_sigma;
+    MoveParams Pp = P;
+    Pp.prn = wk->g_rn;
+    Pp.prow = wk->g_row;
+    Pp.pu = wk->g_u;
+    Pp.pdchi = wk->g_dchi;
+    for (int k = 0; k < nsw; ++k) {
+      Q.sweep = wk->sweep;
+      Pp.sweep0 = wk->sweep;
+      Pp.nsweeps = 1;
+      Pp.c0 = wk->counter;
+      Pp.skip_final_refresh = k == nsw - 1 ? skip : 0;
+      Timed tm(wk, 0, st);
+      cudaError_t e = fp64 ? launch_propose_group<double>(s->dev, Q, st) : launch_propose_group<float>(s->dev, Q, st);
+      if (e == cudaSuccess) e = fp64 ? launch_move<double>(s->dev, lm, Pp, st) : launch_move<float>(s->dev, lm, Pp, st);
+      if (e != cudaSuccess) return cuda_fail(e, "proposal or move kernel launch");
+      wk->sweep += 1;
+      wk->counter = (int)((wk->counter + (long long)s->Ne) % refresh_k);
+    }
     return VMCF_OK;
   };
   if (!measure) {
@@ -1721,6 +1773,10 @@ int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double
 int vmcf_set_tuning(vmcf_system_t s, const char* key, int value) {
   if (!s || !key) return fail(VMCF_EINVAL, "bad arguments");
   const std::string k(key);
+  if (k == "group_proposal_pass") {  // walker-group sweeps: proposals formed ahead (1) or in the move kernel (0)
+    s->group_prepass = value != 0;
+    return VMCF_OK;
+  }
   if (k == "move_lanes_per_walker") {
     if (value != 1 && value != 2 && value != 4 && value != 8) return fail(VMCF_EINVAL, "lanes per walker: 1, 2, 4 or 8");
     s->move_lpw = value;

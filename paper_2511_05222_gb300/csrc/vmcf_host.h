@@ -40,6 +40,7 @@ struct vmcf_system_s {
   size_t small_move_smem = 0;  // shared memory of the proposal kernel (C staging, Jastrow-basis rows)
   int propose_warps = 8;       // warps per CTA of the proposal kernel
   int move_lpw = 2;            // lanes per walker in the move kernel (1, 2, 4 or 8)
+  bool group_prepass = true;   // walker-group sweeps take their proposals from propose_group
   bool tc_sums = false;        // mixed small path: walker sums of O on the tensor cores
   int tc_Mp = 0, tc_Np = 0;    // padded AO rows and Y columns of those tiles
   int tc_nch = 1;              // chunks of 16 electron slots per walker
@@ -77,6 +78,12 @@ struct vmcf_walkers_s {
   double* stage = nullptr;  // [W][Ne][3] staging for layout conversion
   void* prop = nullptr;     // small-system path: one sweep's proposals (see pr)
   vmcf::SmallProposals pr{};
+  // walker-group path: one sweep's proposals from propose_group ([W][Ne][3] r', [W][Ne][nmax] rows, [W][Ne] u, dchi)
+  void* gprop = nullptr;
+  double* g_rn = nullptr;
+  void* g_row = nullptr;
+  double* g_u = nullptr;
+  void* g_dchi = nullptr;
   // per-kernel timing (kind 0 move, 1 measure, 2 refresh): event pairs around launches
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;

@@ -40,6 +40,24 @@ struct MoveParams {
   int nsweeps, kref, c0, skip_final_refresh;
   double sigma;
   double eps;       // guiding function max(1, eps sqrt(S)) of reweighted sampling; 0: plain |Psi|^2
+  // the proposals of this launch's sweep (nsweeps = 1) from propose_group, or NULL: computed in the kernel,
+  // with the same arithmetic. Electron e of walker w at index w Ne + e.
+  const double* prn;  // [W][Ne][3] r'_e
+  const void* prow;   // T [W][Ne][nmax]: orbital row of the electron's spin at r'_e
+  const double* pu;   // [W][Ne] acceptance uniform
+  const void* pdchi;  // T [W][Ne] change of the electron-nucleus Jastrow terms
+};
+
+// The proposals of one sweep for every (walker, electron), computed ahead of the walker-group moves.
+struct GroupProposeParams {
+  const double* pos;  // [W][Ne][3] positions at the start of the sweep
+  double* prn;
+  void* prow;
+  double* pu;
+  void* pdchi;
+  int W;
+  uint64_t wid0, k0, k1, sweep;
+  double sigma;
 };
 
 struct MeasParams {
@@ -69,6 +87,8 @@ template <typename T>
 cudaError_t launch_measure(const DevSys& S, const Launch& lc, const MeasParams& P, cudaStream_t st);
 template <typename T>
 cudaError_t set_smem_limits(int GS);
+template <typename T>
+cudaError_t launch_propose_group(const DevSys& S, const GroupProposeParams& P, cudaStream_t st);
 
 // ---- small-system path (kernels_small.cuh)
 struct BatchClock;

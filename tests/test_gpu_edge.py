@@ -3,7 +3,8 @@
 and 16 orbitals per spin: every lane holds an electron and the register rows are full), an
 open-shell system (n_up = n_dn + 1) in both kernel families, a run of zero sweeps, a walker count
 that fills no CTA, warp or jackknife block evenly, and a re-inversion interval k lowered between
-calls below the moves already made since the last re-inversion (single path and batch)."""
+calls below the moves already made since the last re-inversion (single path and batch), and walker-group
+sweeps with and without the proposal pass (the same chains)."""
 import numpy as np
 import pytest
 
@@ -172,3 +173,26 @@ def test_batch_lowering_k_between_calls_follows_the_single_path(sys0):
         w.sample(2, 0.3, 7)
     for g in range(2):
         np.testing.assert_array_equal(wa[g].positions(), wb[g].positions())
+
+
+@pytest.mark.parametrize("cfg,precision", [(0, vmcf.FP64), (0, vmcf.MIXED), (4, vmcf.MIXED)])
+def test_group_proposal_pass_changes_no_chain(cfg, precision):
+    """Walker-group sweeps with their proposals formed ahead by the proposal pass (the default) and drawn inside
+    the move kernel: the same chains bit for bit (the same draws, orbital rows and Jastrow changes), across
+    re-inversions inside a sweep (k = 7) and measured sweeps, and the same walker sums to rounding."""
+    sx = S.make_system(cfg)
+    W = 48 if cfg == 0 else 8
+    pos = S.initial_walkers(sx, W, seed=31)
+    runs = []
+    for prepass in (1, 0):
+        g = vmcf.System(sx, precision, force_group=True)
+        g.set_tuning("group_proposal_pass", prepass)
+        wk = vmcf.Walkers(g, pos, key=(5222, 77), nblocks=4)
+        wk.sample(2, 0.3, 7, measure=False)
+        wk.reset_accumulators(-100.0)
+        wk.sample(2, 0.3, 7, measure=True)
+        runs.append((wk.positions(), wk.block_sums(), wk.counters()))
+    (pa, sa, ca), (pb, sb, cb) = runs
+    np.testing.assert_array_equal(pa, pb)
+    assert ca["accepted"] == cb["accepted"] and ca["refreshes"] == cb["refreshes"]
+    assert rel(sa, sb) < (1e-12 if precision == vmcf.FP64 else 1e-5)
