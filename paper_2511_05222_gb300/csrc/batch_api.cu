@@ -189,6 +189,12 @@ void fill_geo(vmcf_batch_s& b, int g) {
   }
   G.Mp.eps = w.eps;
   G.P.eps = w.eps;
+  if (b.bucket[g] >= 0 && s.group_prepass && w.gprop) {  // the sweep's proposals come from propose_group
+    G.P.prn = w.g_rn;
+    G.P.prow = w.g_row;
+    G.P.pu = w.g_u;
+    G.P.pdchi = w.g_dchi;
+  }
   G.Mp.accL = s.accL;
   G.Mp.acc_in_smem = 0;
   G.Mp.e_ref = w.e_ref;
@@ -315,6 +321,31 @@ cudaError_t launch_k(const vmcf_batch_s& b, int k, int mode, int kref, double si
 
 // One sweep of the batch as a graph: per phase (the evaluation only when measuring), fork
 // one branch per persistent kernel and join; then advance the clocks and rewind the queues.
+// The proposals of the coming sweep for every walker-group geometry with take[g] (all when take is empty) whose
+// descriptor reads them, each geometry's sweep index from its device clock.
+cudaError_t launch_batch_proposals(const vmcf_batch_s& b, const std::vector<char>& take, double sigma, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int g = 0; g < b.G && e == cudaSuccess; ++g) {
+    if (b.bucket[g] < 0 || !b.h_geo[g].P.prn || !(take.empty() || take[g])) continue;
+    const vmcf_system_s& s = *b.sys[g];
+    const vmcf_walkers_s& w = *b.wk[g];
+    GroupProposeParams Q{};
+    Q.pos = w.pos;
+    Q.prn = w.g_rn;
+    Q.prow = w.g_row;
+    Q.pu = w.g_u;
+    Q.pdchi = w.g_dchi;
+    Q.W = w.W;
+    Q.wid0 = w.wid0;
+    Q.k0 = w.k0;
+    Q.k1 = w.k1;
+    Q.sigma = sigma;
+    Q.clk = b.d_clk + g;
+    e = s.precision == VMCF_FP64 ? launch_propose_group<double>(s.dev, Q, st) : launch_propose_group<float>(s.dev, Q, st);
+  }
+  return e;
+}
+
 int capture(vmcf_batch_s& b, int mode, int kref, double sigma) {
   invalidate_graph(b);
   BATCH_CUDA(cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal));
@@ -330,6 +361,8 @@ int capture(vmcf_batch_s& b, int mode, int kref, double sigma) {
     b.s_eref[i] = b.wk[g]->e_ref;
     b.s_eps[i] = b.wk[g]->eps;
   }
+  // the walker-group geometries' proposals, ahead of the sweep phase
+  if (e == cudaSuccess) e = launch_batch_proposals(b, {}, sigma, b.cap);
   for (int phase = 0; phase < 2 && e == cudaSuccess; ++phase) {
     if (phase == 1 && mode == 0) break;
     e = cudaEventRecord(b.fork_ev, b.cap);
@@ -574,7 +607,8 @@ int vmcf_batch_autotune(vmcf_batch_t b, double step_sigma, int refresh_k, void* 
         rc = upload_state(*b, st);
         if (rc != VMCF_OK) break;
         const int mode = phase == 0 ? 0 : 2;
-        cudaError_t e = cudaEventRecord(t0, st);
+        cudaError_t e = phase == 0 ? launch_batch_proposals(*b, take, step_sigma, st) : cudaSuccess;
+        if (e == cudaSuccess) e = cudaEventRecord(t0, st);
         if (e == cudaSuccess) e = launch_k(*b, 0, mode, refresh_k, step_sigma, st);
         if (e == cudaSuccess) e = cudaEventRecord(t1, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);

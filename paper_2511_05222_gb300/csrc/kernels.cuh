@@ -1100,8 +1100,8 @@ __global__ void __launch_bounds__(256) propose_group(DevSys S, GroupProposeParam
   const long long nitem = (long long)P.W * Ne;
   for (long long it = (long long)blockIdx.x * nwarps + warp; it < nitem; it += (long long)gridDim.x * nwarps) {
     const int w = (int)(it / Ne), e = (int)(it - (long long)w * Ne);
-    const uint64_t wid = P.wid0 + (uint64_t)w;
-    uint64_t r[4] = {wid, P.sweep, (uint64_t)e, 0};
+    const uint64_t wid = P.wid0 + (uint64_t)w, sweep = P.clk ? P.clk->sweep : P.sweep;
+    uint64_t r[4] = {wid, sweep, (uint64_t)e, 0};
     philox4x64_10(r, P.k0, P.k1);
     double xi[3];
     normals3(r, xi, T(0));
@@ -1125,7 +1125,7 @@ __global__ void __launch_bounds__(256) propose_group(DevSys S, GroupProposeParam
 #pragma unroll
       for (int k = 0; k < 3; ++k) P.prn[(size_t)it * 3 + k] = rn[k];
       reinterpret_cast<T*>(P.pdchi)[it] = en;
-      uint64_t r2[4] = {wid, P.sweep, (uint64_t)e, 1};
+      uint64_t r2[4] = {wid, sweep, (uint64_t)e, 1};
       philox4x64_10(r2, P.k0, P.k1);
       P.pu[it] = u01(r2[0]);
     }

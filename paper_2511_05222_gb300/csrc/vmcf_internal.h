@@ -8,6 +8,8 @@
 
 namespace vmcf {
 
+struct BatchClock;  // per-geometry chain clock of a ragged batch (below)
+
 // Byte offsets of one walker group's shared-memory region; computed on the host.
 struct GroupLayout {
   int pos, ph, pl, Bd, Bt, P, Q, Jg, Jl, gd, ao, frc, fa, ew, Ow, D, piv, f, red, scal, row, wv, col;
@@ -58,6 +60,7 @@ struct GroupProposeParams {
   int W;
   uint64_t wid0, k0, k1, sweep;
   double sigma;
+  const BatchClock* clk;  // in a batch graph: the sweep index comes from the geometry's device clock
 };
 
 struct MeasParams {
@@ -77,6 +80,7 @@ struct MeasParams {
   int W;
 };
 
+
 // Launchers (one instantiation per precision and group size, see k_fp64.cu / k_fp32.cu).
 template <typename T>
 cudaError_t launch_refresh(const DevSys& S, const Launch& lc, const double* pos, void* B, int W,
@@ -91,7 +95,6 @@ template <typename T>
 cudaError_t launch_propose_group(const DevSys& S, const GroupProposeParams& P, cudaStream_t st);
 
 // ---- small-system path (kernels_small.cuh)
-struct BatchClock;
 
 // The proposals of one sweep for every walker and electron (filled by propose_small before the
 // sweep's moves): electron e of walker w at index w * Ne + e.
