@@ -371,7 +371,10 @@ def main():
                     help="skip the C9O4H8 (94 e-, 65536 walkers) block of the default line")
     ap.add_argument("--jastrow-basis", action="store_true",
                     help="add the AO-expanded Jastrow terms (seeded medium Jastrow basis) to the workload")
+    ap.add_argument("--tuning", action="append", default=[], metavar="KEY=VALUE",
+                    help="vmcf_set_tuning on the measured system, e.g. tensor_core_rows=0 (repeatable)")
     args = ap.parse_args()
+    tunings = [(kv.split("=")[0], int(kv.split("=")[1])) for kv in args.tuning]
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, wl)
@@ -438,6 +441,8 @@ def main():
         (equilibrated) configurations."""
         pos0 = S.initial_walkers(sysx, W, seed=seed)
         g = vmcf.System(sysx, prec, force_group=group)
+        for k, v in tunings:
+            g.set_tuning(k, v)
         wk = vmcf.Walkers(g, pos0, key=(5222, 1), wid0=rank * W, nblocks=nb, stream=stream)
         wk.sample(args.equil, 0.3, 26, measure=False, stream=stream)
         wk.reset_accumulators(0.0, stream=stream)
@@ -456,8 +461,10 @@ def main():
         est = wk.reduce_estimators(stream=stream)
         work = workmodel.per_walker_eval(sysx.K, g.M, sysx.n_up, sysx.n_dn, int(sysx.shell_nprim.sum()), acc,
                                          jb.MJ if jb else 0, int(jb.shell_nprim.sum()) if jb else 0)
-        dom = max(("move", "measure"), key=lambda k: kt[k]["ms"])
-        t_launch = kt[dom]["ms"] / max(1, kt[dom]["launches"]) * 1e-3
+        # the work model's "move" covers a sweep's proposals and moves together
+        ktw = dict(kt, move={"ms": kt["move"]["ms"] + kt["propose"]["ms"], "launches": kt["move"]["launches"]})
+        dom = max(("move", "measure"), key=lambda k: ktw[k]["ms"])
+        t_launch = ktw[dom]["ms"] / max(1, ktw[dom]["launches"]) * 1e-3
         bound, _ = workmodel.roofline_time(work[dom], peaks)
         pipe_flops = {"fp32": work[dom]["fp32"], "fp64": work[dom]["fp64"], "sfu": work[dom]["exp"]}[bound]
         peak = {"fp32": peaks["fp32_tflops"], "fp64": peaks["fp64_tflops"], "sfu": peaks["exp_gops"] / 1e3}[bound]

@@ -20,7 +20,7 @@ LIB = OUT_DIR / "libvmcf.so"
 UNITS = ["vmcf_api.cu", "k_fp64.cu", "k_fp32.cu", "k_fp64_jb.cu", "k_fp32_jb.cu", "k_small_fp64.cu", "k_small_fp32.cu",
          "k_small_fp64_jb.cu", "k_small_fp32_jb.cu",
          "k_reduce.cu", "k_probe.cu", "noalloc.cu", "k_tc_sumprod.cu", "k_batch.cu", "k_batch_fp64.cu", "k_batch_jb.cu",
-         "k_batch_fp64_jb.cu", "batch_api.cu", "checkpoint.cu"]
+         "k_batch_fp64_jb.cu", "batch_api.cu", "checkpoint.cu", "k_tc_rows.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -341,7 +341,7 @@ cudaError_t launch_batch_proposals(const vmcf_batch_s& b, const std::vector<char
     Q.k1 = w.k1;
     Q.sigma = sigma;
     Q.clk = b.d_clk + g;
-    e = s.precision == VMCF_FP64 ? launch_propose_group<double>(s.dev, Q, st) : launch_propose_group<float>(s.dev, Q, st);
+    e = launch_propose_rows(s, Q, st);
   }
   return e;
 }

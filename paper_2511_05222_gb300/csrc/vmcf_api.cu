@@ -1038,6 +1038,13 @@ int vmcf_init_system(const vmcf_nuclei* nuc, const vmcf_basis* bas, const double
     D.jXr_f = reinterpret_cast<const float*>(b + oJXrf);
   }
   s->scratch_counters = reinterpret_cast<double*>(b + oCnt);
+  const int trc = tc_rows_setup(s);
+  if (trc != VMCF_OK) {
+    cudaFree(s->tcr_mem);
+    cudaFree(s->dmem);
+    delete s;
+    return trc;
+  }
   *out = s;
   return VMCF_OK;
 }
@@ -1108,6 +1115,8 @@ int vmcf_system_set_geometry(vmcf_system_t s, const double* R, const double* C_u
   s->C[0].swap(C[0]);
   s->C[1].swap(C[1]);
   D.Vnn = Vnn;
+  const int trc = tc_rows_upload(s);  // the tensor-core proposal pass's split coefficients
+  if (trc != VMCF_OK) return trc;
   ++s->geometry_version;
   s->has_S = S != nullptr;
   if (S) s->S.assign(S, S + (size_t)M * M);
@@ -1118,6 +1127,7 @@ int vmcf_system_set_geometry(vmcf_system_t s, const double* R, const double* C_u
 int vmcf_system_destroy(vmcf_system_t s) {
   if (!s) return VMCF_OK;
   if (s->dmem) cudaFree(s->dmem);
+  if (s->tcr_mem) cudaFree(s->tcr_mem);
   delete s;
   return VMCF_OK;
 }
@@ -1365,7 +1375,7 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
     const int qgrid = std::max(1, std::min((wk->W + s->propose_warps - 1) / s->propose_warps, 8 * s->small_sms));
     for (int sw = 0; sw < n_sweeps; ++sw) {
       {  // the sweep's proposals, from the positions at its start
-        Timed tm(wk, 0, st);
+        Timed tm(wk, 4, st);
         Q.sweep = wk->sweep;
         cudaError_t e = fp64 ? launch_propose_small<double>(s->dev, s->small_nm, qgrid, s->propose_warps, s->small_move_smem, Q, st)
                              : launch_propose_small<float>(s->dev, s->small_nm, qgrid, s->propose_warps, s->small_move_smem, Q, st);
@@ -1455,10 +1465,14 @@ int vmcf_sample(vmcf_system_t s, vmcf_walkers_t wk, int n_sweeps, double step_si
       Pp.nsweeps = 1;
       Pp.c0 = wk->counter;
       Pp.skip_final_refresh = k == nsw - 1 ? skip : 0;
+      {
+        Timed tm(wk, 4, st);
+        cudaError_t e = launch_propose_rows(*s, Q, st);
+        if (e != cudaSuccess) return cuda_fail(e, "proposal kernel launch");
+      }
       Timed tm(wk, 0, st);
-      cudaError_t e = fp64 ? launch_propose_group<double>(s->dev, Q, st) : launch_propose_group<float>(s->dev, Q, st);
-      if (e == cudaSuccess) e = fp64 ? launch_move<double>(s->dev, lm, Pp, st) : launch_move<float>(s->dev, lm, Pp, st);
-      if (e != cudaSuccess) return cuda_fail(e, "proposal or move kernel launch");
+      cudaError_t e = fp64 ? launch_move<double>(s->dev, lm, Pp, st) : launch_move<float>(s->dev, lm, Pp, st);
+      if (e != cudaSuccess) return cuda_fail(e, "move kernel launch");
       wk->sweep += 1;
       wk->counter = (int)((wk->counter + (long long)s->Ne) % refresh_k);
     }
@@ -1550,6 +1564,12 @@ int vmcf_block_sums(vmcf_system_t s, vmcf_walkers_t wk, double* out, void* strea
     VMCF_CUDA(cudaMemcpyAsync(&flag, wk->tc_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     VMCF_CUDA(cudaStreamSynchronize(st));
     if (flag) return fail(VMCF_ETIMEOUT, "tensor-core walker-sum kernel: a bounded wait timed out");
+  }
+  if (s->tcr_flag) {
+    int flag = 0;
+    VMCF_CUDA(cudaMemcpyAsync(&flag, s->tcr_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VMCF_CUDA(cudaStreamSynchronize(st));
+    if (flag) return fail(VMCF_ETIMEOUT, "tensor-core proposal kernel: a bounded wait timed out");
   }
   VMCF_CUDA(cudaMemcpyAsync(out, wk->blocks, 8 * (size_t)wk->nblocks * s->accL, cudaMemcpyDeviceToHost, st));
   VMCF_CUDA(cudaStreamSynchronize(st));
@@ -1777,6 +1797,12 @@ int vmcf_set_tuning(vmcf_system_t s, const char* key, int value) {
     s->group_prepass = value != 0;
     return VMCF_OK;
   }
+  if (k == "tensor_core_rows") {  // walker-group proposal pass, mixed precision: orbital rows on the tensor cores
+    if (value != 0 && !s->tcr_mem)
+      return fail(VMCF_EINVAL, "tensor-core orbital rows need mixed precision on the walker-group kernels");
+    s->tc_rows = value != 0;
+    return VMCF_OK;
+  }
   if (k == "move_lanes_per_walker") {
     if (value != 1 && value != 2 && value != 4 && value != 8) return fail(VMCF_EINVAL, "lanes per walker: 1, 2, 4 or 8");
     s->move_lpw = value;
@@ -1828,13 +1854,59 @@ int vmcf_kernel_times(vmcf_walkers_t wk, double* ms, long long* count, int reset
     cudaEventDestroy(ev.second.second);
   }
   wk->events.clear();
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 5; ++k) {
     if (ms) ms[k] = wk->kernel_ms[k];
     if (count) count[k] = wk->kernel_n[k];
     if (reset) {
       wk->kernel_ms[k] = 0.0;
       wk->kernel_n[k] = 0;
     }
+  }
+  return VMCF_OK;
+}
+
+int vmcf_diag_group_proposals(vmcf_walkers_t wk, double step_sigma, double* rnew, double* rows, double* u,
+                              double* dchi, void* stream) {
+  if (!wk || !rnew || !rows || !u || !dchi || !(step_sigma > 0.0)) return fail(VMCF_EINVAL, "bad arguments");
+  vmcf_system_s* s = wk->sys;
+  if (s->small || !wk->gprop) return fail(VMCF_EINVAL, "the proposal pass of the walker-group kernels only");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GroupProposeParams Q{};
+  Q.pos = wk->pos;
+  Q.prn = wk->g_rn;
+  Q.prow = wk->g_row;
+  Q.pu = wk->g_u;
+  Q.pdchi = wk->g_dchi;
+  Q.W = wk->W;
+  Q.wid0 = wk->wid0;
+  Q.k0 = wk->k0;
+  Q.k1 = wk->k1;
+  Q.sweep = wk->sweep;
+  Q.sigma = step_sigma;
+  if (wk->W == 0) return VMCF_OK;
+  cudaError_t e = launch_propose_rows(*s, Q, st);
+  if (e != cudaSuccess) return cuda_fail(e, "proposal kernel launch");
+  const size_t n = (size_t)wk->W * s->Ne, nr = n * s->nmax;
+  const bool fp64 = s->precision == VMCF_FP64;
+  std::vector<float> rf(fp64 ? 0 : nr), df(fp64 ? 0 : n);
+  VMCF_CUDA(cudaMemcpyAsync(rnew, wk->g_rn, 24 * n, cudaMemcpyDeviceToHost, st));
+  VMCF_CUDA(cudaMemcpyAsync(u, wk->g_u, 8 * n, cudaMemcpyDeviceToHost, st));
+  if (fp64) {
+    VMCF_CUDA(cudaMemcpyAsync(rows, wk->g_row, 8 * nr, cudaMemcpyDeviceToHost, st));
+    VMCF_CUDA(cudaMemcpyAsync(dchi, wk->g_dchi, 8 * n, cudaMemcpyDeviceToHost, st));
+  } else {
+    VMCF_CUDA(cudaMemcpyAsync(rf.data(), wk->g_row, 4 * nr, cudaMemcpyDeviceToHost, st));
+    VMCF_CUDA(cudaMemcpyAsync(df.data(), wk->g_dchi, 4 * n, cudaMemcpyDeviceToHost, st));
+  }
+  VMCF_CUDA(cudaStreamSynchronize(st));
+  if (!fp64) {
+    for (size_t i = 0; i < nr; ++i) rows[i] = rf[i];
+    for (size_t i = 0; i < n; ++i) dchi[i] = df[i];
+  }
+  if (s->tcr_flag) {
+    int flag = 0;
+    VMCF_CUDA(cudaMemcpy(&flag, s->tcr_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(VMCF_ETIMEOUT, "tensor-core proposal kernel: a bounded wait timed out");
   }
   return VMCF_OK;
 }

@@ -48,6 +48,14 @@ struct vmcf_system_s {
   bool tcg_sums = false;
   int tcg_Mf = 0, tcg_Nf = 0, tcg_nch = 1;
   vmcf::GroupLayout LmeasTC{};  // measurement layout that stages AO values instead of holding O
+  // walker-group path, mixed precision: orbital rows of the proposal pass on the tensor cores (k_tc_rows.cu)
+  bool tc_rows = false;
+  int tcr_Kp = 0, tcr_Np = 0;   // AO columns and orbital rows of the operands, padded to 16
+  size_t tcr_smem = 0;
+  int tcr_grid = 1;             // CTAs per spin
+  void* tcr_mem = nullptr;      // [spin][part][Np][Kp] bf16 split coefficients (part 0 hi, 1 lo), then the flag
+  int* tcr_flag = nullptr;      // set by a timed-out wait of the kernel
+  alignas(64) unsigned char tcr_map[128] = {};  // tensor map (CUtensorMap) over the split coefficients
 };
 
 struct vmcf_walkers_s {
@@ -84,11 +92,11 @@ struct vmcf_walkers_s {
   void* g_row = nullptr;
   double* g_u = nullptr;
   void* g_dchi = nullptr;
-  // per-kernel timing (kind 0 move, 1 measure, 2 refresh): event pairs around launches
+  // per-kernel timing (kind 0 move, 1 measure, 2 refresh, 3 tensor-core sums, 4 proposals): event pairs
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
-  double kernel_ms[4] = {0, 0, 0, 0};  // move, measure, refresh, tensor-core walker sums
-  long long kernel_n[4] = {0, 0, 0, 0};
+  double kernel_ms[5] = {0, 0, 0, 0, 0};  // move, measure, refresh, tensor-core walker sums, proposal pass
+  long long kernel_n[5] = {0, 0, 0, 0, 0};
 };
 
 
@@ -111,4 +119,9 @@ int refresh_walker_set(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st);
 // the sweep's schedule read from the geometry's device clock clk, for capture into a batch graph.
 cudaError_t small_sweep_launches(vmcf_system_s* s, vmcf_walkers_s* wk, const BatchClock* clk, int mode, int kref,
                                  double sigma, cudaStream_t st);
+// Tensor-core orbital rows of the walker-group proposal pass (k_tc_rows.cu): plan, buffer and tensor map at system
+// set-up; the split coefficients again after a geometry change; the proposal-pass launch of either precision.
+int tc_rows_setup(vmcf_system_s* s);
+int tc_rows_upload(vmcf_system_s* s);
+cudaError_t launch_propose_rows(const vmcf_system_s& s, const GroupProposeParams& P, cudaStream_t st);
 }  // namespace vmcf

@@ -104,6 +104,7 @@ def lib(build_if_missing: bool = True):
         L.vmcf_set_tuning.argtypes = [_vp, ctypes.c_char_p, ctypes.c_int]
         L.vmcf_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
         L.vmcf_probe_pipes.argtypes = [_dp, _dp, _dp, _vp]
+        L.vmcf_diag_group_proposals.argtypes = [_vp, ctypes.c_double, _dp, _dp, _dp, _dp, _vp]
         L.vmcf_set_guiding.argtypes = [_vp, ctypes.c_double]
         L.vmcf_evaluate_warp.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.vmcf_reduce_warp.argtypes = [_vp, _vp, _dp, _dp, _vp]
@@ -278,6 +279,18 @@ class Walkers:
         except Exception:
             pass
 
+    def group_proposals(self, sigma: float = 0.3, stream=None) -> dict:
+        """vmcf_diag_group_proposals: the proposal pass of the next sweep (walker-group kernels) as host arrays:
+        rnew (W, Ne, 3), rows (W, Ne, nmax), u (W, Ne), dchi (W, Ne). The chain does not advance."""
+        sx = self.system
+        Ne, nmax = sx.n_up + sx.n_dn, max(sx.n_up, sx.n_dn)
+        out = {"rnew": np.zeros((self.W, Ne, 3)), "rows": np.zeros((self.W, Ne, nmax)), "u": np.zeros((self.W, Ne)),
+               "dchi": np.zeros((self.W, Ne))}
+        _check(lib().vmcf_diag_group_proposals(self.h, float(sigma), *[out[k].ctypes.data_as(_dp) for k in
+                                                                        ("rnew", "rows", "u", "dchi")],
+                                                _stream(stream)), "vmcf_diag_group_proposals")
+        return out
+
     def set_positions(self, pos, stream=None):
         if isinstance(pos, np.ndarray):
             a = _np(pos, np.float64)
@@ -354,11 +367,11 @@ class Walkers:
         _check(lib().vmcf_profile(self.h, int(enable)), "vmcf_profile")
 
     def kernel_times(self, reset: bool = True) -> dict:
-        ms = (ctypes.c_double * 4)()
-        n = (ctypes.c_longlong * 4)()
+        ms = (ctypes.c_double * 5)()
+        n = (ctypes.c_longlong * 5)()
         _check(lib().vmcf_kernel_times(self.h, ms, n, int(reset)), "vmcf_kernel_times")
-        names = ("move", "measure", "refresh", "tc_sums")
-        return {names[k]: {"ms": float(ms[k]), "launches": int(n[k])} for k in range(4)}
+        names = ("move", "measure", "refresh", "tc_sums", "propose")
+        return {names[k]: {"ms": float(ms[k]), "launches": int(n[k])} for k in range(5)}
 
     def counters(self, stream=None) -> dict:
         c = Counters()
