@@ -550,12 +550,14 @@ def main():
         for _ in range(ke):
             wk.set_positions(host, stream=stream)          # H2D, inverses rebuilt
             wk.sample(1, 0.3, 26, measure=True, stream=stream)
-            _ = wk.reduce_estimators(stream=stream)         # D2H block sums + host finish
+            _ = wk.reduce_estimators(stream=stream)         # estimators finished on the device, D2H of the results
             wk.positions(stream=stream, out=host)           # D2H positions (pinned) for the next step
         barrier()
         te = max_over_ranks(time.perf_counter() - t0)
         h2d = W * sysx.Ne * 3 * 8
-        d2h = W * sysx.Ne * 3 * 8 + nb * g.accL * 8
+        # positions, and the estimators with their errors (E, F [3K], dE/dC [nO], each with its error bar) plus
+        # status flags; beyond 4096 jackknife blocks the block sums themselves come back instead
+        d2h = W * sysx.Ne * 3 * 8 + (8 * (2 + 6 * sysx.K + 2 * g.M * sysx.Ne) + 12 if nb <= 4096 else nb * g.accL * 8)
         line["e2e"] = {"value": ws * W * ke / te, "unit": "walker-evals/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "steps": ke}
         del wk, g

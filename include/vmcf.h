@@ -227,7 +227,10 @@ int vmcf_evaluate(vmcf_system_t sys, const double* pos, int W, double* EL, doubl
  * Q_projector, AZ_eq_B_elements). Host outputs
  * (any may be NULL): E, E_err (scalars), F, F_err [K][3], dEdC, dEdC_err [M*(n_up+n_dn)],
  * rhs_BQ [M*(n_up+n_dn)] = -sum_mu B_{mu i} Q_{mu nu} (needs S at init, else VMCF_EINVAL).
- * Error bars: delete-one-block jackknife over the walker blocks. */
+ * Error bars: delete-one-block jackknife over the walker blocks. With at most 4096 blocks the block
+ * sums, the estimators and their errors are formed on the device (the arithmetic of
+ * vmcf_finish_estimators, every sum over the blocks in block order) and only the results come back;
+ * beyond that the block sums are copied back and finished on the host. */
 int vmcf_reduce_estimators(vmcf_system_t sys, vmcf_walkers_t wk, double* E, double* E_err, double* F,
                            double* F_err, double* dEdC, double* dEdC_err, double* rhs_BQ, void* stream);
 /* Raw block sums (synchronises): host [nblocks][vmcf_accumulator_length()] doubles, layout
@@ -240,7 +243,8 @@ int vmcf_accumulator_length(vmcf_system_t sys);
 /* Host-only estimator finish (no GPU needed): Eqs. hf/pulay and fc-vmc-eval from block sums
  * `blocks` [nblocks][3 + 9K + 2 M (n_up + n_dn)] in the vmcf_block_sums layout, with e_ref the
  * reference energy the sums were taken with. This is what several ranks call after gathering
- * their block sums (the blocks of all ranks side by side); vmcf_reduce_estimators calls it too.
+ * their block sums (the blocks of all ranks side by side); vmcf_reduce_estimators follows the same
+ * arithmetic on the device.
  * Host outputs as in vmcf_reduce_estimators (any may be NULL). */
 int vmcf_finish_estimators(const double* blocks, int nblocks, int K, int M, int n_up, int n_dn, double e_ref,
                            double* E, double* E_err, double* F, double* F_err, double* dEdC, double* dEdC_err);

@@ -1226,6 +1226,7 @@ int vmcf_walkers_create(vmcf_system_t s, int W, const double* pos, int is_host, 
       (e = cudaMalloc(&wk->acc, 8 * (size_t)wk->grid_meas * s->accL)) ||
       (e = cudaMalloc(&wk->blocks, 8 * (size_t)nblocks * s->accL)) ||
       (e = cudaMallocHost(&wk->h_blocks, 8 * (size_t)nblocks * s->accL)) ||
+      (e = cudaMalloc(&wk->d_fin, 8 * fin_doubles(*s) + 16)) || (e = cudaMallocHost(&wk->h_fin, 8 * fin_doubles(*s) + 16)) ||
       (s->small && (e = cudaMalloc(&wk->stage, 8 * npos))) ||
       (s->small && s->precision == VMCF_MIXED && (e = cudaMalloc(&wk->posf, sizeof(float2) * npos))) ||
       (s->small && (e = alloc_proposals(s, wk))) ||
@@ -1268,6 +1269,8 @@ int vmcf_walkers_destroy(vmcf_walkers_t wk) {
   cudaFree(wk->acc);
   cudaFree(wk->blocks);
   cudaFreeHost(wk->h_blocks);
+  cudaFree(wk->d_fin);
+  cudaFreeHost(wk->h_fin);
   cudaFree(wk->stage);
   cudaFree(wk->posf);
   cudaFree(wk->prop);
@@ -1550,9 +1553,9 @@ int vmcf_evaluate(vmcf_system_t s, const double* pos, int W, double* EL, double*
   return VMCF_OK;
 }
 
-int vmcf_block_sums(vmcf_system_t s, vmcf_walkers_t wk, double* out, void* stream) {
-  if (!s || !wk || !out || wk->sys != s) return fail(VMCF_EINVAL, "bad arguments");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+namespace {
+// Per-block sums of a walker set's CTA slots on the device, with the tensor-core slots folded in.
+int reduce_blocks_on_device(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
   cudaError_t e = launch_block_reduce(wk->acc, wk->grid_meas, wk->cpb, s->accL, wk->blocks, wk->nblocks, st);
   if (e != cudaSuccess) return cuda_fail(e, "block reduce launch");
   if (wk->tc) {
@@ -1560,6 +1563,17 @@ int vmcf_block_sums(vmcf_system_t s, vmcf_walkers_t wk, double* out, void* strea
     e = launch_tc_fold(wk->tc_slots, wk->nblocks, wk->tc_cpb, s->small ? s->tc_Mp : s->tcg_Mf,
                        s->small ? s->tc_Np : s->tcg_Nf, s->M, s->nup, s->ndn, 3 + 9 * s->K, nO, s->accL, wk->blocks, st);
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core fold launch");
+  }
+  return VMCF_OK;
+}
+}  // namespace
+
+int vmcf_block_sums(vmcf_system_t s, vmcf_walkers_t wk, double* out, void* stream) {
+  if (!s || !wk || !out || wk->sys != s) return fail(VMCF_EINVAL, "bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int rc = reduce_blocks_on_device(s, wk, st);
+  if (rc != VMCF_OK) return rc;
+  if (wk->tc) {
     int flag = 0;
     VMCF_CUDA(cudaMemcpyAsync(&flag, wk->tc_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     VMCF_CUDA(cudaStreamSynchronize(st));
@@ -1735,11 +1749,80 @@ int vmcf_evaluate_warp(vmcf_system_t s, const double* pos, int W, double* dEL_dr
   return VMCF_OK;
 }
 
+namespace {
+// -B Q^s per spin from B (host): Q^s = 1 - C^s C^s^T S (Eq. Q_projector); rhs_{nu i} = -sum_mu B_{mu i} Q_{mu nu}
+int rhs_from_B(const vmcf_system_s* s, const std::vector<double>& Bv, double* rhs_BQ) {
+  const int M = s->M;
+  int ooff = 0;
+  for (int sg = 0; sg < 2; ++sg) {
+    const int n = sg == 0 ? s->nup : s->ndn;
+    const std::vector<double>& C = s->C[sg];
+    std::vector<double> CtB((size_t)n * n, 0.0);  // (C^T B)_{k i}
+    for (int k = 0; k < n; ++k)
+      for (int i = 0; i < n; ++i) {
+        double v = 0.0;
+        for (int mu = 0; mu < M; ++mu) v += C[(size_t)mu * n + k] * Bv[ooff + (size_t)mu * n + i];
+        CtB[(size_t)k * n + i] = v;
+      }
+    std::vector<double> SC((size_t)M * n, 0.0);  // (S C)_{nu k}
+    for (int nu = 0; nu < M; ++nu)
+      for (int k = 0; k < n; ++k) {
+        double v = 0.0;
+        for (int la = 0; la < M; ++la) v += s->S[(size_t)nu * M + la] * C[(size_t)la * n + k];
+        SC[(size_t)nu * n + k] = v;
+      }
+    for (int nu = 0; nu < M; ++nu)
+      for (int i = 0; i < n; ++i) {
+        double v = Bv[ooff + (size_t)nu * n + i];
+        for (int k = 0; k < n; ++k) v -= SC[(size_t)nu * n + k] * CtB[(size_t)k * n + i];
+        rhs_BQ[ooff + (size_t)nu * n + i] = -v;
+      }
+    ooff += M * n;
+  }
+  return VMCF_OK;
+}
+}  // namespace
+
 int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double* E_err, double* F, double* F_err,
                            double* dEdC, double* dEdC_err, double* rhs_BQ, void* stream) {
   if (!s || !wk || wk->sys != s) return fail(VMCF_EINVAL, "bad handles");
   if (rhs_BQ && !s->has_S) return fail(VMCF_EINVAL, "rhs_BQ needs the AO overlap S at init");
   const int L = s->accL, nb = wk->nblocks, nO = s->M * (s->nup + s->ndn);
+  thread_local std::vector<double> Bv;
+  if (nb <= kFinishMaxBlocks && wk->d_fin) {
+    // on the device: block sums, then the estimators and their jackknife errors (the host routine's arithmetic);
+    // only the results and the status flags come back, after one synchronisation
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = reduce_blocks_on_device(s, wk, st);
+    if (rc != VMCF_OK) return rc;
+    const int K3 = 3 * s->K;
+    const size_t fn = fin_doubles(*s);
+    int* dstat = reinterpret_cast<int*>(wk->d_fin + fn);
+    int* hflag = reinterpret_cast<int*>(wk->h_fin + fn);  // [0] finish status, [1] tensor-core sums, [2] rows
+    VMCF_CUDA(cudaMemsetAsync(dstat, 0, sizeof(int), st));
+    cudaError_t e = launch_finish(wk->blocks, nb, L, K3, nO, wk->e_ref, wk->d_fin, dstat, st);
+    if (e != cudaSuccess) return cuda_fail(e, "estimator finish launch");
+    hflag[1] = hflag[2] = 0;
+    VMCF_CUDA(cudaMemcpyAsync(wk->h_fin, wk->d_fin, 8 * fn + sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (wk->tc) VMCF_CUDA(cudaMemcpyAsync(hflag + 1, wk->tc_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (s->tcr_flag) VMCF_CUDA(cudaMemcpyAsync(hflag + 2, s->tcr_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VMCF_CUDA(cudaStreamSynchronize(st));
+    if (hflag[1]) return fail(VMCF_ETIMEOUT, "tensor-core walker-sum kernel: a bounded wait timed out");
+    if (hflag[2]) return fail(VMCF_ETIMEOUT, "tensor-core proposal kernel: a bounded wait timed out");
+    if (hflag[0] & 1) return fail(VMCF_EINVAL, "no measured samples");
+    if (hflag[0] & 2) return fail(VMCF_EINVAL, "a jackknife block holds every sample");
+    const double* o = wk->h_fin;
+    const double* Bo = o + 2 + 2 * K3;
+    if (E) *E = o[0];
+    if (E_err) *E_err = o[1];
+    if (F) std::copy(o + 2, o + 2 + K3, F);
+    if (F_err) std::copy(o + 2 + K3, o + 2 + 2 * K3, F_err);
+    if (dEdC) std::copy(Bo, Bo + nO, dEdC);
+    if (dEdC_err) std::copy(Bo + nO, Bo + 2 * nO, dEdC_err);
+    if (!rhs_BQ) return VMCF_OK;
+    Bv.assign(Bo, Bo + nO);
+    return rhs_from_B(s, Bv, rhs_BQ);
+  }
   // the block sums land in the walker set's pinned host buffer (a direct copy, no staging)
   int rc = vmcf_block_sums(s, wk, wk->h_blocks, stream);
   if (rc != VMCF_OK) return rc;
@@ -1751,43 +1834,12 @@ int vmcf_reduce_estimators(vmcf_system_t s, vmcf_walkers_t wk, double* E, double
     for (int b = 0; b < nb; ++b) std::copy(blk + (size_t)b * L, blk + (size_t)b * L + Lb, &base[(size_t)b * Lb]);
     blk = base.data();
   }
-  thread_local std::vector<double> Bv;
   Bv.resize(nO);
   rc = vmcf_finish_estimators(blk, nb, s->K, s->M, s->nup, s->ndn, wk->e_ref, E, E_err, F, F_err,
                               Bv.data(), dEdC_err);
   if (rc != VMCF_OK) return rc;
   if (dEdC) std::copy(Bv.begin(), Bv.end(), dEdC);
-  if (rhs_BQ) {
-    // Q^s = 1 - C^s C^s^T S (Eq. Q_projector); rhs_{nu i} = -sum_mu B_{mu i} Q_{mu nu}
-    const int M = s->M;
-    int ooff = 0;
-    for (int sg = 0; sg < 2; ++sg) {
-      const int n = sg == 0 ? s->nup : s->ndn;
-      const std::vector<double>& C = s->C[sg];
-      std::vector<double> CtB((size_t)n * n, 0.0);  // (C^T B)_{k i}
-      for (int k = 0; k < n; ++k)
-        for (int i = 0; i < n; ++i) {
-          double v = 0.0;
-          for (int mu = 0; mu < M; ++mu) v += C[(size_t)mu * n + k] * Bv[ooff + (size_t)mu * n + i];
-          CtB[(size_t)k * n + i] = v;
-        }
-      std::vector<double> SC((size_t)M * n, 0.0);  // (S C)_{nu k}
-      for (int nu = 0; nu < M; ++nu)
-        for (int k = 0; k < n; ++k) {
-          double v = 0.0;
-          for (int la = 0; la < M; ++la) v += s->S[(size_t)nu * M + la] * C[(size_t)la * n + k];
-          SC[(size_t)nu * n + k] = v;
-        }
-      for (int nu = 0; nu < M; ++nu)
-        for (int i = 0; i < n; ++i) {
-          double v = Bv[ooff + (size_t)nu * n + i];
-          for (int k = 0; k < n; ++k) v -= SC[(size_t)nu * n + k] * CtB[(size_t)k * n + i];
-          rhs_BQ[ooff + (size_t)nu * n + i] = -v;
-        }
-      ooff += M * n;
-    }
-  }
-  return VMCF_OK;
+  return rhs_BQ ? rhs_from_B(s, Bv, rhs_BQ) : VMCF_OK;
 }
 
 int vmcf_set_tuning(vmcf_system_t s, const char* key, int value) {

@@ -70,6 +70,10 @@ struct vmcf_walkers_s {
   double* acc = nullptr;                   // [grid_meas][accL]
   double* blocks = nullptr;                // [nblocks][accL]
   double* h_blocks = nullptr;              // pinned host copy of the block sums [nblocks][accL] (reductions)
+  // estimators finished on the device: [E, E_err, F [3K], F_err [3K], B [nO], B_err [nO]] then int flags
+  // (device: the finish status; pinned host copy: status, tensor-core sum flag, tensor-core row flag)
+  double* d_fin = nullptr;
+  double* h_fin = nullptr;
   uint64_t sweep = 0, measured = 0;
   int counter = 0;
   double e_ref = 0.0;
@@ -105,6 +109,8 @@ namespace vmcf {
 Launch launch_meas(const vmcf_system_s& s, int grid, bool accum, bool withD);
 // Offset of the space-warp sums in an accumulator slot (after the base fields), 0 if off.
 inline int swct_offset(const vmcf_system_s& s) { return s.swct ? 3 + 9 * s.K + 2 * s.M * (s.nup + s.ndn) : 0; }
+// Doubles of the estimators finished on the device: E, E_err, F and F_err (3K each), B and B_err (nO each).
+inline size_t fin_doubles(const vmcf_system_s& s) { return 2 + 6 * (size_t)s.K + 2 * (size_t)s.M * (s.nup + s.ndn); }
 // Walker-group shared-memory plans of the sweep and measurement kernels for group size GS.
 GroupLayout group_layout_rm(const vmcf_system_s& s, int GS);
 GroupLayout group_layout_meas(const vmcf_system_s& s, int GS);

@@ -269,6 +269,11 @@ cudaError_t launch_batch_advance(BatchClock* clk, int G, int mode, int kref, int
 
 cudaError_t run_probes(double* fp64_tflops, double* fp32_tflops, double* exp_gops, cudaStream_t st);
 
+// Estimators and jackknife errors of a walker set's block sums on the device (k_reduce.cu); blocks up to
+// kFinishMaxBlocks (shared memory of the per-block scalars).
+constexpr int kFinishMaxBlocks = 4096;
+cudaError_t launch_finish(const double* blk, int nb, int L, int K3, int nO, double er, double* out, int* status,
+                          cudaStream_t st);
 cudaError_t launch_block_reduce(const double* acc, int grid, int cpb, int accL, double* out, int nblocks,
                                 cudaStream_t st);
 

@@ -198,3 +198,25 @@ def test_group_proposal_pass_changes_no_chain(cfg, precision):
     np.testing.assert_array_equal(pa, pb)
     assert ca["accepted"] == cb["accepted"] and ca["refreshes"] == cb["refreshes"]
     assert rel(sa, sb) < (1e-12 if precision == vmcf.FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("cfg,precision,W,nb", [(0, vmcf.MIXED, 512, 64), (1, vmcf.FP64, 300, 7), (0, vmcf.FP64, 4100, 4097)])
+def test_device_estimator_finish_matches_the_host_finish(cfg, precision, W, nb):
+    """vmcf_reduce_estimators finishes the estimators and their jackknife errors on the device (up to 4096
+    blocks; beyond, on the host): the same values as the host routine vmcf_finish_estimators applied to
+    the same block sums, to 1e-12 (the same operations in the same order; only the FMA contraction of the
+    two compilers differs). 4097 blocks take the host path."""
+    from paper_2511_05222_gb300 import distributed
+    sx = S.make_system(cfg)
+    g = vmcf.System(sx, precision)
+    wk = vmcf.Walkers(g, S.initial_walkers(sx, W, seed=41), key=(5222, 41), nblocks=nb)
+    wk.sample(2, measure=False)
+    wk.reset_accumulators(-70.0 if cfg == 0 else -150.0)
+    wk.sample(2, measure=True)
+    got = wk.reduce_estimators()
+    ref = distributed.finish_estimators(wk.block_sums(), sx.K, g.M, sx.n_up, sx.n_dn, wk.e_ref)
+    assert abs(got["E"] - ref["E"]) <= 1e-12 * abs(ref["E"])
+    assert abs(got["E_err"] - ref["E_err"]) <= 1e-12 * ref["E_err"]
+    for k in ("F", "F_err", "dEdC", "dEdC_err"):
+        a, b = np.ravel(got[k]), np.ravel(ref[k])
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), k
