@@ -53,7 +53,8 @@ cudaError_t launch_tc_fold(const double* slots, int nblocks, int cpb, int Mf, in
 // the totals minus that block's row, the error sqrt((nb - 1)/nb sum_b (theta_b - mean)^2). One thread per
 // component c of (E, F [3K], B [nO]); out: [0] E, [1] E_err, then F [3K], F_err [3K], B [nO], B_err [nO].
 // Each CTA first forms the per-block scalars (leave-one-out sample count, mean E_L - E_ref, reciprocal count) in
-// shared memory ([2 nb + 2] doubles). status |= 1 when there are no samples, |= 2 when one block holds all of them.
+// shared memory ([2 nb + 2] doubles). The loops over the blocks are unrolled so that their loads overlap; the sums
+// keep their order. status |= 1 when there are no samples, |= 2 when one block holds all of them.
 __global__ void finish_kernel(const double* __restrict__ blk, int nb, int L, int K3, int nO, double er,
                               double* __restrict__ out, int* status) {
   extern __shared__ double fin_s[];
@@ -62,6 +63,7 @@ __global__ void finish_kernel(const double* __restrict__ blk, int nb, int L, int
   double* tots = fin_s + 2 * nb;  // [0] total count, [1] total E_L sum
   if (threadIdx.x == 0) {
     double t0 = 0.0, t1 = 0.0;
+#pragma unroll 8
     for (int b = 0; b < nb; ++b) {
       t0 += blk[(size_t)b * L];
       t1 += blk[(size_t)b * L + 1];
@@ -91,6 +93,7 @@ __global__ void finish_kernel(const double* __restrict__ blk, int nb, int L, int
     const int a0 = kind == 1 ? o_dEL + i : o_EO + i, a1 = kind == 1 ? o_Ed + i : o_O + i, a2 = o_d + i;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     if (kind != 0)
+#pragma unroll 8
       for (int b = 0; b < nb; ++b) {
         const double* v = blk + (size_t)b * L;
         s0 += v[a0];
@@ -104,12 +107,14 @@ __global__ void finish_kernel(const double* __restrict__ blk, int nb, int L, int
     };
     const double full = est(s0, s1, s2, in, c, Em);
     double m = 0.0;
+#pragma unroll 8
     for (int b = 0; b < nb; ++b) {
       const double* v = blk + (size_t)b * L;
       m += est(s0 - v[a0], s1 - v[a1], kind == 1 ? s2 - v[a2] : 0.0, inb[b], emb[b] - er, emb[b]);
     }
     m /= nb;
     double var = 0.0;
+#pragma unroll 8
     for (int b = 0; b < nb; ++b) {
       const double* v = blk + (size_t)b * L;
       const double d = est(s0 - v[a0], s1 - v[a1], kind == 1 ? s2 - v[a2] : 0.0, inb[b], emb[b] - er, emb[b]) - m;

@@ -461,7 +461,8 @@ int do_refresh(vmcf_system_s* s, vmcf_walkers_s* wk, cudaStream_t st) {
     P.mode = 0;
     P.Bout = wk->B;
     P.counters = wk->counters;
-    int rc = launch_small_measure(s, eval_grid(*s, wk->W), P, st);
+    // one wave of resident CTAs, each taking a contiguous range of walkers (no partial last wave)
+    int rc = launch_small_measure(s, std::max(1, std::min(eval_grid(*s, wk->W), s->small_res)), P, st);
     if (rc != VMCF_OK) return rc;
     wk->counter = 0;
     return VMCF_OK;
