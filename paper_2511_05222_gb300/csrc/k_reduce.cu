@@ -136,7 +136,9 @@ __global__ void finish_kernel(const double* __restrict__ blk, int nb, int L, int
 
 cudaError_t launch_finish(const double* blk, int nb, int L, int K3, int nO, double er, double* out, int* status,
                           cudaStream_t st) {
-  const int nc = 1 + K3 + nO, threads = 128;
+  // one warp per CTA: each thread's loops carry FP64 work (about 3 x nb estimates), which takes the SM's FP64 pipe
+  // for a whole warp instruction per operation, so the components are spread over as many SMs as they fill
+  const int nc = 1 + K3 + nO, threads = 32;
   const int grid = (nc + threads - 1) / threads;
   finish_kernel<<<grid, threads, (size_t)(2 * nb + 2) * sizeof(double), st>>>(blk, nb, L, K3, nO, er, out, status);
   return cudaGetLastError();
