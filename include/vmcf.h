@@ -286,6 +286,16 @@ int vmcf_finish_covariance(const double* blocks, int nblocks, int K, int M, int 
  * estimators; they show whether the chain is healthy (acceptance rate, walkers on a node). */
 int vmcf_status_counters(vmcf_walkers_t wk, vmcf_counters* out, void* stream);
 
+/* Refresh residual: how far the walker set's current inverses (Sherman-Morrison-updated since the
+ * last FP64 re-inversion, the S6/S7 steps of the sampler in App. A) are from a fresh FP64
+ * re-inversion of its current positions. Per walker the normwise deviation
+ * max_k |B_k - B^fresh_k| / max_k |B^fresh_k| over both spin blocks' entries; outputs (either may be
+ * NULL): max_rel the largest over the walkers, mean_rel their mean. The walker state is not changed
+ * (the fresh inverses go to a temporary device buffer, allocated and freed inside the call; the
+ * counters are not touched). Synchronises the stream. 0 right after a re-inversion (the same kernel
+ * forms both), of order the working precision times the moves since then otherwise. W = 0: both 0. */
+int vmcf_refresh_residual(vmcf_walkers_t wk, double* max_rel, double* mean_rel, void* stream);
+
 /* Checkpoint and resume of a walker set, between library calls. A checkpoint holds everything
  * the chains and the accumulated sums depend on: positions, the current inverses (as the
  * Sherman-Morrison updates left them, so a chain resumes anywhere, not only after a

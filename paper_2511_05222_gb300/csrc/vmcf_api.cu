@@ -1970,6 +1970,66 @@ int vmcf_probe_pipes(double* fp64_tflops, double* fp32_tflops, double* exp_gops,
   return VMCF_OK;
 }
 
+int vmcf_refresh_residual(vmcf_walkers_t wk, double* max_rel, double* mean_rel, void* stream) {
+  if (!wk) return fail(VMCF_EINVAL, "NULL walkers");
+  vmcf_system_s* s = wk->sys;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (max_rel) *max_rel = 0.0;
+  if (mean_rel) *mean_rel = 0.0;
+  const int W = wk->W, nB = s->nB;
+  if (W == 0) return VMCF_OK;
+  const bool fp64 = s->precision == VMCF_FP64;
+  const size_t tsz = fp64 ? 8 : 4, bytes = tsz * (size_t)W * nB;
+  void* fresh = nullptr;
+  VMCF_CUDA(cudaMalloc(&fresh, bytes));
+  // fresh inverses of the current positions into the temporary buffer, with the walker set's own re-inversion
+  // kernel; the evaluation's scratch counters take the kernel's counts
+  cudaError_t e;
+  if (s->small) {
+    SmallMeasParams P = small_params(*s, W);
+    P.pos = wk->pos;
+    P.pos_sk = W;
+    P.pos_sw = 1;
+    P.mode = 0;
+    P.Bout = fresh;
+    P.counters = reinterpret_cast<unsigned long long*>(s->scratch_counters);
+    e = fp64 ? launch_measure_small<double>(s->dev, s->small_nm, s->SL, eval_grid(*s, W), s->small_warps, P, st)
+             : launch_measure_small<float>(s->dev, s->small_nm, s->SL, eval_grid(*s, W), s->small_warps, P, st);
+  } else {
+    const Launch lc = launch_rm(*s, W);
+    e = fp64 ? launch_refresh<double>(s->dev, lc, wk->pos, fresh, W,
+                                      reinterpret_cast<unsigned long long*>(s->scratch_counters), st)
+             : launch_refresh<float>(s->dev, lc, wk->pos, fresh, W,
+                                     reinterpret_cast<unsigned long long*>(s->scratch_counters), st);
+  }
+  std::vector<unsigned char> cur(bytes), frs(bytes);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cur.data(), wk->B, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(frs.data(), fresh, bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(fresh);
+  if (e != cudaSuccess) return cuda_fail(e, "refresh residual");
+  // entry k of walker w: [k][W] (one-warp kernels, walker-interleaved) or [W][nB] (walker groups)
+  auto at = [&](const std::vector<unsigned char>& v, int w, int k) -> double {
+    const size_t i = s->small ? (size_t)k * W + w : (size_t)w * nB + k;
+    return fp64 ? reinterpret_cast<const double*>(v.data())[i] : (double)reinterpret_cast<const float*>(v.data())[i];
+  };
+  double mx = 0.0, sum = 0.0;
+  for (int w = 0; w < W; ++w) {
+    double dmax = 0.0, bmax = 0.0;
+    for (int k = 0; k < nB; ++k) {
+      const double b = at(frs, w, k);
+      dmax = std::max(dmax, std::fabs(at(cur, w, k) - b));
+      bmax = std::max(bmax, std::fabs(b));
+    }
+    const double r = bmax > 0.0 ? dmax / bmax : dmax;
+    mx = std::max(mx, r);
+    sum += r;
+  }
+  if (max_rel) *max_rel = mx;
+  if (mean_rel) *mean_rel = sum / W;
+  return VMCF_OK;
+}
+
 int vmcf_status_counters(vmcf_walkers_t wk, vmcf_counters* out, void* stream) {
   if (!wk || !out) return fail(VMCF_EINVAL, "bad arguments");
   cudaStream_t st = static_cast<cudaStream_t>(stream);

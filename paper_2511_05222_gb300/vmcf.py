@@ -105,6 +105,7 @@ def lib(build_if_missing: bool = True):
         L.vmcf_kernel_times.argtypes = [_vp, _dp, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
         L.vmcf_probe_pipes.argtypes = [_dp, _dp, _dp, _vp]
         L.vmcf_diag_group_proposals.argtypes = [_vp, ctypes.c_double, _dp, _dp, _dp, _dp, _vp]
+        L.vmcf_refresh_residual.argtypes = [_vp, _dp, _dp, _vp]
         L.vmcf_set_guiding.argtypes = [_vp, ctypes.c_double]
         L.vmcf_evaluate_warp.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.vmcf_reduce_warp.argtypes = [_vp, _vp, _dp, _dp, _vp]
@@ -372,6 +373,14 @@ class Walkers:
         _check(lib().vmcf_kernel_times(self.h, ms, n, int(reset)), "vmcf_kernel_times")
         names = ("move", "measure", "refresh", "tc_sums", "propose")
         return {names[k]: {"ms": float(ms[k]), "launches": int(n[k])} for k in range(5)}
+
+    def refresh_residual(self, stream=None) -> dict:
+        """vmcf_refresh_residual: normwise deviation of the current inverses from a fresh FP64 re-inversion of the
+        current positions, per walker; its maximum and mean over the walkers."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().vmcf_refresh_residual(self.h, ctypes.byref(a), ctypes.byref(b), _stream(stream)),
+               "vmcf_refresh_residual")
+        return {"max": a.value, "mean": b.value}
 
     def counters(self, stream=None) -> dict:
         c = Counters()

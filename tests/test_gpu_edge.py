@@ -220,3 +220,30 @@ def test_device_estimator_finish_matches_the_host_finish(cfg, precision, W, nb):
     for k in ("F", "F_err", "dEdC", "dEdC_err"):
         a, b = np.ravel(got[k]), np.ravel(ref[k])
         assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), k
+
+
+@pytest.mark.parametrize("precision", [vmcf.FP64, vmcf.MIXED])
+@pytest.mark.parametrize("force_group", [False, True])
+def test_refresh_residual(precision, force_group):
+    """vmcf_refresh_residual: exactly 0 right after a re-inversion (the walker set's creation runs the
+    same kernel on the same positions), and after a sweep of Sherman-Morrison updates without one
+    (k = 1000 > the 10 moves) of the order of the working precision: FP64 below 1e-8; mixed above 0,
+    on average below 1e-3. The call leaves the walker set unchanged: its chain continues as that of
+    a walker set that never made it."""
+    sx = S.make_system(0)
+    pos = S.initial_walkers(sx, 64, seed=51)
+    g = vmcf.System(sx, precision, force_group=force_group)
+    wk = vmcf.Walkers(g, pos, key=(5222, 51), nblocks=4)
+    r0 = wk.refresh_residual()
+    assert r0["max"] == 0.0 and r0["mean"] == 0.0
+    wk.sample(1, 0.3, 1000, measure=False)
+    r1 = wk.refresh_residual()
+    assert r1["mean"] <= r1["max"]
+    if precision == vmcf.FP64:
+        assert r1["max"] < 1e-8, r1
+    else:
+        assert r1["max"] > 0.0 and r1["mean"] < 1e-3, r1
+    wk.sample(2, 0.3, 1000, measure=False)
+    wk2 = vmcf.Walkers(vmcf.System(sx, precision, force_group=force_group), pos, key=(5222, 51), nblocks=4)
+    wk2.sample(3, 0.3, 1000, measure=False)
+    np.testing.assert_array_equal(wk.positions(), wk2.positions())
