@@ -233,7 +233,8 @@ def test_mixed_estimators_within_a_tenth_of_their_error_bars(cfg):
 def test_tensor_core_walker_sums_match_simt(cfg, force_group):
     """The tcgen05 GEMM that forms sum_w O_w and sum_w (E_L - E_ref) O_w (bf16 operands, FP32
     accumulation; tiles of 128 AOs x 32 columns, chunks of 16 electrons) against the SIMT sums
-    of the same kernel family, on the same configurations."""
+    of the same kernel family, on the same configurations, and (water, C2OH6) against the
+    oracle's FP64 sums on them."""
     sysx = S.make_system(cfg)
     W = 2048 if cfg != 4 else 512
     if cfg != 4:
@@ -265,6 +266,16 @@ def test_tensor_core_walker_sums_match_simt(cfg, force_group):
         assert rel(a[:, sec], b[:, sec]) < (1e-2 if cfg != 4 else 2e-2), rel(a[:, sec], b[:, sec])
         # per-element agreement well beyond chance: correlation of the two sum vectors
         assert np.corrcoef(a[:, sec].ravel(), b[:, sec].ravel())[0, 1] > 0.9999
+    if cfg != 4:
+        # the tensor-core sums against the oracle's FP64 sums of O and (E_L - E_ref) O over the same
+        # configurations (two measurements: twice each sum), to the same bf16 tolerance
+        ref = o.eval(pos, want=("EL", "O"))
+        e_ref = {0: -70.0, 1: -150.0}[cfg]
+        so = 2.0 * ref["O"].sum(0)
+        seo = 2.0 * ((ref["EL"] - e_ref)[:, None] * ref["O"]).sum(0)
+        at = a.sum(0)
+        assert rel(at[oo:oo + nO], so) < 1e-2, rel(at[oo:oo + nO], so)
+        assert rel(at[oo + nO:oo + 2 * nO], seo) < 1e-2, rel(at[oo + nO:oo + 2 * nO], seo)
 
 
 
