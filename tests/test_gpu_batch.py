@@ -76,41 +76,43 @@ def test_batch_follows_the_single_geometry_path(ragged, precision):
 
 @pytest.mark.parametrize("small", [False, True])
 def test_batch_estimators_match_the_oracle(ragged, small):
-    """The water geometry inside a ragged FP64 batch, on the walker-group kernels or (small) on the
-    small-system kernels in a branch of the batch graph: chain and estimators as the oracle's."""
+    """Three geometries of different sizes in one ragged FP64 batch (water, 10 electrons, on the
+    walker-group kernels or (small) on the small-system kernels in a branch of the batch graph; a
+    38- and a 76-electron molecule on walker-group kernels of 32 and 128 threads per walker): every
+    geometry's chain and estimators as the oracle's."""
     specs = [(ragged[0][0], 128), (ragged[1][0], 32), (ragged[2][0], 16)]
-    sys0 = specs[0][0]
-    W, nb, warm, meas, e_ref = 128, 8, 3, 3, -76.0
+    nbs, keys, e_refs = (8, 4, 4), [(5222, 0), (5222, 10), (5222, 11)], (-76.0, -150.0, -300.0)
+    warm, meas = 3, 3
     systems = [vmcf.System(sx, vmcf.FP64, force_group=not (small and g == 0)) for g, (sx, _) in enumerate(specs)]
-    pos = S.initial_walkers(sys0, W, seed=10)
-    wk = [vmcf.Walkers(systems[0], pos, key=(5222, 0), nblocks=nb)]
-    wk += [vmcf.Walkers(systems[g], S.initial_walkers(specs[g][0], specs[g][1], seed=g), key=(5222, 9 + g),
-                        nblocks=4) for g in (1, 2)]
+    pos = [S.initial_walkers(sx, W, seed=10 + g) for g, (sx, W) in enumerate(specs)]
+    wk = [vmcf.Walkers(systems[g], pos[g], key=keys[g], nblocks=nbs[g]) for g in range(3)]
     batch = vmcf.Batch(systems, wk)
-    o = oracle.Oracle(sys0)
-    st = o.new_state(pos, key=(5222, 0))
-    o.sample(st, warm)
     batch.sample(warm, measure=False)
     for g, w in enumerate(wk):
-        w.reset_accumulators(e_ref if g == 0 else -100.0)
+        w.reset_accumulators(e_refs[g])
     batch.sample(meas, measure=True)
-    sums = estimators.new_sums(nb, sys0.K, o.nO)
-    blk = np.zeros(W, dtype=np.int64)
-    for b in range(nb):
-        blk[(W * b) // nb:(W * (b + 1)) // nb] = b
-    for _ in range(meas):
-        o.sample(st, 1)
-        o.force_refresh(st)
-        out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
-        estimators.accumulate(sums, blk, out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], e_ref)
-    assert st["margin"].min() >= 1e-9
-    assert np.abs(wk[0].positions() - st["pos"]).max() < 1e-9
-    ref = estimators.finish(sums, e_ref)
-    got = wk[0].reduce_estimators()
-    assert abs(got["E"] - ref["E"]) < 1e-10 * abs(ref["E"])
-    assert rel(got["F"].ravel(), ref["F"]) < 1e-9
-    assert rel(got["dEdC"], ref["dEdC"]) < 1e-9
-    assert abs(got["E_err"] - ref["E_err"]) < 1e-8 * ref["E_err"]
+    for g, (sx, W) in enumerate(specs):
+        o = oracle.Oracle(sx)
+        st = o.new_state(pos[g], key=keys[g])
+        o.sample(st, warm)
+        nb = nbs[g]
+        sums = estimators.new_sums(nb, sx.K, o.nO)
+        blk = np.zeros(W, dtype=np.int64)
+        for b in range(nb):
+            blk[(W * b) // nb:(W * (b + 1)) // nb] = b
+        for _ in range(meas):
+            o.sample(st, 1)
+            o.force_refresh(st)
+            out = o.eval(st["pos"], want=("EL", "dlnpsi_dR", "dEL_dR", "O"))
+            estimators.accumulate(sums, blk, out["EL"], out["dlnpsi_dR"], out["dEL_dR"], out["O"], e_refs[g])
+        assert st["margin"].min() >= 1e-9, g  # every decision clear of a tie: the chains are the same
+        assert np.abs(wk[g].positions() - st["pos"]).max() < 1e-9, g
+        ref = estimators.finish(sums, e_refs[g])
+        got = wk[g].reduce_estimators()
+        assert abs(got["E"] - ref["E"]) < 1e-10 * abs(ref["E"]), g
+        assert rel(got["F"].ravel(), ref["F"]) < 1e-9, g
+        assert rel(got["dEdC"], ref["dEdC"]) < 1e-9, g
+        assert abs(got["E_err"] - ref["E_err"]) < 1e-8 * ref["E_err"], g
     if small:
         assert batch.info()["geometries"][0]["bucket"] == -1
 
