@@ -356,15 +356,25 @@ int vmcf_walkers_load(vmcf_walkers_t wk, const void* buf, uint64_t bytes, void* 
 int vmcf_evaluate_sums_noalloc(vmcf_system_t sys, const double* pos, int W, double e_ref, double* sums,
                                void* stream);
 
-/* Launch-shape knobs of a system (not part of the paper's method; results are unchanged):
+/* Launch-shape and kernel-choice knobs of a system (not part of the paper's method). The launch
+ * shapes leave every result unchanged; the two tensor-core switches change mixed-precision results
+ * by rounding only:
  *   "move_lanes_per_walker": 1, 2, 4 or 8 lanes share one walker in the Metropolis kernel of
  *                            the small-system path (default 2);
  *   "measure_warps":         2, 4 or 8 walkers (one warp each) per CTA of the small-system
  *                            measurement kernel (default: the most that fit shared memory, up to 8);
+ *   "measure_group_size":    32, 128 or 256 threads per walker in the walker-group measurement
+ *                            kernel (default from the orbital count);
+ *   "group_proposal_pass":   1: walker-group sweeps take their proposals from a pass over every
+ *                            (walker, electron) ahead of the sweep (default); 0: drawn inside the
+ *                            sweep kernel, with the same arithmetic as the SIMT pass;
  *   "tensor_core_sums":      1: in mixed precision, the walker sums of O and (E_L - E_ref) O are
  *                            one bf16 GEMM on the tensor cores (tcgen05, FP32 accumulation in
- *                            tensor memory, FP64 across CTAs); 0: FP32 SIMT sums (default 1 where
- *                            the AOs fit 128 rows and 2 n_up fits 32 columns).
+ *                            tensor memory, FP64 across CTAs); 0: FP32 SIMT sums (default 1);
+ *   "tensor_core_rows":      1: in mixed precision on the walker-group kernels, the orbital rows
+ *                            of that proposal pass are a split-bf16 GEMM on the tensor cores
+ *                            (default where the tile fits shared memory); 0: FP32 SIMT rows;
+ *                            VMCF_EINVAL where the system has no tensor-core form of them.
  * Takes effect for walker sets created afterwards (measure_warps) or at the next call. */
 int vmcf_set_tuning(vmcf_system_t sys, const char* key, int value);
 
